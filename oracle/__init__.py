@@ -1,0 +1,187 @@
+"""CPU oracle for sigma = H c over a sorted determinant list.
+
+TEST INFRASTRUCTURE ONLY.  Only tests/, the smoke check and the CPU-baseline leg of the
+benchmark may import this package.  It shares no code with the CUDA path: the C library
+``sciref.c`` evaluates Slater-Condon elements by explicit operator application
+(paper Sec. 2.1, Eq. Hamiltonian) and finds connections by generation + binary search;
+``fock_route`` assembles H literally from the second-quantised operators.
+
+Parity status: every function here is pinned by tests/test_oracle_pins.py (closed forms,
+textbook limits, invariances, an independent NumPy route and brute force).  The paper's
+own molecular energies need integrals that are not available, so real-molecule parity
+is unpinned (stated in the design notes).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sciref.c")
+_LIB_PATH = os.path.join(_HERE, "libsciref.so")
+_lock = threading.Lock()
+_lib = None
+
+SCIREF_OK = 0
+SCIREF_ERR_CAP = -8
+
+
+def build(force: bool = False) -> str:
+    """Compile sciref.c into oracle/libsciref.so (plain gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-shared", "-fPIC",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB_PATH)
+            vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+            L.sciref_create.argtypes = [ctypes.POINTER(vp), i32, i32, i32, vp, vp]
+            L.sciref_destroy.argtypes = [vp]
+            L.sciref_destroy.restype = None
+            L.sciref_set_determinants.argtypes = [vp, vp, i64]
+            L.sciref_diagonal.argtypes = [vp, vp]
+            L.sciref_hij.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, vp]
+            L.sciref_connections.argtypes = [vp, i64, vp, vp, vp, vp, i64]
+            L.sciref_row_elements.argtypes = [vp, i64, vp, vp, vp, i64]
+            L.sciref_count_pairs.argtypes = [vp, i64, i64, vp]
+            L.sciref_sigma_rows.argtypes = [vp, vp, i64, vp, i32, vp]
+            L.sciref_sigma_brute_rows.argtypes = [vp, vp, i64, vp, i32, vp]
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class Oracle:
+    """One Hamiltonian (h, dense (pq|rs)) plus one sorted determinant list.
+
+    mode: "spin_orbitals" (n spatial orbitals, real) or "spinors" (n spinors, complex).
+    h: n x n; eri: n x n x n x n in Mulliken order [p,q,r,s] = (pq|rs).
+    """
+
+    def __init__(self, mode: str, n: int, h: np.ndarray, eri: np.ndarray, keys=None):
+        self.L = _load()
+        self.mode = mode
+        self.is_complex = bool(np.iscomplexobj(h) or np.iscomplexobj(eri))
+        self.dtype = np.complex128 if self.is_complex else np.float64
+        hh = np.ascontiguousarray(h, dtype=self.dtype)
+        ee = np.ascontiguousarray(eri, dtype=self.dtype)
+        self._h, self._eri = hh, ee
+        self.ctx = ctypes.c_void_p()
+        rc = self.L.sciref_create(ctypes.byref(self.ctx), int(self.is_complex),
+                                  int(mode == "spinors"), int(n), _ptr(hh), _ptr(ee))
+        if rc != SCIREF_OK:
+            raise ValueError(f"sciref_create failed ({rc})")
+        self.M = 0
+        if keys is not None:
+            self.set_determinants(keys)
+
+    @classmethod
+    def from_workload(cls, w):
+        return cls(w.mode, w.n, w.ints.h, w.ints.eri(), w.keys)
+
+    def __del__(self):
+        if getattr(self, "ctx", None):
+            self.L.sciref_destroy(self.ctx)
+            self.ctx = None
+
+    def set_determinants(self, keys):
+        self.keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        rc = self.L.sciref_set_determinants(self.ctx, _ptr(self.keys), len(self.keys))
+        if rc != SCIREF_OK:
+            raise ValueError(f"sciref_set_determinants failed ({rc})")
+        self.M = len(self.keys)
+
+    def diagonal(self) -> np.ndarray:
+        out = np.zeros(self.M, dtype=self.dtype)
+        self.L.sciref_diagonal(self.ctx, _ptr(out))
+        return out
+
+    def hij(self, bra: int, ket: int):
+        out = np.zeros(1, dtype=self.dtype)
+        self.L.sciref_hij(self.ctx, ctypes.c_uint64(int(bra)), ctypes.c_uint64(int(ket)), _ptr(out))
+        return out[0]
+
+    def connections(self, row: int):
+        cnt = np.zeros(1, dtype=np.int64)
+        cap = 1 << 12
+        while True:
+            J = np.zeros(cap, dtype=np.int64)
+            deg = np.zeros(cap, dtype=np.int8)
+            ph = np.zeros(cap, dtype=np.int8)
+            rc = self.L.sciref_connections(self.ctx, int(row), _ptr(cnt), _ptr(J), _ptr(deg), _ptr(ph), cap)
+            if rc == SCIREF_ERR_CAP:
+                cap = int(cnt[0])
+                continue
+            if rc != SCIREF_OK:
+                raise ValueError(rc)
+            n = int(cnt[0])
+            return J[:n], deg[:n], ph[:n]
+
+    def row_elements(self, row: int):
+        cnt = np.zeros(1, dtype=np.int64)
+        cap = 1 << 12
+        while True:
+            J = np.zeros(cap, dtype=np.int64)
+            hv = np.zeros(cap, dtype=self.dtype)
+            rc = self.L.sciref_row_elements(self.ctx, int(row), _ptr(cnt), _ptr(J), _ptr(hv), cap)
+            if rc == SCIREF_ERR_CAP:
+                cap = int(cnt[0])
+                continue
+            if rc != SCIREF_OK:
+                raise ValueError(rc)
+            n = int(cnt[0])
+            return J[:n], hv[:n]
+
+    def count_pairs(self, row_begin: int = 0, row_end: int | None = None) -> int:
+        row_end = self.M if row_end is None else row_end
+        out = np.zeros(1, dtype=np.int64)
+        rc = self.L.sciref_count_pairs(self.ctx, int(row_begin), int(row_end), _ptr(out))
+        if rc != SCIREF_OK:
+            raise ValueError(rc)
+        return int(out[0])
+
+    def _sigma(self, fn, rows, C):
+        C = np.ascontiguousarray(C, dtype=self.dtype)
+        if C.ndim == 1:
+            C = C[:, None]
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        S = np.zeros((len(rows), C.shape[1]), dtype=self.dtype)
+        rc = fn(self.ctx, _ptr(rows), len(rows), _ptr(C), C.shape[1], _ptr(S))
+        if rc != SCIREF_OK:
+            raise ValueError(rc)
+        return S
+
+    def sigma_rows(self, rows, C) -> np.ndarray:
+        """sigma restricted to `rows` (generation + lookup route)."""
+        return self._sigma(self.L.sciref_sigma_rows, rows, C)
+
+    def sigma_brute_rows(self, rows, C) -> np.ndarray:
+        """sigma restricted to `rows` (all-pairs route)."""
+        return self._sigma(self.L.sciref_sigma_brute_rows, rows, C)
+
+    def sigma(self, C) -> np.ndarray:
+        return self.sigma_rows(np.arange(self.M), C)
+
+    def dense(self) -> np.ndarray:
+        """Dense H on the list (small spaces only)."""
+        H = np.zeros((self.M, self.M), dtype=self.dtype)
+        H[np.arange(self.M), np.arange(self.M)] = self.diagonal()
+        for r in range(self.M):
+            J, hv = self.row_elements(r)
+            H[r, J] = hv
+        return H

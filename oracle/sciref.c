@@ -1,0 +1,435 @@
+/*
+ * sciref.c -- plain CPU oracle for sigma = H c over a sorted determinant list.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark load this library.  It shares no code, header, table or helper with the
+ * CUDA path; it is slow on purpose and written to be checked against the paper by eye.
+ *
+ * What it computes (paper, Sec. 2.1, Eq. Hamiltonian and Eq. sym_op):
+ *   H = sum_pq h_pq a+_p a_q + 1/2 sum_pqrs (pq|rs) a+_p a+_r a_s a_q      (Mulliken)
+ *   sigma_I = sum_J <D_I|H|D_J> c_J                                          (Sec. 2.4,
+ *             the diagonalisation paragraph: H is applied through matrix-vector
+ *             products with elements recomputed when needed, never stored)
+ *
+ * Determinants and phases.  A determinant is a 64-bit occupation string; bit p is
+ * spin-orbital (or spinor) p.  |D> = a+_{p1} a+_{p2} ... |0> with p1 < p2 < ... in bit
+ * order.  Spin-orbital mode with n spatial orbitals: bit p < n is alpha orbital p, bit
+ * n + p is beta orbital p, and the spatial integrals are expanded to spin-orbital ones
+ * with (pq|rs) nonzero only for spin(p) = spin(q) and spin(r) = spin(s).
+ *
+ * Matrix elements (Slater-Condon rules, derived from the operator form above):
+ *   diagonal:  H_II = sum_{i in occ} h_ii + 1/2 sum_{i,j in occ} [(ii|jj) - (ij|ji)]
+ *   single I = a+_a a_i J:
+ *              H_IJ = s [ h_ai + sum_{k in occ(J), k != i} ((ai|kk) - (ak|ki)) ]
+ *   double I = a+_b a+_a a_i a_j J (i<j, a<b; a_j applied first):
+ *              H_IJ = s [ (ai|bj) - (aj|bi) ]
+ *   s is the sign picked up while applying the operators one at a time to the ket
+ *   string: each a_p or a+_p passes over the occupied orbitals below p, counted with an
+ *   explicit loop over bits.
+ *
+ * Connections of row I are found by generating every single and double excitation of
+ * D_I (spin-orbital mode: only those conserving the numbers of alpha and beta
+ * electrons) and looking each up in the sorted list (binary search).  An independent
+ * all-pairs route (sciref_sigma_brute_rows) tests every J of the list instead.
+ * Rows are independent and are run in parallel with OpenMP.
+ */
+#include <complex.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define SCIREF_OK 0
+#define SCIREF_ERR_ARG (-1)
+#define SCIREF_ERR_UNSORTED (-2)
+#define SCIREF_ERR_CAP (-8)
+
+typedef double complex zd;
+
+typedef struct sciref_ctx {
+    int is_complex;   /* 0: real FP64 scalars, 1: complex128 scalars */
+    int spinors;      /* 0: spin-orbital mode, 1: spinor mode */
+    int n;            /* spatial orbitals or spinors */
+    int norb;         /* bits in use: 2n (spin-orbital) or n (spinor) */
+    zd *h;            /* norb x norb */
+    zd *eri;          /* norb^4, [p][q][r][s] = (pq|rs) */
+    uint64_t *keys;
+    int64_t M;
+} sciref_ctx;
+
+static int spin_of(const sciref_ctx *c, int p) { return c->spinors ? 0 : (p >= c->n); }
+static int spatial_of(const sciref_ctx *c, int p) { return c->spinors ? p : (p % c->n); }
+
+static zd H1(const sciref_ctx *c, int p, int q) { return c->h[(size_t)p * c->norb + q]; }
+static zd ERI(const sciref_ctx *c, int p, int q, int r, int s)
+{
+    size_t m = (size_t)c->norb;
+    return c->eri[((p * m + q) * m + r) * m + s];
+}
+
+/* ------------------------------------------------------------------ creation */
+/* h: n*n, eri: n^4 (row-major, [p][q][r][s] = (pq|rs)); complex data interleaved re,im.
+ * Spin-orbital mode expands them to the 2n spin-orbitals. */
+int sciref_create(sciref_ctx **out, int is_complex, int spinors, int n,
+                  const double *h, const double *eri)
+{
+    if (!out || !h || !eri || n <= 0) return SCIREF_ERR_ARG;
+    if (spinors ? n > 64 : n > 32) return SCIREF_ERR_ARG;
+    sciref_ctx *c = (sciref_ctx *)calloc(1, sizeof(sciref_ctx));
+    c->is_complex = is_complex;
+    c->spinors = spinors;
+    c->n = n;
+    c->norb = spinors ? n : 2 * n;
+    size_t m = (size_t)c->norb;
+    c->h = (zd *)calloc(m * m, sizeof(zd));
+    c->eri = (zd *)calloc(m * m * m * m, sizeof(zd));
+    if (!c->h || !c->eri) { free(c->h); free(c->eri); free(c); return SCIREF_ERR_ARG; }
+    for (int p = 0; p < c->norb; p++)
+        for (int q = 0; q < c->norb; q++) {
+            if (spin_of(c, p) != spin_of(c, q)) continue;
+            size_t s = (size_t)spatial_of(c, p) * n + spatial_of(c, q);
+            c->h[p * m + q] = is_complex ? CMPLX(h[2 * s], h[2 * s + 1]) : CMPLX(h[s], 0.0);
+        }
+    for (int p = 0; p < c->norb; p++)
+        for (int q = 0; q < c->norb; q++) {
+            if (spin_of(c, p) != spin_of(c, q)) continue;
+            for (int r = 0; r < c->norb; r++)
+                for (int s = 0; s < c->norb; s++) {
+                    if (spin_of(c, r) != spin_of(c, s)) continue;
+                    size_t P = spatial_of(c, p), Q = spatial_of(c, q), R = spatial_of(c, r), S = spatial_of(c, s);
+                    size_t t = ((P * n + Q) * n + R) * n + S;
+                    c->eri[((p * m + q) * m + r) * m + s] =
+                        is_complex ? CMPLX(eri[2 * t], eri[2 * t + 1]) : CMPLX(eri[t], 0.0);
+                }
+        }
+    *out = c;
+    return SCIREF_OK;
+}
+
+void sciref_destroy(sciref_ctx *c)
+{
+    if (!c) return;
+    free(c->h);
+    free(c->eri);
+    free(c->keys);
+    free(c);
+}
+
+/* The list must be strictly ascending as unsigned 64-bit integers. */
+int sciref_set_determinants(sciref_ctx *c, const uint64_t *keys, int64_t M)
+{
+    if (!c || (M > 0 && !keys) || M < 0) return SCIREF_ERR_ARG;
+    for (int64_t i = 1; i < M; i++)
+        if (!(keys[i - 1] < keys[i])) return SCIREF_ERR_UNSORTED;
+    free(c->keys);
+    c->keys = (uint64_t *)malloc((size_t)(M > 0 ? M : 1) * sizeof(uint64_t));
+    if (M > 0) memcpy(c->keys, keys, (size_t)M * sizeof(uint64_t));
+    c->M = M;
+    return SCIREF_OK;
+}
+
+/* ------------------------------------------------------------------ helpers */
+static int occupied(uint64_t d, int p) { return (int)((d >> p) & 1u); }
+
+/* number of occupied orbitals strictly below p, counted one bit at a time */
+static int count_below(uint64_t d, int p)
+{
+    int cnt = 0;
+    for (int q = 0; q < p; q++) cnt += occupied(d, q);
+    return cnt;
+}
+
+/* apply a_p to *d: returns +1/-1, or 0 if p is empty */
+static int annihilate(uint64_t *d, int p)
+{
+    if (!occupied(*d, p)) return 0;
+    int s = (count_below(*d, p) & 1) ? -1 : 1;
+    *d &= ~((uint64_t)1 << p);
+    return s;
+}
+
+/* apply a+_p to *d: returns +1/-1, or 0 if p is occupied */
+static int create(uint64_t *d, int p)
+{
+    if (occupied(*d, p)) return 0;
+    int s = (count_below(*d, p) & 1) ? -1 : 1;
+    *d |= ((uint64_t)1 << p);
+    return s;
+}
+
+static int n_diff(uint64_t a, uint64_t b)
+{
+    int cnt = 0;
+    for (int p = 0; p < 64; p++) cnt += occupied(a, p) != occupied(b, p);
+    return cnt;
+}
+
+static int64_t find_key(const sciref_ctx *c, uint64_t k)
+{
+    int64_t lo = 0, hi = c->M;          /* first index with keys[idx] >= k */
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (c->keys[mid] < k) lo = mid + 1; else hi = mid;
+    }
+    return (lo < c->M && c->keys[lo] == k) ? lo : -1;
+}
+
+/* <D_I|H|D_I> */
+static zd diag_element(const sciref_ctx *c, uint64_t d)
+{
+    zd e = 0;
+    for (int i = 0; i < c->norb; i++) {
+        if (!occupied(d, i)) continue;
+        e += H1(c, i, i);
+        for (int j = 0; j < c->norb; j++) {
+            if (!occupied(d, j)) continue;
+            e += 0.5 * (ERI(c, i, i, j, j) - ERI(c, i, j, j, i));
+        }
+    }
+    return e;
+}
+
+/* <D_I|H|D_J> for I != J; *degree receives the excitation degree and *sign the phase.
+ * Returns 0 with *degree > 2 when the pair is not connected. */
+static zd offdiag_element(const sciref_ctx *c, uint64_t bra, uint64_t ket, int *degree, int *sign)
+{
+    int nd = n_diff(bra, ket);
+    *degree = nd / 2;
+    *sign = 0;
+    if (nd != 2 && nd != 4) return 0;
+    int from[2], to[2], nf = 0, nt = 0;        /* from: in ket only; to: in bra only */
+    for (int p = 0; p < 64; p++) {
+        if (occupied(ket, p) && !occupied(bra, p)) from[nf++] = p;
+        if (occupied(bra, p) && !occupied(ket, p)) to[nt++] = p;
+    }
+    uint64_t d = ket;
+    if (nd == 2) {
+        int i = from[0], a = to[0];
+        int s = annihilate(&d, i);
+        s *= create(&d, a);
+        zd v = H1(c, a, i);
+        for (int k = 0; k < c->norb; k++) {
+            if (!occupied(ket, k) || k == i) continue;
+            v += ERI(c, a, i, k, k) - ERI(c, a, k, k, i);
+        }
+        *sign = s;
+        return s * v;
+    }
+    int i = from[0], j = from[1], a = to[0], b = to[1];   /* i<j, a<b */
+    int s = annihilate(&d, j);
+    s *= annihilate(&d, i);
+    s *= create(&d, a);
+    s *= create(&d, b);
+    *sign = s;
+    return s * (ERI(c, a, i, b, j) - ERI(c, a, j, b, i));
+}
+
+/* connections of row I by generation + lookup, sorted ascending by J */
+typedef struct { int64_t j; int8_t degree; int8_t sign; zd h; } conn_t;
+
+static int cmp_conn(const void *x, const void *y)
+{
+    int64_t a = ((const conn_t *)x)->j, b = ((const conn_t *)y)->j;
+    return (a > b) - (a < b);
+}
+
+static int64_t row_connections(const sciref_ctx *c, int64_t row, conn_t **out)
+{
+    uint64_t d = c->keys[row];
+    int occ[64], vir[64], no = 0, nv = 0;
+    for (int p = 0; p < c->norb; p++) {
+        if (occupied(d, p)) occ[no++] = p; else vir[nv++] = p;
+    }
+    size_t cap = 64, cnt = 0;
+    conn_t *list = (conn_t *)malloc(cap * sizeof(conn_t));
+    /* singles: i -> a */
+    for (int x = 0; x < no; x++)
+        for (int y = 0; y < nv; y++) {
+            int i = occ[x], a = vir[y];
+            if (spin_of(c, i) != spin_of(c, a)) continue;
+            uint64_t e = (d & ~((uint64_t)1 << i)) | ((uint64_t)1 << a);
+            int64_t J = find_key(c, e);
+            if (J < 0) continue;
+            if (cnt == cap) { cap *= 2; list = (conn_t *)realloc(list, cap * sizeof(conn_t)); }
+            int deg, sg;
+            list[cnt].h = offdiag_element(c, d, e, &deg, &sg);
+            list[cnt].j = J; list[cnt].degree = (int8_t)deg; list[cnt].sign = (int8_t)sg;
+            cnt++;
+        }
+    /* doubles: i<j -> a<b */
+    for (int x1 = 0; x1 < no; x1++)
+        for (int x2 = x1 + 1; x2 < no; x2++)
+            for (int y1 = 0; y1 < nv; y1++)
+                for (int y2 = y1 + 1; y2 < nv; y2++) {
+                    int i = occ[x1], j = occ[x2], a = vir[y1], b = vir[y2];
+                    if (spin_of(c, i) + spin_of(c, j) != spin_of(c, a) + spin_of(c, b)) continue;
+                    uint64_t e = d & ~((uint64_t)1 << i) & ~((uint64_t)1 << j);
+                    e |= ((uint64_t)1 << a) | ((uint64_t)1 << b);
+                    int64_t J = find_key(c, e);
+                    if (J < 0) continue;
+                    if (cnt == cap) { cap *= 2; list = (conn_t *)realloc(list, cap * sizeof(conn_t)); }
+                    int deg, sg;
+                    list[cnt].h = offdiag_element(c, d, e, &deg, &sg);
+                    list[cnt].j = J; list[cnt].degree = (int8_t)deg; list[cnt].sign = (int8_t)sg;
+                    cnt++;
+                }
+    qsort(list, cnt, sizeof(conn_t), cmp_conn);
+    *out = list;
+    return (int64_t)cnt;
+}
+
+/* ------------------------------------------------------------------ exports */
+/* H_II for all rows; out has M scalars (complex: interleaved). */
+int sciref_diagonal(const sciref_ctx *c, double *out)
+{
+    if (!c || !out) return SCIREF_ERR_ARG;
+#pragma omp parallel for schedule(static)
+    for (int64_t row = 0; row < c->M; row++) {
+        zd e = diag_element(c, c->keys[row]);
+        if (c->is_complex) { out[2 * row] = creal(e); out[2 * row + 1] = cimag(e); }
+        else out[row] = creal(e);
+    }
+    return SCIREF_OK;
+}
+
+/* One matrix element <bra|H|ket> of two occupation strings (need not be in the list). */
+int sciref_hij(const sciref_ctx *c, uint64_t bra, uint64_t ket, double *out)
+{
+    if (!c || !out) return SCIREF_ERR_ARG;
+    zd v;
+    if (bra == ket) v = diag_element(c, bra);
+    else { int deg, sg; v = offdiag_element(c, bra, ket, &deg, &sg); }
+    out[0] = creal(v);
+    if (c->is_complex) out[1] = cimag(v);
+    return SCIREF_OK;
+}
+
+/* Connection list of one row: J ascending, excitation degree, phase (+1/-1).
+ * Returns SCIREF_ERR_CAP (with *count set) when cap is too small. */
+int sciref_connections(const sciref_ctx *c, int64_t row, int64_t *count, int64_t *J,
+                       int8_t *degree, int8_t *phase, int64_t cap)
+{
+    if (!c || !count || row < 0 || row >= c->M) return SCIREF_ERR_ARG;
+    conn_t *list;
+    int64_t n = row_connections(c, row, &list);
+    *count = n;
+    if (n > cap) { free(list); return SCIREF_ERR_CAP; }
+    for (int64_t t = 0; t < n; t++) {
+        if (J) J[t] = list[t].j;
+        if (degree) degree[t] = list[t].degree;
+        if (phase) phase[t] = list[t].sign;
+    }
+    free(list);
+    return SCIREF_OK;
+}
+
+/* Connections of one row together with their matrix elements <D_row|H|D_J>
+ * (complex: interleaved).  Returns SCIREF_ERR_CAP (with *count set) when cap is too small. */
+int sciref_row_elements(const sciref_ctx *c, int64_t row, int64_t *count, int64_t *J,
+                        double *hvals, int64_t cap)
+{
+    if (!c || !count || row < 0 || row >= c->M) return SCIREF_ERR_ARG;
+    conn_t *list;
+    int64_t n = row_connections(c, row, &list);
+    *count = n;
+    if (n > cap) { free(list); return SCIREF_ERR_CAP; }
+    for (int64_t t = 0; t < n; t++) {
+        if (J) J[t] = list[t].j;
+        if (hvals) {
+            if (c->is_complex) { hvals[2 * t] = creal(list[t].h); hvals[2 * t + 1] = cimag(list[t].h); }
+            else hvals[t] = creal(list[t].h);
+        }
+    }
+    free(list);
+    return SCIREF_OK;
+}
+
+/* Number of connected ordered pairs (I, J), I != J, over rows [row_begin, row_end). */
+int sciref_count_pairs(const sciref_ctx *c, int64_t row_begin, int64_t row_end, int64_t *count)
+{
+    if (!c || !count || row_begin < 0 || row_end > c->M || row_begin > row_end) return SCIREF_ERR_ARG;
+    int64_t total = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : total)
+    for (int64_t row = row_begin; row < row_end; row++) {
+        conn_t *list;
+        total += row_connections(c, row, &list);
+        free(list);
+    }
+    *count = total;
+    return SCIREF_OK;
+}
+
+/* sigma for the listed rows: S[r][v] = sum_J <D_rows[r]|H|D_J> C[J][v].
+ * C is [M][nvec] row-major (complex interleaved); S is [nrows][nvec].
+ * The diagonal term comes first, then connections in ascending J. */
+int sciref_sigma_rows(const sciref_ctx *c, const int64_t *rows, int64_t nrows,
+                      const double *C, int nvec, double *S)
+{
+    if (!c || !rows || !C || !S || nvec <= 0) return SCIREF_ERR_ARG;
+    for (int64_t r = 0; r < nrows; r++)
+        if (rows[r] < 0 || rows[r] >= c->M) return SCIREF_ERR_ARG;
+    const int z = c->is_complex;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t r = 0; r < nrows; r++) {
+        int64_t row = rows[r];
+        zd *acc = (zd *)malloc((size_t)nvec * sizeof(zd));
+        zd hd = diag_element(c, c->keys[row]);
+        for (int v = 0; v < nvec; v++) {
+            size_t t = (size_t)row * nvec + v;
+            zd cv = z ? CMPLX(C[2 * t], C[2 * t + 1]) : CMPLX(C[t], 0.0);
+            acc[v] = hd * cv;
+        }
+        conn_t *list;
+        int64_t n = row_connections(c, row, &list);
+        for (int64_t k = 0; k < n; k++)
+            for (int v = 0; v < nvec; v++) {
+                size_t t = (size_t)list[k].j * nvec + v;
+                zd cv = z ? CMPLX(C[2 * t], C[2 * t + 1]) : CMPLX(C[t], 0.0);
+                acc[v] += list[k].h * cv;
+            }
+        free(list);
+        for (int v = 0; v < nvec; v++) {
+            size_t t = (size_t)r * nvec + v;
+            if (z) { S[2 * t] = creal(acc[v]); S[2 * t + 1] = cimag(acc[v]); }
+            else S[t] = creal(acc[v]);
+        }
+        free(acc);
+    }
+    return SCIREF_OK;
+}
+
+/* The same sigma rows by the all-pairs route: every J of the list is tested, the
+ * excitation degree taken by counting differing bits; no excitation is generated. */
+int sciref_sigma_brute_rows(const sciref_ctx *c, const int64_t *rows, int64_t nrows,
+                            const double *C, int nvec, double *S)
+{
+    if (!c || !rows || !C || !S || nvec <= 0) return SCIREF_ERR_ARG;
+    for (int64_t r = 0; r < nrows; r++)
+        if (rows[r] < 0 || rows[r] >= c->M) return SCIREF_ERR_ARG;
+    const int z = c->is_complex;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t r = 0; r < nrows; r++) {
+        int64_t row = rows[r];
+        uint64_t bra = c->keys[row];
+        zd *acc = (zd *)calloc((size_t)nvec, sizeof(zd));
+        for (int64_t col = 0; col < c->M; col++) {
+            uint64_t ket = c->keys[col];
+            int nd = n_diff(bra, ket);
+            if (nd > 4) continue;
+            zd hv;
+            if (col == row) hv = diag_element(c, bra);
+            else { int deg, sg; hv = offdiag_element(c, bra, ket, &deg, &sg); }
+            for (int v = 0; v < nvec; v++) {
+                size_t t = (size_t)col * nvec + v;
+                zd cv = z ? CMPLX(C[2 * t], C[2 * t + 1]) : CMPLX(C[t], 0.0);
+                acc[v] += hv * cv;
+            }
+        }
+        for (int v = 0; v < nvec; v++) {
+            size_t t = (size_t)r * nvec + v;
+            if (z) { S[2 * t] = creal(acc[v]); S[2 * t + 1] = cimag(acc[v]); }
+            else S[t] = creal(acc[v]);
+        }
+        free(acc);
+    }
+    return SCIREF_OK;
+}
