@@ -1,0 +1,306 @@
+"""Benchmark: sigma = H c Slater-Condon pairs per second on GB300.
+
+One step is one sigma = H c over the whole selected determinant space (every kernel of
+the hot path: diagonal term, double-excitation and single-excitation kernels), with the
+integrals, determinant tables and c resident in HBM.  Default workload: 30 spatial
+orbitals, 10 alpha + 10 beta electrons, 2,000,000 selected determinants (HF + all singles
+and doubles + seeded random triples/quadruples), Cholesky rank 120, FP64, one vector.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload sel_30o|sel_64s|fci_8o]
+                    [--nvec V] [--impl gb300|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload (weak
+scaling, no collective on the data path); the value is all ranks' pairs / max time.
+`--impl reference` times the CPU oracle (the only reference implementation: the paper
+ships no code) on a bounded sample of rows of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2501_18185_gb300 import workloads as W  # noqa: E402
+
+METRIC = "sigma Slater-Condon pairs/sec"
+UNIT = "pairs/s"
+GOLDEN = os.path.join(ROOT, "tests", "golden", "pair_counts.json")
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def make_workload(name: str, nvec: int):
+    if name == "sel_30o":
+        return W.selected_30o(nvec=nvec)
+    if name == "sel_64s":
+        return W.selected_spinor_64(nvec=nvec)
+    if name == "fci_8o":
+        return W.fci_small_8o()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def golden_pairs(w):
+    try:
+        return json.load(open(GOLDEN)).get(w.name, {}).get("pairs")
+    except (OSError, ValueError):
+        return None
+
+
+def hbm_peak():
+    try:
+        return float(json.load(open(PEAKS))["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(w, budget_s: float = 12.0, seed: int = 0):
+    """Time the CPU oracle, as it stands, on a bounded random sample of rows."""
+    from oracle import Oracle
+
+    o = Oracle.from_workload(w)
+    rng = np.random.default_rng(seed)
+    rows = np.sort(rng.choice(w.M, min(w.M, 200), replace=False))
+    t = time.perf_counter()
+    o.sigma_rows(rows, w.c)
+    per_row = (time.perf_counter() - t) / len(rows)
+    n = int(min(w.M, max(200, budget_s / max(per_row, 1e-9))))
+    rows = np.sort(rng.choice(w.M, n, replace=False))
+    t = time.perf_counter()
+    o.sigma_rows(rows, w.c)
+    dt = time.perf_counter() - t
+    pairs = sum(len(o.connections(int(r))[0]) for r in rows)
+    cores = len(os.sched_getaffinity(0))
+    return {"value": pairs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} random rows of {w.M} ({pairs} pairs, {dt:.1f} s, OpenMP {cores} threads)"}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the CPU oracle on bounded samples of the same workload."""
+    if rank != 0:
+        return
+    from oracle import Oracle
+
+    w = make_workload(args.workload, args.nvec)
+    o = Oracle.from_workload(w)
+    rng = np.random.default_rng(1)
+    nrows = args.ref_rows
+    samples = [np.sort(rng.choice(w.M, min(nrows, w.M), replace=False)) for _ in range(args.warmup + args.steps)]
+    for s in samples[:args.warmup]:
+        o.sigma_rows(s, w.c)
+    tot_t, tot_p = 0.0, 0
+    for s in samples[args.warmup:]:
+        t = time.perf_counter()
+        o.sigma_rows(s, w.c)
+        tot_t += time.perf_counter() - t
+        tot_p += sum(len(o.connections(int(r))[0]) for r in s)
+    value = tot_p / tot_t
+    cores = len(os.sched_getaffinity(0))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64" if not w.ints.complex_ else "c128",
+            "data": "synthetic", "config": {"workload": w.name, "nvec": w.c.shape[1], "rows_per_step": int(nrows)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} x {nrows} random rows of {w.M}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="sel_30o")
+    ap.add_argument("--nvec", type=int, default=1)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--ref-rows", type=int, default=2000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+
+    from paper_2501_18185_gb300 import build, sci
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    build.build()
+
+    w = make_workload(args.workload, args.nvec)
+    stream = torch.cuda.current_stream(dev)
+    t = time.perf_counter()
+    H = sci.Hamiltonian(local, stream)
+    H.set_integrals(w.mode, w.ints.h, chol=w.ints.chol)
+    H.set_determinants(w.keys, w.n_alpha, w.n_beta)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t
+    info = H.info()
+    pairs = info["pairs"]
+    gp = golden_pairs(w)
+    if gp is not None and gp != pairs:
+        raise SystemExit(f"pair count {pairs} differs from the oracle's {gp}")
+
+    C = torch.from_numpy(np.ascontiguousarray(w.c)).to(dev)
+    S = torch.empty_like(C)
+    flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=dev)  # 256 MB > L2
+    nv = C.shape[1]
+    for _ in range(args.warmup):
+        H.sigma(C, out=S)
+    H.sync_status()
+    sci.sci_profile(H.ctx, True)
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms, kern = [], []
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.zero_()                      # evict L2 between timed steps
+        ev0.record(stream)
+        H.sigma(C, out=S)
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        kern.append(sci.sci_kernel_times(H.ctx))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    sci.sci_profile(H.ctx, False)
+    H.sync_status()
+
+    total_ms = sum(step_ms)
+    if dist:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms = total_ms / args.steps
+    value = world * pairs * args.steps / (total_ms / 1e3)
+
+    # end to end through the public API with host buffers (pinned), copies inside
+    Ch = torch.from_numpy(np.ascontiguousarray(w.c)).pin_memory()
+    Sh = torch.empty_like(Ch).pin_memory()
+    sci.sci_sigma_host(H.ctx, Ch, Sh, nv, sci.SCI_PREC_F64)
+    e2e_t = []
+    for _ in range(max(3, min(args.steps, 10))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        sci.sci_sigma_host(H.ctx, Ch, Sh, nv, sci.SCI_PREC_F64)
+        e2e_t.append(time.perf_counter() - t)
+    e2e = world * pairs / statistics.mean(e2e_t)
+    nbytes = Ch.numel() * Ch.element_size()
+
+    # roofline of the dominant kernel (double excitations): algorithmic bytes per launch
+    sb = 16 if w.ints.complex_ else 8
+    dbl_ms = statistics.mean(k[1] for k in kern)
+    sgl_ms = statistics.mean(k[2] for k in kern)
+    init_ms = statistics.mean(k[0] for k in kern)
+    alg_bytes = info["pairs_doubles"] * (nv * sb + sb)
+    peak, peak_kind = hbm_peak()
+    achieved = alg_bytes / (dbl_ms / 1e3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get(f"{w.name}/nvec{nv}")
+        except ValueError:
+            traffic = None
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": "k_doubles", "peak_source": peak_kind,
+            "algorithmic_bytes_per_launch": alg_bytes,
+            "kernel_ms": {"init": init_ms, "doubles": dbl_ms, "singles": sgl_ms}}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(w)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c128" if w.ints.complex_ else "f64", "data": "synthetic",
+            "config": {"workload": w.name, "M": w.M, "nvec": nv, "pairs_per_step": pairs,
+                       "l2": "flushed between timed steps (256 MB write)", "setup_s": round(setup_s, 3),
+                       "parallelism": f"replicas{world}" if world > 1 else "single"},
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+            "gpu_launches": args.steps * (1 + 2 * ((nv + 7) // 8 if not w.ints.complex_ else (nv + 3) // 4)),
+            "roofline": roof, "cpu_baseline": cpu, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

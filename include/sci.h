@@ -1,0 +1,167 @@
+/*
+ * sci.h -- C ABI of libsci: sigma = H c for selected configuration interaction on one
+ * GB300 (sm_103a).
+ *
+ * The operation (MetaWave, arXiv 2501.18185):
+ *   H = sum_pq h_pq a+_p a_q + 1/2 sum_pqrs (pq|rs) a+_p a+_r a_s a_q   (Sec. 2.1,
+ *       Eq. Hamiltonian / Eq. sym_op, Mulliken notation, H = H^+)
+ *   sigma_I = sum_J <D_I|H|D_J> C_J over a sorted determinant list   (Sec. 2.4, the
+ *       diagonalisation paragraph: H is applied through matrix-vector products whose
+ *       nonzero elements are recomputed whenever needed and never stored)
+ * The library stores integrals (Sec. 3.2, IntegralManager) and a sorted basis
+ * (Sec. 3.2, BasisManager) in device memory and evaluates every Slater-Condon element
+ * on the fly.
+ *
+ * Determinant keys.  One uint64 per determinant.
+ *   Spin-orbital mode (n spatial orbitals, n <= 32): bit p (p < n) is alpha orbital p,
+ *   bit n+p is beta orbital p; bits >= 2n are zero.
+ *   Spinor mode (n spinors, n <= 64): bit p is spinor p.
+ * Phase convention: |D> = a+_{p1} a+_{p2} ... |0> with p1 < p2 < ... in bit order (so
+ * every alpha creator precedes every beta creator).  Energies do not depend on this
+ * convention; the signs of sigma and of off-diagonal elements do.
+ * The list must be strictly ascending as unsigned 64-bit integers; a list that is not
+ * is rejected (no resorting).
+ *
+ * Vectors.  C and S are [M][nvec] row-major: the nvec coefficients of one determinant
+ * are contiguous.  Real mode: double (or float input, see SCI_PREC_*).  Complex mode:
+ * interleaved (re, im) double pairs.  There is no conjugation of C: S = H C.
+ *
+ * Errors.  Every call returns SCI_OK (0) or a negative code; no C++ exception crosses
+ * the ABI.  Argument errors are detected before any work is queued.  Conditions found
+ * on the device set a sticky status word that sci_sync_status() returns.  After an
+ * error the context stays valid; calls that need missing state return SCI_ERR_STATE.
+ * sci_last_error() gives a readable message for the last failure of a context.
+ *
+ * Ownership.  The caller owns every pointer it passes.  The library copies integrals
+ * and keys into device memory owned by the context and freed by sci_destroy().  C and S
+ * of sci_sigma() are borrowed device pointers (e.g. torch tensor data_ptr()).
+ *
+ * Streams.  Work is queued on the stream given at creation (or by sci_set_stream); a
+ * NULL stream is the legacy default stream.  sci_sigma() allocates nothing, takes no
+ * host synchronisation and only queues kernels.
+ */
+#ifndef SCI_H
+#define SCI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sci_ctx sci_ctx;
+
+enum {
+    SCI_OK = 0,
+    SCI_ERR_ARG = -1,        /* invalid argument (null pointer, bad size, bad enum, ...) */
+    SCI_ERR_UNSORTED = -2,   /* determinant list not ascending */
+    SCI_ERR_DUPLICATE = -3,  /* determinant list holds a key twice */
+    SCI_ERR_POPCOUNT = -4,   /* a key has the wrong electron count or stray bits */
+    SCI_ERR_NOMEM = -5,      /* device allocation failed */
+    SCI_ERR_CUDA = -6,       /* a CUDA runtime call failed */
+    SCI_ERR_STATE = -7,      /* call needs state that is missing (e.g. no integrals) */
+    SCI_ERR_OVERFLOW = -8,   /* a size exceeds an internal limit or an output capacity */
+    SCI_ERR_TIMEOUT = -9     /* reserved: a bounded device wait gave up */
+};
+
+enum { SCI_REAL64 = 1, SCI_COMPLEX128 = 2 };                 /* Hamiltonian scalar type */
+enum { SCI_SPIN_ORBITALS = 1, SCI_SPINORS = 2 };             /* orbital mode */
+enum {
+    SCI_PREC_F64 = 1,                /* C double (complex: double pairs), S double */
+    SCI_PREC_F32_STORE_F64_ACC = 2   /* C float, integrals rounded to float, products and
+                                        accumulation in FP64, S double (real mode only) */
+};
+
+/* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t (may be
+ * NULL).  Allocates no device buffers yet.  Returns SCI_ERR_ARG for a bad device. */
+int sci_create(sci_ctx **out, int device, void *cuda_stream);
+
+/* Free every device buffer of the context and the context itself.  NULL is allowed. */
+int sci_destroy(sci_ctx *ctx);
+
+/* Change the stream used by later calls. */
+int sci_set_stream(sci_ctx *ctx, void *cuda_stream);
+
+/* Load the Hamiltonian (Sec. 2.1, Eq. Hamiltonian; Sec. 3.2, IntegralManager).
+ *   scalar: SCI_REAL64 or SCI_COMPLEX128.  mode: SCI_SPIN_ORBITALS (n <= 32 spatial
+ *   orbitals, real only) or SCI_SPINORS (n <= 64 spinors).
+ *   h:    host, n*n row-major, h[p*n+q] = h_pq, Hermitian (complex: interleaved re,im).
+ *   eri:  host, n^4 row-major, eri[((p*n+q)*n+r)*n+s] = (pq|rs), or NULL.
+ *   chol: host, naux*n*n, (pq|rs) = sum_P chol[P][p][q] chol[P][r][s], or NULL.
+ * Exactly one of eri / chol must be given.  The permutation symmetries
+ * (pq|rs) = (rs|pq) = (qp|sr)^* and h = h^+ (Sec. 3.2, IntegralManager; the symmetry of
+ * Eq. sym_op) are checked to 1e-10 relative and violations return SCI_ERR_ARG.
+ * Synchronous: returns after the device tables are built.  A later call with the same
+ * mode and n keeps the determinant list; a different mode or n drops it. */
+int sci_set_integrals(sci_ctx *ctx, int scalar, int mode, int n, const void *h,
+                      const void *eri, int naux, const void *chol);
+
+/* Load a strictly ascending determinant list (Sec. 3.2, BasisManager) and build the
+ * connection tables: keys are validated on the device (order, duplicates, electron
+ * counts), the (N-2)- and (N-1)-hole bucket tables are sorted out, and the diagonal
+ * H_II is computed.  Needs integrals (SCI_ERR_STATE otherwise).
+ *   keys: host or device pointer (keys_on_device 0/1), M entries, M >= 0.
+ *   n_alpha, n_beta: electrons per spin (spin-orbital mode); spinor mode: n_alpha = N
+ *   electrons and n_beta = -1.
+ * Errors: SCI_ERR_UNSORTED, SCI_ERR_DUPLICATE, SCI_ERR_POPCOUNT for bad lists,
+ * SCI_ERR_NOMEM when the tables do not fit, SCI_ERR_OVERFLOW for M >= 2^31.
+ * Synchronous. */
+int sci_set_determinants(sci_ctx *ctx, const uint64_t *keys, int64_t M, int n_alpha,
+                         int n_beta, int keys_on_device);
+
+/* Copy the diagonal H_II (real, FP64) into the device array hdiag[M].  Queued on the
+ * context stream. */
+int sci_diagonal(sci_ctx *ctx, double *hdiag);
+
+/* S = H C (Sec. 2.4, the diagonalisation paragraph) for nvec >= 1 vectors.
+ *   C: device, [M][nvec]; S: device, [M][nvec], overwritten (see SCI_PREC_* for types).
+ *   C and S must not overlap.  Queued on the context stream; allocates nothing.
+ * Accumulation into S uses FP64 atomic adds, so the summation order (and the last bits
+ * of S) can differ between calls. */
+int sci_sigma(sci_ctx *ctx, const void *C, void *S, int nvec, int prec);
+
+/* Connection list of rows [row_begin, row_end) for tests and debugging: every ordered
+ * pair (I, J), I != J, with excitation degree 1 or 2 and both in the list, sorted by
+ * (I, J), with the degree and the phase (+1/-1) of <D_I| relative to the excitation
+ * operator applied to |D_J> (a+_a a_i for singles; a+_b a+_a a_i a_j, i<j, a<b, for
+ * doubles).  rows, J, degree, phase are host arrays of capacity cap (any may be NULL).
+ * *count receives the number of pairs; SCI_ERR_OVERFLOW if it exceeds cap.
+ * Synchronous; allocates temporary device memory. */
+int sci_connections(sci_ctx *ctx, int64_t row_begin, int64_t row_end, int64_t *count,
+                    int64_t *rows, int64_t *J, int8_t *degree, int8_t *phase, int64_t cap);
+
+/* Number of connected ordered pairs (I, J), I != J, excitation degree <= 2 (every
+ * off-diagonal element that sigma evaluates, counted whether or not its value is 0). */
+int sci_count_pairs(sci_ctx *ctx, int64_t *pairs);
+
+/* sigma for callers holding HOST buffers: C_host [M][nvec] is copied to the device, S
+ * is computed as by sci_sigma() and copied back into S_host [M][nvec].  Staging buffers
+ * are allocated by the context on first use (and grown when nvec grows).  Synchronous.
+ * Host buffers may be pageable; pinned ones copy faster. */
+int sci_sigma_host(sci_ctx *ctx, const void *C_host, void *S_host, int nvec, int prec);
+
+/* Table sizes, for reports: out[0..n) receives, in order, M, pairs, entries and buckets
+ * of the (N-2)-hole table, entries and buckets of the (N-1)-hole table, the largest
+ * bucket, the device bytes held by the context, the double-excitation pairs and the
+ * single-excitation pairs.  n <= 10. */
+int sci_info(sci_ctx *ctx, int64_t *out, int n);
+
+/* Kernel timing for reports.  sci_profile(ctx, 1) makes later sci_sigma() calls record
+ * CUDA events on the context stream around each of their kernels; sci_kernel_times()
+ * waits for the last such call and writes the durations in milliseconds of its diagonal
+ * initialisation, double-excitation and single-excitation kernels to ms[0..n), n <= 3. */
+int sci_profile(sci_ctx *ctx, int enable);
+int sci_kernel_times(sci_ctx *ctx, float *ms, int n);
+
+/* Wait for the context stream and return the device status word (SCI_OK or the first
+ * device-side error code). */
+int sci_sync_status(sci_ctx *ctx);
+
+/* Message of the last error of this context ("" if none).  Valid until the next call. */
+const char *sci_last_error(const sci_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCI_H */

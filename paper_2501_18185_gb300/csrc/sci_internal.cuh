@@ -1,0 +1,114 @@
+// Internal declarations of libsci (sigma = H c for selected CI on sm_103a).
+//
+// Data layout in device memory (all owned by the context):
+//   keys[M]            uint64 determinant keys, ascending.
+//   hdiag[M]           FP64 diagonal H_II (Sec. 2.1, Eq. decompositionH: H_1^0 + H_2^0).
+//   tab                pair-integral table read by the double-excitation kernel.  Real
+//                      spin-orbital mode: [ T | W ] with
+//                        T[y'][x'][y][x] = (x x'|y y')  (alpha x<-x', beta y<-y')
+//                        W[P(i,j)][P(a,b)] = (ai|bj) - (aj|bi), a<b, i<j same spin,
+//                      spinor mode: W only (complex), P(a,b) = b(b-1)/2 + a.
+//                      The bra (row) indices are the fast ones so that lanes that own
+//                      consecutive rows of one bucket read consecutive addresses.
+//   g_so[k][i][a]      (ai|kk) - (ak|ki) over spin-orbitals/spinors (singles).
+//   fref[i][a]         h_ai + sum_{k in ref} g_so[k][i][a]: the Fock matrix of the
+//                      reference determinant ref (lowest orbitals), the closed-shell
+//                      reference trick of Sec. 2.3.
+//   Doubles table "B2" (structure of arrays over E2 entries): every determinant D
+//     emits the (N-2)-electron keys K = D minus two occupied bits; entries sharing K
+//     form a bucket and are within a double excitation of each other.  Buckets of size
+//     1 are dropped; the rest are stored contiguously, largest first.
+//       e2_idx[p]     determinant index of the member
+//       e2_mask[p]    bit mask of the two extra orbitals of the member (D = K | mask)
+//       e2_col[p]     offset of the member's ket indices in tab
+//       e2_meta[p]    bits 0-15 bra offset in tab, bit 16 phase parity, bits 32-47
+//                     position inside the bucket, bits 48-63 bucket size
+//   Singles table "B1": the same with (N-1)-electron keys S = D minus one bit.
+//       e1_idx[p], e1_S[p] (the bucket key S), e1_meta[p]: bits 0-6 extra orbital,
+//       bit 7 parity, bits 8-19 position in bucket, bits 20-31 bucket size.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "sci.h"
+
+namespace sci {
+
+struct zdbl {
+    double x, y;
+};
+
+enum DevErr : int {
+    DEV_UNSORTED = 1,
+    DEV_DUPLICATE = 2,
+    DEV_POPCOUNT = 4,
+    DEV_OVERFLOW = 8,
+};
+
+}  // namespace sci
+
+struct sci_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+
+    // Hamiltonian
+    int have_ints = 0;
+    int cplx = 0;     // 1: complex128 scalars
+    int spinors = 0;  // 1: spinor mode
+    int n = 0;        // spatial orbitals or spinors
+    int norb = 0;     // bits in a key: 2n or n
+    void *h_so = nullptr;   // [norb][norb], spin-orbital h (scalar)
+    void *jd = nullptr;     // [norb][norb] (ii|jj)
+    void *kd = nullptr;     // [norb][norb] (ij|ji)
+    void *g_so = nullptr;   // [norb][norb][norb]
+    void *tab = nullptr;    // pair table (scalar)
+    float *tab32 = nullptr; // FP32 copy of tab (real mode)
+    int64_t tab_elems = 0;
+
+    // determinants
+    int have_dets = 0;
+    int64_t M = 0;
+    int na = 0, nb = 0, N = 0;
+    uint64_t ref = 0;
+    uint64_t *keys = nullptr;
+    double *hdiag = nullptr;
+    void *fref = nullptr;   // [norb][norb]
+
+    int64_t e2 = 0, nb2 = 0;
+    uint32_t *e2_idx = nullptr;
+    uint64_t *e2_mask = nullptr;
+    uint32_t *e2_col = nullptr;
+    uint64_t *e2_meta = nullptr;
+    int64_t e1 = 0, nb1 = 0;
+    uint32_t *e1_idx = nullptr;
+    uint64_t *e1_S = nullptr;
+    uint32_t *e1_meta = nullptr;
+    int maxb2 = 0, maxb1 = 0;
+    int64_t pairs = 0, pairs2 = 0, pairs1 = 0;
+
+    // host-buffer sigma staging
+    void *stage_c = nullptr, *stage_s = nullptr;
+    size_t stage_bytes = 0;
+
+    // kernel timing
+    int profile = 0;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+
+    int *status = nullptr;  // device status word (sci::DevErr bits)
+    size_t bytes_held = 0;
+};
+
+// helpers shared by the translation units of the library
+int sci_fail(sci_ctx *ctx, int code, const std::string &msg);
+int sci_cuda_check(sci_ctx *ctx, cudaError_t e, const char *what);
+
+// launchers (sci_sigma.cu)
+int sci_launch_sigma(sci_ctx *ctx, const void *C, void *S, int nvec, int prec);
+int sci_count_pairs_device(sci_ctx *ctx, int64_t *pairs2, int64_t *pairs1);
+int sci_connections_device(sci_ctx *ctx, int64_t row_begin, int64_t row_end, int64_t *count,
+                           int64_t *rows, int64_t *J, int8_t *degree, int8_t *phase,
+                           int64_t cap);

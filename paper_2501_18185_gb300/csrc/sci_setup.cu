@@ -1,0 +1,999 @@
+// libsci setup: context, integral tables and the determinant bucket tables.
+//
+// Everything here runs once per Hamiltonian or per determinant space (the paper's
+// "classify and sort pairs" steps of the batch evaluation scheme, Sec. 2.3); the hot
+// path sigma = H c lives in sci_sigma.cu.  The radix sorts and scans of the setup use
+// CUB (header-only, part of the CUDA toolkit).
+#include <cub/cub.cuh>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "sci_internal.cuh"
+
+using sci::zdbl;
+
+// ------------------------------------------------------------------ error helpers
+int sci_fail(sci_ctx *ctx, int code, const std::string &msg)
+{
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int sci_cuda_check(sci_ctx *ctx, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return SCI_OK;
+    cudaGetLastError();  // clear non-sticky errors
+    int code = (e == cudaErrorMemoryAllocation) ? SCI_ERR_NOMEM : SCI_ERR_CUDA;
+    return sci_fail(ctx, code, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define SCI_CK(call)                                                 \
+    do {                                                             \
+        int _rc = sci_cuda_check(ctx, (call), #call);                \
+        if (_rc != SCI_OK) return _rc;                               \
+    } while (0)
+
+namespace {
+
+// device buffer owned by a scope (temporaries of the setup)
+struct TmpBuf {
+    void *p = nullptr;
+    ~TmpBuf() { if (p) cudaFree(p); }
+    template <typename T> T *as() { return static_cast<T *>(p); }
+};
+
+cudaError_t alloc_held(sci_ctx *ctx, void **p, size_t bytes)
+{
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e == cudaSuccess) ctx->bytes_held += bytes;
+    return e;
+}
+
+template <typename T> void free_held(sci_ctx *ctx, T *&p)
+{
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+    (void)ctx;
+}
+
+__host__ __device__ inline int pair_index(int a, int b) { return b * (b - 1) / 2 + a; }  // a < b
+
+// ------------------------------------------------------------------ scalar helpers
+template <typename S> struct Sc;
+template <> struct Sc<double> {
+    __device__ static double zero() { return 0.0; }
+    __device__ static double mul(double a, double b) { return a * b; }
+    __device__ static double add(double a, double b) { return a + b; }
+    __device__ static double sub(double a, double b) { return a - b; }
+    __device__ static double re(double a) { return a; }
+};
+template <> struct Sc<zdbl> {
+    __device__ static zdbl zero() { return zdbl{0.0, 0.0}; }
+    __device__ static zdbl mul(zdbl a, zdbl b) { return zdbl{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+    __device__ static zdbl add(zdbl a, zdbl b) { return zdbl{a.x + b.x, a.y + b.y}; }
+    __device__ static zdbl sub(zdbl a, zdbl b) { return zdbl{a.x - b.x, a.y - b.y}; }
+    __device__ static double re(zdbl a) { return a.x; }
+};
+
+// ------------------------------------------------------------------ integral kernels
+// (pq|rs) = sum_P L^P_pq L^P_rs, dense n^4
+template <typename S>
+__global__ void k_eri_from_chol(const S *__restrict__ L, int naux, int n, S *__restrict__ eri)
+{
+    int64_t n2 = (int64_t)n * n;
+    int64_t total = n2 * n2;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t pq = t / n2, rs = t % n2;
+        S acc = Sc<S>::zero();
+        for (int P = 0; P < naux; P++) acc = Sc<S>::add(acc, Sc<S>::mul(L[P * n2 + pq], L[P * n2 + rs]));
+        eri[t] = acc;
+    }
+}
+
+struct OrbMap {
+    int n, spinors;
+    __device__ int spin(int p) const { return spinors ? 0 : (p >= n); }
+    __device__ int sp(int p) const { return spinors ? p : (p >= n ? p - n : p); }
+};
+
+// spin-orbital integral from the spatial (or spinor) table
+template <typename S>
+__device__ S eri_so(const S *__restrict__ eri, OrbMap m, int p, int q, int r, int s)
+{
+    if (m.spin(p) != m.spin(q) || m.spin(r) != m.spin(s)) return Sc<S>::zero();
+    int64_t n = m.n;
+    return eri[((m.sp(p) * n + m.sp(q)) * n + m.sp(r)) * n + m.sp(s)];
+}
+
+template <typename S>
+__global__ void k_small_tables(const S *__restrict__ h, const S *__restrict__ eri, OrbMap m, int norb,
+                               S *__restrict__ h_so, S *__restrict__ jd, S *__restrict__ kd,
+                               S *__restrict__ g_so)
+{
+    int64_t total = (int64_t)norb * norb * norb;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int k = (int)(t / ((int64_t)norb * norb));
+        int i = (int)((t / norb) % norb);
+        int a = (int)(t % norb);
+        // g_so[k][i][a] = (ai|kk) - (ak|ki)
+        g_so[t] = Sc<S>::sub(eri_so(eri, m, a, i, k, k), eri_so(eri, m, a, k, k, i));
+        if (k == 0) {
+            // [i][a] tables
+            int64_t u = (int64_t)i * norb + a;
+            h_so[u] = (m.spin(i) == m.spin(a)) ? h[(int64_t)m.sp(i) * m.n + m.sp(a)] : Sc<S>::zero();
+            jd[u] = eri_so(eri, m, i, i, a, a);
+            kd[u] = eri_so(eri, m, i, a, a, i);
+        }
+    }
+}
+
+// real spin-orbital pair table: T (n^4) then W (NP^2)
+__global__ void k_tab_real(const double *__restrict__ eri, int n, double *__restrict__ tab)
+{
+    int64_t n2 = (int64_t)n * n, n4 = n2 * n2;
+    int64_t NP = (int64_t)n * (n - 1) / 2;
+    int64_t total = n4 + NP * NP;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (t < n4) {
+            // t = ((y'*n + x')*n + y)*n + x  ->  (x x'|y y')
+            int x = (int)(t % n), y = (int)((t / n) % n), xp = (int)((t / n2) % n), yp = (int)(t / (n2 * n));
+            tab[t] = eri[((int64_t)(x * n + xp) * n + y) * n + yp];
+        } else {
+            int64_t u = t - n4;
+            int64_t col = u / NP, row = u % NP;   // col = P(i,j), row = P(a,b)
+            int b = (int)((1 + sqrt(1.0 + 8.0 * row)) / 2);
+            while (b * (b - 1) / 2 > row) b--;
+            while ((b + 1) * b / 2 <= row) b++;
+            int a = (int)(row - (int64_t)b * (b - 1) / 2);
+            int j = (int)((1 + sqrt(1.0 + 8.0 * col)) / 2);
+            while (j * (j - 1) / 2 > col) j--;
+            while ((j + 1) * j / 2 <= col) j++;
+            int i = (int)(col - (int64_t)j * (j - 1) / 2);
+            // (ai|bj) - (aj|bi)
+            tab[t] = eri[((int64_t)(a * n + i) * n + b) * n + j] - eri[((int64_t)(a * n + j) * n + b) * n + i];
+        }
+    }
+}
+
+// spinor pair table: W (NP^2), complex
+__global__ void k_tab_spinor(const zdbl *__restrict__ eri, int n, zdbl *__restrict__ tab)
+{
+    int64_t NP = (int64_t)n * (n - 1) / 2;
+    int64_t total = NP * NP;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t col = t / NP, row = t % NP;
+        int b = (int)((1 + sqrt(1.0 + 8.0 * row)) / 2);
+        while (b * (b - 1) / 2 > row) b--;
+        while ((b + 1) * b / 2 <= row) b++;
+        int a = (int)(row - (int64_t)b * (b - 1) / 2);
+        int j = (int)((1 + sqrt(1.0 + 8.0 * col)) / 2);
+        while (j * (j - 1) / 2 > col) j--;
+        while ((j + 1) * j / 2 <= col) j++;
+        int i = (int)(col - (int64_t)j * (j - 1) / 2);
+        zdbl u = eri[((int64_t)(a * n + i) * n + b) * n + j];
+        zdbl v = eri[((int64_t)(a * n + j) * n + b) * n + i];
+        tab[t] = zdbl{u.x - v.x, u.y - v.y};
+    }
+}
+
+__global__ void k_to_f32(const double *__restrict__ in, float *__restrict__ out, int64_t n)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        out[t] = (float)in[t];
+}
+
+// ------------------------------------------------------------------ determinant kernels
+struct KeyRule {
+    int spinors, n, na, nb, N;
+};
+
+__global__ void k_validate(const uint64_t *__restrict__ keys, int64_t M, KeyRule r, int *status)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t d = keys[i];
+        int bad = 0;
+        if (r.spinors) {
+            if (__popcll(d) != r.N) bad |= sci::DEV_POPCOUNT;
+            if (r.n < 64 && (d >> r.n) != 0) bad |= sci::DEV_POPCOUNT;
+        } else {
+            uint64_t am = (r.n >= 64) ? ~0ull : ((1ull << r.n) - 1);
+            if (__popcll(d & am) != r.na || __popcll((d >> r.n) & am) != r.nb) bad |= sci::DEV_POPCOUNT;
+            if (2 * r.n < 64 && (d >> (2 * r.n)) != 0) bad |= sci::DEV_POPCOUNT;
+        }
+        if (i > 0) {
+            uint64_t prev = keys[i - 1];
+            if (prev == d) bad |= sci::DEV_DUPLICATE;
+            else if (prev > d) bad |= sci::DEV_UNSORTED;
+        }
+        if (bad) atomicOr(status, bad);
+    }
+}
+
+// H_II = sum_{i in occ} h_ii + 1/2 sum_{i,j in occ} [(ii|jj) - (ij|ji)]
+template <typename S>
+__global__ void k_diag(const uint64_t *__restrict__ keys, int64_t M, int norb, const S *__restrict__ h_so,
+                       const S *__restrict__ jd, const S *__restrict__ kd, double *__restrict__ hdiag)
+{
+    for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < M; I += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t d = keys[I];
+        double e1 = 0.0, e2 = 0.0;
+        for (uint64_t m = d; m; m &= m - 1) {
+            int i = __ffsll((long long)m) - 1;
+            e1 += Sc<S>::re(h_so[i * norb + i]);
+            for (uint64_t m2 = d; m2; m2 &= m2 - 1) {
+                int j = __ffsll((long long)m2) - 1;
+                e2 += Sc<S>::re(jd[i * norb + j]) - Sc<S>::re(kd[i * norb + j]);
+            }
+        }
+        hdiag[I] = e1 + 0.5 * e2;
+    }
+}
+
+// fref[i][a] = h_ai + sum_{k in ref} g_so[k][i][a]
+template <typename S>
+__global__ void k_fref(int norb, uint64_t ref, const S *__restrict__ h_so, const S *__restrict__ g_so,
+                       S *__restrict__ fref)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= norb * norb) return;
+    int i = t / norb, a = t % norb;
+    S f = h_so[a * norb + i];
+    for (uint64_t m = ref; m; m &= m - 1) {
+        int k = __ffsll((long long)m) - 1;
+        f = Sc<S>::add(f, g_so[((int64_t)k * norb + i) * norb + a]);
+    }
+    fref[t] = f;
+}
+
+// every determinant emits its keys with `holes` occupied bits removed (1 or 2)
+__global__ void k_emit(const uint64_t *__restrict__ keys, int64_t M, int holes, int per_det,
+                       uint64_t *__restrict__ out_keys, uint64_t *__restrict__ out_vals)
+{
+    for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < M; I += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t d = keys[I];
+        int64_t base = I * per_det;
+        int t = 0;
+        for (uint64_t m1 = d; m1; m1 &= m1 - 1) {
+            int x = __ffsll((long long)m1) - 1;
+            uint64_t bx = 1ull << x;
+            if (holes == 1) {
+                out_keys[base + t] = d & ~bx;
+                out_vals[base + t] = (uint64_t)I | ((uint64_t)x << 32);
+                t++;
+                continue;
+            }
+            for (uint64_t m2 = m1 & (m1 - 1); m2; m2 &= m2 - 1) {
+                int y = __ffsll((long long)m2) - 1;
+                out_keys[base + t] = d & ~bx & ~(1ull << y);
+                out_vals[base + t] = (uint64_t)I | ((uint64_t)x << 32) | ((uint64_t)y << 40);
+                t++;
+            }
+        }
+    }
+}
+
+__global__ void k_iota_u32(uint32_t *a, int64_t n)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        a[t] = (uint32_t)t;
+}
+
+__global__ void k_size_keys(const uint32_t *__restrict__ counts, int64_t n, uint16_t *__restrict__ sk,
+                            unsigned long long *kept, int *maxb)
+{
+    unsigned long long k = 0;
+    int mx = 0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t c = counts[t];
+        sk[t] = (uint16_t)(0xFFFFu - min(c, 0xFFFFu));
+        k += (c >= 2);
+        mx = max(mx, (int)min(c, 0x7FFFFFFFu));
+    }
+    for (int o = 16; o; o >>= 1) {
+        k += __shfl_down_sync(0xffffffffu, k, o);
+        mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (k) atomicAdd(kept, k);
+        atomicMax(maxb, mx);
+    }
+}
+
+__global__ void k_gather_sizes(const uint32_t *__restrict__ order, const uint32_t *__restrict__ counts, int64_t n,
+                               uint32_t *__restrict__ out)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        out[t] = counts[order[t]];
+}
+
+struct TabRule {
+    int spinors, n;
+};
+
+// bra offset (row) and ket offset (column) of a member with extra orbitals x < y
+__device__ inline void pair_offsets(TabRule r, int x, int y, uint32_t &rowoff, uint32_t &colbase)
+{
+    if (r.spinors) {
+        uint32_t NP = (uint32_t)(r.n * (r.n - 1) / 2);
+        uint32_t p = (uint32_t)pair_index(x, y);
+        rowoff = p;
+        colbase = p * NP;
+        return;
+    }
+    int n = r.n;
+    uint32_t n2 = (uint32_t)(n * n);
+    if (x < n && y >= n) {           // alpha-beta
+        uint32_t u = (uint32_t)((y - n) * n + x);
+        rowoff = u;
+        colbase = u * n2;
+    } else {                         // same spin
+        int a = x >= n ? x - n : x, b = y >= n ? y - n : y;
+        uint32_t NP = (uint32_t)(n * (n - 1) / 2);
+        uint32_t p = (uint32_t)pair_index(a, b);
+        rowoff = p;
+        colbase = n2 * n2 + p * NP;
+    }
+}
+
+__device__ inline int count_below(uint64_t k, int p) { return __popcll(k & ((1ull << p) - 1ull)); }
+
+// warp per kept bucket: scatter members into the final doubles table
+__global__ void k_fill2(const uint32_t *__restrict__ order, const uint32_t *__restrict__ counts,
+                        const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ newoff,
+                        const uint64_t *__restrict__ ukeys, const uint64_t *__restrict__ vals, int64_t kept,
+                        TabRule r, uint32_t *__restrict__ e_idx, uint64_t *__restrict__ e_mask,
+                        uint32_t *__restrict__ e_col, uint64_t *__restrict__ e_meta)
+{
+    int lane = threadIdx.x & 31;
+    int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t j = w; j < kept; j += nw) {
+        uint32_t b = order[j];
+        uint32_t size = counts[b], old = offsets[b], dst = newoff[j];
+        uint64_t K = ukeys[b];
+        for (uint32_t t = lane; t < size; t += 32) {
+            uint64_t v = vals[old + t];
+            int x = (int)((v >> 32) & 0xFF), y = (int)((v >> 40) & 0xFF);
+            uint32_t rowoff, colbase;
+            pair_offsets(r, x, y, rowoff, colbase);
+            uint64_t par = (uint64_t)((count_below(K, x) + count_below(K, y)) & 1);
+            e_idx[dst + t] = (uint32_t)(v & 0xFFFFFFFFull);
+            e_mask[dst + t] = (1ull << x) | (1ull << y);
+            e_col[dst + t] = colbase;
+            e_meta[dst + t] = (uint64_t)rowoff | (par << 16) | ((uint64_t)t << 32) | ((uint64_t)size << 48);
+        }
+    }
+}
+
+__global__ void k_fill1(const uint32_t *__restrict__ order, const uint32_t *__restrict__ counts,
+                        const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ newoff,
+                        const uint64_t *__restrict__ ukeys, const uint64_t *__restrict__ vals, int64_t kept,
+                        uint32_t *__restrict__ e_idx, uint64_t *__restrict__ e_S, uint32_t *__restrict__ e_meta)
+{
+    int lane = threadIdx.x & 31;
+    int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t j = w; j < kept; j += nw) {
+        uint32_t b = order[j];
+        uint32_t size = counts[b], old = offsets[b], dst = newoff[j];
+        uint64_t K = ukeys[b];
+        for (uint32_t t = lane; t < size; t += 32) {
+            uint64_t v = vals[old + t];
+            int x = (int)((v >> 32) & 0xFF);
+            uint32_t par = (uint32_t)(count_below(K, x) & 1);
+            e_idx[dst + t] = (uint32_t)(v & 0xFFFFFFFFull);
+            e_S[dst + t] = K;
+            e_meta[dst + t] = (uint32_t)x | (par << 7) | (t << 8) | (size << 20);
+        }
+    }
+}
+
+int grid_for(int64_t n, int threads = 256)
+{
+    int64_t g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > 152 * 64) g = 152 * 64;
+    return (int)g;
+}
+
+// Sort the emitted (key, value) pairs, group equal keys, drop singletons and return the
+// kept buckets ordered by size (largest first).
+struct Buckets {
+    TmpBuf ukeys, counts, offsets, order, newoff, vals_sorted;
+    int64_t kept = 0, entries = 0;
+    int maxb = 0;
+};
+
+int build_buckets(sci_ctx *ctx, int holes, int per_det, Buckets &B)
+{
+    cudaStream_t st = ctx->stream;
+    int64_t M = ctx->M;
+    int64_t total = M * per_det;
+    if (total >= (int64_t)1 << 31) return sci_fail(ctx, SCI_ERR_OVERFLOW, "too many bucket entries (>= 2^31)");
+    if (total == 0) return SCI_OK;
+    int nitems = (int)total;
+    TmpBuf ka, kb, va;
+    SCI_CK(cudaMalloc(&ka.p, total * 8));
+    SCI_CK(cudaMalloc(&kb.p, total * 8));
+    SCI_CK(cudaMalloc(&va.p, total * 8));
+    SCI_CK(cudaMalloc(&B.vals_sorted.p, total * 8));
+    k_emit<<<grid_for(M), 256, 0, st>>>(ctx->keys, M, holes, per_det, ka.as<uint64_t>(), va.as<uint64_t>());
+    SCI_CK(cudaGetLastError());
+    cub::DoubleBuffer<uint64_t> dk(ka.as<uint64_t>(), kb.as<uint64_t>());
+    cub::DoubleBuffer<uint64_t> dv(va.as<uint64_t>(), B.vals_sorted.as<uint64_t>());
+    int end_bit = ctx->norb;
+    size_t tb = 0;
+    SCI_CK(cub::DeviceRadixSort::SortPairs(nullptr, tb, dk, dv, nitems, 0, end_bit, st));
+    {
+        TmpBuf tmp;
+        SCI_CK(cudaMalloc(&tmp.p, tb));
+        SCI_CK(cub::DeviceRadixSort::SortPairs(tmp.p, tb, dk, dv, nitems, 0, end_bit, st));
+    }
+    // keep the sorted values; release the other value buffer
+    if (dv.Current() != B.vals_sorted.as<uint64_t>()) std::swap(va.p, B.vals_sorted.p);
+    cudaFree(va.p);
+    va.p = nullptr;
+    const uint64_t *sorted_keys = dk.Current();
+
+    // run-length encode the sorted keys
+    SCI_CK(cudaMalloc(&B.ukeys.p, total * 8));
+    SCI_CK(cudaMalloc(&B.counts.p, total * 4));
+    TmpBuf nruns_d;
+    SCI_CK(cudaMalloc(&nruns_d.p, 8));
+    tb = 0;
+    SCI_CK(cub::DeviceRunLengthEncode::Encode(nullptr, tb, sorted_keys, B.ukeys.as<uint64_t>(),
+                                              B.counts.as<uint32_t>(), nruns_d.as<int>(), nitems, st));
+    {
+        TmpBuf tmp;
+        SCI_CK(cudaMalloc(&tmp.p, tb));
+        SCI_CK(cub::DeviceRunLengthEncode::Encode(tmp.p, tb, sorted_keys, B.ukeys.as<uint64_t>(),
+                                                  B.counts.as<uint32_t>(), nruns_d.as<int>(), nitems, st));
+    }
+    int nruns = 0;
+    SCI_CK(cudaMemcpyAsync(&nruns, nruns_d.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SCI_CK(cudaStreamSynchronize(st));
+    cudaFree(ka.p); ka.p = nullptr;
+    cudaFree(kb.p); kb.p = nullptr;
+
+    // offsets of the runs in sorted order
+    SCI_CK(cudaMalloc(&B.offsets.p, (size_t)nruns * 4));
+    tb = 0;
+    SCI_CK(cub::DeviceScan::ExclusiveSum(nullptr, tb, B.counts.as<uint32_t>(), B.offsets.as<uint32_t>(), nruns, st));
+    {
+        TmpBuf tmp;
+        SCI_CK(cudaMalloc(&tmp.p, tb));
+        SCI_CK(cub::DeviceScan::ExclusiveSum(tmp.p, tb, B.counts.as<uint32_t>(), B.offsets.as<uint32_t>(), nruns, st));
+    }
+
+    // order runs by size, largest first (stable: equal sizes keep key order)
+    TmpBuf sk, sk2, ids, ids2, kept_d;
+    SCI_CK(cudaMalloc(&sk.p, (size_t)nruns * 2));
+    SCI_CK(cudaMalloc(&sk2.p, (size_t)nruns * 2));
+    SCI_CK(cudaMalloc(&ids.p, (size_t)nruns * 4));
+    SCI_CK(cudaMalloc(&ids2.p, (size_t)nruns * 4));
+    SCI_CK(cudaMalloc(&kept_d.p, 16));
+    SCI_CK(cudaMemsetAsync(kept_d.p, 0, 16, st));
+    k_size_keys<<<grid_for(nruns), 256, 0, st>>>(B.counts.as<uint32_t>(), nruns, sk.as<uint16_t>(),
+                                                 kept_d.as<unsigned long long>(),
+                                                 (int *)(kept_d.as<char>() + 8));
+    k_iota_u32<<<grid_for(nruns), 256, 0, st>>>(ids.as<uint32_t>(), nruns);
+    SCI_CK(cudaGetLastError());
+    cub::DoubleBuffer<uint16_t> dsk(sk.as<uint16_t>(), sk2.as<uint16_t>());
+    cub::DoubleBuffer<uint32_t> dids(ids.as<uint32_t>(), ids2.as<uint32_t>());
+    tb = 0;
+    SCI_CK(cub::DeviceRadixSort::SortPairs(nullptr, tb, dsk, dids, nruns, 0, 16, st));
+    {
+        TmpBuf tmp;
+        SCI_CK(cudaMalloc(&tmp.p, tb));
+        SCI_CK(cub::DeviceRadixSort::SortPairs(tmp.p, tb, dsk, dids, nruns, 0, 16, st));
+    }
+    unsigned long long kept_h = 0;
+    int maxb_h = 0;
+    SCI_CK(cudaMemcpyAsync(&kept_h, kept_d.p, 8, cudaMemcpyDeviceToHost, st));
+    SCI_CK(cudaMemcpyAsync(&maxb_h, kept_d.as<char>() + 8, 4, cudaMemcpyDeviceToHost, st));
+    SCI_CK(cudaStreamSynchronize(st));
+    B.kept = (int64_t)kept_h;
+    B.maxb = B.kept > 0 ? maxb_h : 0;
+    // keep the order array
+    if (dids.Current() == ids.as<uint32_t>()) std::swap(ids.p, B.order.p);
+    else std::swap(ids2.p, B.order.p);
+    if (B.kept == 0) return SCI_OK;
+
+    // new offsets of the kept runs
+    TmpBuf ksz;
+    SCI_CK(cudaMalloc(&ksz.p, (size_t)B.kept * 4));
+    SCI_CK(cudaMalloc(&B.newoff.p, (size_t)B.kept * 4));
+    k_gather_sizes<<<grid_for(B.kept), 256, 0, st>>>(B.order.as<uint32_t>(), B.counts.as<uint32_t>(), B.kept,
+                                                     ksz.as<uint32_t>());
+    SCI_CK(cudaGetLastError());
+    tb = 0;
+    SCI_CK(cub::DeviceScan::ExclusiveSum(nullptr, tb, ksz.as<uint32_t>(), B.newoff.as<uint32_t>(), (int)B.kept, st));
+    {
+        TmpBuf tmp;
+        SCI_CK(cudaMalloc(&tmp.p, tb));
+        SCI_CK(cub::DeviceScan::ExclusiveSum(tmp.p, tb, ksz.as<uint32_t>(), B.newoff.as<uint32_t>(), (int)B.kept, st));
+    }
+    uint32_t last_off = 0, last_size = 0;
+    SCI_CK(cudaMemcpyAsync(&last_off, B.newoff.as<uint32_t>() + (B.kept - 1), 4, cudaMemcpyDeviceToHost, st));
+    SCI_CK(cudaMemcpyAsync(&last_size, ksz.as<uint32_t>() + (B.kept - 1), 4, cudaMemcpyDeviceToHost, st));
+    SCI_CK(cudaStreamSynchronize(st));
+    B.entries = (int64_t)last_off + last_size;
+    return SCI_OK;
+}
+
+void free_dets(sci_ctx *ctx)
+{
+    free_held(ctx, ctx->keys);
+    free_held(ctx, ctx->hdiag);
+    free_held(ctx, ctx->fref);
+    free_held(ctx, ctx->e2_idx);
+    free_held(ctx, ctx->e2_mask);
+    free_held(ctx, ctx->e2_col);
+    free_held(ctx, ctx->e2_meta);
+    free_held(ctx, ctx->e1_idx);
+    free_held(ctx, ctx->e1_S);
+    free_held(ctx, ctx->e1_meta);
+    ctx->have_dets = 0;
+    ctx->M = 0;
+    ctx->e1 = ctx->e2 = ctx->nb1 = ctx->nb2 = 0;
+    ctx->maxb1 = ctx->maxb2 = 0;
+    ctx->pairs = ctx->pairs1 = ctx->pairs2 = 0;
+}
+
+void free_ints(sci_ctx *ctx)
+{
+    free_held(ctx, ctx->h_so);
+    free_held(ctx, ctx->jd);
+    free_held(ctx, ctx->kd);
+    free_held(ctx, ctx->g_so);
+    free_held(ctx, ctx->tab);
+    free_held(ctx, ctx->tab32);
+    ctx->have_ints = 0;
+}
+
+size_t scalar_bytes(const sci_ctx *ctx) { return ctx->cplx ? 16 : 8; }
+
+// diagonal and reference Fock matrix for the current integrals and determinants
+int compute_diag_fref(sci_ctx *ctx)
+{
+    cudaStream_t st = ctx->stream;
+    int norb = ctx->norb;
+    if (!ctx->fref) SCI_CK(alloc_held(ctx, &ctx->fref, (size_t)norb * norb * scalar_bytes(ctx)));
+    int nn = norb * norb;
+    if (ctx->cplx) {
+        k_fref<zdbl><<<(nn + 255) / 256, 256, 0, st>>>(norb, ctx->ref, (const zdbl *)ctx->h_so,
+                                                        (const zdbl *)ctx->g_so, (zdbl *)ctx->fref);
+        if (ctx->M > 0)
+            k_diag<zdbl><<<grid_for(ctx->M), 256, 0, st>>>(ctx->keys, ctx->M, norb, (const zdbl *)ctx->h_so,
+                                                           (const zdbl *)ctx->jd, (const zdbl *)ctx->kd, ctx->hdiag);
+    } else {
+        k_fref<double><<<(nn + 255) / 256, 256, 0, st>>>(norb, ctx->ref, (const double *)ctx->h_so,
+                                                          (const double *)ctx->g_so, (double *)ctx->fref);
+        if (ctx->M > 0)
+            k_diag<double><<<grid_for(ctx->M), 256, 0, st>>>(ctx->keys, ctx->M, norb, (const double *)ctx->h_so,
+                                                             (const double *)ctx->jd, (const double *)ctx->kd,
+                                                             ctx->hdiag);
+    }
+    SCI_CK(cudaGetLastError());
+    return SCI_OK;
+}
+
+bool rel_close(double a, double b, double scale) { return std::fabs(a - b) <= 1e-10 * scale; }
+
+}  // namespace
+
+// ================================================================== public API
+extern "C" int sci_create(sci_ctx **out, int device, void *cuda_stream)
+{
+    if (!out) return SCI_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        cudaGetLastError();
+        return SCI_ERR_CUDA;
+    }
+    if (device < 0 || device >= ndev) return SCI_ERR_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return SCI_ERR_CUDA;
+    sci_ctx *ctx = new sci_ctx();
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    if (cudaMalloc(&ctx->status, sizeof(int)) != cudaSuccess || cudaMemset(ctx->status, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return SCI_ERR_NOMEM;
+    }
+    *out = ctx;
+    return SCI_OK;
+}
+
+extern "C" int sci_destroy(sci_ctx *ctx)
+{
+    if (!ctx) return SCI_OK;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    free_dets(ctx);
+    free_ints(ctx);
+    if (ctx->stage_c) cudaFree(ctx->stage_c);
+    if (ctx->stage_s) cudaFree(ctx->stage_s);
+    for (auto &e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    if (ctx->status) cudaFree(ctx->status);
+    delete ctx;
+    return SCI_OK;
+}
+
+extern "C" int sci_set_stream(sci_ctx *ctx, void *cuda_stream)
+{
+    if (!ctx) return SCI_ERR_ARG;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return SCI_OK;
+}
+
+extern "C" int sci_set_integrals(sci_ctx *ctx, int scalar, int mode, int n, const void *h, const void *eri,
+                                 int naux, const void *chol)
+{
+    if (!ctx) return SCI_ERR_ARG;
+    ctx->err.clear();
+    if (scalar != SCI_REAL64 && scalar != SCI_COMPLEX128) return sci_fail(ctx, SCI_ERR_ARG, "bad scalar type");
+    if (mode != SCI_SPIN_ORBITALS && mode != SCI_SPINORS) return sci_fail(ctx, SCI_ERR_ARG, "bad mode");
+    if (mode == SCI_SPIN_ORBITALS && (n < 1 || n > 32)) return sci_fail(ctx, SCI_ERR_ARG, "spin-orbital mode needs 1 <= n <= 32");
+    if (mode == SCI_SPINORS && (n < 1 || n > 64)) return sci_fail(ctx, SCI_ERR_ARG, "spinor mode needs 1 <= n <= 64");
+    if (mode == SCI_SPIN_ORBITALS && scalar != SCI_REAL64)
+        return sci_fail(ctx, SCI_ERR_ARG, "spin-orbital mode takes real integrals");
+    if (!h) return sci_fail(ctx, SCI_ERR_ARG, "h is NULL");
+    if ((eri == nullptr) == (chol == nullptr)) return sci_fail(ctx, SCI_ERR_ARG, "give exactly one of eri / chol");
+    if (chol && naux < 1) return sci_fail(ctx, SCI_ERR_ARG, "naux < 1");
+    SCI_CK(cudaSetDevice(ctx->device));
+    const int cplx = scalar == SCI_COMPLEX128;
+    const int sw = cplx ? 2 : 1;  // doubles per scalar
+    const double *hd = (const double *)h;
+    int64_t n2 = (int64_t)n * n, n4 = n2 * n2;
+
+    // ---- host-side symmetry checks (h Hermitian; (pq|rs) = (rs|pq) = (qp|sr)^*)
+    double hs = 0;
+    for (int64_t t = 0; t < n2 * sw; t++) hs = std::max(hs, std::fabs(hd[t]));
+    for (int p = 0; p < n; p++)
+        for (int q = 0; q < n; q++) {
+            int64_t a = (int64_t)p * n + q, b = (int64_t)q * n + p;
+            if (!rel_close(hd[a * sw], hd[b * sw], hs + 1e-300) ||
+                (cplx && !rel_close(hd[a * sw + 1], -hd[b * sw + 1], hs + 1e-300)))
+                return sci_fail(ctx, SCI_ERR_ARG, "h is not Hermitian");
+        }
+    if (eri) {
+        const double *e = (const double *)eri;
+        double es = 0;
+        for (int64_t t = 0; t < n4 * sw; t++) es = std::max(es, std::fabs(e[t]));
+        es += 1e-300;
+        for (int p = 0; p < n; p++)
+            for (int q = 0; q < n; q++)
+                for (int r = 0; r < n; r++)
+                    for (int s = 0; s < n; s++) {
+                        int64_t a = ((int64_t)(p * n + q) * n + r) * n + s;
+                        int64_t b = ((int64_t)(r * n + s) * n + p) * n + q;
+                        int64_t c = ((int64_t)(q * n + p) * n + s) * n + r;
+                        if (!rel_close(e[a * sw], e[b * sw], es) || !rel_close(e[a * sw], e[c * sw], es))
+                            return sci_fail(ctx, SCI_ERR_ARG, "eri lacks (pq|rs)=(rs|pq)=(qp|sr)^* symmetry");
+                        if (cplx && (!rel_close(e[a * sw + 1], e[b * sw + 1], es) ||
+                                     !rel_close(e[a * sw + 1], -e[c * sw + 1], es)))
+                            return sci_fail(ctx, SCI_ERR_ARG, "eri lacks (pq|rs)=(rs|pq)=(qp|sr)^* symmetry");
+                    }
+    } else {
+        const double *L = (const double *)chol;
+        double ls = 0;
+        for (int64_t t = 0; t < (int64_t)naux * n2 * sw; t++) ls = std::max(ls, std::fabs(L[t]));
+        ls += 1e-300;
+        for (int P = 0; P < naux; P++)
+            for (int p = 0; p < n; p++)
+                for (int q = 0; q < n; q++) {
+                    int64_t a = P * n2 + (int64_t)p * n + q, b = P * n2 + (int64_t)q * n + p;
+                    if (!rel_close(L[a * sw], L[b * sw], ls) || (cplx && !rel_close(L[a * sw + 1], -L[b * sw + 1], ls)))
+                        return sci_fail(ctx, SCI_ERR_ARG, "Cholesky vectors are not Hermitian");
+                }
+    }
+
+    int keep_dets = ctx->have_dets && ctx->have_ints && ctx->cplx == cplx && ctx->n == n &&
+                    ctx->spinors == (mode == SCI_SPINORS);
+    if (!keep_dets) free_dets(ctx);
+    free_ints(ctx);
+    ctx->cplx = cplx;
+    ctx->spinors = mode == SCI_SPINORS;
+    ctx->n = n;
+    ctx->norb = ctx->spinors ? n : 2 * n;
+    const size_t sb = cplx ? 16 : 8;
+    cudaStream_t st = ctx->stream;
+
+    TmpBuf dh, deri;
+    SCI_CK(cudaMalloc(&dh.p, n2 * sb));
+    SCI_CK(cudaMemcpyAsync(dh.p, h, n2 * sb, cudaMemcpyHostToDevice, st));
+    SCI_CK(cudaMalloc(&deri.p, n4 * sb));
+    if (eri) {
+        SCI_CK(cudaMemcpyAsync(deri.p, eri, n4 * sb, cudaMemcpyHostToDevice, st));
+    } else {
+        TmpBuf dl;
+        SCI_CK(cudaMalloc(&dl.p, (size_t)naux * n2 * sb));
+        SCI_CK(cudaMemcpyAsync(dl.p, chol, (size_t)naux * n2 * sb, cudaMemcpyHostToDevice, st));
+        if (cplx) k_eri_from_chol<zdbl><<<grid_for(n4), 256, 0, st>>>(dl.as<zdbl>(), naux, n, deri.as<zdbl>());
+        else k_eri_from_chol<double><<<grid_for(n4), 256, 0, st>>>(dl.as<double>(), naux, n, deri.as<double>());
+        SCI_CK(cudaGetLastError());
+        SCI_CK(cudaStreamSynchronize(st));
+    }
+    int norb = ctx->norb;
+    SCI_CK(alloc_held(ctx, &ctx->h_so, (size_t)norb * norb * sb));
+    SCI_CK(alloc_held(ctx, &ctx->jd, (size_t)norb * norb * sb));
+    SCI_CK(alloc_held(ctx, &ctx->kd, (size_t)norb * norb * sb));
+    SCI_CK(alloc_held(ctx, &ctx->g_so, (size_t)norb * norb * norb * sb));
+    OrbMap om{n, ctx->spinors};
+    int64_t n3 = (int64_t)norb * norb * norb;
+    if (cplx)
+        k_small_tables<zdbl><<<grid_for(n3), 256, 0, st>>>(dh.as<zdbl>(), deri.as<zdbl>(), om, norb, (zdbl *)ctx->h_so,
+                                                           (zdbl *)ctx->jd, (zdbl *)ctx->kd, (zdbl *)ctx->g_so);
+    else
+        k_small_tables<double><<<grid_for(n3), 256, 0, st>>>(dh.as<double>(), deri.as<double>(), om, norb,
+                                                             (double *)ctx->h_so, (double *)ctx->jd, (double *)ctx->kd,
+                                                             (double *)ctx->g_so);
+    SCI_CK(cudaGetLastError());
+    int64_t NP = (int64_t)n * (n - 1) / 2;
+    if (ctx->spinors) {
+        ctx->tab_elems = NP * NP;
+        SCI_CK(alloc_held(ctx, &ctx->tab, (size_t)ctx->tab_elems * sb));
+        if (cplx) {
+            if (ctx->tab_elems > 0)
+                k_tab_spinor<<<grid_for(ctx->tab_elems), 256, 0, st>>>(deri.as<zdbl>(), n, (zdbl *)ctx->tab);
+        } else {
+            return sci_fail(ctx, SCI_ERR_ARG, "spinor mode takes complex integrals");
+        }
+    } else {
+        ctx->tab_elems = n4 + NP * NP;
+        SCI_CK(alloc_held(ctx, &ctx->tab, (size_t)ctx->tab_elems * sb));
+        k_tab_real<<<grid_for(ctx->tab_elems), 256, 0, st>>>(deri.as<double>(), n, (double *)ctx->tab);
+        SCI_CK(alloc_held(ctx, (void **)&ctx->tab32, (size_t)ctx->tab_elems * 4));
+        k_to_f32<<<grid_for(ctx->tab_elems), 256, 0, st>>>((const double *)ctx->tab, ctx->tab32, ctx->tab_elems);
+    }
+    SCI_CK(cudaGetLastError());
+    ctx->have_ints = 1;
+    if (ctx->have_dets) {
+        int rc = compute_diag_fref(ctx);
+        if (rc != SCI_OK) return rc;
+    }
+    SCI_CK(cudaStreamSynchronize(st));
+    return SCI_OK;
+}
+
+extern "C" int sci_set_determinants(sci_ctx *ctx, const uint64_t *keys, int64_t M, int n_alpha, int n_beta,
+                                    int keys_on_device)
+{
+    if (!ctx) return SCI_ERR_ARG;
+    ctx->err.clear();
+    if (!ctx->have_ints) return sci_fail(ctx, SCI_ERR_STATE, "set integrals before determinants");
+    if (M < 0 || (M > 0 && !keys)) return sci_fail(ctx, SCI_ERR_ARG, "bad key array");
+    if (M >= ((int64_t)1 << 31)) return sci_fail(ctx, SCI_ERR_OVERFLOW, "M >= 2^31");
+    int N;
+    if (ctx->spinors) {
+        if (n_beta != -1 || n_alpha < 0 || n_alpha > ctx->n)
+            return sci_fail(ctx, SCI_ERR_ARG, "spinor mode: n_alpha = N in [0, n], n_beta = -1");
+        N = n_alpha;
+    } else {
+        if (n_alpha < 0 || n_beta < 0 || n_alpha > ctx->n || n_beta > ctx->n)
+            return sci_fail(ctx, SCI_ERR_ARG, "electron counts out of range");
+        N = n_alpha + n_beta;
+    }
+    SCI_CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    free_dets(ctx);
+    ctx->M = M;
+    ctx->na = n_alpha;
+    ctx->nb = ctx->spinors ? -1 : n_beta;
+    ctx->N = N;
+    if (ctx->spinors) ctx->ref = (N >= 64) ? ~0ull : ((1ull << N) - 1);
+    else ctx->ref = ((1ull << n_alpha) - 1) | (((1ull << n_beta) - 1) << ctx->n);
+
+    SCI_CK(alloc_held(ctx, (void **)&ctx->keys, (size_t)M * 8));
+    SCI_CK(alloc_held(ctx, (void **)&ctx->hdiag, (size_t)M * 8));
+    if (M > 0)
+        SCI_CK(cudaMemcpyAsync(ctx->keys, keys, (size_t)M * 8,
+                               keys_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    // K0: validation
+    SCI_CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), st));
+    if (M > 0) {
+        KeyRule kr{ctx->spinors, ctx->n, n_alpha, n_beta, N};
+        k_validate<<<grid_for(M), 256, 0, st>>>(ctx->keys, M, kr, ctx->status);
+        SCI_CK(cudaGetLastError());
+    }
+    int dev_status = 0;
+    SCI_CK(cudaMemcpyAsync(&dev_status, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SCI_CK(cudaStreamSynchronize(st));
+    if (dev_status) {
+        cudaMemsetAsync(ctx->status, 0, sizeof(int), st);
+        free_dets(ctx);
+        if (dev_status & sci::DEV_DUPLICATE) return sci_fail(ctx, SCI_ERR_DUPLICATE, "determinant list has duplicates");
+        if (dev_status & sci::DEV_UNSORTED) return sci_fail(ctx, SCI_ERR_UNSORTED, "determinant list is not ascending");
+        return sci_fail(ctx, SCI_ERR_POPCOUNT, "a key has the wrong electron count or stray bits");
+    }
+    int rc = compute_diag_fref(ctx);
+    if (rc != SCI_OK) return rc;
+
+    // (N-2)-hole buckets: doubles
+    TabRule tr{ctx->spinors, ctx->n};
+    if (N >= 2) {
+        Buckets B;
+        rc = build_buckets(ctx, 2, N * (N - 1) / 2, B);
+        if (rc != SCI_OK) { free_dets(ctx); return rc; }
+        ctx->e2 = B.entries;
+        ctx->nb2 = B.kept;
+        ctx->maxb2 = B.maxb;
+        SCI_CK(alloc_held(ctx, (void **)&ctx->e2_idx, (size_t)B.entries * 4));
+        SCI_CK(alloc_held(ctx, (void **)&ctx->e2_mask, (size_t)B.entries * 8));
+        SCI_CK(alloc_held(ctx, (void **)&ctx->e2_col, (size_t)B.entries * 4));
+        SCI_CK(alloc_held(ctx, (void **)&ctx->e2_meta, (size_t)B.entries * 8));
+        if (B.kept > 0) {
+            k_fill2<<<grid_for(B.kept * 32), 256, 0, st>>>(B.order.as<uint32_t>(), B.counts.as<uint32_t>(),
+                                                          B.offsets.as<uint32_t>(), B.newoff.as<uint32_t>(),
+                                                          B.ukeys.as<uint64_t>(), B.vals_sorted.as<uint64_t>(), B.kept,
+                                                          tr, ctx->e2_idx, ctx->e2_mask, ctx->e2_col, ctx->e2_meta);
+            SCI_CK(cudaGetLastError());
+        }
+        SCI_CK(cudaStreamSynchronize(st));
+    }
+    // (N-1)-hole buckets: singles
+    if (N >= 1) {
+        Buckets B;
+        rc = build_buckets(ctx, 1, N, B);
+        if (rc != SCI_OK) { free_dets(ctx); return rc; }
+        ctx->e1 = B.entries;
+        ctx->nb1 = B.kept;
+        ctx->maxb1 = B.maxb;
+        SCI_CK(alloc_held(ctx, (void **)&ctx->e1_idx, (size_t)B.entries * 4));
+        SCI_CK(alloc_held(ctx, (void **)&ctx->e1_S, (size_t)B.entries * 8));
+        SCI_CK(alloc_held(ctx, (void **)&ctx->e1_meta, (size_t)B.entries * 4));
+        if (B.kept > 0) {
+            k_fill1<<<grid_for(B.kept * 32), 256, 0, st>>>(B.order.as<uint32_t>(), B.counts.as<uint32_t>(),
+                                                          B.offsets.as<uint32_t>(), B.newoff.as<uint32_t>(),
+                                                          B.ukeys.as<uint64_t>(), B.vals_sorted.as<uint64_t>(), B.kept,
+                                                          ctx->e1_idx, ctx->e1_S, ctx->e1_meta);
+            SCI_CK(cudaGetLastError());
+        }
+        SCI_CK(cudaStreamSynchronize(st));
+    }
+    if (ctx->maxb2 > 0xFFFF || ctx->maxb1 > 4095) {
+        free_dets(ctx);
+        return sci_fail(ctx, SCI_ERR_OVERFLOW, "bucket larger than the table format allows");
+    }
+    ctx->have_dets = 1;
+    int64_t p2 = 0, p1 = 0;
+    rc = sci_count_pairs_device(ctx, &p2, &p1);
+    if (rc != SCI_OK) { free_dets(ctx); return rc; }
+    ctx->pairs2 = p2;
+    ctx->pairs1 = p1;
+    ctx->pairs = p1 + p2;
+    return SCI_OK;
+}
+
+extern "C" int sci_diagonal(sci_ctx *ctx, double *hdiag)
+{
+    if (!ctx) return SCI_ERR_ARG;
+    if (!ctx->have_dets) return sci_fail(ctx, SCI_ERR_STATE, "no determinants");
+    if (ctx->M > 0 && !hdiag) return sci_fail(ctx, SCI_ERR_ARG, "hdiag is NULL");
+    if (ctx->M == 0) return SCI_OK;
+    SCI_CK(cudaSetDevice(ctx->device));
+    SCI_CK(cudaMemcpyAsync(hdiag, ctx->hdiag, (size_t)ctx->M * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    return SCI_OK;
+}
+
+extern "C" int sci_sigma(sci_ctx *ctx, const void *C, void *S, int nvec, int prec)
+{
+    if (!ctx) return SCI_ERR_ARG;
+    if (!ctx->have_dets || !ctx->have_ints) return sci_fail(ctx, SCI_ERR_STATE, "integrals and determinants needed");
+    if (nvec < 1) return sci_fail(ctx, SCI_ERR_ARG, "nvec < 1");
+    if (prec != SCI_PREC_F64 && prec != SCI_PREC_F32_STORE_F64_ACC) return sci_fail(ctx, SCI_ERR_ARG, "bad prec");
+    if (prec == SCI_PREC_F32_STORE_F64_ACC && ctx->cplx)
+        return sci_fail(ctx, SCI_ERR_ARG, "FP32 storage is available for real Hamiltonians only");
+    if (ctx->M == 0) return SCI_OK;
+    if (!C || !S) return sci_fail(ctx, SCI_ERR_ARG, "C or S is NULL");
+    SCI_CK(cudaSetDevice(ctx->device));
+    return sci_launch_sigma(ctx, C, S, nvec, prec);
+}
+
+extern "C" int sci_sigma_host(sci_ctx *ctx, const void *C_host, void *S_host, int nvec, int prec)
+{
+    if (!ctx) return SCI_ERR_ARG;
+    if (!ctx->have_dets || !ctx->have_ints) return sci_fail(ctx, SCI_ERR_STATE, "integrals and determinants needed");
+    if (nvec < 1) return sci_fail(ctx, SCI_ERR_ARG, "nvec < 1");
+    if (ctx->M == 0) return SCI_OK;
+    if (!C_host || !S_host) return sci_fail(ctx, SCI_ERR_ARG, "C or S is NULL");
+    if (prec != SCI_PREC_F64 && prec != SCI_PREC_F32_STORE_F64_ACC) return sci_fail(ctx, SCI_ERR_ARG, "bad prec");
+    SCI_CK(cudaSetDevice(ctx->device));
+    size_t sb = ctx->cplx ? 16 : 8;
+    size_t cb = (size_t)ctx->M * nvec * (prec == SCI_PREC_F32_STORE_F64_ACC ? 4 : sb);
+    size_t obytes = (size_t)ctx->M * nvec * sb;
+    size_t need = std::max(cb, obytes);
+    if (need > ctx->stage_bytes) {
+        if (ctx->stage_c) cudaFree(ctx->stage_c);
+        if (ctx->stage_s) cudaFree(ctx->stage_s);
+        ctx->stage_c = ctx->stage_s = nullptr;
+        ctx->stage_bytes = 0;
+        SCI_CK(cudaMalloc(&ctx->stage_c, need));
+        SCI_CK(cudaMalloc(&ctx->stage_s, need));
+        ctx->stage_bytes = need;
+    }
+    SCI_CK(cudaMemcpyAsync(ctx->stage_c, C_host, cb, cudaMemcpyHostToDevice, ctx->stream));
+    int rc = sci_sigma(ctx, ctx->stage_c, ctx->stage_s, nvec, prec);
+    if (rc != SCI_OK) return rc;
+    SCI_CK(cudaMemcpyAsync(S_host, ctx->stage_s, obytes, cudaMemcpyDeviceToHost, ctx->stream));
+    SCI_CK(cudaStreamSynchronize(ctx->stream));
+    return SCI_OK;
+}
+
+extern "C" int sci_profile(sci_ctx *ctx, int enable)
+{
+    if (!ctx) return SCI_ERR_ARG;
+    SCI_CK(cudaSetDevice(ctx->device));
+    if (enable)
+        for (auto &e : ctx->ev)
+            if (!e) SCI_CK(cudaEventCreate(&e));
+    ctx->profile = enable ? 1 : 0;
+    return SCI_OK;
+}
+
+extern "C" int sci_kernel_times(sci_ctx *ctx, float *ms, int n)
+{
+    if (!ctx || !ms || n < 0 || n > 3) return SCI_ERR_ARG;
+    if (!ctx->ev[3]) return sci_fail(ctx, SCI_ERR_STATE, "profiling was never enabled");
+    SCI_CK(cudaSetDevice(ctx->device));
+    SCI_CK(cudaEventSynchronize(ctx->ev[3]));
+    for (int i = 0; i < n; i++) SCI_CK(cudaEventElapsedTime(&ms[i], ctx->ev[i], ctx->ev[i + 1]));
+    return SCI_OK;
+}
+
+extern "C" int sci_connections(sci_ctx *ctx, int64_t row_begin, int64_t row_end, int64_t *count, int64_t *rows,
+                               int64_t *J, int8_t *degree, int8_t *phase, int64_t cap)
+{
+    if (!ctx || !count) return SCI_ERR_ARG;
+    if (!ctx->have_dets) return sci_fail(ctx, SCI_ERR_STATE, "no determinants");
+    if (row_begin < 0 || row_end > ctx->M || row_begin > row_end || cap < 0)
+        return sci_fail(ctx, SCI_ERR_ARG, "bad row range or capacity");
+    SCI_CK(cudaSetDevice(ctx->device));
+    return sci_connections_device(ctx, row_begin, row_end, count, rows, J, degree, phase, cap);
+}
+
+extern "C" int sci_count_pairs(sci_ctx *ctx, int64_t *pairs)
+{
+    if (!ctx || !pairs) return SCI_ERR_ARG;
+    if (!ctx->have_dets) return sci_fail(ctx, SCI_ERR_STATE, "no determinants");
+    *pairs = ctx->pairs;
+    return SCI_OK;
+}
+
+extern "C" int sci_info(sci_ctx *ctx, int64_t *out, int n)
+{
+    if (!ctx || !out || n < 0 || n > 10) return SCI_ERR_ARG;
+    int64_t v[10] = {ctx->M, ctx->pairs, ctx->e2, ctx->nb2, ctx->e1, ctx->nb1, std::max(ctx->maxb1, ctx->maxb2),
+                     (int64_t)ctx->bytes_held, ctx->pairs2, ctx->pairs1};
+    for (int i = 0; i < n; i++) out[i] = v[i];
+    return SCI_OK;
+}
+
+extern "C" int sci_sync_status(sci_ctx *ctx)
+{
+    if (!ctx) return SCI_ERR_ARG;
+    SCI_CK(cudaSetDevice(ctx->device));
+    int s = 0;
+    SCI_CK(cudaMemcpyAsync(&s, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    SCI_CK(cudaStreamSynchronize(ctx->stream));
+    if (s & sci::DEV_OVERFLOW) return sci_fail(ctx, SCI_ERR_OVERFLOW, "device reported an overflow");
+    if (s) return sci_fail(ctx, SCI_ERR_CUDA, "device status word set");
+    return SCI_OK;
+}
+
+extern "C" const char *sci_last_error(const sci_ctx *ctx)
+{
+    if (!ctx) return "null context";
+    return ctx->err.c_str();
+}

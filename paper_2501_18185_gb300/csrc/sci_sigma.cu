@@ -1,0 +1,506 @@
+// libsci hot path: sigma = H c (Sec. 2.4, the diagonalisation paragraph).
+//
+// sigma_I = H_II c_I + sum_{J single of I} H_IJ c_J + sum_{J double of I} H_IJ c_J,
+// each off-diagonal element evaluated on the fly from the two occupation strings by the
+// Slater-Condon rules (Sec. 2.3: matrix-element categories with 0, 1, 2 differences).
+//
+// Connection finding is done once at setup by bucketing: two determinants are within a
+// double excitation exactly when they share an (N-2)-electron sub-string K, and they
+// share exactly one such K when they differ by a double excitation.  So the doubles of
+// the whole space are the disjoint pairs inside the buckets of equal K.  For a bra
+// I = K + {a,b} and a ket J = K + {i,j} (a<b, i<j):
+//     H_IJ = (-1)^(pi_I + pi_J) [(ai|bj) - (aj|bi)],
+//     pi_X = #(K below x) + #(K below y) for the extras {x,y} of X,
+// since applying a_j, a_i, a+_a, a+_b to J passes pi_J + pi_I + 2 occupied orbitals.
+// Singles are the pairs inside the buckets of equal (N-1)-electron S:
+//     H_IJ = (-1)^(pi_I + pi_J) [h_ai + sum_{k in S} ((ai|kk) - (ak|ki))],
+// evaluated as F^ref_ai plus the terms of the orbitals where S and the reference differ
+// (the closed-shell reference simplification of Sec. 2.3).
+//
+// Kernel shape (bucket-major, no tensor cores: this is a sparse gather).  A CTA owns a
+// contiguous range of table entries (rows) and stages, in shared memory, every member of
+// the buckets those rows belong to: the member's extra-orbital mask, its ket offset into
+// the pair-integral table and its coefficients pre-multiplied by (-1)^pi.  Each thread
+// owns a row and walks the members of its bucket; lanes of a warp that share a bucket
+// read the same member (a shared-memory broadcast) and consecutive pair-table entries
+// (the table stores bra indices fastest).  A row's partial sum is added to sigma with
+// one FP64 atomic add per (bucket, member).
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
+#include "sci_internal.cuh"
+
+using sci::zdbl;
+
+namespace {
+
+// ------------------------------------------------------------------ scalar ops
+__device__ __forceinline__ double neg(double a) { return -a; }
+__device__ __forceinline__ float neg(float a) { return -a; }
+__device__ __forceinline__ zdbl neg(zdbl a) { return zdbl{-a.x, -a.y}; }
+
+__device__ __forceinline__ void zero(double &a) { a = 0.0; }
+__device__ __forceinline__ void zero(zdbl &a) { a = zdbl{0.0, 0.0}; }
+
+// acc += t * c
+__device__ __forceinline__ void fma_acc(double &acc, double t, double c) { acc = fma(t, c, acc); }
+__device__ __forceinline__ void fma_acc(double &acc, float t, float c) { acc = fma((double)t, (double)c, acc); }
+__device__ __forceinline__ void fma_acc(zdbl &acc, zdbl t, zdbl c)
+{
+    acc.x = fma(t.x, c.x, acc.x);
+    acc.x = fma(-t.y, c.y, acc.x);
+    acc.y = fma(t.x, c.y, acc.y);
+    acc.y = fma(t.y, c.x, acc.y);
+}
+__device__ __forceinline__ void fma_acc(double &acc, double t, float c) { acc = fma(t, (double)c, acc); }
+
+__device__ __forceinline__ void red_add(double *p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void red_add(zdbl *p, zdbl v)
+{
+    atomicAdd(&p->x, v.x);
+    atomicAdd(&p->y, v.y);
+}
+
+__device__ __forceinline__ double sgn(bool neg_, double a) { return neg_ ? -a : a; }
+__device__ __forceinline__ zdbl sgn(bool neg_, zdbl a) { return neg_ ? zdbl{-a.x, -a.y} : a; }
+
+template <typename T> __device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
+template <> __device__ __forceinline__ zdbl ldg<zdbl>(const zdbl *p)
+{
+    double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+    return zdbl{v.x, v.y};
+}
+
+// acc type for a storage type
+template <typename TS> struct AccOf { using type = double; };
+template <> struct AccOf<zdbl> { using type = zdbl; };
+
+constexpr int kThreads = 256;
+
+// ------------------------------------------------------------------ sigma = diag * c
+template <typename TC, typename TA>
+__global__ void k_sigma_init(const double *__restrict__ hdiag, const TC *__restrict__ C, TA *__restrict__ S,
+                             int64_t M, int nvec)
+{
+    int64_t total = M * nvec;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        double h = hdiag[t / nvec];
+        TA s;
+        zero(s);
+        if constexpr (sizeof(TC) == sizeof(zdbl)) {
+            zdbl c = C[t];
+            s = TA{h * c.x, h * c.y};
+        } else {
+            s = (TA)(h * (double)C[t]);
+        }
+        S[t] = s;
+    }
+}
+
+// ------------------------------------------------------------------ doubles
+// TS: storage type of tab and staged coefficients; TA: accumulator (FP64 / complex128).
+template <typename TS, typename TC, int NV>
+__global__ void __launch_bounds__(kThreads)
+k_doubles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_mask, const uint32_t *__restrict__ e_col,
+          const uint64_t *__restrict__ e_meta, int64_t E, int CH, const TS *__restrict__ tab,
+          const TC *__restrict__ C, int nvec, int v0, typename AccOf<TS>::type *__restrict__ Sout)
+{
+    using TA = typename AccOf<TS>::type;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int64_t r0 = (int64_t)blockIdx.x * CH;
+    if (r0 >= E) return;
+    const int64_t r1 = min(r0 + (int64_t)CH, E);
+    const uint64_t mf = e_meta[r0], ml = e_meta[r1 - 1];
+    const int64_t w0 = r0 - (int64_t)((mf >> 32) & 0xFFFF);
+    const int64_t w1 = (r1 - 1) - (int64_t)((ml >> 32) & 0xFFFF) + (int64_t)(ml >> 48);
+    const int W = (int)(w1 - w0);
+    TS *s_c = reinterpret_cast<TS *>(smem);
+    size_t cbytes = ((size_t)W * NV * sizeof(TS) + 15) & ~(size_t)15;
+    uint64_t *s_mask = reinterpret_cast<uint64_t *>(smem + cbytes);
+    uint32_t *s_col = reinterpret_cast<uint32_t *>(s_mask + W);
+
+    for (int q = threadIdx.x; q < W; q += blockDim.x) {
+        const int64_t g = w0 + q;
+        const uint32_t idx = e_idx[g];
+        const bool par = (e_meta[g] >> 16) & 1;
+        s_mask[q] = e_mask[g];
+        s_col[q] = e_col[g];
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            TS c = (TS)C[(int64_t)idx * nvec + v0 + v];
+            s_c[q * NV + v] = par ? neg(c) : c;
+        }
+    }
+    __syncthreads();
+
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        const int q0 = (int)(r - w0);
+        const uint64_t meta = e_meta[r];
+        const uint32_t rowoff = (uint32_t)(meta & 0xFFFF);
+        const bool par = (meta >> 16) & 1;
+        const int bs = q0 - (int)((meta >> 32) & 0xFFFF);
+        const int be = bs + (int)(meta >> 48);
+        const uint64_t rmask = s_mask[q0];
+        TA acc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) zero(acc[v]);
+        for (int j = bs; j < be; j++) {
+            if (s_mask[j] & rmask) continue;  // same member, or a single: not a double
+            const TS t = ldg(tab + s_col[j] + rowoff);
+#pragma unroll
+            for (int v = 0; v < NV; v++) fma_acc(acc[v], t, s_c[j * NV + v]);
+        }
+        const uint32_t idx = e_idx[r];
+#pragma unroll
+        for (int v = 0; v < NV; v++) red_add(Sout + (int64_t)idx * nvec + v0 + v, sgn(par, acc[v]));
+    }
+}
+
+// ------------------------------------------------------------------ singles
+template <typename TS, typename TC, int NV>
+__global__ void __launch_bounds__(kThreads)
+k_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S, const uint32_t *__restrict__ e_meta,
+          int64_t E, int norb, uint64_t ref, const TS *__restrict__ fref, const TS *__restrict__ g_so,
+          const TC *__restrict__ C, int nvec, int v0, typename AccOf<TS>::type *__restrict__ Sout)
+{
+    using TA = typename AccOf<TS>::type;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t meta = e_meta[p];
+        const int a = (int)(meta & 0x7F);
+        const bool par = (meta >> 7) & 1;
+        const int64_t bs = p - (int64_t)((meta >> 8) & 0xFFF);
+        const int64_t be = bs + (int64_t)(meta >> 20);
+        const uint64_t Sk = e_S[p];
+        const uint64_t part = Sk & ~ref, holes = ref & ~Sk;
+        TA acc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) zero(acc[v]);
+        for (int64_t q = bs; q < be; q++) {
+            if (q == p) continue;
+            const uint32_t mq = e_meta[q];
+            const int i = (int)(mq & 0x7F);
+            const bool parq = (mq >> 7) & 1;
+            const uint32_t idxq = e_idx[q];
+            TS f = ldg(fref + i * norb + a);
+            for (uint64_t m = part; m; m &= m - 1) {
+                int k = __ffsll((long long)m) - 1;
+                TS g = ldg(g_so + ((int64_t)k * norb + i) * norb + a);
+                if constexpr (sizeof(TS) == sizeof(zdbl)) { f.x += g.x; f.y += g.y; } else { f += g; }
+            }
+            for (uint64_t m = holes; m; m &= m - 1) {
+                int k = __ffsll((long long)m) - 1;
+                TS g = ldg(g_so + ((int64_t)k * norb + i) * norb + a);
+                if constexpr (sizeof(TS) == sizeof(zdbl)) { f.x -= g.x; f.y -= g.y; } else { f -= g; }
+            }
+#pragma unroll
+            for (int v = 0; v < NV; v++) {
+                TC c = C[(int64_t)idxq * nvec + v0 + v];
+                if (parq) c = neg(c);
+                fma_acc(acc[v], f, c);
+            }
+        }
+        const uint32_t idx = e_idx[p];
+#pragma unroll
+        for (int v = 0; v < NV; v++) red_add(Sout + (int64_t)idx * nvec + v0 + v, sgn(par, acc[v]));
+    }
+}
+
+int grid_for(int64_t n, int threads = kThreads)
+{
+    int64_t g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > 152 * 32) g = 152 * 32;
+    return (int)g;
+}
+
+// rows per CTA so that the staged window fits the shared-memory budget
+int choose_rows(int maxb, size_t bytes_per_entry, size_t &smem)
+{
+    const size_t budgets[2] = {100 * 1024, 200 * 1024};
+    for (size_t budget : budgets) {
+        int64_t ch = (int64_t)(budget / bytes_per_entry) - 2 * (int64_t)(maxb - 1) - 8;
+        if (ch >= 512 || (budget == budgets[1] && ch >= 64)) {
+            ch = std::min<int64_t>(ch, 2048);
+            ch = std::max<int64_t>(64, ch & ~(int64_t)63);
+            smem = (size_t)(ch + 2 * (maxb - 1)) * bytes_per_entry + 64;
+            return (int)ch;
+        }
+    }
+    return -1;
+}
+
+template <typename TS, typename TC, int NV>
+int launch_doubles(sci_ctx *ctx, const TS *tab, const TC *C, typename AccOf<TS>::type *S, int nvec, int v0)
+{
+    if (ctx->e2 == 0) return SCI_OK;
+    size_t per = NV * sizeof(TS) + 8 + 4;
+    size_t smem = 0;
+    int ch = choose_rows(ctx->maxb2, per, smem);
+    if (ch < 0) return sci_fail(ctx, SCI_ERR_OVERFLOW, "bucket too large for shared memory");
+    auto kern = k_doubles<TS, TC, NV>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return sci_cuda_check(ctx, e, "cudaFuncSetAttribute");
+    int64_t blocks = (ctx->e2 + ch - 1) / ch;
+    kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(ctx->e2_idx, ctx->e2_mask, ctx->e2_col, ctx->e2_meta,
+                                                          ctx->e2, ch, tab, C, nvec, v0, S);
+    return sci_cuda_check(ctx, cudaGetLastError(), "k_doubles launch");
+}
+
+template <typename TS, typename TC, int NV>
+int launch_singles(sci_ctx *ctx, const TC *C, typename AccOf<TS>::type *S, int nvec, int v0)
+{
+    if (ctx->e1 == 0) return SCI_OK;
+    k_singles<TS, TC, NV><<<grid_for(ctx->e1), kThreads, 0, ctx->stream>>>(
+        ctx->e1_idx, ctx->e1_S, ctx->e1_meta, ctx->e1, ctx->norb, ctx->ref, (const TS *)ctx->fref,
+        (const TS *)ctx->g_so, C, nvec, v0, S);
+    return sci_cuda_check(ctx, cudaGetLastError(), "k_singles launch");
+}
+
+template <typename TS, typename TC>
+int sigma_groups(sci_ctx *ctx, const TS *tab, const TC *C, typename AccOf<TS>::type *S, int nvec)
+{
+    int rc = SCI_OK;
+    for (int v0 = 0; v0 < nvec && rc == SCI_OK;) {
+        int left = nvec - v0;
+        int g = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+        if (sizeof(TS) == 16 && g > 4) g = 4;
+        size_t smem_probe = 0;  // shrink the vector group until its window fits
+        while (g > 1 && choose_rows(ctx->maxb2, g * sizeof(TS) + 12, smem_probe) < 0) g >>= 1;
+        switch (g) {
+        case 8: rc = launch_doubles<TS, TC, 8>(ctx, tab, C, S, nvec, v0); break;
+        case 4: rc = launch_doubles<TS, TC, 4>(ctx, tab, C, S, nvec, v0); break;
+        case 2: rc = launch_doubles<TS, TC, 2>(ctx, tab, C, S, nvec, v0); break;
+        default: rc = launch_doubles<TS, TC, 1>(ctx, tab, C, S, nvec, v0); break;
+        }
+        v0 += g;
+    }
+    return rc;
+}
+
+template <typename TS, typename TC>
+int singles_groups(sci_ctx *ctx, const TC *C, typename AccOf<TS>::type *S, int nvec)
+{
+    int rc = SCI_OK;
+    for (int v0 = 0; v0 < nvec && rc == SCI_OK;) {
+        int left = nvec - v0;
+        int g = left >= 4 ? 4 : left >= 2 ? 2 : 1;
+        switch (g) {
+        case 4: rc = launch_singles<TS, TC, 4>(ctx, C, S, nvec, v0); break;
+        case 2: rc = launch_singles<TS, TC, 2>(ctx, C, S, nvec, v0); break;
+        default: rc = launch_singles<TS, TC, 1>(ctx, C, S, nvec, v0); break;
+        }
+        v0 += g;
+    }
+    return rc;
+}
+
+// ------------------------------------------------------------------ pair counting
+__global__ void k_count2(const uint64_t *__restrict__ e_mask, const uint64_t *__restrict__ e_meta, int64_t E,
+                         unsigned long long *out)
+{
+    unsigned long long cnt = 0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t meta = e_meta[p];
+        int64_t bs = p - (int64_t)((meta >> 32) & 0xFFFF), be = bs + (int64_t)(meta >> 48);
+        uint64_t m = e_mask[p];
+        for (int64_t q = bs; q < be; q++) cnt += (e_mask[q] & m) == 0;
+    }
+    for (int o = 16; o; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(out, cnt);
+}
+
+__global__ void k_count1(const uint32_t *__restrict__ e_meta, int64_t E, unsigned long long *out)
+{
+    unsigned long long cnt = 0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x)
+        cnt += (e_meta[p] >> 20) - 1;
+    for (int o = 16; o; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(out, cnt);
+}
+
+// ------------------------------------------------------------------ connection export
+struct ConnOut {
+    int64_t *row, *col;
+    int8_t *deg, *ph;
+    int64_t cap;
+    unsigned long long *counter;
+};
+
+__device__ __forceinline__ void conn_put(ConnOut o, int64_t r, int64_t c, int d, int ph)
+{
+    unsigned long long s = atomicAdd(o.counter, 1ull);
+    if ((int64_t)s < o.cap) {
+        o.row[s] = r;
+        o.col[s] = c;
+        o.deg[s] = (int8_t)d;
+        o.ph[s] = (int8_t)ph;
+    }
+}
+
+__global__ void k_conn2(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_mask,
+                        const uint64_t *__restrict__ e_meta, int64_t E, int64_t rb, int64_t re, ConnOut o)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
+        int64_t I = e_idx[p];
+        if (I < rb || I >= re) continue;
+        uint64_t meta = e_meta[p];
+        int64_t bs = p - (int64_t)((meta >> 32) & 0xFFFF), be = bs + (int64_t)(meta >> 48);
+        uint64_t m = e_mask[p];
+        int par = (meta >> 16) & 1;
+        for (int64_t q = bs; q < be; q++) {
+            if (e_mask[q] & m) continue;
+            int parq = (e_meta[q] >> 16) & 1;
+            conn_put(o, I, e_idx[q], 2, (par ^ parq) ? -1 : 1);
+        }
+    }
+}
+
+__global__ void k_conn1(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_meta, int64_t E, int64_t rb,
+                        int64_t re, ConnOut o)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
+        int64_t I = e_idx[p];
+        if (I < rb || I >= re) continue;
+        uint32_t meta = e_meta[p];
+        int64_t bs = p - (int64_t)((meta >> 8) & 0xFFF), be = bs + (int64_t)(meta >> 20);
+        int par = (meta >> 7) & 1;
+        for (int64_t q = bs; q < be; q++) {
+            if (q == p) continue;
+            int parq = (e_meta[q] >> 7) & 1;
+            conn_put(o, I, e_idx[q], 1, (par ^ parq) ? -1 : 1);
+        }
+    }
+}
+
+}  // namespace
+
+#define SCI_CK(call)                                                 \
+    do {                                                             \
+        int _rc = sci_cuda_check(ctx, (call), #call);                \
+        if (_rc != SCI_OK) return _rc;                               \
+    } while (0)
+
+namespace {
+inline void mark(sci_ctx *ctx, int i)
+{
+    if (ctx->profile) cudaEventRecord(ctx->ev[i], ctx->stream);
+}
+}  // namespace
+
+int sci_launch_sigma(sci_ctx *ctx, const void *C, void *S, int nvec, int prec)
+{
+    cudaStream_t st = ctx->stream;
+    int64_t M = ctx->M;
+    int rc;
+    mark(ctx, 0);
+    if (ctx->cplx) {
+        const zdbl *Cz = (const zdbl *)C;
+        zdbl *Sz = (zdbl *)S;
+        k_sigma_init<zdbl, zdbl><<<grid_for(M * nvec), kThreads, 0, st>>>(ctx->hdiag, Cz, Sz, M, nvec);
+        SCI_CK(cudaGetLastError());
+        mark(ctx, 1);
+        rc = sigma_groups<zdbl, zdbl>(ctx, (const zdbl *)ctx->tab, Cz, Sz, nvec);
+        mark(ctx, 2);
+        if (rc == SCI_OK) rc = singles_groups<zdbl, zdbl>(ctx, Cz, Sz, nvec);
+        mark(ctx, 3);
+        return rc;
+    }
+    double *Sd = (double *)S;
+    if (prec == SCI_PREC_F64) {
+        const double *Cd = (const double *)C;
+        k_sigma_init<double, double><<<grid_for(M * nvec), kThreads, 0, st>>>(ctx->hdiag, Cd, Sd, M, nvec);
+        SCI_CK(cudaGetLastError());
+        mark(ctx, 1);
+        rc = sigma_groups<double, double>(ctx, (const double *)ctx->tab, Cd, Sd, nvec);
+        mark(ctx, 2);
+        if (rc == SCI_OK) rc = singles_groups<double, double>(ctx, Cd, Sd, nvec);
+        mark(ctx, 3);
+        return rc;
+    }
+    const float *Cf = (const float *)C;
+    k_sigma_init<float, double><<<grid_for(M * nvec), kThreads, 0, st>>>(ctx->hdiag, Cf, Sd, M, nvec);
+    SCI_CK(cudaGetLastError());
+    mark(ctx, 1);
+    rc = sigma_groups<float, float>(ctx, ctx->tab32, Cf, Sd, nvec);
+    mark(ctx, 2);
+    if (rc == SCI_OK) rc = singles_groups<double, float>(ctx, Cf, Sd, nvec);
+    mark(ctx, 3);
+    return rc;
+}
+
+int sci_count_pairs_device(sci_ctx *ctx, int64_t *pairs2, int64_t *pairs1)
+{
+    cudaStream_t st = ctx->stream;
+    unsigned long long *d = nullptr;
+    SCI_CK(cudaMalloc(&d, 16));
+    cudaMemsetAsync(d, 0, 16, st);
+    if (ctx->e2 > 0) k_count2<<<grid_for(ctx->e2), kThreads, 0, st>>>(ctx->e2_mask, ctx->e2_meta, ctx->e2, d);
+    if (ctx->e1 > 0) k_count1<<<grid_for(ctx->e1), kThreads, 0, st>>>(ctx->e1_meta, ctx->e1, d + 1);
+    unsigned long long h[2] = {0, 0};
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, 16, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d);
+    SCI_CK(e);
+    *pairs2 = (int64_t)h[0];
+    *pairs1 = (int64_t)h[1];
+    return SCI_OK;
+}
+
+int sci_connections_device(sci_ctx *ctx, int64_t row_begin, int64_t row_end, int64_t *count, int64_t *rows,
+                           int64_t *J, int8_t *degree, int8_t *phase, int64_t cap)
+{
+    cudaStream_t st = ctx->stream;
+    unsigned long long *counter = nullptr;
+    SCI_CK(cudaMalloc(&counter, 8));
+    // pass 1: count
+    ConnOut o{nullptr, nullptr, nullptr, nullptr, 0, counter};
+    cudaMemsetAsync(counter, 0, 8, st);
+    if (ctx->e2 > 0) k_conn2<<<grid_for(ctx->e2), kThreads, 0, st>>>(ctx->e2_idx, ctx->e2_mask, ctx->e2_meta, ctx->e2, row_begin, row_end, o);
+    if (ctx->e1 > 0) k_conn1<<<grid_for(ctx->e1), kThreads, 0, st>>>(ctx->e1_idx, ctx->e1_meta, ctx->e1, row_begin, row_end, o);
+    unsigned long long n = 0;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&n, counter, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { cudaFree(counter); return sci_cuda_check(ctx, e, "connection count"); }
+    *count = (int64_t)n;
+    if ((int64_t)n > cap) { cudaFree(counter); return sci_fail(ctx, SCI_ERR_OVERFLOW, "connection list exceeds cap"); }
+    if (n == 0) { cudaFree(counter); return SCI_OK; }
+    // pass 2: fill
+    void *buf = nullptr;
+    e = cudaMalloc(&buf, n * 18);
+    if (e != cudaSuccess) { cudaFree(counter); return sci_cuda_check(ctx, e, "connection buffer"); }
+    o.row = (int64_t *)buf;
+    o.col = o.row + n;
+    o.deg = (int8_t *)(o.col + n);
+    o.ph = o.deg + n;
+    o.cap = (int64_t)n;
+    cudaMemsetAsync(counter, 0, 8, st);
+    if (ctx->e2 > 0) k_conn2<<<grid_for(ctx->e2), kThreads, 0, st>>>(ctx->e2_idx, ctx->e2_mask, ctx->e2_meta, ctx->e2, row_begin, row_end, o);
+    if (ctx->e1 > 0) k_conn1<<<grid_for(ctx->e1), kThreads, 0, st>>>(ctx->e1_idx, ctx->e1_meta, ctx->e1, row_begin, row_end, o);
+    std::vector<int64_t> hr(n), hc(n);
+    std::vector<int8_t> hd(n), hp(n);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hr.data(), o.row, n * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), o.col, n * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hd.data(), o.deg, n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hp.data(), o.ph, n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(buf);
+    cudaFree(counter);
+    SCI_CK(e);
+    std::vector<int64_t> perm(n);
+    for (size_t t = 0; t < n; t++) perm[t] = (int64_t)t;
+    std::sort(perm.begin(), perm.end(), [&](int64_t a, int64_t b) {
+        return hr[a] != hr[b] ? hr[a] < hr[b] : hc[a] < hc[b];
+    });
+    for (size_t t = 0; t < n; t++) {
+        int64_t s = perm[t];
+        if (rows) rows[t] = hr[s];
+        if (J) J[t] = hc[s];
+        if (degree) degree[t] = hd[s];
+        if (phase) phase[t] = hp[s];
+    }
+    return SCI_OK;
+}

@@ -1,0 +1,291 @@
+"""Python binding of libsci (include/sci.h): argument marshalling only.
+
+Every step of the sigma path runs in the CUDA kernels of libsci.so; this module passes
+pointers and sizes.  PyTorch supplies device memory and the stream.  There is no CPU
+fallback: if libsci.so is missing or no GPU is visible, the calls raise.
+
+The functions named sci_* mirror the C entry points one to one; ``Hamiltonian`` is a
+small convenience class over them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+SCI_OK = 0
+SCI_ERR_ARG = -1
+SCI_ERR_UNSORTED = -2
+SCI_ERR_DUPLICATE = -3
+SCI_ERR_POPCOUNT = -4
+SCI_ERR_NOMEM = -5
+SCI_ERR_CUDA = -6
+SCI_ERR_STATE = -7
+SCI_ERR_OVERFLOW = -8
+SCI_ERR_TIMEOUT = -9
+SCI_REAL64, SCI_COMPLEX128 = 1, 2
+SCI_SPIN_ORBITALS, SCI_SPINORS = 1, 2
+SCI_PREC_F64, SCI_PREC_F32_STORE_F64_ACC = 1, 2
+
+# every entry point declared in include/sci.h, with (restype, argtypes)
+_vp, _i32, _i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+SIGNATURES = {
+    "sci_create": (_i32, [ctypes.POINTER(_vp), _i32, _vp]),
+    "sci_destroy": (_i32, [_vp]),
+    "sci_set_stream": (_i32, [_vp, _vp]),
+    "sci_set_integrals": (_i32, [_vp, _i32, _i32, _i32, _vp, _vp, _i32, _vp]),
+    "sci_set_determinants": (_i32, [_vp, _vp, _i64, _i32, _i32, _i32]),
+    "sci_diagonal": (_i32, [_vp, _vp]),
+    "sci_sigma": (_i32, [_vp, _vp, _vp, _i32, _i32]),
+    "sci_connections": (_i32, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _i64]),
+    "sci_count_pairs": (_i32, [_vp, _vp]),
+    "sci_sigma_host": (_i32, [_vp, _vp, _vp, _i32, _i32]),
+    "sci_info": (_i32, [_vp, _vp, _i32]),
+    "sci_profile": (_i32, [_vp, _i32]),
+    "sci_kernel_times": (_i32, [_vp, _vp, _i32]),
+    "sci_sync_status": (_i32, [_vp]),
+    "sci_last_error": (ctypes.c_char_p, [_vp]),
+}
+
+_lib = None
+
+
+class SciError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libsci error {code}: {msg}")
+        self.code = code
+
+
+def load(path: str | None = None):
+    """Load libsci.so (built by build.build()); raises if it is missing."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is not built: run paper_2501_18185_gb300.build.build() "
+                           "(there is no CPU fallback)")
+    L = ctypes.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    if path is None:
+        _lib = L
+    return L
+
+
+def _check(ctx, rc):
+    if rc != SCI_OK:
+        msg = load().sci_last_error(ctx) if ctx else b""
+        raise SciError(rc, (msg or b"").decode())
+    return rc
+
+
+def _p(x):
+    """Raw address of a numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return ctypes.c_void_p(x.ctypes.data)
+    return ctypes.c_void_p(x.data_ptr())
+
+
+# ---------------------------------------------------------------- thin C mirrors
+def sci_create(device: int = 0, stream: int | None = None):
+    ctx = ctypes.c_void_p()
+    rc = load().sci_create(ctypes.byref(ctx), device, ctypes.c_void_p(stream or 0))
+    if rc != SCI_OK:
+        raise SciError(rc, "sci_create failed")
+    return ctx
+
+
+def sci_destroy(ctx):
+    return load().sci_destroy(ctx)
+
+
+def sci_set_stream(ctx, stream: int | None):
+    return _check(ctx, load().sci_set_stream(ctx, ctypes.c_void_p(stream or 0)))
+
+
+def sci_set_integrals(ctx, scalar, mode, n, h, eri=None, naux=0, chol=None):
+    return _check(ctx, load().sci_set_integrals(ctx, scalar, mode, n, _p(h), _p(eri), naux, _p(chol)))
+
+
+def sci_set_determinants(ctx, keys, M, n_alpha, n_beta, keys_on_device):
+    return _check(ctx, load().sci_set_determinants(ctx, _p(keys), M, n_alpha, n_beta, keys_on_device))
+
+
+def sci_diagonal(ctx, hdiag):
+    return _check(ctx, load().sci_diagonal(ctx, _p(hdiag)))
+
+
+def sci_sigma(ctx, C, S, nvec, prec):
+    return _check(ctx, load().sci_sigma(ctx, _p(C), _p(S), nvec, prec))
+
+
+def sci_connections(ctx, row_begin, row_end, cap):
+    cnt = np.zeros(1, dtype=np.int64)
+    rows = np.zeros(max(cap, 1), dtype=np.int64)
+    J = np.zeros(max(cap, 1), dtype=np.int64)
+    deg = np.zeros(max(cap, 1), dtype=np.int8)
+    ph = np.zeros(max(cap, 1), dtype=np.int8)
+    rc = load().sci_connections(ctx, row_begin, row_end, _p(cnt), _p(rows), _p(J), _p(deg), _p(ph), cap)
+    if rc == SCI_ERR_OVERFLOW:
+        return int(cnt[0]), None
+    _check(ctx, rc)
+    n = int(cnt[0])
+    return n, (rows[:n], J[:n], deg[:n], ph[:n])
+
+
+def sci_count_pairs(ctx) -> int:
+    out = np.zeros(1, dtype=np.int64)
+    _check(ctx, load().sci_count_pairs(ctx, _p(out)))
+    return int(out[0])
+
+
+def sci_sigma_host(ctx, C, S, nvec, prec):
+    return _check(ctx, load().sci_sigma_host(ctx, _p(C), _p(S), nvec, prec))
+
+
+def sci_info(ctx) -> dict:
+    out = np.zeros(10, dtype=np.int64)
+    _check(ctx, load().sci_info(ctx, _p(out), 10))
+    keys = ["M", "pairs", "b2_entries", "b2_buckets", "b1_entries", "b1_buckets", "max_bucket", "device_bytes",
+            "pairs_doubles", "pairs_singles"]
+    return dict(zip(keys, (int(v) for v in out)))
+
+
+def sci_profile(ctx, enable: bool):
+    return _check(ctx, load().sci_profile(ctx, int(enable)))
+
+
+def sci_kernel_times(ctx) -> list:
+    ms = np.zeros(3, dtype=np.float32)
+    _check(ctx, load().sci_kernel_times(ctx, _p(ms), 3))
+    return [float(x) for x in ms]
+
+
+def sci_sync_status(ctx):
+    return _check(ctx, load().sci_sync_status(ctx))
+
+
+def sci_last_error(ctx) -> str:
+    return (load().sci_last_error(ctx) or b"").decode()
+
+
+# ---------------------------------------------------------------- convenience class
+class Hamiltonian:
+    """One libsci context: integrals + a sorted determinant list on one GPU.
+
+    mode "spin_orbitals" (n <= 32 spatial orbitals, real) or "spinors" (n <= 64 spinors,
+    complex).  Tensors are torch CUDA tensors on the context's device; work is queued on
+    the torch stream that is current when the context is created (or set_stream()).
+    """
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("libsci needs a CUDA device (no CPU fallback)")
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.stream = s
+        self.ctx = sci_create(device, s.cuda_stream)
+        self.mode = None
+        self.M = 0
+        self.complex = False
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            sci_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self.stream = stream
+        sci_set_stream(self.ctx, stream.cuda_stream)
+
+    def set_integrals(self, mode: str, h, eri=None, chol=None):
+        self.mode = mode
+        self.complex = bool(np.iscomplexobj(h))
+        dt = np.complex128 if self.complex else np.float64
+        n = h.shape[0]
+        h = np.ascontiguousarray(h, dtype=dt)
+        e = None if eri is None else np.ascontiguousarray(eri, dtype=dt)
+        L = None if chol is None else np.ascontiguousarray(chol, dtype=dt)
+        sci_set_integrals(self.ctx, SCI_COMPLEX128 if self.complex else SCI_REAL64,
+                          SCI_SPINORS if mode == "spinors" else SCI_SPIN_ORBITALS, n, h, e,
+                          0 if L is None else L.shape[0], L)
+        self.n = n
+
+    def set_determinants(self, keys, n_alpha: int, n_beta: int):
+        torch = self.torch
+        if isinstance(keys, torch.Tensor):
+            k = keys.contiguous()
+            on_dev = int(k.is_cuda)
+            M = k.numel()
+        else:
+            k = np.ascontiguousarray(keys, dtype=np.uint64)
+            on_dev = 0
+            M = len(k)
+        sci_set_determinants(self.ctx, k, M, n_alpha, n_beta if self.mode != "spinors" else -1, on_dev)
+        self.M = M
+
+    @classmethod
+    def from_workload(cls, w, device: int = 0, use_chol: bool = True):
+        H = cls(device)
+        if use_chol:
+            H.set_integrals(w.mode, w.ints.h, chol=w.ints.chol)
+        else:
+            H.set_integrals(w.mode, w.ints.h, eri=w.ints.eri())
+        H.set_determinants(w.keys, w.n_alpha, w.n_beta)
+        return H
+
+    def diagonal(self):
+        d = self.torch.empty(self.M, dtype=self.torch.float64, device=self.device)
+        sci_diagonal(self.ctx, d)
+        return d
+
+    def sigma(self, C, out=None, prec: int = SCI_PREC_F64):
+        """S = H C for C of shape [M] or [M, nvec] (torch CUDA, contiguous)."""
+        torch = self.torch
+        squeeze = C.dim() == 1
+        nvec = 1 if squeeze else C.shape[1]
+        C2 = C.reshape(self.M, nvec).contiguous()
+        odt = torch.complex128 if self.complex else torch.float64
+        S = out if out is not None else torch.empty((self.M, nvec), dtype=odt, device=self.device)
+        sci_sigma(self.ctx, C2, S, nvec, prec)
+        return S.reshape(-1) if squeeze and out is None else S
+
+    def connections(self, row_begin: int = 0, row_end: int | None = None):
+        row_end = self.M if row_end is None else row_end
+        n, _ = sci_connections(self.ctx, row_begin, row_end, 0)
+        n2, arrs = sci_connections(self.ctx, row_begin, row_end, n)
+        return arrs
+
+    def count_pairs(self) -> int:
+        return sci_count_pairs(self.ctx)
+
+    def sigma_host(self, C: np.ndarray, out: np.ndarray | None = None, prec: int = SCI_PREC_F64):
+        """S = H C with host (numpy or pinned torch CPU) buffers; synchronous."""
+        nvec = 1 if C.ndim == 1 else C.shape[1]
+        if out is None:
+            out = np.empty((self.M, nvec), dtype=np.complex128 if self.complex else np.float64)
+        sci_sigma_host(self.ctx, C, out, nvec, prec)
+        return out
+
+    def info(self) -> dict:
+        return sci_info(self.ctx)
+
+    def sync_status(self):
+        return sci_sync_status(self.ctx)
