@@ -39,11 +39,11 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
 
-def make_workload(name: str, nvec: int):
+def make_workload(name: str, nvec: int, M: int | None = None):
     if name == "sel_30o":
-        return W.selected_30o(nvec=nvec)
+        return W.selected_30o(nvec=nvec) if M is None else W.selected_30o(M=M, nvec=nvec)
     if name == "sel_64s":
-        return W.selected_spinor_64(nvec=nvec)
+        return W.selected_spinor_64(nvec=nvec) if M is None else W.selected_spinor_64(M=M, nvec=nvec)
     if name == "fci_8o":
         return W.fci_small_8o()
     raise SystemExit(f"unknown workload {name}")
@@ -134,7 +134,7 @@ def run_reference(args, rank, world):
         return
     from oracle import Oracle
 
-    w = make_workload(args.workload, args.nvec)
+    w = make_workload(args.workload, args.nvec, args.M)
     o = Oracle.from_workload(w)
     rng = np.random.default_rng(1)
     nrows = args.ref_rows
@@ -166,6 +166,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="sel_30o")
     ap.add_argument("--nvec", type=int, default=1)
+    ap.add_argument("--M", type=int, default=None, help="smaller space of the same recipe (profiling)")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--ref-rows", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -193,7 +194,7 @@ def main():
     torch.cuda.set_device(dev)
     build.build()
 
-    w = make_workload(args.workload, args.nvec)
+    w = make_workload(args.workload, args.nvec, args.M)
     stream = torch.cuda.current_stream(dev)
     t = time.perf_counter()
     H = sci.Hamiltonian(local, stream)
