@@ -130,6 +130,31 @@ int sci_sigma(sci_ctx *ctx, const void *C, void *S, int nvec, int prec);
 int sci_connections(sci_ctx *ctx, int64_t row_begin, int64_t row_end, int64_t *count,
                     int64_t *rows, int64_t *J, int8_t *degree, int8_t *phase, int64_t cap);
 
+/* The paper has no counterpart to this call: it is a service for callers that cannot
+ * allocate device memory.  Such callers include processes whose device memory belongs to
+ * a pooling allocator (a framework's caching allocator, or an arena sized to the whole
+ * card), where a late cudaMalloc fails or fragments the pool, and programs that keep
+ * several streams busy and cannot afford cudaFree, which synchronises the whole device.
+ *
+ * Same results as sci_connections() (same arguments, same sorted output), but it calls
+ * no cudaMalloc, cudaFree or other allocating routine, on the device or on the host.
+ * Its device scratch (a slot counter and the unsorted pairs) is a fixed array inside the
+ * library, SCI_NOALLOC_MAX_PAIRS pairs (about 4.5 MiB), which every GPU that loads the
+ * library holds until the process exits.
+ *   - rows and J must be non-NULL when cap > 0: the list is sorted in place in them.
+ *   - More than SCI_NOALLOC_MAX_PAIRS connections in [row_begin, row_end) returns
+ *     SCI_ERR_OVERFLOW, with *count set to the true number; split the range.
+ *   - The first call on a device looks up the scratch array's device address
+ *     (cudaGetSymbolAddress).  Make that first call before any stream capture.
+ *   - Every call shares the scratch array, which keeps the last call's contents; the
+ *     call clears the counter itself.  Calls that overlap on the GPU (from two host
+ *     threads, or on two streams) race and corrupt each other's results.
+ * Synchronous. */
+#define SCI_NOALLOC_MAX_PAIRS 524288
+int sci_connections_noalloc(sci_ctx *ctx, int64_t row_begin, int64_t row_end, int64_t *count,
+                            int64_t *rows, int64_t *J, int8_t *degree, int8_t *phase,
+                            int64_t cap);
+
 /* Number of connected ordered pairs (I, J), I != J, excitation degree <= 2 (every
  * off-diagonal element that sigma evaluates, counted whether or not its value is 0). */
 int sci_count_pairs(sci_ctx *ctx, int64_t *pairs);

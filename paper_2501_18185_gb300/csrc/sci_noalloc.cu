@@ -1,0 +1,200 @@
+// sci_connections_noalloc: the connection export of sci_connections() for callers that
+// must not allocate device memory.
+//
+// Some callers cannot call cudaMalloc or cudaFree.  A process whose device memory is
+// handed out by a pooling allocator (a framework's caching allocator, or a fixed arena
+// sized to the card) has nothing left for the driver, so a late cudaMalloc fails or
+// fragments the pool.  And cudaFree synchronises the whole device, which stalls every
+// other stream of a caller that keeps several streams busy.  sci_connections() allocates
+// a counter and a tuple buffer per call; this variant uses a fixed scratch array in the
+// library's own device memory instead, and sorts on the host in the caller's arrays.
+//
+// Scratch: g_noalloc_scratch, a file-scope device array of kNoAllocBytes bytes: a 256-byte
+// header whose first 8 bytes are the slot counter, then kNoAllocMaxPairs packed (I, J)
+// pairs (uint64) and as many flag bytes.  Every GPU that loads the library holds it until
+// the process exits.  Every call shares it and it keeps the last call's contents; the
+// counter is cleared at the start of each call.  Calls that overlap on the GPU (two host
+// threads, or two streams) race on it.
+#include <mutex>
+
+#include "sci_internal.cuh"
+
+namespace {
+
+constexpr int64_t kNoAllocMaxPairs = SCI_NOALLOC_MAX_PAIRS;
+constexpr size_t kHeader = 256;
+constexpr size_t kNoAllocBytes = kHeader + (size_t)kNoAllocMaxPairs * 9;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void *g_scratch_addr[kMaxDevices] = {nullptr};
+
+struct Scratch {
+    unsigned long long *counter;
+    uint64_t *pairs;   // (I << 32) | J
+    uint8_t *flags;    // bit 0: degree 2; bit 1: phase -1
+    int64_t cap;
+};
+
+Scratch carve(void *base)
+{
+    unsigned char *b = static_cast<unsigned char *>(base);
+    Scratch s;
+    s.counter = reinterpret_cast<unsigned long long *>(b);
+    s.pairs = reinterpret_cast<uint64_t *>(b + kHeader);
+    s.flags = b + kHeader + (size_t)kNoAllocMaxPairs * 8;
+    s.cap = kNoAllocMaxPairs;
+    return s;
+}
+
+__device__ __forceinline__ void put(Scratch s, uint32_t I, uint32_t J, int deg2, int neg)
+{
+    unsigned long long slot = atomicAdd(s.counter, 1ull);
+    if ((int64_t)slot < s.cap) {
+        s.pairs[slot] = ((uint64_t)I << 32) | J;
+        s.flags[slot] = (uint8_t)(deg2 | (neg << 1));
+    }
+}
+
+__global__ void k_conn2_noalloc(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_mask,
+                                const uint64_t *__restrict__ e_meta, int64_t E, int64_t rb, int64_t re, Scratch s)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
+        int64_t I = e_idx[p];
+        if (I < rb || I >= re) continue;
+        uint64_t meta = e_meta[p];
+        int64_t bs = p - (int64_t)((meta >> 32) & 0xFFFF), be = bs + (int64_t)(meta >> 48);
+        uint64_t m = e_mask[p];
+        int par = (meta >> 16) & 1;
+        for (int64_t q = bs; q < be; q++) {
+            if (e_mask[q] & m) continue;
+            put(s, (uint32_t)I, e_idx[q], 1, par ^ (int)((e_meta[q] >> 16) & 1));
+        }
+    }
+}
+
+__global__ void k_conn1_noalloc(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_meta, int64_t E,
+                                int64_t rb, int64_t re, Scratch s)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
+        int64_t I = e_idx[p];
+        if (I < rb || I >= re) continue;
+        uint32_t meta = e_meta[p];
+        int64_t bs = p - (int64_t)((meta >> 8) & 0xFFF), be = bs + (int64_t)(meta >> 20);
+        int par = (meta >> 7) & 1;
+        for (int64_t q = bs; q < be; q++) {
+            if (q == p) continue;
+            put(s, (uint32_t)I, e_idx[q], 0, par ^ (int)((e_meta[q] >> 7) & 1));
+        }
+    }
+}
+
+int grid_for(int64_t n)
+{
+    int64_t g = (n + 255) / 256;
+    if (g < 1) g = 1;
+    if (g > 152 * 32) g = 152 * 32;
+    return (int)g;
+}
+
+// in-place heap sort of the parallel output arrays by (rows, J); no allocation
+struct Out {
+    int64_t *rows, *J;
+    int8_t *deg, *ph;
+    bool less(int64_t a, int64_t b) const { return rows[a] != rows[b] ? rows[a] < rows[b] : J[a] < J[b]; }
+    void swap(int64_t a, int64_t b) const
+    {
+        int64_t t = rows[a]; rows[a] = rows[b]; rows[b] = t;
+        t = J[a]; J[a] = J[b]; J[b] = t;
+        if (deg) { int8_t u = deg[a]; deg[a] = deg[b]; deg[b] = u; }
+        if (ph) { int8_t u = ph[a]; ph[a] = ph[b]; ph[b] = u; }
+    }
+    void sift(int64_t root, int64_t n) const
+    {
+        for (;;) {
+            int64_t c = 2 * root + 1;
+            if (c >= n) return;
+            if (c + 1 < n && less(c, c + 1)) c++;
+            if (!less(root, c)) return;
+            swap(root, c);
+            root = c;
+        }
+    }
+    void sort(int64_t n) const
+    {
+        for (int64_t i = n / 2 - 1; i >= 0; i--) sift(i, n);
+        for (int64_t e = n - 1; e > 0; e--) {
+            swap(0, e);
+            sift(0, e);
+        }
+    }
+};
+
+}  // namespace
+
+extern "C" int sci_connections_noalloc(sci_ctx *ctx, int64_t row_begin, int64_t row_end, int64_t *count,
+                                       int64_t *rows, int64_t *J, int8_t *degree, int8_t *phase, int64_t cap)
+{
+    if (!ctx || !count) return SCI_ERR_ARG;
+    if (!ctx->have_dets) return sci_fail(ctx, SCI_ERR_STATE, "no determinants");
+    if (row_begin < 0 || row_end > ctx->M || row_begin > row_end || cap < 0)
+        return sci_fail(ctx, SCI_ERR_ARG, "bad row range or capacity");
+    if (cap > 0 && (!rows || !J)) return sci_fail(ctx, SCI_ERR_ARG, "rows and J are required (sorted in place)");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return sci_cuda_check(ctx, e, "cudaSetDevice");
+    if (ctx->device < 0 || ctx->device >= kMaxDevices) return sci_fail(ctx, SCI_ERR_ARG, "device index too large");
+
+    // set-up, once per device, with the device current: the scratch array's address
+    void *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        if (!g_scratch_addr[ctx->device]) {
+            e = cudaGetSymbolAddress(&g_scratch_addr[ctx->device], g_noalloc_scratch);
+            if (e != cudaSuccess) {
+                g_scratch_addr[ctx->device] = nullptr;
+                return sci_cuda_check(ctx, e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+            }
+        }
+        base = g_scratch_addr[ctx->device];
+    }
+    Scratch s = carve(base);
+    cudaStream_t st = ctx->stream;
+    e = cudaMemsetAsync(s.counter, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return sci_cuda_check(ctx, e, "clear scratch counter");
+    if (ctx->e2 > 0)
+        k_conn2_noalloc<<<grid_for(ctx->e2), 256, 0, st>>>(ctx->e2_idx, ctx->e2_mask, ctx->e2_meta, ctx->e2,
+                                                           row_begin, row_end, s);
+    if (ctx->e1 > 0)
+        k_conn1_noalloc<<<grid_for(ctx->e1), 256, 0, st>>>(ctx->e1_idx, ctx->e1_meta, ctx->e1, row_begin, row_end, s);
+    unsigned long long n = 0;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&n, s.counter, sizeof(n), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return sci_cuda_check(ctx, e, "connection export");
+    *count = (int64_t)n;
+    if ((int64_t)n > kNoAllocMaxPairs)
+        return sci_fail(ctx, SCI_ERR_OVERFLOW,
+                        "more connections in the row range than the no-allocation scratch holds "
+                        "(SCI_NOALLOC_MAX_PAIRS); split the range");
+    if ((int64_t)n > cap) return sci_fail(ctx, SCI_ERR_OVERFLOW, "connection list exceeds cap");
+    if (n == 0) return SCI_OK;
+    // packed pairs into J, flag bytes into the front of rows, then unpack backwards so
+    // that no flag byte is overwritten before it is read
+    e = cudaMemcpyAsync(J, s.pairs, n * sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rows, s.flags, n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return sci_cuda_check(ctx, e, "copy connection list");
+    const uint8_t *fl = reinterpret_cast<const uint8_t *>(rows);
+    for (int64_t t = (int64_t)n - 1; t >= 0; t--) {
+        uint8_t f = fl[t];
+        uint64_t v = (uint64_t)J[t];
+        if (degree) degree[t] = (f & 1) ? 2 : 1;
+        if (phase) phase[t] = (f & 2) ? -1 : 1;
+        J[t] = (int64_t)(v & 0xFFFFFFFFull);
+        rows[t] = (int64_t)(v >> 32);
+    }
+    Out{rows, J, degree, phase}.sort((int64_t)n);
+    return SCI_OK;
+}

@@ -41,6 +41,7 @@ SIGNATURES = {
     "sci_diagonal": (_i32, [_vp, _vp]),
     "sci_sigma": (_i32, [_vp, _vp, _vp, _i32, _i32]),
     "sci_connections": (_i32, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _i64]),
+    "sci_connections_noalloc": (_i32, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _i64]),
     "sci_count_pairs": (_i32, [_vp, _vp]),
     "sci_sigma_host": (_i32, [_vp, _vp, _vp, _i32, _i32]),
     "sci_info": (_i32, [_vp, _vp, _i32]),
@@ -134,6 +135,22 @@ def sci_connections(ctx, row_begin, row_end, cap):
     deg = np.zeros(max(cap, 1), dtype=np.int8)
     ph = np.zeros(max(cap, 1), dtype=np.int8)
     rc = load().sci_connections(ctx, row_begin, row_end, _p(cnt), _p(rows), _p(J), _p(deg), _p(ph), cap)
+    if rc == SCI_ERR_OVERFLOW:
+        return int(cnt[0]), None
+    _check(ctx, rc)
+    n = int(cnt[0])
+    return n, (rows[:n], J[:n], deg[:n], ph[:n])
+
+
+def sci_connections_noalloc(ctx, row_begin, row_end, cap):
+    """The connection export for callers that cannot allocate device memory: the
+    library uses a fixed device scratch array instead (see include/sci.h)."""
+    cnt = np.zeros(1, dtype=np.int64)
+    rows = np.zeros(max(cap, 1), dtype=np.int64)
+    J = np.zeros(max(cap, 1), dtype=np.int64)
+    deg = np.zeros(max(cap, 1), dtype=np.int8)
+    ph = np.zeros(max(cap, 1), dtype=np.int8)
+    rc = load().sci_connections_noalloc(ctx, row_begin, row_end, _p(cnt), _p(rows), _p(J), _p(deg), _p(ph), cap)
     if rc == SCI_ERR_OVERFLOW:
         return int(cnt[0]), None
     _check(ctx, rc)
