@@ -170,6 +170,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--ref-rows", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--prec", default="f64", choices=["f64", "ds"],
+                    help="f64: FP64 FMA path; ds: paired-FP32 products/sums (FP64 tolerance)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -212,8 +214,11 @@ def main():
     S = torch.empty_like(C)
     flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=dev)  # 256 MB > L2
     nv = C.shape[1]
+    prec = sci.SCI_PREC_F64 if args.prec == "f64" else sci.SCI_PREC_F64_DS
+    other = sci.SCI_PREC_F64_DS if args.prec == "f64" else sci.SCI_PREC_F64
     for _ in range(args.warmup):
-        H.sigma(C, out=S)
+        H.sigma(C, out=S, prec=prec)
+        H.sigma(C, out=S, prec=other)
     H.sync_status()
     sci.sci_profile(H.ctx, True)
 
@@ -222,21 +227,34 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    step_ms, kern = [], []
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    for _ in range(args.steps):
-        flush.zero_()                      # evict L2 between timed steps
-        ev0.record(stream)
-        H.sigma(C, out=S)
-        ev1.record(stream)
-        ev1.synchronize()
-        step_ms.append(ev0.elapsed_time(ev1))
-        kern.append(sci.sci_kernel_times(H.ctx))
+
+    def timed(prec, steps):
+        ms_, kern_ = [], []
+        for _ in range(steps):
+            flush.zero_()                      # evict L2 between timed steps
+            ev0.record(stream)
+            H.sigma(C, out=S, prec=prec)
+            ev1.record(stream)
+            ev1.synchronize()
+            ms_.append(ev0.elapsed_time(ev1))
+            kern_.append(sci.sci_kernel_times(H.ctx))
+        return ms_, kern_
+
+    step_ms, kern = timed(prec, args.steps)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clocks = sampler.stop()
+    # the other precision mode on the same inputs (same protocol, fewer steps)
+    o_ms, o_kern = timed(other, max(3, min(args.steps, 5)))
+    variant = {"prec": "ds" if other == sci.SCI_PREC_F64_DS else "f64",
+               "ms_per_step": statistics.mean(o_ms),
+               "value": world * pairs / (statistics.mean(o_ms) / 1e3),
+               "kernel_ms": {"init": statistics.mean(k[0] for k in o_kern),
+                             "doubles": statistics.mean(k[1] for k in o_kern),
+                             "singles": statistics.mean(k[2] for k in o_kern)}}
     sci.sci_profile(H.ctx, False)
     H.sync_status()
 
@@ -251,13 +269,13 @@ def main():
     # end to end through the public API with host buffers (pinned), copies inside
     Ch = torch.from_numpy(np.ascontiguousarray(w.c)).pin_memory()
     Sh = torch.empty_like(Ch).pin_memory()
-    sci.sci_sigma_host(H.ctx, Ch, Sh, nv, sci.SCI_PREC_F64)
+    sci.sci_sigma_host(H.ctx, Ch, Sh, nv, prec)
     e2e_t = []
     for _ in range(max(3, min(args.steps, 10))):
         flush.zero_()
         torch.cuda.synchronize()
         t = time.perf_counter()
-        sci.sci_sigma_host(H.ctx, Ch, Sh, nv, sci.SCI_PREC_F64)
+        sci.sci_sigma_host(H.ctx, Ch, Sh, nv, prec)
         e2e_t.append(time.perf_counter() - t)
     e2e = world * pairs / statistics.mean(e2e_t)
     nbytes = Ch.numel() * Ch.element_size()
@@ -297,7 +315,8 @@ def main():
                        "parallelism": f"replicas{world}" if world > 1 else "single"},
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
             "gpu_launches": args.steps * (1 + 2 * ((nv + 7) // 8 if not w.ints.complex_ else (nv + 3) // 4)),
-            "roofline": roof, "cpu_baseline": cpu, "clocks": clocks}
+            "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "prec": args.prec,
+            "other_prec": variant}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -68,8 +68,15 @@ enum { SCI_REAL64 = 1, SCI_COMPLEX128 = 2 };                 /* Hamiltonian scal
 enum { SCI_SPIN_ORBITALS = 1, SCI_SPINORS = 2 };             /* orbital mode */
 enum {
     SCI_PREC_F64 = 1,                /* C double (complex: double pairs), S double */
-    SCI_PREC_F32_STORE_F64_ACC = 2   /* C float, integrals rounded to float, products and
+    SCI_PREC_F32_STORE_F64_ACC = 2,  /* C float, integrals rounded to float, products and
                                         accumulation in FP64, S double (real mode only) */
+    SCI_PREC_F64_DS = 3              /* C and S as for SCI_PREC_F64; the double-excitation
+                                        products and per-bucket sums run in paired FP32
+                                        ("double-single") arithmetic on the FP32 pipes:
+                                        each FP64 operand is split into hi + lo floats,
+                                        products keep ~47 bits, sums are compensated, and
+                                        the bucket sums are added to S in FP64.  Agrees with
+                                        SCI_PREC_F64 to ~1e-13 relative. */
 };
 
 /* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t (may be

@@ -67,6 +67,8 @@ struct sci_ctx {
     void *g_so = nullptr;   // [norb][norb][norb]
     void *tab = nullptr;    // pair table (scalar)
     float *tab32 = nullptr; // FP32 copy of tab (real mode)
+    void *tab_ds = nullptr; // tab split into (hi, lo) floats: float2 (real) / float4 (complex)
+    void *c_ds = nullptr;   // per-call split of one vector group of C: [M][<=8] float2 or [M][<=4] float4
     int64_t tab_elems = 0;
 
     // determinants

@@ -184,6 +184,16 @@ __global__ void k_tab_spinor(const zdbl *__restrict__ eri, int n, zdbl *__restri
     }
 }
 
+// split doubles into (hi, lo) float pairs: hi = fl32(x), lo = fl32(x - hi)
+__global__ void k_split_ds(const double *__restrict__ in, float2 *__restrict__ out, int64_t n)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        double x = in[t];
+        float hi = (float)x;
+        out[t] = make_float2(hi, (float)(x - (double)hi));
+    }
+}
+
 __global__ void k_to_f32(const double *__restrict__ in, float *__restrict__ out, int64_t n)
 {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
@@ -534,6 +544,7 @@ void free_dets(sci_ctx *ctx)
     free_held(ctx, ctx->keys);
     free_held(ctx, ctx->hdiag);
     free_held(ctx, ctx->fref);
+    free_held(ctx, ctx->c_ds);
     free_held(ctx, ctx->e2_idx);
     free_held(ctx, ctx->e2_mask);
     free_held(ctx, ctx->e2_col);
@@ -556,6 +567,7 @@ void free_ints(sci_ctx *ctx)
     free_held(ctx, ctx->g_so);
     free_held(ctx, ctx->tab);
     free_held(ctx, ctx->tab32);
+    free_held(ctx, ctx->tab_ds);
     ctx->have_ints = 0;
 }
 
@@ -757,6 +769,12 @@ extern "C" int sci_set_integrals(sci_ctx *ctx, int scalar, int mode, int n, cons
         SCI_CK(alloc_held(ctx, (void **)&ctx->tab32, (size_t)ctx->tab_elems * 4));
         k_to_f32<<<grid_for(ctx->tab_elems), 256, 0, st>>>((const double *)ctx->tab, ctx->tab32, ctx->tab_elems);
     }
+    // paired-FP32 copy of the pair table (complex: re and im parts each split)
+    {
+        int64_t nd = ctx->tab_elems * (cplx ? 2 : 1);
+        SCI_CK(alloc_held(ctx, &ctx->tab_ds, (size_t)nd * 8));
+        if (nd > 0) k_split_ds<<<grid_for(nd), 256, 0, st>>>((const double *)ctx->tab, (float2 *)ctx->tab_ds, nd);
+    }
     SCI_CK(cudaGetLastError());
     ctx->have_ints = 1;
     if (ctx->have_dets) {
@@ -797,6 +815,7 @@ extern "C" int sci_set_determinants(sci_ctx *ctx, const uint64_t *keys, int64_t 
 
     SCI_CK(alloc_held(ctx, (void **)&ctx->keys, (size_t)M * 8));
     SCI_CK(alloc_held(ctx, (void **)&ctx->hdiag, (size_t)M * 8));
+    SCI_CK(alloc_held(ctx, &ctx->c_ds, (size_t)M * 64));  // paired-FP32 coefficients, 64 B per determinant
     if (M > 0)
         SCI_CK(cudaMemcpyAsync(ctx->keys, keys, (size_t)M * 8,
                                keys_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
@@ -892,7 +911,8 @@ extern "C" int sci_sigma(sci_ctx *ctx, const void *C, void *S, int nvec, int pre
     if (!ctx) return SCI_ERR_ARG;
     if (!ctx->have_dets || !ctx->have_ints) return sci_fail(ctx, SCI_ERR_STATE, "integrals and determinants needed");
     if (nvec < 1) return sci_fail(ctx, SCI_ERR_ARG, "nvec < 1");
-    if (prec != SCI_PREC_F64 && prec != SCI_PREC_F32_STORE_F64_ACC) return sci_fail(ctx, SCI_ERR_ARG, "bad prec");
+    if (prec != SCI_PREC_F64 && prec != SCI_PREC_F32_STORE_F64_ACC && prec != SCI_PREC_F64_DS)
+        return sci_fail(ctx, SCI_ERR_ARG, "bad prec");
     if (prec == SCI_PREC_F32_STORE_F64_ACC && ctx->cplx)
         return sci_fail(ctx, SCI_ERR_ARG, "FP32 storage is available for real Hamiltonians only");
     if (ctx->M == 0) return SCI_OK;
@@ -908,7 +928,8 @@ extern "C" int sci_sigma_host(sci_ctx *ctx, const void *C_host, void *S_host, in
     if (nvec < 1) return sci_fail(ctx, SCI_ERR_ARG, "nvec < 1");
     if (ctx->M == 0) return SCI_OK;
     if (!C_host || !S_host) return sci_fail(ctx, SCI_ERR_ARG, "C or S is NULL");
-    if (prec != SCI_PREC_F64 && prec != SCI_PREC_F32_STORE_F64_ACC) return sci_fail(ctx, SCI_ERR_ARG, "bad prec");
+    if (prec != SCI_PREC_F64 && prec != SCI_PREC_F32_STORE_F64_ACC && prec != SCI_PREC_F64_DS)
+        return sci_fail(ctx, SCI_ERR_ARG, "bad prec");
     SCI_CK(cudaSetDevice(ctx->device));
     size_t sb = ctx->cplx ? 16 : 8;
     size_t cb = (size_t)ctx->M * nvec * (prec == SCI_PREC_F32_STORE_F64_ACC ? 4 : sb);

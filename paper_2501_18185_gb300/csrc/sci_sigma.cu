@@ -36,11 +36,17 @@ using sci::zdbl;
 namespace {
 
 // ------------------------------------------------------------------ scalar ops
-__device__ __forceinline__ double neg(double a) { return -a; }
-__device__ __forceinline__ float neg(float a) { return -a; }
-__device__ __forceinline__ zdbl neg(zdbl a) { return zdbl{-a.x, -a.y}; }
+// Sign flips are integer XORs of the sign bit: on GB300 the FP64 pipe is the scarce
+// resource (1.2 TFLOP/s), so no FP64 instruction is spent on a negation.
+__device__ __forceinline__ double flip(bool f, double a)
+{
+    return __longlong_as_double(__double_as_longlong(a) ^ ((unsigned long long)f << 63));
+}
+__device__ __forceinline__ float flip(bool f, float a) { return __int_as_float(__float_as_int(a) ^ ((int)f << 31)); }
+__device__ __forceinline__ zdbl flip(bool f, zdbl a) { return zdbl{flip(f, a.x), flip(f, a.y)}; }
 
 __device__ __forceinline__ void zero(double &a) { a = 0.0; }
+__device__ __forceinline__ void zero(float &a) { a = 0.0f; }
 __device__ __forceinline__ void zero(zdbl &a) { a = zdbl{0.0, 0.0}; }
 
 // acc += t * c
@@ -62,14 +68,31 @@ __device__ __forceinline__ void red_add(zdbl *p, zdbl v)
     atomicAdd(&p->y, v.y);
 }
 
-__device__ __forceinline__ double sgn(bool neg_, double a) { return neg_ ? -a : a; }
-__device__ __forceinline__ zdbl sgn(bool neg_, zdbl a) { return neg_ ? zdbl{-a.x, -a.y} : a; }
-
 template <typename T> __device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
 template <> __device__ __forceinline__ zdbl ldg<zdbl>(const zdbl *p)
 {
     double2 v = __ldg(reinterpret_cast<const double2 *>(p));
     return zdbl{v.x, v.y};
+}
+
+// Disjointness test of two members of one bucket.  A member with extra orbitals x < y
+// is coded as bytes (x, y, x, y) when it is the bra (row) and (x', y', y', x') when it is
+// the ket (column); the XOR of the two codes has a zero byte exactly when they share an
+// orbital (x = x', y = y', x = y' or y = x').
+__device__ __forceinline__ uint32_t row_code(uint64_t mask)
+{
+    uint32_t x = (uint32_t)(__ffsll((long long)mask) - 1), y = 63u - (uint32_t)__clzll((long long)mask);
+    return x | (y << 8) | (x << 16) | (y << 24);
+}
+__device__ __forceinline__ uint32_t col_code(uint64_t mask)
+{
+    uint32_t x = (uint32_t)(__ffsll((long long)mask) - 1), y = 63u - (uint32_t)__clzll((long long)mask);
+    return x | (y << 8) | (y << 16) | (x << 24);
+}
+__device__ __forceinline__ bool disjoint(uint32_t rc, uint32_t cc)
+{
+    uint32_t v = rc ^ cc;
+    return ((v - 0x01010101u) & ~v & 0x80808080u) == 0u;
 }
 
 // acc type for a storage type
@@ -100,6 +123,10 @@ __global__ void k_sigma_init(const double *__restrict__ hdiag, const TC *__restr
 
 // ------------------------------------------------------------------ doubles
 // TS: storage type of tab and staged coefficients; TA: accumulator (FP64 / complex128).
+// Shared memory per staged member: (ket code, ket table offset) as uint2, and its NV
+// coefficients times (-1)^pi.
+constexpr int kUnroll = 4;
+
 template <typename TS, typename TC, int NV>
 __global__ void __launch_bounds__(kThreads)
 k_doubles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_mask, const uint32_t *__restrict__ e_col,
@@ -117,19 +144,256 @@ k_doubles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_mas
     const int W = (int)(w1 - w0);
     TS *s_c = reinterpret_cast<TS *>(smem);
     size_t cbytes = ((size_t)W * NV * sizeof(TS) + 15) & ~(size_t)15;
-    uint64_t *s_mask = reinterpret_cast<uint64_t *>(smem + cbytes);
-    uint32_t *s_col = reinterpret_cast<uint32_t *>(s_mask + W);
+    uint2 *s_kc = reinterpret_cast<uint2 *>(smem + cbytes);
 
     for (int q = threadIdx.x; q < W; q += blockDim.x) {
         const int64_t g = w0 + q;
         const uint32_t idx = e_idx[g];
         const bool par = (e_meta[g] >> 16) & 1;
-        s_mask[q] = e_mask[g];
-        s_col[q] = e_col[g];
+        s_kc[q] = make_uint2(col_code(e_mask[g]), e_col[g]);
+#pragma unroll
+        for (int v = 0; v < NV; v++) s_c[q * NV + v] = flip(par, (TS)C[(int64_t)idx * nvec + v0 + v]);
+    }
+    __syncthreads();
+
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        const int q0 = (int)(r - w0);
+        const uint64_t meta = e_meta[r];
+        const uint32_t rowoff = (uint32_t)(meta & 0xFFFF);
+        const bool par = (meta >> 16) & 1;
+        const int bs = q0 - (int)((meta >> 32) & 0xFFFF);
+        const int be = bs + (int)(meta >> 48);
+        const uint32_t rc = row_code(e_mask[r]);
+        const TS *trow = tab + rowoff;
+        TA acc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) zero(acc[v]);
+        int j = bs;
+        // groups of kUnroll members: a group with no double of this row (members equal
+        // to the row or single excitations of it) is skipped, and so is the whole warp's
+        // work when no lane has one; otherwise up to kUnroll table loads are in flight per
+        // thread and a non-double member contributes t = 0
+        for (; j + kUnroll <= be; j += kUnroll) {
+            uint2 kc[kUnroll];
+            TS t[kUnroll];
+            unsigned vm = 0;
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                kc[u] = s_kc[j + u];
+                vm |= (unsigned)disjoint(rc, kc[u].x) << u;
+            }
+            if (vm == 0) continue;
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                zero(t[u]);
+                if (vm & (1u << u)) t[u] = ldg(trow + kc[u].y);
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++)
+#pragma unroll
+                for (int v = 0; v < NV; v++) fma_acc(acc[v], t[u], s_c[(j + u) * NV + v]);
+        }
+        for (; j < be; j++) {
+            const uint2 kc = s_kc[j];
+            if (!disjoint(rc, kc.x)) continue;
+            const TS t = ldg(trow + kc.y);
+#pragma unroll
+            for (int v = 0; v < NV; v++) fma_acc(acc[v], t, s_c[j * NV + v]);
+        }
+        const uint32_t idx = e_idx[r];
+#pragma unroll
+        for (int v = 0; v < NV; v++) red_add(Sout + (int64_t)idx * nvec + v0 + v, flip(par, acc[v]));
+    }
+}
+
+// ------------------------------------------------------------------ doubles, paired FP32
+// The same bucket walk with the products and per-row sums in "double-single" arithmetic
+// on the FP32 pipes: an FP64 value x is carried as hi + lo with hi = fl32(x) and
+// lo = fl32(x - hi).  For t = th + tl and c = ch + cl the product is
+//     p = fl(th*ch),  e = (th*ch - p) + th*cl + tl*ch      (exact first term via FMA;
+// the dropped tl*cl is ~2^-48 of |tc|), and the sum (hi, lo) takes p by TwoSum
+// (Knuth) with e and the rounding error folded into lo.  lo is renormalised into hi every
+// kUnroll pairs.  The row sum leaves the kernel as fp64(hi) + fp64(lo) through the same
+// FP64 atomic add as the FP64 path.
+struct Ds {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void ds_zero(Ds &a) { a.hi = 0.f, a.lo = 0.f; }
+
+// a += t * c
+__device__ __forceinline__ void ds_fma(Ds &a, float2 t, float2 c)
+{
+    const float p = t.x * c.x;
+    float e = fmaf(t.x, c.x, -p);
+    e = fmaf(t.x, c.y, e);
+    e = fmaf(t.y, c.x, e);
+    const float s = a.hi + p;
+    const float bv = s - a.hi;
+    const float err = (a.hi - (s - bv)) + (p - bv);
+    a.lo += err + e;
+    a.hi = s;
+}
+
+__device__ __forceinline__ void ds_renorm(Ds &a)
+{
+    const float s = a.hi + a.lo;
+    a.lo = a.lo - (s - a.hi);
+    a.hi = s;
+}
+
+// float -> double by bit assembly on the integer pipes (the F2F conversion instructions
+// share the narrow FP64 pipe).  Normal numbers, zero, inf and NaN convert exactly; a
+// float denormal (|x| < 1.2e-38) becomes a signed zero.
+__device__ __forceinline__ double f2d_int(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xFFu;
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    unsigned long long bits = sign;
+    if (e == 0xFFu) bits |= (0x7FFull << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    else if (e != 0u) bits |= ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
+__device__ __forceinline__ double ds_value(Ds a) { return f2d_int(a.hi) + f2d_int(a.lo); }
+
+__device__ __forceinline__ float2 flip(bool f, float2 a) { return make_float2(flip(f, a.x), flip(f, a.y)); }
+__device__ __forceinline__ float4 flip(bool f, float4 a)
+{
+    return make_float4(flip(f, a.x), flip(f, a.y), flip(f, a.z), flip(f, a.w));
+}
+
+__device__ __forceinline__ float2 ds_split(double x)
+{
+    const float hi = (float)x;
+    return make_float2(hi, (float)(x - (double)hi));
+}
+
+// split the vector group C[:, v0:v0+G] into paired floats, once per sigma call (so the
+// staging in the bucket kernel, which touches each coefficient many times, only copies)
+__global__ void k_split_c(const double *__restrict__ C, int64_t M, int nvec, int v0, int G, float2 *__restrict__ out)
+{
+    const int64_t total = M * G;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
+        out[t] = ds_split(C[(t / G) * nvec + v0 + t % G]);
+}
+
+__global__ void k_split_cz(const zdbl *__restrict__ C, int64_t M, int nvec, int v0, int G, float4 *__restrict__ out)
+{
+    const int64_t total = M * G;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const zdbl c = C[(t / G) * nvec + v0 + t % G];
+        const float2 re = ds_split(c.x), im = ds_split(c.y);
+        out[t] = make_float4(re.x, re.y, im.x, im.y);
+    }
+}
+
+// real: tab2 is the (hi, lo) split of the pair table
+template <int NV>
+__global__ void __launch_bounds__(kThreads)
+k_doubles_ds(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_mask,
+             const uint32_t *__restrict__ e_col, const uint64_t *__restrict__ e_meta, int64_t E, int CH,
+             const float2 *__restrict__ tab2, const float2 *__restrict__ C2, int nvec, int v0,
+             double *__restrict__ Sout)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int64_t r0 = (int64_t)blockIdx.x * CH;
+    if (r0 >= E) return;
+    const int64_t r1 = min(r0 + (int64_t)CH, E);
+    const uint64_t mf = e_meta[r0], ml = e_meta[r1 - 1];
+    const int64_t w0 = r0 - (int64_t)((mf >> 32) & 0xFFFF);
+    const int64_t w1 = (r1 - 1) - (int64_t)((ml >> 32) & 0xFFFF) + (int64_t)(ml >> 48);
+    const int W = (int)(w1 - w0);
+    float2 *s_c = reinterpret_cast<float2 *>(smem);
+    size_t cbytes = ((size_t)W * NV * sizeof(float2) + 15) & ~(size_t)15;
+    uint2 *s_kc = reinterpret_cast<uint2 *>(smem + cbytes);
+
+    for (int q = threadIdx.x; q < W; q += blockDim.x) {
+        const int64_t g = w0 + q;
+        const uint32_t idx = e_idx[g];
+        const bool par = (e_meta[g] >> 16) & 1;
+        s_kc[q] = make_uint2(col_code(e_mask[g]), e_col[g]);
+#pragma unroll
+        for (int v = 0; v < NV; v++) s_c[q * NV + v] = flip(par, C2[(int64_t)idx * NV + v]);
+    }
+    __syncthreads();
+
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        const int q0 = (int)(r - w0);
+        const uint64_t meta = e_meta[r];
+        const uint32_t rowoff = (uint32_t)(meta & 0xFFFF);
+        const bool par = (meta >> 16) & 1;
+        const int bs = q0 - (int)((meta >> 32) & 0xFFFF);
+        const int be = bs + (int)(meta >> 48);
+        const uint32_t rc = row_code(e_mask[r]);
+        const float2 *trow = tab2 + rowoff;
+        Ds acc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) ds_zero(acc[v]);
+        int j = bs;
+        for (; j + kUnroll <= be; j += kUnroll) {
+            uint2 kc[kUnroll];
+            float2 t[kUnroll];
+            unsigned vm = 0;
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                kc[u] = s_kc[j + u];
+                vm |= (unsigned)disjoint(rc, kc[u].x) << u;
+            }
+            if (vm == 0) continue;
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                t[u] = make_float2(0.f, 0.f);
+                if (vm & (1u << u)) t[u] = __ldg(trow + kc[u].y);
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++)
+#pragma unroll
+                for (int v = 0; v < NV; v++) ds_fma(acc[v], t[u], s_c[(j + u) * NV + v]);
+#pragma unroll
+            for (int v = 0; v < NV; v++) ds_renorm(acc[v]);
+        }
+        for (; j < be; j++) {
+            const uint2 kc = s_kc[j];
+            if (!disjoint(rc, kc.x)) continue;
+            const float2 t = __ldg(trow + kc.y);
+#pragma unroll
+            for (int v = 0; v < NV; v++) ds_fma(acc[v], t, s_c[j * NV + v]);
+        }
+        const uint32_t idx = e_idx[r];
+#pragma unroll
+        for (int v = 0; v < NV; v++) red_add(Sout + (int64_t)idx * nvec + v0 + v, flip(par, ds_value(acc[v])));
+    }
+}
+
+// complex: tab4 holds (re_hi, re_lo, im_hi, im_lo); staged c as (re, im) float2 pairs
+template <int NV>
+__global__ void __launch_bounds__(kThreads)
+k_doubles_dsz(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_mask,
+              const uint32_t *__restrict__ e_col, const uint64_t *__restrict__ e_meta, int64_t E, int CH,
+              const float4 *__restrict__ tab4, const float4 *__restrict__ C4, int nvec, int v0, zdbl *__restrict__ Sout)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int64_t r0 = (int64_t)blockIdx.x * CH;
+    if (r0 >= E) return;
+    const int64_t r1 = min(r0 + (int64_t)CH, E);
+    const uint64_t mf = e_meta[r0], ml = e_meta[r1 - 1];
+    const int64_t w0 = r0 - (int64_t)((mf >> 32) & 0xFFFF);
+    const int64_t w1 = (r1 - 1) - (int64_t)((ml >> 32) & 0xFFFF) + (int64_t)(ml >> 48);
+    const int W = (int)(w1 - w0);
+    float4 *s_c = reinterpret_cast<float4 *>(smem);   // (re_hi, re_lo, im_hi, im_lo)
+    size_t cbytes = ((size_t)W * NV * sizeof(float4) + 15) & ~(size_t)15;
+    uint2 *s_kc = reinterpret_cast<uint2 *>(smem + cbytes);
+
+    for (int q = threadIdx.x; q < W; q += blockDim.x) {
+        const int64_t g = w0 + q;
+        const uint32_t idx = e_idx[g];
+        const bool par = (e_meta[g] >> 16) & 1;
+        s_kc[q] = make_uint2(col_code(e_mask[g]), e_col[g]);
 #pragma unroll
         for (int v = 0; v < NV; v++) {
-            TS c = (TS)C[(int64_t)idx * nvec + v0 + v];
-            s_c[q * NV + v] = par ? neg(c) : c;
+            s_c[q * NV + v] = flip(par, C4[(int64_t)idx * NV + v]);
         }
     }
     __syncthreads();
@@ -141,19 +405,35 @@ k_doubles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_mas
         const bool par = (meta >> 16) & 1;
         const int bs = q0 - (int)((meta >> 32) & 0xFFFF);
         const int be = bs + (int)(meta >> 48);
-        const uint64_t rmask = s_mask[q0];
-        TA acc[NV];
+        const uint32_t rc = row_code(e_mask[r]);
+        const float4 *trow = tab4 + rowoff;
+        Ds ar[NV], ai[NV];
 #pragma unroll
-        for (int v = 0; v < NV; v++) zero(acc[v]);
-        for (int j = bs; j < be; j++) {
-            if (s_mask[j] & rmask) continue;  // same member, or a single: not a double
-            const TS t = ldg(tab + s_col[j] + rowoff);
+        for (int v = 0; v < NV; v++) ds_zero(ar[v]), ds_zero(ai[v]);
+        int j = bs;
+        for (; j < be; j++) {
+            const uint2 kc = s_kc[j];
+            float4 t = __ldg(trow + kc.y);
+            if (!disjoint(rc, kc.x)) t = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float2 tr = make_float2(t.x, t.y), ti = make_float2(t.z, t.w);
+            const float2 mti = make_float2(-t.z, -t.w);
 #pragma unroll
-            for (int v = 0; v < NV; v++) fma_acc(acc[v], t, s_c[j * NV + v]);
+            for (int v = 0; v < NV; v++) {
+                const float4 c = s_c[j * NV + v];
+                const float2 cr = make_float2(c.x, c.y), ci = make_float2(c.z, c.w);
+                ds_fma(ar[v], tr, cr);
+                ds_fma(ar[v], mti, ci);
+                ds_fma(ai[v], tr, ci);
+                ds_fma(ai[v], ti, cr);
+            }
+            if (((j - bs) & 3) == 3)
+#pragma unroll
+                for (int v = 0; v < NV; v++) ds_renorm(ar[v]), ds_renorm(ai[v]);
         }
         const uint32_t idx = e_idx[r];
 #pragma unroll
-        for (int v = 0; v < NV; v++) red_add(Sout + (int64_t)idx * nvec + v0 + v, sgn(par, acc[v]));
+        for (int v = 0; v < NV; v++)
+            red_add(Sout + (int64_t)idx * nvec + v0 + v, flip(par, zdbl{ds_value(ar[v]), ds_value(ai[v])}));
     }
 }
 
@@ -195,14 +475,12 @@ k_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S, 
             }
 #pragma unroll
             for (int v = 0; v < NV; v++) {
-                TC c = C[(int64_t)idxq * nvec + v0 + v];
-                if (parq) c = neg(c);
-                fma_acc(acc[v], f, c);
+                fma_acc(acc[v], f, flip(parq, C[(int64_t)idxq * nvec + v0 + v]));
             }
         }
         const uint32_t idx = e_idx[p];
 #pragma unroll
-        for (int v = 0; v < NV; v++) red_add(Sout + (int64_t)idx * nvec + v0 + v, sgn(par, acc[v]));
+        for (int v = 0; v < NV; v++) red_add(Sout + (int64_t)idx * nvec + v0 + v, flip(par, acc[v]));
     }
 }
 
@@ -214,14 +492,17 @@ int grid_for(int64_t n, int threads = kThreads)
     return (int)g;
 }
 
-// rows per CTA so that the staged window fits the shared-memory budget
+// rows per CTA so that the staged window fits the shared-memory budget; small windows
+// first (more resident CTAs per SM), larger ones only when the buckets need them
 int choose_rows(int maxb, size_t bytes_per_entry, size_t &smem)
 {
-    const size_t budgets[2] = {100 * 1024, 200 * 1024};
+    const size_t budgets[3] = {48 * 1024, 100 * 1024, 200 * 1024};
     for (size_t budget : budgets) {
         int64_t ch = (int64_t)(budget / bytes_per_entry) - 2 * (int64_t)(maxb - 1) - 8;
-        if (ch >= 512 || (budget == budgets[1] && ch >= 64)) {
-            ch = std::min<int64_t>(ch, 2048);
+        if (ch >= 512 || (budget == budgets[2] && ch >= 64)) {
+            // measured on the 2M/1M workloads: 2048-row windows for 16-byte staged
+            // entries, 1024 for wider ones
+            ch = std::min<int64_t>(ch, bytes_per_entry <= 16 ? 2048 : 1024);
             ch = std::max<int64_t>(64, ch & ~(int64_t)63);
             smem = (size_t)(ch + 2 * (maxb - 1)) * bytes_per_entry + 64;
             return (int)ch;
@@ -234,7 +515,7 @@ template <typename TS, typename TC, int NV>
 int launch_doubles(sci_ctx *ctx, const TS *tab, const TC *C, typename AccOf<TS>::type *S, int nvec, int v0)
 {
     if (ctx->e2 == 0) return SCI_OK;
-    size_t per = NV * sizeof(TS) + 8 + 4;
+    size_t per = NV * sizeof(TS) + 8;
     size_t smem = 0;
     int ch = choose_rows(ctx->maxb2, per, smem);
     if (ch < 0) return sci_fail(ctx, SCI_ERR_OVERFLOW, "bucket too large for shared memory");
@@ -245,6 +526,65 @@ int launch_doubles(sci_ctx *ctx, const TS *tab, const TC *C, typename AccOf<TS>:
     kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(ctx->e2_idx, ctx->e2_mask, ctx->e2_col, ctx->e2_meta,
                                                           ctx->e2, ch, tab, C, nvec, v0, S);
     return sci_cuda_check(ctx, cudaGetLastError(), "k_doubles launch");
+}
+
+// paired-FP32 doubles: real (float2 table, float2 staged c) or complex (float4 / float4)
+template <bool CPLX, int NV>
+int launch_doubles_ds(sci_ctx *ctx, const void *C, void *S, int nvec, int v0)
+{
+    if (ctx->e2 == 0) return SCI_OK;
+    size_t per = NV * (CPLX ? sizeof(float4) : sizeof(float2)) + 8;
+    size_t smem = 0;
+    int ch = choose_rows(ctx->maxb2, per, smem);
+    if (ch < 0) return sci_fail(ctx, SCI_ERR_OVERFLOW, "bucket too large for shared memory");
+    int64_t blocks = (ctx->e2 + ch - 1) / ch;
+    cudaError_t e;
+    // the vector group, split into paired floats in the context's c_ds buffer
+    // (64 bytes per determinant: up to 8 real or 4 complex coefficients)
+    if constexpr (CPLX)
+        k_split_cz<<<grid_for(ctx->M * NV), kThreads, 0, ctx->stream>>>((const zdbl *)C, ctx->M, nvec, v0, NV,
+                                                                        (float4 *)ctx->c_ds);
+    else
+        k_split_c<<<grid_for(ctx->M * NV), kThreads, 0, ctx->stream>>>((const double *)C, ctx->M, nvec, v0, NV,
+                                                                       (float2 *)ctx->c_ds);
+    if constexpr (CPLX) {
+        auto kern = k_doubles_dsz<NV>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return sci_cuda_check(ctx, e, "cudaFuncSetAttribute");
+        kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(ctx->e2_idx, ctx->e2_mask, ctx->e2_col, ctx->e2_meta,
+                                                              ctx->e2, ch, (const float4 *)ctx->tab_ds,
+                                                              (const float4 *)ctx->c_ds, nvec, v0, (zdbl *)S);
+    } else {
+        auto kern = k_doubles_ds<NV>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return sci_cuda_check(ctx, e, "cudaFuncSetAttribute");
+        kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(ctx->e2_idx, ctx->e2_mask, ctx->e2_col, ctx->e2_meta,
+                                                              ctx->e2, ch, (const float2 *)ctx->tab_ds,
+                                                              (const float2 *)ctx->c_ds, nvec, v0, (double *)S);
+    }
+    return sci_cuda_check(ctx, cudaGetLastError(), "k_doubles_ds launch");
+}
+
+template <bool CPLX>
+int ds_groups(sci_ctx *ctx, const void *C, void *S, int nvec)
+{
+    int rc = SCI_OK;
+    const size_t unit = CPLX ? sizeof(float4) : sizeof(float2);
+    for (int v0 = 0; v0 < nvec && rc == SCI_OK;) {
+        int left = nvec - v0;
+        int g = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+        if (CPLX && g > 4) g = 4;
+        size_t smem_probe = 0;
+        while (g > 1 && choose_rows(ctx->maxb2, g * unit + 8, smem_probe) < 0) g >>= 1;
+        switch (g) {
+        case 8: rc = launch_doubles_ds<CPLX, 8>(ctx, C, S, nvec, v0); break;
+        case 4: rc = launch_doubles_ds<CPLX, 4>(ctx, C, S, nvec, v0); break;
+        case 2: rc = launch_doubles_ds<CPLX, 2>(ctx, C, S, nvec, v0); break;
+        default: rc = launch_doubles_ds<CPLX, 1>(ctx, C, S, nvec, v0); break;
+        }
+        v0 += g;
+    }
+    return rc;
 }
 
 template <typename TS, typename TC, int NV>
@@ -266,7 +606,7 @@ int sigma_groups(sci_ctx *ctx, const TS *tab, const TC *C, typename AccOf<TS>::t
         int g = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
         if (sizeof(TS) == 16 && g > 4) g = 4;
         size_t smem_probe = 0;  // shrink the vector group until its window fits
-        while (g > 1 && choose_rows(ctx->maxb2, g * sizeof(TS) + 12, smem_probe) < 0) g >>= 1;
+        while (g > 1 && choose_rows(ctx->maxb2, g * sizeof(TS) + 8, smem_probe) < 0) g >>= 1;
         switch (g) {
         case 8: rc = launch_doubles<TS, TC, 8>(ctx, tab, C, S, nvec, v0); break;
         case 4: rc = launch_doubles<TS, TC, 4>(ctx, tab, C, S, nvec, v0); break;
@@ -400,19 +740,21 @@ int sci_launch_sigma(sci_ctx *ctx, const void *C, void *S, int nvec, int prec)
         k_sigma_init<zdbl, zdbl><<<grid_for(M * nvec), kThreads, 0, st>>>(ctx->hdiag, Cz, Sz, M, nvec);
         SCI_CK(cudaGetLastError());
         mark(ctx, 1);
-        rc = sigma_groups<zdbl, zdbl>(ctx, (const zdbl *)ctx->tab, Cz, Sz, nvec);
+        rc = prec == SCI_PREC_F64_DS ? ds_groups<true>(ctx, C, S, nvec)
+                                     : sigma_groups<zdbl, zdbl>(ctx, (const zdbl *)ctx->tab, Cz, Sz, nvec);
         mark(ctx, 2);
         if (rc == SCI_OK) rc = singles_groups<zdbl, zdbl>(ctx, Cz, Sz, nvec);
         mark(ctx, 3);
         return rc;
     }
     double *Sd = (double *)S;
-    if (prec == SCI_PREC_F64) {
+    if (prec == SCI_PREC_F64 || prec == SCI_PREC_F64_DS) {
         const double *Cd = (const double *)C;
         k_sigma_init<double, double><<<grid_for(M * nvec), kThreads, 0, st>>>(ctx->hdiag, Cd, Sd, M, nvec);
         SCI_CK(cudaGetLastError());
         mark(ctx, 1);
-        rc = sigma_groups<double, double>(ctx, (const double *)ctx->tab, Cd, Sd, nvec);
+        rc = prec == SCI_PREC_F64_DS ? ds_groups<false>(ctx, C, S, nvec)
+                                     : sigma_groups<double, double>(ctx, (const double *)ctx->tab, Cd, Sd, nvec);
         mark(ctx, 2);
         if (rc == SCI_OK) rc = singles_groups<double, double>(ctx, Cd, Sd, nvec);
         mark(ctx, 3);

@@ -28,7 +28,7 @@ SCI_ERR_OVERFLOW = -8
 SCI_ERR_TIMEOUT = -9
 SCI_REAL64, SCI_COMPLEX128 = 1, 2
 SCI_SPIN_ORBITALS, SCI_SPINORS = 1, 2
-SCI_PREC_F64, SCI_PREC_F32_STORE_F64_ACC = 1, 2
+SCI_PREC_F64, SCI_PREC_F32_STORE_F64_ACC, SCI_PREC_F64_DS = 1, 2, 3
 
 # every entry point declared in include/sci.h, with (restype, argtypes)
 _vp, _i32, _i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
@@ -277,10 +277,12 @@ class Hamiltonian:
         """S = H C for C of shape [M] or [M, nvec] (torch CUDA, contiguous)."""
         torch = self.torch
         squeeze = C.dim() == 1
-        nvec = 1 if squeeze else C.shape[1]
-        C2 = C.reshape(self.M, nvec).contiguous()
+        C2 = (C.reshape(-1, 1) if squeeze else C).contiguous()
+        nvec = C2.shape[1]
+        if self.M and C2.shape[0] != self.M:
+            raise ValueError(f"C has {C2.shape[0]} rows, the determinant list {self.M}")
         odt = torch.complex128 if self.complex else torch.float64
-        S = out if out is not None else torch.empty((self.M, nvec), dtype=odt, device=self.device)
+        S = out if out is not None else torch.empty((C2.shape[0], nvec), dtype=odt, device=self.device)
         sci_sigma(self.ctx, C2, S, nvec, prec)
         return S.reshape(-1) if squeeze and out is None else S
 

@@ -114,6 +114,24 @@ def test_sigma_fp64(gpu, name, nvec):
     assert rel_err(S[rows], ref) < TOL
 
 
+@pytest.mark.parametrize("name", ["fci_8o_4a4b", "so_sel_7o", "spinor_sel_16_5", "spinor_64_2", "sel_30o_60k",
+                                  "sel_64s_120k"])
+@pytest.mark.parametrize("nvec", [1, 3])
+def test_sigma_paired_fp32_matches_fp64_tolerance(gpu, name, nvec):
+    """SCI_PREC_F64_DS (double-excitation products and bucket sums in paired FP32) is
+    held to the same 1e-11 bar against the FP64 oracle as the FP64 path."""
+    torch = gpu
+    w, o = case(name)
+    H = gpu_ham(w, torch)
+    rng = np.random.default_rng(200 + nvec)
+    C = w.c if nvec == 1 else rng.normal(size=(w.M, nvec)) + (1j * rng.normal(size=(w.M, nvec)) if w.mode == "spinors" else 0)
+    C = np.ascontiguousarray(C)
+    S = H.sigma(torch.from_numpy(C).cuda().reshape(w.M, -1), prec=sci.SCI_PREC_F64_DS).cpu().numpy().reshape(w.M, -1)
+    H.sync_status()
+    rows = sample_rows(w, 3000)
+    assert rel_err(S[rows], o.sigma_rows(rows, C)) < TOL
+
+
 def test_sigma_nvec8_and_repeat(gpu):
     torch = gpu
     w, o = case("sel_30o_60k")
