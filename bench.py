@@ -128,6 +128,64 @@ def cpu_baseline(w, budget_s: float = 12.0, seed: int = 0):
             "sample": f"{n} random rows of {w.M} ({pairs} pairs, {dt:.1f} s, OpenMP {cores} threads)"}
 
 
+def davidson_bench(H, w, nroots=8, tol=1e-6):
+    """Time to the lowest `nroots` energies: plain FP64 Davidson against the FP32-storage
+    block Davidson with FP64 refinement (and against FP64-accurate paired-FP32 sigma).
+    E_ref is a tight FP64 run (residual 1e-8, energy error ~ residual^2 / gap); every
+    energy's error against it is reported.  Wall-clock seconds, each solver timed after
+    one untimed warm-up sigma; the sigma time of each precision at `nroots` vectors is
+    reported beside them (CUDA events, mean of 5)."""
+    import torch
+
+    from paper_2501_18185_gb300 import sci
+    from paper_2501_18185_gb300.davidson import davidson, davidson_mixed
+
+    diag = H.diagonal()
+
+    def hi(X):
+        return H.sigma(X.contiguous())
+
+    def lo(X):
+        return H.sigma(X.to(torch.float32).contiguous(), prec=sci.SCI_PREC_F32_STORE_F64_ACC)
+
+    def ds(X):
+        return H.sigma(X.contiguous(), prec=sci.SCI_PREC_F64_DS)
+
+    probe = torch.zeros((H.M, nroots), dtype=torch.float64, device=H.device)
+    sig_ms = {}
+    for name, f in (("fp64", hi), ("fp32_storage", lo), ("ds", ds)):
+        f(probe)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(5):
+            f(probe)
+        e1.record()
+        torch.cuda.synchronize()
+        sig_ms[name] = e0.elapsed_time(e1) / 5
+    ref = davidson(hi, diag, nroots=nroots, tol=1e-8, max_iter=1000)
+    e_ref = ref.energies.cpu().numpy()
+    out = {"nroots": nroots, "residual_tol": tol, "ref_residual": 1e-8, "ref_converged": bool(ref.converged),
+           "E_ref": [float(x) for x in e_ref], f"sigma_ms_nvec{nroots}": sig_ms}
+    for name, run in (("fp64", lambda: davidson(hi, diag, nroots=nroots, tol=tol, max_iter=600)),
+                      ("fp32_refined", lambda: davidson_mixed(lo, hi, diag, nroots=nroots, tol=tol, max_iter=600)),
+                      ("ds", lambda: davidson(ds, diag, nroots=nroots, tol=tol, max_iter=600))):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        res = run()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        err = np.abs(res.energies.cpu().numpy() - e_ref)
+        out[name] = {"seconds": dt, "converged": bool(res.converged), "iterations": res.iterations,
+                     "sigma_calls": res.sigma_calls, "max_abs_err_Eh": float(err.max()),
+                     "errors_Eh": [float(x) for x in err]}
+        if name == "fp32_refined":
+            out[name]["sigma_calls_fp32"] = res.sigma_calls_lo
+            out[name]["sigma_calls_fp64"] = res.sigma_calls_hi
+    out["speedup_fp32_refined_vs_fp64"] = out["fp64"]["seconds"] / out["fp32_refined"]["seconds"]
+    return out
+
+
 def run_reference(args, rank, world):
     """--impl reference: the CPU oracle on bounded samples of the same workload."""
     if rank != 0:
@@ -170,6 +228,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--ref-rows", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-davidson", action="store_true",
+                    help="skip the FP64 vs FP32-refined 8-root Davidson timing")
     ap.add_argument("--prec", default="f64", choices=["f64", "ds"],
                     help="f64: FP64 FMA path; ds: paired-FP32 products/sums (FP64 tolerance)")
     args = ap.parse_args()
@@ -307,6 +367,9 @@ def main():
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(w)
+    dav = None
+    if not args.no_davidson and world == 1 and not w.ints.complex_:
+        dav = davidson_bench(H, w)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c128" if w.ints.complex_ else "f64", "data": "synthetic",
@@ -316,7 +379,7 @@ def main():
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
             "gpu_launches": args.steps * (1 + 2 * ((nv + 7) // 8 if not w.ints.complex_ else (nv + 3) // 4)),
             "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "prec": args.prec,
-            "other_prec": variant}
+            "other_prec": variant, "davidson": dav}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -68,8 +68,15 @@ enum { SCI_REAL64 = 1, SCI_COMPLEX128 = 2 };                 /* Hamiltonian scal
 enum { SCI_SPIN_ORBITALS = 1, SCI_SPINORS = 2 };             /* orbital mode */
 enum {
     SCI_PREC_F64 = 1,                /* C double (complex: double pairs), S double */
-    SCI_PREC_F32_STORE_F64_ACC = 2,  /* C float, integrals rounded to float, products and
-                                        accumulation in FP64, S double (real mode only) */
+    SCI_PREC_F32_STORE_F64_ACC = 2,  /* real mode only.  C float, S double.  The double-
+                                        excitation table ((ai|bj) - (aj|bi) and (ai|bj))
+                                        is rounded to float once; each product of two
+                                        floats is formed exactly (FMA error term), the
+                                        per-bucket sums are compensated (paired FP32) and
+                                        accumulated into S in FP64.  Singles use the
+                                        paired-FP32 Fock sums of SCI_PREC_F64_DS.  The
+                                        result carries the FP32 rounding of the integrals
+                                        and of C (~1e-7 relative). */
     SCI_PREC_F64_DS = 3              /* C and S as for SCI_PREC_F64; the double-excitation
                                         products and per-bucket sums run in paired FP32
                                         ("double-single") arithmetic on the FP32 pipes:

@@ -58,6 +58,7 @@ def _load():
             L.sciref_count_pairs.argtypes = [vp, i64, i64, vp]
             L.sciref_sigma_rows.argtypes = [vp, vp, i64, vp, i32, vp]
             L.sciref_sigma_brute_rows.argtypes = [vp, vp, i64, vp, i32, vp]
+            L.sciref_rdm12.argtypes = [vp, vp, vp, vp]
             _lib = L
     return _lib
 
@@ -176,6 +177,18 @@ class Oracle:
 
     def sigma(self, C) -> np.ndarray:
         return self.sigma_rows(np.arange(self.M), C)
+
+    def rdm12(self, c):
+        """Unnormalised 1- and 2-RDM of vector c over spin-orbitals (spinors):
+        g1[p,q] = <c|a+_p a_q|c>, g2[p,q,r,s] = <c|a+_p a+_r a_s a_q|c>."""
+        c = np.ascontiguousarray(np.asarray(c).reshape(-1), dtype=self.dtype)
+        norb = self._h.shape[0] * (1 if self.mode == "spinors" else 2)
+        g1 = np.zeros((norb, norb), dtype=self.dtype)
+        g2 = np.zeros((norb,) * 4, dtype=self.dtype)
+        rc = self.L.sciref_rdm12(self.ctx, _ptr(c), _ptr(g1), _ptr(g2))
+        if rc != SCIREF_OK:
+            raise ValueError(rc)
+        return g1, g2
 
     def dense(self) -> np.ndarray:
         """Dense H on the list (small spaces only)."""

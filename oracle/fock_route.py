@@ -103,6 +103,34 @@ def hamiltonian(keys: np.ndarray, h_so: np.ndarray, eri_so: np.ndarray) -> np.nd
     return H
 
 
+def rdm12(keys: np.ndarray, c: np.ndarray, norb: int):
+    """<c|a+_p a_q|c> and <c|a+_p a+_r a_s a_q|c> by applying each operator string to c
+    (c indexed like the sorted keys; unnormalised)."""
+    keys = np.asarray(keys, dtype=np.uint64)
+    c = np.asarray(c).reshape(-1)
+    dt = np.complex128 if np.iscomplexobj(c) else np.float64
+    g1 = np.zeros((norb, norb), dtype=dt)
+    g2 = np.zeros((norb,) * 4, dtype=dt)
+
+    def expect(ops):
+        k = _apply_string(keys, ops)
+        idx = np.minimum(np.searchsorted(keys, k.s), len(keys) - 1)
+        hit = k.ok & (keys[idx] == k.s)
+        return np.sum(np.conj(c[idx[hit]]) * c[hit] * k.sign[hit])
+
+    for p in range(norb):
+        for q in range(norb):
+            g1[p, q] = expect([("c", p), ("a", q)])
+    for p in range(norb):
+        for q in range(norb):
+            for r in range(norb):
+                for s in range(norb):
+                    if p == r or q == s:
+                        continue
+                    g2[p, q, r, s] = expect([("c", p), ("c", r), ("a", s), ("a", q)])
+    return g1, g2
+
+
 def hamiltonian_decomposed(keys: np.ndarray, h_so: np.ndarray, eri_so: np.ndarray,
                            printed_h20: bool = False) -> np.ndarray:
     """H from Eq. decompositionH: H_1^0 + H_1^1 + H_2^0 + H_2^1 + H_2^2.

@@ -433,3 +433,124 @@ int sciref_sigma_brute_rows(const sciref_ctx *c, const int64_t *rows, int64_t nr
     }
     return SCIREF_OK;
 }
+
+/* ------------------------------------------------------------------ density matrices */
+/* <bra| a+_p a+_r a_s a_q |ket>: the operators applied one at a time to the ket, right
+ * to left (a_q first); 0 when the result is not bra. */
+static int two_body_sign(uint64_t bra, uint64_t ket, int p, int q, int r, int s)
+{
+    uint64_t d = ket;
+    int sg = annihilate(&d, q);
+    if (!sg) return 0;
+    sg *= annihilate(&d, s);
+    if (!sg) return 0;
+    sg *= create(&d, r);
+    if (!sg) return 0;
+    sg *= create(&d, p);
+    if (!sg || d != bra) return 0;
+    return sg;
+}
+
+static int one_body_sign(uint64_t bra, uint64_t ket, int p, int q)
+{
+    uint64_t d = ket;
+    int sg = annihilate(&d, q);
+    if (!sg) return 0;
+    sg *= create(&d, p);
+    if (!sg || d != bra) return 0;
+    return sg;
+}
+
+static void add_z(double *a, size_t idx, int is_complex, zd v)
+{
+    if (is_complex) {
+#pragma omp atomic
+        a[2 * idx] += creal(v);
+#pragma omp atomic
+        a[2 * idx + 1] += cimag(v);
+    } else {
+#pragma omp atomic
+        a[idx] += creal(v);
+    }
+}
+
+/* One- and two-particle density matrices of one vector C (paper Sec. 3.4, density
+ * matrices), over spin-orbitals (spin-orbital mode) or spinors:
+ *   g1[p][q]       = sum_IJ C_I^* C_J <D_I| a+_p a_q |D_J>
+ *   g2[p][q][r][s] = sum_IJ C_I^* C_J <D_I| a+_p a+_r a_s a_q |D_J>
+ * so that sum_pq h_pq g1_pq + 1/2 sum_pqrs (pq|rs) g2_pqrs = C^+ H C (Eq. Hamiltonian).
+ * Unnormalised (divide by C^+C).  Every candidate operator string for a connected pair
+ * (I, J) (the diagonal, singles and doubles of generation + lookup) is applied to D_J
+ * explicitly.  g1: norb^2 scalars, g2: norb^4 scalars, zeroed here (complex interleaved). */
+int sciref_rdm12(const sciref_ctx *c, const double *C, double *g1, double *g2)
+{
+    if (!c || !C || !g1 || !g2) return SCIREF_ERR_ARG;
+    const int z = c->is_complex;
+    const size_t m = (size_t)c->norb;
+    memset(g1, 0, m * m * (z ? 2 : 1) * sizeof(double));
+    memset(g2, 0, m * m * m * m * (z ? 2 : 1) * sizeof(double));
+#pragma omp parallel
+    {
+        const int maxc = 2 * 64 * 64;  /* candidate operator strings per pair */
+        int *cq = (int *)malloc(4 * sizeof(int) * maxc);
+        int *cs = cq + maxc, *cp = cs + maxc, *cr = cp + maxc;
+#pragma omp for schedule(dynamic, 8)
+        for (int64_t row = 0; row < c->M; row++) {
+            const uint64_t bra = c->keys[row];
+            const zd cI = conj(z ? CMPLX(C[2 * row], C[2 * row + 1]) : CMPLX(C[row], 0.0));
+            conn_t *list;
+            int64_t n = row_connections(c, row, &list);
+            for (int64_t t = -1; t < n; t++) {   /* t = -1: the diagonal */
+                const int64_t col = t < 0 ? row : list[t].j;
+                const uint64_t ket = c->keys[col];
+                const zd w = cI * (z ? CMPLX(C[2 * col], C[2 * col + 1]) : CMPLX(C[col], 0.0));
+                int occ[64], no = 0, from[2], to[2], nf = 0, nt = 0;
+                for (int p = 0; p < c->norb; p++) {
+                    if (occupied(ket, p)) occ[no++] = p;
+                    if (occupied(ket, p) && !occupied(bra, p)) from[nf++] = p;
+                    if (occupied(bra, p) && !occupied(ket, p)) to[nt++] = p;
+                }
+                /* candidate annihilated (q, s) and created (p, r) orbitals */
+                int nc = 0;
+                if (nf == 0) {
+                    for (int x = 0; x < no; x++) {
+                        add_z(g1, (size_t)occ[x] * m + occ[x], z, one_body_sign(bra, ket, occ[x], occ[x]) * w);
+                        for (int y = 0; y < no; y++) {
+                            if (x == y) continue;
+                            cq[nc] = occ[x]; cs[nc] = occ[y]; cp[nc] = occ[x]; cr[nc] = occ[y]; nc++;
+                            cq[nc] = occ[x]; cs[nc] = occ[y]; cp[nc] = occ[y]; cr[nc] = occ[x]; nc++;
+                        }
+                    }
+                } else if (nf == 1) {
+                    const int i = from[0], a = to[0];
+                    add_z(g1, (size_t)a * m + i, z, one_body_sign(bra, ket, a, i) * w);
+                    for (int x = 0; x < no; x++) {
+                        const int k = occ[x];
+                        if (k == i) continue;
+                        const int qs[2][2] = {{i, k}, {k, i}}, pr[2][2] = {{a, k}, {k, a}};
+                        for (int u = 0; u < 2; u++)
+                            for (int v = 0; v < 2; v++) {
+                                cq[nc] = qs[u][0]; cs[nc] = qs[u][1]; cp[nc] = pr[v][0]; cr[nc] = pr[v][1]; nc++;
+                            }
+                    }
+                } else {
+                    const int qs[2][2] = {{from[0], from[1]}, {from[1], from[0]}};
+                    const int pr[2][2] = {{to[0], to[1]}, {to[1], to[0]}};
+                    for (int u = 0; u < 2; u++)
+                        for (int v = 0; v < 2; v++) {
+                            cq[nc] = qs[u][0]; cs[nc] = qs[u][1]; cp[nc] = pr[v][0]; cr[nc] = pr[v][1]; nc++;
+                        }
+                }
+                for (int e = 0; e < nc; e++) {
+                    const int sg = two_body_sign(bra, ket, cp[e], cq[e], cr[e], cs[e]);
+                    if (!sg) continue;
+                    const size_t idx = (((size_t)cp[e] * m + cq[e]) * m + cr[e]) * m + cs[e];
+                    add_z(g2, idx, z, sg * w);
+                }
+            }
+            free(list);
+        }
+        free(cq);
+    }
+    return SCIREF_OK;
+}

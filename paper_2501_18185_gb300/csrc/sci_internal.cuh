@@ -17,12 +17,15 @@
 //   Doubles table "B2" (structure of arrays over E2 entries): every determinant D
 //     emits the (N-2)-electron keys K = D minus two occupied bits; entries sharing K
 //     form a bucket and are within a double excitation of each other.  Buckets of size
-//     1 are dropped; the rest are stored contiguously, largest first.
+//     1 are dropped; the rest are stored contiguously, largest first.  12 bytes each:
 //       e2_idx[p]     determinant index of the member
-//       e2_mask[p]    bit mask of the two extra orbitals of the member (D = K | mask)
-//       e2_col[p]     offset of the member's ket indices in tab
-//       e2_meta[p]    bits 0-15 bra offset in tab, bit 16 phase parity, bits 32-47
-//                     position inside the bucket, bits 48-63 bucket size
+//       e2_code[p]    bits 0-7 x, bits 8-15 y: the two extra orbitals x < y of the
+//                     member (D = K | 2^x | 2^y); bit 16 the phase parity
+//                     #(K below x) + #(K below y); bits 17-22 the member's position
+//                     inside its y-group (members of the bucket with the same y);
+//                     bits 23-29 the y-group size
+//       e2_pos[p]     bits 0-15 position inside the bucket, bits 16-31 bucket size
+//     Table offsets are derived from (x, y) by pair_offsets().
 //   Singles table "B1": the same with (N-1)-electron keys S = D minus one bit.
 //       e1_idx[p], e1_S[p] (the bucket key S), e1_meta[p]: bits 0-6 extra orbital,
 //       bit 7 parity, bits 8-19 position in bucket, bits 20-31 bucket size.
@@ -48,6 +51,53 @@ enum DevErr : int {
     DEV_OVERFLOW = 8,
 };
 
+// fields of an (N-2)-table code word and position word
+__host__ __device__ __forceinline__ int code_x(uint32_t c) { return (int)(c & 0xFFu); }
+__host__ __device__ __forceinline__ int code_y(uint32_t c) { return (int)((c >> 8) & 0xFFu); }
+__host__ __device__ __forceinline__ bool code_par(uint32_t c) { return (c >> 16) & 1u; }
+__host__ __device__ __forceinline__ int code_gofs(uint32_t c) { return (int)((c >> 17) & 0x3Fu); }
+__host__ __device__ __forceinline__ int code_gsize(uint32_t c) { return (int)((c >> 23) & 0x7Fu); }
+__host__ __device__ __forceinline__ uint32_t make_code(int x, int y, int par, int gofs, int gsize)
+{
+    return (uint32_t)x | ((uint32_t)y << 8) | ((uint32_t)par << 16) | ((uint32_t)gofs << 17) | ((uint32_t)gsize << 23);
+}
+__host__ __device__ __forceinline__ int pos_off(uint32_t p) { return (int)(p & 0xFFFFu); }
+__host__ __device__ __forceinline__ int pos_size(uint32_t p) { return (int)(p >> 16); }
+__host__ __device__ __forceinline__ uint64_t code_mask(uint32_t c)
+{
+    return (1ull << code_x(c)) | (1ull << code_y(c));
+}
+
+// Layout of the pair-integral table (see tab above).
+struct TabRule {
+    int spinors, n;
+};
+
+// bra (row) offset and ket (column) base of a member with extra orbitals x < y
+__host__ __device__ __forceinline__ void pair_offsets(TabRule r, int x, int y, uint32_t &rowoff, uint32_t &colbase)
+{
+    if (r.spinors) {
+        const uint32_t NP = (uint32_t)(r.n * (r.n - 1) / 2);
+        const uint32_t p = (uint32_t)(y * (y - 1) / 2 + x);
+        rowoff = p;
+        colbase = p * NP;
+        return;
+    }
+    const int n = r.n;
+    const uint32_t n2 = (uint32_t)(n * n);
+    if (x < n && y >= n) {  // alpha-beta
+        const uint32_t u = (uint32_t)((y - n) * n + x);
+        rowoff = u;
+        colbase = u * n2;
+    } else {                // same spin
+        const int a = x >= n ? x - n : x, b = y >= n ? y - n : y;
+        const uint32_t NP = (uint32_t)(n * (n - 1) / 2);
+        const uint32_t p = (uint32_t)(b * (b - 1) / 2 + a);
+        rowoff = p;
+        colbase = n2 * n2 + p * NP;
+    }
+}
+
 }  // namespace sci
 
 struct sci_ctx {
@@ -69,6 +119,8 @@ struct sci_ctx {
     float *tab32 = nullptr; // FP32 copy of tab (real mode)
     void *tab_ds = nullptr; // tab split into (hi, lo) floats: float2 (real) / float4 (complex)
     void *c_ds = nullptr;   // per-call split of one vector group of C: [M][<=8] float2 or [M][<=4] float4
+    void *g_ds = nullptr;   // g_so split into (hi, lo) floats
+    void *fref_ds = nullptr;  // fref split into (hi, lo) floats
     int64_t tab_elems = 0;
 
     // determinants
@@ -82,9 +134,8 @@ struct sci_ctx {
 
     int64_t e2 = 0, nb2 = 0;
     uint32_t *e2_idx = nullptr;
-    uint64_t *e2_mask = nullptr;
-    uint32_t *e2_col = nullptr;
-    uint64_t *e2_meta = nullptr;
+    uint32_t *e2_code = nullptr;
+    uint32_t *e2_pos = nullptr;
     int64_t e1 = 0, nb1 = 0;
     uint32_t *e1_idx = nullptr;
     uint64_t *e1_S = nullptr;

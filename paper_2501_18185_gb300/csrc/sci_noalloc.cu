@@ -58,19 +58,20 @@ __device__ __forceinline__ void put(Scratch s, uint32_t I, uint32_t J, int deg2,
     }
 }
 
-__global__ void k_conn2_noalloc(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_mask,
-                                const uint64_t *__restrict__ e_meta, int64_t E, int64_t rb, int64_t re, Scratch s)
+__global__ void k_conn2_noalloc(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_code,
+                                const uint32_t *__restrict__ e_pos, int64_t E, int64_t rb, int64_t re, Scratch s)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
         int64_t I = e_idx[p];
         if (I < rb || I >= re) continue;
-        uint64_t meta = e_meta[p];
-        int64_t bs = p - (int64_t)((meta >> 32) & 0xFFFF), be = bs + (int64_t)(meta >> 48);
-        uint64_t m = e_mask[p];
-        int par = (meta >> 16) & 1;
+        const uint32_t pos = e_pos[p], code = e_code[p];
+        int64_t bs = p - sci::pos_off(pos), be = bs + sci::pos_size(pos);
+        uint64_t m = sci::code_mask(code);
+        int par = sci::code_par(code);
         for (int64_t q = bs; q < be; q++) {
-            if (e_mask[q] & m) continue;
-            put(s, (uint32_t)I, e_idx[q], 1, par ^ (int)((e_meta[q] >> 16) & 1));
+            const uint32_t cq = e_code[q];
+            if (sci::code_mask(cq) & m) continue;
+            put(s, (uint32_t)I, e_idx[q], 1, par ^ (int)sci::code_par(cq));
         }
     }
 }
@@ -164,7 +165,7 @@ extern "C" int sci_connections_noalloc(sci_ctx *ctx, int64_t row_begin, int64_t 
     e = cudaMemsetAsync(s.counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return sci_cuda_check(ctx, e, "clear scratch counter");
     if (ctx->e2 > 0)
-        k_conn2_noalloc<<<grid_for(ctx->e2), 256, 0, st>>>(ctx->e2_idx, ctx->e2_mask, ctx->e2_meta, ctx->e2,
+        k_conn2_noalloc<<<grid_for(ctx->e2), 256, 0, st>>>(ctx->e2_idx, ctx->e2_code, ctx->e2_pos, ctx->e2,
                                                            row_begin, row_end, s);
     if (ctx->e1 > 0)
         k_conn1_noalloc<<<grid_for(ctx->e1), 256, 0, st>>>(ctx->e1_idx, ctx->e1_meta, ctx->e1, row_begin, row_end, s);

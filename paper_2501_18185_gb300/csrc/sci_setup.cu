@@ -324,43 +324,15 @@ __global__ void k_gather_sizes(const uint32_t *__restrict__ order, const uint32_
         out[t] = counts[order[t]];
 }
 
-struct TabRule {
-    int spinors, n;
-};
-
-// bra offset (row) and ket offset (column) of a member with extra orbitals x < y
-__device__ inline void pair_offsets(TabRule r, int x, int y, uint32_t &rowoff, uint32_t &colbase)
-{
-    if (r.spinors) {
-        uint32_t NP = (uint32_t)(r.n * (r.n - 1) / 2);
-        uint32_t p = (uint32_t)pair_index(x, y);
-        rowoff = p;
-        colbase = p * NP;
-        return;
-    }
-    int n = r.n;
-    uint32_t n2 = (uint32_t)(n * n);
-    if (x < n && y >= n) {           // alpha-beta
-        uint32_t u = (uint32_t)((y - n) * n + x);
-        rowoff = u;
-        colbase = u * n2;
-    } else {                         // same spin
-        int a = x >= n ? x - n : x, b = y >= n ? y - n : y;
-        uint32_t NP = (uint32_t)(n * (n - 1) / 2);
-        uint32_t p = (uint32_t)pair_index(a, b);
-        rowoff = p;
-        colbase = n2 * n2 + p * NP;
-    }
-}
-
 __device__ inline int count_below(uint64_t k, int p) { return __popcll(k & ((1ull << p) - 1ull)); }
 
-// warp per kept bucket: scatter members into the final doubles table
+// warp per kept bucket: scatter members into the final doubles table.  Members of a
+// bucket arrive in ascending determinant order, i.e. ascending (y, x); a y-group is the
+// run of members with the same y.
 __global__ void k_fill2(const uint32_t *__restrict__ order, const uint32_t *__restrict__ counts,
                         const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ newoff,
                         const uint64_t *__restrict__ ukeys, const uint64_t *__restrict__ vals, int64_t kept,
-                        TabRule r, uint32_t *__restrict__ e_idx, uint64_t *__restrict__ e_mask,
-                        uint32_t *__restrict__ e_col, uint64_t *__restrict__ e_meta)
+                        uint32_t *__restrict__ e_idx, uint32_t *__restrict__ e_code, uint32_t *__restrict__ e_pos)
 {
     int lane = threadIdx.x & 31;
     int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -372,13 +344,13 @@ __global__ void k_fill2(const uint32_t *__restrict__ order, const uint32_t *__re
         for (uint32_t t = lane; t < size; t += 32) {
             uint64_t v = vals[old + t];
             int x = (int)((v >> 32) & 0xFF), y = (int)((v >> 40) & 0xFF);
-            uint32_t rowoff, colbase;
-            pair_offsets(r, x, y, rowoff, colbase);
-            uint64_t par = (uint64_t)((count_below(K, x) + count_below(K, y)) & 1);
+            uint32_t gs = t, ge = t + 1;
+            while (gs > 0 && (int)((vals[old + gs - 1] >> 40) & 0xFF) == y) gs--;
+            while (ge < size && (int)((vals[old + ge] >> 40) & 0xFF) == y) ge++;
+            int par = (count_below(K, x) + count_below(K, y)) & 1;
             e_idx[dst + t] = (uint32_t)(v & 0xFFFFFFFFull);
-            e_mask[dst + t] = (1ull << x) | (1ull << y);
-            e_col[dst + t] = colbase;
-            e_meta[dst + t] = (uint64_t)rowoff | (par << 16) | ((uint64_t)t << 32) | ((uint64_t)size << 48);
+            e_code[dst + t] = sci::make_code(x, y, par, (int)(t - gs), (int)(ge - gs));
+            e_pos[dst + t] = t | (size << 16);
         }
     }
 }
@@ -545,10 +517,10 @@ void free_dets(sci_ctx *ctx)
     free_held(ctx, ctx->hdiag);
     free_held(ctx, ctx->fref);
     free_held(ctx, ctx->c_ds);
+    free_held(ctx, ctx->fref_ds);
     free_held(ctx, ctx->e2_idx);
-    free_held(ctx, ctx->e2_mask);
-    free_held(ctx, ctx->e2_col);
-    free_held(ctx, ctx->e2_meta);
+    free_held(ctx, ctx->e2_code);
+    free_held(ctx, ctx->e2_pos);
     free_held(ctx, ctx->e1_idx);
     free_held(ctx, ctx->e1_S);
     free_held(ctx, ctx->e1_meta);
@@ -568,6 +540,7 @@ void free_ints(sci_ctx *ctx)
     free_held(ctx, ctx->tab);
     free_held(ctx, ctx->tab32);
     free_held(ctx, ctx->tab_ds);
+    free_held(ctx, ctx->g_ds);
     ctx->have_ints = 0;
 }
 
@@ -594,6 +567,10 @@ int compute_diag_fref(sci_ctx *ctx)
                                                              (const double *)ctx->jd, (const double *)ctx->kd,
                                                              ctx->hdiag);
     }
+    // paired-FP32 copy of fref for the paired-FP32 singles
+    const int64_t nd = (int64_t)nn * (ctx->cplx ? 2 : 1);
+    if (!ctx->fref_ds) SCI_CK(alloc_held(ctx, &ctx->fref_ds, (size_t)nd * 8));
+    k_split_ds<<<grid_for(nd), 256, 0, st>>>((const double *)ctx->fref, (float2 *)ctx->fref_ds, nd);
     SCI_CK(cudaGetLastError());
     return SCI_OK;
 }
@@ -774,6 +751,9 @@ extern "C" int sci_set_integrals(sci_ctx *ctx, int scalar, int mode, int n, cons
         int64_t nd = ctx->tab_elems * (cplx ? 2 : 1);
         SCI_CK(alloc_held(ctx, &ctx->tab_ds, (size_t)nd * 8));
         if (nd > 0) k_split_ds<<<grid_for(nd), 256, 0, st>>>((const double *)ctx->tab, (float2 *)ctx->tab_ds, nd);
+        const int64_t ng = (int64_t)norb * norb * norb * (cplx ? 2 : 1);
+        SCI_CK(alloc_held(ctx, &ctx->g_ds, (size_t)ng * 8));
+        k_split_ds<<<grid_for(ng), 256, 0, st>>>((const double *)ctx->g_so, (float2 *)ctx->g_ds, ng);
     }
     SCI_CK(cudaGetLastError());
     ctx->have_ints = 1;
@@ -840,7 +820,6 @@ extern "C" int sci_set_determinants(sci_ctx *ctx, const uint64_t *keys, int64_t 
     if (rc != SCI_OK) return rc;
 
     // (N-2)-hole buckets: doubles
-    TabRule tr{ctx->spinors, ctx->n};
     if (N >= 2) {
         Buckets B;
         rc = build_buckets(ctx, 2, N * (N - 1) / 2, B);
@@ -849,14 +828,13 @@ extern "C" int sci_set_determinants(sci_ctx *ctx, const uint64_t *keys, int64_t 
         ctx->nb2 = B.kept;
         ctx->maxb2 = B.maxb;
         SCI_CK(alloc_held(ctx, (void **)&ctx->e2_idx, (size_t)B.entries * 4));
-        SCI_CK(alloc_held(ctx, (void **)&ctx->e2_mask, (size_t)B.entries * 8));
-        SCI_CK(alloc_held(ctx, (void **)&ctx->e2_col, (size_t)B.entries * 4));
-        SCI_CK(alloc_held(ctx, (void **)&ctx->e2_meta, (size_t)B.entries * 8));
+        SCI_CK(alloc_held(ctx, (void **)&ctx->e2_code, (size_t)B.entries * 4));
+        SCI_CK(alloc_held(ctx, (void **)&ctx->e2_pos, (size_t)B.entries * 4));
         if (B.kept > 0) {
             k_fill2<<<grid_for(B.kept * 32), 256, 0, st>>>(B.order.as<uint32_t>(), B.counts.as<uint32_t>(),
                                                           B.offsets.as<uint32_t>(), B.newoff.as<uint32_t>(),
                                                           B.ukeys.as<uint64_t>(), B.vals_sorted.as<uint64_t>(), B.kept,
-                                                          tr, ctx->e2_idx, ctx->e2_mask, ctx->e2_col, ctx->e2_meta);
+                                                          ctx->e2_idx, ctx->e2_code, ctx->e2_pos);
             SCI_CK(cudaGetLastError());
         }
         SCI_CK(cudaStreamSynchronize(st));

@@ -17,14 +17,14 @@
 // evaluated as F^ref_ai plus the terms of the orbitals where S and the reference differ
 // (the closed-shell reference simplification of Sec. 2.3).
 //
-// Kernel shape (bucket-major, no tensor cores: this is a sparse gather).  A CTA owns a
-// contiguous range of table entries (rows) and stages, in shared memory, every member of
-// the buckets those rows belong to: the member's extra-orbital mask, its ket offset into
-// the pair-integral table and its coefficients pre-multiplied by (-1)^pi.  Each thread
-// owns a row and walks the members of its bucket; lanes of a warp that share a bucket
-// read the same member (a shared-memory broadcast) and consecutive pair-table entries
-// (the table stores bra indices fastest).  A row's partial sum is added to sigma with
-// one FP64 atomic add per (bucket, member).
+// Kernel shape (bucket-major, no tensor cores: this is a sparse gather).  A CTA owns
+// the whole buckets that start in its range of CH table rows (its window), and stages
+// every member of them in shared memory: the member's ket code, its ket offset into the
+// pair-integral table and its coefficients pre-multiplied by (-1)^pi.  Each thread owns
+// a row and walks the members of its bucket; lanes of a warp that share a bucket read
+// the same member (a shared-memory broadcast) and consecutive pair-table entries (the
+// table stores bra indices fastest).  A row's partial sum is added to sigma with one
+// FP64 atomic add per (bucket, member).
 #include <algorithm>
 #include <cstdio>
 #include <vector>
@@ -44,14 +44,17 @@ __device__ __forceinline__ double flip(bool f, double a)
 }
 __device__ __forceinline__ float flip(bool f, float a) { return __int_as_float(__float_as_int(a) ^ ((int)f << 31)); }
 __device__ __forceinline__ zdbl flip(bool f, zdbl a) { return zdbl{flip(f, a.x), flip(f, a.y)}; }
+__device__ __forceinline__ float2 flip(bool f, float2 a) { return make_float2(flip(f, a.x), flip(f, a.y)); }
+__device__ __forceinline__ float4 flip(bool f, float4 a)
+{
+    return make_float4(flip(f, a.x), flip(f, a.y), flip(f, a.z), flip(f, a.w));
+}
 
 __device__ __forceinline__ void zero(double &a) { a = 0.0; }
-__device__ __forceinline__ void zero(float &a) { a = 0.0f; }
 __device__ __forceinline__ void zero(zdbl &a) { a = zdbl{0.0, 0.0}; }
 
 // acc += t * c
 __device__ __forceinline__ void fma_acc(double &acc, double t, double c) { acc = fma(t, c, acc); }
-__device__ __forceinline__ void fma_acc(double &acc, float t, float c) { acc = fma((double)t, (double)c, acc); }
 __device__ __forceinline__ void fma_acc(zdbl &acc, zdbl t, zdbl c)
 {
     acc.x = fma(t.x, c.x, acc.x);
@@ -59,7 +62,6 @@ __device__ __forceinline__ void fma_acc(zdbl &acc, zdbl t, zdbl c)
     acc.y = fma(t.x, c.y, acc.y);
     acc.y = fma(t.y, c.x, acc.y);
 }
-__device__ __forceinline__ void fma_acc(double &acc, double t, float c) { acc = fma(t, (double)c, acc); }
 
 __device__ __forceinline__ void red_add(double *p, double v) { atomicAdd(p, v); }
 __device__ __forceinline__ void red_add(zdbl *p, zdbl v)
@@ -79,19 +81,19 @@ template <> __device__ __forceinline__ zdbl ldg<zdbl>(const zdbl *p)
 // is coded as bytes (x, y, x, y) when it is the bra (row) and (x', y', y', x') when it is
 // the ket (column); the XOR of the two codes has a zero byte exactly when they share an
 // orbital (x = x', y = y', x = y' or y = x').
-__device__ __forceinline__ uint32_t row_code(uint64_t mask)
+__device__ __forceinline__ uint32_t row_code(uint32_t code)
 {
-    uint32_t x = (uint32_t)(__ffsll((long long)mask) - 1), y = 63u - (uint32_t)__clzll((long long)mask);
+    const uint32_t x = code & 0xFFu, y = (code >> 8) & 0xFFu;
     return x | (y << 8) | (x << 16) | (y << 24);
 }
-__device__ __forceinline__ uint32_t col_code(uint64_t mask)
+__device__ __forceinline__ uint32_t col_code(uint32_t code)
 {
-    uint32_t x = (uint32_t)(__ffsll((long long)mask) - 1), y = 63u - (uint32_t)__clzll((long long)mask);
+    const uint32_t x = code & 0xFFu, y = (code >> 8) & 0xFFu;
     return x | (y << 8) | (y << 16) | (x << 24);
 }
 __device__ __forceinline__ bool disjoint(uint32_t rc, uint32_t cc)
 {
-    uint32_t v = rc ^ cc;
+    const uint32_t v = rc ^ cc;
     return ((v - 0x01010101u) & ~v & 0x80808080u) == 0u;
 }
 
@@ -100,6 +102,22 @@ template <typename TS> struct AccOf { using type = double; };
 template <> struct AccOf<zdbl> { using type = zdbl; };
 
 constexpr int kThreads = 256;
+constexpr int kUnroll = 4;
+// Rows per CTA.  Eight 256-thread CTAs fit an SM; what shared memory leaves of the
+// 256 KB L1 for caching decides the speed (measured on the 2M-determinant space:
+// 5.20 ms at 768 rows, 5.34 at 1024, 7.63 at 1280, where L1 is nearly gone).
+constexpr int kRowsPerCta = 768;
+
+// The rows of CTA b: the buckets that start in [b*CH, (b+1)*CH), i.e. from the start of
+// the bucket holding row b*CH to the start of the bucket holding row (b+1)*CH.  Every
+// bucket lands in exactly one window; a window has at most CH + maxb - 1 rows (it can be
+// empty when one bucket spans a whole range).
+__device__ __forceinline__ void window(const uint32_t *__restrict__ e_pos, int64_t E, int CH, int64_t &r0, int64_t &r1)
+{
+    const int64_t a0 = (int64_t)blockIdx.x * CH, a1 = a0 + CH;
+    r0 = a0 - sci::pos_off(e_pos[a0]);
+    r1 = a1 < E ? a1 - sci::pos_off(e_pos[a1]) : E;
+}
 
 // ------------------------------------------------------------------ sigma = diag * c
 template <typename TC, typename TA>
@@ -121,49 +139,44 @@ __global__ void k_sigma_init(const double *__restrict__ hdiag, const TC *__restr
     }
 }
 
-// ------------------------------------------------------------------ doubles
+// ------------------------------------------------------------------ doubles (FP64)
 // TS: storage type of tab and staged coefficients; TA: accumulator (FP64 / complex128).
 // Shared memory per staged member: (ket code, ket table offset) as uint2, and its NV
 // coefficients times (-1)^pi.
-constexpr int kUnroll = 4;
-
 template <typename TS, typename TC, int NV>
 __global__ void __launch_bounds__(kThreads)
-k_doubles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_mask, const uint32_t *__restrict__ e_col,
-          const uint64_t *__restrict__ e_meta, int64_t E, int CH, const TS *__restrict__ tab,
-          const TC *__restrict__ C, int nvec, int v0, typename AccOf<TS>::type *__restrict__ Sout)
+k_doubles(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_code, const uint32_t *__restrict__ e_pos,
+          int64_t E, int CH, sci::TabRule tr, const TS *__restrict__ tab, const TC *__restrict__ C, int nvec, int v0,
+          typename AccOf<TS>::type *__restrict__ Sout)
 {
     using TA = typename AccOf<TS>::type;
     extern __shared__ __align__(16) unsigned char smem[];
-    const int64_t r0 = (int64_t)blockIdx.x * CH;
-    if (r0 >= E) return;
-    const int64_t r1 = min(r0 + (int64_t)CH, E);
-    const uint64_t mf = e_meta[r0], ml = e_meta[r1 - 1];
-    const int64_t w0 = r0 - (int64_t)((mf >> 32) & 0xFFFF);
-    const int64_t w1 = (r1 - 1) - (int64_t)((ml >> 32) & 0xFFFF) + (int64_t)(ml >> 48);
-    const int W = (int)(w1 - w0);
+    int64_t r0, r1;
+    window(e_pos, E, CH, r0, r1);
+    if (r0 >= r1) return;
+    const int W = (int)(r1 - r0);
     TS *s_c = reinterpret_cast<TS *>(smem);
-    size_t cbytes = ((size_t)W * NV * sizeof(TS) + 15) & ~(size_t)15;
+    const size_t cbytes = ((size_t)W * NV * sizeof(TS) + 15) & ~(size_t)15;
     uint2 *s_kc = reinterpret_cast<uint2 *>(smem + cbytes);
 
     for (int q = threadIdx.x; q < W; q += blockDim.x) {
-        const int64_t g = w0 + q;
-        const uint32_t idx = e_idx[g];
-        const bool par = (e_meta[g] >> 16) & 1;
-        s_kc[q] = make_uint2(col_code(e_mask[g]), e_col[g]);
+        const int64_t g = r0 + q;
+        const uint32_t idx = e_idx[g], code = e_code[g];
+        uint32_t rowoff, colbase;
+        sci::pair_offsets(tr, sci::code_x(code), sci::code_y(code), rowoff, colbase);
+        s_kc[q] = make_uint2(col_code(code), colbase);
+        const bool par = sci::code_par(code);
 #pragma unroll
         for (int v = 0; v < NV; v++) s_c[q * NV + v] = flip(par, (TS)C[(int64_t)idx * nvec + v0 + v]);
     }
     __syncthreads();
 
-    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-        const int q0 = (int)(r - w0);
-        const uint64_t meta = e_meta[r];
-        const uint32_t rowoff = (uint32_t)(meta & 0xFFFF);
-        const bool par = (meta >> 16) & 1;
-        const int bs = q0 - (int)((meta >> 32) & 0xFFFF);
-        const int be = bs + (int)(meta >> 48);
-        const uint32_t rc = row_code(e_mask[r]);
+    for (int q0 = threadIdx.x; q0 < W; q0 += blockDim.x) {
+        const uint32_t code = e_code[r0 + q0], pos = e_pos[r0 + q0];
+        uint32_t rowoff, colbase;
+        sci::pair_offsets(tr, sci::code_x(code), sci::code_y(code), rowoff, colbase);
+        const int bs = q0 - sci::pos_off(pos), be = bs + sci::pos_size(pos);
+        const uint32_t rc = row_code(code);
         const TS *trow = tab + rowoff;
         TA acc[NV];
 #pragma unroll
@@ -200,7 +213,8 @@ k_doubles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_mas
 #pragma unroll
             for (int v = 0; v < NV; v++) fma_acc(acc[v], t, s_c[j * NV + v]);
         }
-        const uint32_t idx = e_idx[r];
+        const uint32_t idx = e_idx[r0 + q0];
+        const bool par = sci::code_par(code);
 #pragma unroll
         for (int v = 0; v < NV; v++) red_add(Sout + (int64_t)idx * nvec + v0 + v, flip(par, acc[v]));
     }
@@ -258,25 +272,112 @@ __device__ __forceinline__ double f2d_int(float f)
 
 __device__ __forceinline__ double ds_value(Ds a) { return f2d_int(a.hi) + f2d_int(a.lo); }
 
-__device__ __forceinline__ float2 flip(bool f, float2 a) { return make_float2(flip(f, a.x), flip(f, a.y)); }
-__device__ __forceinline__ float4 flip(bool f, float4 a)
-{
-    return make_float4(flip(f, a.x), flip(f, a.y), flip(f, a.z), flip(f, a.w));
-}
-
 __device__ __forceinline__ float2 ds_split(double x)
 {
     const float hi = (float)x;
     return make_float2(hi, (float)(x - (double)hi));
 }
 
+__device__ __forceinline__ float2 ds_split(float x) { return make_float2(x, 0.f); }
+
 // split the vector group C[:, v0:v0+G] into paired floats, once per sigma call (so the
 // staging in the bucket kernel, which touches each coefficient many times, only copies)
-__global__ void k_split_c(const double *__restrict__ C, int64_t M, int nvec, int v0, int G, float2 *__restrict__ out)
+template <typename TC>
+__global__ void k_split_c(const TC *__restrict__ C, int64_t M, int nvec, int v0, int G, float2 *__restrict__ out)
 {
     const int64_t total = M * G;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
         out[t] = ds_split(C[(t / G) * nvec + v0 + t % G]);
+}
+
+// a += t * c for FP32 t and c: the product is exact as p + e (e by FMA), the sum is
+// compensated as in ds_fma
+__device__ __forceinline__ void ds_fma1(Ds &a, float t, float c)
+{
+    const float p = t * c;
+    const float e = fmaf(t, c, -p);
+    const float s = a.hi + p;
+    const float bv = s - a.hi;
+    const float err = (a.hi - (s - bv)) + (p - bv);
+    a.lo += err + e;
+    a.hi = s;
+}
+
+// FP32 storage: the pair table rounded to FP32 (tab32) and FP32 coefficients, exact
+// products, compensated bucket sums, FP64 accumulation into sigma
+template <int NV>
+__global__ void __launch_bounds__(kThreads)
+k_doubles_f32(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_code,
+              const uint32_t *__restrict__ e_pos, int64_t E, int CH, sci::TabRule tr,
+              const float *__restrict__ tab32, const float *__restrict__ C, int nvec, int v0,
+              double *__restrict__ Sout)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    int64_t r0, r1;
+    window(e_pos, E, CH, r0, r1);
+    if (r0 >= r1) return;
+    const int W = (int)(r1 - r0);
+    float *s_c = reinterpret_cast<float *>(smem);
+    const size_t cbytes = ((size_t)W * NV * sizeof(float) + 15) & ~(size_t)15;
+    uint2 *s_kc = reinterpret_cast<uint2 *>(smem + cbytes);
+
+    for (int q = threadIdx.x; q < W; q += blockDim.x) {
+        const int64_t g = r0 + q;
+        const uint32_t idx = e_idx[g], code = e_code[g];
+        uint32_t rowoff, colbase;
+        sci::pair_offsets(tr, sci::code_x(code), sci::code_y(code), rowoff, colbase);
+        s_kc[q] = make_uint2(col_code(code), colbase);
+        const bool par = sci::code_par(code);
+#pragma unroll
+        for (int v = 0; v < NV; v++) s_c[q * NV + v] = flip(par, C[(int64_t)idx * nvec + v0 + v]);
+    }
+    __syncthreads();
+
+    for (int q0 = threadIdx.x; q0 < W; q0 += blockDim.x) {
+        const uint32_t code = e_code[r0 + q0], pos = e_pos[r0 + q0];
+        uint32_t rowoff, colbase;
+        sci::pair_offsets(tr, sci::code_x(code), sci::code_y(code), rowoff, colbase);
+        const int bs = q0 - sci::pos_off(pos), be = bs + sci::pos_size(pos);
+        const uint32_t rc = row_code(code);
+        const float *trow = tab32 + rowoff;
+        Ds acc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) ds_zero(acc[v]);
+        int j = bs;
+        for (; j + kUnroll <= be; j += kUnroll) {
+            uint2 kc[kUnroll];
+            float t[kUnroll];
+            unsigned vm = 0;
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                kc[u] = s_kc[j + u];
+                vm |= (unsigned)disjoint(rc, kc[u].x) << u;
+            }
+            if (vm == 0) continue;
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                t[u] = 0.f;
+                if (vm & (1u << u)) t[u] = __ldg(trow + kc[u].y);
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++)
+#pragma unroll
+                for (int v = 0; v < NV; v++) ds_fma1(acc[v], t[u], s_c[(j + u) * NV + v]);
+#pragma unroll
+            for (int v = 0; v < NV; v++) ds_renorm(acc[v]);
+        }
+        for (; j < be; j++) {
+            const uint2 kc = s_kc[j];
+            if (!disjoint(rc, kc.x)) continue;
+            const float t = __ldg(trow + kc.y);
+#pragma unroll
+            for (int v = 0; v < NV; v++) ds_fma1(acc[v], t, s_c[j * NV + v]);
+        }
+        const uint32_t idx = e_idx[r0 + q0];
+        const bool par = sci::code_par(code);
+#pragma unroll
+        for (int v = 0; v < NV; v++) red_add(Sout + (int64_t)idx * nvec + v0 + v, flip(par, ds_value(acc[v])));
+    }
 }
 
 __global__ void k_split_cz(const zdbl *__restrict__ C, int64_t M, int nvec, int v0, int G, float4 *__restrict__ out)
@@ -289,44 +390,41 @@ __global__ void k_split_cz(const zdbl *__restrict__ C, int64_t M, int nvec, int 
     }
 }
 
-// real: tab2 is the (hi, lo) split of the pair table
+// real: tab2 is the (hi, lo) split of the pair table, C2 the split vector group
 template <int NV>
 __global__ void __launch_bounds__(kThreads)
-k_doubles_ds(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_mask,
-             const uint32_t *__restrict__ e_col, const uint64_t *__restrict__ e_meta, int64_t E, int CH,
+k_doubles_ds(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_code,
+             const uint32_t *__restrict__ e_pos, int64_t E, int CH, sci::TabRule tr,
              const float2 *__restrict__ tab2, const float2 *__restrict__ C2, int nvec, int v0,
              double *__restrict__ Sout)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int64_t r0 = (int64_t)blockIdx.x * CH;
-    if (r0 >= E) return;
-    const int64_t r1 = min(r0 + (int64_t)CH, E);
-    const uint64_t mf = e_meta[r0], ml = e_meta[r1 - 1];
-    const int64_t w0 = r0 - (int64_t)((mf >> 32) & 0xFFFF);
-    const int64_t w1 = (r1 - 1) - (int64_t)((ml >> 32) & 0xFFFF) + (int64_t)(ml >> 48);
-    const int W = (int)(w1 - w0);
+    int64_t r0, r1;
+    window(e_pos, E, CH, r0, r1);
+    if (r0 >= r1) return;
+    const int W = (int)(r1 - r0);
     float2 *s_c = reinterpret_cast<float2 *>(smem);
-    size_t cbytes = ((size_t)W * NV * sizeof(float2) + 15) & ~(size_t)15;
+    const size_t cbytes = ((size_t)W * NV * sizeof(float2) + 15) & ~(size_t)15;
     uint2 *s_kc = reinterpret_cast<uint2 *>(smem + cbytes);
 
     for (int q = threadIdx.x; q < W; q += blockDim.x) {
-        const int64_t g = w0 + q;
-        const uint32_t idx = e_idx[g];
-        const bool par = (e_meta[g] >> 16) & 1;
-        s_kc[q] = make_uint2(col_code(e_mask[g]), e_col[g]);
+        const int64_t g = r0 + q;
+        const uint32_t idx = e_idx[g], code = e_code[g];
+        uint32_t rowoff, colbase;
+        sci::pair_offsets(tr, sci::code_x(code), sci::code_y(code), rowoff, colbase);
+        s_kc[q] = make_uint2(col_code(code), colbase);
+        const bool par = sci::code_par(code);
 #pragma unroll
         for (int v = 0; v < NV; v++) s_c[q * NV + v] = flip(par, C2[(int64_t)idx * NV + v]);
     }
     __syncthreads();
 
-    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-        const int q0 = (int)(r - w0);
-        const uint64_t meta = e_meta[r];
-        const uint32_t rowoff = (uint32_t)(meta & 0xFFFF);
-        const bool par = (meta >> 16) & 1;
-        const int bs = q0 - (int)((meta >> 32) & 0xFFFF);
-        const int be = bs + (int)(meta >> 48);
-        const uint32_t rc = row_code(e_mask[r]);
+    for (int q0 = threadIdx.x; q0 < W; q0 += blockDim.x) {
+        const uint32_t code = e_code[r0 + q0], pos = e_pos[r0 + q0];
+        uint32_t rowoff, colbase;
+        sci::pair_offsets(tr, sci::code_x(code), sci::code_y(code), rowoff, colbase);
+        const int bs = q0 - sci::pos_off(pos), be = bs + sci::pos_size(pos);
+        const uint32_t rc = row_code(code);
         const float2 *trow = tab2 + rowoff;
         Ds acc[NV];
 #pragma unroll
@@ -361,76 +459,73 @@ k_doubles_ds(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_
 #pragma unroll
             for (int v = 0; v < NV; v++) ds_fma(acc[v], t, s_c[j * NV + v]);
         }
-        const uint32_t idx = e_idx[r];
+        const uint32_t idx = e_idx[r0 + q0];
+        const bool par = sci::code_par(code);
 #pragma unroll
         for (int v = 0; v < NV; v++) red_add(Sout + (int64_t)idx * nvec + v0 + v, flip(par, ds_value(acc[v])));
     }
 }
 
-// complex: tab4 holds (re_hi, re_lo, im_hi, im_lo); staged c as (re, im) float2 pairs
+// complex: tab4 holds (re_hi, re_lo, im_hi, im_lo); C4 the split vector group
 template <int NV>
 __global__ void __launch_bounds__(kThreads)
-k_doubles_dsz(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_mask,
-              const uint32_t *__restrict__ e_col, const uint64_t *__restrict__ e_meta, int64_t E, int CH,
+k_doubles_dsz(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_code,
+              const uint32_t *__restrict__ e_pos, int64_t E, int CH, sci::TabRule tr,
               const float4 *__restrict__ tab4, const float4 *__restrict__ C4, int nvec, int v0, zdbl *__restrict__ Sout)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int64_t r0 = (int64_t)blockIdx.x * CH;
-    if (r0 >= E) return;
-    const int64_t r1 = min(r0 + (int64_t)CH, E);
-    const uint64_t mf = e_meta[r0], ml = e_meta[r1 - 1];
-    const int64_t w0 = r0 - (int64_t)((mf >> 32) & 0xFFFF);
-    const int64_t w1 = (r1 - 1) - (int64_t)((ml >> 32) & 0xFFFF) + (int64_t)(ml >> 48);
-    const int W = (int)(w1 - w0);
-    float4 *s_c = reinterpret_cast<float4 *>(smem);   // (re_hi, re_lo, im_hi, im_lo)
-    size_t cbytes = ((size_t)W * NV * sizeof(float4) + 15) & ~(size_t)15;
+    int64_t r0, r1;
+    window(e_pos, E, CH, r0, r1);
+    if (r0 >= r1) return;
+    const int W = (int)(r1 - r0);
+    float4 *s_c = reinterpret_cast<float4 *>(smem);
+    const size_t cbytes = ((size_t)W * NV * sizeof(float4) + 15) & ~(size_t)15;
     uint2 *s_kc = reinterpret_cast<uint2 *>(smem + cbytes);
 
     for (int q = threadIdx.x; q < W; q += blockDim.x) {
-        const int64_t g = w0 + q;
-        const uint32_t idx = e_idx[g];
-        const bool par = (e_meta[g] >> 16) & 1;
-        s_kc[q] = make_uint2(col_code(e_mask[g]), e_col[g]);
+        const int64_t g = r0 + q;
+        const uint32_t idx = e_idx[g], code = e_code[g];
+        uint32_t rowoff, colbase;
+        sci::pair_offsets(tr, sci::code_x(code), sci::code_y(code), rowoff, colbase);
+        s_kc[q] = make_uint2(col_code(code), colbase);
+        const bool par = sci::code_par(code);
 #pragma unroll
-        for (int v = 0; v < NV; v++) {
-            s_c[q * NV + v] = flip(par, C4[(int64_t)idx * NV + v]);
-        }
+        for (int v = 0; v < NV; v++) s_c[q * NV + v] = flip(par, C4[(int64_t)idx * NV + v]);
     }
     __syncthreads();
 
-    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-        const int q0 = (int)(r - w0);
-        const uint64_t meta = e_meta[r];
-        const uint32_t rowoff = (uint32_t)(meta & 0xFFFF);
-        const bool par = (meta >> 16) & 1;
-        const int bs = q0 - (int)((meta >> 32) & 0xFFFF);
-        const int be = bs + (int)(meta >> 48);
-        const uint32_t rc = row_code(e_mask[r]);
+    for (int q0 = threadIdx.x; q0 < W; q0 += blockDim.x) {
+        const uint32_t code = e_code[r0 + q0], pos = e_pos[r0 + q0];
+        uint32_t rowoff, colbase;
+        sci::pair_offsets(tr, sci::code_x(code), sci::code_y(code), rowoff, colbase);
+        const int bs = q0 - sci::pos_off(pos), be = bs + sci::pos_size(pos);
+        const uint32_t rc = row_code(code);
         const float4 *trow = tab4 + rowoff;
         Ds ar[NV], ai[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) ds_zero(ar[v]), ds_zero(ai[v]);
-        int j = bs;
-        for (; j < be; j++) {
+        int nused = 0;
+        for (int j = bs; j < be; j++) {
             const uint2 kc = s_kc[j];
-            float4 t = __ldg(trow + kc.y);
-            if (!disjoint(rc, kc.x)) t = make_float4(0.f, 0.f, 0.f, 0.f);
-            const float2 tr = make_float2(t.x, t.y), ti = make_float2(t.z, t.w);
+            if (!disjoint(rc, kc.x)) continue;
+            const float4 t = __ldg(trow + kc.y);
+            const float2 tr_ = make_float2(t.x, t.y), ti = make_float2(t.z, t.w);
             const float2 mti = make_float2(-t.z, -t.w);
 #pragma unroll
             for (int v = 0; v < NV; v++) {
                 const float4 c = s_c[j * NV + v];
                 const float2 cr = make_float2(c.x, c.y), ci = make_float2(c.z, c.w);
-                ds_fma(ar[v], tr, cr);
+                ds_fma(ar[v], tr_, cr);
                 ds_fma(ar[v], mti, ci);
-                ds_fma(ai[v], tr, ci);
+                ds_fma(ai[v], tr_, ci);
                 ds_fma(ai[v], ti, cr);
             }
-            if (((j - bs) & 3) == 3)
+            if ((++nused & 3) == 0)
 #pragma unroll
                 for (int v = 0; v < NV; v++) ds_renorm(ar[v]), ds_renorm(ai[v]);
         }
-        const uint32_t idx = e_idx[r];
+        const uint32_t idx = e_idx[r0 + q0];
+        const bool par = sci::code_par(code);
 #pragma unroll
         for (int v = 0; v < NV; v++)
             red_add(Sout + (int64_t)idx * nvec + v0 + v, flip(par, zdbl{ds_value(ar[v]), ds_value(ai[v])}));
@@ -474,13 +569,127 @@ k_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S, 
                 if constexpr (sizeof(TS) == sizeof(zdbl)) { f.x -= g.x; f.y -= g.y; } else { f -= g; }
             }
 #pragma unroll
-            for (int v = 0; v < NV; v++) {
-                fma_acc(acc[v], f, flip(parq, C[(int64_t)idxq * nvec + v0 + v]));
-            }
+            for (int v = 0; v < NV; v++) fma_acc(acc[v], f, flip(parq, C[(int64_t)idxq * nvec + v0 + v]));
         }
         const uint32_t idx = e_idx[p];
 #pragma unroll
         for (int v = 0; v < NV; v++) red_add(Sout + (int64_t)idx * nvec + v0 + v, flip(par, acc[v]));
+    }
+}
+
+// ------------------------------------------------------------------ singles, paired FP32
+// F^S_ai = F^ref_ai + sum_{k in S\ref} g_ai(k) - sum_{k in ref\S} g_ai(k) summed in
+// paired FP32 from split copies of fref and g_so, then multiplied into the row sum like
+// the doubles.  C2/C4 is the split vector group (row stride NV).
+__device__ __forceinline__ void ds_add(Ds &a, float2 b)
+{
+    const float s = a.hi + b.x;
+    const float bv = s - a.hi;
+    const float err = (a.hi - (s - bv)) + (b.x - bv);
+    a.lo += err + b.y;
+    a.hi = s;
+}
+
+template <int NV>
+__global__ void __launch_bounds__(kThreads)
+k_singles_ds(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S, const uint32_t *__restrict__ e_meta,
+             int64_t E, int norb, uint64_t ref, const float2 *__restrict__ fref2, const float2 *__restrict__ g2,
+             const float2 *__restrict__ C2, int nvec, int v0, double *__restrict__ Sout)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t meta = e_meta[p];
+        const int a = (int)(meta & 0x7F);
+        const bool par = (meta >> 7) & 1;
+        const int64_t bs = p - (int64_t)((meta >> 8) & 0xFFF);
+        const int64_t be = bs + (int64_t)(meta >> 20);
+        const uint64_t Sk = e_S[p];
+        const uint64_t part = Sk & ~ref, holes = ref & ~Sk;
+        Ds acc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) ds_zero(acc[v]);
+        for (int64_t q = bs; q < be; q++) {
+            if (q == p) continue;
+            const uint32_t mq = e_meta[q];
+            const int i = (int)(mq & 0x7F);
+            const bool parq = (mq >> 7) & 1;
+            const uint32_t idxq = e_idx[q];
+            const float2 f0 = __ldg(fref2 + i * norb + a);
+            Ds f{f0.x, f0.y};
+            for (uint64_t m = part; m; m &= m - 1) {
+                const int k = __ffsll((long long)m) - 1;
+                ds_add(f, __ldg(g2 + ((int64_t)k * norb + i) * norb + a));
+            }
+            for (uint64_t m = holes; m; m &= m - 1) {
+                const int k = __ffsll((long long)m) - 1;
+                ds_add(f, flip(true, __ldg(g2 + ((int64_t)k * norb + i) * norb + a)));
+            }
+            ds_renorm(f);
+            const float2 fv = make_float2(f.hi, f.lo);
+#pragma unroll
+            for (int v = 0; v < NV; v++) ds_fma(acc[v], fv, flip(parq, C2[(int64_t)idxq * NV + v]));
+        }
+        const uint32_t idx = e_idx[p];
+#pragma unroll
+        for (int v = 0; v < NV; v++) red_add(Sout + (int64_t)idx * nvec + v0 + v, flip(par, ds_value(acc[v])));
+    }
+}
+
+template <int NV>
+__global__ void __launch_bounds__(kThreads)
+k_singles_dsz(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S,
+              const uint32_t *__restrict__ e_meta, int64_t E, int norb, uint64_t ref,
+              const float4 *__restrict__ fref4, const float4 *__restrict__ g4, const float4 *__restrict__ C4,
+              int nvec, int v0, zdbl *__restrict__ Sout)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t meta = e_meta[p];
+        const int a = (int)(meta & 0x7F);
+        const bool par = (meta >> 7) & 1;
+        const int64_t bs = p - (int64_t)((meta >> 8) & 0xFFF);
+        const int64_t be = bs + (int64_t)(meta >> 20);
+        const uint64_t Sk = e_S[p];
+        const uint64_t part = Sk & ~ref, holes = ref & ~Sk;
+        Ds ar[NV], ai[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) ds_zero(ar[v]), ds_zero(ai[v]);
+        for (int64_t q = bs; q < be; q++) {
+            if (q == p) continue;
+            const uint32_t mq = e_meta[q];
+            const int i = (int)(mq & 0x7F);
+            const bool parq = (mq >> 7) & 1;
+            const uint32_t idxq = e_idx[q];
+            const float4 f0 = __ldg(fref4 + i * norb + a);
+            Ds fr{f0.x, f0.y}, fi{f0.z, f0.w};
+            for (uint64_t m = part; m; m &= m - 1) {
+                const int k = __ffsll((long long)m) - 1;
+                const float4 g = __ldg(g4 + ((int64_t)k * norb + i) * norb + a);
+                ds_add(fr, make_float2(g.x, g.y));
+                ds_add(fi, make_float2(g.z, g.w));
+            }
+            for (uint64_t m = holes; m; m &= m - 1) {
+                const int k = __ffsll((long long)m) - 1;
+                const float4 g = flip(true, __ldg(g4 + ((int64_t)k * norb + i) * norb + a));
+                ds_add(fr, make_float2(g.x, g.y));
+                ds_add(fi, make_float2(g.z, g.w));
+            }
+            ds_renorm(fr);
+            ds_renorm(fi);
+            const float2 tr_ = make_float2(fr.hi, fr.lo), ti = make_float2(fi.hi, fi.lo);
+            const float2 mti = make_float2(-fi.hi, -fi.lo);
+#pragma unroll
+            for (int v = 0; v < NV; v++) {
+                const float4 c = flip(parq, C4[(int64_t)idxq * NV + v]);
+                const float2 cr = make_float2(c.x, c.y), ci = make_float2(c.z, c.w);
+                ds_fma(ar[v], tr_, cr);
+                ds_fma(ar[v], mti, ci);
+                ds_fma(ai[v], tr_, ci);
+                ds_fma(ai[v], ti, cr);
+            }
+        }
+        const uint32_t idx = e_idx[p];
+#pragma unroll
+        for (int v = 0; v < NV; v++)
+            red_add(Sout + (int64_t)idx * nvec + v0 + v, flip(par, zdbl{ds_value(ar[v]), ds_value(ai[v])}));
     }
 }
 
@@ -492,24 +701,25 @@ int grid_for(int64_t n, int threads = kThreads)
     return (int)g;
 }
 
-// rows per CTA so that the staged window fits the shared-memory budget; small windows
-// first (more resident CTAs per SM), larger ones only when the buckets need them
+// Rows per CTA (CH) so that the staged window, at most CH + maxb - 1 members, fits the
+// shared-memory budget; small windows first (more resident CTAs per SM), larger ones
+// only when the buckets need them.
 int choose_rows(int maxb, size_t bytes_per_entry, size_t &smem)
 {
     const size_t budgets[3] = {48 * 1024, 100 * 1024, 200 * 1024};
     for (size_t budget : budgets) {
-        int64_t ch = (int64_t)(budget / bytes_per_entry) - 2 * (int64_t)(maxb - 1) - 8;
+        int64_t ch = (int64_t)(budget / bytes_per_entry) - (int64_t)maxb - 8;
         if (ch >= 512 || (budget == budgets[2] && ch >= 64)) {
-            // measured on the 2M/1M workloads: 2048-row windows for 16-byte staged
-            // entries, 1024 for wider ones
-            ch = std::min<int64_t>(ch, bytes_per_entry <= 16 ? 2048 : 1024);
+            ch = std::min<int64_t>(ch, kRowsPerCta);
             ch = std::max<int64_t>(64, ch & ~(int64_t)63);
-            smem = (size_t)(ch + 2 * (maxb - 1)) * bytes_per_entry + 64;
+            smem = (size_t)(ch + maxb) * bytes_per_entry + 64;
             return (int)ch;
         }
     }
     return -1;
 }
+
+sci::TabRule tab_rule(const sci_ctx *ctx) { return sci::TabRule{ctx->spinors, ctx->n}; }
 
 template <typename TS, typename TC, int NV>
 int launch_doubles(sci_ctx *ctx, const TS *tab, const TC *C, typename AccOf<TS>::type *S, int nvec, int v0)
@@ -523,8 +733,8 @@ int launch_doubles(sci_ctx *ctx, const TS *tab, const TC *C, typename AccOf<TS>:
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return sci_cuda_check(ctx, e, "cudaFuncSetAttribute");
     int64_t blocks = (ctx->e2 + ch - 1) / ch;
-    kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(ctx->e2_idx, ctx->e2_mask, ctx->e2_col, ctx->e2_meta,
-                                                          ctx->e2, ch, tab, C, nvec, v0, S);
+    kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(ctx->e2_idx, ctx->e2_code, ctx->e2_pos, ctx->e2, ch,
+                                                          tab_rule(ctx), tab, C, nvec, v0, S);
     return sci_cuda_check(ctx, cudaGetLastError(), "k_doubles launch");
 }
 
@@ -551,15 +761,15 @@ int launch_doubles_ds(sci_ctx *ctx, const void *C, void *S, int nvec, int v0)
         auto kern = k_doubles_dsz<NV>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return sci_cuda_check(ctx, e, "cudaFuncSetAttribute");
-        kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(ctx->e2_idx, ctx->e2_mask, ctx->e2_col, ctx->e2_meta,
-                                                              ctx->e2, ch, (const float4 *)ctx->tab_ds,
+        kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(ctx->e2_idx, ctx->e2_code, ctx->e2_pos, ctx->e2, ch,
+                                                              tab_rule(ctx), (const float4 *)ctx->tab_ds,
                                                               (const float4 *)ctx->c_ds, nvec, v0, (zdbl *)S);
     } else {
         auto kern = k_doubles_ds<NV>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return sci_cuda_check(ctx, e, "cudaFuncSetAttribute");
-        kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(ctx->e2_idx, ctx->e2_mask, ctx->e2_col, ctx->e2_meta,
-                                                              ctx->e2, ch, (const float2 *)ctx->tab_ds,
+        kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(ctx->e2_idx, ctx->e2_code, ctx->e2_pos, ctx->e2, ch,
+                                                              tab_rule(ctx), (const float2 *)ctx->tab_ds,
                                                               (const float2 *)ctx->c_ds, nvec, v0, (double *)S);
     }
     return sci_cuda_check(ctx, cudaGetLastError(), "k_doubles_ds launch");
@@ -581,6 +791,86 @@ int ds_groups(sci_ctx *ctx, const void *C, void *S, int nvec)
         case 4: rc = launch_doubles_ds<CPLX, 4>(ctx, C, S, nvec, v0); break;
         case 2: rc = launch_doubles_ds<CPLX, 2>(ctx, C, S, nvec, v0); break;
         default: rc = launch_doubles_ds<CPLX, 1>(ctx, C, S, nvec, v0); break;
+        }
+        v0 += g;
+    }
+    return rc;
+}
+
+// FP32-storage doubles (SCI_PREC_F32_STORE_F64_ACC)
+template <int NV>
+int launch_doubles_f32(sci_ctx *ctx, const float *C, double *S, int nvec, int v0)
+{
+    if (ctx->e2 == 0) return SCI_OK;
+    size_t per = NV * sizeof(float) + 8;
+    size_t smem = 0;
+    int ch = choose_rows(ctx->maxb2, per, smem);
+    if (ch < 0) return sci_fail(ctx, SCI_ERR_OVERFLOW, "bucket too large for shared memory");
+    int64_t blocks = (ctx->e2 + ch - 1) / ch;
+    auto kern = k_doubles_f32<NV>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return sci_cuda_check(ctx, e, "cudaFuncSetAttribute");
+    kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(ctx->e2_idx, ctx->e2_code, ctx->e2_pos, ctx->e2, ch,
+                                                          tab_rule(ctx), ctx->tab32, C, nvec, v0, S);
+    return sci_cuda_check(ctx, cudaGetLastError(), "k_doubles_f32 launch");
+}
+
+int f32_groups(sci_ctx *ctx, const float *C, double *S, int nvec)
+{
+    int rc = SCI_OK;
+    for (int v0 = 0; v0 < nvec && rc == SCI_OK;) {
+        int left = nvec - v0;
+        int g = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+        size_t smem_probe = 0;
+        while (g > 1 && choose_rows(ctx->maxb2, g * sizeof(float) + 8, smem_probe) < 0) g >>= 1;
+        switch (g) {
+        case 8: rc = launch_doubles_f32<8>(ctx, C, S, nvec, v0); break;
+        case 4: rc = launch_doubles_f32<4>(ctx, C, S, nvec, v0); break;
+        case 2: rc = launch_doubles_f32<2>(ctx, C, S, nvec, v0); break;
+        default: rc = launch_doubles_f32<1>(ctx, C, S, nvec, v0); break;
+        }
+        v0 += g;
+    }
+    return rc;
+}
+
+// paired-FP32 singles; real coefficients may come in as double or float
+template <bool CPLX, int NV, typename TC = double>
+int launch_singles_ds(sci_ctx *ctx, const void *C, void *S, int nvec, int v0)
+{
+    if (ctx->e1 == 0) return SCI_OK;
+    const int g = grid_for(ctx->e1);
+    if constexpr (CPLX) {
+        k_split_cz<<<grid_for(ctx->M * NV), kThreads, 0, ctx->stream>>>((const zdbl *)C, ctx->M, nvec, v0, NV,
+                                                                        (float4 *)ctx->c_ds);
+        k_singles_dsz<NV><<<g, kThreads, 0, ctx->stream>>>(ctx->e1_idx, ctx->e1_S, ctx->e1_meta, ctx->e1, ctx->norb,
+                                                           ctx->ref, (const float4 *)ctx->fref_ds,
+                                                           (const float4 *)ctx->g_ds, (const float4 *)ctx->c_ds, nvec,
+                                                           v0, (zdbl *)S);
+    } else {
+        k_split_c<TC><<<grid_for(ctx->M * NV), kThreads, 0, ctx->stream>>>((const TC *)C, ctx->M, nvec, v0, NV,
+                                                                           (float2 *)ctx->c_ds);
+        k_singles_ds<NV><<<g, kThreads, 0, ctx->stream>>>(ctx->e1_idx, ctx->e1_S, ctx->e1_meta, ctx->e1, ctx->norb,
+                                                          ctx->ref, (const float2 *)ctx->fref_ds,
+                                                          (const float2 *)ctx->g_ds, (const float2 *)ctx->c_ds, nvec,
+                                                          v0, (double *)S);
+    }
+    return sci_cuda_check(ctx, cudaGetLastError(), "k_singles_ds launch");
+}
+
+template <bool CPLX, typename TC = double>
+int ds_singles_groups(sci_ctx *ctx, const void *C, void *S, int nvec)
+{
+    int rc = SCI_OK;
+    for (int v0 = 0; v0 < nvec && rc == SCI_OK;) {
+        int left = nvec - v0;
+        int g = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+        if (CPLX && g > 4) g = 4;
+        switch (g) {
+        case 8: rc = launch_singles_ds<CPLX, 8, TC>(ctx, C, S, nvec, v0); break;
+        case 4: rc = launch_singles_ds<CPLX, 4, TC>(ctx, C, S, nvec, v0); break;
+        case 2: rc = launch_singles_ds<CPLX, 2, TC>(ctx, C, S, nvec, v0); break;
+        default: rc = launch_singles_ds<CPLX, 1, TC>(ctx, C, S, nvec, v0); break;
         }
         v0 += g;
     }
@@ -636,15 +926,15 @@ int singles_groups(sci_ctx *ctx, const TC *C, typename AccOf<TS>::type *S, int n
 }
 
 // ------------------------------------------------------------------ pair counting
-__global__ void k_count2(const uint64_t *__restrict__ e_mask, const uint64_t *__restrict__ e_meta, int64_t E,
+__global__ void k_count2(const uint32_t *__restrict__ e_code, const uint32_t *__restrict__ e_pos, int64_t E,
                          unsigned long long *out)
 {
     unsigned long long cnt = 0;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t meta = e_meta[p];
-        int64_t bs = p - (int64_t)((meta >> 32) & 0xFFFF), be = bs + (int64_t)(meta >> 48);
-        uint64_t m = e_mask[p];
-        for (int64_t q = bs; q < be; q++) cnt += (e_mask[q] & m) == 0;
+        const uint32_t pos = e_pos[p];
+        const int64_t bs = p - sci::pos_off(pos), be = bs + sci::pos_size(pos);
+        const uint64_t m = sci::code_mask(e_code[p]);
+        for (int64_t q = bs; q < be; q++) cnt += (sci::code_mask(e_code[q]) & m) == 0;
     }
     for (int o = 16; o; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
     if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(out, cnt);
@@ -678,20 +968,20 @@ __device__ __forceinline__ void conn_put(ConnOut o, int64_t r, int64_t c, int d,
     }
 }
 
-__global__ void k_conn2(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_mask,
-                        const uint64_t *__restrict__ e_meta, int64_t E, int64_t rb, int64_t re, ConnOut o)
+__global__ void k_conn2(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_code,
+                        const uint32_t *__restrict__ e_pos, int64_t E, int64_t rb, int64_t re, ConnOut o)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
-        int64_t I = e_idx[p];
+        const int64_t I = e_idx[p];
         if (I < rb || I >= re) continue;
-        uint64_t meta = e_meta[p];
-        int64_t bs = p - (int64_t)((meta >> 32) & 0xFFFF), be = bs + (int64_t)(meta >> 48);
-        uint64_t m = e_mask[p];
-        int par = (meta >> 16) & 1;
+        const uint32_t pos = e_pos[p], code = e_code[p];
+        const int64_t bs = p - sci::pos_off(pos), be = bs + sci::pos_size(pos);
+        const uint64_t m = sci::code_mask(code);
+        const int par = sci::code_par(code);
         for (int64_t q = bs; q < be; q++) {
-            if (e_mask[q] & m) continue;
-            int parq = (e_meta[q] >> 16) & 1;
-            conn_put(o, I, e_idx[q], 2, (par ^ parq) ? -1 : 1);
+            const uint32_t cq = e_code[q];
+            if (sci::code_mask(cq) & m) continue;
+            conn_put(o, I, e_idx[q], 2, (par ^ (int)sci::code_par(cq)) ? -1 : 1);
         }
     }
 }
@@ -713,6 +1003,11 @@ __global__ void k_conn1(const uint32_t *__restrict__ e_idx, const uint32_t *__re
     }
 }
 
+inline void mark(sci_ctx *ctx, int i)
+{
+    if (ctx->profile) cudaEventRecord(ctx->ev[i], ctx->stream);
+}
+
 }  // namespace
 
 #define SCI_CK(call)                                                 \
@@ -720,13 +1015,6 @@ __global__ void k_conn1(const uint32_t *__restrict__ e_idx, const uint32_t *__re
         int _rc = sci_cuda_check(ctx, (call), #call);                \
         if (_rc != SCI_OK) return _rc;                               \
     } while (0)
-
-namespace {
-inline void mark(sci_ctx *ctx, int i)
-{
-    if (ctx->profile) cudaEventRecord(ctx->ev[i], ctx->stream);
-}
-}  // namespace
 
 int sci_launch_sigma(sci_ctx *ctx, const void *C, void *S, int nvec, int prec)
 {
@@ -743,7 +1031,9 @@ int sci_launch_sigma(sci_ctx *ctx, const void *C, void *S, int nvec, int prec)
         rc = prec == SCI_PREC_F64_DS ? ds_groups<true>(ctx, C, S, nvec)
                                      : sigma_groups<zdbl, zdbl>(ctx, (const zdbl *)ctx->tab, Cz, Sz, nvec);
         mark(ctx, 2);
-        if (rc == SCI_OK) rc = singles_groups<zdbl, zdbl>(ctx, Cz, Sz, nvec);
+        if (rc == SCI_OK)
+            rc = prec == SCI_PREC_F64_DS ? ds_singles_groups<true>(ctx, C, S, nvec)
+                                         : singles_groups<zdbl, zdbl>(ctx, Cz, Sz, nvec);
         mark(ctx, 3);
         return rc;
     }
@@ -756,7 +1046,9 @@ int sci_launch_sigma(sci_ctx *ctx, const void *C, void *S, int nvec, int prec)
         rc = prec == SCI_PREC_F64_DS ? ds_groups<false>(ctx, C, S, nvec)
                                      : sigma_groups<double, double>(ctx, (const double *)ctx->tab, Cd, Sd, nvec);
         mark(ctx, 2);
-        if (rc == SCI_OK) rc = singles_groups<double, double>(ctx, Cd, Sd, nvec);
+        if (rc == SCI_OK)
+            rc = prec == SCI_PREC_F64_DS ? ds_singles_groups<false>(ctx, C, S, nvec)
+                                         : singles_groups<double, double>(ctx, Cd, Sd, nvec);
         mark(ctx, 3);
         return rc;
     }
@@ -764,9 +1056,9 @@ int sci_launch_sigma(sci_ctx *ctx, const void *C, void *S, int nvec, int prec)
     k_sigma_init<float, double><<<grid_for(M * nvec), kThreads, 0, st>>>(ctx->hdiag, Cf, Sd, M, nvec);
     SCI_CK(cudaGetLastError());
     mark(ctx, 1);
-    rc = sigma_groups<float, float>(ctx, ctx->tab32, Cf, Sd, nvec);
+    rc = f32_groups(ctx, Cf, Sd, nvec);
     mark(ctx, 2);
-    if (rc == SCI_OK) rc = singles_groups<double, float>(ctx, Cf, Sd, nvec);
+    if (rc == SCI_OK) rc = ds_singles_groups<false, float>(ctx, C, S, nvec);
     mark(ctx, 3);
     return rc;
 }
@@ -777,7 +1069,7 @@ int sci_count_pairs_device(sci_ctx *ctx, int64_t *pairs2, int64_t *pairs1)
     unsigned long long *d = nullptr;
     SCI_CK(cudaMalloc(&d, 16));
     cudaMemsetAsync(d, 0, 16, st);
-    if (ctx->e2 > 0) k_count2<<<grid_for(ctx->e2), kThreads, 0, st>>>(ctx->e2_mask, ctx->e2_meta, ctx->e2, d);
+    if (ctx->e2 > 0) k_count2<<<grid_for(ctx->e2), kThreads, 0, st>>>(ctx->e2_code, ctx->e2_pos, ctx->e2, d);
     if (ctx->e1 > 0) k_count1<<<grid_for(ctx->e1), kThreads, 0, st>>>(ctx->e1_meta, ctx->e1, d + 1);
     unsigned long long h[2] = {0, 0};
     cudaError_t e = cudaGetLastError();
@@ -799,8 +1091,11 @@ int sci_connections_device(sci_ctx *ctx, int64_t row_begin, int64_t row_end, int
     // pass 1: count
     ConnOut o{nullptr, nullptr, nullptr, nullptr, 0, counter};
     cudaMemsetAsync(counter, 0, 8, st);
-    if (ctx->e2 > 0) k_conn2<<<grid_for(ctx->e2), kThreads, 0, st>>>(ctx->e2_idx, ctx->e2_mask, ctx->e2_meta, ctx->e2, row_begin, row_end, o);
-    if (ctx->e1 > 0) k_conn1<<<grid_for(ctx->e1), kThreads, 0, st>>>(ctx->e1_idx, ctx->e1_meta, ctx->e1, row_begin, row_end, o);
+    if (ctx->e2 > 0)
+        k_conn2<<<grid_for(ctx->e2), kThreads, 0, st>>>(ctx->e2_idx, ctx->e2_code, ctx->e2_pos, ctx->e2, row_begin,
+                                                         row_end, o);
+    if (ctx->e1 > 0)
+        k_conn1<<<grid_for(ctx->e1), kThreads, 0, st>>>(ctx->e1_idx, ctx->e1_meta, ctx->e1, row_begin, row_end, o);
     unsigned long long n = 0;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(&n, counter, 8, cudaMemcpyDeviceToHost, st);
@@ -819,8 +1114,11 @@ int sci_connections_device(sci_ctx *ctx, int64_t row_begin, int64_t row_end, int
     o.ph = o.deg + n;
     o.cap = (int64_t)n;
     cudaMemsetAsync(counter, 0, 8, st);
-    if (ctx->e2 > 0) k_conn2<<<grid_for(ctx->e2), kThreads, 0, st>>>(ctx->e2_idx, ctx->e2_mask, ctx->e2_meta, ctx->e2, row_begin, row_end, o);
-    if (ctx->e1 > 0) k_conn1<<<grid_for(ctx->e1), kThreads, 0, st>>>(ctx->e1_idx, ctx->e1_meta, ctx->e1, row_begin, row_end, o);
+    if (ctx->e2 > 0)
+        k_conn2<<<grid_for(ctx->e2), kThreads, 0, st>>>(ctx->e2_idx, ctx->e2_code, ctx->e2_pos, ctx->e2, row_begin,
+                                                         row_end, o);
+    if (ctx->e1 > 0)
+        k_conn1<<<grid_for(ctx->e1), kThreads, 0, st>>>(ctx->e1_idx, ctx->e1_meta, ctx->e1, row_begin, row_end, o);
     std::vector<int64_t> hr(n), hc(n);
     std::vector<int8_t> hd(n), hp(n);
     e = cudaGetLastError();

@@ -132,6 +132,28 @@ def test_sigma_paired_fp32_matches_fp64_tolerance(gpu, name, nvec):
     assert rel_err(S[rows], o.sigma_rows(rows, C)) < TOL
 
 
+@pytest.mark.parametrize("name", ["fci_8o_4a4b", "so_sel_7o", "sel_30o_60k"])
+@pytest.mark.parametrize("nvec", [1, 8])
+def test_sigma_fp32_storage(gpu, name, nvec):
+    """SCI_PREC_F32_STORE_F64_ACC: C and the pair table in FP32, exact products,
+    compensated sums.  Against the FP64 oracle the error is the FP32 rounding of the
+    inputs: bounded here by 2e-6 relative (a few units of 2^-24 times the conditioning of
+    the sums), and it must shrink to the oracle's own value if the inputs are exactly
+    representable in FP32 (checked on C)."""
+    torch = gpu
+    w, o = case(name)
+    H = gpu_ham(w, torch)
+    rng = np.random.default_rng(300 + nvec)
+    C = w.c if nvec == 1 else rng.normal(size=(w.M, nvec))
+    C32 = np.ascontiguousarray(C, dtype=np.float32)
+    S = H.sigma(torch.from_numpy(C32).cuda().reshape(w.M, -1),
+                prec=sci.SCI_PREC_F32_STORE_F64_ACC).cpu().numpy().reshape(w.M, -1)
+    H.sync_status()
+    rows = sample_rows(w, 2000)
+    ref = o.sigma_rows(rows, C32.astype(np.float64))
+    assert rel_err(S[rows], ref) < 2e-6
+
+
 def test_sigma_nvec8_and_repeat(gpu):
     torch = gpu
     w, o = case("sel_30o_60k")
@@ -221,6 +243,32 @@ def test_invalid_inputs_return_codes(gpu):
 
 
 # ------------------------------------------------------------------ Davidson
+def test_davidson_mixed_matches_fp64_selected_space(gpu):
+    """Block Davidson (4 roots) on the 60,000-determinant space: the FP32-storage solver
+    with FP64 refinement reaches the plain FP64 solver's energies (residual 1e-8) to
+    1e-9 Eh, and its returned vectors have exact FP64 residuals below the tolerance."""
+    torch = gpu
+    from paper_2501_18185_gb300.davidson import davidson, davidson_mixed
+
+    w, o = case("sel_30o_60k")
+    H = gpu_ham(w, torch)
+    diag = H.diagonal()
+    hi = lambda X: H.sigma(X.contiguous())  # noqa: E731
+    lo = lambda X: H.sigma(X.to(torch.float32).contiguous(), prec=sci.SCI_PREC_F32_STORE_F64_ACC)  # noqa: E731
+    ref = davidson(hi, diag, nroots=4, tol=1e-8, max_iter=600)
+    mix = davidson_mixed(lo, hi, diag, nroots=4, tol=1e-7)
+    assert ref.converged and mix.converged
+    assert np.abs(mix.energies.cpu().numpy() - ref.energies.cpu().numpy()).max() < 1e-9
+    X = mix.vectors
+    R = hi(X) - X * mix.energies
+    assert float(torch.linalg.vector_norm(R, dim=0).max()) <= 1e-7
+    # the Rayleigh quotient of the first vector against the oracle's sigma on sampled rows
+    rows = sample_rows(w, 500)
+    x0 = X[:, 0].cpu().numpy()
+    s = o.sigma_rows(rows, x0[:, None])[:, 0]
+    assert np.allclose(s, hi(X[:, :1]).cpu().numpy()[rows, 0], rtol=0, atol=1e-11)
+
+
 def test_davidson_fci_8o_matches_dense_eigh(gpu):
     torch = gpu
     from paper_2501_18185_gb300.davidson import davidson
