@@ -169,6 +169,8 @@ def davidson_bench(H, w, nroots=8, tol=1e-6):
            "E_ref": [float(x) for x in e_ref], f"sigma_ms_nvec{nroots}": sig_ms}
     for name, run in (("fp64", lambda: davidson(hi, diag, nroots=nroots, tol=tol, max_iter=600)),
                       ("fp32_refined", lambda: davidson_mixed(lo, hi, diag, nroots=nroots, tol=tol, max_iter=600)),
+                      ("fp32_refined_dsblock", lambda: davidson_mixed(lo, hi, diag, nroots=nroots, tol=tol,
+                                                                      max_iter=600, arith="ds")),
                       ("ds", lambda: davidson(ds, diag, nroots=nroots, tol=tol, max_iter=600))):
         torch.cuda.synchronize()
         t = time.perf_counter()
@@ -179,7 +181,7 @@ def davidson_bench(H, w, nroots=8, tol=1e-6):
         out[name] = {"seconds": dt, "converged": bool(res.converged), "iterations": res.iterations,
                      "sigma_calls": res.sigma_calls, "max_abs_err_Eh": float(err.max()),
                      "errors_Eh": [float(x) for x in err]}
-        if name == "fp32_refined":
+        if name.startswith("fp32_refined"):
             out[name]["sigma_calls_fp32"] = res.sigma_calls_lo
             out[name]["sigma_calls_fp64"] = res.sigma_calls_hi
     out["speedup_fp32_refined_vs_fp64"] = out["fp64"]["seconds"] / out["fp32_refined"]["seconds"]

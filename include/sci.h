@@ -192,6 +192,39 @@ int sci_info(sci_ctx *ctx, int64_t *out, int n);
 int sci_profile(sci_ctx *ctx, int enable);
 int sci_kernel_times(sci_ctx *ctx, float *ms, int n);
 
+/* Block-vector products for the subspace algebra of a block Davidson solver around
+ * sigma (Sec. 2.4, the diagonalisation paragraph: the eigenproblem is solved through
+ * matrix-vector products; the paper leaves the solver's linear algebra unspecified).
+ * Real FP64 data only.  All matrices are device pointers, row-major with the given
+ * leading dimension (in elements; lda >= width).  Asynchronous on the context stream;
+ * they need no Hamiltonian or determinant list.
+ * prec: SCI_PREC_F64 (FP64 FMA) or SCI_PREC_F64_DS (paired FP32 on the FP32 pipes,
+ * inputs carried to 2^-47 relative, sums folded into FP64 every 32 rows).
+ *
+ * sci_bv_gemm_tn: P[k][a] = A^T B for A [M][lda] (first k columns) and B [M][ldb] (first
+ *   a columns).  1 <= a <= 16 and k <= 8 * 256 / pow2(a) (256 for a <= 8, 128 for a <= 16).
+ *   Deterministic (fixed reduction order).  The context holds a partial-sum buffer of
+ *   (CTAs x k x a) doubles, allocated on first use and grown when k x a grows; calls that
+ *   grow it are not graph-capturable.
+ * sci_bv_gemm_nn: C[m][j] = sum_i A1[m][i] S1[i][j] + sum_i A2[m][i] S2[i][j]
+ *   (+ beta C[m][j] when beta != 0) for j < a, S1 [k1][a] and S2 [k2][a] row-major on the
+ *   device, 1 <= a <= 16, k1 + k2 <= 256 (either may be 0 with a NULL operand).  Each row
+ *   is computed from its own inputs only, so C may alias A1 or A2 (same base and stride)
+ *   for an in-place update.  Optional epilogue for residuals:
+ *     colsq (device [a], or NULL): += sum_m C[m][j]^2 of the value before preconditioning
+ *       (FP64 atomics; the order of the additions is not fixed);
+ *     dg (device [M]) and shift (device [a]), or NULL: the stored value becomes
+ *       C[m][j] / (shift[j] - dg[m]) with a denominator below 1e-8 in magnitude replaced
+ *       by 1e-8 (the Davidson diagonal preconditioner), the quotient taken in FP32.
+ * Errors: SCI_ERR_ARG for sizes out of range or NULL operands; SCI_ERR_NOMEM if the
+ * partial-sum buffer cannot be grown. */
+int sci_bv_gemm_tn(sci_ctx *ctx, int64_t M, int k, int a, const double *A, int64_t lda,
+                   const double *B, int64_t ldb, double *P, int prec);
+int sci_bv_gemm_nn(sci_ctx *ctx, int64_t M, int a, const double *A1, int64_t lda1, int k1,
+                   const double *S1, const double *A2, int64_t lda2, int k2, const double *S2,
+                   double beta, double *C, int64_t ldc, const double *dg, const double *shift,
+                   double *colsq, int prec);
+
 /* Wait for the context stream and return the device status word (SCI_OK or the first
  * device-side error code). */
 int sci_sync_status(sci_ctx *ctx);

@@ -147,6 +147,10 @@ struct sci_ctx {
     void *stage_c = nullptr, *stage_s = nullptr;
     size_t stage_bytes = 0;
 
+    // block-vector kernels: per-CTA partials of P = A^T B, grown on demand
+    void *bv_part = nullptr;
+    size_t bv_bytes = 0;
+
     // kernel timing
     int profile = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};

@@ -612,6 +612,7 @@ extern "C" int sci_destroy(sci_ctx *ctx)
     free_ints(ctx);
     if (ctx->stage_c) cudaFree(ctx->stage_c);
     if (ctx->stage_s) cudaFree(ctx->stage_s);
+    if (ctx->bv_part) cudaFree(ctx->bv_part);
     for (auto &e : ctx->ev)
         if (e) cudaEventDestroy(e);
     if (ctx->status) cudaFree(ctx->status);

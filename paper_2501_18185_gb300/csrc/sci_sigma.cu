@@ -29,6 +29,7 @@
 #include <cstdio>
 #include <vector>
 
+#include "sci_ds.cuh"
 #include "sci_internal.cuh"
 
 using sci::zdbl;
@@ -229,48 +230,12 @@ k_doubles(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_cod
 // (Knuth) with e and the rounding error folded into lo.  lo is renormalised into hi every
 // kUnroll pairs.  The row sum leaves the kernel as fp64(hi) + fp64(lo) through the same
 // FP64 atomic add as the FP64 path.
-struct Ds {
-    float hi, lo;
-};
-
-__device__ __forceinline__ void ds_zero(Ds &a) { a.hi = 0.f, a.lo = 0.f; }
-
-// a += t * c
-__device__ __forceinline__ void ds_fma(Ds &a, float2 t, float2 c)
-{
-    const float p = t.x * c.x;
-    float e = fmaf(t.x, c.x, -p);
-    e = fmaf(t.x, c.y, e);
-    e = fmaf(t.y, c.x, e);
-    const float s = a.hi + p;
-    const float bv = s - a.hi;
-    const float err = (a.hi - (s - bv)) + (p - bv);
-    a.lo += err + e;
-    a.hi = s;
-}
-
-__device__ __forceinline__ void ds_renorm(Ds &a)
-{
-    const float s = a.hi + a.lo;
-    a.lo = a.lo - (s - a.hi);
-    a.hi = s;
-}
-
-// float -> double by bit assembly on the integer pipes (the F2F conversion instructions
-// share the narrow FP64 pipe).  Normal numbers, zero, inf and NaN convert exactly; a
-// float denormal (|x| < 1.2e-38) becomes a signed zero.
-__device__ __forceinline__ double f2d_int(float f)
-{
-    const uint32_t u = __float_as_uint(f);
-    const uint32_t e = (u >> 23) & 0xFFu;
-    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
-    unsigned long long bits = sign;
-    if (e == 0xFFu) bits |= (0x7FFull << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
-    else if (e != 0u) bits |= ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
-    return __longlong_as_double((long long)bits);
-}
-
-__device__ __forceinline__ double ds_value(Ds a) { return f2d_int(a.hi) + f2d_int(a.lo); }
+using sci::Ds;
+using sci::ds_fma;
+using sci::ds_renorm;
+using sci::ds_value;
+using sci::ds_zero;
+using sci::f2d_int;
 
 __device__ __forceinline__ float2 ds_split(double x)
 {

@@ -1,21 +1,31 @@
-"""Block Davidson eigensolvers over sigma = H X (torch, FP64 host-side loop).
+"""Block Davidson eigensolvers over sigma = H X.
 
 The paper diagonalises the variational space through matrix-vector products
 sigma_i = H X_i whose elements are recomputed, never stored (Sec. 2.4, the
 diagonalisation paragraph; MetaWave uses the iVI solver there).  These drivers use the
-Davidson method with the diagonal preconditioner (E - H_II)^-1: every product with H
-goes through libsci's sigma kernels; Gram-Schmidt, the subspace matrix, the small
-Hermitian eigenproblem and the residual are FP64 torch operations on the GPU.
+Davidson method with the diagonal preconditioner (E - H_II)^-1.  Every product with H goes
+through libsci's sigma kernels; every tall-skinny product of the subspace algebra
+(projections, Gram matrices, Ritz vectors, residuals) through libsci's block-vector
+kernels (sci_bv_gemm_tn / sci_bv_gemm_nn); the small dense problems (the projected matrix
+G = V^+ H V, its eigenpairs, the Gram eigenproblems of Gram-Schmidt) are solved in FP64
+on the host.
 
-The projected matrix G = V^+ H V is kept and extended by its new rows and columns only
-(two thin products per iteration); a full V^+ W every iteration would dominate the
-iteration time on GB300, whose FP64 rate is 1.2 TFLOP/s.  Restarts are thick: the
-subspace collapses to the lowest `keep` Ritz vectors (2 x nroots by default).
+Search space: V and W = H V live in preallocated [M, max_space] device buffers, so a new
+block is orthonormalised, multiplied and appended in place; G is extended by its new
+rows only.  Restarts are thick: the space collapses to the lowest `keep` Ritz vectors
+(2 x nroots by default), V and W rotated in place.
+
+Gram-Schmidt is block classical Gram-Schmidt, twice (more if the second pass still
+removes a sizeable component), each pass followed by symmetric orthonormalisation of the
+new block from its Gram matrix (directions whose remaining norm is below threshold are
+dropped).  The Gram matrix of the projected block comes from the same pass as the
+projection: for T' = T - V S with S = V^T T, T'^T T' = T^T T - S^T S.
 """
 from __future__ import annotations
 
 from dataclasses import dataclass, field
 
+import numpy as np
 import torch
 
 
@@ -32,109 +42,262 @@ class DavidsonResult:
     sigma_calls_hi: int = 0
 
 
-def _orthonormalize(V: torch.Tensor | None, T: torch.Tensor, drop: float = 1e-10) -> torch.Tensor:
-    """Orthonormalise the columns of T against V and among themselves: two passes of
-    block classical Gram-Schmidt against V, then Cholesky QR of the block (twice),
-    dropping directions that are numerically in span(V)."""
-    for _ in range(2):
-        if V is not None and V.shape[1] > 0:
-            T = T - V @ (V.conj().T @ T)
-    nrm = torch.linalg.vector_norm(T, dim=0)
-    T = T[:, nrm > drop]
-    if T.shape[1] == 0:
-        return T
-    T = T / torch.linalg.vector_norm(T, dim=0)
-    for _ in range(2):
-        G = T.conj().T @ T
-        evals, evecs = torch.linalg.eigh(G)
-        good = evals > 1e-12
-        if not bool(good.all()):
-            T = T @ evecs[:, good]
-            G = T.conj().T @ T
-        L = torch.linalg.cholesky(G)
-        T = torch.linalg.solve_triangular(L.conj().T, T, upper=True, left=False)
-        if V is not None and V.shape[1] > 0:
-            T = T - V @ (V.conj().T @ T)
-    return T
+# ---------------------------------------------------------------- block operations
+class TorchBlockOps:
+    """Tall-skinny products through torch (CPU tensors, or complex data on the GPU)."""
+
+    def tn(self, A, B) -> np.ndarray:
+        """A^+ B as a host array."""
+        return (A.conj().T @ B).cpu().numpy()
+
+    def nn(self, C, a, A1=None, S1=None, A2=None, S2=None, beta=0.0, dg=None, shift=None, colsq=False):
+        """C[:, :a] = A1 S1 + A2 S2 (+ beta C); optional residual norms and preconditioner
+        (see sci_bv_gemm_nn).  Returns the column sums of squares when colsq."""
+        acc = None
+        for A, S in ((A1, S1), (A2, S2)):
+            if A is None or S is None or A.shape[1] == 0:
+                continue
+            t = A @ torch.as_tensor(np.ascontiguousarray(S), dtype=A.dtype, device=A.device)
+            acc = t if acc is None else acc + t
+        if beta != 0.0:
+            acc = acc + beta * C[:, :a]
+        cs = (acc.abs() ** 2).sum(dim=0).real.cpu().numpy() if colsq else None
+        if dg is not None:
+            sh = torch.as_tensor(np.real(shift), dtype=torch.float64, device=C.device)
+            den = sh[None, :] - dg[:, None]
+            den = torch.where(den.abs() < 1e-8, torch.full_like(den, 1e-8), den)
+            acc = acc / den.to(acc.dtype)
+        C[:, :a] = acc
+        return cs
 
 
-def _guess(diag, nvec, dtype, seed: int = 20250130, noise: float = 1e-3):
-    """Unit vectors on the lowest diagonal entries plus a small seeded random part.
-    Without the random part the start block can lie entirely in one symmetry sector of
-    H (e.g. have exactly zero overlap with the ground state), which a symmetry-blind
-    solver would then never leave."""
+class SciBlockOps:
+    """Tall-skinny products through libsci's block-vector kernels (real FP64 CUDA tensors).
+
+    arith "f64": FP64 FMA; "ds": paired FP32 on the FP32 pipes (48-bit significands,
+    FP64 folds).  Work is queued on the torch stream current at construction."""
+
+    def __init__(self, device, arith: str = "f64"):
+        from . import sci
+
+        self.sci = sci
+        self.device = torch.device(device)
+        idx = self.device.index if self.device.index is not None else torch.cuda.current_device()
+        self.ctx = sci.sci_create(idx, torch.cuda.current_stream(self.device).cuda_stream)
+        self.prec = {"f64": sci.SCI_PREC_F64, "ds": sci.SCI_PREC_F64_DS}[arith]
+
+    def __del__(self):
+        try:
+            if getattr(self, "ctx", None) is not None:
+                self.sci.sci_destroy(self.ctx)
+                self.ctx = None
+        except Exception:
+            pass
+
+    @staticmethod
+    def _ld(x):
+        assert x.dtype == torch.float64 and x.is_cuda and (x.shape[1] <= 1 or x.stride(1) == 1)
+        return x.stride(0) if x.shape[0] > 1 else max(1, x.shape[1])
+
+    def _dev(self, S):
+        return torch.as_tensor(np.ascontiguousarray(S, dtype=np.float64), device=self.device)
+
+    def tn(self, A, B) -> np.ndarray:
+        M, k = A.shape
+        a = B.shape[1]
+        P = torch.empty((k, a), dtype=torch.float64, device=self.device)
+        self.sci.sci_bv_gemm_tn(self.ctx, M, k, a, A, self._ld(A), B, self._ld(B), P, self.prec)
+        return P.cpu().numpy()
+
+    def nn(self, C, a, A1=None, S1=None, A2=None, S2=None, beta=0.0, dg=None, shift=None, colsq=False):
+        M = C.shape[0]
+        k1 = 0 if A1 is None else A1.shape[1]
+        k2 = 0 if A2 is None else A2.shape[1]
+        s1 = self._dev(S1) if k1 else None
+        s2 = self._dev(S2) if k2 else None
+        sh = self._dev(np.real(shift)) if dg is not None else None
+        cs = torch.zeros(a, dtype=torch.float64, device=self.device) if colsq else None
+        self.sci.sci_bv_gemm_nn(self.ctx, M, a, A1, self._ld(A1) if k1 else 1, k1, s1, A2, self._ld(A2) if k2 else 1, k2,
+                                s2, beta, C, self._ld(C), dg, sh, cs, self.prec)
+        return cs.cpu().numpy() if colsq else None
+
+
+def default_ops(diag: torch.Tensor, dtype, arith: str = "f64"):
+    """libsci block kernels for real data on the GPU, torch otherwise."""
+    if diag.is_cuda and dtype == torch.float64:
+        return SciBlockOps(diag.device, arith)
+    return TorchBlockOps()
+
+
+# ---------------------------------------------------------------- search space
+class _Space:
+    """V, W = H V in [M, cap] buffers; G = V^+ H V on the host; ex marks the columns of W
+    that come from the FP64 product (mixed solver)."""
+
+    def __init__(self, ops, M, cap, dtype, device):
+        self.ops = ops
+        self.V = torch.zeros((M, cap), dtype=dtype, device=device)
+        self.W = torch.zeros((M, cap), dtype=dtype, device=device)
+        self.k = 0
+        self.G = np.zeros((0, 0), dtype=np.complex128 if dtype.is_complex else np.float64)
+        self.ex = np.zeros(0, dtype=bool)
+
+    def orthonormalize_new(self, a: int) -> int:
+        """Orthonormalise V[:, k:k+a] against V[:, :k] and among themselves, in place.
+        Returns the number of directions kept (packed to the front of the block)."""
+        V, k, ops = self.V, self.k, self.ops
+        for p in range(4):
+            if a == 0:
+                return 0
+            P = ops.tn(V[:, :k + a], V[:, k:k + a])
+            S, Gm = P[:k], P[k:]
+            Gm = 0.5 * (Gm + Gm.conj().T)
+            d = np.sqrt(np.maximum(np.real(np.diag(Gm)), 1e-300))
+            Gp = Gm - S.conj().T @ S
+            Gn = Gp / d[:, None] / d[None, :]
+            lam, U = np.linalg.eigh(0.5 * (Gn + Gn.conj().T))
+            keep = lam > (1e-12 if p == 0 else 1e-10)
+            Z = (U[:, keep] / np.sqrt(lam[keep])[None, :]) / d[:, None]
+            if Z.shape[1] == 0:
+                return 0
+            ops.nn(V[:, k:], Z.shape[1], A1=V[:, :k] if k else None, S1=-(S @ Z) if k else None,
+                   A2=V[:, k:k + a], S2=Z)
+            a = Z.shape[1]
+            # stop once a pass after the first removed only a rounding-level component
+            if p >= 1 and (k == 0 or np.abs(S).max() < 1e-10 * d.max()) and np.abs(lam[keep] - 1).max(initial=0) < 1e-8:
+                break
+        return a
+
+    def append(self, a: int, WT, exact: bool, mixed: bool):
+        """W[:, k:k+a] = WT (= H V[:, k:k+a]); extend G by the new rows and columns."""
+        V, W, k, ops = self.V, self.W, self.k, self.ops
+        W[:, k:k + a].copy_(WT)
+        P1 = ops.tn(V[:, :k + a], W[:, k:k + a])            # v_i^+ (H t_j)
+        if mixed:
+            P2 = ops.tn(W[:, :k + a], V[:, k:k + a])        # (H v_i)^+ t_j
+            B = np.where(self.ex[:, None], P2[:k], 0.5 * (P1[:k] + P2[:k])) if not exact else P1[:k]
+            C = 0.5 * (P1[k:] + P2[k:]) if not exact else P1[k:]
+        else:
+            B, C = P1[:k], P1[k:]
+        C = 0.5 * (C + C.conj().T)
+        G = np.zeros((k + a, k + a), dtype=self.G.dtype)
+        G[:k, :k], G[:k, k:], G[k:, :k], G[k:, k:] = self.G, B, B.conj().T, C
+        self.G = G
+        self.ex = np.concatenate([self.ex, np.full(a, exact)])
+        self.k = k + a
+
+    def rotate(self, Yk: np.ndarray, with_w: bool = True):
+        """V <- V Yk (and W <- W Yk) in place (columns of Yk orthonormal)."""
+        k, m = self.k, Yk.shape[1]
+        self.ops.nn(self.V, m, A1=self.V[:, :k], S1=Yk)
+        if with_w:
+            self.ops.nn(self.W, m, A1=self.W[:, :k], S1=Yk)
+        self.ex = np.full(m, bool(self.ex.all()))
+        self.k = m
+
+    def residual(self, Y, theta, diag):
+        """Preconditioned residuals (H x - theta x) / (theta - H_II) of the Ritz vectors
+        x = V Y, written to V[:, k:k+r]; returns the residual 2-norms."""
+        k, r = self.k, Y.shape[1]
+        cs = self.ops.nn(self.V[:, k:], r, A1=self.W[:, :k], S1=Y, A2=self.V[:, :k], S2=-(Y * theta[None, :]),
+                         dg=diag, shift=theta, colsq=True)
+        return np.sqrt(np.maximum(cs, 0.0))
+
+    def ritz_vectors(self, Y):
+        X = torch.empty((self.V.shape[0], Y.shape[1]), dtype=self.V.dtype, device=self.V.device)
+        self.ops.nn(X, Y.shape[1], A1=self.V[:, :self.k], S1=Y)
+        return X
+
+
+def _guess_block(sp: _Space, diag, nvec, seed: int = 20250130, noise: float = 1e-3) -> int:
+    """Unit vectors on the lowest diagonal entries plus a small seeded random part, into
+    V[:, :nvec].  Without the random part the start block can lie entirely in one symmetry
+    sector of H (e.g. have exactly zero overlap with the ground state), which a
+    symmetry-blind solver would then never leave."""
     M = diag.shape[0]
     k = min(M, nvec)
     idx = torch.argsort(diag)[:k]
     g = torch.Generator(device="cpu").manual_seed(seed)
-    V = noise * torch.randn((M, k), generator=g, dtype=torch.float64).to(diag.device).to(dtype) / (M ** 0.5)
-    V[idx, torch.arange(k, device=diag.device)] += 1.0
-    return _orthonormalize(None, V)
+    B = noise * torch.randn((M, k), generator=g, dtype=torch.float64) / (M ** 0.5)
+    sp.V[:, :k].copy_(B.to(sp.V.device).to(sp.V.dtype))
+    sp.V[idx, torch.arange(k, device=sp.V.device)] += 1.0
+    return sp.orthonormalize_new(k)
 
 
-def _corrections(R, theta, diag, active, dtype):
-    T = []
-    for j in active:
-        den = theta[j] - diag
-        den = torch.where(den.abs() < 1e-8, torch.full_like(den, 1e-8), den)
-        T.append(R[:, j] / den.to(dtype))
-    return torch.stack(T, dim=1)
+def _start(sigma, diag, nroots, max_space, keep, guess, dtype, ops, arith):
+    M = diag.shape[0]
+    keep = min(M, keep or 2 * nroots)
+    max_space = min(M, max_space or max(12 * nroots, keep + 2 * nroots, 24))
+    ops = ops or default_ops(diag, dtype, arith)
+    sp = _Space(ops, M, max_space + 2 * nroots, dtype, diag.device)
+    if guess is None:
+        a = _guess_block(sp, diag, max(keep, 8))
+    else:
+        a = guess.shape[1]
+        sp.V[:, :a].copy_(guess.to(dtype))
+        a = sp.orthonormalize_new(a)
+    return sp, a, keep, max_space
 
 
-def _herm(G):
-    return 0.5 * (G + G.conj().T)
+def _ritz(sp: _Space, nroots):
+    evals, evecs = np.linalg.eigh(sp.G)
+    return evals, evecs, evals[:nroots].real.copy(), evecs[:, :nroots]
 
 
 def davidson(sigma, diag: torch.Tensor, nroots: int = 1, tol: float = 1e-9, max_iter: int = 300,
              max_space: int | None = None, keep: int | None = None, guess: torch.Tensor | None = None,
-             dtype=torch.float64) -> DavidsonResult:
+             dtype=torch.float64, ops=None, arith: str = "f64") -> DavidsonResult:
     """Lowest `nroots` eigenpairs of H.
 
     sigma(X [M,k]) -> H X (same dtype); diag: H_II (float64, [M]).  Converged when every
-    root's residual 2-norm ||H x - E x|| <= tol.
+    root's residual 2-norm ||H x - E x|| <= tol.  ops: block-product backend (default:
+    libsci block kernels for real CUDA data, arithmetic `arith`).
     """
-    M = diag.shape[0]
-    keep = min(M, keep or 2 * nroots)
-    max_space = min(M, max_space or max(12 * nroots, keep + 2 * nroots, 24))
-    # at least 8 start vectors
-    V = _guess(diag, max(keep, 8), dtype) if guess is None else _orthonormalize(None, guess.to(dtype))
-    W = sigma(V)
-    G = _herm(V.conj().T @ W)
-    calls = 1
+    sp, a, keep, max_space = _start(sigma, diag, nroots, max_space, keep, guess, dtype, ops, arith)
+    calls = 0
     hist = []
-    theta = X = rn = None
+    theta = rn = Y = None
     for it in range(1, max_iter + 1):
-        evals, evecs = torch.linalg.eigh(G)
-        theta = evals[:nroots].real.to(torch.float64)
-        Y = evecs[:, :nroots]
-        X = V @ Y
-        R = W @ Y - X * theta.to(dtype)
-        rn = torch.linalg.vector_norm(R, dim=0).real
-        hist.append((it, theta.clone().cpu(), rn.clone().cpu()))
-        if bool((rn <= tol).all()):
-            return DavidsonResult(theta, X, rn, it, calls, True, hist, 0, calls)
-        active = [j for j in range(nroots) if rn[j] > tol]
-        T = _corrections(R, theta, diag, active, dtype)
-        if V.shape[1] + T.shape[1] > max_space:
-            Yk = evecs[:, :min(keep, V.shape[1])]
-            V, W = V @ Yk, W @ Yk
-            G = torch.diag(evals[:Yk.shape[1]]).to(dtype)
-        T = _orthonormalize(V, T)
-        if T.shape[1] == 0:
+        if a == 0:
             break
-        WT = sigma(T)
+        WT = sigma(sp.V[:, sp.k:sp.k + a].contiguous())
         calls += 1
-        B = V.conj().T @ WT                       # old x new block
-        C = _herm(T.conj().T @ WT)                # new x new block
-        G = torch.cat([torch.cat([G, B], dim=1), torch.cat([B.conj().T, C], dim=1)], dim=0)
-        V = torch.cat([V, T], dim=1)
-        W = torch.cat([W, WT], dim=1)
-    return DavidsonResult(theta, X, rn, max_iter, calls, False, hist, 0, calls)
+        sp.append(a, WT, True, False)
+        evals, evecs, theta, Y = _ritz(sp, nroots)
+        rn = sp.residual(Y, theta, diag)
+        hist.append((it, theta.copy(), rn.copy()))
+        if bool((rn <= tol).all()):
+            return _result(sp, theta, Y, rn, it, calls, True, hist, 0, calls)
+        active = np.nonzero(rn > tol)[0]
+        if sp.k + len(active) > max_space:
+            old_k = sp.k
+            sp.rotate(evecs[:, :min(keep, sp.k)])
+            sp.G = np.diag(evals[:sp.k]).astype(sp.G.dtype)
+            # the Ritz vectors and their residuals are unchanged by the rotation
+            sp.V[:, sp.k:sp.k + nroots] = sp.V[:, old_k:old_k + nroots].clone()
+        _pack(sp, nroots, active)
+        a = sp.orthonormalize_new(len(active))
+    return _result(sp, theta, Y, rn, max_iter, calls, False, hist, 0, calls)
+
+
+def _pack(sp: _Space, nroots, active):
+    """Move the preconditioned residuals of the active roots to the front of the block."""
+    k = sp.k
+    if len(active) < nroots:
+        sp.V[:, k:k + len(active)] = sp.V[:, k + torch.as_tensor(active, device=sp.V.device)]
+
+
+def _result(sp, theta, Y, rn, it, calls, conv, hist, lo, hi):
+    X = sp.ritz_vectors(Y) if Y is not None else None
+    dev = sp.V.device
+    return DavidsonResult(torch.as_tensor(theta, device=dev), X, torch.as_tensor(rn, device=dev), it, calls, conv, hist,
+                          lo, hi)
 
 
 def davidson_mixed(sigma_lo, sigma_hi, diag: torch.Tensor, nroots: int = 1, tol: float = 1e-6,
                    max_iter: int = 400, max_space: int | None = None, keep: int | None = None,
-                   guess: torch.Tensor | None = None, dtype=torch.float64) -> DavidsonResult:
+                   guess: torch.Tensor | None = None, dtype=torch.float64, ops=None,
+                   arith: str = "f64") -> DavidsonResult:
     """Davidson with low-precision products for the correction vectors and FP64 refinement.
 
     sigma_lo(X) -> H X from the FP32-storage sigma (C rounded to FP32, exact products,
@@ -151,37 +314,32 @@ def davidson_mixed(sigma_lo, sigma_hi, diag: torch.Tensor, nroots: int = 1, tol:
     residual.  FP64 is kept for the Gram-Schmidt, the subspace matrix, the Rayleigh
     quotient and the final energies.
     """
-    M = diag.shape[0]
-    dev = diag.device
-    keep = min(M, keep or 2 * nroots)
-    max_space = min(M, max_space or max(12 * nroots, keep + 2 * nroots, 24))
-    V = _guess(diag, max(keep, 8), dtype) if guess is None else _orthonormalize(None, guess.to(dtype))
-    W = sigma_lo(V)
-    G = _herm(0.5 * (V.conj().T @ W + W.conj().T @ V))
-    ex = torch.zeros(V.shape[1], dtype=torch.bool, device=dev)   # columns of W from sigma_hi
-    calls_lo, calls_hi = 1, 0
+    sp, a, keep, max_space = _start(sigma_lo, diag, nroots, max_space, keep, guess, dtype, ops, arith)
+    calls_lo, calls_hi = 0, 0
     best_est, stall = None, 0
     hist = []
-    theta = X = rn = None
-
-    def refine(Vn):
-        nonlocal calls_hi
-        Wn = sigma_hi(Vn)
-        calls_hi += 1
-        return Vn, Wn, _herm(Vn.conj().T @ Wn), torch.ones(Vn.shape[1], dtype=torch.bool, device=dev)
-
+    theta = rn = Y = None
+    exact_next = False
     for it in range(1, max_iter + 1):
-        evals, evecs = torch.linalg.eigh(G)
-        theta = evals[:nroots].real.to(torch.float64)
-        Y = evecs[:, :nroots]
-        X = V @ Y
-        R = W @ Y - X * theta.to(dtype)
-        rn = torch.linalg.vector_norm(R, dim=0).real
+        if a == 0:
+            break
+        X = sp.V[:, sp.k:sp.k + a].contiguous()
+        if exact_next:
+            WT = sigma_hi(X)
+            calls_hi += 1
+        else:
+            WT = sigma_lo(X)
+            calls_lo += 1
+        sp.append(a, WT, exact_next, True)
+        exact_next = False
+        evals, evecs, theta, Y = _ritz(sp, nroots)
+        rn = sp.residual(Y, theta, diag)
         rmax = float(rn.max())
-        exact = bool(ex.all())
-        hist.append((it, theta.clone().cpu(), rn.clone().cpu(), exact))
+        exact = bool(sp.ex.all())
+        hist.append((it, theta.copy(), rn.copy(), exact))
         if exact and rmax <= tol:
-            return DavidsonResult(theta, X, rn, it, calls_lo + calls_hi, True, hist, calls_lo, calls_hi)
+            return _result(sp, theta, Y, rn, it, calls_lo + calls_hi, True, hist, calls_lo, calls_hi)
+        refine = False
         if exact:
             best_est, stall = rmax, 0
         else:
@@ -189,31 +347,20 @@ def davidson_mixed(sigma_lo, sigma_hi, diag: torch.Tensor, nroots: int = 1, tol:
                 best_est, stall = rmax, 0
             else:
                 stall += 1
-            if rmax <= tol or stall >= 6:
-                V, W, G, ex = refine(V @ evecs[:, :min(keep, V.shape[1])])
-                best_est, stall = None, 0
-                continue
-        active = [j for j in range(nroots) if rn[j] > tol]
-        T = _corrections(R, theta, diag, active, dtype)
-        if V.shape[1] + T.shape[1] > max_space:
-            # a full space collapses with FP64 products: rotating the stored W would mix
-            # the FP32 error into the exact block of the kept Ritz vectors
-            V, W, G, ex = refine(V @ evecs[:, :min(keep, V.shape[1])])
+            refine = rmax <= tol or stall >= 6
+        active = np.nonzero(rn > tol)[0]
+        # a full space also collapses with FP64 products: rotating the stored W would mix
+        # the FP32 error into the exact block of the kept Ritz vectors
+        if refine or sp.k + len(active) > max_space:
+            m = min(keep, sp.k)
+            sp.rotate(evecs[:, :m], with_w=False)
+            # the kept Ritz vectors become the next block, multiplied in FP64
+            sp.k, a = 0, m
+            sp.G = sp.G[:0, :0]
+            sp.ex = sp.ex[:0]
+            exact_next = True
             best_est, stall = None, 0
             continue
-        T = _orthonormalize(V, T)
-        if T.shape[1] == 0:
-            V, W, G, ex = refine(V @ evecs[:, :min(keep, V.shape[1])])
-            continue
-        WT = sigma_lo(T)
-        calls_lo += 1
-        # old x new block: exact side when the old column's product is exact
-        B1 = V.conj().T @ WT                      # v_i^+ (H_lo t_j)
-        B2 = W.conj().T @ T                       # (H v_i)^+ t_j
-        B = torch.where(ex[:, None], B2, 0.5 * (B1 + B2))
-        C = _herm(0.5 * (T.conj().T @ WT + WT.conj().T @ T))
-        G = torch.cat([torch.cat([G, B], dim=1), torch.cat([B.conj().T, C], dim=1)], dim=0)
-        V = torch.cat([V, T], dim=1)
-        W = torch.cat([W, WT], dim=1)
-        ex = torch.cat([ex, torch.zeros(T.shape[1], dtype=torch.bool, device=dev)])
-    return DavidsonResult(theta, X, rn, max_iter, calls_lo + calls_hi, False, hist, calls_lo, calls_hi)
+        _pack(sp, nroots, active)
+        a = sp.orthonormalize_new(len(active))
+    return _result(sp, theta, Y, rn, max_iter, calls_lo + calls_hi, False, hist, calls_lo, calls_hi)

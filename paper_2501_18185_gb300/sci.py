@@ -47,6 +47,9 @@ SIGNATURES = {
     "sci_info": (_i32, [_vp, _vp, _i32]),
     "sci_profile": (_i32, [_vp, _i32]),
     "sci_kernel_times": (_i32, [_vp, _vp, _i32]),
+    "sci_bv_gemm_tn": (_i32, [_vp, _i64, _i32, _i32, _vp, _i64, _vp, _i64, _vp, _i32]),
+    "sci_bv_gemm_nn": (_i32, [_vp, _i64, _i32, _vp, _i64, _i32, _vp, _vp, _i64, _i32, _vp, ctypes.c_double, _vp,
+                              _i64, _vp, _vp, _vp, _i32]),
     "sci_sync_status": (_i32, [_vp]),
     "sci_last_error": (ctypes.c_char_p, [_vp]),
 }
@@ -184,6 +187,15 @@ def sci_kernel_times(ctx) -> list:
     ms = np.zeros(3, dtype=np.float32)
     _check(ctx, load().sci_kernel_times(ctx, _p(ms), 3))
     return [float(x) for x in ms]
+
+
+def sci_bv_gemm_tn(ctx, M, k, a, A, lda, B, ldb, P, prec):
+    return _check(ctx, load().sci_bv_gemm_tn(ctx, M, k, a, _p(A), lda, _p(B), ldb, _p(P), prec))
+
+
+def sci_bv_gemm_nn(ctx, M, a, A1, lda1, k1, S1, A2, lda2, k2, S2, beta, C, ldc, dg, shift, colsq, prec):
+    return _check(ctx, load().sci_bv_gemm_nn(ctx, M, a, _p(A1), lda1, k1, _p(S1), _p(A2), lda2, k2, _p(S2), float(beta),
+                                             _p(C), ldc, _p(dg), _p(shift), _p(colsq), prec))
 
 
 def sci_sync_status(ctx):
