@@ -173,12 +173,14 @@ class _Space:
         V, W, k, ops = self.V, self.W, self.k, self.ops
         W[:, k:k + a].copy_(WT)
         P1 = ops.tn(V[:, :k + a], W[:, k:k + a])            # v_i^+ (H t_j)
-        if mixed:
-            P2 = ops.tn(W[:, :k + a], V[:, k:k + a])        # (H v_i)^+ t_j
-            B = np.where(self.ex[:, None], P2[:k], 0.5 * (P1[:k] + P2[:k])) if not exact else P1[:k]
-            C = 0.5 * (P1[k:] + P2[k:]) if not exact else P1[k:]
-        else:
-            B, C = P1[:k], P1[k:]
+        B, C = P1[:k].copy(), P1[k:]
+        if mixed and not exact:
+            # rows of columns with an exact product take the exact side (H v_i)^+ t_j; the
+            # exact columns are a prefix (the refined block), so one narrow product serves
+            nex = int(self.ex.sum())
+            assert self.ex[:nex].all()
+            if nex:
+                B[:nex] = ops.tn(W[:, :nex], V[:, k:k + a])
         C = 0.5 * (C + C.conj().T)
         G = np.zeros((k + a, k + a), dtype=self.G.dtype)
         G[:k, :k], G[:k, k:], G[k:, :k], G[k:, k:] = self.G, B, B.conj().T, C

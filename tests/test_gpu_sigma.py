@@ -167,6 +167,28 @@ def test_sigma_nvec8_and_repeat(gpu):
     assert rel_err(S1[rows], ref) < TOL and rel_err(S2, S1) < 1e-14
 
 
+@pytest.mark.parametrize("name,nvec", [("sel_30o_60k", 11), ("sel_30o_60k", 16), ("sel_64s_120k", 5)])
+def test_sigma_wide_blocks_all_precisions(gpu, name, nvec):
+    """Blocks wider than one vector group (8 real / 4 complex vectors per kernel pass),
+    with a ragged last group: FP64 and paired FP32 against the oracle on sampled rows,
+    FP32 storage against the oracle run on the FP32-rounded vectors."""
+    torch = gpu
+    w, o = case(name)
+    H = gpu_ham(w, torch)
+    rng = np.random.default_rng(400 + nvec)
+    C = rng.normal(size=(w.M, nvec)) + (1j * rng.normal(size=(w.M, nvec)) if w.mode == "spinors" else 0)
+    Ct = torch.from_numpy(C).cuda()
+    rows = sample_rows(w, 400)
+    ref = o.sigma_rows(rows, C)
+    assert rel_err(H.sigma(Ct).cpu().numpy()[rows], ref) < TOL
+    assert rel_err(H.sigma(Ct, prec=sci.SCI_PREC_F64_DS).cpu().numpy()[rows], ref) < TOL
+    if w.mode != "spinors":
+        C32 = np.ascontiguousarray(C, dtype=np.float32)
+        ref32 = o.sigma_rows(rows, C32.astype(np.float64))
+        S32 = H.sigma(torch.from_numpy(C32).cuda(), prec=sci.SCI_PREC_F32_STORE_F64_ACC).cpu().numpy()
+        assert rel_err(S32[rows], ref32) < 2e-6
+
+
 def test_keys_on_device_and_stream(gpu):
     torch = gpu
     w, o = case("so_sel_7o")
