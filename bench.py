@@ -188,6 +188,46 @@ def davidson_bench(H, w, nroots=8, tol=1e-6):
     return out
 
 
+def rdm_bench(H, w, nvec=4, reps=3):
+    """Density matrices and the autograd energy on the bench space with `nvec` vectors
+    (seeded normal coefficients, normalised; the cost does not depend on the values):
+    CUDA-event milliseconds of sci_rdm12 without and with the 2-RDM, and of one forward +
+    backward of the Rayleigh-quotient energy with respect to h, the Cholesky factors and
+    C (mean of `reps` after one warm-up)."""
+    import torch
+
+    from paper_2501_18185_gb300.autograd import rayleigh_energy
+
+    g = torch.Generator(device="cpu").manual_seed(5)
+    C = torch.randn((H.M, nvec), generator=g, dtype=torch.float64).to(H.device)
+    C /= torch.linalg.vector_norm(C, dim=0)
+    h = torch.from_numpy(w.ints.h.copy()).to(H.device)
+    L = torch.from_numpy(w.ints.chol.copy()).to(H.device)
+
+    def ev_ms(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def fwd_bwd():
+        hh, LL, CC = h.clone().requires_grad_(True), L.clone().requires_grad_(True), C.clone().requires_grad_(True)
+        rayleigh_energy(hh, LL, CC, H).sum().backward()
+
+    out = {"nvec": nvec, "norb": H.norb,
+           "rdm1_ms": ev_ms(lambda: H.rdm12(C, rdm2=False)),
+           "rdm12_ms": ev_ms(lambda: H.rdm12(C)),
+           "energy_forward_backward_ms": ev_ms(fwd_bwd)}
+    # the energy path re-uploaded the same integrals: leave the context as it was
+    H.set_integrals(w.mode, w.ints.h, chol=w.ints.chol)
+    return out
+
+
 def run_reference(args, rank, world):
     """--impl reference: the CPU oracle on bounded samples of the same workload."""
     if rank != 0:
@@ -231,7 +271,7 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-davidson", action="store_true",
-                    help="skip the FP64 vs FP32-refined 8-root Davidson timing")
+                    help="skip the 8-root Davidson timing and the density-matrix timing")
     ap.add_argument("--prec", default="f64", choices=["f64", "ds"],
                     help="f64: FP64 FMA path; ds: paired-FP32 products/sums (FP64 tolerance)")
     args = ap.parse_args()
@@ -370,8 +410,10 @@ def main():
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(w)
     dav = None
+    rdm = None
     if not args.no_davidson and world == 1 and not w.ints.complex_:
         dav = davidson_bench(H, w)
+        rdm = rdm_bench(H, w)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c128" if w.ints.complex_ else "f64", "data": "synthetic",
@@ -381,7 +423,7 @@ def main():
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
             "gpu_launches": args.steps * (1 + 2 * ((nv + 7) // 8 if not w.ints.complex_ else (nv + 3) // 4)),
             "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "prec": args.prec,
-            "other_prec": variant, "davidson": dav}
+            "other_prec": variant, "davidson": dav, "rdm": rdm}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

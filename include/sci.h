@@ -192,6 +192,28 @@ int sci_info(sci_ctx *ctx, int64_t *out, int n);
 int sci_profile(sci_ctx *ctx, int enable);
 int sci_kernel_times(sci_ctx *ctx, float *ms, int n);
 
+/* One- and two-particle reduced density matrices (Sec. 3.4), summed over the columns of
+ * C with weights:
+ *   rdm1[p][q]       = sum_k w_k <c_k| a+_p a_q |c_k>
+ *   rdm2[p][q][r][s] = sum_k w_k <c_k| a+_p a+_r a_s a_q |c_k>
+ * over the norb = 2n spin-orbitals (spin-orbital mode, bit order of the keys) or the n
+ * spinors, unnormalised: for a normalised c the energy of Eq. Hamiltonian is
+ * sum h_pq rdm1_pq + 1/2 sum (pq|rs) rdm2_pqrs (spin-orbital integrals).
+ *   C: device, [M][nvec], double (real mode) or complex128 (complex mode), nvec >= 1.
+ *   weights: HOST, nvec doubles, or NULL for all ones.
+ *   rdm1: device, [norb][norb] scalars, overwritten.
+ *   rdm2: device, [norb]^4 scalars, overwritten; or NULL to skip the double-excitation
+ *     walk (then only rdm1 is formed).
+ * Connections are recomputed from the tables built by sci_set_determinants(); the context
+ * allocates a scratch buffer (about norb^3 + the pair-table size scalars) on first use and
+ * grows it when needed, so calls that grow it are not graph-capturable.  Queued on the
+ * context stream (the weights are copied synchronously).  The summation order of the
+ * device atomics is not fixed: results agree with a fixed-order sum to rounding.
+ * Errors: SCI_ERR_STATE before integrals and determinants, SCI_ERR_ARG for NULL C/rdm1 or
+ * nvec < 1, SCI_ERR_OVERFLOW if the largest (N-2) bucket does not fit the staging window,
+ * SCI_ERR_NOMEM. */
+int sci_rdm12(sci_ctx *ctx, const void *C, int nvec, const double *weights, void *rdm1, void *rdm2);
+
 /* Block-vector products for the subspace algebra of a block Davidson solver around
  * sigma (Sec. 2.4, the diagonalisation paragraph: the eigenproblem is solved through
  * matrix-vector products; the paper leaves the solver's linear algebra unspecified).

@@ -1,0 +1,105 @@
+"""Differentiable Rayleigh quotients E_k = c_k^T H c_k / c_k^T c_k through libsci.
+
+H is the Hamiltonian of Eq. Hamiltonian (Sec. 2.1) on the determinant list held by a
+`sci.Hamiltonian`, built from h and either the dense (pq|rs) or Cholesky factors L^P with
+(pq|rs) = sum_P L^P_pq L^P_rs (real spin-orbital mode).  Forward: one sigma = H C.
+Backward, hand-written (the connections are recomputed by libsci's density-matrix walk,
+never stored), with G_k = grad_output_k / (c_k^T c_k) and the spin-summed density matrices
+gamma (n x n) and Gamma (n^4) of the weighted ensemble sum_k G_k |c_k><c_k|:
+    dL/dh_pq        = gamma_pq                     (gamma_pq = sum_s g1[p s, q s])
+    dL/d(pq|rs)     = 1/2 Gamma_pqrs               (Gamma_pqrs = sum_st g2[p s, q s, r t, s t])
+    dL/dL^P_pq      = sum_rs Gamma_pqrs L^P_rs
+    dL/dc_k         = 2 G_k (sigma_k - E_k c_k)
+The factor 1/2 on (pq|rs) is that of Eq. Hamiltonian: E = sum h g1 + 1/2 sum (pq|rs) g2.
+h, (pq|rs) and L^P are treated as free entries (no symmetrisation of the gradient); a
+perturbation that keeps H Hermitian moves a whole symmetry orbit and picks up the sum of
+the orbit's entries.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+
+def spin_sum_rdm(g1: torch.Tensor, g2: torch.Tensor | None, n: int):
+    """Spin-orbital (2n) -> spatial (n) density matrices: gamma[p,q] = sum_s g1[ps, qs],
+    Gamma[p,q,r,s] = sum_{s,t} g2[ps, qs, rt, st] (bit p < n is alpha p, bit n+p beta p)."""
+    g = g1.reshape(2, n, 2, n)
+    gamma = g[0, :, 0, :] + g[1, :, 1, :]
+    if g2 is None:
+        return gamma, None
+    G = g2.reshape(2, n, 2, n, 2, n, 2, n)
+    Gamma = torch.zeros((n, n, n, n), dtype=g2.dtype, device=g2.device)
+    for s in range(2):
+        for t in range(2):
+            Gamma += G[s, :, s, :, t, :, t, :]
+    return gamma, Gamma
+
+
+class _Energy(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, h, L, C, ham, kind):
+        n = h.shape[0]
+        hn = h.detach().cpu().numpy()
+        Ln = L.detach().cpu().numpy()
+        if kind == "chol":
+            ham.set_integrals("spin_orbitals", hn, chol=Ln)
+        else:
+            ham.set_integrals("spin_orbitals", hn, eri=Ln)
+        Cd = C.detach().contiguous()
+        S = ham.sigma(Cd)
+        den = (Cd * Cd).sum(dim=0)
+        E = (Cd * S).sum(dim=0) / den
+        ctx.save_for_backward(L, Cd, S, E, den)
+        ctx.ham, ctx.kind, ctx.n = ham, kind, n
+        return E
+
+    @staticmethod
+    def backward(ctx, gE):
+        L, C, S, E, den = ctx.saved_tensors
+        ham, kind, n = ctx.ham, ctx.kind, ctx.n
+        G = (gE / den).detach()
+        need_h, need_L, need_C = ctx.needs_input_grad[0], ctx.needs_input_grad[1], ctx.needs_input_grad[2]
+        gh = gL = gC = None
+        if need_h or need_L:
+            g1, g2 = ham.rdm12(C, weights=G.cpu().numpy(), rdm2=need_L)
+            gamma, Gamma = spin_sum_rdm(g1, g2, n)
+            if need_h:
+                gh = gamma.to(L.device)
+            if need_L:
+                Gamma = Gamma.to(L.device)
+                if kind == "chol":
+                    naux = L.shape[0]
+                    gL = (Gamma.reshape(n * n, n * n) @ L.reshape(naux, n * n).T).T.reshape(naux, n, n)
+                else:
+                    gL = 0.5 * Gamma
+        if need_C:
+            gC = 2.0 * (S - C * E) * G
+        return gh, gL, gC, None, None
+
+
+def rayleigh_energy(h: torch.Tensor, L: torch.Tensor, C: torch.Tensor, ham, kind: str = "chol") -> torch.Tensor:
+    """E_k = c_k^T H c_k / c_k^T c_k for the columns of C ([M, nroots], CUDA float64).
+
+    h: [n, n]; L: Cholesky factors [naux, n, n] (kind "chol") or the dense (pq|rs) [n]^4
+    (kind "eri").  `ham` is a sci.Hamiltonian holding the determinant list; its integrals
+    are replaced by (h, L) on every forward.  Differentiable in h, L and C."""
+    if kind not in ("chol", "eri"):
+        raise ValueError("kind is 'chol' or 'eri'")
+    if C.dim() == 1:
+        C = C.reshape(-1, 1)
+    return _Energy.apply(h, L, C, ham, kind)
+
+
+def symmetry_orbit(p: int, q: int, r: int, s: int):
+    """The entries (pq|rs) = (qp|rs) = (pq|sr) = (rs|pq) = ... of one real permutation
+    orbit (8-fold), as a set of index tuples."""
+    return {(p, q, r, s), (q, p, r, s), (p, q, s, r), (q, p, s, r),
+            (r, s, p, q), (s, r, p, q), (r, s, q, p), (s, r, q, p)}
+
+
+def orbit_mask(n: int, idx) -> np.ndarray:
+    m = np.zeros((n,) * 4)
+    for t in symmetry_orbit(*idx):
+        m[t] = 1.0
+    return m

@@ -151,6 +151,12 @@ struct sci_ctx {
     void *bv_part = nullptr;
     size_t bv_bytes = 0;
 
+    // density matrices: per-call scratch (grown on demand) and the device copy of the weights
+    void *rdm_scratch = nullptr;
+    size_t rdm_bytes = 0;
+    void *rdm_w = nullptr;
+    size_t rdm_wbytes = 0;
+
     // kernel timing
     int profile = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};

@@ -1,0 +1,394 @@
+// Reduced density matrices (Sec. 3.4) by the same bucket walks as sigma.
+//
+//   g1[p][q]       = sum_k w_k <c_k| a+_p a_q |c_k>
+//   g2[p][q][r][s] = sum_k w_k <c_k| a+_p a+_r a_s a_q |c_k>
+// over spin-orbitals (bit order of the keys) or spinors, unnormalised, so that for a
+// normalised c the energy of Eq. Hamiltonian is sum h g1 + 1/2 sum (pq|rs) g2.
+//
+// The connections are recomputed from the setup tables, never stored.  The pairs of the
+// three Slater-Condon classes (Sec. 2.3: zero, one and two differences) touch disjoint
+// sets of g2 elements, so each class is accumulated into its own compact table and
+// expanded once at the end:
+//   diagonal (I = J): g1[p][p] and g2[p][p][r][r] = -g2[p][r][r][p] = sum_I w_I n_p n_r.
+//     With n(I) = n(ref) + Delta(I) (Delta nonzero on the <= 2 x level orbitals where I
+//     and the reference differ) the pair occupation is
+//       O[p][r] = Wt n_p n_r + n_p D_r + D_p n_r + DD[p][r],
+//     Wt = sum w_I, D = sum w_I Delta(I), DD = sum w_I Delta Delta^T,
+//     accumulated per CTA in shared memory.
+//   singles (members X = S + x, Y = S + y of one (N-1) bucket): w = conj(c_X) c_Y ph,
+//     g1[x][y] += w, and for every spectator k in S
+//       g2[x][y][k][k] = g2[k][k][x][y] = -g2[x][k][k][y] = -g2[k][y][x][k] += w.
+//     The spectator sum b[x][y][k] = sum w n_k(S) is kept as A[x][y] n_k(ref) + Bc[x][y][k]
+//     with Bc taking only the orbitals of S that differ from the reference (the same
+//     reference decomposition as the sigma singles).
+//   doubles (members I = K + {a,b}, J = K + {i,j} of one (N-2) bucket, disjoint): one
+//     atomic add of w = conj(c_I) c_J ph into a table laid out like the pair-integral
+//     table (with separate alpha-alpha and beta-beta regions), for the pairs with the
+//     bra before the ket in the bucket; the other orientation is its conjugate.  Then
+//       g2[a][i][b][j] = g2[b][j][a][i] = -g2[a][j][b][i] = -g2[b][i][a][j]
+//         = dT[bra, ket] + conj(dT[ket, bra]).
+// Signs: <I| a+_a a+_b a_j a_i |J> is the phase (-1)^(pi_I + pi_J) of the sigma kernels.
+#include <algorithm>
+#include <vector>
+
+#include "sci_bucket.cuh"
+#include "sci_internal.cuh"
+
+using sci::zdbl;
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxVec = 8;  // vectors per walk; wider blocks take several walks
+
+__device__ __forceinline__ double sflip(bool f, double a) { return __longlong_as_double(__double_as_longlong(a) ^ ((long long)f << 63)); }
+__device__ __forceinline__ zdbl sflip(bool f, zdbl a) { return zdbl{sflip(f, a.x), sflip(f, a.y)}; }
+__device__ __forceinline__ double conjv(double a) { return a; }
+__device__ __forceinline__ zdbl conjv(zdbl a) { return zdbl{a.x, -a.y}; }
+__device__ __forceinline__ double sqnorm(double a) { return a * a; }
+__device__ __forceinline__ double sqnorm(zdbl a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ double scale(double a, double s) { return a * s; }
+__device__ __forceinline__ zdbl scale(zdbl a, double s) { return zdbl{a.x * s, a.y * s}; }
+__device__ __forceinline__ void zero(double &a) { a = 0.0; }
+__device__ __forceinline__ void zero(zdbl &a) { a = zdbl{0.0, 0.0}; }
+// a += x * y
+__device__ __forceinline__ void mac(double &a, double x, double y) { a = fma(x, y, a); }
+__device__ __forceinline__ void mac(zdbl &a, zdbl x, zdbl y)
+{
+    a.x = fma(x.x, y.x, fma(-x.y, y.y, a.x));
+    a.y = fma(x.x, y.y, fma(x.y, y.x, a.y));
+}
+__device__ __forceinline__ void red(double *p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void red(zdbl *p, zdbl v)
+{
+    atomicAdd(&p->x, v.x);
+    atomicAdd(&p->y, v.y);
+}
+__device__ __forceinline__ double neg(double a) { return -a; }
+__device__ __forceinline__ zdbl neg(zdbl a) { return zdbl{-a.x, -a.y}; }
+__device__ __forceinline__ double add(double a, double b) { return a + b; }
+template <typename TC> __device__ __forceinline__ TC from_real(double v);
+template <> __device__ __forceinline__ double from_real<double>(double v) { return v; }
+template <> __device__ __forceinline__ zdbl from_real<zdbl>(double v) { return zdbl{v, 0.0}; }
+__device__ __forceinline__ zdbl add(zdbl a, zdbl b) { return zdbl{a.x + b.x, a.y + b.y}; }
+
+// gradient-table offsets: the pair-table offsets, with beta-beta pairs moved to a region
+// of their own after the alpha-alpha one (real spin-orbital mode)
+__device__ __forceinline__ void grad_offsets(sci::TabRule tr, int x, int y, uint32_t bb_off, uint32_t &rowoff,
+                                             uint32_t &colbase)
+{
+    sci::pair_offsets(tr, x, y, rowoff, colbase);
+    if (!tr.spinors && x >= tr.n) colbase += bb_off;
+}
+
+// ------------------------------------------------------------------ diagonal
+template <typename TC>
+__global__ void __launch_bounds__(kThreads)
+k_rdm_diag(const uint64_t *__restrict__ keys, int64_t M, int norb, uint64_t ref, const TC *__restrict__ C, int nvec, int v0,
+           int nv, const double *__restrict__ wk, double *__restrict__ Wt, double *__restrict__ D, double *__restrict__ DD)
+{
+    __shared__ double sDD[64 * 64];
+    __shared__ double sD[64];
+    __shared__ double sW[kThreads / 32];
+    for (int i = threadIdx.x; i < norb * norb; i += blockDim.x) sDD[i] = 0.0;
+    for (int i = threadIdx.x; i < norb; i += blockDim.x) sD[i] = 0.0;
+    __syncthreads();
+    double wsum = 0.0;
+    for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < M; I += (int64_t)gridDim.x * blockDim.x) {
+        double w = 0.0;
+        for (int v = 0; v < nv; v++) w = fma(wk[v0 + v], sqnorm(C[I * nvec + v0 + v]), w);
+        wsum += w;
+        const uint64_t key = keys[I], d = key ^ ref;
+        for (uint64_t m = d; m; m &= m - 1) {
+            const int p = __ffsll((long long)m) - 1;
+            const double wp = (key >> p) & 1 ? w : -w;
+            atomicAdd(&sD[p], wp);
+            for (uint64_t m2 = d; m2; m2 &= m2 - 1) {
+                const int r = __ffsll((long long)m2) - 1;
+                atomicAdd(&sDD[p * norb + r], (key >> r) & 1 ? wp : -wp);
+            }
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, off);
+    if ((threadIdx.x & 31) == 0) sW[threadIdx.x >> 5] = wsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < kThreads / 32; i++) t += sW[i];
+        atomicAdd(Wt, t);
+    }
+    for (int i = threadIdx.x; i < norb * norb; i += blockDim.x)
+        if (sDD[i] != 0.0) atomicAdd(DD + i, sDD[i]);
+    for (int i = threadIdx.x; i < norb; i += blockDim.x)
+        if (sD[i] != 0.0) atomicAdd(D + i, sD[i]);
+}
+
+// ------------------------------------------------------------------ singles
+template <typename TC>
+__global__ void __launch_bounds__(kThreads)
+k_rdm_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S, const uint32_t *__restrict__ e_meta,
+              int64_t E, int norb, uint64_t ref, const TC *__restrict__ C, int nvec, int v0, int nv,
+              const double *__restrict__ wk, TC *__restrict__ A, TC *__restrict__ Bc)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t meta = e_meta[p];
+        const int x = (int)(meta & 0x7F);
+        const bool par = (meta >> 7) & 1;
+        const int64_t bs = p - (int64_t)((meta >> 8) & 0xFFF);
+        const int64_t be = bs + (int64_t)(meta >> 20);
+        const uint64_t Sk = e_S[p];
+        const uint64_t part = Sk & ~ref, holes = ref & ~Sk;
+        const int64_t idx = e_idx[p];
+        TC rowc[kMaxVec];
+#pragma unroll
+        for (int v = 0; v < kMaxVec; v++) {
+            zero(rowc[v]);
+            if (v < nv) rowc[v] = scale(conjv(sflip(par, C[idx * nvec + v0 + v])), wk[v0 + v]);
+        }
+        for (int64_t q = bs; q < be; q++) {
+            if (q == p) continue;
+            const uint32_t mq = e_meta[q];
+            const int y = (int)(mq & 0x7F);
+            const bool parq = (mq >> 7) & 1;
+            const int64_t idxq = e_idx[q];
+            TC w;
+            zero(w);
+#pragma unroll
+            for (int v = 0; v < kMaxVec; v++)
+                if (v < nv) mac(w, rowc[v], sflip(parq, C[idxq * nvec + v0 + v]));
+            const int64_t xy = (int64_t)x * norb + y;
+            red(A + xy, w);
+            for (uint64_t m = part; m; m &= m - 1) red(Bc + xy * norb + (__ffsll((long long)m) - 1), w);
+            const TC nw = neg(w);
+            for (uint64_t m = holes; m; m &= m - 1) red(Bc + xy * norb + (__ffsll((long long)m) - 1), nw);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ doubles
+template <typename TC>
+__global__ void __launch_bounds__(kThreads)
+k_rdm_doubles(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_code, const uint32_t *__restrict__ e_pos,
+              int64_t E, int CH, sci::TabRule tr, uint32_t bb_off, const TC *__restrict__ C, int nvec, int v0, int nv,
+              const double *__restrict__ wk, TC *__restrict__ dT)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    int64_t r0, r1;
+    sci::window(e_pos, E, CH, r0, r1);
+    if (r0 >= r1) return;
+    const int W = (int)(r1 - r0);
+    TC *s_c = reinterpret_cast<TC *>(smem);  // [W][nv]: c of each member times (-1)^pi
+    const size_t cbytes = ((size_t)W * nv * sizeof(TC) + 15) & ~(size_t)15;
+    uint2 *s_kc = reinterpret_cast<uint2 *>(smem + cbytes);
+    for (int q = threadIdx.x; q < W; q += blockDim.x) {
+        const int64_t g = r0 + q;
+        const uint32_t code = e_code[g];
+        const int64_t idx = e_idx[g];
+        uint32_t rowoff, colbase;
+        grad_offsets(tr, sci::code_x(code), sci::code_y(code), bb_off, rowoff, colbase);
+        s_kc[q] = make_uint2(sci::col_code(code), colbase);
+        const bool par = sci::code_par(code);
+        for (int v = 0; v < nv; v++) s_c[q * nv + v] = sflip(par, C[idx * nvec + v0 + v]);
+    }
+    __syncthreads();
+    for (int q0 = threadIdx.x; q0 < W; q0 += blockDim.x) {
+        const uint32_t code = e_code[r0 + q0], pos = e_pos[r0 + q0];
+        uint32_t rowoff, colbase;
+        grad_offsets(tr, sci::code_x(code), sci::code_y(code), bb_off, rowoff, colbase);
+        const int be = q0 - sci::pos_off(pos) + sci::pos_size(pos);
+        const uint32_t rc = sci::row_code(code);
+        TC rowc[kMaxVec];
+#pragma unroll
+        for (int v = 0; v < kMaxVec; v++) {
+            zero(rowc[v]);
+            if (v < nv) rowc[v] = scale(conjv(s_c[q0 * nv + v]), wk[v0 + v]);
+        }
+        TC *trow = dT + rowoff;
+        for (int j = q0 + 1; j < be; j++) {
+            const uint2 kc = s_kc[j];
+            if (!sci::disjoint(rc, kc.x)) continue;
+            TC w;
+            zero(w);
+#pragma unroll
+            for (int v = 0; v < kMaxVec; v++)
+                if (v < nv) mac(w, rowc[v], s_c[j * nv + v]);
+            red(trow + kc.y, w);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ expansion
+// g1 and the g2 elements of the diagonal and single-excitation classes; one thread per
+// (x, y)
+template <typename TC>
+__global__ void k_rdm_expand1(int norb, uint64_t ref, const double *__restrict__ Wt, const double *__restrict__ D,
+                              const double *__restrict__ DD, const TC *__restrict__ A, const TC *__restrict__ Bc,
+                              TC *__restrict__ g1, TC *__restrict__ g2)
+{
+    const int64_t n2 = (int64_t)norb * norb, n3 = n2 * norb;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n2; t += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(t / norb), y = (int)(t % norb);
+        const double nx = (double)((ref >> x) & 1), ny = (double)((ref >> y) & 1);
+        const double O = *Wt * nx * ny + nx * D[y] + D[x] * ny + DD[t];
+        const TC o = from_real<TC>(O);
+        if (x == y) {
+            g1[t] = o;
+            continue;
+        }
+        const TC a = A[t];
+        g1[t] = a;
+        if (!g2) continue;
+        g2[(int64_t)x * n3 + (int64_t)x * n2 + (int64_t)y * norb + y] = o;         // (x x | y y)
+        g2[(int64_t)x * n3 + (int64_t)y * n2 + (int64_t)y * norb + x] = neg(o);    // (x y | y x)
+        for (int k = 0; k < norb; k++) {
+            if (k == x || k == y) continue;
+            const TC b = add(scale(a, (double)((ref >> k) & 1)), Bc[t * norb + k]);
+            const TC nb = neg(b);
+            g2[(int64_t)x * n3 + (int64_t)y * n2 + (int64_t)k * norb + k] = b;     // (x y | k k)
+            g2[(int64_t)k * n3 + (int64_t)k * n2 + (int64_t)x * norb + y] = b;     // (k k | x y)
+            g2[(int64_t)x * n3 + (int64_t)k * n2 + (int64_t)k * norb + y] = nb;    // (x k | k y)
+            g2[(int64_t)k * n3 + (int64_t)y * n2 + (int64_t)x * norb + k] = nb;    // (k y | x k)
+        }
+    }
+}
+
+// unordered pair index P(a, b) = b(b-1)/2 + a, a < b -> (a, b)
+__device__ __forceinline__ void unpair(int P, int &a, int &b)
+{
+    int bb = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)P)) * 0.5f);
+    while (bb * (bb - 1) / 2 > P) bb--;
+    while ((bb + 1) * bb / 2 <= P) bb++;
+    b = bb;
+    a = P - bb * (bb - 1) / 2;
+}
+
+// g2 elements of the double-excitation class from the gradient table; one thread per
+// table entry (bra, ket), writing the four elements of that orientation
+template <typename TC>
+__global__ void k_rdm_expand2(sci::TabRule tr, int norb, int64_t nT, const TC *__restrict__ dT, TC *__restrict__ g2)
+{
+    const int n = tr.n;
+    const int64_t n2 = (int64_t)norb * norb, n3 = n2 * norb;
+    const int64_t NP = (int64_t)n * (n - 1) / 2;
+    const int64_t nab = tr.spinors ? 0 : (int64_t)n * n * n * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nT; e += (int64_t)gridDim.x * blockDim.x) {
+        int a, b, i, j;
+        int64_t et;
+        if (e < nab) {  // alpha-beta: e = u_ket * n^2 + u_bra, u = (y - n) * n + x
+            const int64_t ub = e % ((int64_t)n * n), uk = e / ((int64_t)n * n);
+            a = (int)(ub % n), b = n + (int)(ub / n);
+            i = (int)(uk % n), j = n + (int)(uk / n);
+            et = ub * ((int64_t)n * n) + uk;
+        } else {        // same spin (spinor mode: all): e = p_ket * NP + p_bra
+            const int64_t e2 = e - nab;
+            const int64_t reg = e2 / (NP * NP), r = e2 % (NP * NP);
+            const int pb = (int)(r % NP), pk = (int)(r / NP);
+            unpair(pb, a, b);
+            unpair(pk, i, j);
+            if (reg) a += n, b += n, i += n, j += n;  // beta-beta region
+            et = nab + reg * (NP * NP) + (int64_t)pb * NP + pk;
+        }
+        if (a == i || a == j || b == i || b == j) continue;  // not a double: other classes own these
+        const TC u = add(dT[e], conjv(dT[et]));
+        const TC nu = neg(u);
+        g2[(int64_t)a * n3 + (int64_t)i * n2 + (int64_t)b * norb + j] = u;
+        g2[(int64_t)b * n3 + (int64_t)j * n2 + (int64_t)a * norb + i] = u;
+        g2[(int64_t)a * n3 + (int64_t)j * n2 + (int64_t)b * norb + i] = nu;
+        g2[(int64_t)b * n3 + (int64_t)i * n2 + (int64_t)a * norb + j] = nu;
+    }
+}
+
+int grid_for(int64_t n)
+{
+    const int64_t b = (n + kThreads - 1) / kThreads;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
+}
+
+template <typename TC>
+int rdm_run(sci_ctx *ctx, const TC *C, int nvec, const double *wk_dev, TC *g1, TC *g2)
+{
+    const int norb = ctx->norb, n = ctx->n;
+    const int64_t n2 = (int64_t)norb * norb;
+    const int64_t NP = (int64_t)n * (n - 1) / 2;
+    const int64_t nT = ctx->spinors ? NP * NP : (int64_t)n * n * n * n + 2 * NP * NP;
+    const uint32_t bb_off = ctx->spinors ? 0u : (uint32_t)(NP * NP);
+    // scratch: Wt, D[norb], DD[norb^2] (double); A[norb^2], Bc[norb^3], dT[nT] (TC)
+    const size_t dbytes = sizeof(double) * (1 + norb + n2);
+    const size_t tbytes = sizeof(TC) * (n2 + n2 * norb + (g2 ? nT : 0));
+    const size_t need = ((dbytes + 255) & ~(size_t)255) + tbytes;
+    if (need > ctx->rdm_bytes) {
+        if (ctx->rdm_scratch) cudaFree(ctx->rdm_scratch);
+        ctx->rdm_scratch = nullptr, ctx->rdm_bytes = 0;
+        if (cudaMalloc(&ctx->rdm_scratch, need) != cudaSuccess) return sci_fail(ctx, SCI_ERR_NOMEM, "rdm12: scratch");
+        ctx->rdm_bytes = need;
+    }
+    unsigned char *base = static_cast<unsigned char *>(ctx->rdm_scratch);
+    double *Wt = reinterpret_cast<double *>(base), *D = Wt + 1, *DD = D + norb;
+    TC *A = reinterpret_cast<TC *>(base + ((dbytes + 255) & ~(size_t)255));
+    TC *Bc = A + n2;
+    TC *dT = Bc + n2 * norb;
+    if (sci_cuda_check(ctx, cudaMemsetAsync(ctx->rdm_scratch, 0, need, ctx->stream), "rdm12 memset") ||
+        (g2 && sci_cuda_check(ctx, cudaMemsetAsync(g2, 0, sizeof(TC) * n2 * n2, ctx->stream), "rdm12 memset g2")))
+        return SCI_ERR_CUDA;
+    const sci::TabRule tr{ctx->spinors, n};
+    const int CH = 768;
+    auto stage_bytes = [&](int nv) {
+        return (((size_t)(CH + ctx->maxb2) * nv * sizeof(TC) + 15) & ~(size_t)15) + (size_t)(CH + ctx->maxb2) * sizeof(uint2);
+    };
+    // vectors per walk: at most kMaxVec, fewer when the staged window would not fit
+    int kv = kMaxVec;
+    while (kv > 1 && stage_bytes(kv) > 200 * 1024) kv >>= 1;
+    if (g2 && ctx->e2 > 0 && stage_bytes(kv) > 200 * 1024)
+        return sci_fail(ctx, SCI_ERR_OVERFLOW, "rdm12: largest bucket too large for shared memory");
+    for (int v0 = 0; v0 < nvec; v0 += kv) {
+        const int nv = std::min(kv, nvec - v0);
+        k_rdm_diag<TC><<<grid_for(ctx->M), kThreads, 0, ctx->stream>>>(ctx->keys, ctx->M, norb, ctx->ref, C, nvec, v0, nv,
+                                                                       wk_dev, Wt, D, DD);
+        if (ctx->e1 > 0)
+            k_rdm_singles<TC><<<grid_for(ctx->e1), kThreads, 0, ctx->stream>>>(
+                ctx->e1_idx, ctx->e1_S, ctx->e1_meta, ctx->e1, norb, ctx->ref, C, nvec, v0, nv, wk_dev, A, Bc);
+        if (g2 && ctx->e2 > 0) {
+            const size_t smem = stage_bytes(nv);
+            auto kern = k_rdm_doubles<TC>;
+            if (smem > 48 * 1024 &&
+                sci_cuda_check(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                               "rdm12 attr"))
+                return SCI_ERR_CUDA;
+            const int64_t blocks = (ctx->e2 + CH - 1) / CH;
+            kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(ctx->e2_idx, ctx->e2_code, ctx->e2_pos, ctx->e2, CH, tr,
+                                                                   bb_off, C, nvec, v0, nv, wk_dev, dT);
+        }
+    }
+    k_rdm_expand1<TC><<<grid_for(n2), kThreads, 0, ctx->stream>>>(norb, ctx->ref, Wt, D, DD, A, Bc, g1, g2);
+    if (g2) k_rdm_expand2<TC><<<grid_for(nT), kThreads, 0, ctx->stream>>>(tr, norb, nT, dT, g2);
+    return sci_cuda_check(ctx, cudaGetLastError(), "rdm12 launch") ? SCI_ERR_CUDA : SCI_OK;
+}
+
+}  // namespace
+
+extern "C" int sci_rdm12(sci_ctx *ctx, const void *C, int nvec, const double *weights, void *rdm1, void *rdm2)
+{
+    if (!ctx) return SCI_ERR_ARG;
+    if (!ctx->have_ints || !ctx->have_dets) return sci_fail(ctx, SCI_ERR_STATE, "rdm12: integrals and determinants first");
+    if (nvec < 1 || !rdm1 || (ctx->M > 0 && !C)) return sci_fail(ctx, SCI_ERR_ARG, "rdm12: need nvec >= 1, C and rdm1");
+    if (ctx->norb > 64) return sci_fail(ctx, SCI_ERR_ARG, "rdm12: at most 64 orbitals");
+    if (sci_cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) return SCI_ERR_CUDA;
+    // weights to the device (a host array of nvec doubles, NULL = all ones)
+    const size_t wbytes = sizeof(double) * nvec;
+    if (wbytes > ctx->rdm_wbytes) {
+        if (ctx->rdm_w) cudaFree(ctx->rdm_w);
+        ctx->rdm_w = nullptr, ctx->rdm_wbytes = 0;
+        if (cudaMalloc(&ctx->rdm_w, wbytes) != cudaSuccess) return sci_fail(ctx, SCI_ERR_NOMEM, "rdm12: weights");
+        ctx->rdm_wbytes = wbytes;
+    }
+    std::vector<double> w(nvec, 1.0);
+    if (weights) std::copy(weights, weights + nvec, w.begin());
+    if (sci_cuda_check(ctx, cudaMemcpyAsync(ctx->rdm_w, w.data(), wbytes, cudaMemcpyHostToDevice, ctx->stream), "rdm12 weights") ||
+        sci_cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "rdm12 weights sync"))
+        return SCI_ERR_CUDA;
+    const double *wk = static_cast<const double *>(ctx->rdm_w);
+    if (ctx->cplx)
+        return rdm_run<zdbl>(ctx, static_cast<const zdbl *>(C), nvec, wk, static_cast<zdbl *>(rdm1), static_cast<zdbl *>(rdm2));
+    return rdm_run<double>(ctx, static_cast<const double *>(C), nvec, wk, static_cast<double *>(rdm1), static_cast<double *>(rdm2));
+}

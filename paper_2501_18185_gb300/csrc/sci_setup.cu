@@ -613,6 +613,8 @@ extern "C" int sci_destroy(sci_ctx *ctx)
     if (ctx->stage_c) cudaFree(ctx->stage_c);
     if (ctx->stage_s) cudaFree(ctx->stage_s);
     if (ctx->bv_part) cudaFree(ctx->bv_part);
+    if (ctx->rdm_scratch) cudaFree(ctx->rdm_scratch);
+    if (ctx->rdm_w) cudaFree(ctx->rdm_w);
     for (auto &e : ctx->ev)
         if (e) cudaEventDestroy(e);
     if (ctx->status) cudaFree(ctx->status);

@@ -47,6 +47,7 @@ SIGNATURES = {
     "sci_info": (_i32, [_vp, _vp, _i32]),
     "sci_profile": (_i32, [_vp, _i32]),
     "sci_kernel_times": (_i32, [_vp, _vp, _i32]),
+    "sci_rdm12": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp]),
     "sci_bv_gemm_tn": (_i32, [_vp, _i64, _i32, _i32, _vp, _i64, _vp, _i64, _vp, _i32]),
     "sci_bv_gemm_nn": (_i32, [_vp, _i64, _i32, _vp, _i64, _i32, _vp, _vp, _i64, _i32, _vp, ctypes.c_double, _vp,
                               _i64, _vp, _vp, _vp, _i32]),
@@ -189,6 +190,11 @@ def sci_kernel_times(ctx) -> list:
     return [float(x) for x in ms]
 
 
+def sci_rdm12(ctx, C, nvec, weights, rdm1, rdm2):
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    return _check(ctx, load().sci_rdm12(ctx, _p(C), nvec, _p(w), _p(rdm1), _p(rdm2)))
+
+
 def sci_bv_gemm_tn(ctx, M, k, a, A, lda, B, ldb, P, prec):
     return _check(ctx, load().sci_bv_gemm_tn(ctx, M, k, a, _p(A), lda, _p(B), ldb, _p(P), prec))
 
@@ -297,6 +303,27 @@ class Hamiltonian:
         S = out if out is not None else torch.empty((C2.shape[0], nvec), dtype=odt, device=self.device)
         sci_sigma(self.ctx, C2, S, nvec, prec)
         return S.reshape(-1) if squeeze and out is None else S
+
+    @property
+    def norb(self) -> int:
+        """Bits of a key: 2n spin-orbitals or n spinors."""
+        return self.n if self.mode == "spinors" else 2 * self.n
+
+    def rdm12(self, C, weights=None, rdm2: bool = True):
+        """(g1 [norb, norb], g2 [norb]^4 or None): sum_k w_k of the unnormalised density
+        matrices of the columns of C ([M] or [M, nvec], torch CUDA) -- see sci_rdm12."""
+        torch = self.torch
+        C2 = (C.reshape(-1, 1) if C.dim() == 1 else C).contiguous()
+        if self.M and C2.shape[0] != self.M:
+            raise ValueError(f"C has {C2.shape[0]} rows, the determinant list {self.M}")
+        dt = torch.complex128 if self.complex else torch.float64
+        if C2.dtype != dt:
+            raise ValueError(f"C must be {dt} for this Hamiltonian")
+        no = self.norb
+        g1 = torch.empty((no, no), dtype=dt, device=self.device)
+        g2 = torch.empty((no, no, no, no), dtype=dt, device=self.device) if rdm2 else None
+        sci_rdm12(self.ctx, C2, C2.shape[1], weights, g1, g2)
+        return g1, g2
 
     def connections(self, row_begin: int = 0, row_end: int | None = None):
         row_end = self.M if row_end is None else row_end
