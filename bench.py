@@ -228,6 +228,58 @@ def rdm_bench(H, w, nvec=4, reps=3):
     return out
 
 
+def batch_bench(reps=10):
+    """The 64 heterogeneous full-CI instances in one persistent launch: setup, autotuner
+    time and choices, and CUDA-event milliseconds per batched sigma (L2 flushed before
+    each timed launch) for the graph-captured AUTO plan, the all-TILE and all-WARP plans,
+    and the 64 instances' own sci_sigma calls one after another."""
+    import torch
+
+    from paper_2501_18185_gb300 import sci
+    from paper_2501_18185_gb300 import workloads as W
+
+    t = time.perf_counter()
+    ws = W.batch_instances()
+    hams = [sci.Hamiltonian.from_workload(w) for w in ws]
+    setup_s = time.perf_counter() - t
+    C = torch.from_numpy(np.concatenate([w.c[:, 0] for w in ws])).cuda()
+    S = torch.empty_like(C)
+    flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=C.device)
+    stream = torch.cuda.current_stream()
+
+    def ev_ms(fn):
+        fn()
+        out = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return statistics.median(out)
+
+    B = sci.Batch(hams)
+    res = {"instances": len(ws), "M_total": B.M, "setup_s": round(setup_s, 3)}
+    for name, sch in (("tile", sci.SCI_SCHED_TILE), ("warp", sci.SCI_SCHED_WARP)):
+        B.plan(sch)
+        res[f"ms_all_{name}"] = ev_ms(lambda: B.sigma(C, out=S))
+    t = time.perf_counter()
+    B.plan(sci.SCI_SCHED_AUTO, C, S)
+    res["autotune_s"] = round(time.perf_counter() - t, 3)
+    B.capture(C, S)
+    res["ms_auto_graph"] = ev_ms(B.replay)
+    res["ms_instances_one_by_one"] = ev_ms(
+        lambda: [H.sigma(C[o:o + H.M], out=S[o:o + H.M].view(-1, 1)) for H, o in zip(hams, B.offsets)])
+    it = B.items()
+    res.update({"pairs": it["pairs"], "work_items": it["items"], "persistent_ctas": it["ctas"],
+                "pairs_per_s_auto_graph": it["pairs"] / (res["ms_auto_graph"] / 1e3),
+                "schedules": {k: sum(1 for i in range(len(ws)) if B.info(i)["schedule"] == k) for k in ("tile", "warp")},
+                "l2": "flushed before each timed launch (256 MB write)"})
+    return res
+
+
 def run_reference(args, rank, world):
     """--impl reference: the CPU oracle on bounded samples of the same workload."""
     if rank != 0:
@@ -410,10 +462,11 @@ def main():
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(w)
     dav = None
-    rdm = None
+    rdm = batch = None
     if not args.no_davidson and world == 1 and not w.ints.complex_:
         dav = davidson_bench(H, w)
         rdm = rdm_bench(H, w)
+        batch = batch_bench()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c128" if w.ints.complex_ else "f64", "data": "synthetic",
@@ -423,7 +476,7 @@ def main():
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
             "gpu_launches": args.steps * (1 + 2 * ((nv + 7) // 8 if not w.ints.complex_ else (nv + 3) // 4)),
             "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "prec": args.prec,
-            "other_prec": variant, "davidson": dav, "rdm": rdm}
+            "other_prec": variant, "davidson": dav, "rdm": rdm, "batch": batch}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -214,6 +214,45 @@ int sci_kernel_times(sci_ctx *ctx, float *ms, int n);
  * SCI_ERR_NOMEM. */
 int sci_rdm12(sci_ctx *ctx, const void *C, int nvec, const double *weights, void *rdm1, void *rdm2);
 
+/* ---------------------------------------------------------------- batched instances
+ * Many small real spin-orbital Hamiltonians (each a sci_ctx with integrals and
+ * determinants set) applied to their vectors in ONE persistent kernel launch, the GPU
+ * form of the paper's dynamic task scheduling (Sec. 3.1).  The paper has no batched
+ * entry point; its tasks are oCFG pairs of one Hamiltonian.
+ *
+ * Vectors: all instances' C (and S) live in one device array of sum_i M_i doubles,
+ * instance i at offset sum_{j<i} M_j (its add order); one vector per instance.
+ * Schedules: SCI_SCHED_TILE walks the bucket tables (any determinant list, atomics into
+ * S); SCI_SCHED_WARP gives each determinant a warp that generates its excitations and
+ * indexes them by combinatorial ranking (full-CI instances only, S stored directly);
+ * SCI_SCHED_AUTO times both on each instance and keeps the faster (decisions and times
+ * cached by (n, n_alpha, n_beta, M) in the batch, so equal shapes are timed once).
+ * The batch keeps pointers into the instances' tables: an instance must outlive the
+ * batch and must not be re-set after sci_batch_plan().  Work runs on a stream of the
+ * batch, ordered after the work queued on the caller's stream at the time of the call
+ * and before later work queued there. */
+typedef struct sci_batch sci_batch;
+enum { SCI_SCHED_AUTO = 0, SCI_SCHED_TILE = 1, SCI_SCHED_WARP = 2 };
+int sci_batch_create(sci_batch **out, int device, void *cuda_stream);
+int sci_batch_destroy(sci_batch *b);
+/* Append an instance; returns its index (>= 0) or a negative error code. */
+int sci_batch_add(sci_batch *b, sci_ctx *instance);
+/* Choose the schedules and build the work list (items ordered by decreasing cost).  AUTO
+ * runs both schedules on C -> S (device arrays as above; S is overwritten) to time them;
+ * TILE and WARP need no vectors (C, S may be NULL).  Synchronous. */
+int sci_batch_plan(sci_batch *b, int schedule, const double *C, double *S);
+/* S = H_i C_i for every instance, one persistent launch (after a counter reset and a
+ * clear of S). */
+int sci_batch_sigma(sci_batch *b, const double *C, double *S);
+/* Capture that launch for fixed C and S in a CUDA graph owned by the batch; replay it. */
+int sci_batch_capture(sci_batch *b, const double *C, double *S);
+int sci_batch_replay(sci_batch *b);
+/* Per instance: chosen schedule, autotuner times in ms (-1 if not timed), offset. */
+int sci_batch_info(sci_batch *b, int i, int *schedule, float *ms_tile, float *ms_warp, int64_t *offset);
+/* out[0..n): work items, persistent CTAs, total determinants, total pairs; n <= 4. */
+int sci_batch_items(sci_batch *b, int64_t *out, int n);
+const char *sci_batch_last_error(const sci_batch *b);
+
 /* Block-vector products for the subspace algebra of a block Davidson solver around
  * sigma (Sec. 2.4, the diagonalisation paragraph: the eigenproblem is solved through
  * matrix-vector products; the paper leaves the solver's linear algebra unspecified).

@@ -33,11 +33,16 @@ __device__ __forceinline__ bool disjoint(uint32_t rc, uint32_t cc)
 // the bucket holding row b*CH to the start of the bucket holding row (b+1)*CH.  Every
 // bucket lands in exactly one window; a window has at most CH + maxb - 1 rows (it can be
 // empty when one bucket spans a whole range).
-__device__ __forceinline__ void window(const uint32_t *__restrict__ e_pos, int64_t E, int CH, int64_t &r0, int64_t &r1)
+__device__ __forceinline__ void window_of(const uint32_t *__restrict__ e_pos, int64_t E, int CH, int64_t b, int64_t &r0,
+                                          int64_t &r1)
 {
-    const int64_t a0 = (int64_t)blockIdx.x * CH, a1 = a0 + CH;
+    const int64_t a0 = b * CH, a1 = a0 + CH;
     r0 = a0 - pos_off(e_pos[a0]);
     r1 = a1 < E ? a1 - pos_off(e_pos[a1]) : E;
+}
+__device__ __forceinline__ void window(const uint32_t *__restrict__ e_pos, int64_t E, int CH, int64_t &r0, int64_t &r1)
+{
+    window_of(e_pos, E, CH, blockIdx.x, r0, r1);
 }
 
 }  // namespace sci

@@ -48,6 +48,16 @@ SIGNATURES = {
     "sci_profile": (_i32, [_vp, _i32]),
     "sci_kernel_times": (_i32, [_vp, _vp, _i32]),
     "sci_rdm12": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp]),
+    "sci_batch_create": (_i32, [ctypes.POINTER(_vp), _i32, _vp]),
+    "sci_batch_destroy": (_i32, [_vp]),
+    "sci_batch_add": (_i32, [_vp, _vp]),
+    "sci_batch_plan": (_i32, [_vp, _i32, _vp, _vp]),
+    "sci_batch_sigma": (_i32, [_vp, _vp, _vp]),
+    "sci_batch_capture": (_i32, [_vp, _vp, _vp]),
+    "sci_batch_replay": (_i32, [_vp]),
+    "sci_batch_info": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp]),
+    "sci_batch_items": (_i32, [_vp, _vp, _i32]),
+    "sci_batch_last_error": (ctypes.c_char_p, [_vp]),
     "sci_bv_gemm_tn": (_i32, [_vp, _i64, _i32, _i32, _vp, _i64, _vp, _i64, _vp, _i32]),
     "sci_bv_gemm_nn": (_i32, [_vp, _i64, _i32, _vp, _i64, _i32, _vp, _vp, _i64, _i32, _vp, ctypes.c_double, _vp,
                               _i64, _vp, _vp, _vp, _i32]),
@@ -193,6 +203,63 @@ def sci_kernel_times(ctx) -> list:
 def sci_rdm12(ctx, C, nvec, weights, rdm1, rdm2):
     w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
     return _check(ctx, load().sci_rdm12(ctx, _p(C), nvec, _p(w), _p(rdm1), _p(rdm2)))
+
+
+SCI_SCHED_AUTO, SCI_SCHED_TILE, SCI_SCHED_WARP = 0, 1, 2
+
+
+def _bcheck(b, rc):
+    if rc < 0:
+        msg = load().sci_batch_last_error(b) if b else b""
+        raise SciError(rc, (msg or b"").decode())
+    return rc
+
+
+def sci_batch_create(device: int = 0, stream: int | None = None):
+    b = ctypes.c_void_p()
+    rc = load().sci_batch_create(ctypes.byref(b), device, ctypes.c_void_p(stream or 0))
+    if rc != SCI_OK:
+        raise SciError(rc, "sci_batch_create failed")
+    return b
+
+
+def sci_batch_destroy(b):
+    return load().sci_batch_destroy(b)
+
+
+def sci_batch_add(b, ctx) -> int:
+    return _bcheck(b, load().sci_batch_add(b, ctx))
+
+
+def sci_batch_plan(b, schedule, C=None, S=None):
+    return _bcheck(b, load().sci_batch_plan(b, schedule, _p(C), _p(S)))
+
+
+def sci_batch_sigma(b, C, S):
+    return _bcheck(b, load().sci_batch_sigma(b, _p(C), _p(S)))
+
+
+def sci_batch_capture(b, C, S):
+    return _bcheck(b, load().sci_batch_capture(b, _p(C), _p(S)))
+
+
+def sci_batch_replay(b):
+    return _bcheck(b, load().sci_batch_replay(b))
+
+
+def sci_batch_info(b, i) -> dict:
+    sch = ctypes.c_int()
+    mt, mw = ctypes.c_float(), ctypes.c_float()
+    off = ctypes.c_int64()
+    _bcheck(b, load().sci_batch_info(b, i, ctypes.byref(sch), ctypes.byref(mt), ctypes.byref(mw), ctypes.byref(off)))
+    return {"schedule": {0: "auto", 1: "tile", 2: "warp"}[sch.value], "ms_tile": mt.value, "ms_warp": mw.value,
+            "offset": off.value}
+
+
+def sci_batch_items(b) -> dict:
+    out = np.zeros(4, dtype=np.int64)
+    _bcheck(b, load().sci_batch_items(b, _p(out), 4))
+    return dict(zip(["items", "ctas", "M", "pairs"], (int(v) for v in out)))
 
 
 def sci_bv_gemm_tn(ctx, M, k, a, A, lda, B, ldb, P, prec):
@@ -347,3 +414,60 @@ class Hamiltonian:
 
     def sync_status(self):
         return sci_sync_status(self.ctx)
+
+
+class Batch:
+    """Heterogeneous instances (sci.Hamiltonian, real spin-orbital mode) applied to their
+    vectors in one persistent launch.  Vectors are concatenated: instance i occupies
+    rows offsets[i] : offsets[i] + M_i of one [sum M] float64 CUDA tensor."""
+
+    def __init__(self, hams, device: int = 0, stream=None):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.b = sci_batch_create(device, s.cuda_stream)
+        self.hams = list(hams)          # the batch points into their tables: keep them alive
+        self.offsets = []
+        off = 0
+        for H in self.hams:
+            sci_batch_add(self.b, H.ctx)
+            self.offsets.append(off)
+            off += H.M
+        self.M = off
+
+    def close(self):
+        if getattr(self, "b", None) is not None:
+            sci_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def plan(self, schedule: int = SCI_SCHED_AUTO, C=None, S=None):
+        if schedule == SCI_SCHED_AUTO and C is None:
+            C = self.torch.ones(self.M, dtype=self.torch.float64, device=self.device)
+        if schedule == SCI_SCHED_AUTO and S is None:
+            S = self.torch.empty(self.M, dtype=self.torch.float64, device=self.device)
+        sci_batch_plan(self.b, schedule, C, S)
+
+    def sigma(self, C, out=None):
+        S = out if out is not None else self.torch.empty_like(C)
+        sci_batch_sigma(self.b, C.contiguous(), S)
+        return S
+
+    def capture(self, C, S):
+        sci_batch_capture(self.b, C, S)
+
+    def replay(self):
+        sci_batch_replay(self.b)
+
+    def info(self, i: int) -> dict:
+        return sci_batch_info(self.b, i)
+
+    def items(self) -> dict:
+        return sci_batch_items(self.b)

@@ -324,3 +324,27 @@ def random_small(seed: int, mode: str, n: int, na: int, nb: int, naux: int = 6,
         w.keys = keys[keep]
     w.c = coefficient_vector(rng, w.keys, w.hf_key(), nvec, mode == "spinors", decay_by_level=False)
     return w
+
+
+def batch_instances(count: int = 64, max_dim: int = 200_000, seed_offset: int = 3) -> list[Workload]:
+    """Heterogeneous small full-CI instances: (n, n_alpha, n_beta) drawn uniformly from
+    n in 6..16 and 2..8 electrons per spin (with n_sigma <= n), rejected when the FCI
+    dimension C(n, n_alpha) C(n, n_beta) exceeds `max_dim`.  Each instance has integrals
+    as in the 8-orbital workload with n Cholesky vectors of sym N(0, 0.3), and one
+    N(0,1) unit vector c.
+    Draw order: all shapes first, then per instance its integrals and c."""
+    rng = np.random.default_rng(SEED_BASE + seed_offset)
+    shapes = []
+    while len(shapes) < count:
+        n = int(rng.integers(6, 17))
+        na, nb = int(rng.integers(2, 9)), int(rng.integers(2, 9))
+        if na > n or nb > n or comb(n, na) * comb(n, nb) > max_dim:
+            continue
+        shapes.append((n, na, nb))
+    out = []
+    for i, (n, na, nb) in enumerate(shapes):
+        ints = real_integrals(rng, n, n, None)
+        keys = fci_keys(n, na, nb)
+        c = coefficient_vector(rng, keys, np.uint64(0), 1, False, decay_by_level=False)
+        out.append(Workload(f"fci_{n}o_{na}a{nb}b_i{i}", "spin_orbitals", n, na, nb, keys, ints, c))
+    return out
