@@ -224,7 +224,7 @@ int sci_rdm12(sci_ctx *ctx, const void *C, int nvec, const double *weights, void
  * instance i at offset sum_{j<i} M_j (its add order); one vector per instance.
  * Schedules: SCI_SCHED_TILE walks the bucket tables (any determinant list, atomics into
  * S); SCI_SCHED_WARP gives each determinant a warp that generates its excitations and
- * indexes them by combinatorial ranking (full-CI instances only, S stored directly);
+ * indexes them by combinatorial ranking (full-CI instances of at most 20 orbitals, S stored directly);
  * SCI_SCHED_AUTO times both on each instance and keeps the faster (decisions and times
  * cached by (n, n_alpha, n_beta, M) in the batch, so equal shapes are timed once).
  * The batch keeps pointers into the instances' tables: an instance must outlive the

@@ -127,70 +127,70 @@ __device__ void tile_singles(const Inst &B, int64_t a, const double *C, double *
 }
 
 // ---------------------------------------------------------------- WARP items
-// rank of an n-bit string in the combinatorial number system: sum_m C(p_m, m) over its
-// set bits p_1 < p_2 < ... (m from 1); for strings of equal popcount this is their rank
-// in ascending numeric order
-__device__ __forceinline__ int64_t str_rank(uint32_t s, const uint32_t *binom)
-{
-    int64_t r = 0;
-    int m = 1;
-    for (; s; s &= s - 1, m++) r += binom[(__ffs(s) - 1) * 33 + m];
-    return r;
-}
+// The rank of a string in the combinatorial number system, sum_m C(p_m, m) over its set
+// bits p_1 < p_2 < ... (m from 1), is its position among the strings of equal popcount in
+// ascending numeric order, whatever the orbital count: one table of 2^kRankBits ranks
+// serves every instance with up to kRankBits orbitals.
+constexpr int kRankBits = 20;
+constexpr int kMaxPairs = 32 * 31 / 2;
 
-// bit position of the k-th (0-based) set bit of s
-__device__ __forceinline__ int kth_bit(uint32_t s, int k)
+__global__ void k_rank_table(uint32_t *rank)
 {
-    for (int i = 0; i < k; i++) s &= s - 1;
-    return __ffs((int)s) - 1;
-}
-
-__device__ __forceinline__ void unpair(int P, int &a, int &b)
-{
-    int bb = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)P)) * 0.5f);
-    while (bb * (bb - 1) / 2 > P) bb--;
-    while ((bb + 1) * bb / 2 <= P) bb++;
-    b = bb;
-    a = P - bb * (bb - 1) / 2;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < (1ll << kRankBits);
+         s += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t r = 0;
+        int m = 1;
+        for (uint32_t x = (uint32_t)s; x; x &= x - 1, m++) {
+            const int p = __ffs((int)x) - 1;  // C(p, m)
+            uint64_t c = m <= p ? 1 : 0;
+            for (int k = 1; k <= m && m <= p; k++) c = c * (uint64_t)(p - m + k) / (uint64_t)k;
+            r += c;
+        }
+        rank[s] = (uint32_t)r;
+    }
 }
 
 __device__ __forceinline__ int below(uint64_t K, int x) { return __popcll(K & ((1ull << x) - 1)); }
 
+__device__ __forceinline__ int64_t fci_index(const Inst &B, uint64_t J, const uint32_t *__restrict__ rank)
+{
+    const uint32_t ja = (uint32_t)(J & ((1ull << B.n) - 1)), jb = (uint32_t)(J >> B.n);
+    return (int64_t)__ldg(rank + jb) * B.nA + __ldg(rank + ja);
+}
+
 // H_IJ c_J for the double excitation I -> J with bra extras x < y (in I) and ket extras
 // u < v (in J), spin-orbital indices
 __device__ __forceinline__ double warp_double(const Inst &B, uint64_t key, int x, int y, int u, int v, const double *C,
-                                              const uint32_t *binom)
+                                              const uint32_t *__restrict__ rank)
 {
     const uint64_t K = key & ~(1ull << x) & ~(1ull << y);
     const uint64_t J = K | (1ull << u) | (1ull << v);
-    const int n = B.n;
-    const uint32_t ja = (uint32_t)(J & ((1ull << n) - 1)), jb = (uint32_t)(J >> n);
-    const int64_t jidx = str_rank(jb, binom) * B.nA + str_rank(ja, binom);
     uint32_t rowoff, colbase, r2, cb2;
-    const sci::TabRule tr{0, n};
+    const sci::TabRule tr{0, B.n};
     sci::pair_offsets(tr, x, y, rowoff, r2);
     sci::pair_offsets(tr, u, v, cb2, colbase);
     const bool ph = (below(K, x) + below(K, y) + below(K, u) + below(K, v)) & 1;
-    return sflip(ph, __ldg(B.tab + rowoff + colbase) * C[B.off + jidx]);
+    return sflip(ph, __ldg(B.tab + rowoff + colbase) * C[B.off + fci_index(B, J, rank)]);
 }
 
 __device__ __forceinline__ double warp_single(const Inst &B, uint64_t key, int x, int u, const double *C,
-                                              const uint32_t *binom)
+                                              const uint32_t *__restrict__ rank)
 {
     const uint64_t Sk = key & ~(1ull << x);
     const uint64_t J = Sk | (1ull << u);
-    const int n = B.n, norb = B.norb;
-    const uint32_t ja = (uint32_t)(J & ((1ull << n) - 1)), jb = (uint32_t)(J >> n);
-    const int64_t jidx = str_rank(jb, binom) * B.nA + str_rank(ja, binom);
+    const int norb = B.norb;
     double f = __ldg(B.fref + u * norb + x);
     const uint64_t part = Sk & ~B.ref, holes = B.ref & ~Sk;
     for (uint64_t m = part; m; m &= m - 1) f += __ldg(B.g_so + ((int64_t)(__ffsll((long long)m) - 1) * norb + u) * norb + x);
     for (uint64_t m = holes; m; m &= m - 1) f -= __ldg(B.g_so + ((int64_t)(__ffsll((long long)m) - 1) * norb + u) * norb + x);
     const bool ph = (below(Sk, x) + below(Sk, u)) & 1;
-    return sflip(ph, f * C[B.off + jidx]);
+    return sflip(ph, f * C[B.off + fci_index(B, J, rank)]);
 }
 
-__device__ void warp_rows(const Inst &B, int64_t a, const double *C, double *S, const uint32_t *binom)
+// orb: this warp's lists [occupied alpha | virtual alpha | occupied beta | virtual beta]
+// x 32 spin-orbital indices; pairs[P] = a | b << 8 with P = b(b-1)/2 + a, a < b
+__device__ void warp_rows(const Inst &B, int64_t a, const double *C, double *S, const uint32_t *__restrict__ rank,
+                          const uint16_t *pairs, uint8_t *orb)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t r = a * kWarps + warp;
@@ -200,46 +200,45 @@ __device__ void warp_rows(const Inst &B, int64_t a, const double *C, double *S, 
     const uint32_t full = (uint32_t)((1ull << n) - 1);
     const uint32_t oa = (uint32_t)(key & full), ob = (uint32_t)(key >> n);
     const uint32_t va = full & ~oa, vb = full & ~ob;
+    if (lane < n) {
+        const uint32_t lm = (1u << lane) - 1;
+        if ((oa >> lane) & 1) orb[__popc(oa & lm)] = (uint8_t)lane;
+        else orb[32 + __popc(va & lm)] = (uint8_t)lane;
+        if ((ob >> lane) & 1) orb[64 + __popc(ob & lm)] = (uint8_t)(n + lane);
+        else orb[96 + __popc(vb & lm)] = (uint8_t)(n + lane);
+    }
+    __syncwarp();
     const int na = B.na, nb = B.nb, ua = n - na, ub = n - nb;
     // candidate classes: alpha singles, beta singles, alpha-alpha, beta-beta, alpha-beta
-    const int64_t c0 = (int64_t)na * ua, c1 = (int64_t)nb * ub;
-    const int64_t pa = (int64_t)na * (na - 1) / 2, qa = (int64_t)ua * (ua - 1) / 2;
-    const int64_t pb = (int64_t)nb * (nb - 1) / 2, qb = (int64_t)ub * (ub - 1) / 2;
-    const int64_t c2 = pa * qa, c3 = pb * qb, c4 = c0 * c1;
-    const int64_t T = c0 + c1 + c2 + c3 + c4;
+    const int c0 = na * ua, c1 = nb * ub;
+    const int qa = ua * (ua - 1) / 2, qb = ub * (ub - 1) / 2;
+    const int c2 = na * (na - 1) / 2 * qa, c3 = nb * (nb - 1) / 2 * qb;
+    const int T = c0 + c1 + c2 + c3 + c0 * c1;
     double acc = 0.0;
-    for (int64_t t = lane; t < T; t += 32) {
-        int64_t s = t;
+    for (int t = lane; t < T; t += 32) {
+        int s = t;
         if (s < c0) {                       // alpha single x -> u
-            const int x = kth_bit(oa, (int)(s / ua)), u = kth_bit(va, (int)(s % ua));
-            acc += warp_single(B, key, x, u, C, binom);
+            acc += warp_single(B, key, orb[s / ua], orb[32 + s % ua], C, rank);
             continue;
         }
         s -= c0;
         if (s < c1) {                       // beta single
-            const int x = n + kth_bit(ob, (int)(s / ub)), u = n + kth_bit(vb, (int)(s % ub));
-            acc += warp_single(B, key, x, u, C, binom);
+            acc += warp_single(B, key, orb[64 + s / ub], orb[96 + s % ub], C, rank);
             continue;
         }
         s -= c1;
-        if (s < c2 + c3) {                  // same spin double
+        if (s < c2 + c3) {                  // same-spin double
             const bool beta = s >= c2;
             if (beta) s -= c2;
-            const int64_t q = beta ? qb : qa;
-            const uint32_t occ = beta ? ob : oa, vir = beta ? vb : va;
-            int i0, i1, j0, j1;
-            unpair((int)(s / q), i0, i1);
-            unpair((int)(s % q), j0, j1);
-            const int sh = beta ? n : 0;
-            acc += warp_double(B, key, sh + kth_bit(occ, i0), sh + kth_bit(occ, i1), sh + kth_bit(vir, j0),
-                               sh + kth_bit(vir, j1), C, binom);
+            const int q = beta ? qb : qa;
+            const uint8_t *occ = orb + (beta ? 64 : 0), *vir = orb + (beta ? 96 : 32);
+            const uint16_t po = pairs[s / q], pv = pairs[s % q];
+            acc += warp_double(B, key, occ[po & 0xFF], occ[po >> 8], vir[pv & 0xFF], vir[pv >> 8], C, rank);
             continue;
         }
         s -= c2 + c3;                       // alpha-beta double
-        const int64_t sa = s / c1, sb = s % c1;
-        const int x = kth_bit(oa, (int)(sa / ua)), u = kth_bit(va, (int)(sa % ua));
-        const int y = n + kth_bit(ob, (int)(sb / ub)), v = n + kth_bit(vb, (int)(sb % ub));
-        acc += warp_double(B, key, x, y, u, v, C, binom);
+        const int sa = s / c1, sb = s % c1;
+        acc += warp_double(B, key, orb[sa / ua], orb[64 + sb / ub], orb[32 + sa % ua], orb[96 + sb % ub], C, rank);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
@@ -249,19 +248,16 @@ __device__ void warp_rows(const Inst &B, int64_t a, const double *C, double *S, 
 // ---------------------------------------------------------------- the persistent kernel
 __global__ void __launch_bounds__(kThreads)
 k_batch(const Inst *__restrict__ insts, const Item *__restrict__ items, int nitems, int *counter,
-        const double *__restrict__ C, double *__restrict__ S)
+        const double *__restrict__ C, double *__restrict__ S, const uint32_t *__restrict__ rank)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ uint32_t binom[33 * 33];
+    __shared__ uint16_t pairs[kMaxPairs];
+    __shared__ uint8_t orb[kWarps * 128];
     __shared__ int s_item;
-    for (int t = threadIdx.x; t < 33 * 33; t += blockDim.x) {
-        const int a = t / 33, b = t % 33;  // C(a, b)
-        uint64_t v = 0;
-        if (b <= a) {
-            v = 1;
-            for (int k = 1; k <= b; k++) v = v * (uint64_t)(a - b + k) / (uint64_t)k;
-        }
-        binom[t] = (uint32_t)v;
+    for (int P = threadIdx.x; P < kMaxPairs; P += blockDim.x) {
+        int b = 1;
+        while ((b + 1) * b / 2 <= P) b++;
+        pairs[P] = (uint16_t)((P - b * (b - 1) / 2) | (b << 8));
     }
     for (;;) {
         __syncthreads();
@@ -275,7 +271,7 @@ k_batch(const Inst *__restrict__ insts, const Item *__restrict__ items, int nite
             case IT_DIAG: tile_diag(B, I.a, C, S); break;
             case IT_DOUBLES: tile_doubles(B, I.a, C, S, smem); break;
             case IT_SINGLES: tile_singles(B, I.a, C, S); break;
-            default: warp_rows(B, I.a, C, S, binom); break;
+            default: warp_rows(B, I.a, C, S, rank, pairs, orb + (threadIdx.x >> 5) * 128); break;
         }
     }
 }
@@ -309,6 +305,7 @@ struct sci_batch {
     Item *d_items = nullptr;
     int nitems = 0, items_cap = 0;
     int *d_counter = nullptr;
+    uint32_t *d_rank = nullptr;  // combinatorial ranks of all strings of kRankBits bits
     size_t smem = 0;
     int grid = 0;
     int64_t total_M = 0, total_pairs = 0;
@@ -330,9 +327,10 @@ int bfail(sci_batch *b, int code, const std::string &m)
         if (e_ != cudaSuccess) return bfail(b, SCI_ERR_CUDA, cudaGetErrorString(e_)); \
     } while (0)
 
-bool is_fci(const sci_ctx *c)
+// WARP needs a full-CI list (so that J is found by ranking) of at most kRankBits orbitals
+bool warp_ok(const sci_ctx *c)
 {
-    return binom_host(c->n, c->na) * binom_host(c->n, c->nb) == c->M;
+    return c->n <= kRankBits && binom_host(c->n, c->na) * binom_host(c->n, c->nb) == c->M;
 }
 
 // the items of one instance under one schedule, with a cost estimate per item
@@ -368,7 +366,7 @@ int launch(sci_batch *b, const double *C, double *S)
 {
     BCK(cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream));
     if (b->total_M > 0) BCK(cudaMemsetAsync(S, 0, sizeof(double) * b->total_M, b->stream));
-    k_batch<<<b->grid, kThreads, b->smem, b->stream>>>(b->d_inst, b->d_items, b->nitems, b->d_counter, C, S);
+    k_batch<<<b->grid, kThreads, b->smem, b->stream>>>(b->d_inst, b->d_items, b->nitems, b->d_counter, C, S, b->d_rank);
     BCK(cudaGetLastError());
     return SCI_OK;
 }
@@ -403,6 +401,7 @@ extern "C" int sci_batch_destroy(sci_batch *b)
     if (b->d_inst) cudaFree(b->d_inst);
     if (b->d_items) cudaFree(b->d_items);
     if (b->d_counter) cudaFree(b->d_counter);
+    if (b->d_rank) cudaFree(b->d_rank);
     for (cudaEvent_t e : {b->ev_in, b->ev_out, b->t0, b->t1})
         if (e) cudaEventDestroy(e);
     if (b->stream) cudaStreamDestroy(b->stream);
@@ -452,6 +451,12 @@ extern "C" int sci_batch_plan(sci_batch *b, int schedule, const double *C, doubl
     b->d_inst = nullptr;
     BCK(cudaMalloc(&b->d_inst, sizeof(Inst) * std::max(1, ni)));
     if (ni) BCK(cudaMemcpy(b->d_inst, b->host.data(), sizeof(Inst) * ni, cudaMemcpyHostToDevice));
+    if (!b->d_rank) {
+        BCK(cudaMalloc(&b->d_rank, sizeof(uint32_t) << kRankBits));
+        k_rank_table<<<1024, kThreads, 0, b->stream>>>(b->d_rank);
+        BCK(cudaGetLastError());
+        BCK(cudaStreamSynchronize(b->stream));
+    }
     // shared memory for the largest TILE window; a grid of one wave
     int maxb = 1;
     for (auto *c : b->ctxs) maxb = std::max(maxb, c->maxb2);
@@ -465,8 +470,9 @@ extern "C" int sci_batch_plan(sci_batch *b, int schedule, const double *C, doubl
 
     std::vector<float> cost(ni, 0.f);
     for (int i = 0; i < ni; i++) {
-        const bool fci = is_fci(b->ctxs[i]);
-        if (schedule == SCI_SCHED_WARP && !fci) return bfail(b, SCI_ERR_ARG, "batch_plan: WARP needs full-CI instances");
+        const bool fci = warp_ok(b->ctxs[i]);
+        if (schedule == SCI_SCHED_WARP && !fci)
+            return bfail(b, SCI_ERR_ARG, "batch_plan: WARP needs full-CI instances of at most 20 orbitals");
         if (schedule != SCI_SCHED_AUTO) {
             b->sched[i] = schedule;
             continue;
@@ -492,7 +498,8 @@ extern "C" int sci_batch_plan(sci_batch *b, int schedule, const double *C, doubl
                 if (rep == 1) BCK(cudaEventRecord(b->t0, b->stream));
                 BCK(cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream));
                 BCK(cudaMemsetAsync(S + B.off, 0, sizeof(double) * B.M, b->stream));
-                k_batch<<<b->grid, kThreads, b->smem, b->stream>>>(b->d_inst, b->d_items, b->nitems, b->d_counter, C, S);
+                k_batch<<<b->grid, kThreads, b->smem, b->stream>>>(b->d_inst, b->d_items, b->nitems, b->d_counter, C, S,
+                                                                    b->d_rank);
                 BCK(cudaGetLastError());
             }
             BCK(cudaEventRecord(b->t1, b->stream));
