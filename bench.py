@@ -56,6 +56,14 @@ def golden_pairs(w):
         return None
 
 
+def measured_peaks() -> dict:
+    """The generated peaks of this GPU pool ({} when the file is absent)."""
+    try:
+        return json.load(open(PEAKS))
+    except (OSError, ValueError):
+        return {}
+
+
 def hbm_peak():
     try:
         return float(json.load(open(PEAKS))["hbm_gbs"]), "measured"
@@ -228,6 +236,67 @@ def rdm_bench(H, w, nvec=4, reps=3):
     return out
 
 
+def blockvec_bench(M=2_000_000, k=96, a=8, reps=5):
+    """The tall-skinny products of the 8-root Davidson at its largest shapes (k = 96
+    search vectors, blocks of a = 8, M rows): CUDA-event milliseconds (L2 flushed before
+    each launch) of sci_bv_gemm_tn (P = [V T]^T T over k + a columns) and sci_bv_gemm_nn
+    (the residual R = W Y - V (Y theta) with the preconditioner epilogue), FP64 and paired
+    FP32.  Roofline: the FP64 policy is bound by the FP64 pipe, whose peak is derived as
+    2 FMA per clock per SM x SMs x the maximum SM clock; the paired policy is reported
+    against the same FP64-equivalent work."""
+    import torch
+
+    from paper_2501_18185_gb300 import sci
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    g = torch.Generator(device="cpu").manual_seed(9)
+    V = torch.randn((M, k + a), generator=g, dtype=torch.float64).to(dev)
+    W = torch.randn((M, k), generator=g, dtype=torch.float64).to(dev)
+    Y = torch.randn((k, a), generator=g, dtype=torch.float64).to(dev)
+    th = torch.linspace(-3, -1, a, dtype=torch.float64).to(dev)
+    Yt = (-(Y * th[None, :])).contiguous()
+    d = torch.randn(M, generator=g, dtype=torch.float64).to(dev)
+    P = torch.empty((k + a, a), dtype=torch.float64, device=dev)
+    R = torch.empty((M, a), dtype=torch.float64, device=dev)
+    cs = torch.zeros(a, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=dev)
+    ctx = sci.sci_create(dev.index, torch.cuda.current_stream().cuda_stream)
+    stream = torch.cuda.current_stream()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks = measured_peaks()
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp64_peak = 2 * 2 * sms * mhz * 1e6 / 1e12   # TFLOP/s
+
+    def ev_ms(fn):
+        fn()
+        out = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return statistics.median(out)
+
+    res = {"M": M, "k": k, "a": a, "fp64_peak_tflops": fp64_peak,
+           "peak_source": f"derived: 2 FP64 FMA/clk/SM x {sms} SMs x {mhz:.0f} MHz"}
+    flops_tn, flops_nn = 2.0 * M * (k + a) * a, 2.0 * M * 2 * k * a
+    for name, prec in (("f64", sci.SCI_PREC_F64), ("ds", sci.SCI_PREC_F64_DS)):
+        t_tn = ev_ms(lambda: sci.sci_bv_gemm_tn(ctx, M, k + a, a, V, k + a, V[:, k:], k + a, P, prec))
+        t_nn = ev_ms(lambda: sci.sci_bv_gemm_nn(ctx, M, a, W, k, k, Y, V, k + a, k, Yt, 0.0, R, a, d, th, cs, prec))
+        res[name] = {"tn_ms": t_tn, "nn_ms": t_nn,
+                     "tn_tflops": flops_tn / t_tn / 1e9, "nn_tflops": flops_nn / t_nn / 1e9,
+                     "tn_frac_fp64_peak": flops_tn / t_tn / 1e9 / fp64_peak,
+                     "nn_frac_fp64_peak": flops_nn / t_nn / 1e9 / fp64_peak,
+                     "tn_GBps": M * (k + a) * 8 / t_tn / 1e6, "nn_GBps": (M * 2 * k * 8 + M * a * 16) / t_nn / 1e6}
+    VT = V[:, :k + a]
+    res["cublas_f64_tn_ms"] = ev_ms(lambda: VT.T @ V[:, k:])
+    sci.sci_destroy(ctx)
+    return res
+
+
 def batch_bench(reps=10):
     """The 64 heterogeneous full-CI instances in one persistent launch: setup, autotuner
     time and choices, and CUDA-event milliseconds per batched sigma (L2 flushed before
@@ -324,6 +393,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-davidson", action="store_true",
                     help="skip the 8-root Davidson timing and the density-matrix timing")
+    ap.add_argument("--only", default=None, choices=["blockvec", "rdm", "batch", "davidson"],
+                    help="run one side section alone and print its JSON (profiling runs)")
     ap.add_argument("--prec", default="f64", choices=["f64", "ds"],
                     help="f64: FP64 FMA path; ds: paired-FP32 products/sums (FP64 tolerance)")
     args = ap.parse_args()
@@ -350,6 +421,10 @@ def main():
     torch.cuda.set_device(dev)
     build.build()
 
+    if args.only in ("blockvec", "batch"):
+        out = blockvec_bench(M=args.M or 2_000_000) if args.only == "blockvec" else batch_bench()
+        print(json.dumps({args.only: out}), flush=True)
+        return
     w = make_workload(args.workload, args.nvec, args.M)
     stream = torch.cuda.current_stream(dev)
     t = time.perf_counter()
@@ -364,6 +439,10 @@ def main():
     if gp is not None and gp != pairs:
         raise SystemExit(f"pair count {pairs} differs from the oracle's {gp}")
 
+    if args.only in ("rdm", "davidson"):
+        out = rdm_bench(H, w) if args.only == "rdm" else davidson_bench(H, w)
+        print(json.dumps({args.only: out}), flush=True)
+        return
     C = torch.from_numpy(np.ascontiguousarray(w.c)).to(dev)
     S = torch.empty_like(C)
     flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=dev)  # 256 MB > L2
@@ -465,6 +544,7 @@ def main():
     rdm = batch = None
     if not args.no_davidson and world == 1 and not w.ints.complex_:
         dav = davidson_bench(H, w)
+        dav["blockvec"] = blockvec_bench()
         rdm = rdm_bench(H, w)
         batch = batch_bench()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -125,10 +125,10 @@ k_rdm_diag(const uint64_t *__restrict__ keys, int64_t M, int norb, uint64_t ref,
 }
 
 // ------------------------------------------------------------------ singles
-template <typename TC>
+template <typename TC, int NV>
 __global__ void __launch_bounds__(kThreads)
 k_rdm_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S, const uint32_t *__restrict__ e_meta,
-              int64_t E, int norb, uint64_t ref, const TC *__restrict__ C, int nvec, int v0, int nv,
+              int64_t E, int norb, uint64_t ref, const TC *__restrict__ C, int nvec, int v0,
               const double *__restrict__ wk, TC *__restrict__ A, TC *__restrict__ Bc)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
@@ -140,12 +140,9 @@ k_rdm_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e
         const uint64_t Sk = e_S[p];
         const uint64_t part = Sk & ~ref, holes = ref & ~Sk;
         const int64_t idx = e_idx[p];
-        TC rowc[kMaxVec];
+        TC rowc[NV];
 #pragma unroll
-        for (int v = 0; v < kMaxVec; v++) {
-            zero(rowc[v]);
-            if (v < nv) rowc[v] = scale(conjv(sflip(par, C[idx * nvec + v0 + v])), wk[v0 + v]);
-        }
+        for (int v = 0; v < NV; v++) rowc[v] = scale(conjv(sflip(par, C[idx * nvec + v0 + v])), wk[v0 + v]);
         for (int64_t q = bs; q < be; q++) {
             if (q == p) continue;
             const uint32_t mq = e_meta[q];
@@ -155,8 +152,7 @@ k_rdm_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e
             TC w;
             zero(w);
 #pragma unroll
-            for (int v = 0; v < kMaxVec; v++)
-                if (v < nv) mac(w, rowc[v], sflip(parq, C[idxq * nvec + v0 + v]));
+            for (int v = 0; v < NV; v++) mac(w, rowc[v], sflip(parq, C[idxq * nvec + v0 + v]));
             const int64_t xy = (int64_t)x * norb + y;
             red(A + xy, w);
             for (uint64_t m = part; m; m &= m - 1) red(Bc + xy * norb + (__ffsll((long long)m) - 1), w);
@@ -167,12 +163,17 @@ k_rdm_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e
 }
 
 // ------------------------------------------------------------------ doubles
-template <typename TC>
+// Each unordered pair of a bucket of size s is walked once, with balanced work per lane:
+// the member at position q takes the members at q + d (mod s) for d = 1 .. (s-1)/2, and
+// for even s the member at distance s/2 is taken by the first half of the bucket.  The
+// orientation of a pair does not matter: the expansion adds both orientations.
+template <typename TC, int NV>
 __global__ void __launch_bounds__(kThreads)
 k_rdm_doubles(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_code, const uint32_t *__restrict__ e_pos,
-              int64_t E, int CH, sci::TabRule tr, uint32_t bb_off, const TC *__restrict__ C, int nvec, int v0, int nv,
+              int64_t E, int CH, sci::TabRule tr, uint32_t bb_off, const TC *__restrict__ C, int nvec, int v0,
               const double *__restrict__ wk, TC *__restrict__ dT)
 {
+    constexpr int nv = NV;
     extern __shared__ __align__(16) unsigned char smem[];
     int64_t r0, r1;
     sci::window(e_pos, E, CH, r0, r1);
@@ -196,23 +197,22 @@ k_rdm_doubles(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e
         const uint32_t code = e_code[r0 + q0], pos = e_pos[r0 + q0];
         uint32_t rowoff, colbase;
         grad_offsets(tr, sci::code_x(code), sci::code_y(code), bb_off, rowoff, colbase);
-        const int be = q0 - sci::pos_off(pos) + sci::pos_size(pos);
+        const int qp = sci::pos_off(pos), sz = sci::pos_size(pos), bs = q0 - qp;
+        const int dmax = (sz - 1) / 2 + ((sz & 1) == 0 && qp < sz / 2 ? 1 : 0);
         const uint32_t rc = sci::row_code(code);
-        TC rowc[kMaxVec];
+        TC rowc[NV];
 #pragma unroll
-        for (int v = 0; v < kMaxVec; v++) {
-            zero(rowc[v]);
-            if (v < nv) rowc[v] = scale(conjv(s_c[q0 * nv + v]), wk[v0 + v]);
-        }
+        for (int v = 0; v < NV; v++) rowc[v] = scale(conjv(s_c[q0 * nv + v]), wk[v0 + v]);
         TC *trow = dT + rowoff;
-        for (int j = q0 + 1; j < be; j++) {
-            const uint2 kc = s_kc[j];
+        int j = qp;
+        for (int d = 1; d <= dmax; d++) {
+            j = j + 1 == sz ? 0 : j + 1;
+            const uint2 kc = s_kc[bs + j];
             if (!sci::disjoint(rc, kc.x)) continue;
             TC w;
             zero(w);
 #pragma unroll
-            for (int v = 0; v < kMaxVec; v++)
-                if (v < nv) mac(w, rowc[v], s_c[j * nv + v]);
+            for (int v = 0; v < NV; v++) mac(w, rowc[v], s_c[(bs + j) * nv + v]);
             red(trow + kc.y, w);
         }
     }
@@ -305,6 +305,37 @@ int grid_for(int64_t n)
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
 }
 
+template <typename TC> struct Walk {
+    const TC *C;
+    int nvec, v0;
+    const double *wk;
+    TC *A, *Bc, *dT;  // dT == nullptr: no double-excitation walk
+    int CH;
+    size_t smem;
+    sci::TabRule tr;
+    uint32_t bb_off;
+};
+
+// the single- and double-excitation walks for one group of NV vectors
+template <typename TC, int NV>
+int launch_walks(sci_ctx *ctx, const Walk<TC> &w)
+{
+    if (ctx->e1 > 0)
+        k_rdm_singles<TC, NV><<<grid_for(ctx->e1), kThreads, 0, ctx->stream>>>(
+            ctx->e1_idx, ctx->e1_S, ctx->e1_meta, ctx->e1, ctx->norb, ctx->ref, w.C, w.nvec, w.v0, w.wk, w.A, w.Bc);
+    if (w.dT) {
+        auto kern = k_rdm_doubles<TC, NV>;
+        if (w.smem > 48 * 1024 &&
+            sci_cuda_check(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w.smem),
+                           "rdm12 attr"))
+            return SCI_ERR_CUDA;
+        const int64_t blocks = (ctx->e2 + w.CH - 1) / w.CH;
+        kern<<<(unsigned)blocks, kThreads, w.smem, ctx->stream>>>(ctx->e2_idx, ctx->e2_code, ctx->e2_pos, ctx->e2, w.CH,
+                                                                 w.tr, w.bb_off, w.C, w.nvec, w.v0, w.wk, w.dT);
+    }
+    return SCI_OK;
+}
+
 template <typename TC>
 int rdm_run(sci_ctx *ctx, const TC *C, int nvec, const double *wk_dev, TC *g1, TC *g2)
 {
@@ -345,20 +376,19 @@ int rdm_run(sci_ctx *ctx, const TC *C, int nvec, const double *wk_dev, TC *g1, T
         const int nv = std::min(kv, nvec - v0);
         k_rdm_diag<TC><<<grid_for(ctx->M), kThreads, 0, ctx->stream>>>(ctx->keys, ctx->M, norb, ctx->ref, C, nvec, v0, nv,
                                                                        wk_dev, Wt, D, DD);
-        if (ctx->e1 > 0)
-            k_rdm_singles<TC><<<grid_for(ctx->e1), kThreads, 0, ctx->stream>>>(
-                ctx->e1_idx, ctx->e1_S, ctx->e1_meta, ctx->e1, norb, ctx->ref, C, nvec, v0, nv, wk_dev, A, Bc);
-        if (g2 && ctx->e2 > 0) {
-            const size_t smem = stage_bytes(nv);
-            auto kern = k_rdm_doubles<TC>;
-            if (smem > 48 * 1024 &&
-                sci_cuda_check(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                               "rdm12 attr"))
-                return SCI_ERR_CUDA;
-            const int64_t blocks = (ctx->e2 + CH - 1) / CH;
-            kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(ctx->e2_idx, ctx->e2_code, ctx->e2_pos, ctx->e2, CH, tr,
-                                                                   bb_off, C, nvec, v0, nv, wk_dev, dT);
+        const Walk<TC> wlk{C, nvec, v0, wk_dev, A, Bc, g2 && ctx->e2 > 0 ? dT : nullptr, CH, stage_bytes(nv), tr, bb_off};
+        int rc = SCI_OK;
+        switch (nv) {
+            case 1: rc = launch_walks<TC, 1>(ctx, wlk); break;
+            case 2: rc = launch_walks<TC, 2>(ctx, wlk); break;
+            case 3: rc = launch_walks<TC, 3>(ctx, wlk); break;
+            case 4: rc = launch_walks<TC, 4>(ctx, wlk); break;
+            case 5: rc = launch_walks<TC, 5>(ctx, wlk); break;
+            case 6: rc = launch_walks<TC, 6>(ctx, wlk); break;
+            case 7: rc = launch_walks<TC, 7>(ctx, wlk); break;
+            default: rc = launch_walks<TC, 8>(ctx, wlk); break;
         }
+        if (rc) return rc;
     }
     k_rdm_expand1<TC><<<grid_for(n2), kThreads, 0, ctx->stream>>>(norb, ctx->ref, Wt, D, DD, A, Bc, g1, g2);
     if (g2) k_rdm_expand2<TC><<<grid_for(nT), kThreads, 0, ctx->stream>>>(tr, norb, nT, dT, g2);
