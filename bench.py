@@ -395,8 +395,9 @@ def main():
                     help="skip the 8-root Davidson timing and the density-matrix timing")
     ap.add_argument("--only", default=None, choices=["blockvec", "rdm", "batch", "davidson"],
                     help="run one side section alone and print its JSON (profiling runs)")
-    ap.add_argument("--prec", default="f64", choices=["f64", "ds"],
-                    help="f64: FP64 FMA path; ds: paired-FP32 products/sums (FP64 tolerance)")
+    ap.add_argument("--prec", default="f64", choices=["f64", "ds", "f32"],
+                    help="f64: FP64 FMA path; ds: paired-FP32 products/sums (FP64 tolerance); "
+                         "f32: FP32 storage of C and the tables, FP64 accumulation (real mode)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -443,15 +444,21 @@ def main():
         out = rdm_bench(H, w) if args.only == "rdm" else davidson_bench(H, w)
         print(json.dumps({args.only: out}), flush=True)
         return
-    C = torch.from_numpy(np.ascontiguousarray(w.c)).to(dev)
-    S = torch.empty_like(C)
+    C64 = torch.from_numpy(np.ascontiguousarray(w.c)).to(dev)
+    if args.prec == "f32" and w.ints.complex_:
+        raise SystemExit("--prec f32 is a real-mode precision")
+    C = C64.float() if args.prec == "f32" else C64
+    S = torch.empty_like(C64)
     flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=dev)  # 256 MB > L2
     nv = C.shape[1]
-    prec = sci.SCI_PREC_F64 if args.prec == "f64" else sci.SCI_PREC_F64_DS
+    prec = {"f64": sci.SCI_PREC_F64, "ds": sci.SCI_PREC_F64_DS, "f32": sci.SCI_PREC_F32_STORE_F64_ACC}[args.prec]
     other = sci.SCI_PREC_F64_DS if args.prec == "f64" else sci.SCI_PREC_F64
+    def vec(p):
+        return C if p == prec else C64
+
     for _ in range(args.warmup):
-        H.sigma(C, out=S, prec=prec)
-        H.sigma(C, out=S, prec=other)
+        H.sigma(vec(prec), out=S, prec=prec)
+        H.sigma(vec(other), out=S, prec=other)
     H.sync_status()
     sci.sci_profile(H.ctx, True)
 
@@ -468,7 +475,7 @@ def main():
         for _ in range(steps):
             flush.zero_()                      # evict L2 between timed steps
             ev0.record(stream)
-            H.sigma(C, out=S, prec=prec)
+            H.sigma(vec(prec), out=S, prec=prec)
             ev1.record(stream)
             ev1.synchronize()
             ms_.append(ev0.elapsed_time(ev1))
@@ -500,8 +507,8 @@ def main():
     value = world * pairs * args.steps / (total_ms / 1e3)
 
     # end to end through the public API with host buffers (pinned), copies inside
-    Ch = torch.from_numpy(np.ascontiguousarray(w.c)).pin_memory()
-    Sh = torch.empty_like(Ch).pin_memory()
+    Ch = torch.from_numpy(np.ascontiguousarray(w.c, dtype=np.float32 if args.prec == "f32" else None)).pin_memory()
+    Sh = torch.empty(tuple(C64.shape), dtype=C64.dtype).pin_memory()
     sci.sci_sigma_host(H.ctx, Ch, Sh, nv, prec)
     e2e_t = []
     for _ in range(max(3, min(args.steps, 10))):
@@ -512,9 +519,10 @@ def main():
         e2e_t.append(time.perf_counter() - t)
     e2e = world * pairs / statistics.mean(e2e_t)
     nbytes = Ch.numel() * Ch.element_size()
+    nbytes_out = Sh.numel() * Sh.element_size()
 
     # roofline of the dominant kernel (double excitations): algorithmic bytes per launch
-    sb = 16 if w.ints.complex_ else 8
+    sb = 16 if w.ints.complex_ else (4 if args.prec == "f32" else 8)
     dbl_ms = statistics.mean(k[1] for k in kern)
     sgl_ms = statistics.mean(k[2] for k in kern)
     init_ms = statistics.mean(k[0] for k in kern)
@@ -529,7 +537,9 @@ def main():
         except ValueError:
             traffic = None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": "k_doubles", "peak_source": peak_kind,
+            "traffic": traffic if args.prec == "f64" else None,
+            "kernel": {"f64": "k_doubles", "ds": "k_doubles_ds", "f32": "k_doubles_f32"}[args.prec],
+            "peak_source": peak_kind,
             "algorithmic_bytes_per_launch": alg_bytes,
             "kernel_ms": {"init": init_ms, "doubles": dbl_ms, "singles": sgl_ms}}
 
@@ -549,12 +559,15 @@ def main():
         batch = batch_bench()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "c128" if w.ints.complex_ else "f64", "data": "synthetic",
+            "vs_baseline": None,
+            "dtype": "c128" if w.ints.complex_ else {"f64": "f64", "ds": "f64", "f32": "f32-store/f64-acc"}[args.prec],
+            "data": "synthetic",
             "config": {"workload": w.name, "M": w.M, "nvec": nv, "pairs_per_step": pairs,
                        "l2": "flushed between timed steps (256 MB write)", "setup_s": round(setup_s, 3),
                        "parallelism": f"replicas{world}" if world > 1 else "single"},
-            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
-            "gpu_launches": args.steps * (1 + 2 * ((nv + 7) // 8 if not w.ints.complex_ else (nv + 3) // 4)),
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes_out},
+            "gpu_launches": args.steps * (1 + {"f64": 2, "ds": 4, "f32": 3}[args.prec]
+                                          * ((nv + 7) // 8 if not w.ints.complex_ else (nv + 3) // 4)),
             "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "prec": args.prec,
             "other_prec": variant, "davidson": dav, "rdm": rdm, "batch": batch}
     print(json.dumps(line), flush=True)
