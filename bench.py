@@ -297,6 +297,41 @@ def blockvec_bench(M=2_000_000, k=96, a=8, reps=5):
     return res
 
 
+def pt2_bench(sizes=(60_000, 200_000, 1_000_000, 2_000_000), table_gb=48.0):
+    """Epstein-Nesbet PT2 of the ground state on spaces of the bench recipe: (E0, c) from
+    the FP64 block Davidson (residual 1e-6), then exact sci_enpt2 (no screening).  Wall
+    seconds of sci_enpt2 (synchronous), batches, distinct determinants of W summed, the
+    generated contributions (M x excitations per determinant) and E2[Q]."""
+    import torch
+
+    from paper_2501_18185_gb300 import sci
+    from paper_2501_18185_gb300 import workloads as W
+
+    out = []
+    for M in sizes:
+        w = W.selected_30o(M=M)
+        H = sci.Hamiltonian.from_workload(w)
+        from paper_2501_18185_gb300.davidson import davidson
+
+        r = davidson(lambda X: H.sigma(X.contiguous()), H.diagonal(), nroots=1, tol=1e-6, max_iter=400)
+        c = r.vectors.contiguous()
+        E0 = [float(r.energies[0])]
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        e2w, e2p, e2q, st = H.enpt2(c, E0, table_bytes=int(table_gb * (1 << 30)))
+        dt = time.perf_counter() - t
+        n, na, nb = w.n, w.n_alpha, w.n_beta
+        ua, ub = n - na, n - nb
+        per = na * ua + nb * ub + na * (na - 1) // 2 * (ua * (ua - 1) // 2) + nb * (nb - 1) // 2 * (ub * (ub - 1) // 2) \
+            + na * ua * nb * ub
+        out.append({"M": M, "seconds": dt, "davidson_converged": bool(r.converged), "E0": E0[0],
+                    "E0_plus_E2": E0[0] + float(e2q[0]), "E2_Q": float(e2q[0]), "E2_W": float(e2w[0]),
+                    "E2_P": float(e2p[0]), "generated": M * per, "generated_per_s": M * per / dt, **st})
+        del H
+        torch.cuda.empty_cache()
+    return out
+
+
 def batch_bench(reps=10):
     """The 64 heterogeneous full-CI instances in one persistent launch: setup, autotuner
     time and choices, and CUDA-event milliseconds per batched sigma (L2 flushed before
@@ -393,7 +428,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-davidson", action="store_true",
                     help="skip the 8-root Davidson timing and the density-matrix timing")
-    ap.add_argument("--only", default=None, choices=["blockvec", "rdm", "batch", "davidson"],
+    ap.add_argument("--only", default=None, choices=["blockvec", "rdm", "batch", "davidson", "pt2"],
                     help="run one side section alone and print its JSON (profiling runs)")
     ap.add_argument("--prec", default="f64", choices=["f64", "ds", "f32"],
                     help="f64: FP64 FMA path; ds: paired-FP32 products/sums (FP64 tolerance); "
@@ -422,8 +457,10 @@ def main():
     torch.cuda.set_device(dev)
     build.build()
 
-    if args.only in ("blockvec", "batch"):
-        out = blockvec_bench(M=args.M or 2_000_000) if args.only == "blockvec" else batch_bench()
+    if args.only in ("blockvec", "batch", "pt2"):
+        out = (blockvec_bench(M=args.M or 2_000_000) if args.only == "blockvec" else
+               batch_bench() if args.only == "batch" else
+               pt2_bench(sizes=(args.M,) if args.M else (60_000, 200_000, 1_000_000, 2_000_000)))
         print(json.dumps({args.only: out}), flush=True)
         return
     w = make_workload(args.workload, args.nvec, args.M)
@@ -551,12 +588,13 @@ def main():
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(w)
     dav = None
-    rdm = batch = None
+    rdm = batch = pt2 = None
     if not args.no_davidson and world == 1 and not w.ints.complex_:
         dav = davidson_bench(H, w)
         dav["blockvec"] = blockvec_bench()
         rdm = rdm_bench(H, w)
         batch = batch_bench()
+        pt2 = pt2_bench(sizes=(200_000,))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
@@ -569,7 +607,7 @@ def main():
             "gpu_launches": args.steps * (1 + {"f64": 2, "ds": 4, "f32": 3}[args.prec]
                                           * ((nv + 7) // 8 if not w.ints.complex_ else (nv + 3) // 4)),
             "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "prec": args.prec,
-            "other_prec": variant, "davidson": dav, "rdm": rdm, "batch": batch}
+            "other_prec": variant, "davidson": dav, "rdm": rdm, "batch": batch, "pt2": pt2}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

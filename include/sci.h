@@ -214,6 +214,32 @@ int sci_kernel_times(sci_ctx *ctx, float *ms, int n);
  * SCI_ERR_NOMEM. */
 int sci_rdm12(sci_ctx *ctx, const void *C, int nvec, const double *weights, void *rdm1, void *rdm2);
 
+/* Epstein-Nesbet second-order energy of roots of the variational space (Sec. 2.4,
+ * constraint-based ENPT2, with P_m = P):
+ *   E2_k[Q] = E2_k[W] - E2_k[P]                                         (Eq. PT2final)
+ *   E2_k[W] = sum_{I in W} (sum_{J in P} H_IJ c_Jk)^2 / (E0_k - H_II)    (Eq. EW1)
+ *   E2_k[P] = sum_{I in P} (<I|H|c_k> - c_Ik H_II)^2 / (E0_k - H_II)     (Eq. EP1)
+ * over W, the determinants within a single or double excitation of the list.  Real
+ * spin-orbital mode, n <= 32.
+ *   C: device, [M][nroots] doubles, 1 <= nroots <= 8 (need not be normalised; the
+ *      formulas use c as given, so pass normalised eigenvectors for energies).
+ *   E0: HOST, nroots doubles (the zeroth-order energies E0_k).
+ *   eps: screening; a generated contribution with |H_IJ| max_k |c_Jk| < eps is dropped
+ *      (0 = exact).
+ *   table_bytes: device memory for the hash table of one batch (8 + 8 nroots bytes per
+ *      entry, capacity the largest power of two within the budget).  W is split into
+ *      2^t batches (t <= 10) so that a batch's generated excitations fill at most 60% of
+ *      it; a batch that still overflows (or probes too far) restarts the sum with twice
+ *      the batches.
+ *   E2: HOST, 3 x nroots doubles, overwritten: E2[W], then E2[P], then E2[Q].
+ *   stats: HOST, 4 int64 or NULL: batches, distinct W determinants summed, passes run,
+ *      table capacity.
+ * Synchronous.  Allocates sigma scratch (M x nroots doubles) and the table for the call.
+ * Errors: SCI_ERR_ARG (mode, sizes, NULL), SCI_ERR_STATE, SCI_ERR_NOMEM, SCI_ERR_OVERFLOW
+ * (the table is too small even at 1024 batches). */
+int sci_enpt2(sci_ctx *ctx, const double *C, int nroots, const double *E0, double eps,
+              size_t table_bytes, double *E2, int64_t *stats);
+
 /* ---------------------------------------------------------------- batched instances
  * Many small real spin-orbital Hamiltonians (each a sci_ctx with integrals and
  * determinants set) applied to their vectors in ONE persistent kernel launch, the GPU

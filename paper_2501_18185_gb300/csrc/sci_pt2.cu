@@ -1,0 +1,513 @@
+// Epstein-Nesbet second-order energies (Sec. 2.4, constraint-based ENPT2) on the GPU.
+//
+// For the roots (E0_k, c_k) of the variational space P (here P_m = P):
+//   E2_k[Q] = E2_k[W] - E2_k[P]                                      (Eq. PT2final)
+//   E2_k[W] = sum_{I in W} (sum_{J in P, J != I} H_IJ c_Jk)^2 / (E0_k - H_II)     (Eq. EW1)
+//   E2_k[P] = sum_{I in P} (<I|H|c_k> - c_Ik H_II)^2 / (E0_k - H_II)              (Eq. EP1)
+// where W is every determinant a single or double excitation away from some J in P.
+// The W - P form avoids testing membership of each generated determinant in P.
+//
+// E2[W] is accumulated in batches W_b, disjoint by a constraint on the determinant I, so
+// that the numerators of one batch fit a hash table in device memory (the memory-bounded
+// pipeline of the paper's constraint-based algorithm).  The constraint here is a linear
+// code over GF(2) of I's beta string, f(I_beta) = XOR of g(o) over its occupied orbitals,
+// with g a random t-bit code per orbital: the batch of an excitation of J follows from
+// f(J_beta) and the codes of the moved beta orbitals alone, so a warp that owns J reaches
+// exactly the excitations of the current batch --
+//   alpha singles and alpha-alpha doubles: all of them when f(J_beta) = b;
+//   beta singles j -> v (and the alpha-beta doubles built on them): g(j) ^ g(v) = b ^ f(J_beta);
+//   beta-beta doubles j1 j2 -> b1 < b2: g(b2) = b ^ f(J_beta) ^ g(j1) ^ g(j2) ^ g(b1),
+// with the orbitals grouped by code so that each lookup is a short list.
+// Each generated (I, H_IJ c_J) is added to the table entry of I (open addressing, linear
+// probing bounded by kMaxProbe, FP64 atomic adds); then every entry is evaluated with
+//   H_II = E_ref - sum_{i in holes} F_ii + sum_{a in particles} F_aa
+//          + sum_{pairs in holes} G + sum_{pairs in particles} G - sum_{holes x particles} G,
+// F the Fock diagonal of the reference and G_pq = (pp|qq) - (pq|qp): O(level^2) per I.
+// Element formulas and phases are those of the sigma kernels (bra I, ket J).
+#include <algorithm>
+#include <cstring>
+#include <random>
+#include <vector>
+
+#include "sci_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr uint64_t kEmpty = ~0ull;
+constexpr int kMaxProbe = 1 << 12;
+constexpr int kMaxBits = 10;   // at most 1024 batches
+constexpr int kMaxPairs = 32 * 31 / 2;
+
+struct Pt2 {
+    int n, norb, na, nb;
+    uint64_t ref;
+    const double *tab, *fref, *g_so;
+    const double *fdiag, *G;  // [norb], [norb][norb]
+    const double *Eref;
+    uint32_t gcode[32];       // beta-orbital codes
+    uint8_t obc[32];          // the n beta orbitals sorted by code
+    uint8_t cstart[(1 << kMaxBits) + 1];  // first index in obc of each code
+    uint64_t *keys;
+    double *vals;
+    uint64_t mask;            // capacity - 1
+    unsigned long long *count;
+    unsigned long long limit;
+    int *flag;
+    double eps;
+};
+
+__device__ __forceinline__ double sflip(bool f, double a)
+{
+    return __longlong_as_double(__double_as_longlong(a) ^ ((long long)f << 63));
+}
+__device__ __forceinline__ int below(uint64_t K, int x) { return __popcll(K & ((1ull << x) - 1)); }
+__device__ __forceinline__ uint64_t mix64(uint64_t x)
+{
+    x ^= x >> 33;
+    x *= 0xff51afd7ed558ccdull;
+    x ^= x >> 33;
+    x *= 0xc4ceb9fe1a85ec53ull;
+    x ^= x >> 33;
+    return x;
+}
+
+// H_IJ for I = J - {i, j} + {a, b} (i < j, a < b, spin-orbital indices)
+__device__ __forceinline__ double h_double(const Pt2 &p, uint64_t J, int i, int j, int a, int b)
+{
+    const uint64_t K = J & ~(1ull << i) & ~(1ull << j);
+    uint32_t rowoff, colbase, r2, c2;
+    const sci::TabRule tr{0, p.n};
+    sci::pair_offsets(tr, a, b, rowoff, r2);      // bra (I) extras
+    sci::pair_offsets(tr, i, j, c2, colbase);     // ket (J) extras
+    const bool ph = (below(K, a) + below(K, b) + below(K, i) + below(K, j)) & 1;
+    return sflip(ph, __ldg(p.tab + rowoff + colbase));
+}
+
+// H_IJ for I = J - {i} + {a}
+__device__ __forceinline__ double h_single(const Pt2 &p, uint64_t J, int i, int a)
+{
+    const uint64_t S = J & ~(1ull << i);
+    const int norb = p.norb;
+    double f = __ldg(p.fref + i * norb + a);
+    const uint64_t part = S & ~p.ref, holes = p.ref & ~S;
+    for (uint64_t m = part; m; m &= m - 1) f += __ldg(p.g_so + ((int64_t)(__ffsll((long long)m) - 1) * norb + i) * norb + a);
+    for (uint64_t m = holes; m; m &= m - 1) f -= __ldg(p.g_so + ((int64_t)(__ffsll((long long)m) - 1) * norb + i) * norb + a);
+    const bool ph = (below(S, a) + below(S, i)) & 1;
+    return sflip(ph, f);
+}
+
+template <int R>
+__device__ __forceinline__ void insert(const Pt2 &p, uint64_t I, double hij, const double *cJ, double cmax)
+{
+    if (p.eps > 0.0 && fabs(hij) * cmax < p.eps) return;
+    uint64_t s = mix64(I) & p.mask;
+    for (int probe = 0; probe < kMaxProbe; probe++) {
+        uint64_t k = p.keys[s];
+        if (k == kEmpty) {
+            k = atomicCAS(reinterpret_cast<unsigned long long *>(p.keys + s), (unsigned long long)kEmpty,
+                          (unsigned long long)I);
+            if (k == kEmpty) {
+                if (atomicAdd(p.count, 1ull) >= p.limit) atomicOr(p.flag, 1);
+                k = I;
+            }
+        }
+        if (k == I) {
+#pragma unroll
+            for (int v = 0; v < R; v++) atomicAdd(p.vals + s * R + v, hij * cJ[v]);
+            return;
+        }
+        s = (s + 1) & p.mask;
+    }
+    atomicOr(p.flag, 2);  // probe limit: the table is too full
+}
+
+__device__ __forceinline__ uint32_t code_of(const uint32_t *g, uint32_t s)
+{
+    uint32_t c = 0;
+    for (; s; s &= s - 1) c ^= g[__ffs((int)s) - 1];
+    return c;
+}
+
+// warp per determinant J of P: the excitations of J that fall in batch `batch`
+template <int R>
+__global__ void __launch_bounds__(kThreads)
+k_pt2_gen(const uint64_t *__restrict__ Pkeys, int64_t M, const double *__restrict__ C, Pt2 p, uint32_t batch, int tbits)
+{
+    __shared__ uint8_t s_orb[kWarps][128];      // occ alpha | vir alpha | occ beta | vir beta
+    __shared__ uint16_t s_list[kWarps][32 * 32]; // beta singles of this batch (j | v << 8)
+    __shared__ uint16_t s_pair[kMaxPairs];       // P -> (a, b)
+    __shared__ uint8_t s_cstart[(1 << kMaxBits) + 1];
+    __shared__ uint8_t s_obc[32];                // beta orbitals sorted by code
+    __shared__ uint32_t s_g[32];                 // beta-orbital codes
+    __shared__ int s_nl[kWarps];
+    for (int P = threadIdx.x; P < kMaxPairs; P += blockDim.x) {
+        int b = 1;
+        while ((b + 1) * b / 2 <= P) b++;
+        s_pair[P] = (uint16_t)((P - b * (b - 1) / 2) | (b << 8));
+    }
+    for (int c = threadIdx.x; c <= (1 << tbits); c += blockDim.x) s_cstart[c] = p.cstart[c];
+    if (threadIdx.x < 32) s_obc[threadIdx.x] = p.obc[threadIdx.x], s_g[threadIdx.x] = p.gcode[threadIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint8_t *orb = s_orb[w];
+    const int n = p.n, na = p.na, nb = p.nb, ua = n - na, ub = n - nb;
+    const uint32_t full = (uint32_t)((1ull << n) - 1);
+    const int64_t warps_total = (int64_t)gridDim.x * kWarps;
+    for (int64_t J = (int64_t)blockIdx.x * kWarps + w; J < M; J += warps_total) {
+        const uint64_t key = Pkeys[J];
+        const uint32_t oa = (uint32_t)(key & full), ob = (uint32_t)(key >> n);
+        const uint32_t va = full & ~oa, vb = full & ~ob;
+        double cJ[R], cmax = 0.0;
+#pragma unroll
+        for (int v = 0; v < R; v++) cJ[v] = C[J * R + v], cmax = fmax(cmax, fabs(cJ[v]));
+        __syncwarp();
+        if (lane < n) {
+            const uint32_t lm = (1u << lane) - 1;
+            if ((oa >> lane) & 1) orb[__popc(oa & lm)] = (uint8_t)lane;
+            else orb[32 + __popc(va & lm)] = (uint8_t)lane;
+            if ((ob >> lane) & 1) orb[64 + __popc(ob & lm)] = (uint8_t)lane;
+            else orb[96 + __popc(vb & lm)] = (uint8_t)lane;
+        }
+        __syncwarp();
+        const uint32_t target = batch ^ code_of(s_g, ob);
+
+        // alpha singles and alpha-alpha doubles: the beta string is unchanged
+        if (target == 0) {
+            const int c0 = na * ua, qa = ua * (ua - 1) / 2, c2 = na * (na - 1) / 2 * qa;
+            for (int t = lane; t < c0 + c2; t += 32) {
+                if (t < c0) {
+                    const int i = orb[t / ua], a = orb[32 + t % ua];
+                    insert<R>(p, (key & ~(1ull << i)) | (1ull << a), h_single(p, key, i, a), cJ, cmax);
+                } else {
+                    const int s = t - c0;
+                    const uint16_t po = s_pair[s / qa], pv = s_pair[s % qa];
+                    const int i = orb[po & 0xFF], j = orb[po >> 8], a = orb[32 + (pv & 0xFF)], b = orb[32 + (pv >> 8)];
+                    const uint64_t I = (key & ~(1ull << i) & ~(1ull << j)) | (1ull << a) | (1ull << b);
+                    insert<R>(p, I, h_double(p, key, i, j, a, b), cJ, cmax);
+                }
+            }
+        }
+
+        // beta singles j -> v of this batch (g(v) = target ^ g(j)), and the alpha-beta
+        // doubles built on them
+        if (lane == 0) s_nl[w] = 0;
+        __syncwarp();
+        if (lane < nb) {
+            const int j = orb[64 + lane];
+            const uint32_t c = target ^ s_g[j];
+            for (int q = s_cstart[c]; q < s_cstart[c + 1]; q++) {
+                const int v = s_obc[q];
+                if ((ob >> v) & 1) continue;
+                const int slot = atomicAdd(&s_nl[w], 1);
+                s_list[w][slot] = (uint16_t)(j | (v << 8));
+            }
+        }
+        __syncwarp();
+        const int nl = s_nl[w], c0 = na * ua;
+        for (int t = lane; t < nl * (1 + c0); t += 32) {
+            const uint16_t e = s_list[w][t / (1 + c0)];
+            const int jb = n + (e & 0xFF), vb_ = n + (e >> 8);
+            const int s = t % (1 + c0);
+            if (s == 0) {
+                insert<R>(p, (key & ~(1ull << jb)) | (1ull << vb_), h_single(p, key, jb, vb_), cJ, cmax);
+            } else {
+                const int i = orb[(s - 1) / ua], a = orb[32 + (s - 1) % ua];
+                const uint64_t I = (key & ~(1ull << i) & ~(1ull << jb)) | (1ull << a) | (1ull << vb_);
+                insert<R>(p, I, h_double(p, key, i, jb, a, vb_), cJ, cmax);
+            }
+        }
+
+        // beta-beta doubles j1 < j2 -> b1 < b2: for each occupied pair and first virtual
+        // b1, the second virtual has code target ^ g(j1) ^ g(j2) ^ g(b1)
+        const int pb = nb * (nb - 1) / 2;
+        for (int t = lane; t < pb * ub; t += 32) {
+            const uint16_t po = s_pair[t / ub];
+            const int j1 = orb[64 + (po & 0xFF)], j2 = orb[64 + (po >> 8)], b1 = orb[96 + t % ub];
+            const uint32_t c = target ^ s_g[j1] ^ s_g[j2] ^ s_g[b1];
+            for (int q = s_cstart[c]; q < s_cstart[c + 1]; q++) {
+                const int b2 = s_obc[q];
+                if (b2 <= b1 || ((ob >> b2) & 1)) continue;
+                const uint64_t I = (key & ~(1ull << (n + j1)) & ~(1ull << (n + j2))) | (1ull << (n + b1)) | (1ull << (n + b2));
+                insert<R>(p, I, h_double(p, key, n + j1, n + j2, n + b1, n + b2), cJ, cmax);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// sum over the table entries of num^2 / (E0 - H_II)
+template <int R>
+__global__ void __launch_bounds__(kThreads)
+k_pt2_eval(Pt2 p, uint64_t cap, const double *__restrict__ E0, double *__restrict__ out)
+{
+    __shared__ double sG[64 * 64];
+    __shared__ double sF[64];
+    __shared__ double red[kWarps][R];
+    const int norb = p.norb;
+    for (int t = threadIdx.x; t < norb * norb; t += blockDim.x) sG[t] = p.G[t];
+    for (int t = threadIdx.x; t < norb; t += blockDim.x) sF[t] = p.fdiag[t];
+    __syncthreads();
+    const double Eref = *p.Eref;
+    double acc[R];
+#pragma unroll
+    for (int v = 0; v < R; v++) acc[v] = 0.0;
+    for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < cap; s += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t I = p.keys[s];
+        if (I == kEmpty) continue;
+        const uint64_t H = p.ref & ~I, Pm = I & ~p.ref;
+        double e = Eref;
+        for (uint64_t m = H; m; m &= m - 1) {
+            const int i = __ffsll((long long)m) - 1;
+            e -= sF[i];
+            for (uint64_t m2 = m & (m - 1); m2; m2 &= m2 - 1) e += sG[i * norb + __ffsll((long long)m2) - 1];
+            for (uint64_t m2 = Pm; m2; m2 &= m2 - 1) e -= sG[i * norb + __ffsll((long long)m2) - 1];
+        }
+        for (uint64_t m = Pm; m; m &= m - 1) {
+            const int a = __ffsll((long long)m) - 1;
+            e += sF[a];
+            for (uint64_t m2 = m & (m - 1); m2; m2 &= m2 - 1) e += sG[a * norb + __ffsll((long long)m2) - 1];
+        }
+#pragma unroll
+        for (int v = 0; v < R; v++) {
+            const double num = p.vals[s * R + v];
+            acc[v] += num * num / (E0[v] - e);
+        }
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int v = 0; v < R; v++) {
+        double x = acc[v];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) red[w][v] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < R) {
+        double x = 0.0;
+        for (int i = 0; i < kWarps; i++) x += red[i][threadIdx.x];
+        atomicAdd(out + threadIdx.x, x);
+    }
+}
+
+// E2[P] of Eq. EP1 from sigma = H c and the diagonal
+template <int R>
+__global__ void __launch_bounds__(kThreads)
+k_pt2_p(int64_t M, const double *__restrict__ C, const double *__restrict__ S, const double *__restrict__ hdiag,
+        const double *__restrict__ E0, double *__restrict__ out)
+{
+    __shared__ double red[kWarps][R];
+    double acc[R];
+#pragma unroll
+    for (int v = 0; v < R; v++) acc[v] = 0.0;
+    for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < M; I += (int64_t)gridDim.x * blockDim.x) {
+        const double d = hdiag[I];
+#pragma unroll
+        for (int v = 0; v < R; v++) {
+            const double num = S[I * R + v] - C[I * R + v] * d;
+            acc[v] += num * num / (E0[v] - d);
+        }
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int v = 0; v < R; v++) {
+        double x = acc[v];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) red[w][v] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < R) {
+        double x = 0.0;
+        for (int i = 0; i < kWarps; i++) x += red[i][threadIdx.x];
+        atomicAdd(out + threadIdx.x, x);
+    }
+}
+
+// G = (pp|qq) - (pq|qp) without the diagonal, the reference Fock diagonal and E_ref
+__global__ void k_pt2_setup(int norb, uint64_t ref, const double *__restrict__ h_so, const double *__restrict__ jd,
+                            const double *__restrict__ kd, double *__restrict__ G, double *__restrict__ fdiag,
+                            double *__restrict__ Eref)
+{
+    for (int t = threadIdx.x; t < norb * norb; t += blockDim.x) {
+        const int a = t / norb, b = t % norb;
+        G[t] = a == b ? 0.0 : jd[t] - kd[t];
+    }
+    __syncthreads();
+    for (int a = threadIdx.x; a < norb; a += blockDim.x) {
+        double f = h_so[a * norb + a];
+        for (uint64_t m = ref; m; m &= m - 1) f += G[a * norb + __ffsll((long long)m) - 1];
+        fdiag[a] = f;
+    }
+    if (threadIdx.x == 0) {
+        double e = 0.0;
+        for (uint64_t m = ref; m; m &= m - 1) {
+            const int i = __ffsll((long long)m) - 1;
+            e += h_so[i * norb + i];
+            for (uint64_t m2 = m & (m - 1); m2; m2 &= m2 - 1) e += G[i * norb + __ffsll((long long)m2) - 1];
+        }
+        *Eref = e;
+    }
+}
+
+int grid_for(int64_t n)
+{
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, 152 * 8));
+}
+
+template <int R>
+int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t table_bytes, double *E2, int64_t *stats)
+{
+    const int64_t M = ctx->M;
+    const int n = ctx->n, norb = ctx->norb, na = ctx->na, nb = ctx->nb;
+    cudaStream_t st = ctx->stream;
+    // scratch: sigma [M][R], E0 [R], results W/P [2R], G, fdiag, Eref, count, flag
+    double *S = nullptr, *small = nullptr;
+    uint64_t *keys = nullptr;
+    double *vals = nullptr;
+    int rc = SCI_OK;
+    auto cleanup = [&]() {
+        if (S) cudaFree(S);
+        if (small) cudaFree(small);
+        if (keys) cudaFree(keys);
+        if (vals) cudaFree(vals);
+    };
+    const size_t nsmall = (size_t)R * 3 + (size_t)norb * norb + norb + 1 + 2;
+    if (cudaMalloc(&S, sizeof(double) * std::max<int64_t>(1, M) * R) != cudaSuccess ||
+        cudaMalloc(&small, sizeof(double) * nsmall) != cudaSuccess) {
+        cleanup();
+        return sci_fail(ctx, SCI_ERR_NOMEM, "enpt2: scratch");
+    }
+    double *dE0 = small, *outW = small + R, *outP = small + 2 * R, *G = small + 3 * R, *fdiag = G + norb * norb,
+           *Eref = fdiag + norb;
+    unsigned long long *count = reinterpret_cast<unsigned long long *>(Eref + 1);
+    int *flag = reinterpret_cast<int *>(count + 1);
+    if (sci_cuda_check(ctx, cudaMemsetAsync(small, 0, sizeof(double) * nsmall, st), "enpt2 memset") ||
+        sci_cuda_check(ctx, cudaMemcpyAsync(dE0, E0h, sizeof(double) * R, cudaMemcpyHostToDevice, st), "enpt2 E0")) {
+        cleanup();
+        return SCI_ERR_CUDA;
+    }
+    // E2[P]: one FP64 sigma
+    if (M > 0) {
+        rc = sci_launch_sigma(ctx, C, S, R, SCI_PREC_F64);
+        if (rc) {
+            cleanup();
+            return rc;
+        }
+        k_pt2_p<R><<<grid_for(M), kThreads, 0, st>>>(M, C, S, ctx->hdiag, dE0, outP);
+    }
+    k_pt2_setup<<<1, 256, 0, st>>>(norb, ctx->ref, (const double *)ctx->h_so, (const double *)ctx->jd,
+                                    (const double *)ctx->kd, G, fdiag, Eref);
+    // the table: capacity a power of two within the budget
+    const size_t slot = sizeof(uint64_t) + sizeof(double) * R;
+    uint64_t cap = 1ull << 16;
+    while ((cap << 1) * slot <= table_bytes) cap <<= 1;
+    if (cudaMalloc(&keys, cap * sizeof(uint64_t)) != cudaSuccess || cudaMalloc(&vals, cap * sizeof(double) * R) != cudaSuccess) {
+        cleanup();
+        return sci_fail(ctx, SCI_ERR_NOMEM, "enpt2: hash table");
+    }
+    // batches: the generated excitations (an upper bound on the distinct determinants)
+    // split so that one batch fills at most 60% of the table
+    const int64_t ua = n - na, ub = n - nb;
+    const int64_t per = na * ua + nb * ub + (int64_t)na * (na - 1) / 2 * (ua * (ua - 1) / 2) +
+                        (int64_t)nb * (nb - 1) / 2 * (ub * (ub - 1) / 2) + (int64_t)na * ua * nb * ub;
+    const double total = (double)M * (double)per;
+    int tbits = 0;
+    while (tbits < kMaxBits && total / (double)(1ull << tbits) > 0.6 * (double)cap) tbits++;
+    if (total / (double)(1ull << tbits) > 0.6 * (double)cap) {
+        cleanup();
+        return sci_fail(ctx, SCI_ERR_OVERFLOW, "enpt2: hash table too small for 1024 batches");
+    }
+    Pt2 p{};
+    p.n = n, p.norb = norb, p.na = na, p.nb = nb, p.ref = ctx->ref;
+    p.tab = (const double *)ctx->tab, p.fref = (const double *)ctx->fref, p.g_so = (const double *)ctx->g_so;
+    p.fdiag = fdiag, p.G = G, p.Eref = Eref;
+    p.keys = keys, p.vals = vals, p.mask = cap - 1, p.count = count, p.flag = flag;
+    p.limit = (unsigned long long)(0.85 * (double)cap);
+    p.eps = eps;
+    int64_t passes = 0, distinct = 0;
+    for (;;) {
+        std::mt19937 rng(20250130u + (unsigned)tbits);
+        for (int o = 0; o < 32; o++) p.gcode[o] = tbits ? (uint32_t)(rng() & ((1u << tbits) - 1)) : 0u;
+        {   // orbitals 0..n-1 grouped by code
+            std::vector<int> cnt((1 << tbits) + 1, 0);
+            for (int o = 0; o < n; o++) cnt[p.gcode[o] + 1]++;
+            for (int c = 1; c <= (1 << tbits); c++) cnt[c] += cnt[c - 1];
+            for (int c = 0; c <= (1 << tbits); c++) p.cstart[c] = (uint8_t)cnt[c];
+            std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+            for (int o = 0; o < n; o++) p.obc[fill[p.gcode[o]]++] = (uint8_t)o;
+        }
+        bool overflow = false;
+        distinct = 0;
+        if (sci_cuda_check(ctx, cudaMemsetAsync(outW, 0, sizeof(double) * R, st), "enpt2 memset")) {
+            cleanup();
+            return SCI_ERR_CUDA;
+        }
+        for (uint32_t b = 0; b < (1u << tbits) && !overflow; b++) {
+            if (sci_cuda_check(ctx, cudaMemsetAsync(keys, 0xFF, cap * sizeof(uint64_t), st), "enpt2 keys") ||
+                sci_cuda_check(ctx, cudaMemsetAsync(vals, 0, cap * sizeof(double) * R, st), "enpt2 vals") ||
+                sci_cuda_check(ctx, cudaMemsetAsync(count, 0, sizeof(unsigned long long) + sizeof(int) * 2, st), "enpt2 count")) {
+                cleanup();
+                return SCI_ERR_CUDA;
+            }
+            if (M > 0)
+                k_pt2_gen<R><<<(unsigned)std::min<int64_t>((M + kWarps - 1) / kWarps, 152 * 16), kThreads, 0, st>>>(
+                    ctx->keys, M, C, p, b, tbits);
+            k_pt2_eval<R><<<grid_for((int64_t)std::min<uint64_t>(cap, 1ull << 40)), kThreads, 0, st>>>(p, cap, dE0, outW);
+            unsigned long long hc[2] = {0, 0};
+            if (sci_cuda_check(ctx, cudaMemcpyAsync(hc, count, sizeof(hc), cudaMemcpyDeviceToHost, st), "enpt2 flag") ||
+                sci_cuda_check(ctx, cudaStreamSynchronize(st), "enpt2 pass")) {
+                cleanup();
+                return SCI_ERR_CUDA;
+            }
+            const int f = (int)(hc[1] & 0xFFFFFFFFull);
+            distinct += (int64_t)hc[0];
+            passes++;
+            overflow = f != 0;
+        }
+        if (!overflow) break;
+        if (++tbits > kMaxBits) {
+            cleanup();
+            return sci_fail(ctx, SCI_ERR_OVERFLOW, "enpt2: a batch overflowed the hash table at 1024 batches");
+        }
+    }
+    double hw[R], hp[R];
+    if (sci_cuda_check(ctx, cudaMemcpyAsync(hw, outW, sizeof(hw), cudaMemcpyDeviceToHost, st), "enpt2 W") ||
+        sci_cuda_check(ctx, cudaMemcpyAsync(hp, outP, sizeof(hp), cudaMemcpyDeviceToHost, st), "enpt2 P") ||
+        sci_cuda_check(ctx, cudaStreamSynchronize(st), "enpt2 result")) {
+        cleanup();
+        return SCI_ERR_CUDA;
+    }
+    for (int v = 0; v < R; v++) E2[v] = hw[v], E2[R + v] = hp[v], E2[2 * R + v] = hw[v] - hp[v];
+    if (stats) {
+        stats[0] = 1ll << tbits;
+        stats[1] = distinct;
+        stats[2] = passes;
+        stats[3] = (int64_t)cap;
+    }
+    cleanup();
+    return SCI_OK;
+}
+
+}  // namespace
+
+extern "C" int sci_enpt2(sci_ctx *ctx, const double *C, int nroots, const double *E0, double eps, size_t table_bytes,
+                         double *E2, int64_t *stats)
+{
+    if (!ctx) return SCI_ERR_ARG;
+    if (!ctx->have_ints || !ctx->have_dets) return sci_fail(ctx, SCI_ERR_STATE, "enpt2: integrals and determinants first");
+    if (ctx->cplx || ctx->spinors) return sci_fail(ctx, SCI_ERR_ARG, "enpt2: real spin-orbital mode only");
+    if (nroots < 1 || nroots > 8 || !E0 || !E2 || (ctx->M > 0 && !C))
+        return sci_fail(ctx, SCI_ERR_ARG, "enpt2: need 1 <= nroots <= 8, C, E0 and E2");
+    if (eps < 0.0) return sci_fail(ctx, SCI_ERR_ARG, "enpt2: eps < 0");
+    if (sci_cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) return SCI_ERR_CUDA;
+    switch (nroots) {
+        case 1: return pt2_run<1>(ctx, C, E0, eps, table_bytes, E2, stats);
+        case 2: return pt2_run<2>(ctx, C, E0, eps, table_bytes, E2, stats);
+        case 3: return pt2_run<3>(ctx, C, E0, eps, table_bytes, E2, stats);
+        case 4: return pt2_run<4>(ctx, C, E0, eps, table_bytes, E2, stats);
+        case 5: return pt2_run<5>(ctx, C, E0, eps, table_bytes, E2, stats);
+        case 6: return pt2_run<6>(ctx, C, E0, eps, table_bytes, E2, stats);
+        case 7: return pt2_run<7>(ctx, C, E0, eps, table_bytes, E2, stats);
+        default: return pt2_run<8>(ctx, C, E0, eps, table_bytes, E2, stats);
+    }
+}

@@ -48,6 +48,7 @@ SIGNATURES = {
     "sci_profile": (_i32, [_vp, _i32]),
     "sci_kernel_times": (_i32, [_vp, _vp, _i32]),
     "sci_rdm12": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp]),
+    "sci_enpt2": (_i32, [_vp, _vp, _i32, _vp, ctypes.c_double, ctypes.c_size_t, _vp, _vp]),
     "sci_batch_create": (_i32, [ctypes.POINTER(_vp), _i32, _vp]),
     "sci_batch_destroy": (_i32, [_vp]),
     "sci_batch_add": (_i32, [_vp, _vp]),
@@ -203,6 +204,16 @@ def sci_kernel_times(ctx) -> list:
 def sci_rdm12(ctx, C, nvec, weights, rdm1, rdm2):
     w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
     return _check(ctx, load().sci_rdm12(ctx, _p(C), nvec, _p(w), _p(rdm1), _p(rdm2)))
+
+
+def sci_enpt2(ctx, C, nroots, E0, eps=0.0, table_bytes=1 << 30):
+    """(E2[W], E2[P], E2[Q]) as three arrays of nroots, and the stats dict."""
+    e0 = np.ascontiguousarray(E0, dtype=np.float64).reshape(-1)
+    out = np.zeros(3 * nroots, dtype=np.float64)
+    st = np.zeros(4, dtype=np.int64)
+    _check(ctx, load().sci_enpt2(ctx, _p(C), nroots, _p(e0), float(eps), int(table_bytes), _p(out), _p(st)))
+    stats = dict(zip(["batches", "distinct_W", "passes", "table_capacity"], (int(v) for v in st)))
+    return out[:nroots], out[nroots:2 * nroots], out[2 * nroots:], stats
 
 
 SCI_SCHED_AUTO, SCI_SCHED_TILE, SCI_SCHED_WARP = 0, 1, 2
@@ -391,6 +402,12 @@ class Hamiltonian:
         g2 = torch.empty((no, no, no, no), dtype=dt, device=self.device) if rdm2 else None
         sci_rdm12(self.ctx, C2, C2.shape[1], weights, g1, g2)
         return g1, g2
+
+    def enpt2(self, C, E0, eps: float = 0.0, table_bytes: int = 1 << 30):
+        """Epstein-Nesbet second-order energies of the columns of C ([M, nroots] float64
+        CUDA) with zeroth-order energies E0: (E2[W], E2[P], E2[Q], stats) -- see sci_enpt2."""
+        C2 = (C.reshape(-1, 1) if C.dim() == 1 else C).contiguous()
+        return sci_enpt2(self.ctx, C2, C2.shape[1], E0, eps, table_bytes)
 
     def connections(self, row_begin: int = 0, row_end: int | None = None):
         row_end = self.M if row_end is None else row_end

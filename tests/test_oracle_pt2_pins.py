@@ -1,0 +1,59 @@
+"""Pins of the oracle's ENPT2 (oracle/pt2.py, Eq. ENPT2E).
+
+- Against the dense Hamiltonian of the literal operator route (fock_route): the same
+  definition evaluated with H[Q, P] c and H[q, q] from Eq. Hamiltonian applied operator by
+  operator, no Slater-Condon closed forms.
+- P = the whole space gives E2 = 0 (Q is empty).
+- A two-determinant space in closed form: P = {D0} alone, Q = {D1}, E2 = H_10^2 / (H_00 - H_11).
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from oracle import fock_route as F
+from oracle import pt2 as PT
+from paper_2501_18185_gb300 import workloads as W
+
+
+@pytest.mark.parametrize("n,na,nb,frac,nroots", [(5, 2, 2, 0.4, 1), (6, 3, 1, 0.5, 2), (5, 3, 2, 0.3, 3)])
+def test_enpt2_matches_dense_literal_route(n, na, nb, frac, nroots):
+    w = W.random_small(211 + n, "spin_orbitals", n, na, nb, naux=4, frac=frac)
+    h, eri = w.ints.h, w.ints.eri()
+    P = w.keys
+    ev, U = np.linalg.eigh(Oracle("spin_orbitals", n, h, eri, P).dense())
+    C, E0 = U[:, :nroots], ev[:nroots]
+    full = PT.full_space_keys("spin_orbitals", n, na, nb)
+    hs, es = F.spin_orbital_integrals(h, eri)
+    H = F.hamiltonian(full, hs, es)
+    pos = np.searchsorted(full, P)
+    q = np.setdiff1d(np.arange(len(full)), pos)
+    num = H[np.ix_(q, pos)] @ C
+    ref = (num ** 2 / (E0[None, :] - np.diag(H)[q][:, None])).sum(0)
+    got = PT.enpt2("spin_orbitals", n, na, nb, h, eri, P, C, E0)
+    assert np.allclose(got, ref, rtol=1e-12, atol=1e-14)
+    assert np.all(got < 0)   # lowest roots: E0 below the external diagonal here
+
+
+def test_enpt2_full_space_is_zero():
+    w = W.random_small(223, "spin_orbitals", 5, 2, 2, naux=4)
+    o = Oracle.from_workload(w)
+    ev, U = np.linalg.eigh(o.dense())
+    assert np.abs(PT.enpt2("spin_orbitals", 5, 2, 2, w.ints.h, w.ints.eri(), w.keys, U[:, :2], ev[:2])).max() == 0.0
+
+
+def test_enpt2_two_determinant_closed_form():
+    """One electron in 2 spinors: the full space is {D0, D1}; with P = {D0} and c = 1,
+    E2 = |H_10|^2 / (H_00 - H_11)."""
+    rng = np.random.default_rng(5)
+    h = np.array([[-1.0, 0.3 + 0.1j], [0.3 - 0.1j, 0.5]])
+    L = rng.normal(size=(2, 2, 2)) * 0.1
+    L = 0.5 * (L + np.swapaxes(L, 1, 2))
+    eri = np.einsum("Ppq,Prs->pqrs", L, L).astype(np.complex128)
+    full = PT.full_space_keys("spinors", 2, 1, 0)
+    o = Oracle("spinors", 2, h, eri, full)
+    H = o.dense()
+    P = full[:1]
+    E0 = H[0, 0].real
+    ref = abs(H[1, 0]) ** 2 / (E0 - H[1, 1].real)
+    got = PT.enpt2("spinors", 2, 1, 0, h, eri, P, np.ones((1, 1), dtype=np.complex128), [E0])
+    assert abs(got[0] - ref) < 1e-15
