@@ -297,7 +297,7 @@ def blockvec_bench(M=2_000_000, k=96, a=8, reps=5):
     return res
 
 
-def pt2_bench(sizes=(60_000, 200_000, 1_000_000, 2_000_000), table_gb=48.0):
+def pt2_bench(sizes=(60_000, 200_000, 1_000_000, 2_000_000), table_gb=96.0):
     """Epstein-Nesbet PT2 of the ground state on spaces of the bench recipe: (E0, c) from
     the FP64 block Davidson (residual 1e-6), then exact sci_enpt2 (no screening).  Wall
     seconds of sci_enpt2 (synchronous), batches, distinct determinants of W summed, the
@@ -428,6 +428,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-davidson", action="store_true",
                     help="skip the 8-root Davidson timing and the density-matrix timing")
+    ap.add_argument("--pt2-table-gb", type=float, default=96.0, help="hash-table memory of the pt2 section")
     ap.add_argument("--only", default=None, choices=["blockvec", "rdm", "batch", "davidson", "pt2"],
                     help="run one side section alone and print its JSON (profiling runs)")
     ap.add_argument("--prec", default="f64", choices=["f64", "ds", "f32"],
@@ -460,7 +461,8 @@ def main():
     if args.only in ("blockvec", "batch", "pt2"):
         out = (blockvec_bench(M=args.M or 2_000_000) if args.only == "blockvec" else
                batch_bench() if args.only == "batch" else
-               pt2_bench(sizes=(args.M,) if args.M else (60_000, 200_000, 1_000_000, 2_000_000)))
+               pt2_bench(sizes=(args.M,) if args.M else (60_000, 200_000, 1_000_000, 2_000_000),
+                         table_gb=args.pt2_table_gb))
         print(json.dumps({args.only: out}), flush=True)
         return
     w = make_workload(args.workload, args.nvec, args.M)

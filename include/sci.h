@@ -227,13 +227,17 @@ int sci_rdm12(sci_ctx *ctx, const void *C, int nvec, const double *weights, void
  *   eps: screening; a generated contribution with |H_IJ| max_k |c_Jk| < eps is dropped
  *      (0 = exact).
  *   table_bytes: device memory for the hash table of one batch (8 + 8 nroots bytes per
- *      entry, capacity the largest power of two within the budget).  W is split into
+ *      entry, capacity the largest power of two within the budget, at least 256).  W is split into
  *      2^t batches (t <= 10) so that a batch's generated excitations fill at most 60% of
  *      it; a batch that still overflows (or probes too far) restarts the sum with twice
  *      the batches.
  *   E2: HOST, 3 x nroots doubles, overwritten: E2[W], then E2[P], then E2[Q].
- *   stats: HOST, 4 int64 or NULL: batches, distinct W determinants summed, passes run,
- *      table capacity.
+ *   stats: HOST, 8 int64 or NULL: batches, distinct W determinants summed, passes run
+ *      (with restarts), table capacity, microseconds spent clearing the table,
+ *      generating and evaluating (CUDA events), and the distinct count of the sampling
+ *      batch (-1 if none).  Before the sum, one batch of a four-times finer split is
+ *      generated to estimate the distinct determinants; the batch count is chosen from
+ *      that estimate (25% margin) and never exceeds the bound from the generated count.
  * Synchronous.  Allocates sigma scratch (M x nroots doubles) and the table for the call.
  * Errors: SCI_ERR_ARG (mode, sizes, NULL), SCI_ERR_STATE, SCI_ERR_NOMEM, SCI_ERR_OVERFLOW
  * (the table is too small even at 1024 batches). */

@@ -399,7 +399,7 @@ int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t
                                     (const double *)ctx->kd, G, fdiag, Eref);
     // the table: capacity a power of two within the budget
     const size_t slot = sizeof(uint64_t) + sizeof(double) * R;
-    uint64_t cap = 1ull << 16;
+    uint64_t cap = 1ull << 8;  // at least 256 entries
     while ((cap << 1) * slot <= table_bytes) cap <<= 1;
     if (cudaMalloc(&keys, cap * sizeof(uint64_t)) != cudaSuccess || cudaMalloc(&vals, cap * sizeof(double) * R) != cudaSuccess) {
         cleanup();
@@ -411,12 +411,10 @@ int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t
     const int64_t per = na * ua + nb * ub + (int64_t)na * (na - 1) / 2 * (ua * (ua - 1) / 2) +
                         (int64_t)nb * (nb - 1) / 2 * (ub * (ub - 1) / 2) + (int64_t)na * ua * nb * ub;
     const double total = (double)M * (double)per;
+    // (at most 1024 batches: when even that bound does not fit, the distinct count decides,
+    // and a batch that overflows the table ends with SCI_ERR_OVERFLOW)
     int tbits = 0;
     while (tbits < kMaxBits && total / (double)(1ull << tbits) > 0.6 * (double)cap) tbits++;
-    if (total / (double)(1ull << tbits) > 0.6 * (double)cap) {
-        cleanup();
-        return sci_fail(ctx, SCI_ERR_OVERFLOW, "enpt2: hash table too small for 1024 batches");
-    }
     Pt2 p{};
     p.n = n, p.norb = norb, p.na = na, p.nb = nb, p.ref = ctx->ref;
     p.tab = (const double *)ctx->tab, p.fref = (const double *)ctx->fref, p.g_so = (const double *)ctx->g_so;
@@ -424,52 +422,95 @@ int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t
     p.keys = keys, p.vals = vals, p.mask = cap - 1, p.count = count, p.flag = flag;
     p.limit = (unsigned long long)(0.85 * (double)cap);
     p.eps = eps;
-    int64_t passes = 0, distinct = 0;
-    for (;;) {
-        std::mt19937 rng(20250130u + (unsigned)tbits);
-        for (int o = 0; o < 32; o++) p.gcode[o] = tbits ? (uint32_t)(rng() & ((1u << tbits) - 1)) : 0u;
-        {   // orbitals 0..n-1 grouped by code
-            std::vector<int> cnt((1 << tbits) + 1, 0);
-            for (int o = 0; o < n; o++) cnt[p.gcode[o] + 1]++;
-            for (int c = 1; c <= (1 << tbits); c++) cnt[c] += cnt[c - 1];
-            for (int c = 0; c <= (1 << tbits); c++) p.cstart[c] = (uint8_t)cnt[c];
-            std::vector<int> fill(cnt.begin(), cnt.end() - 1);
-            for (int o = 0; o < n; o++) p.obc[fill[p.gcode[o]]++] = (uint8_t)o;
+    int64_t passes = 0, distinct = 0, sample = -1;
+    float t_clear = 0.f, t_gen = 0.f, t_eval = 0.f;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (auto &e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cleanup();
+            return sci_fail(ctx, SCI_ERR_CUDA, "enpt2: events");
         }
+    auto done = [&](int code) {
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+        cleanup();
+        return code;
+    };
+    // the batch code: t random bits per beta orbital, and the orbitals grouped by code
+    auto set_codes = [&](int t) {
+        std::mt19937 rng(20250130u + (unsigned)t);
+        for (int o = 0; o < 32; o++) p.gcode[o] = t ? (uint32_t)(rng() & ((1u << t) - 1)) : 0u;
+        std::vector<int> cnt((1 << t) + 1, 0);
+        for (int o = 0; o < n; o++) cnt[p.gcode[o] + 1]++;
+        for (int c = 1; c <= (1 << t); c++) cnt[c] += cnt[c - 1];
+        for (int c = 0; c <= (1 << t); c++) p.cstart[c] = (uint8_t)cnt[c];
+        std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+        for (int o = 0; o < n; o++) p.obc[fill[p.gcode[o]]++] = (uint8_t)o;
+    };
+    // one batch: clear the table, generate, evaluate (optional); returns the distinct
+    // count and the overflow flag
+    auto pass = [&](uint32_t b, int t, bool eval, int64_t &cnt_out, int &flag_out) -> int {
+        if (sci_cuda_check(ctx, cudaEventRecord(ev[0], st), "enpt2 event") ||
+            sci_cuda_check(ctx, cudaMemsetAsync(keys, 0xFF, cap * sizeof(uint64_t), st), "enpt2 keys") ||
+            sci_cuda_check(ctx, cudaMemsetAsync(vals, 0, cap * sizeof(double) * R, st), "enpt2 vals") ||
+            sci_cuda_check(ctx, cudaMemsetAsync(count, 0, sizeof(unsigned long long) + sizeof(int) * 2, st), "enpt2 count") ||
+            sci_cuda_check(ctx, cudaEventRecord(ev[1], st), "enpt2 event"))
+            return SCI_ERR_CUDA;
+        if (M > 0)
+            k_pt2_gen<R><<<(unsigned)std::min<int64_t>((M + kWarps - 1) / kWarps, 152 * 16), kThreads, 0, st>>>(
+                ctx->keys, M, C, p, b, t);
+        if (sci_cuda_check(ctx, cudaEventRecord(ev[2], st), "enpt2 event")) return SCI_ERR_CUDA;
+        if (eval)
+            k_pt2_eval<R><<<grid_for((int64_t)std::min<uint64_t>(cap, 1ull << 40)), kThreads, 0, st>>>(p, cap, dE0, outW);
+        unsigned long long hc[2] = {0, 0};
+        if (sci_cuda_check(ctx, cudaEventRecord(ev[3], st), "enpt2 event") ||
+            sci_cuda_check(ctx, cudaMemcpyAsync(hc, count, sizeof(hc), cudaMemcpyDeviceToHost, st), "enpt2 flag") ||
+            sci_cuda_check(ctx, cudaStreamSynchronize(st), "enpt2 pass"))
+            return SCI_ERR_CUDA;
+        float a = 0.f, g = 0.f, e = 0.f;
+        cudaEventElapsedTime(&a, ev[0], ev[1]);
+        cudaEventElapsedTime(&g, ev[1], ev[2]);
+        cudaEventElapsedTime(&e, ev[2], ev[3]);
+        t_clear += a, t_gen += g, t_eval += e;
+        cnt_out = (int64_t)hc[0];
+        flag_out = (int)(hc[1] & 0xFFFFFFFFull);
+        return SCI_OK;
+    };
+    // sampling: one batch of a four-times finer split estimates the distinct determinants
+    // of W (duplicates make them far fewer than the generated excitations); the batch
+    // count is chosen from that estimate with a 25% margin, never above the upper bound
+    if (tbits > 0 && M > 0) {
+        const int ts = std::min(kMaxBits, tbits + 2);
+        set_codes(ts);
+        int64_t c0 = 0;
+        int f0 = 0;
+        if (int rc2 = pass(0, ts, false, c0, f0)) return done(rc2);
+        if (f0 == 0) {
+            sample = c0;
+            const double D = 1.25 * (double)c0 * (double)(1ull << ts);
+            int t = 0;
+            while (t < tbits && D / (double)(1ull << t) > 0.6 * (double)cap) t++;
+            tbits = t;
+        }
+    }
+    for (;;) {
+        set_codes(tbits);
         bool overflow = false;
         distinct = 0;
-        if (sci_cuda_check(ctx, cudaMemsetAsync(outW, 0, sizeof(double) * R, st), "enpt2 memset")) {
-            cleanup();
-            return SCI_ERR_CUDA;
-        }
+        if (sci_cuda_check(ctx, cudaMemsetAsync(outW, 0, sizeof(double) * R, st), "enpt2 memset")) return done(SCI_ERR_CUDA);
         for (uint32_t b = 0; b < (1u << tbits) && !overflow; b++) {
-            if (sci_cuda_check(ctx, cudaMemsetAsync(keys, 0xFF, cap * sizeof(uint64_t), st), "enpt2 keys") ||
-                sci_cuda_check(ctx, cudaMemsetAsync(vals, 0, cap * sizeof(double) * R, st), "enpt2 vals") ||
-                sci_cuda_check(ctx, cudaMemsetAsync(count, 0, sizeof(unsigned long long) + sizeof(int) * 2, st), "enpt2 count")) {
-                cleanup();
-                return SCI_ERR_CUDA;
-            }
-            if (M > 0)
-                k_pt2_gen<R><<<(unsigned)std::min<int64_t>((M + kWarps - 1) / kWarps, 152 * 16), kThreads, 0, st>>>(
-                    ctx->keys, M, C, p, b, tbits);
-            k_pt2_eval<R><<<grid_for((int64_t)std::min<uint64_t>(cap, 1ull << 40)), kThreads, 0, st>>>(p, cap, dE0, outW);
-            unsigned long long hc[2] = {0, 0};
-            if (sci_cuda_check(ctx, cudaMemcpyAsync(hc, count, sizeof(hc), cudaMemcpyDeviceToHost, st), "enpt2 flag") ||
-                sci_cuda_check(ctx, cudaStreamSynchronize(st), "enpt2 pass")) {
-                cleanup();
-                return SCI_ERR_CUDA;
-            }
-            const int f = (int)(hc[1] & 0xFFFFFFFFull);
-            distinct += (int64_t)hc[0];
+            int64_t c = 0;
+            int f = 0;
+            if (int rc2 = pass(b, tbits, true, c, f)) return done(rc2);
+            distinct += c;
             passes++;
             overflow = f != 0;
         }
         if (!overflow) break;
-        if (++tbits > kMaxBits) {
-            cleanup();
-            return sci_fail(ctx, SCI_ERR_OVERFLOW, "enpt2: a batch overflowed the hash table at 1024 batches");
-        }
+        if (++tbits > kMaxBits) return done(sci_fail(ctx, SCI_ERR_OVERFLOW, "enpt2: a batch overflowed the hash table at 1024 batches"));
     }
+    for (auto &e : ev)
+        if (e) cudaEventDestroy(e), e = nullptr;
     double hw[R], hp[R];
     if (sci_cuda_check(ctx, cudaMemcpyAsync(hw, outW, sizeof(hw), cudaMemcpyDeviceToHost, st), "enpt2 W") ||
         sci_cuda_check(ctx, cudaMemcpyAsync(hp, outP, sizeof(hp), cudaMemcpyDeviceToHost, st), "enpt2 P") ||
@@ -483,6 +524,10 @@ int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t
         stats[1] = distinct;
         stats[2] = passes;
         stats[3] = (int64_t)cap;
+        stats[4] = (int64_t)(1e3f * t_clear);
+        stats[5] = (int64_t)(1e3f * t_gen);
+        stats[6] = (int64_t)(1e3f * t_eval);
+        stats[7] = sample;
     }
     cleanup();
     return SCI_OK;

@@ -210,9 +210,10 @@ def sci_enpt2(ctx, C, nroots, E0, eps=0.0, table_bytes=1 << 30):
     """(E2[W], E2[P], E2[Q]) as three arrays of nroots, and the stats dict."""
     e0 = np.ascontiguousarray(E0, dtype=np.float64).reshape(-1)
     out = np.zeros(3 * nroots, dtype=np.float64)
-    st = np.zeros(4, dtype=np.int64)
+    st = np.zeros(8, dtype=np.int64)
     _check(ctx, load().sci_enpt2(ctx, _p(C), nroots, _p(e0), float(eps), int(table_bytes), _p(out), _p(st)))
-    stats = dict(zip(["batches", "distinct_W", "passes", "table_capacity"], (int(v) for v in st)))
+    stats = dict(zip(["batches", "distinct_W", "passes", "table_capacity", "clear_us", "generate_us", "evaluate_us",
+                      "sample_distinct"], (int(v) for v in st)))
     return out[:nroots], out[nroots:2 * nroots], out[2 * nroots:], stats
 
 

@@ -40,8 +40,9 @@ def test_enpt2_matches_oracle(gpu, seed, n, na, nb, frac, nroots):
     e2w, e2p, e2q, st = H.enpt2(Ct, E0)
     assert np.allclose(e2q, ref, rtol=1e-10, atol=1e-14), (e2q, ref)
     assert st["batches"] >= 1 and st["distinct_W"] > 0
-    # a table a few hundred entries wide: many batches, the same sums
-    e2w_b, e2p_b, e2q_b, st_b = H.enpt2(Ct, E0, table_bytes=4096 * (8 + 8 * nroots))
+    # a table of 512 entries: many batches (and restarts when a batch overflows), the
+    # same sums
+    e2w_b, e2p_b, e2q_b, st_b = H.enpt2(Ct, E0, table_bytes=512 * (8 + 8 * nroots))
     assert st_b["batches"] > st["batches"]
     assert np.allclose(e2q_b, e2q, rtol=1e-12, atol=1e-15) and np.allclose(e2p_b, e2p, rtol=1e-14)
     # E2[P] (Eq. EP1) at exact eigenvectors equals Eq. EP2: sum c^2 (E0 - H_II)
