@@ -35,6 +35,16 @@ __device__ __forceinline__ void ds_fma(Ds &a, float2 t, float2 c)
     a.hi = s;
 }
 
+// a += b for a paired-FP32 value b = (hi, lo)
+__device__ __forceinline__ void ds_add(Ds &a, float2 b)
+{
+    const float s = a.hi + b.x;
+    const float bv = s - a.hi;
+    const float err = (a.hi - (s - bv)) + (b.x - bv);
+    a.lo += err + b.y;
+    a.hi = s;
+}
+
 __device__ __forceinline__ void ds_renorm(Ds &a)
 {
     const float s = a.hi + a.lo;

@@ -19,7 +19,8 @@
 //   beta-beta doubles j1 j2 -> b1 < b2: g(b2) = b ^ f(J_beta) ^ g(j1) ^ g(j2) ^ g(b1),
 // with the orbitals grouped by code so that each lookup is a short list.
 // Each generated (I, H_IJ c_J) is added to the table entry of I (open addressing, linear
-// probing bounded by kMaxProbe, FP64 atomic adds); then every entry is evaluated with
+// probing bounded by kMaxProbe, key and values in one slot, FP64 atomic adds); then every
+// entry is evaluated with
 //   H_II = E_ref - sum_{i in holes} F_ii + sum_{a in particles} F_aa
 //          + sum_{pairs in holes} G + sum_{pairs in particles} G - sum_{holes x particles} G,
 // F the Fock diagonal of the reference and G_pq = (pp|qq) - (pq|qp): O(level^2) per I.
@@ -29,13 +30,14 @@
 #include <random>
 #include <vector>
 
+#include "sci_ds.cuh"
 #include "sci_internal.cuh"
 
 namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr uint64_t kEmpty = ~0ull;
+constexpr uint64_t kEmpty = 0;   // no determinant with electrons has key 0
 constexpr int kMaxProbe = 1 << 12;
 constexpr int kMaxBits = 10;   // at most 1024 batches
 constexpr int kMaxPairs = 32 * 31 / 2;
@@ -49,8 +51,7 @@ struct Pt2 {
     uint32_t gcode[32];       // beta-orbital codes
     uint8_t obc[32];          // the n beta orbitals sorted by code
     uint8_t cstart[(1 << kMaxBits) + 1];  // first index in obc of each code
-    uint64_t *keys;
-    double *vals;
+    uint64_t *tab2;           // slots of (key, value[R]) words, key 0 = empty
     uint64_t mask;            // capacity - 1
     unsigned long long *count;
     unsigned long long limit;
@@ -104,18 +105,18 @@ __device__ __forceinline__ void insert(const Pt2 &p, uint64_t I, double hij, con
     if (p.eps > 0.0 && fabs(hij) * cmax < p.eps) return;
     uint64_t s = mix64(I) & p.mask;
     for (int probe = 0; probe < kMaxProbe; probe++) {
-        uint64_t k = p.keys[s];
+        uint64_t *slot = p.tab2 + s * (R + 1);
+        uint64_t k = *slot;
         if (k == kEmpty) {
-            k = atomicCAS(reinterpret_cast<unsigned long long *>(p.keys + s), (unsigned long long)kEmpty,
-                          (unsigned long long)I);
+            k = atomicCAS(reinterpret_cast<unsigned long long *>(slot), (unsigned long long)kEmpty, (unsigned long long)I);
             if (k == kEmpty) {
                 if (atomicAdd(p.count, 1ull) >= p.limit) atomicOr(p.flag, 1);
                 k = I;
             }
         }
-        if (k == I) {
+        if (k == I) {   // the value words share the key's sector
 #pragma unroll
-            for (int v = 0; v < R; v++) atomicAdd(p.vals + s * R + v, hij * cJ[v]);
+            for (int v = 0; v < R; v++) atomicAdd(reinterpret_cast<double *>(slot + 1 + v), hij * cJ[v]);
             return;
         }
         s = (s + 1) & p.mask;
@@ -237,45 +238,73 @@ k_pt2_gen(const uint64_t *__restrict__ Pkeys, int64_t M, const double *__restric
     }
 }
 
-// sum over the table entries of num^2 / (E0 - H_II)
+// sum over the table entries of num^2 / (E0 - H_II).  Each warp packs the occupied slots
+// it scans into a buffer of 32 and evaluates full buffers, so every lane works; H_II
+// (E_ref plus O(level^2) table terms) is summed in paired FP32 from split copies of F and
+// G in shared memory, and added to E_ref in FP64.
 template <int R>
 __global__ void __launch_bounds__(kThreads)
 k_pt2_eval(Pt2 p, uint64_t cap, const double *__restrict__ E0, double *__restrict__ out)
 {
-    __shared__ double sG[64 * 64];
-    __shared__ double sF[64];
+    __shared__ float2 sG[64 * 64];
+    __shared__ float2 sF[64];
+    __shared__ uint64_t sbuf[kWarps][64];
     __shared__ double red[kWarps][R];
     const int norb = p.norb;
-    for (int t = threadIdx.x; t < norb * norb; t += blockDim.x) sG[t] = p.G[t];
-    for (int t = threadIdx.x; t < norb; t += blockDim.x) sF[t] = p.fdiag[t];
+    for (int t = threadIdx.x; t < norb * norb; t += blockDim.x) sG[t] = sci::ds_split_int(p.G[t]);
+    for (int t = threadIdx.x; t < norb; t += blockDim.x) sF[t] = sci::ds_split_int(p.fdiag[t]);
     __syncthreads();
     const double Eref = *p.Eref;
-    double acc[R];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double acc[R], e0[R];
 #pragma unroll
-    for (int v = 0; v < R; v++) acc[v] = 0.0;
-    for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < cap; s += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t I = p.keys[s];
-        if (I == kEmpty) continue;
+    for (int v = 0; v < R; v++) acc[v] = 0.0, e0[v] = E0[v];
+    auto evaluate = [&](uint64_t s) {
+        const uint64_t *slot = p.tab2 + s * (R + 1);
+        const uint64_t I = slot[0];
         const uint64_t H = p.ref & ~I, Pm = I & ~p.ref;
-        double e = Eref;
+        sci::Ds e;
+        sci::ds_zero(e);
         for (uint64_t m = H; m; m &= m - 1) {
             const int i = __ffsll((long long)m) - 1;
-            e -= sF[i];
-            for (uint64_t m2 = m & (m - 1); m2; m2 &= m2 - 1) e += sG[i * norb + __ffsll((long long)m2) - 1];
-            for (uint64_t m2 = Pm; m2; m2 &= m2 - 1) e -= sG[i * norb + __ffsll((long long)m2) - 1];
+            const float2 f = sF[i];
+            sci::ds_add(e, make_float2(-f.x, -f.y));
+            for (uint64_t m2 = m & (m - 1); m2; m2 &= m2 - 1) sci::ds_add(e, sG[i * norb + __ffsll((long long)m2) - 1]);
+            for (uint64_t m2 = Pm; m2; m2 &= m2 - 1) {
+                const float2 g = sG[i * norb + __ffsll((long long)m2) - 1];
+                sci::ds_add(e, make_float2(-g.x, -g.y));
+            }
         }
         for (uint64_t m = Pm; m; m &= m - 1) {
             const int a = __ffsll((long long)m) - 1;
-            e += sF[a];
-            for (uint64_t m2 = m & (m - 1); m2; m2 &= m2 - 1) e += sG[a * norb + __ffsll((long long)m2) - 1];
+            sci::ds_add(e, sF[a]);
+            for (uint64_t m2 = m & (m - 1); m2; m2 &= m2 - 1) sci::ds_add(e, sG[a * norb + __ffsll((long long)m2) - 1]);
         }
+        const double hii = Eref + sci::ds_value(e);
 #pragma unroll
         for (int v = 0; v < R; v++) {
-            const double num = p.vals[s * R + v];
-            acc[v] += num * num / (E0[v] - e);
+            const double num = __longlong_as_double((long long)slot[1 + v]);
+            acc[v] += num * num / (e0[v] - hii);
+        }
+    };
+    int nbuf = 0;  // occupied slots waiting in this warp's buffer (warp-uniform)
+    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
+    for (uint64_t s0 = (uint64_t)blockIdx.x * kThreads + (uint64_t)w * 32; s0 < cap; s0 += stride) {
+        const uint64_t s = s0 + lane;
+        const bool occ = s < cap && p.tab2[s * (R + 1)] != kEmpty;
+        const unsigned m = __ballot_sync(0xffffffffu, occ);
+        if (occ) sbuf[w][nbuf + __popc(m & ((1u << lane) - 1))] = s;
+        nbuf += __popc(m);
+        __syncwarp();
+        if (nbuf >= 32) {
+            evaluate(sbuf[w][lane]);
+            __syncwarp();
+            if (lane < nbuf - 32) sbuf[w][lane] = sbuf[w][32 + lane];
+            nbuf -= 32;
+            __syncwarp();
         }
     }
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane < nbuf) evaluate(sbuf[w][lane]);
 #pragma unroll
     for (int v = 0; v < R; v++) {
         double x = acc[v];
@@ -362,14 +391,12 @@ int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t
     cudaStream_t st = ctx->stream;
     // scratch: sigma [M][R], E0 [R], results W/P [2R], G, fdiag, Eref, count, flag
     double *S = nullptr, *small = nullptr;
-    uint64_t *keys = nullptr;
-    double *vals = nullptr;
+    uint64_t *tab2 = nullptr;
     int rc = SCI_OK;
     auto cleanup = [&]() {
         if (S) cudaFree(S);
         if (small) cudaFree(small);
-        if (keys) cudaFree(keys);
-        if (vals) cudaFree(vals);
+        if (tab2) cudaFree(tab2);
     };
     const size_t nsmall = (size_t)R * 3 + (size_t)norb * norb + norb + 1 + 2;
     if (cudaMalloc(&S, sizeof(double) * std::max<int64_t>(1, M) * R) != cudaSuccess ||
@@ -401,7 +428,7 @@ int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t
     const size_t slot = sizeof(uint64_t) + sizeof(double) * R;
     uint64_t cap = 1ull << 8;  // at least 256 entries
     while ((cap << 1) * slot <= table_bytes) cap <<= 1;
-    if (cudaMalloc(&keys, cap * sizeof(uint64_t)) != cudaSuccess || cudaMalloc(&vals, cap * sizeof(double) * R) != cudaSuccess) {
+    if (cudaMalloc(&tab2, cap * slot) != cudaSuccess) {
         cleanup();
         return sci_fail(ctx, SCI_ERR_NOMEM, "enpt2: hash table");
     }
@@ -419,7 +446,7 @@ int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t
     p.n = n, p.norb = norb, p.na = na, p.nb = nb, p.ref = ctx->ref;
     p.tab = (const double *)ctx->tab, p.fref = (const double *)ctx->fref, p.g_so = (const double *)ctx->g_so;
     p.fdiag = fdiag, p.G = G, p.Eref = Eref;
-    p.keys = keys, p.vals = vals, p.mask = cap - 1, p.count = count, p.flag = flag;
+    p.tab2 = tab2, p.mask = cap - 1, p.count = count, p.flag = flag;
     p.limit = (unsigned long long)(0.85 * (double)cap);
     p.eps = eps;
     int64_t passes = 0, distinct = 0, sample = -1;
@@ -451,8 +478,7 @@ int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t
     // count and the overflow flag
     auto pass = [&](uint32_t b, int t, bool eval, int64_t &cnt_out, int &flag_out) -> int {
         if (sci_cuda_check(ctx, cudaEventRecord(ev[0], st), "enpt2 event") ||
-            sci_cuda_check(ctx, cudaMemsetAsync(keys, 0xFF, cap * sizeof(uint64_t), st), "enpt2 keys") ||
-            sci_cuda_check(ctx, cudaMemsetAsync(vals, 0, cap * sizeof(double) * R, st), "enpt2 vals") ||
+            sci_cuda_check(ctx, cudaMemsetAsync(tab2, 0, cap * slot, st), "enpt2 table") ||
             sci_cuda_check(ctx, cudaMemsetAsync(count, 0, sizeof(unsigned long long) + sizeof(int) * 2, st), "enpt2 count") ||
             sci_cuda_check(ctx, cudaEventRecord(ev[1], st), "enpt2 event"))
             return SCI_ERR_CUDA;

@@ -521,14 +521,7 @@ k_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S, 
 // F^S_ai = F^ref_ai + sum_{k in S\ref} g_ai(k) - sum_{k in ref\S} g_ai(k) summed in
 // paired FP32 from split copies of fref and g_so, then multiplied into the row sum like
 // the doubles.  C2/C4 is the split vector group (row stride NV).
-__device__ __forceinline__ void ds_add(Ds &a, float2 b)
-{
-    const float s = a.hi + b.x;
-    const float bv = s - a.hi;
-    const float err = (a.hi - (s - bv)) + (b.x - bv);
-    a.lo += err + b.y;
-    a.hi = s;
-}
+using sci::ds_add;
 
 template <int NV>
 __global__ void __launch_bounds__(kThreads)
