@@ -102,24 +102,76 @@ class SciBlockOps:
     def _dev(self, S):
         return torch.as_tensor(np.ascontiguousarray(S, dtype=np.float64), device=self.device)
 
+    # one kernel call takes blocks of at most 16 columns, P = A^T B with at most
+    # 8 * 256 / pow2(a) columns of A, and C = A1 S1 + A2 S2 with at most 256 columns in all;
+    # larger products are cut into such calls here
+    MAX_A, MAX_NN = 16, 256
+
+    @staticmethod
+    def _tn_kmax(a):
+        p2 = 1
+        while p2 < a:
+            p2 <<= 1
+        return 8 * (256 // p2)
+
     def tn(self, A, B) -> np.ndarray:
         M, k = A.shape
         a = B.shape[1]
         P = torch.empty((k, a), dtype=torch.float64, device=self.device)
-        self.sci.sci_bv_gemm_tn(self.ctx, M, k, a, A, self._ld(A), B, self._ld(B), P, self.prec)
+        for j0 in range(0, a, self.MAX_A):
+            j1 = min(a, j0 + self.MAX_A)
+            kmax = self._tn_kmax(j1 - j0)
+            for i0 in range(0, k, kmax):
+                i1 = min(k, i0 + kmax)
+                Pc = P[i0:i1, j0:j1] if (j0 == 0 and j1 == a) else torch.empty((i1 - i0, j1 - j0), dtype=torch.float64,
+                                                                                 device=self.device)
+                Ai, Bj = A[:, i0:i1], B[:, j0:j1]
+                self.sci.sci_bv_gemm_tn(self.ctx, M, i1 - i0, j1 - j0, Ai, self._ld(Ai), Bj, self._ld(Bj), Pc, self.prec)
+                if not (j0 == 0 and j1 == a):
+                    P[i0:i1, j0:j1] = Pc
         return P.cpu().numpy()
 
     def nn(self, C, a, A1=None, S1=None, A2=None, S2=None, beta=0.0, dg=None, shift=None, colsq=False):
+        """C[:, :a] = A1 S1 + A2 S2 (+ beta C), the epilogue as in sci_bv_gemm_nn.  One call
+        is row-local, so C may alias A1 or A2 (in-place updates).  A product wider than one
+        call is cut into calls over output columns and operand segments (beta = 1 after the
+        first, the epilogue on the last) that write a temporary, copied to C at the end."""
         M = C.shape[0]
-        k1 = 0 if A1 is None else A1.shape[1]
-        k2 = 0 if A2 is None else A2.shape[1]
-        s1 = self._dev(S1) if k1 else None
-        s2 = self._dev(S2) if k2 else None
-        sh = self._dev(np.real(shift)) if dg is not None else None
-        cs = torch.zeros(a, dtype=torch.float64, device=self.device) if colsq else None
-        self.sci.sci_bv_gemm_nn(self.ctx, M, a, A1, self._ld(A1) if k1 else 1, k1, s1, A2, self._ld(A2) if k2 else 1, k2,
-                                s2, beta, C, self._ld(C), dg, sh, cs, self.prec)
-        return cs.cpu().numpy() if colsq else None
+        segs = []  # (A, S) operand segments of at most MAX_NN columns
+        for A, S in ((A1, S1), (A2, S2)):
+            if A is None or A.shape[1] == 0:
+                continue
+            for i0 in range(0, A.shape[1], self.MAX_NN):
+                i1 = min(A.shape[1], i0 + self.MAX_NN)
+                segs.append((A[:, i0:i1], np.asarray(S)[i0:i1]))
+        calls = [segs] if sum(x[0].shape[1] for x in segs) <= self.MAX_NN else [[sg] for sg in segs]
+        chunked = a > self.MAX_A or len(calls) > 1
+        out = C
+        if chunked:
+            out = C[:, :a].clone() if beta != 0.0 else torch.empty((M, a), dtype=torch.float64, device=self.device)
+        cs_all = np.zeros(a) if colsq else None
+        for j0 in range(0, a, self.MAX_A):
+            j1 = min(a, j0 + self.MAX_A)
+            for ci, ops in enumerate(calls):
+                last = ci == len(calls) - 1
+                A1c, S1c = (ops[0][0], ops[0][1][:, j0:j1]) if len(ops) > 0 else (None, None)
+                A2c, S2c = (ops[1][0], ops[1][1][:, j0:j1]) if len(ops) > 1 else (None, None)
+                k1 = 0 if A1c is None else A1c.shape[1]
+                k2 = 0 if A2c is None else A2c.shape[1]
+                s1 = self._dev(S1c) if k1 else None
+                s2 = self._dev(S2c) if k2 else None
+                use_epi = last and dg is not None
+                sh = self._dev(np.real(np.asarray(shift))[j0:j1]) if use_epi else None
+                cs = torch.zeros(j1 - j0, dtype=torch.float64, device=self.device) if (colsq and last) else None
+                Cc = out[:, j0:]
+                self.sci.sci_bv_gemm_nn(self.ctx, M, j1 - j0, A1c, self._ld(A1c) if k1 else 1, k1, s1, A2c,
+                                        self._ld(A2c) if k2 else 1, k2, s2, beta if ci == 0 else 1.0, Cc, self._ld(Cc),
+                                        dg if use_epi else None, sh, cs, self.prec)
+                if cs is not None:
+                    cs_all[j0:j1] = cs.cpu().numpy()
+        if chunked:
+            C[:, :a].copy_(out)
+        return cs_all
 
 
 def default_ops(diag: torch.Tensor, dtype, arith: str = "f64"):

@@ -159,3 +159,51 @@ def test_davidson_block_kernels_match_torch_ops(gpu, arith):
     assert float(torch.linalg.vector_norm(At @ X - X * r1.energies, dim=0).max()) <= 1e-9
     # orthonormal Ritz vectors
     assert float((X.T @ X - torch.eye(4, dtype=torch.float64, device="cuda")).abs().max()) < 1e-12
+
+
+def test_block_ops_wider_than_one_call(gpu):
+    """SciBlockOps cuts products wider than one kernel call (blocks of more than 16
+    columns, more than 256 operand columns) into several calls; the results equal torch's."""
+    torch = gpu
+    from paper_2501_18185_gb300.davidson import SciBlockOps
+
+    ops = SciBlockOps("cuda")
+    g = torch.Generator(device="cpu").manual_seed(13)
+    M = 20_011
+    A = torch.randn((M, 300), generator=g, dtype=torch.float64).cuda()
+    B = torch.randn((M, 37), generator=g, dtype=torch.float64).cuda()
+    P = ops.tn(A, B)
+    ref = (A.T @ B).cpu().numpy()
+    assert np.abs(P - ref).max() < 1e-12 * np.abs(ref).max()
+    S1 = np.random.default_rng(1).normal(size=(300, 21))
+    S2 = np.random.default_rng(2).normal(size=(37, 21))
+    C = torch.randn((M, 25), generator=g, dtype=torch.float64).cuda()
+    C0 = C.clone()
+    d = torch.randn(M, generator=g, dtype=torch.float64).cuda()
+    sh = np.linspace(-2.0, -1.0, 21)
+    cs = ops.nn(C, 21, A1=A, S1=S1, A2=B, S2=S2, beta=0.5, dg=d, shift=sh, colsq=True)
+    R = A @ torch.from_numpy(S1).cuda() + B @ torch.from_numpy(S2).cuda() + 0.5 * C0[:, :21]
+    assert np.allclose(cs, (R * R).sum(0).cpu().numpy(), rtol=1e-11)
+    den = torch.from_numpy(sh).cuda()[None, :] - d[:, None]
+    assert float(((C[:, :21] - R / den).abs() / (R / den).abs().clamp_min(1e-300)).max()) < 2e-6
+    assert torch.equal(C[:, 21:], C0[:, 21:])
+
+
+@pytest.mark.parametrize("nroots,max_space", [(20, None), (4, 200)])
+def test_davidson_many_roots_and_wide_space(gpu, nroots, max_space):
+    """More roots than one block call takes (20 > 16), and a search space wider than one
+    residual call (2 x 200 > 256 columns): energies as dense eigh."""
+    torch = gpu
+    from paper_2501_18185_gb300.davidson import davidson
+
+    n = 2500
+    rng = np.random.default_rng(17)
+    A = rng.normal(scale=0.05, size=(n, n))
+    A = 0.5 * (A + A.T)
+    A[np.diag_indices(n)] = np.sort(rng.uniform(-5.0, 5.0, n))
+    At = torch.from_numpy(A).cuda()
+    ref = np.linalg.eigvalsh(A)[:nroots]
+    r = davidson(lambda X: At @ X, At.diagonal().contiguous(), nroots=nroots, tol=1e-8, max_space=max_space,
+                 max_iter=500)
+    assert r.converged
+    assert np.abs(r.energies.cpu().numpy() - ref).max() < 1e-9
