@@ -56,6 +56,24 @@ def golden_pairs(w):
         return None
 
 
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The largest x over the ranks of the process group (a job lasts as long as its
+    slowest rank); x itself without a group."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(pairs_per_step: int, steps: int, world: int, total_ms: float) -> float:
+    """Whole-job pairs/s: every rank runs its own replica of `pairs_per_step` pairs per
+    step (weak scaling), timed by the slowest rank's total."""
+    return world * pairs_per_step * steps / (total_ms / 1e3)
+
+
 def measured_peaks() -> dict:
     """The generated peaks of this GPU pool ({} when the file is absent)."""
     try:
@@ -537,13 +555,9 @@ def main():
     sci.sci_profile(H.ctx, False)
     H.sync_status()
 
-    total_ms = sum(step_ms)
-    if dist:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
     ms = total_ms / args.steps
-    value = world * pairs * args.steps / (total_ms / 1e3)
+    value = job_throughput(pairs, args.steps, world, total_ms)
 
     # end to end through the public API with host buffers (pinned), copies inside
     Ch = torch.from_numpy(np.ascontiguousarray(w.c, dtype=np.float32 if args.prec == "f32" else None)).pin_memory()
