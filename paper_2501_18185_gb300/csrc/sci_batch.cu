@@ -25,6 +25,7 @@
 #include <tuple>
 #include <vector>
 
+#include "sci_bits.cuh"
 #include "sci_bucket.cuh"
 #include "sci_internal.cuh"
 
@@ -58,10 +59,9 @@ struct Item {
     int64_t a;
 };
 
-__device__ __forceinline__ double sflip(bool f, double a)
-{
-    return __longlong_as_double(__double_as_longlong(a) ^ ((long long)f << 63));
-}
+using sci::below;
+using sci::kMaxPairs;
+using sci::sflip;
 
 // ---------------------------------------------------------------- TILE items
 __device__ void tile_diag(const Inst &B, int64_t a, const double *C, double *S)
@@ -132,7 +132,6 @@ __device__ void tile_singles(const Inst &B, int64_t a, const double *C, double *
 // ascending numeric order, whatever the orbital count: one table of 2^kRankBits ranks
 // serves every instance with up to kRankBits orbitals.
 constexpr int kRankBits = 20;
-constexpr int kMaxPairs = 32 * 31 / 2;
 
 __global__ void k_rank_table(uint32_t *rank)
 {
@@ -150,7 +149,6 @@ __global__ void k_rank_table(uint32_t *rank)
     }
 }
 
-__device__ __forceinline__ int below(uint64_t K, int x) { return __popcll(K & ((1ull << x) - 1)); }
 
 __device__ __forceinline__ int64_t fci_index(const Inst &B, uint64_t J, const uint32_t *__restrict__ rank)
 {
@@ -254,11 +252,7 @@ k_batch(const Inst *__restrict__ insts, const Item *__restrict__ items, int nite
     __shared__ uint16_t pairs[kMaxPairs];
     __shared__ uint8_t orb[kWarps * 128];
     __shared__ int s_item;
-    for (int P = threadIdx.x; P < kMaxPairs; P += blockDim.x) {
-        int b = 1;
-        while ((b + 1) * b / 2 <= P) b++;
-        pairs[P] = (uint16_t)((P - b * (b - 1) / 2) | (b << 8));
-    }
+    sci::fill_pair_table(pairs);
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);

@@ -30,6 +30,7 @@
 #include <random>
 #include <vector>
 
+#include "sci_bits.cuh"
 #include "sci_ds.cuh"
 #include "sci_internal.cuh"
 
@@ -40,7 +41,6 @@ constexpr int kWarps = kThreads / 32;
 constexpr uint64_t kEmpty = 0;   // no determinant with electrons has key 0
 constexpr int kMaxProbe = 1 << 12;
 constexpr int kMaxBits = 10;   // at most 1024 batches
-constexpr int kMaxPairs = 32 * 31 / 2;
 
 struct Pt2 {
     int n, norb, na, nb;
@@ -59,11 +59,10 @@ struct Pt2 {
     double eps;
 };
 
-__device__ __forceinline__ double sflip(bool f, double a)
-{
-    return __longlong_as_double(__double_as_longlong(a) ^ ((long long)f << 63));
-}
-__device__ __forceinline__ int below(uint64_t K, int x) { return __popcll(K & ((1ull << x) - 1)); }
+using sci::below;
+using sci::kMaxPairs;
+using sci::sflip;
+
 __device__ __forceinline__ uint64_t mix64(uint64_t x)
 {
     x ^= x >> 33;
@@ -143,11 +142,7 @@ k_pt2_gen(const uint64_t *__restrict__ Pkeys, int64_t M, const double *__restric
     __shared__ uint8_t s_obc[32];                // beta orbitals sorted by code
     __shared__ uint32_t s_g[32];                 // beta-orbital codes
     __shared__ int s_nl[kWarps];
-    for (int P = threadIdx.x; P < kMaxPairs; P += blockDim.x) {
-        int b = 1;
-        while ((b + 1) * b / 2 <= P) b++;
-        s_pair[P] = (uint16_t)((P - b * (b - 1) / 2) | (b << 8));
-    }
+    sci::fill_pair_table(s_pair);
     for (int c = threadIdx.x; c <= (1 << tbits); c += blockDim.x) s_cstart[c] = p.cstart[c];
     if (threadIdx.x < 32) s_obc[threadIdx.x] = p.obc[threadIdx.x], s_g[threadIdx.x] = p.gcode[threadIdx.x];
     __syncthreads();

@@ -31,6 +31,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "sci_bits.cuh"
 #include "sci_bucket.cuh"
 #include "sci_internal.cuh"
 
@@ -41,8 +42,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kMaxVec = 8;  // vectors per walk; wider blocks take several walks
 
-__device__ __forceinline__ double sflip(bool f, double a) { return __longlong_as_double(__double_as_longlong(a) ^ ((long long)f << 63)); }
-__device__ __forceinline__ zdbl sflip(bool f, zdbl a) { return zdbl{sflip(f, a.x), sflip(f, a.y)}; }
+using sci::sflip;
 __device__ __forceinline__ double conjv(double a) { return a; }
 __device__ __forceinline__ zdbl conjv(zdbl a) { return zdbl{a.x, -a.y}; }
 __device__ __forceinline__ double sqnorm(double a) { return a * a; }
