@@ -399,7 +399,40 @@ def batch_bench(reps=10):
                 "pairs_per_s_auto_graph": it["pairs"] / (res["ms_auto_graph"] / 1e3),
                 "schedules": {k: sum(1 for i in range(len(ws)) if B.info(i)["schedule"] == k) for k in ("tile", "warp")},
                 "l2": "flushed before each timed launch (256 MB write)"})
+    res["ground_states"] = batch_ground_states(ws, hams)
     return res
+
+
+def batch_ground_states(ws, hams, tol=1e-8):
+    """Lowest eigenpair of all 64 instances: the batched Davidson (one graph-replayed
+    batched sigma per iteration) against the single-instance FP64 Davidson run on each
+    instance in turn (wall seconds, synchronised)."""
+    import torch
+
+    from paper_2501_18185_gb300 import sci
+    from paper_2501_18185_gb300.batch_davidson import davidson_batched
+    from paper_2501_18185_gb300.davidson import davidson
+
+    B = sci.Batch(hams)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    r = davidson_batched(B, tol=tol, max_iter=400)
+    torch.cuda.synchronize()
+    batched_s = time.perf_counter() - t
+    t = time.perf_counter()
+    E1, conv1, calls1 = [], 0, 0
+    for H in hams:
+        one = davidson(lambda Y, H=H: H.sigma(Y.contiguous()), H.diagonal(), nroots=1, tol=tol)
+        E1.append(float(one.energies[0]))
+        conv1 += bool(one.converged)
+        calls1 += one.sigma_calls
+    torch.cuda.synchronize()
+    one_s = time.perf_counter() - t
+    return {"batched_s": round(batched_s, 3), "one_by_one_s": round(one_s, 3),
+            "batched_iterations": r.iterations, "batched_sigma_launches": r.sigma_launches,
+            "batched_converged": int(r.converged.sum()), "one_by_one_converged": conv1,
+            "one_by_one_sigma_calls": calls1, "tol": tol,
+            "max_abs_diff_Eh": float(np.abs(np.asarray(E1) - r.energies).max())}
 
 
 def run_reference(args, rank, world):
