@@ -277,6 +277,11 @@ int sci_batch_sigma(sci_batch *b, const double *C, double *S);
 /* Capture that launch for fixed C and S in a CUDA graph owned by the batch; replay it. */
 int sci_batch_capture(sci_batch *b, const double *C, double *S);
 int sci_batch_replay(sci_batch *b);
+/* Instances taking part in later sigma launches and replays (captured graphs included):
+ * active (host, n = instance count) nonzero = computed, 0 = skipped (its S stays zero).
+ * Copied on the batch stream, ordered after the launches already queued there.
+ * sci_batch_plan() makes every instance active. */
+int sci_batch_set_active(sci_batch *b, const int32_t *active, int n);
 /* Per instance: chosen schedule, autotuner times in ms (-1 if not timed), offset. */
 int sci_batch_info(sci_batch *b, int i, int *schedule, float *ms_tile, float *ms_warp, int64_t *offset);
 /* out[0..n): work items, persistent CTAs, total determinants, total pairs; n <= 4. */
@@ -315,6 +320,39 @@ int sci_bv_gemm_nn(sci_ctx *ctx, int64_t M, int a, const double *A1, int64_t lda
                    const double *S1, const double *A2, int64_t lda2, int k2, const double *S2,
                    double beta, double *C, int64_t ldc, const double *dg, const double *shift,
                    double *colsq, int prec);
+
+/* Segmented block-vector products: the subspace algebra of many independent solvers
+ * (the instances of a batch) whose vectors lie end to end in one device array, instance
+ * s on rows [offsets[s], offsets[s+1]).  A block of k such vectors is column-major:
+ * column j starts at A + j * lda (lda >= offsets[nseg] when k > 1).  FP64, device
+ * pointers, asynchronous on the stream given at creation (NULL: the legacy default
+ * stream).  Same role as the sci_bv_* products for one instance (Sec. 2.4, the
+ * diagonalisation paragraph).
+ *
+ * sci_seg_create: offsets (host, nseg + 1 values, offsets[0] = 0, non-decreasing; empty
+ *   instances allowed); kmax (1..256) bounds k, k1 and k2.  Allocates the work list and
+ *   a partial-sum buffer ((total rows / 2048 + nseg) x kmax doubles).  Synchronous.
+ *   Errors: SCI_ERR_ARG, SCI_ERR_OVERFLOW, SCI_ERR_NOMEM.
+ * sci_seg_tn: out[s * k + j] = sum_{i in s} A[j * lda + i] t[i] for j < k (out: device,
+ *   nseg x k; 0 for an empty instance).  Deterministic: per-item partials summed in item
+ *   order.
+ * sci_seg_nn: y[i] = beta[s] y[i] + alpha1 sum_{j<k1} A1[j * lda1 + i] c1[s * k1 + j]
+ *                                 + alpha2 sum_{j<k2} A2[j * lda2 + i] c2[s * k2 + j]
+ *   for i in instance s (beta, c1, c2: device arrays [nseg], [nseg x k1], [nseg x k2];
+ *   beta NULL means 0; y is not read where beta[s] = 0).  k1 or k2 may be 0 with NULL
+ *   operands.  If dg (device [total rows]) is given, the stored value is then divided by
+ *   shift[s] - dg[i] (shift: device [nseg]), a denominator below 1e-8 in magnitude
+ *   replaced by 1e-8 (the Davidson diagonal preconditioner).  y must not overlap A1, A2
+ *   or dg.
+ * Errors: SCI_ERR_ARG for k out of range, NULL operands or lda below the total rows. */
+typedef struct sci_seg sci_seg;
+int sci_seg_create(sci_seg **out, int device, int nseg, const int64_t *offsets, int kmax, void *cuda_stream);
+int sci_seg_destroy(sci_seg *s);
+int sci_seg_tn(sci_seg *s, int k, const double *A, int64_t lda, const double *t, double *out);
+int sci_seg_nn(sci_seg *s, double *y, const double *beta, int k1, const double *A1, int64_t lda1,
+               const double *c1, double alpha1, int k2, const double *A2, int64_t lda2,
+               const double *c2, double alpha2, const double *dg, const double *shift);
+const char *sci_seg_last_error(const sci_seg *s);
 
 /* Wait for the context stream and return the device status word (SCI_OK or the first
  * device-side error code). */

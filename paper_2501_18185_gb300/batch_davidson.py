@@ -3,14 +3,22 @@ instance, with one batched sigma launch per iteration.
 
 The instances are the sci.Hamiltonian contexts of a sci.Batch (heterogeneous sizes).
 Every iteration applies H to the new search vector of every instance in one persistent
-launch, replayed from a CUDA graph captured once over fixed vector buffers (the batched
-sigma of config 3b).  The subspace algebra runs batched over instances: the search spaces
-are padded to the largest instance, [B, M_max, k], and the projections, Rayleigh-Ritz
-problems ([B, k, k] eigh), residuals and Gram-Schmidt are batched tensor operations in
-FP64.  All instances grow their space together (one column per iteration); an instance
-whose space is exhausted (M_i <= k), or that has converged, takes a null column whose
-diagonal in G is set above its lowest Ritz values, so it is never chosen.  Restarts are
-thick (the space collapses to the `keep` lowest Ritz vectors of each instance).
+launch, replayed from a CUDA graph captured once over fixed vector buffers; instances
+that have converged are switched off in that launch (sci_batch_set_active), so the late
+iterations pay only for the instances still running.
+
+The vectors of all instances lie end to end, as in the batch: the search space is one
+column-major block V [k, sum M_i] (and W = H V), without padding.  Projections, norms,
+Gram-Schmidt updates, residuals and the diagonal preconditioner are the segmented
+products of libsci (sci_seg_tn / sci_seg_nn), one launch each for all instances.  The
+projected matrices G_i = V_i^T H V_i stay on the device, [B, k, k], and their lowest
+eigenpairs come from one batched symmetric eigensolver call; the only host read per
+iteration is the vector of residual norms.
+
+All instances grow their space together (one column per iteration).  An instance that
+has converged, or whose space is exhausted (M_i <= k), takes a null column: zero vector,
+zero coupling, and a diagonal in G above its spectrum, so it is never chosen.  Restarts
+are thick (the space collapses to the `keep` lowest Ritz vectors of each instance).
 
 The method per instance is that of davidson.davidson with one root: diagonal
 preconditioner (theta - H_II)^-1, convergence when ||H x - theta x|| <= tol.  The start
@@ -26,8 +34,6 @@ import torch
 
 from . import sci
 
-_PAD = 1e30   # diagonal of the padding rows: their preconditioned residual is zero
-
 
 @dataclass
 class BatchDavidsonResult:
@@ -37,120 +43,120 @@ class BatchDavidsonResult:
     iterations: int
     sigma_launches: int
     vectors: torch.Tensor       # concatenated [sum M_i], instance i at batch.offsets[i]
+    active_per_launch: list     # instances computed in each sigma launch
 
 
-class _Padded:
-    """Index maps between the concatenated vector of the batch ([sum M_i], instance i at
-    its offset) and the padded block [B, M_max]; the diagonal and the valid-row mask."""
-
-    def __init__(self, batch):
-        dev = batch.device
-        hams = batch.hams
-        self.B = len(hams)
-        Ms = torch.tensor([H.M for H in hams], device=dev)
-        self.Mmax = int(Ms.max())
-        self.Mtot = batch.M
-        off = torch.tensor(batch.offsets, device=dev)
-        inst = torch.repeat_interleave(torch.arange(self.B, device=dev), Ms)
-        self.flat = inst * self.Mmax + (torch.arange(self.Mtot, device=dev) - off[inst])
-        hd = torch.cat([H.diagonal() for H in hams])
-        diag = torch.full((self.B * self.Mmax,), _PAD, dtype=torch.float64, device=dev)
-        diag[self.flat] = hd
-        self.diag = diag.view(self.B, self.Mmax)
-        valid = torch.zeros(self.B * self.Mmax, dtype=torch.float64, device=dev)
-        valid[self.flat] = 1.0
-        self.valid = valid.view(self.B, self.Mmax)
-        # G entry of a null column: above the lowest Ritz values (bounded by the diagonal),
-        # small enough to keep eigh's absolute error at the level of the spectrum
-        self.penalty = 10.0 * float(hd.abs().max()) + 10.0
-        self.dev = dev
-
-    def to_concat(self, T):
-        return T.reshape(-1)[self.flat]
-
-    def from_concat(self, x):
-        out = torch.zeros(self.B * self.Mmax, dtype=torch.float64, device=self.dev)
-        out[self.flat] = x
-        return out.view(self.B, self.Mmax)
-
-    def start_block(self, nstart, seed=20250130, noise=1e-3):
-        """[B, Mmax, nstart]: unit vectors on the nstart lowest diagonal entries of each
-        instance plus seeded noise of norm ~noise (valid rows only)."""
-        g = torch.Generator(device="cpu").manual_seed(seed)
-        T = noise * torch.randn((self.B, self.Mmax, nstart), generator=g, dtype=torch.float64).to(self.dev)
-        T = T * self.valid[:, :, None] / max(1.0, self.Mmax ** 0.5)
-        idx = torch.argsort(self.diag, dim=1)[:, :nstart]              # [B, nstart]
-        unit = torch.eye(nstart, dtype=torch.float64, device=self.dev)[None].expand(self.B, nstart, nstart)
-        T.scatter_add_(1, idx[:, :, None].expand(self.B, nstart, nstart).contiguous(), unit.contiguous())
-        return T * self.valid[:, :, None]
+def start_block(offsets, diag: np.ndarray, nstart: int, seed: int = 20250130, noise: float = 1e-3) -> np.ndarray:
+    """[nstart, sum M_i]: per instance, unit vectors on its nstart lowest diagonal entries
+    (fewer if M_i < nstart) plus seeded N(0, noise^2 / M_i) entries."""
+    M = int(offsets[-1])
+    rng = np.random.default_rng(seed)
+    T = rng.standard_normal((nstart, M)) * noise
+    for s in range(len(offsets) - 1):
+        a, b = int(offsets[s]), int(offsets[s + 1])
+        if b == a:
+            continue
+        T[:, a:b] /= np.sqrt(b - a)
+        low = np.argsort(diag[a:b], kind="stable")[:nstart]
+        T[np.arange(len(low)), a + low] += 1.0
+    return T
 
 
 def davidson_batched(batch: "sci.Batch", tol: float = 1e-8, max_iter: int = 300, max_space: int = 24,
-                     keep: int = 2, nstart: int = 4, schedule: int = sci.SCI_SCHED_AUTO) -> BatchDavidsonResult:
+                     keep: int = 2, nstart: int = 4, schedule: int = sci.SCI_SCHED_AUTO,
+                     drop_converged: bool = True) -> BatchDavidsonResult:
     """Lowest eigenpair of every instance of `batch` (a sci.Batch of real spin-orbital
     Hamiltonians): converged when ||H x - theta x|| <= tol for every instance."""
-    pd = _Padded(batch)
-    B, Mmax, dev = pd.B, pd.Mmax, pd.dev
-    Cbuf = torch.zeros(pd.Mtot, dtype=torch.float64, device=dev)
-    Sbuf = torch.zeros(pd.Mtot, dtype=torch.float64, device=dev)
-    batch.plan(schedule, Cbuf.normal_(), Sbuf)
-    batch.capture(Cbuf, Sbuf)
-    launches = 0
-    V = torch.zeros((B, Mmax, max_space), dtype=torch.float64, device=dev)
+    dev = batch.device
+    f64 = dict(dtype=torch.float64, device=dev)
+    offsets = np.asarray(list(batch.offsets) + [batch.M], dtype=np.int64)
+    B, M = len(offsets) - 1, int(batch.M)
+    nstart = max(1, min(nstart, max_space - 1))
+    keep = max(1, min(keep, max_space - 1))
+    seg = sci.Segments(offsets, kmax=max_space, device=dev.index)
+    diag = torch.cat([H.diagonal() for H in batch.hams]).to(**f64)
+    penalty = 10.0 * float(diag.abs().max()) + 10.0 if M else 10.0
+    V = torch.zeros((max_space + keep, M), **f64)   # rows >= max_space: restart scratch
     Wm = torch.zeros_like(V)
-    G = torch.zeros((B, max_space, max_space), dtype=torch.float64, device=dev)
+    T = torch.zeros(M, **f64)
+    S = torch.zeros(M, **f64)
+    batch.plan(schedule, T.normal_(), S)
+    batch.capture(T, S)
+    G = torch.zeros((B, max_space, max_space), **f64)
+    ones = torch.ones(B, **f64)
+    act = np.ones(B, dtype=bool)          # instances not converged yet
+    act_dev = ones.clone()
+    launches, per_launch = 0, []
     k = 0
 
-    def append(T):
-        """Orthonormalise T [B, Mmax] against V[:, :, :k] (two passes), multiply it by H in
-        one replay of the captured launch and append both; a direction with no remaining
-        norm becomes a null column."""
+    def append():
+        """T holds one direction per instance (zero for an instance that takes none):
+        orthonormalise it against V[:k] (two Gram-Schmidt passes), multiply it by H in one
+        replay, and append it to V, W and G."""
         nonlocal k, launches
-        T = T * pd.valid
-        T = T / torch.linalg.vector_norm(T, dim=1, keepdim=True).clamp_min(1e-300)
+        n0 = seg.tn(T, T)[:, 0].clone()
         for _ in range(2):
             if k:
-                Vk = V[:, :, :k]
-                T = T - torch.bmm(Vk, torch.bmm(Vk.transpose(1, 2), T.unsqueeze(2))).squeeze(2)
-        nrm = torch.linalg.vector_norm(T, dim=1, keepdim=True)
-        null = nrm[:, 0] < 1e-8
-        T = torch.where(null[:, None], torch.zeros_like(T), T / nrm.clamp_min(1e-300))
-        Cbuf.copy_(pd.to_concat(T))
+                seg.nn(T, ones, A1=V[:k], c1=seg.tn(V[:k], T), alpha1=-1.0)
+        n1 = seg.tn(T, T)[:, 0]
+        live = n1 > 1e-16 * n0                     # False also where T was zero
+        scale = torch.where(live, torch.rsqrt(torch.where(live, n1, ones)), torch.zeros_like(n1))
+        seg.nn(T, scale)
         batch.replay()
         launches += 1
-        WT = pd.from_concat(Sbuf)
-        V[:, :, k] = T
-        Wm[:, :, k] = WT
-        g = torch.bmm(V[:, :, :k + 1].transpose(1, 2), WT.unsqueeze(2)).squeeze(2)   # [B, k+1]
+        per_launch.append(int(act.sum()) if drop_converged else B)
+        V[k].copy_(T)
+        Wm[k].copy_(S)
+        g = seg.tn(V[:k + 1], S)                    # [B, k+1]; zero for a null column
         G[:, :k + 1, k] = g
         G[:, k, :k + 1] = g
-        G[null, k, k] = pd.penalty
+        G[:, k, k] = torch.where(live, g[:, k], torch.full_like(n1, penalty))
         k += 1
 
-    start = pd.start_block(max(1, min(nstart, max_space - 1)))
-    for j in range(start.shape[2]):
-        append(start[:, :, j])
-    theta = rn = evecs = None
+    st = start_block(offsets, diag.cpu().numpy(), nstart)
+    for j in range(nstart):
+        T.copy_(torch.from_numpy(st[j]))
+        append()
+    del st
+    rn = np.zeros(B)
+    theta_h = np.zeros(B)
     it = 0
     for it in range(1, max_iter + 1):
-        evals, evecs = torch.linalg.eigh(0.5 * (G[:, :k, :k] + G[:, :k, :k].transpose(1, 2)))
-        theta, y = evals[:, 0], evecs[:, :, 0:1]
-        x = torch.bmm(V[:, :, :k], y).squeeze(2)
-        r = torch.bmm(Wm[:, :, :k], y).squeeze(2) - theta[:, None] * x
-        rn = torch.linalg.vector_norm(r, dim=1)
-        if bool((rn <= tol).all()):
+        evals, evecs = torch.linalg.eigh(G[:, :k, :k])
+        theta, y = evals[:, 0].contiguous(), evecs[:, :, 0].contiguous()
+        # residual H x - theta x = W y - theta V y of the running instances, into T
+        yc = y * act_dev[:, None]
+        seg.nn(T, None, A1=Wm[:k], c1=yc, A2=V[:k], c2=(theta[:, None] * yc).contiguous(), alpha2=-1.0)
+        host = torch.stack([torch.sqrt(seg.tn(T, T)[:, 0]), theta]).cpu().numpy()   # the one host read
+        rn = np.where(act, host[0], rn)
+        theta_h = np.where(act, host[1], theta_h)
+        done = act & (rn <= tol)
+        if done.any():
+            act &= ~done
+            act_dev = torch.from_numpy(act.astype(np.float64)).to(dev)
+            if drop_converged:
+                batch.set_active(act)
+        if not act.any():
             break
         if k == max_space:   # thick restart to the lowest `keep` Ritz vectors
             Y = evecs[:, :, :keep]
-            V[:, :, :keep] = torch.bmm(V[:, :, :k], Y)
-            Wm[:, :, :keep] = torch.bmm(Wm[:, :, :k], Y)
+            for j in range(keep):
+                cj = Y[:, :, j].contiguous()
+                seg.nn(V[max_space + j], None, A1=V[:k], c1=cj)
+                seg.nn(Wm[max_space + j], None, A1=Wm[:k], c1=cj)
+            V[:keep].copy_(V[max_space:max_space + keep])
+            Wm[:keep].copy_(Wm[max_space:max_space + keep])
             G.zero_()
             G[:, :keep, :keep] = torch.diag_embed(evals[:, :keep])
             k = keep
-        den = theta[:, None] - pd.diag
-        den = torch.where(den.abs() < 1e-8, torch.full_like(den, 1e-8), den)
-        append(torch.where(rn[:, None] > tol, r / den, torch.zeros_like(r)))
-    evals, evecs = torch.linalg.eigh(0.5 * (G[:, :k, :k] + G[:, :k, :k].transpose(1, 2)))
-    X = pd.to_concat(torch.bmm(V[:, :, :k], evecs[:, :, 0:1]).squeeze(2))
-    rnh = rn.cpu().numpy()
-    return BatchDavidsonResult(theta.cpu().numpy(), rnh, rnh <= tol, it, launches, X)
+        # preconditioned residual of the running instances: T / (theta - H_II)
+        seg.nn(T, act_dev, dg=diag, shift=theta)
+        append()
+    # Ritz vectors: unchanged for an instance since it converged (its later columns are
+    # null and decoupled, and restarts keep its lowest Ritz vectors)
+    evals, evecs = torch.linalg.eigh(G[:, :k, :k])
+    X = torch.empty(M, **f64)
+    seg.nn(X, None, A1=V[:k], c1=evecs[:, :, 0].contiguous())
+    batch.set_active(np.ones(B, dtype=bool))
+    seg.close()
+    return BatchDavidsonResult(theta_h, rn, rn <= tol, it, launches, X, per_launch)

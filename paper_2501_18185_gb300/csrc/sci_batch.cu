@@ -246,7 +246,8 @@ __device__ void warp_rows(const Inst &B, int64_t a, const double *C, double *S, 
 // ---------------------------------------------------------------- the persistent kernel
 __global__ void __launch_bounds__(kThreads)
 k_batch(const Inst *__restrict__ insts, const Item *__restrict__ items, int nitems, int *counter,
-        const double *__restrict__ C, double *__restrict__ S, const uint32_t *__restrict__ rank)
+        const double *__restrict__ C, double *__restrict__ S, const uint32_t *__restrict__ rank,
+        const int *__restrict__ active)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint16_t pairs[kMaxPairs];
@@ -260,6 +261,7 @@ k_batch(const Inst *__restrict__ insts, const Item *__restrict__ items, int nite
         const int it = s_item;
         if (it >= nitems) break;
         const Item I = items[it];
+        if (!active[I.inst]) continue;   // the same for every thread of the CTA
         const Inst &B = insts[I.inst];
         switch (I.type) {
             case IT_DIAG: tile_diag(B, I.a, C, S); break;
@@ -300,6 +302,9 @@ struct sci_batch {
     int nitems = 0, items_cap = 0;
     int *d_counter = nullptr;
     uint32_t *d_rank = nullptr;  // combinatorial ranks of all strings of kRankBits bits
+    int *d_active = nullptr;     // per instance: nonzero = computed
+    int active_n = 0;
+    std::vector<int> h_active;
     size_t smem = 0;
     int grid = 0;
     int64_t total_M = 0, total_pairs = 0;
@@ -358,9 +363,11 @@ int upload_items(sci_batch *b, const std::vector<Item> &items)
 
 int launch(sci_batch *b, const double *C, double *S)
 {
+    if (!b->d_active || b->active_n != (int)b->host.size()) return bfail(b, SCI_ERR_STATE, "batch launch: no complete plan");
     BCK(cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream));
     if (b->total_M > 0) BCK(cudaMemsetAsync(S, 0, sizeof(double) * b->total_M, b->stream));
-    k_batch<<<b->grid, kThreads, b->smem, b->stream>>>(b->d_inst, b->d_items, b->nitems, b->d_counter, C, S, b->d_rank);
+    k_batch<<<b->grid, kThreads, b->smem, b->stream>>>(b->d_inst, b->d_items, b->nitems, b->d_counter, C, S, b->d_rank,
+                                                        b->d_active);
     BCK(cudaGetLastError());
     return SCI_OK;
 }
@@ -396,6 +403,7 @@ extern "C" int sci_batch_destroy(sci_batch *b)
     if (b->d_items) cudaFree(b->d_items);
     if (b->d_counter) cudaFree(b->d_counter);
     if (b->d_rank) cudaFree(b->d_rank);
+    if (b->d_active) cudaFree(b->d_active);
     for (cudaEvent_t e : {b->ev_in, b->ev_out, b->t0, b->t1})
         if (e) cudaEventDestroy(e);
     if (b->stream) cudaStreamDestroy(b->stream);
@@ -445,6 +453,16 @@ extern "C" int sci_batch_plan(sci_batch *b, int schedule, const double *C, doubl
     b->d_inst = nullptr;
     BCK(cudaMalloc(&b->d_inst, sizeof(Inst) * std::max(1, ni)));
     if (ni) BCK(cudaMemcpy(b->d_inst, b->host.data(), sizeof(Inst) * ni, cudaMemcpyHostToDevice));
+    BCK(cudaStreamSynchronize(b->stream));
+    if (b->active_n != ni) {
+        if (b->d_active) cudaFree(b->d_active);
+        b->d_active = nullptr;
+        b->active_n = 0;
+        BCK(cudaMalloc(&b->d_active, sizeof(int) * std::max(1, ni)));
+        b->active_n = ni;
+    }
+    b->h_active.assign(std::max(1, ni), 1);
+    BCK(cudaMemcpy(b->d_active, b->h_active.data(), sizeof(int) * std::max(1, ni), cudaMemcpyHostToDevice));
     if (!b->d_rank) {
         BCK(cudaMalloc(&b->d_rank, sizeof(uint32_t) << kRankBits));
         k_rank_table<<<1024, kThreads, 0, b->stream>>>(b->d_rank);
@@ -493,7 +511,7 @@ extern "C" int sci_batch_plan(sci_batch *b, int schedule, const double *C, doubl
                 BCK(cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream));
                 BCK(cudaMemsetAsync(S + B.off, 0, sizeof(double) * B.M, b->stream));
                 k_batch<<<b->grid, kThreads, b->smem, b->stream>>>(b->d_inst, b->d_items, b->nitems, b->d_counter, C, S,
-                                                                    b->d_rank);
+                                                                    b->d_rank, b->d_active);
                 BCK(cudaGetLastError());
             }
             BCK(cudaEventRecord(b->t1, b->stream));
@@ -573,6 +591,18 @@ extern "C" int sci_batch_replay(sci_batch *b)
     BCK(cudaGraphLaunch(b->exec, b->stream));
     BCK(cudaEventRecord(b->ev_out, b->stream));
     BCK(cudaStreamWaitEvent(b->user, b->ev_out, 0));
+    return SCI_OK;
+}
+
+extern "C" int sci_batch_set_active(sci_batch *b, const int32_t *active, int n)
+{
+    if (!b) return SCI_ERR_ARG;
+    if (!b->d_active) return bfail(b, SCI_ERR_STATE, "batch_set_active: call sci_batch_plan first");
+    if (!active || n != (int)b->host.size() || n != b->active_n) return bfail(b, SCI_ERR_ARG, "batch_set_active: one flag per instance");
+    BCK(cudaSetDevice(b->device));
+    for (int i = 0; i < n; i++) b->h_active[i] = active[i] != 0;
+    // pageable source: the copy is staged before the call returns, so h_active may change after
+    if (n) BCK(cudaMemcpyAsync(b->d_active, b->h_active.data(), sizeof(int) * n, cudaMemcpyHostToDevice, b->stream));
     return SCI_OK;
 }
 

@@ -56,9 +56,16 @@ SIGNATURES = {
     "sci_batch_sigma": (_i32, [_vp, _vp, _vp]),
     "sci_batch_capture": (_i32, [_vp, _vp, _vp]),
     "sci_batch_replay": (_i32, [_vp]),
+    "sci_batch_set_active": (_i32, [_vp, _vp, _i32]),
     "sci_batch_info": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp]),
     "sci_batch_items": (_i32, [_vp, _vp, _i32]),
     "sci_batch_last_error": (ctypes.c_char_p, [_vp]),
+    "sci_seg_create": (_i32, [ctypes.POINTER(_vp), _i32, _i32, _vp, _i32, _vp]),
+    "sci_seg_destroy": (_i32, [_vp]),
+    "sci_seg_tn": (_i32, [_vp, _i32, _vp, _i64, _vp, _vp]),
+    "sci_seg_nn": (_i32, [_vp, _vp, _vp, _i32, _vp, _i64, _vp, ctypes.c_double, _i32, _vp, _i64, _vp,
+                          ctypes.c_double, _vp, _vp]),
+    "sci_seg_last_error": (ctypes.c_char_p, [_vp]),
     "sci_bv_gemm_tn": (_i32, [_vp, _i64, _i32, _i32, _vp, _i64, _vp, _i64, _vp, _i32]),
     "sci_bv_gemm_nn": (_i32, [_vp, _i64, _i32, _vp, _i64, _i32, _vp, _vp, _i64, _i32, _vp, ctypes.c_double, _vp,
                               _i64, _vp, _vp, _vp, _i32]),
@@ -259,6 +266,11 @@ def sci_batch_replay(b):
     return _bcheck(b, load().sci_batch_replay(b))
 
 
+def sci_batch_set_active(b, active):
+    a = np.ascontiguousarray(active, dtype=np.int32)
+    return _bcheck(b, load().sci_batch_set_active(b, _p(a), int(a.size)))
+
+
 def sci_batch_info(b, i) -> dict:
     sch = ctypes.c_int()
     mt, mw = ctypes.c_float(), ctypes.c_float()
@@ -272,6 +284,35 @@ def sci_batch_items(b) -> dict:
     out = np.zeros(4, dtype=np.int64)
     _bcheck(b, load().sci_batch_items(b, _p(out), 4))
     return dict(zip(["items", "ctas", "M", "pairs"], (int(v) for v in out)))
+
+
+def _scheck(sg, rc):
+    if rc < 0:
+        msg = load().sci_seg_last_error(sg) if sg else b""
+        raise SciError(rc, (msg or b"").decode())
+    return rc
+
+
+def sci_seg_create(device, offsets, kmax, stream=None):
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    sg = ctypes.c_void_p()
+    rc = load().sci_seg_create(ctypes.byref(sg), device, int(off.size) - 1, _p(off), int(kmax), ctypes.c_void_p(stream or 0))
+    if rc != SCI_OK:
+        raise SciError(rc, "sci_seg_create failed")
+    return sg
+
+
+def sci_seg_destroy(sg):
+    return load().sci_seg_destroy(sg)
+
+
+def sci_seg_tn(sg, k, A, lda, t, out):
+    return _scheck(sg, load().sci_seg_tn(sg, k, _p(A), lda, _p(t), _p(out)))
+
+
+def sci_seg_nn(sg, y, beta, k1, A1, lda1, c1, alpha1, k2, A2, lda2, c2, alpha2, dg=None, shift=None):
+    return _scheck(sg, load().sci_seg_nn(sg, _p(y), _p(beta), k1, _p(A1), lda1, _p(c1), float(alpha1), k2, _p(A2), lda2,
+                                         _p(c2), float(alpha2), _p(dg), _p(shift)))
 
 
 def sci_bv_gemm_tn(ctx, M, k, a, A, lda, B, ldb, P, prec):
@@ -484,8 +525,67 @@ class Batch:
     def replay(self):
         sci_batch_replay(self.b)
 
+    def set_active(self, active):
+        """Per-instance flags (nonzero = computed) for later launches and replays."""
+        sci_batch_set_active(self.b, active)
+
     def info(self, i: int) -> dict:
         return sci_batch_info(self.b, i)
 
     def items(self) -> dict:
         return sci_batch_items(self.b)
+
+
+class Segments:
+    """Segmented block-vector products over vectors stored end to end (instance s on rows
+    offsets[s] : offsets[s+1] of one float64 CUDA array); blocks are column-major
+    [k, total rows] tensors whose rows are the columns of the block."""
+
+    def __init__(self, offsets, kmax: int, device: int = 0, stream=None):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        self.nseg, self.M, self.kmax = len(self.offsets) - 1, int(self.offsets[-1]), int(kmax)
+        self.sg = sci_seg_create(device, self.offsets, kmax, s.cuda_stream)
+
+    def close(self):
+        if getattr(self, "sg", None) is not None:
+            sci_seg_destroy(self.sg)
+            self.sg = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _ld(A):
+        return int(A.stride(0)) if A.dim() == 2 else 0
+
+    def tn(self, A, t, out=None):
+        """[nseg, k]: per instance, the dot products of the k rows of A [k, M] with t [M]."""
+        A2 = A if A.dim() == 2 else A.view(1, -1)
+        k = A2.shape[0]
+        assert A2.stride(1) == 1 and t.stride(0) == 1 and A2.shape[1] == self.M and t.shape[0] == self.M
+        if out is None:
+            out = self.torch.empty((self.nseg, k), dtype=self.torch.float64, device=self.device)
+        sci_seg_tn(self.sg, k, A2, self._ld(A2), t, out)
+        return out
+
+    def nn(self, y, beta=None, A1=None, c1=None, alpha1=1.0, A2=None, c2=None, alpha2=1.0, dg=None, shift=None):
+        """y = beta_s y + alpha1 A1^T c1_s + alpha2 A2^T c2_s per instance, then / (shift_s - dg)
+        if dg is given (A: [k, M] row blocks, c: [nseg, k], beta and shift: [nseg])."""
+        def op(A, c):
+            if A is None or A.shape[0] == 0:
+                return 0, None, 0, None
+            assert A.stride(1) == 1 and A.shape[1] == self.M and c.shape == (self.nseg, A.shape[0]) and c.is_contiguous()
+            return A.shape[0], A, int(A.stride(0)), c
+        k1, A1, l1, c1 = op(A1, c1)
+        k2, A2, l2, c2 = op(A2, c2)
+        assert y.stride(0) == 1 and y.shape[0] == self.M
+        sci_seg_nn(self.sg, y, beta, k1, A1, l1, c1, alpha1, k2, A2, l2, c2, alpha2, dg, shift)
+        return y

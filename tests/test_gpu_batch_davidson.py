@@ -7,7 +7,8 @@
   to 1e-9 Eh (the residual bound gives |dE| <= rn^2 / gap, far below that);
 - each returned vector has unit norm and, through the instance's own sci_sigma, the
   residual the solver reports;
-- the launch count: the start block, then one launch per iteration that did not converge.
+- the launch count: the start block, then one launch per iteration that did not converge;
+- instances leave the batched launch as they converge, without changing the results.
 """
 import numpy as np
 import pytest
@@ -30,6 +31,14 @@ def test_batched_ground_states(gpu):
     res = davidson_batched(B, tol=1e-8, max_iter=400, nstart=4)
     assert res.converged.all(), [w.name for w, c in zip(ws, res.converged) if not c]
     assert res.sigma_launches == 4 + res.iterations - 1
+    # converged instances leave the launch: the active count never grows, and the null
+    # columns they take have a zero product either way, so the results agree with the
+    # solve that keeps every instance in the launch (to rounding: the TILE schedule sums
+    # into S by FP64 atomics, in no fixed order)
+    per = res.active_per_launch
+    assert per[0] == len(ws) and all(a >= b for a, b in zip(per, per[1:])) and per[-1] < len(ws)
+    full = davidson_batched(sci.Batch(hams), tol=1e-8, max_iter=400, nstart=4, drop_converged=False)
+    assert full.converged.all() and np.abs(full.energies - res.energies).max() < 1e-10
     X = res.vectors
     for i, (w, H, off) in enumerate(zip(ws, hams, B.offsets)):
         if w.M <= 3000:
