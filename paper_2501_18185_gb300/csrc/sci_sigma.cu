@@ -151,24 +151,27 @@ k_doubles(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_cod
         const uint32_t code = e_code[r0 + q0], pos = e_pos[r0 + q0];
         uint32_t rowoff, colbase;
         sci::pair_offsets(tr, sci::code_x(code), sci::code_y(code), rowoff, colbase);
-        const int bs = q0 - sci::pos_off(pos), be = bs + sci::pos_size(pos);
+        const int bs = q0 - sci::pos_off(pos), je = bs + sci::pos_size(pos) - 1;
         const uint32_t rc = row_code(code);
         const TS *trow = tab + rowoff;
         TA acc[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) zero(acc[v]);
-        int j = bs;
-        // groups of kUnroll members: a group with no double of this row (members equal
-        // to the row or single excitations of it) is skipped, and so is the whole warp's
+        // the members other than the row itself: j in [bs, je) stands for bucket position
+        // j + (j >= q0), so rows of equal bucket size (windows hold buckets of one size,
+        // largest first) run the same trip count and no FP64 FMA is spent on the row (one
+        // in 3.5 members on average).  Groups of kUnroll members: a group with no double
+        // of this row (single excitations of it) is skipped, and so is the whole warp's
         // work when no lane has one; otherwise up to kUnroll table loads are in flight per
         // thread and a non-double member contributes t = 0
-        for (; j + kUnroll <= be; j += kUnroll) {
+        int j = bs;
+        for (; j + kUnroll <= je; j += kUnroll) {
             uint2 kc[kUnroll];
             TS t[kUnroll];
             unsigned vm = 0;
 #pragma unroll
             for (int u = 0; u < kUnroll; u++) {
-                kc[u] = s_kc[j + u];
+                kc[u] = s_kc[j + u + (j + u >= q0)];
                 vm |= (unsigned)disjoint(rc, kc[u].x) << u;
             }
             if (vm == 0) continue;
@@ -180,14 +183,15 @@ k_doubles(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_cod
 #pragma unroll
             for (int u = 0; u < kUnroll; u++)
 #pragma unroll
-                for (int v = 0; v < NV; v++) fma_acc(acc[v], t[u], s_c[(j + u) * NV + v]);
+                for (int v = 0; v < NV; v++) fma_acc(acc[v], t[u], s_c[(j + u + (j + u >= q0)) * NV + v]);
         }
-        for (; j < be; j++) {
-            const uint2 kc = s_kc[j];
+        for (; j < je; j++) {
+            const int m = j + (j >= q0);
+            const uint2 kc = s_kc[m];
             if (!disjoint(rc, kc.x)) continue;
             const TS t = ldg(trow + kc.y);
 #pragma unroll
-            for (int v = 0; v < NV; v++) fma_acc(acc[v], t, s_c[j * NV + v]);
+            for (int v = 0; v < NV; v++) fma_acc(acc[v], t, s_c[m * NV + v]);
         }
         const uint32_t idx = e_idx[r0 + q0];
         const bool par = sci::code_par(code);
@@ -283,6 +287,8 @@ k_doubles_f32(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e
         Ds acc[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) ds_zero(acc[v]);
+        // all members, the row itself included (t = 0): this kernel is bound by its FP64
+        // atomics, and the aligned walk keeps lanes of one bucket on the same member
         int j = bs;
         for (; j + kUnroll <= be; j += kUnroll) {
             uint2 kc[kUnroll];
@@ -369,6 +375,9 @@ k_doubles_ds(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_
         Ds acc[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) ds_zero(acc[v]);
+        // all members, the row itself included (it contributes t = 0): lanes of one bucket
+        // then read the same member and neighbouring table entries at every step, which
+        // this LSU-bound kernel needs more than the skipped arithmetic
         int j = bs;
         for (; j + kUnroll <= be; j += kUnroll) {
             uint2 kc[kUnroll];
@@ -438,22 +447,24 @@ k_doubles_dsz(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e
         const uint32_t code = e_code[r0 + q0], pos = e_pos[r0 + q0];
         uint32_t rowoff, colbase;
         sci::pair_offsets(tr, sci::code_x(code), sci::code_y(code), rowoff, colbase);
-        const int bs = q0 - sci::pos_off(pos), be = bs + sci::pos_size(pos);
+        const int bs = q0 - sci::pos_off(pos), je = bs + sci::pos_size(pos) - 1;
         const uint32_t rc = row_code(code);
         const float4 *trow = tab4 + rowoff;
         Ds ar[NV], ai[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) ds_zero(ar[v]), ds_zero(ai[v]);
         int nused = 0;
-        for (int j = bs; j < be; j++) {
-            const uint2 kc = s_kc[j];
+        // the members other than the row itself (bucket position j + (j >= q0))
+        for (int j = bs; j < je; j++) {
+            const int m = j + (j >= q0);
+            const uint2 kc = s_kc[m];
             if (!disjoint(rc, kc.x)) continue;
             const float4 t = __ldg(trow + kc.y);
             const float2 tr_ = make_float2(t.x, t.y), ti = make_float2(t.z, t.w);
             const float2 mti = make_float2(-t.z, -t.w);
 #pragma unroll
             for (int v = 0; v < NV; v++) {
-                const float4 c = s_c[j * NV + v];
+                const float4 c = s_c[m * NV + v];
                 const float2 cr = make_float2(c.x, c.y), ci = make_float2(c.z, c.w);
                 ds_fma(ar[v], tr_, cr);
                 ds_fma(ar[v], mti, ci);
