@@ -91,13 +91,16 @@ __device__ void tile_doubles(const Inst &B, int64_t b, const double *C, double *
         const uint32_t code = B.e2_code[r0 + q0], pos = B.e2_pos[r0 + q0];
         uint32_t rowoff, colbase;
         sci::pair_offsets(tr, sci::code_x(code), sci::code_y(code), rowoff, colbase);
-        const int bs = q0 - sci::pos_off(pos), be = bs + sci::pos_size(pos);
+        // the members other than the row itself (bucket position j + (j >= q0)): no FP64
+        // instruction is issued for the row, and rows of one bucket size run equal counts
+        const int bs = q0 - sci::pos_off(pos), je = bs + sci::pos_size(pos) - 1;
         const uint32_t rc = sci::row_code(code);
         const double *trow = B.tab + rowoff;
         double acc = 0.0;
-        for (int j = bs; j < be; j++) {
-            const uint2 kc = s_kc[j];
-            if (sci::disjoint(rc, kc.x)) acc = fma(__ldg(trow + kc.y), s_c[j], acc);
+        for (int j = bs; j < je; j++) {
+            const int m = j + (j >= q0);
+            const uint2 kc = s_kc[m];
+            if (sci::disjoint(rc, kc.x)) acc = fma(__ldg(trow + kc.y), s_c[m], acc);
         }
         if (acc != 0.0) atomicAdd(S + B.off + B.e2_idx[r0 + q0], sflip(sci::code_par(code), acc));
     }
