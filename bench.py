@@ -156,7 +156,9 @@ def cpu_baseline(w, budget_s: float = 12.0, seed: int = 0):
 
 def davidson_bench(H, w, nroots=8, tol=1e-6):
     """Time to the lowest `nroots` energies: plain FP64 Davidson against the FP32-storage
-    block Davidson with FP64 refinement (and against FP64-accurate paired-FP32 sigma).
+    block Davidson with FP64 refinement (its residual estimates in paired FP32, and in
+    FP64 beside it; with paired-FP32 block kernels throughout; and plain Davidson on the
+    FP64-accurate paired-FP32 sigma).
     E_ref is a tight FP64 run (residual 1e-8, energy error ~ residual^2 / gap); every
     energy's error against it is reported.  Wall-clock seconds, each solver timed after
     one untimed warm-up sigma; the sigma time of each precision at `nroots` vectors is
@@ -195,6 +197,8 @@ def davidson_bench(H, w, nroots=8, tol=1e-6):
            "E_ref": [float(x) for x in e_ref], f"sigma_ms_nvec{nroots}": sig_ms}
     for name, run in (("fp64", lambda: davidson(hi, diag, nroots=nroots, tol=tol, max_iter=600)),
                       ("fp32_refined", lambda: davidson_mixed(lo, hi, diag, nroots=nroots, tol=tol, max_iter=600)),
+                      ("fp32_refined_f64_estimates", lambda: davidson_mixed(lo, hi, diag, nroots=nroots, tol=tol,
+                                                                            max_iter=600, est_arith="f64")),
                       ("fp32_refined_dsblock", lambda: davidson_mixed(lo, hi, diag, nroots=nroots, tol=tol,
                                                                       max_iter=600, arith="ds")),
                       ("ds", lambda: davidson(ds, diag, nroots=nroots, tol=tol, max_iter=600))):

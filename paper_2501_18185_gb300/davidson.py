@@ -249,12 +249,13 @@ class _Space:
         self.ex = np.full(m, bool(self.ex.all()))
         self.k = m
 
-    def residual(self, Y, theta, diag):
+    def residual(self, Y, theta, diag, ops=None):
         """Preconditioned residuals (H x - theta x) / (theta - H_II) of the Ritz vectors
-        x = V Y, written to V[:, k:k+r]; returns the residual 2-norms."""
+        x = V Y, written to V[:, k:k+r]; returns the residual 2-norms.  ops: the block
+        backend for this product (default: the space's own)."""
         k, r = self.k, Y.shape[1]
-        cs = self.ops.nn(self.V[:, k:], r, A1=self.W[:, :k], S1=Y, A2=self.V[:, :k], S2=-(Y * theta[None, :]),
-                         dg=diag, shift=theta, colsq=True)
+        cs = (ops or self.ops).nn(self.V[:, k:], r, A1=self.W[:, :k], S1=Y, A2=self.V[:, :k],
+                                  S2=-(Y * theta[None, :]), dg=diag, shift=theta, colsq=True)
         return np.sqrt(np.maximum(cs, 0.0))
 
     def ritz_vectors(self, Y):
@@ -351,7 +352,7 @@ def _result(sp, theta, Y, rn, it, calls, conv, hist, lo, hi):
 def davidson_mixed(sigma_lo, sigma_hi, diag: torch.Tensor, nroots: int = 1, tol: float = 1e-6,
                    max_iter: int = 400, max_space: int | None = None, keep: int | None = None,
                    guess: torch.Tensor | None = None, dtype=torch.float64, ops=None,
-                   arith: str = "f64") -> DavidsonResult:
+                   arith: str = "f64", est_arith: str | None = "ds") -> DavidsonResult:
     """Davidson with low-precision products for the correction vectors and FP64 refinement.
 
     sigma_lo(X) -> H X from the FP32-storage sigma (C rounded to FP32, exact products,
@@ -366,9 +367,17 @@ def davidson_mixed(sigma_lo, sigma_hi, diag: torch.Tensor, nroots: int = 1, tol:
     exact side (v_i^+ (H v_j) or (H v_i)^+ v_j), so the FP32 error stays in the block of
     low-precision columns, whose coefficients in the Ritz vectors are of the size of the
     residual.  FP64 is kept for the Gram-Schmidt, the subspace matrix, the Rayleigh
-    quotient and the final energies.
+    quotient, the final energies and the exact residuals that decide convergence.
+
+    est_arith: block arithmetic of the residual estimates of iterations whose space holds
+    low-precision columns ("ds": paired FP32, the default; "f64" or None: the space's
+    own).  Those residuals carry the FP32-storage error of sigma_lo; the paired-FP32
+    product adds ~2^-47 of its operands, far below it, at ~5x the FP64 rate.
     """
     sp, a, keep, max_space = _start(sigma_lo, diag, nroots, max_space, keep, guess, dtype, ops, arith)
+    est_ops = None
+    if est_arith == "ds" and isinstance(sp.ops, SciBlockOps) and arith == "f64":
+        est_ops = SciBlockOps(diag.device, "ds")
     calls_lo, calls_hi = 0, 0
     best_est, stall = None, 0
     hist = []
@@ -387,9 +396,9 @@ def davidson_mixed(sigma_lo, sigma_hi, diag: torch.Tensor, nroots: int = 1, tol:
         sp.append(a, WT, exact_next, True)
         exact_next = False
         evals, evecs, theta, Y = _ritz(sp, nroots)
-        rn = sp.residual(Y, theta, diag)
-        rmax = float(rn.max())
         exact = bool(sp.ex.all())
+        rn = sp.residual(Y, theta, diag, ops=None if exact else est_ops)
+        rmax = float(rn.max())
         hist.append((it, theta.copy(), rn.copy(), exact))
         if exact and rmax <= tol:
             return _result(sp, theta, Y, rn, it, calls_lo + calls_hi, True, hist, calls_lo, calls_hi)
