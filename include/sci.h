@@ -354,6 +354,23 @@ int sci_seg_nn(sci_seg *s, double *y, const double *beta, int k1, const double *
                const double *c2, double alpha2, const double *dg, const double *shift);
 const char *sci_seg_last_error(const sci_seg *s);
 
+/* Eigenpairs of nb real symmetric n x n matrices (the projected matrices of the solvers
+ * above), one CTA each: cyclic Jacobi with the parallel round-robin ordering (Golub and
+ * Van Loan, Matrix Computations, Sec. 8.5).  Device pointers, asynchronous on
+ * cuda_stream (NULL: the legacy default stream).
+ *   A: matrix b at A + b * strideA, row-major with leading dimension lda; both triangles
+ *      are read and (a_ij + a_ji) / 2 is used.  Not modified.
+ *   w: eigenvalues of matrix b, ascending, at w + b * stridew.
+ *   V: eigenvectors as columns (V[i][j] = component i of eigenvector j, same order as w),
+ *      matrix b at V + b * strideV with leading dimension ldv.
+ *   Sweeps stop when the off-diagonal sum of squares is below 1e-30 of the total, or
+ *   after max_sweeps; not_converged (device int, or NULL) is then incremented per matrix.
+ * 1 <= n <= 64 (n = 0 or nb = 0: nothing to do).  Errors: SCI_ERR_ARG for sizes, strides
+ * or NULL pointers; SCI_ERR_CUDA. */
+int sci_syev_batched(int device, int nb, int n, const double *A, int64_t lda, int64_t strideA,
+                     double *w, int64_t stridew, double *V, int64_t ldv, int64_t strideV,
+                     int max_sweeps, int *not_converged, void *cuda_stream);
+
 /* Wait for the context stream and return the device status word (SCI_OK or the first
  * device-side error code). */
 int sci_sync_status(sci_ctx *ctx);

@@ -11,9 +11,9 @@ The vectors of all instances lie end to end, as in the batch: the search space i
 column-major block V [k, sum M_i] (and W = H V), without padding.  Projections, norms,
 Gram-Schmidt updates, residuals and the diagonal preconditioner are the segmented
 products of libsci (sci_seg_tn / sci_seg_nn), one launch each for all instances.  The
-projected matrices G_i = V_i^T H V_i stay on the device, [B, k, k], and their lowest
-eigenpairs come from one batched symmetric eigensolver call; the only host read per
-iteration is the vector of residual norms.
+projected matrices G_i = V_i^T H V_i stay on the device, [B, k, k], and their
+eigenpairs come from one launch of libsci's batched Jacobi eigensolver
+(sci_syev_batched); the only host read per iteration is the vector of residual norms.
 
 All instances grow their space together (one column per iteration).  An instance that
 has converged, or whose space is exhausted (M_i <= k), takes a null column: zero vector,
@@ -83,6 +83,12 @@ def davidson_batched(batch: "sci.Batch", tol: float = 1e-8, max_iter: int = 300,
     batch.plan(schedule, T.normal_(), S)
     batch.capture(T, S)
     G = torch.zeros((B, max_space, max_space), **f64)
+    ev_w = torch.empty((B, max_space), **f64)
+    ev_V = torch.empty((B, max_space, max_space), **f64)
+
+    def eig(k):
+        """Eigenpairs of every G_s[:k, :k], ascending (one batched Jacobi launch)."""
+        return sci.syev_batched(G, n=k, w=ev_w, V=ev_V)
     ones = torch.ones(B, **f64)
     act = np.ones(B, dtype=bool)          # instances not converged yet
     act_dev = ones.clone()
@@ -122,7 +128,7 @@ def davidson_batched(batch: "sci.Batch", tol: float = 1e-8, max_iter: int = 300,
     theta_h = np.zeros(B)
     it = 0
     for it in range(1, max_iter + 1):
-        evals, evecs = torch.linalg.eigh(G[:, :k, :k])
+        evals, evecs = eig(k)
         theta, y = evals[:, 0].contiguous(), evecs[:, :, 0].contiguous()
         # residual H x - theta x = W y - theta V y of the running instances, into T
         yc = y * act_dev[:, None]
@@ -154,7 +160,7 @@ def davidson_batched(batch: "sci.Batch", tol: float = 1e-8, max_iter: int = 300,
         append()
     # Ritz vectors: unchanged for an instance since it converged (its later columns are
     # null and decoupled, and restarts keep its lowest Ritz vectors)
-    evals, evecs = torch.linalg.eigh(G[:, :k, :k])
+    evals, evecs = eig(k)
     X = torch.empty(M, **f64)
     seg.nn(X, None, A1=V[:k], c1=evecs[:, :, 0].contiguous())
     batch.set_active(np.ones(B, dtype=bool))

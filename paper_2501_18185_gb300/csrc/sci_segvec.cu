@@ -108,6 +108,134 @@ k_seg_nn(const SegItem *__restrict__ items, double *y, const double *__restrict_
     }
 }
 
+// ---------------------------------------------------------------- batched eigensolver
+// Eigenpairs of many small real symmetric matrices (the projected matrices G_s of the
+// solvers), one CTA per matrix: the cyclic Jacobi method with the parallel (round-robin)
+// ordering (Golub and Van Loan, Matrix Computations, Sec. 8.5).  A sweep is m - 1 steps
+// (m = n rounded up to even); a step applies m/2 disjoint plane rotations at once, each
+// chosen to zero its off-diagonal entry, as A <- J^T A J (rows, then columns) and V <- V J.
+// Sweeps stop when the off-diagonal sum of squares falls below kJacobiTol^2 of the total,
+// or after max_sweeps (then *not_converged is incremented).  The matrix and V live in
+// shared memory (row stride n + 1).
+constexpr int kJacobiThreads = 256;
+constexpr int kJacobiNmax = 64;
+constexpr double kJacobiTol = 1e-15;
+
+__device__ __forceinline__ void jacobi_pair(int m, int step, int t, int &p, int &q)
+{
+    // circle method: player m-1 fixed, players 0..m-2 rotate
+    int x, y;
+    if (t == 0) {
+        x = step;
+        y = m - 1;
+    } else {
+        x = (step + t) % (m - 1);
+        y = (step - t + (m - 1)) % (m - 1);
+    }
+    p = min(x, y);
+    q = max(x, y);
+}
+
+__global__ void __launch_bounds__(kJacobiThreads)
+k_syev_jacobi(int n, const double *__restrict__ A, int64_t lda, int64_t sA, double *__restrict__ w, int64_t sw,
+              double *__restrict__ V, int64_t ldv, int64_t sV, int max_sweeps, int *not_converged)
+{
+    extern __shared__ double sm[];
+    const int ld = n + 1;
+    double *a = sm, *v = sm + n * ld;
+    __shared__ double s_c[kJacobiNmax / 2], s_s[kJacobiNmax / 2];
+    __shared__ int s_p[kJacobiNmax / 2], s_q[kJacobiNmax / 2];
+    __shared__ double s_red[2][kJacobiThreads / 32];
+    __shared__ int s_done;
+    const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const double *Ab = A + (int64_t)b * sA;
+    for (int e = tid; e < n * n; e += kJacobiThreads) {
+        const int i = e / n, j = e % n;
+        a[i * ld + j] = 0.5 * (Ab[(int64_t)i * lda + j] + Ab[(int64_t)j * lda + i]);
+        v[i * ld + j] = i == j ? 1.0 : 0.0;
+    }
+    const int m = (n + 1) & ~1, npair = m / 2;
+    __syncthreads();
+    bool converged = n <= 1;
+    for (int sweep = 0; sweep < max_sweeps && !converged; sweep++) {
+        double off = 0.0, tot = 0.0;
+        for (int e = tid; e < n * n; e += kJacobiThreads) {
+            const int i = e / n, j = e % n;
+            const double x = a[i * ld + j] * a[i * ld + j];
+            tot += x;
+            if (i != j) off += x;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+            tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        }
+        if (lane == 0) s_red[0][warp] = off, s_red[1][warp] = tot;
+        __syncthreads();
+        if (tid == 0) {
+            double o2 = 0.0, t2 = 0.0;
+            for (int k = 0; k < kJacobiThreads / 32; k++) o2 += s_red[0][k], t2 += s_red[1][k];
+            s_done = o2 <= kJacobiTol * kJacobiTol * t2;
+        }
+        __syncthreads();
+        converged = s_done;
+        if (converged) break;
+        for (int step = 0; step < m - 1; step++) {
+            if (tid < npair) {
+                int p, q;
+                jacobi_pair(m, step, tid, p, q);
+                double c = 1.0, s = 0.0;
+                if (q < n) {
+                    const double apq = a[p * ld + q];
+                    if (apq != 0.0) {
+                        const double tau = (a[q * ld + q] - a[p * ld + p]) / (2.0 * apq);
+                        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                        c = 1.0 / sqrt(1.0 + t * t);
+                        s = t * c;
+                    }
+                }
+                s_p[tid] = p, s_q[tid] = q, s_c[tid] = c, s_s[tid] = s;
+            }
+            __syncthreads();
+            // rows p, q of A (pairs with the padding index m - 1 = n, or no rotation, are skipped)
+            for (int e = tid; e < npair * n; e += kJacobiThreads) {
+                const int t = e / n, j = e % n, p = s_p[t], q = s_q[t];
+                const double c = s_c[t], s = s_s[t];
+                if (q >= n || s == 0.0) continue;
+                const double x = a[p * ld + j], y = a[q * ld + j];
+                a[p * ld + j] = c * x - s * y;
+                a[q * ld + j] = s * x + c * y;
+            }
+            __syncthreads();
+            // columns p, q of A and of V
+            for (int e = tid; e < npair * n; e += kJacobiThreads) {
+                const int t = e / n, i = e % n, p = s_p[t], q = s_q[t];
+                const double c = s_c[t], s = s_s[t];
+                if (q >= n || s == 0.0) continue;
+                const double x = a[i * ld + p], y = a[i * ld + q];
+                a[i * ld + p] = c * x - s * y;
+                a[i * ld + q] = s * x + c * y;
+                const double vx = v[i * ld + p], vy = v[i * ld + q];
+                v[i * ld + p] = c * vx - s * vy;
+                v[i * ld + q] = s * vx + c * vy;
+            }
+            __syncthreads();
+        }
+    }
+    if (!converged && tid == 0 && not_converged) atomicAdd(not_converged, 1);
+    // ascending order: eigenvalue j goes to the position of its rank (ties by index)
+    for (int j = tid; j < n; j += kJacobiThreads) {
+        const double lj = a[j * ld + j];
+        int r = 0;
+        for (int i = 0; i < n; i++) {
+            const double li = a[i * ld + i];
+            r += (li < lj) || (li == lj && i < j);
+        }
+        w[(int64_t)b * sw + r] = lj;
+        for (int i = 0; i < n; i++) V[(int64_t)b * sV + (int64_t)i * ldv + r] = v[i * ld + j];
+    }
+}
+
 }  // namespace
 
 struct sci_seg {
@@ -218,3 +346,22 @@ extern "C" int sci_seg_nn(sci_seg *s, double *y, const double *beta, int k1, con
 }
 
 extern "C" const char *sci_seg_last_error(const sci_seg *s) { return s ? s->err.c_str() : "null segment set"; }
+
+extern "C" int sci_syev_batched(int device, int nb, int n, const double *A, int64_t lda, int64_t strideA, double *w,
+                                int64_t stridew, double *V, int64_t ldv, int64_t strideV, int max_sweeps,
+                                int *not_converged, void *cuda_stream)
+{
+    if (nb < 0 || n < 0 || n > kJacobiNmax || max_sweeps < 1) return SCI_ERR_ARG;
+    if (nb == 0 || n == 0) return SCI_OK;
+    if (!A || !w || !V || lda < n || ldv < n || stridew < n || strideA < (int64_t)(n - 1) * lda + n ||
+        strideV < (int64_t)(n - 1) * ldv + n)
+        return SCI_ERR_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return SCI_ERR_CUDA;
+    const size_t smem = sizeof(double) * 2 * (size_t)n * (n + 1);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k_syev_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return SCI_ERR_CUDA;
+    k_syev_jacobi<<<nb, kJacobiThreads, smem, (cudaStream_t)cuda_stream>>>(n, A, lda, strideA, w, stridew, V, ldv, strideV,
+                                                                         max_sweeps, not_converged);
+    return cudaGetLastError() == cudaSuccess ? SCI_OK : SCI_ERR_CUDA;
+}

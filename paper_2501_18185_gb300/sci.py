@@ -66,6 +66,7 @@ SIGNATURES = {
     "sci_seg_nn": (_i32, [_vp, _vp, _vp, _i32, _vp, _i64, _vp, ctypes.c_double, _i32, _vp, _i64, _vp,
                           ctypes.c_double, _vp, _vp]),
     "sci_seg_last_error": (ctypes.c_char_p, [_vp]),
+    "sci_syev_batched": (_i32, [_i32, _i32, _i32, _vp, _i64, _i64, _vp, _i64, _vp, _i64, _i64, _i32, _vp, _vp]),
     "sci_bv_gemm_tn": (_i32, [_vp, _i64, _i32, _i32, _vp, _i64, _vp, _i64, _vp, _i32]),
     "sci_bv_gemm_nn": (_i32, [_vp, _i64, _i32, _vp, _i64, _i32, _vp, _vp, _i64, _i32, _vp, ctypes.c_double, _vp,
                               _i64, _vp, _vp, _vp, _i32]),
@@ -313,6 +314,35 @@ def sci_seg_tn(sg, k, A, lda, t, out):
 def sci_seg_nn(sg, y, beta, k1, A1, lda1, c1, alpha1, k2, A2, lda2, c2, alpha2, dg=None, shift=None):
     return _scheck(sg, load().sci_seg_nn(sg, _p(y), _p(beta), k1, _p(A1), lda1, _p(c1), float(alpha1), k2, _p(A2), lda2,
                                          _p(c2), float(alpha2), _p(dg), _p(shift)))
+
+
+def sci_syev_batched(device, nb, n, A, lda, strideA, w, stridew, V, ldv, strideV, max_sweeps=30, not_converged=None,
+                     stream=None):
+    rc = load().sci_syev_batched(device, nb, n, _p(A), lda, strideA, _p(w), stridew, _p(V), ldv, strideV, max_sweeps,
+                                 _p(not_converged), ctypes.c_void_p(stream or 0))
+    if rc != SCI_OK:
+        raise SciError(rc, "sci_syev_batched failed")
+    return rc
+
+
+def syev_batched(G, n=None, w=None, V=None, max_sweeps=30):
+    """Eigenvalues (ascending) and eigenvectors (columns) of the leading n x n blocks of
+    the symmetric float64 CUDA matrices G [nb, >= n, >= n] (row-major inner dims).
+    Returns (w [nb, n], V [nb, n, n]) as views of the given or new buffers."""
+    import torch
+
+    nb = G.shape[0]
+    n = G.shape[1] if n is None else n
+    assert G.dtype == torch.float64 and G.is_cuda and G.stride(2) == 1
+    if w is None:
+        w = torch.empty((nb, n), dtype=torch.float64, device=G.device)
+    if V is None:
+        V = torch.empty((nb, n, n), dtype=torch.float64, device=G.device)
+    assert w.stride(1) == 1 and V.stride(2) == 1 and w.shape[1] >= n and V.shape[1] >= n and V.shape[2] >= n
+    stream = torch.cuda.current_stream(G.device).cuda_stream
+    sci_syev_batched(G.device.index or 0, nb, n, G, G.stride(1), G.stride(0), w, w.stride(0), V, V.stride(1),
+                     V.stride(0), max_sweeps, None, stream)
+    return w[:, :n], V[:, :n, :n]
 
 
 def sci_bv_gemm_tn(ctx, M, k, a, A, lda, B, ldb, P, prec):

@@ -1,8 +1,8 @@
 """Host logic of the batched Davidson (batch_davidson.py) on the CPU.
 
-The batched sigma launch and the segmented products are replaced by plain per-instance
-torch arithmetic on dense symmetric matrices, so what is tested here is the solver
-around them:
+The batched sigma launch, the segmented products and the batched eigensolver are
+replaced by plain per-instance torch arithmetic on dense symmetric matrices, so what is
+tested here is the solver around them:
 - every instance reaches the lowest eigenvalue of its matrix (numpy eigvalsh), with
   instances of 1, 2 and 9 rows (spaces exhausted after a few columns) next to larger
   ones, with and without restarts;
@@ -105,9 +105,17 @@ def _matrices(sizes, seed=0):
     return out
 
 
+def _syev(G, n=None, w=None, V=None, max_sweeps=30):
+    """Eigenpairs of the symmetrised leading n x n blocks (torch's CPU eigh)."""
+    n = G.shape[1] if n is None else n
+    Gs = G[:, :n, :n]
+    return torch.linalg.eigh(0.5 * (Gs + Gs.transpose(1, 2)))
+
+
 @pytest.fixture
 def fake_seg(monkeypatch):
     monkeypatch.setattr(sci, "Segments", _Seg)
+    monkeypatch.setattr(sci, "syev_batched", _syev)
 
 
 @pytest.mark.parametrize("max_space,keep,nstart", [(24, 2, 4), (6, 2, 2), (5, 3, 4)])

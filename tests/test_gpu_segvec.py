@@ -129,3 +129,57 @@ def test_batch_active_mask(gpu):
     B.plan(sci.SCI_SCHED_TILE)                     # a new plan makes every instance active
     got = B.sigma(C).cpu().numpy()
     assert np.allclose(got, full, rtol=1e-13, atol=1e-14)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 24, 33, 64])
+def test_syev_batched_random(gpu, n):
+    """Eigenvalues against numpy eigvalsh, eigenvector residuals and orthonormality."""
+    torch = gpu
+    rng = np.random.default_rng(100 + n)
+    nb = 7
+    A = rng.normal(size=(nb, n, n))
+    A = A + A.transpose(0, 2, 1) + np.diag(np.linspace(-5, 5, n))[None]
+    w, V = sci.syev_batched(torch.from_numpy(A).cuda())
+    w, V = w.cpu().numpy(), V.cpu().numpy()
+    for b in range(nb):
+        ref = np.linalg.eigvalsh(A[b])
+        scale = np.abs(A[b]).sum()
+        assert np.abs(w[b] - ref).max() < 1e-13 * scale
+        assert np.all(np.diff(w[b]) >= 0)
+        assert np.abs(A[b] @ V[b] - V[b] * w[b][None, :]).max() < 1e-13 * scale
+        assert np.abs(V[b].T @ V[b] - np.eye(n)).max() < 1e-13 * max(1, n)
+
+
+def test_syev_batched_leading_block_degenerate_and_symmetrised(gpu):
+    """The leading n x n block of a larger strided buffer, as the batched solver uses it;
+    a degenerate pair and a decoupled large diagonal entry (a null column's penalty); an
+    input that is not symmetric is symmetrised."""
+    torch = gpu
+    rng = np.random.default_rng(7)
+    cap, n, nb = 24, 17, 5
+    G = rng.normal(size=(nb, cap, cap))
+    G = G + G.transpose(0, 2, 1)
+    G[1, :n, :n] = np.diag(np.r_[[1.0, 1.0], np.arange(2.0, n + 0.0)])   # degenerate pair
+    G[2, 10, :] = G[2, :, 10] = 0.0
+    G[2, 10, 10] = 1000.0                                                  # decoupled penalty
+    G[3, :n, :n] += np.triu(rng.normal(size=(n, n)), 1)                    # not symmetric
+    Gd = torch.from_numpy(G).cuda()
+    wbuf = torch.full((nb, cap), np.nan, dtype=torch.float64, device="cuda")
+    Vbuf = torch.full((nb, cap, cap), np.nan, dtype=torch.float64, device="cuda")
+    w, V = sci.syev_batched(Gd, n=n, w=wbuf, V=Vbuf)
+    w, V = w.cpu().numpy(), V.cpu().numpy()
+    for b in range(nb):
+        S = 0.5 * (G[b, :n, :n] + G[b, :n, :n].T)
+        assert np.abs(w[b] - np.linalg.eigvalsh(S)).max() < 1e-12 * np.abs(S).sum()
+        assert np.abs(S @ V[b] - V[b] * w[b][None, :]).max() < 1e-12 * np.abs(S).sum()
+    assert w[2, -1] == 1000.0 and abs(abs(V[2][10, -1]) - 1.0) < 1e-15
+    assert np.isnan(wbuf[:, n:].cpu().numpy()).all()          # nothing written past n
+
+
+def test_syev_batched_errors(gpu):
+    torch = gpu
+    G = torch.zeros((2, 65, 65), dtype=torch.float64, device="cuda")
+    with pytest.raises(sci.SciError):
+        sci.syev_batched(G)                                    # n above 64
+    with pytest.raises(sci.SciError):
+        sci.sci_syev_batched(0, 2, 4, G, 3, 65 * 65, G, 65, G, 65, 65 * 65)   # lda < n
