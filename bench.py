@@ -425,8 +425,8 @@ def batch_bench(reps=10):
 def batch_ground_states(ws, hams, tol=1e-8):
     """Lowest eigenpair of all 64 instances: the batched Davidson (one graph-replayed
     batched sigma per iteration; its time includes the batch's autotuned plan and graph
-    capture) against the single-instance FP64 Davidson run on each instance in turn
-    (wall seconds, synchronised)."""
+    capture) against the single-instance FP64 Davidson run on each instance in turn, both
+    with 32-column spaces and restarts keeping 4 vectors (wall seconds, synchronised)."""
     import torch
 
     from paper_2501_18185_gb300 import sci
@@ -445,7 +445,8 @@ def batch_ground_states(ws, hams, tol=1e-8):
     t = time.perf_counter()
     E1, conv1, calls1 = [], 0, 0
     for H in hams:
-        one = davidson(lambda Y, H=H: H.sigma(Y.contiguous()), H.diagonal(), nroots=1, tol=tol)
+        one = davidson(lambda Y, H=H: H.sigma(Y.contiguous()), H.diagonal(), nroots=1, tol=tol, max_space=32,
+                       keep=4)
         E1.append(float(one.energies[0]))
         conv1 += bool(one.converged)
         calls1 += one.sigma_calls
