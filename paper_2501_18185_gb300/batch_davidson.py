@@ -72,6 +72,8 @@ def davidson_batched(batch: "sci.Batch", tol: float = 1e-8, max_iter: int = 300,
     a restart keeps.  On the 64 FCI instances of 6-16 orbitals (tol 1e-8), (32, 4) took
     218 iterations and 1.99 s against 311 and 2.29 s for (24, 2), 200 and 2.09 s for
     (48, 6), 382 and 2.49 s for (16, 2): the slowest instance sets the count."""
+    if not 2 <= max_space <= 64:
+        raise ValueError("max_space must be in 2..64 (the batched eigensolver's limit)")
     dev = batch.device
     f64 = dict(dtype=torch.float64, device=dev)
     offsets = np.asarray(list(batch.offsets) + [batch.M], dtype=np.int64)
@@ -94,6 +96,7 @@ def davidson_batched(batch: "sci.Batch", tol: float = 1e-8, max_iter: int = 300,
     def eig(k):
         """Eigenpairs of every G_s[:k, :k], ascending (one batched Jacobi launch)."""
         return sci.syev_batched(G, n=k, w=ev_w, V=ev_V)
+
     ones = torch.ones(B, **f64)
     act = np.ones(B, dtype=bool)          # instances not converged yet
     act_dev = ones.clone()
