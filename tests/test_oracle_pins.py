@@ -243,3 +243,31 @@ def test_reference_row_connects_to_every_single_and_double(which):
     n1 = 400 if which == "30o" else 700
     assert int((deg == 1).sum()) == n1 and int((deg == 2).sum()) == expected - n1
     assert set(np.unique(ph)) <= {-1, 1}
+
+
+def _spin_swap(keys, n):
+    """Exchange the alpha bits [0, n) and the beta bits [n, 2n) of every key."""
+    keys = np.asarray(keys, dtype=np.uint64)
+    mask = np.uint64((1 << n) - 1)
+    return (keys >> np.uint64(n)) | ((keys & mask) << np.uint64(n))
+
+
+@pytest.mark.parametrize("n,ne,frac", [(6, 3, 0.45), (7, 2, 0.6)])
+def test_alpha_beta_swap_symmetry(n, ne, frac):
+    """With spin-free integrals and n_alpha = n_beta, exchanging the spin labels maps H to
+    itself: S|D> = (-1)^(n_alpha n_beta) |swap D> with the same sign for every D, so on a
+    space closed under the swap sigma(P c) = P sigma(c) for the permutation P of the
+    determinants.  A spin-dependent slip (an exchange term kept between opposite spins,
+    an alpha-beta phase that depends on the spin order) breaks it."""
+    w = _small(500 + n, "spin_orbitals", n, ne, ne, frac=frac)
+    keys = np.unique(np.concatenate([w.keys, _spin_swap(w.keys, n)]))
+    assert len(keys) > len(w.keys)                         # the closure added determinants
+    o = Oracle("spin_orbitals", n, w.ints.h, w.ints.eri(), keys)
+    perm = np.searchsorted(keys, _spin_swap(keys, n))
+    assert np.array_equal(keys[perm], _spin_swap(keys, n))
+    rng = np.random.default_rng(n)
+    c = rng.normal(size=(len(keys), 2))
+    pc = np.empty_like(c)
+    pc[perm] = c
+    s, ps = o.sigma(c), o.sigma(pc)
+    assert np.abs(ps[perm] - s).max() < 1e-12 * np.abs(s).max()
