@@ -162,3 +162,11 @@ def test_start_block():
     noise = T.copy()
     noise[np.abs(noise) > 0.5] -= 1.0
     assert 0 < np.abs(noise).max() < 0.01
+
+
+def test_space_limit():
+    """The batched eigensolver takes matrices up to 64 x 64: larger spaces are refused
+    before any work (no batch method is called)."""
+    for bad in (1, 65):
+        with pytest.raises(ValueError):
+            BD.davidson_batched(object(), max_space=bad)

@@ -183,3 +183,26 @@ def test_syev_batched_errors(gpu):
         sci.syev_batched(G)                                    # n above 64
     with pytest.raises(sci.SciError):
         sci.sci_syev_batched(0, 2, 4, G, 3, 65 * 65, G, 65, G, 65, 65 * 65)   # lda < n
+
+
+def test_syev_batched_sweep_limit_counts_unconverged(gpu):
+    """One sweep does not diagonalise a dense 24 x 24 matrix: every matrix is counted in
+    not_converged, and the result is still an orthogonal similarity (w from V^T A V)."""
+    torch = gpu
+    rng = np.random.default_rng(9)
+    A = rng.normal(size=(3, 24, 24))
+    A = A + A.transpose(0, 2, 1)
+    Ad = torch.from_numpy(A).cuda()
+    w = torch.empty((3, 24), dtype=torch.float64, device="cuda")
+    V = torch.empty((3, 24, 24), dtype=torch.float64, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    sci.sci_syev_batched(0, 3, 24, Ad, 24, 24 * 24, w, 24, V, 24, 24 * 24, 1, cnt,
+                         torch.cuda.current_stream().cuda_stream)
+    assert int(cnt.item()) == 3
+    Vn = V.cpu().numpy()
+    for b in range(3):
+        assert np.abs(Vn[b].T @ Vn[b] - np.eye(24)).max() < 1e-13
+    cnt.zero_()
+    sci.sci_syev_batched(0, 3, 24, Ad, 24, 24 * 24, w, 24, V, 24, 24 * 24, 30, cnt,
+                         torch.cuda.current_stream().cuda_stream)
+    assert int(cnt.item()) == 0
