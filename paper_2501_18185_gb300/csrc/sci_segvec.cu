@@ -358,7 +358,9 @@ extern "C" int sci_syev_batched(int device, int nb, int n, const double *A, int6
         return SCI_ERR_ARG;
     if (cudaSetDevice(device) != cudaSuccess) return SCI_ERR_CUDA;
     const size_t smem = sizeof(double) * 2 * (size_t)n * (n + 1);
-    if (smem > 48 * 1024 &&
+    // dynamic plus static shared memory above 48 KB needs the opt-in (the static part is
+    // under 1 KB, so opt in from 40 KB of dynamic memory on)
+    if (smem > 40 * 1024 &&
         cudaFuncSetAttribute(k_syev_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return SCI_ERR_CUDA;
     k_syev_jacobi<<<nb, kJacobiThreads, smem, (cudaStream_t)cuda_stream>>>(n, A, lda, strideA, w, stridew, V, ldv, strideV,

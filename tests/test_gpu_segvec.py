@@ -131,7 +131,7 @@ def test_batch_active_mask(gpu):
     assert np.allclose(got, full, rtol=1e-13, atol=1e-14)
 
 
-@pytest.mark.parametrize("n", [1, 2, 3, 5, 24, 33, 64])
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 24, 27, 32, 33, 64])
 def test_syev_batched_random(gpu, n):
     """Eigenvalues against numpy eigvalsh, eigenvector residuals and orthonormality."""
     torch = gpu
