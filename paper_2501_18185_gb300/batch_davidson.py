@@ -27,6 +27,7 @@ seeded random part, so that no instance starts inside one symmetry sector of its
 """
 from __future__ import annotations
 
+import contextlib
 from dataclasses import dataclass
 
 import numpy as np
@@ -80,97 +81,100 @@ def davidson_batched(batch: "sci.Batch", tol: float = 1e-8, max_iter: int = 300,
     B, M = len(offsets) - 1, int(batch.M)
     nstart = max(1, min(nstart, max_space - 1))
     keep = max(1, min(keep, max_space - 1))
-    seg = sci.Segments(offsets, kmax=max_space, device=dev.index)
-    diag = torch.cat([H.diagonal() for H in batch.hams]).to(**f64)
-    penalty = 10.0 * float(diag.abs().max()) + 10.0 if M else 10.0
-    V = torch.zeros((max_space + keep, M), **f64)   # rows >= max_space: restart scratch
-    Wm = torch.zeros_like(V)
-    T = torch.zeros(M, **f64)
-    S = torch.zeros(M, **f64)
-    batch.plan(schedule, T.normal_(), S)
-    batch.capture(T, S)
-    G = torch.zeros((B, max_space, max_space), **f64)
-    ev_w = torch.empty((B, max_space), **f64)
-    ev_V = torch.empty((B, max_space, max_space), **f64)
+    # the segment workspace is freed, and the batch's mask restored, on every exit
+    with contextlib.ExitStack() as cleanup:
+        seg = sci.Segments(offsets, kmax=max_space, device=dev.index)
+        cleanup.callback(seg.close)
+        diag = torch.cat([H.diagonal() for H in batch.hams]).to(**f64)
+        penalty = 10.0 * float(diag.abs().max()) + 10.0 if M else 10.0
+        V = torch.zeros((max_space + keep, M), **f64)   # rows >= max_space: restart scratch
+        Wm = torch.zeros_like(V)
+        T = torch.zeros(M, **f64)
+        S = torch.zeros(M, **f64)
+        batch.plan(schedule, T.normal_(), S)
+        # on every exit the batch goes back to computing all instances
+        cleanup.callback(batch.set_active, np.ones(B, dtype=bool))
+        batch.capture(T, S)
+        G = torch.zeros((B, max_space, max_space), **f64)
+        ev_w = torch.empty((B, max_space), **f64)
+        ev_V = torch.empty((B, max_space, max_space), **f64)
 
-    def eig(k):
-        """Eigenpairs of every G_s[:k, :k], ascending (one batched Jacobi launch)."""
-        return sci.syev_batched(G, n=k, w=ev_w, V=ev_V)
+        def eig(k):
+            """Eigenpairs of every G_s[:k, :k], ascending (one batched Jacobi launch)."""
+            return sci.syev_batched(G, n=k, w=ev_w, V=ev_V)
 
-    ones = torch.ones(B, **f64)
-    act = np.ones(B, dtype=bool)          # instances not converged yet
-    act_dev = ones.clone()
-    launches, per_launch = 0, []
-    k = 0
+        ones = torch.ones(B, **f64)
+        act = np.ones(B, dtype=bool)          # instances not converged yet
+        act_dev = ones.clone()
+        launches, per_launch = 0, []
+        k = 0
 
-    def append():
-        """T holds one direction per instance (zero for an instance that takes none):
-        orthonormalise it against V[:k] (two Gram-Schmidt passes), multiply it by H in one
-        replay, and append it to V, W and G."""
-        nonlocal k, launches
-        n0 = seg.tn(T, T)[:, 0].clone()
-        for _ in range(2):
-            if k:
-                seg.nn(T, ones, A1=V[:k], c1=seg.tn(V[:k], T), alpha1=-1.0)
-        n1 = seg.tn(T, T)[:, 0]
-        live = n1 > 1e-16 * n0                     # False also where T was zero
-        scale = torch.where(live, torch.rsqrt(torch.where(live, n1, ones)), torch.zeros_like(n1))
-        seg.nn(T, scale)
-        batch.replay()
-        launches += 1
-        per_launch.append(int(act.sum()) if drop_converged else B)
-        V[k].copy_(T)
-        Wm[k].copy_(S)
-        g = seg.tn(V[:k + 1], S)                    # [B, k+1]; zero for a null column
-        G[:, :k + 1, k] = g
-        G[:, k, :k + 1] = g
-        G[:, k, k] = torch.where(live, g[:, k], torch.full_like(n1, penalty))
-        k += 1
+        def append():
+            """T holds one direction per instance (zero for an instance that takes none):
+            orthonormalise it against V[:k] (two Gram-Schmidt passes), multiply it by H in one
+            replay, and append it to V, W and G."""
+            nonlocal k, launches
+            n0 = seg.tn(T, T)[:, 0].clone()
+            for _ in range(2):
+                if k:
+                    seg.nn(T, ones, A1=V[:k], c1=seg.tn(V[:k], T), alpha1=-1.0)
+            n1 = seg.tn(T, T)[:, 0]
+            live = n1 > 1e-16 * n0                     # False also where T was zero
+            scale = torch.where(live, torch.rsqrt(torch.where(live, n1, ones)), torch.zeros_like(n1))
+            seg.nn(T, scale)
+            batch.replay()
+            launches += 1
+            per_launch.append(int(act.sum()) if drop_converged else B)
+            V[k].copy_(T)
+            Wm[k].copy_(S)
+            g = seg.tn(V[:k + 1], S)                    # [B, k+1]; zero for a null column
+            G[:, :k + 1, k] = g
+            G[:, k, :k + 1] = g
+            G[:, k, k] = torch.where(live, g[:, k], torch.full_like(n1, penalty))
+            k += 1
 
-    st = start_block(offsets, diag.cpu().numpy(), nstart)
-    for j in range(nstart):
-        T.copy_(torch.from_numpy(st[j]))
-        append()
-    del st
-    rn = np.zeros(B)
-    theta_h = np.zeros(B)
-    it = 0
-    for it in range(1, max_iter + 1):
+        st = start_block(offsets, diag.cpu().numpy(), nstart)
+        for j in range(nstart):
+            T.copy_(torch.from_numpy(st[j]))
+            append()
+        del st
+        rn = np.zeros(B)
+        theta_h = np.zeros(B)
+        it = 0
+        for it in range(1, max_iter + 1):
+            evals, evecs = eig(k)
+            theta, y = evals[:, 0].contiguous(), evecs[:, :, 0].contiguous()
+            # residual H x - theta x = W y - theta V y of the running instances, into T
+            yc = y * act_dev[:, None]
+            seg.nn(T, None, A1=Wm[:k], c1=yc, A2=V[:k], c2=(theta[:, None] * yc).contiguous(), alpha2=-1.0)
+            host = torch.stack([torch.sqrt(seg.tn(T, T)[:, 0]), theta]).cpu().numpy()   # the one host read
+            rn = np.where(act, host[0], rn)
+            theta_h = np.where(act, host[1], theta_h)
+            done = act & (rn <= tol)
+            if done.any():
+                act &= ~done
+                act_dev = torch.from_numpy(act.astype(np.float64)).to(dev)
+                if drop_converged:
+                    batch.set_active(act)
+            if not act.any():
+                break
+            if k == max_space:   # thick restart to the lowest `keep` Ritz vectors
+                Y = evecs[:, :, :keep]
+                for j in range(keep):
+                    cj = Y[:, :, j].contiguous()
+                    seg.nn(V[max_space + j], None, A1=V[:k], c1=cj)
+                    seg.nn(Wm[max_space + j], None, A1=Wm[:k], c1=cj)
+                V[:keep].copy_(V[max_space:max_space + keep])
+                Wm[:keep].copy_(Wm[max_space:max_space + keep])
+                G.zero_()
+                G[:, :keep, :keep] = torch.diag_embed(evals[:, :keep])
+                k = keep
+            # preconditioned residual of the running instances: T / (theta - H_II)
+            seg.nn(T, act_dev, dg=diag, shift=theta)
+            append()
+        # Ritz vectors: unchanged for an instance since it converged (its later columns are
+        # null and decoupled, and restarts keep its lowest Ritz vectors)
         evals, evecs = eig(k)
-        theta, y = evals[:, 0].contiguous(), evecs[:, :, 0].contiguous()
-        # residual H x - theta x = W y - theta V y of the running instances, into T
-        yc = y * act_dev[:, None]
-        seg.nn(T, None, A1=Wm[:k], c1=yc, A2=V[:k], c2=(theta[:, None] * yc).contiguous(), alpha2=-1.0)
-        host = torch.stack([torch.sqrt(seg.tn(T, T)[:, 0]), theta]).cpu().numpy()   # the one host read
-        rn = np.where(act, host[0], rn)
-        theta_h = np.where(act, host[1], theta_h)
-        done = act & (rn <= tol)
-        if done.any():
-            act &= ~done
-            act_dev = torch.from_numpy(act.astype(np.float64)).to(dev)
-            if drop_converged:
-                batch.set_active(act)
-        if not act.any():
-            break
-        if k == max_space:   # thick restart to the lowest `keep` Ritz vectors
-            Y = evecs[:, :, :keep]
-            for j in range(keep):
-                cj = Y[:, :, j].contiguous()
-                seg.nn(V[max_space + j], None, A1=V[:k], c1=cj)
-                seg.nn(Wm[max_space + j], None, A1=Wm[:k], c1=cj)
-            V[:keep].copy_(V[max_space:max_space + keep])
-            Wm[:keep].copy_(Wm[max_space:max_space + keep])
-            G.zero_()
-            G[:, :keep, :keep] = torch.diag_embed(evals[:, :keep])
-            k = keep
-        # preconditioned residual of the running instances: T / (theta - H_II)
-        seg.nn(T, act_dev, dg=diag, shift=theta)
-        append()
-    # Ritz vectors: unchanged for an instance since it converged (its later columns are
-    # null and decoupled, and restarts keep its lowest Ritz vectors)
-    evals, evecs = eig(k)
-    X = torch.empty(M, **f64)
-    seg.nn(X, None, A1=V[:k], c1=evecs[:, :, 0].contiguous())
-    batch.set_active(np.ones(B, dtype=bool))
-    seg.close()
-    return BatchDavidsonResult(theta_h, rn, rn <= tol, it, launches, X, per_launch)
+        X = torch.empty(M, **f64)
+        seg.nn(X, None, A1=V[:k], c1=evecs[:, :, 0].contiguous())
+        return BatchDavidsonResult(theta_h, rn, rn <= tol, it, launches, X, per_launch)

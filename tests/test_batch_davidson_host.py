@@ -170,3 +170,23 @@ def test_space_limit():
     for bad in (1, 65):
         with pytest.raises(ValueError):
             BD.davidson_batched(object(), max_space=bad)
+
+
+def test_cleanup_on_failure(fake_seg, monkeypatch):
+    """A launch that fails mid-solve leaves the batch with every instance active again and
+    the segment workspace closed."""
+    closed = []
+    monkeypatch.setattr(_Seg, "close", lambda self: closed.append(True))
+    hams = _matrices([30, 12, 80], seed=4)
+    B = _Batch(hams)
+    orig = B.replay
+
+    def failing():
+        if len(B.computed) == 10:
+            raise RuntimeError("launch failed")
+        orig()
+
+    B.replay = failing
+    with pytest.raises(RuntimeError):
+        BD.davidson_batched(B, tol=1e-12, max_iter=50)
+    assert B.active.all() and closed == [True]
