@@ -154,6 +154,17 @@ def cpu_baseline(w, budget_s: float = 12.0, seed: int = 0):
             "sample": f"{n} random rows of {w.M} ({pairs} pairs, {dt:.1f} s, OpenMP {cores} threads)"}
 
 
+def kato_temple(energies, residuals, nroots, target=1e-8):
+    """From nroots + 1 Ritz values and the residual norms of the first nroots: the gap of
+    each root to the nearest other value, the Kato-Temple bounds r_k^2 / gap_k on
+    |E_k - exact|, and the residual sqrt(target * min gap) that bounds every root's error
+    by `target`."""
+    e = np.asarray(energies, dtype=np.float64)
+    r = np.asarray(residuals, dtype=np.float64)[:nroots]
+    gaps = np.array([min(abs(e[k] - e[j]) for j in range(len(e)) if j != k) for k in range(nroots)])
+    return gaps, r ** 2 / gaps, float(np.sqrt(target * gaps.min()))
+
+
 def davidson_bench(H, w, nroots=8, tol=1e-6):
     """Time to the lowest `nroots` energies: plain FP64 Davidson against the FP32-storage
     block Davidson with FP64 refinement (its residual estimates in paired FP32, and in
@@ -198,12 +209,11 @@ def davidson_bench(H, w, nroots=8, tol=1e-6):
     e_all = ref.energies.cpu().numpy()
     r_all = ref.residual_norms.cpu().numpy()
     e_ref = e_all[:nroots]
-    gaps = np.array([min(abs(e_all[k] - e_all[j]) for j in range(nroots + 1) if j != k) for k in range(nroots)])
     # Kato-Temple: |E_k - exact| <= r_k^2 / gap_k; the residual that guarantees 1e-8 Eh
     # for every root is sqrt(1e-8 * min gap)
-    tol_1e8 = float(np.sqrt(1e-8 * gaps.min()))
+    gaps, bounds, tol_1e8 = kato_temple(e_all, r_all, nroots)
     out = {"nroots": nroots, "residual_tol": tol, "ref_residual": 1e-8, "ref_converged": bool(ref.converged),
-           "E_ref": [float(x) for x in e_ref], "ref_error_bound_Eh": float((r_all[:nroots] ** 2 / gaps).max()),
+           "E_ref": [float(x) for x in e_ref], "ref_error_bound_Eh": float(bounds.max()),
            "min_gap_Eh": float(gaps.min()), "residual_tol_for_1e-8_Eh": tol_1e8, f"sigma_ms_nvec{nroots}": sig_ms}
     for name, run in (("fp64", lambda: davidson(hi, diag, nroots=nroots, tol=tol, max_iter=600)),
                       ("fp32_refined", lambda: davidson_mixed(lo, hi, diag, nroots=nroots, tol=tol, max_iter=600)),

@@ -57,3 +57,35 @@ def test_davidson_mixed_reaches_fp64_energies(nroots):
     X = res.vectors
     R = At @ X - X * res.energies
     assert float(torch.linalg.vector_norm(R, dim=0).max()) <= 1e-8
+
+
+def test_kato_temple_bound_holds_and_sets_the_tolerance():
+    """The bench's claim "residual sqrt(1e-8 * min gap) puts every energy within 1e-8 of
+    the exact one" rests on |E_k - lambda_k| <= r_k^2 / gap_k (Kato-Temple).  Check the
+    bound on loose Davidson runs against dense eigenvalues, and that running to the
+    tolerance it derives (from a tight run with one extra root) meets the target."""
+    import bench
+
+    A = _ci_like(800, 5)
+    lam = np.linalg.eigvalsh(A)
+    At = torch.from_numpy(A)
+    diag = torch.from_numpy(np.diag(A).copy())
+    nroots = 4
+    for tol in (1e-2, 1e-3, 1e-4):
+        r = davidson(lambda X: At @ X, diag, nroots=nroots + 1, tol=tol)
+        gaps, bounds, _ = bench.kato_temple(r.energies.numpy(), r.residual_norms.numpy(), nroots)
+        err = np.abs(r.energies.numpy()[:nroots] - lam[:nroots])
+        assert np.all(err <= bounds * (1 + 1e-6) + 1e-14), (tol, err, bounds)
+    ref = davidson(lambda X: At @ X, diag, nroots=nroots + 1, tol=1e-10)
+    _, _, tol_t = bench.kato_temple(ref.energies.numpy(), ref.residual_norms.numpy(), nroots, target=1e-8)
+    run = davidson(lambda X: At @ X, diag, nroots=nroots, tol=tol_t)
+    assert np.abs(run.energies.numpy() - lam[:nroots]).max() <= 1e-8
+
+
+def test_kato_temple_gaps():
+    import bench
+
+    gaps, bounds, t = bench.kato_temple([-3.0, -2.9, -1.0, 0.5], [1e-3, 2e-3, 1e-4], 3, target=1e-8)
+    assert np.allclose(gaps, [0.1, 0.1, 1.5])
+    assert np.allclose(bounds, [1e-6 / 0.1, 4e-6 / 0.1, 1e-8 / 1.5])
+    assert abs(t - np.sqrt(1e-8 * 0.1)) < 1e-15
