@@ -21,10 +21,11 @@
 // the whole buckets that start in its range of CH table rows (its window), and stages
 // every member of them in shared memory: the member's ket code, its ket offset into the
 // pair-integral table and its coefficients pre-multiplied by (-1)^pi.  Each thread owns
-// a row and walks the members of its bucket; lanes of a warp that share a bucket read
-// the same member (a shared-memory broadcast) and consecutive pair-table entries (the
-// table stores bra indices fastest).  A row's partial sum is added to sigma with one
-// FP64 atomic add per (bucket, member).
+// a row and walks the members of its bucket (in the FP64 kernels, the members other than
+// the row itself); lanes of a warp that share a bucket read the same member, or one of
+// two neighbours (a shared-memory broadcast), and nearby pair-table entries (the table
+// stores bra indices fastest).  A row's partial sum is added to sigma with one FP64
+// atomic add per (bucket, member).
 #include <algorithm>
 #include <cstdio>
 #include <vector>
