@@ -19,6 +19,8 @@
 //         tables (pair table, reference Fock matrix and g_so corrections), reduces over
 //         the warp and stores sigma_I: no atomics, no bucket tables read.
 // Items are ordered by decreasing measured cost so that the tail of the wave is short.
+// A per-instance flag array (sci_batch_set_active) lets a caller drop instances from
+// later launches and graph replays: their items are taken from the counter and skipped.
 #include <algorithm>
 #include <cstring>
 #include <map>

@@ -16,6 +16,9 @@
 // (coalesced, one read of every element), and the passes are HBM-bound.  The projections
 // write one partial row per item and a second kernel sums the items of each instance in
 // item order: the result does not depend on scheduling.
+//
+// The projected matrices of those solvers (k x k, k <= 64) are diagonalised together by
+// sci_syev_batched, one CTA per matrix (cyclic Jacobi, below).
 #include <algorithm>
 #include <string>
 #include <vector>
