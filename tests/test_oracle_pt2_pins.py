@@ -57,3 +57,24 @@ def test_enpt2_two_determinant_closed_form():
     ref = abs(H[1, 0]) ** 2 / (E0 - H[1, 1].real)
     got = PT.enpt2("spinors", 2, 1, 0, h, eri, P, np.ones((1, 1), dtype=np.complex128), [E0])
     assert abs(got[0] - ref) < 1e-15
+
+
+@pytest.mark.parametrize("n,ne,frac,nroots", [(6, 2, 0.4, 1), (7, 3, 0.3, 2)])
+def test_enpt2_spinors_matches_dense_literal_route(n, ne, frac, nroots):
+    """Spinor mode (complex Hermitian h and (pq|rs), no spin conservation): the same
+    definition against the dense H of Eq. Hamiltonian applied operator by operator, with
+    |H_IJ c_J|^2 summed over the explicit complement Q of P."""
+    w = W.random_small(241 + n, "spinors", n, ne, 0, naux=4, frac=frac)
+    h, eri = w.ints.h, w.ints.eri()
+    P = w.keys
+    ev, U = np.linalg.eigh(Oracle("spinors", n, h, eri, P).dense())
+    C, E0 = U[:, :nroots], ev[:nroots]
+    full = PT.full_space_keys("spinors", n, ne, 0)
+    H = F.hamiltonian(full, h, eri)
+    pos = np.searchsorted(full, P)
+    q = np.setdiff1d(np.arange(len(full)), pos)
+    num = H[np.ix_(q, pos)] @ C
+    ref = (np.abs(num) ** 2 / (E0[None, :] - np.real(np.diag(H))[q][:, None])).sum(0)
+    got = PT.enpt2("spinors", n, ne, 0, h, eri, P, C, E0)
+    assert np.allclose(got, ref, rtol=1e-12, atol=1e-14)
+    assert len(q) > 0 and np.all(got < 0)
