@@ -71,3 +71,30 @@ def test_hellmann_feynman_one_body():
         fd = (ep - em) / (2 * step)
         an = g1s[p, q] + (g1s[q, p] if p != q else 0.0)
         assert abs(fd - an) < 1e-7, (p, q, fd, an)
+
+
+def test_hellmann_feynman_two_body():
+    """For an eigenvector, moving a whole permutation orbit of (pq|rs) by eta changes the
+    eigenvalue by eta * 1/2 * sum over the orbit's distinct index tuples of the
+    spin-summed Gamma[p,q,r,s] = sum_{s1,s2} g2[p s1, q s1, r s2, s s2]: the factor 1/2 of
+    the gradient dE/d(pq|rs) = Gamma / 2 (central differences, step 1e-5)."""
+    n = 4
+    w = W.random_small(109, "spin_orbitals", n, 2, 1, naux=4)
+    h, eri = w.ints.h, w.ints.eri()
+    o = Oracle("spin_orbitals", n, h, eri, w.keys)
+    ev, U = np.linalg.eigh(o.dense())
+    _, g2 = o.rdm12(U[:, 0])
+    G = sum(g2[a * n:(a + 1) * n, a * n:(a + 1) * n, b * n:(b + 1) * n, b * n:(b + 1) * n]
+            for a in (0, 1) for b in (0, 1))
+    step = 1e-5
+    for p, q, r, s in [(0, 1, 2, 3), (1, 1, 0, 0), (2, 0, 2, 0), (3, 3, 3, 3), (0, 2, 1, 1)]:
+        orbit = {(p, q, r, s), (q, p, r, s), (p, q, s, r), (q, p, s, r),
+                 (r, s, p, q), (s, r, p, q), (r, s, q, p), (s, r, q, p)}
+        d = np.zeros_like(eri)
+        for t in orbit:
+            d[t] = 1.0
+        ep = np.linalg.eigvalsh(Oracle("spin_orbitals", n, h, eri + step * d, w.keys).dense())[0]
+        em = np.linalg.eigvalsh(Oracle("spin_orbitals", n, h, eri - step * d, w.keys).dense())[0]
+        fd = (ep - em) / (2 * step)
+        an = 0.5 * sum(G[t] for t in orbit)
+        assert abs(fd - an) < 1e-7, ((p, q, r, s), fd, an)
