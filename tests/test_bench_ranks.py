@@ -47,3 +47,26 @@ def test_single_process_needs_no_group():
 
     assert bench.max_over_ranks(3.5) == 3.5
     assert bench.job_throughput(10, 2, 1, 1000.0) == pytest.approx(20.0)
+
+
+def test_reference_arm_json_line():
+    """`bench.py --impl reference` prints one JSON line with the keys the benchmark
+    contract asks of the reference arm (on the 8-orbital FCI workload, a few seconds)."""
+    import json
+    import subprocess
+    import sys
+
+    ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                          "fci_8o", "--steps", "2", "--warmup", "1", "--ref-rows", "200"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.strip().splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 3
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
