@@ -8,8 +8,8 @@ benchmark may import this package.  It shares no code with the CUDA path: the C 
 
 Parity status: every function here is pinned by tests/test_oracle_pins.py (closed forms,
 textbook limits, invariances, an independent NumPy route and brute force).  The paper's
-own molecular energies need integrals that are not available, so real-molecule parity
-is unpinned (stated in the design notes).
+own molecular energies need its Br and Cr2 integrals, which are not available, so
+parity against real molecules is unpinned.
 """
 from __future__ import annotations
 
@@ -58,9 +58,19 @@ def _load():
             L.sciref_count_pairs.argtypes = [vp, i64, i64, vp]
             L.sciref_sigma_rows.argtypes = [vp, vp, i64, vp, i32, vp]
             L.sciref_sigma_brute_rows.argtypes = [vp, vp, i64, vp, i32, vp]
+            L.sciref_sigma_abs_rows.argtypes = [vp, vp, i64, vp, i32, vp]
             L.sciref_rdm12.argtypes = [vp, vp, vp, vp]
+            L.sciref_enpt2.argtypes = [vp, vp, i32, vp, vp, vp]
+            L.sciref_set_threads.argtypes = [i32]
+            L.sciref_set_threads.restype = i32
             _lib = L
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """OpenMP threads of the oracle's parallel loops (n <= 0: the OpenMP default).
+    Returns the number in force afterwards."""
+    return int(_load().sciref_set_threads(int(n)))
 
 
 def _ptr(a: np.ndarray):
@@ -178,6 +188,19 @@ class Oracle:
     def sigma(self, C) -> np.ndarray:
         return self.sigma_rows(np.arange(self.M), C)
 
+    def sigma_abs_rows(self, rows, C) -> np.ndarray:
+        """A[r, v] = |H_II| |C_Iv| + sum_J |H_IJ| |C_Jv| for I = rows[r] (real): the scale
+        of the rounding errors of row I of sigma (sciref_sigma_abs_rows)."""
+        C = np.ascontiguousarray(C, dtype=self.dtype)
+        if C.ndim == 1:
+            C = C[:, None]
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        A = np.zeros((len(rows), C.shape[1]), dtype=np.float64)
+        rc = self.L.sciref_sigma_abs_rows(self.ctx, _ptr(rows), len(rows), _ptr(C), C.shape[1], _ptr(A))
+        if rc != SCIREF_OK:
+            raise ValueError(rc)
+        return A
+
     def rdm12(self, c):
         """Unnormalised 1- and 2-RDM of vector c over spin-orbitals (spinors):
         g1[p,q] = <c|a+_p a_q|c>, g2[p,q,r,s] = <c|a+_p a+_r a_s a_q|c>."""
@@ -189,6 +212,21 @@ class Oracle:
         if rc != SCIREF_OK:
             raise ValueError(rc)
         return g1, g2
+
+    def enpt2(self, C, E0):
+        """Epstein-Nesbet E2_k (Eq. ENPT2E) of the columns of C on this list with
+        zeroth-order energies E0, summed over the single and double excitations of the
+        list that are outside it (sciref_enpt2).  Returns (E2 [nroots], number of distinct
+        external determinants)."""
+        C = np.ascontiguousarray(np.asarray(C).reshape(self.M, -1), dtype=self.dtype)
+        e0 = np.ascontiguousarray(np.asarray(E0, dtype=np.float64).reshape(-1))
+        assert e0.size == C.shape[1]
+        E2 = np.zeros(C.shape[1], dtype=np.float64)
+        nx = np.zeros(1, dtype=np.int64)
+        rc = self.L.sciref_enpt2(self.ctx, _ptr(C), C.shape[1], _ptr(e0), _ptr(E2), _ptr(nx))
+        if rc != SCIREF_OK:
+            raise ValueError(rc)
+        return E2, int(nx[0])
 
     def dense(self) -> np.ndarray:
         """Dense H on the list (small spaces only)."""

@@ -34,6 +34,8 @@
  * Rows are independent and are run in parallel with OpenMP.
  */
 #include <complex.h>
+#include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -125,6 +127,16 @@ int sciref_set_determinants(sciref_ctx *c, const uint64_t *keys, int64_t M)
     if (M > 0) memcpy(c->keys, keys, (size_t)M * sizeof(uint64_t));
     c->M = M;
     return SCIREF_OK;
+}
+
+/* OpenMP threads of the parallel loops below (n <= 0 restores the default); returns the
+ * number that later loops will use.  Timing only: the results do not depend on it. */
+static int sciref_default_threads = 0;
+int sciref_set_threads(int n)
+{
+    if (sciref_default_threads == 0) sciref_default_threads = omp_get_max_threads();
+    omp_set_num_threads(n > 0 ? n : sciref_default_threads);
+    return omp_get_max_threads();
 }
 
 /* ------------------------------------------------------------------ helpers */
@@ -397,6 +409,40 @@ int sciref_sigma_rows(const sciref_ctx *c, const int64_t *rows, int64_t nrows,
     return SCIREF_OK;
 }
 
+/* Row sums of magnitudes, the scale that rounding errors of sigma are measured against:
+ *   A[r][v] = |H_II| |C_Iv| + sum_J |H_IJ| |C_Jv|,   I = rows[r],
+ * over the same connections and elements as sciref_sigma_rows (|.| the modulus in complex
+ * mode; A is real, [nrows][nvec]).  sigma_I is a sum of these terms, so |sigma_I| <= A_I,
+ * and an error of relative size u in every term moves sigma_I by at most u A_I. */
+int sciref_sigma_abs_rows(const sciref_ctx *c, const int64_t *rows, int64_t nrows,
+                          const double *C, int nvec, double *A)
+{
+    if (!c || !rows || !C || !A || nvec <= 0) return SCIREF_ERR_ARG;
+    for (int64_t r = 0; r < nrows; r++)
+        if (rows[r] < 0 || rows[r] >= c->M) return SCIREF_ERR_ARG;
+    const int z = c->is_complex;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t r = 0; r < nrows; r++) {
+        int64_t row = rows[r];
+        const double hd = cabs(diag_element(c, c->keys[row]));
+        for (int v = 0; v < nvec; v++) {
+            size_t t = (size_t)row * nvec + v;
+            A[(size_t)r * nvec + v] = hd * (z ? cabs(CMPLX(C[2 * t], C[2 * t + 1])) : fabs(C[t]));
+        }
+        conn_t *list;
+        int64_t n = row_connections(c, row, &list);
+        for (int64_t k = 0; k < n; k++) {
+            const double hk = cabs(list[k].h);
+            for (int v = 0; v < nvec; v++) {
+                size_t t = (size_t)list[k].j * nvec + v;
+                A[(size_t)r * nvec + v] += hk * (z ? cabs(CMPLX(C[2 * t], C[2 * t + 1])) : fabs(C[t]));
+            }
+        }
+        free(list);
+    }
+    return SCIREF_OK;
+}
+
 /* The same sigma rows by the all-pairs route: every J of the list is tested, the
  * excitation degree taken by counting differing bits; no excitation is generated. */
 int sciref_sigma_brute_rows(const sciref_ctx *c, const int64_t *rows, int64_t nrows,
@@ -552,5 +598,147 @@ int sciref_rdm12(const sciref_ctx *c, const double *C, double *g1, double *g2)
         }
         free(cq);
     }
+    return SCIREF_OK;
+}
+
+/* ------------------------------------------------------------------ ENPT2 */
+/* Epstein-Nesbet second-order energies of the columns of C (paper Sec. 2.4, Eq. ENPT2E):
+ *   E2_k = sum_{I in Q} |sum_{J in P} H_IJ C_Jk|^2 / (E0_k - H_II)
+ * with P the determinant list of the context and Q every determinant outside P.  A
+ * determinant of Q adds a nonzero term only if some J in P is a single or double
+ * excitation away from it (otherwise every H_IJ vanishes), so Q is replaced by the set of
+ * single and double excitations of the members of P that are not members of P; nothing
+ * else is left out.
+ *
+ * Steps, each plain:
+ *   1. for every J in P, generate each single i -> a and double i<j -> a<b (spin-orbital
+ *      mode: alpha and beta counts conserved), in the loops of row_connections, and keep
+ *      the pair (I, J) when I is not in the list (binary search);
+ *   2. put the pairs into 256 bins by a multiplicative hash of I (equal I, equal bin) and
+ *      sort each bin by (I, J), so the J of one I are contiguous and ascending;
+ *   3. for each distinct I: numerator_k = sum over its J (ascending) of H_IJ C_Jk, with H_IJ
+ *      from offdiag_element (operator application, bra I, ket J), H_II from diag_element,
+ *      and add |numerator_k|^2 / (E0_k - H_II) to the bin's partial sum;
+ *   4. E2_k = the bins' partial sums added in bin order (the result does not depend on the
+ *      number of threads).
+ * C: [M][nroots] row-major (complex interleaved); E0, E2: nroots doubles.  *n_external
+ * (if not NULL) receives the number of distinct determinants summed (|Q| restricted as
+ * above).  Memory: 16 bytes per generated external pair. */
+typedef struct { uint64_t key; uint64_t j; } ext_pair;
+
+static int cmp_ext(const void *x, const void *y)
+{
+    const ext_pair *a = (const ext_pair *)x, *b = (const ext_pair *)y;
+    if (a->key != b->key) return (a->key > b->key) - (a->key < b->key);
+    return (a->j > b->j) - (a->j < b->j);
+}
+
+/* single and double excitations of row j that are not in the list, written to out (if
+ * not NULL) in generation order; returns their number */
+static int64_t external_excitations(const sciref_ctx *c, int64_t j, ext_pair *out)
+{
+    uint64_t d = c->keys[j];
+    int occ[64], vir[64], no = 0, nv = 0;
+    for (int p = 0; p < c->norb; p++) {
+        if (occupied(d, p)) occ[no++] = p; else vir[nv++] = p;
+    }
+    int64_t cnt = 0;
+    for (int x = 0; x < no; x++)
+        for (int y = 0; y < nv; y++) {
+            int i = occ[x], a = vir[y];
+            if (spin_of(c, i) != spin_of(c, a)) continue;
+            uint64_t e = (d & ~((uint64_t)1 << i)) | ((uint64_t)1 << a);
+            if (find_key(c, e) >= 0) continue;
+            if (out) { out[cnt].key = e; out[cnt].j = (uint64_t)j; }
+            cnt++;
+        }
+    for (int x1 = 0; x1 < no; x1++)
+        for (int x2 = x1 + 1; x2 < no; x2++)
+            for (int y1 = 0; y1 < nv; y1++)
+                for (int y2 = y1 + 1; y2 < nv; y2++) {
+                    int i = occ[x1], jj = occ[x2], a = vir[y1], b = vir[y2];
+                    if (spin_of(c, i) + spin_of(c, jj) != spin_of(c, a) + spin_of(c, b)) continue;
+                    uint64_t e = d & ~((uint64_t)1 << i) & ~((uint64_t)1 << jj);
+                    e |= ((uint64_t)1 << a) | ((uint64_t)1 << b);
+                    if (find_key(c, e) >= 0) continue;
+                    if (out) { out[cnt].key = e; out[cnt].j = (uint64_t)j; }
+                    cnt++;
+                }
+    return cnt;
+}
+
+#define ENPT2_BINS 256
+static unsigned enpt2_bin(uint64_t key) { return (unsigned)((key * 0x9E3779B97F4A7C15ull) >> 56); }
+
+int sciref_enpt2(const sciref_ctx *c, const double *C, int nroots, const double *E0, double *E2,
+                 int64_t *n_external)
+{
+    if (!c || !E0 || !E2 || nroots <= 0 || (c->M > 0 && !C)) return SCIREF_ERR_ARG;
+    const int z = c->is_complex;
+    const int64_t M = c->M;
+    /* 1. count, then write, the external pairs of each J */
+    int64_t *off = (int64_t *)calloc((size_t)M + 1, sizeof(int64_t));
+    if (!off) return SCIREF_ERR_ARG;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t j = 0; j < M; j++) off[j + 1] = external_excitations(c, j, NULL);
+    for (int64_t j = 0; j < M; j++) off[j + 1] += off[j];
+    const int64_t np = off[M];
+    ext_pair *pairs = (ext_pair *)malloc((size_t)(np > 0 ? np : 1) * sizeof(ext_pair));
+    ext_pair *binned = (ext_pair *)malloc((size_t)(np > 0 ? np : 1) * sizeof(ext_pair));
+    if (!pairs || !binned) { free(off); free(pairs); free(binned); return SCIREF_ERR_ARG; }
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t j = 0; j < M; j++) external_excitations(c, j, pairs + off[j]);
+    free(off);
+    /* 2. bins by hash of I (a counting sort), then each bin sorted by (I, J) */
+    int64_t bstart[ENPT2_BINS + 1], bfill[ENPT2_BINS];
+    memset(bstart, 0, sizeof(bstart));
+    for (int64_t t = 0; t < np; t++) bstart[enpt2_bin(pairs[t].key) + 1]++;
+    for (int b = 0; b < ENPT2_BINS; b++) bstart[b + 1] += bstart[b];
+    for (int b = 0; b < ENPT2_BINS; b++) bfill[b] = bstart[b];
+    for (int64_t t = 0; t < np; t++) binned[bfill[enpt2_bin(pairs[t].key)]++] = pairs[t];
+    free(pairs);
+    double *part = (double *)calloc((size_t)ENPT2_BINS * nroots, sizeof(double));
+    int64_t ndist[ENPT2_BINS];
+    memset(ndist, 0, sizeof(ndist));
+    /* 3. one term per distinct I */
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int b = 0; b < ENPT2_BINS; b++) {
+        ext_pair *v = binned + bstart[b];
+        const int64_t nb = bstart[b + 1] - bstart[b];
+        qsort(v, (size_t)nb, sizeof(ext_pair), cmp_ext);
+        zd *num = (zd *)malloc((size_t)nroots * sizeof(zd));
+        for (int64_t s = 0; s < nb;) {
+            int64_t e = s;
+            while (e < nb && v[e].key == v[s].key) e++;
+            const uint64_t ext = v[s].key;
+            for (int k = 0; k < nroots; k++) num[k] = 0;
+            for (int64_t t = s; t < e; t++) {
+                int deg, sg;
+                const zd hIJ = offdiag_element(c, ext, c->keys[v[t].j], &deg, &sg);
+                for (int k = 0; k < nroots; k++) {
+                    const size_t q = (size_t)v[t].j * nroots + k;
+                    num[k] += hIJ * (z ? CMPLX(C[2 * q], C[2 * q + 1]) : CMPLX(C[q], 0.0));
+                }
+            }
+            const double hII = creal(diag_element(c, ext));
+            for (int k = 0; k < nroots; k++) {
+                const double m2 = creal(num[k]) * creal(num[k]) + cimag(num[k]) * cimag(num[k]);
+                part[(size_t)b * nroots + k] += m2 / (E0[k] - hII);
+            }
+            ndist[b]++;
+            s = e;
+        }
+        free(num);
+    }
+    /* 4. bins in order */
+    int64_t total = 0;
+    for (int k = 0; k < nroots; k++) E2[k] = 0.0;
+    for (int b = 0; b < ENPT2_BINS; b++) {
+        for (int k = 0; k < nroots; k++) E2[k] += part[(size_t)b * nroots + k];
+        total += ndist[b];
+    }
+    if (n_external) *n_external = total;
+    free(part);
+    free(binned);
     return SCIREF_OK;
 }

@@ -290,6 +290,30 @@ def selected_30o(M: int = 2_000_000, nvec: int = 1, seed_offset: int = 2) -> Wor
     return w
 
 
+def selected_30o_cut(M: int = 1000, seed: int = 7) -> Workload:
+    """A small selected space of the 30-orbital recipe, for checks against slow routes:
+    the integrals of selected_30o() and, from its 60,000-determinant space, HF, all 400
+    singles, then M//3 doubles, M//4 triples and the rest quadruples drawn uniformly
+    without replacement (rng seeded by `seed`), sorted.  c as in selected_30o()
+    (|c| = exp(-level), random signs, normalised; drawn from the same seeded rng)."""
+    base = selected_30o(M=60000)
+    hf = base.hf_key()
+    lev = excitation_level(base.keys, hf)
+    rng = np.random.default_rng(seed)
+    keep = [np.flatnonzero(lev <= 1)]
+    n2, n3 = M // 3, M // 4
+    n4 = M - len(keep[0]) - n2 - n3
+    if n4 < 0:
+        raise ValueError("M too small for HF + singles")
+    for level, cnt in ((2, n2), (3, n3), (4, n4)):
+        keep.append(rng.choice(np.flatnonzero(lev == level), cnt, replace=False))
+    keys = base.keys[np.sort(np.concatenate(keep))]
+    w = Workload(f"sel_30o_10a10b_cut{M}_s{seed}", "spin_orbitals", 30, 10, 10, keys, base.ints, None,
+                 {"from": base.name})
+    w.c = coefficient_vector(rng, keys, hf, 1, False)
+    return w
+
+
 def selected_spinor_64(M: int = 1_000_000, nvec: int = 1, seed_offset: int = 4) -> Workload:
     """64 spinors, 14 electrons, selected space of M determinants (HF + singles + doubles
     + random triples); 80 Hermitian complex Cholesky vectors; complex c.

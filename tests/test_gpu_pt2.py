@@ -78,3 +78,44 @@ def test_enpt2_errors(gpu):
     H = sci.Hamiltonian.from_workload(w)
     with pytest.raises(sci.SciError):
         H.enpt2(torch.zeros((w.M, 9), dtype=torch.float64, device="cuda"), [0.0] * 9)
+
+
+@pytest.fixture(scope="module")
+def cut30():
+    """A 1,000-determinant space of the 30-orbital recipe (HF, all singles, sampled
+    doubles, triples and quadruples), its four lowest roots from the oracle's dense H, the
+    oracle's E2 of Eq. ENPT2E summed over the 3e7 external determinants (sciref_enpt2),
+    and the number of members of P connected to another member."""
+    w = W.selected_30o_cut(1000)
+    o = Oracle.from_workload(w)
+    ev, U = np.linalg.eigh(o.dense())
+    C, E0 = U[:, :4].copy(), ev[:4].copy()
+    E2, n_ext = o.enpt2(C, E0)
+    n_conn = sum(1 for r in range(w.M) if len(o.connections(r)[0]) > 0)
+    return w, C, E0, E2, n_ext, n_conn
+
+
+@pytest.mark.parametrize("nroots", [1, 4])
+def test_enpt2_30_orbital_space_matches_oracle(gpu, cut30, nroots):
+    """The GPU paths of the full-size spaces (n = 30: the GF(2) batch code over 30 beta
+    orbitals, the beta-beta lookups per (occupied pair, first virtual), the bounded-probe
+    hash table, H_II of external determinants by the Fock decomposition) against the
+    oracle's direct sum, at 1e-10 relative; the distinct determinants summed by the GPU
+    are exactly W = the oracle's external set plus the connected members of P; a table
+    of 2^22 entries (several batches of the beta-string code) gives the same sums.  (The
+    code batches by beta string, so every alpha excitation of the ~250 members sharing the
+    HF beta string falls into one batch: about 1.5e6 distinct determinants, which no
+    table below ~2^21 entries holds at any batch count.)"""
+    torch = gpu
+    w, C, E0, E2, n_ext, n_conn = cut30
+    H = sci.Hamiltonian.from_workload(w)
+    Ct = torch.from_numpy(C[:, :nroots].copy()).cuda()
+    e2w, e2p, e2q, st = H.enpt2(Ct, E0[:nroots])
+    assert np.allclose(e2q, E2[:nroots], rtol=1e-10, atol=0), (e2q, E2[:nroots])
+    assert st["distinct_W"] == n_ext + n_conn
+    d = H.diagonal().cpu().numpy()
+    ep2 = (C[:, :nroots] ** 2 * (E0[None, :nroots] - d[:, None])).sum(0)
+    assert np.allclose(e2p, ep2, rtol=1e-9)
+    e2w_b, e2p_b, e2q_b, st_b = H.enpt2(Ct, E0[:nroots], table_bytes=(1 << 22) * (8 + 8 * nroots))
+    assert st_b["batches"] >= 8 and st_b["batches"] > st["batches"] and st_b["distinct_W"] == st["distinct_W"]
+    assert np.allclose(e2q_b, E2[:nroots], rtol=1e-10, atol=0)

@@ -271,3 +271,22 @@ def test_alpha_beta_swap_symmetry(n, ne, frac):
     pc[perm] = c
     s, ps = o.sigma(c), o.sigma(pc)
     assert np.abs(ps[perm] - s).max() < 1e-12 * np.abs(s).max()
+
+
+@pytest.mark.parametrize("mode,n,na,nb,frac", [("spin_orbitals", 5, 2, 2, 0.7), ("spinors", 7, 3, 0, 0.5)])
+def test_sigma_abs_rows_matches_literal_route(mode, n, na, nb, frac):
+    """The magnitude row sums A = |H| |C| (the scale of sigma's rounding errors) against
+    the dense H of the literal operator route, and |sigma| <= A row by row."""
+    w = W.random_small(71 + n, mode, n, na, nb, naux=4, frac=frac, nvec=3)
+    Hf = F.hamiltonian(w.keys, *_so_ints(w))
+    o = Oracle.from_workload(w)
+    rows = np.arange(w.M)
+    A = o.sigma_abs_rows(rows, w.c)
+    ref = np.abs(Hf) @ np.abs(w.c)
+    assert np.allclose(A, ref, rtol=1e-13, atol=1e-15)
+    assert np.all(np.abs(o.sigma(w.c)) <= A * (1 + 1e-12) + 1e-15)
+    # equality when every term of a row has one sign: c >= 0 against |H|'s own signs
+    c = np.sign(Hf[0]).real.astype(np.float64) if mode == "spin_orbitals" else None
+    if c is not None:
+        c[c == 0] = 1.0
+        assert abs(abs(o.sigma_rows([0], c)[0, 0]) - o.sigma_abs_rows([0], c)[0, 0]) < 1e-12

@@ -78,3 +78,72 @@ def test_enpt2_spinors_matches_dense_literal_route(n, ne, frac, nroots):
     got = PT.enpt2("spinors", n, ne, 0, h, eri, P, C, E0)
     assert np.allclose(got, ref, rtol=1e-12, atol=1e-14)
     assert len(q) > 0 and np.all(got < 0)
+
+
+def _q_connected(full, P, H):
+    """Members of the complement Q with at least one nonzero-structure connection into P
+    (excitation degree 1 or 2), counted by popcount over the dense key lists."""
+    pos = np.searchsorted(full, P)
+    q = np.setdiff1d(np.arange(len(full)), pos)
+    x = full[q][:, None] ^ P[None, :]
+    deg = np.bitwise_count(x) // 2
+    return int(((deg >= 1) & (deg <= 2)).any(axis=1).sum())
+
+
+@pytest.mark.parametrize("mode,n,na,nb,frac,nroots", [
+    ("spin_orbitals", 5, 2, 2, 0.4, 1), ("spin_orbitals", 6, 3, 1, 0.5, 2), ("spin_orbitals", 6, 2, 3, 0.15, 3),
+    ("spinors", 6, 2, 0, 0.4, 1), ("spinors", 7, 3, 0, 0.3, 2)])
+def test_sciref_enpt2_matches_full_space_routes(mode, n, na, nb, frac, nroots):
+    """sciref_enpt2 (excitations of P minus P, sorted by key) against the sum of Eq.
+    ENPT2E over the whole complement Q of the full space (oracle/pt2.py) and against the
+    dense H of the literal operator route; its external count is the number of Q members
+    within a double excitation of P, counted by popcount."""
+    w = W.random_small(261 + n + 7 * nroots, mode, n, na, nb, naux=4, frac=frac)
+    h, eri = w.ints.h, w.ints.eri()
+    P = w.keys
+    o = Oracle(mode, n, h, eri, P)
+    ev, U = np.linalg.eigh(o.dense())
+    C, E0 = U[:, :nroots], ev[:nroots]
+    got, nx = o.enpt2(C, E0)
+    ref = PT.enpt2(mode, n, na, nb, h, eri, P, C, E0)
+    assert np.allclose(got, ref, rtol=1e-12, atol=1e-15)
+    full = PT.full_space_keys(mode, n, na, nb)
+    if mode == "spinors":
+        Hd = F.hamiltonian(full, h, eri)
+    else:
+        Hd = F.hamiltonian(full, *F.spin_orbital_integrals(h, eri))
+    pos = np.searchsorted(full, P)
+    q = np.setdiff1d(np.arange(len(full)), pos)
+    num = Hd[np.ix_(q, pos)] @ C
+    lit = (np.abs(num) ** 2 / (E0[None, :] - np.real(np.diag(Hd))[q][:, None])).sum(0)
+    assert np.allclose(got, lit, rtol=1e-12, atol=1e-15)
+    assert nx == _q_connected(full, P, Hd) and nx > 0
+
+
+def test_sciref_enpt2_general_vectors_and_energies():
+    """Any C and E0 (not eigenpairs), several columns with different E0: each column is the
+    one-column sum (no cross-talk between columns) and matches the literal route."""
+    w = W.random_small(277, "spin_orbitals", 6, 2, 2, naux=4, frac=0.3, nvec=3)
+    h, eri = w.ints.h, w.ints.eri()
+    o = Oracle.from_workload(w)
+    E0 = np.array([-9.0, -7.5, -12.25])
+    got, _ = o.enpt2(w.c, E0)
+    for k in range(3):
+        one, _ = o.enpt2(w.c[:, k:k + 1], E0[k:k + 1])
+        assert one[0] == got[k]
+    ref = PT.enpt2("spin_orbitals", 6, 2, 2, h, eri, w.keys, w.c, E0)
+    assert np.allclose(got, ref, rtol=1e-12, atol=1e-15)
+
+
+def test_sciref_enpt2_thread_count_does_not_change_the_sum():
+    from oracle import set_threads
+    w = W.random_small(281, "spinors", 7, 3, 0, naux=4, frac=0.2, nvec=2)
+    o = Oracle.from_workload(w)
+    E0 = np.array([-30.0, -29.0])
+    try:
+        set_threads(1)
+        a, na_ = o.enpt2(w.c, E0)
+    finally:
+        set_threads(0)
+    b, nb_ = o.enpt2(w.c, E0)
+    assert np.array_equal(a, b) and na_ == nb_
