@@ -87,7 +87,9 @@ enum {
 };
 
 /* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t (may be
- * NULL).  Allocates no device buffers yet.  Returns SCI_ERR_ARG for a bad device. */
+ * NULL).  Allocates a 4-byte status word; the first context on a device also commits the
+ * fixed scratch array of sci_connections_noalloc() there.  Returns SCI_ERR_ARG for a bad
+ * device, SCI_ERR_CUDA if the device or that scratch cannot be set up. */
 int sci_create(sci_ctx **out, int device, void *cuda_stream);
 
 /* Free every device buffer of the context and the context itself.  NULL is allowed. */
@@ -134,6 +136,30 @@ int sci_diagonal(sci_ctx *ctx, double *hdiag);
  * of S) can differ between calls. */
 int sci_sigma(sci_ctx *ctx, const void *C, void *S, int nvec, int prec);
 
+/* Row range of later sci_sigma() and sci_sigma_host() calls on this context: the data
+ * path of a row-partitioned sigma over several processes.  The paper keeps the static
+ * data on every process and distributes the results, which are merged at the end
+ * (Sec. 3.1, the MPI dynamic scheduler); here every process holds the integrals and the
+ * whole determinant list, computes the rows [row_begin, row_end) of S, and the rows of
+ * all processes are merged by one all-gather (the caller's collective).
+ * After this call sci_sigma() writes S rows [row_begin, row_end) only and leaves every
+ * other row of S as it was (sci_sigma_host() copies back only those rows), and
+ * sci_count_pairs() counts the pairs (I, J) with I in the range.  The call builds range
+ * tables: the (N-2)- and (N-1)-hole buckets that hold a member in the range, whole and in
+ * the order of the full tables, so a range costs device memory in proportion to the
+ * buckets it touches.  row_begin = 0 and row_end = M return to the whole list and free
+ * them; a new determinant list clears the range.  Density matrices, ENPT2, the
+ * connection exports and batches always use the whole list.
+ * Synchronous (waits for the context stream first).  Errors: SCI_ERR_STATE without
+ * determinants, SCI_ERR_ARG for a range outside [0, M], SCI_ERR_NOMEM. */
+int sci_set_row_range(sci_ctx *ctx, int64_t row_begin, int64_t row_end);
+
+/* Cost of each row of sigma, for balancing row ranges: cost[I] = the number of
+ * determinants J != I of the list within a single or double excitation of I (the
+ * off-diagonal elements of row I of H), exact.  cost: device, M int64, overwritten.
+ * Queued on the context stream; uses the whole list whatever the row range. */
+int sci_row_costs(sci_ctx *ctx, int64_t *cost);
+
 /* Connection list of rows [row_begin, row_end) for tests and debugging: every ordered
  * pair (I, J), I != J, with excitation degree 1 or 2 and both in the list, sorted by
  * (I, J), with the degree and the phase (+1/-1) of <D_I| relative to the excitation
@@ -153,13 +179,14 @@ int sci_connections(sci_ctx *ctx, int64_t row_begin, int64_t row_end, int64_t *c
  * Same results as sci_connections() (same arguments, same sorted output), but it calls
  * no cudaMalloc, cudaFree or other allocating routine, on the device or on the host.
  * Its device scratch (a slot counter and the unsorted pairs) is a fixed array inside the
- * library, SCI_NOALLOC_MAX_PAIRS pairs (about 4.5 MiB), which every GPU that loads the
- * library holds until the process exits.
+ * library, SCI_NOALLOC_MAX_PAIRS pairs (about 4.5 MiB).  The CUDA runtime loads the
+ * array's module lazily, so sci_create() loads it on the context's device and looks up
+ * the array's device address (cudaGetSymbolAddress) there: the device memory is
+ * committed when the first context on that device is created and held until the process
+ * exits, and no call of this function is the first touch.
  *   - rows and J must be non-NULL when cap > 0: the list is sorted in place in them.
  *   - More than SCI_NOALLOC_MAX_PAIRS connections in [row_begin, row_end) returns
  *     SCI_ERR_OVERFLOW, with *count set to the true number; split the range.
- *   - The first call on a device looks up the scratch array's device address
- *     (cudaGetSymbolAddress).  Make that first call before any stream capture.
  *   - Every call shares the scratch array, which keeps the last call's contents; the
  *     call clears the counter itself.  Calls that overlap on the GPU (from two host
  *     threads, or on two streams) race and corrupt each other's results.
@@ -170,7 +197,8 @@ int sci_connections_noalloc(sci_ctx *ctx, int64_t row_begin, int64_t row_end, in
                             int64_t cap);
 
 /* Number of connected ordered pairs (I, J), I != J, excitation degree <= 2 (every
- * off-diagonal element that sigma evaluates, counted whether or not its value is 0). */
+ * off-diagonal element that sigma evaluates, counted whether or not its value is 0);
+ * with a row range set (sci_set_row_range), the pairs with I in the range. */
 int sci_count_pairs(sci_ctx *ctx, int64_t *pairs);
 
 /* sigma for callers holding HOST buffers: C_host [M][nvec] is copied to the device, S
@@ -370,6 +398,15 @@ const char *sci_seg_last_error(const sci_seg *s);
 int sci_syev_batched(int device, int nb, int n, const double *A, int64_t lda, int64_t strideA,
                      double *w, int64_t stridew, double *V, int64_t ldv, int64_t strideV,
                      int max_sweeps, int *not_converged, void *cuda_stream);
+
+/* Measured FMA throughput of the GPU, for the benchmark's pipe fractions (the paper has
+ * no counterpart: its timings are CPU wall times).  prec SCI_PREC_F64 times FP64 FMAs,
+ * SCI_PREC_F32_STORE_F64_ACC FP32 FMAs: 8 CTAs of 256 threads per SM, 8 independent FMA
+ * chains of `iters` (>= 8) steps per thread, one untimed warm-up launch, then one launch
+ * timed with CUDA events on cuda_stream (NULL: the legacy default stream).
+ * *fma_per_s receives the FMAs per second (one FMA = 2 flops).  Synchronous; allocates
+ * and frees a small output buffer.  Errors: SCI_ERR_ARG, SCI_ERR_NOMEM, SCI_ERR_CUDA. */
+int sci_peak_fma(int device, int prec, int iters, void *cuda_stream, double *fma_per_s);
 
 /* Wait for the context stream and return the device status word (SCI_OK or the first
  * device-side error code). */

@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libsci.so")
-SOURCES = ["sci_setup.cu", "sci_sigma.cu", "sci_blockvec.cu", "sci_rdm.cu", "sci_batch.cu", "sci_pt2.cu", "sci_noalloc.cu", "sci_segvec.cu"]
+SOURCES = ["sci_setup.cu", "sci_sigma.cu", "sci_blockvec.cu", "sci_rdm.cu", "sci_batch.cu", "sci_pt2.cu", "sci_noalloc.cu", "sci_segvec.cu", "sci_probe.cu", "sci_rows.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

@@ -68,6 +68,11 @@ __host__ __device__ __forceinline__ uint64_t code_mask(uint32_t c)
     return (1ull << code_x(c)) | (1ull << code_y(c));
 }
 
+// Rows whose sigma a launch computes: [rb, re) (sci_set_row_range), every row otherwise.
+struct RowRange {
+    int64_t rb, re;
+};
+
 // Layout of the pair-integral table (see tab above).
 struct TabRule {
     int spinors, n;
@@ -143,6 +148,19 @@ struct sci_ctx {
     int maxb2 = 0, maxb1 = 0;
     int64_t pairs = 0, pairs2 = 0, pairs1 = 0;
 
+    // row range of sci_sigma() (sci_set_row_range): when `ranged`, sigma computes rows
+    // [row_b, row_e) only, walking range tables r2_* / r1_* that keep (whole, in table
+    // order) the buckets with a member in the range; range_pairs counts the connected
+    // pairs (I, J) with I in the range
+    int ranged = 0;
+    int64_t row_b = 0, row_e = 0;
+    int64_t r2 = 0, r1 = 0, range_pairs = 0;
+    uint32_t *r2_idx = nullptr, *r2_code = nullptr, *r2_pos = nullptr;
+    uint32_t *r1_idx = nullptr;
+    uint64_t *r1_S = nullptr;
+    uint32_t *r1_meta = nullptr;
+    size_t range_bytes = 0;
+
     // host-buffer sigma staging
     void *stage_c = nullptr, *stage_s = nullptr;
     size_t stage_bytes = 0;
@@ -169,7 +187,15 @@ struct sci_ctx {
 int sci_fail(sci_ctx *ctx, int code, const std::string &msg);
 int sci_cuda_check(sci_ctx *ctx, cudaError_t e, const char *what);
 
+// Commits the fixed scratch array of sci_connections_noalloc() on `device` (which must be
+// current) and caches its address; sci_noalloc.cu.
+cudaError_t sci_noalloc_prepare(int device);
+
+// row ranges (sci_rows.cu): frees the range tables and clears the range
+void sci_free_range(sci_ctx *ctx);
+
 // launchers (sci_sigma.cu)
+bool sci_sigma_window_fits(const sci_ctx *ctx);
 int sci_launch_sigma(sci_ctx *ctx, const void *C, void *S, int nvec, int prec);
 int sci_count_pairs_device(sci_ctx *ctx, int64_t *pairs2, int64_t *pairs1);
 int sci_connections_device(sci_ctx *ctx, int64_t row_begin, int64_t row_end, int64_t *count,

@@ -11,10 +11,18 @@
 //
 // Scratch: g_noalloc_scratch, a file-scope device array of kNoAllocBytes bytes: a 256-byte
 // header whose first 8 bytes are the slot counter, then kNoAllocMaxPairs packed (I, J)
-// pairs (uint64) and as many flag bytes.  Every GPU that loads the library holds it until
-// the process exits.  Every call shares it and it keeps the last call's contents; the
-// counter is cleared at the start of each call.  Calls that overlap on the GPU (two host
-// threads, or two streams) race on it.
+// pairs (uint64) and as many flag bytes.  Every call shares it and it keeps the last
+// call's contents; the counter is cleared at the start of each call.  Calls that overlap
+// on the GPU (two host threads, or two streams) race on it.
+//
+// When the scratch is committed.  The library is compiled per translation unit, so this
+// file's device code (the array and the two kernels) is a module of its own, and the CUDA
+// runtime loads modules lazily: the driver reserves the array's device memory only when
+// the module is first touched.  A caller that cannot allocate must not meet that moment in
+// the middle of its run, so sci_create() calls sci_noalloc_prepare(), which touches the
+// module on the context's device (the array's address and both kernels' attributes).
+// From the first sci_create() on a device until the process exits, that device holds the
+// array; a later sci_connections_noalloc() call only reads the cached address.
 #include <mutex>
 
 #include "sci_internal.cuh"
@@ -135,6 +143,27 @@ struct Out {
 
 }  // namespace
 
+// Once per device, with that device current: load this file's module (which commits the
+// scratch array) and cache the array's device address.  Called by sci_create(); later
+// calls on the same device return at once.
+cudaError_t sci_noalloc_prepare(int device)
+{
+    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (g_scratch_addr[device]) return cudaSuccess;
+    void *addr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_conn2_noalloc);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_conn1_noalloc);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e;
+    }
+    g_scratch_addr[device] = addr;
+    return cudaSuccess;
+}
+
 extern "C" int sci_connections_noalloc(sci_ctx *ctx, int64_t row_begin, int64_t row_end, int64_t *count,
                                        int64_t *rows, int64_t *J, int8_t *degree, int8_t *phase, int64_t cap)
 {
@@ -147,17 +176,13 @@ extern "C" int sci_connections_noalloc(sci_ctx *ctx, int64_t row_begin, int64_t 
     if (e != cudaSuccess) return sci_cuda_check(ctx, e, "cudaSetDevice");
     if (ctx->device < 0 || ctx->device >= kMaxDevices) return sci_fail(ctx, SCI_ERR_ARG, "device index too large");
 
-    // set-up, once per device, with the device current: the scratch array's address
+    // the scratch array's address, looked up by sci_create() on this device (a context
+    // made by sci_create() always has it; the lookup here only repeats a failed one)
+    e = sci_noalloc_prepare(ctx->device);
+    if (e != cudaSuccess) return sci_cuda_check(ctx, e, "no-allocation scratch set-up");
     void *base = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_scratch_addr[ctx->device]) {
-            e = cudaGetSymbolAddress(&g_scratch_addr[ctx->device], g_noalloc_scratch);
-            if (e != cudaSuccess) {
-                g_scratch_addr[ctx->device] = nullptr;
-                return sci_cuda_check(ctx, e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-            }
-        }
         base = g_scratch_addr[ctx->device];
     }
     Scratch s = carve(base);

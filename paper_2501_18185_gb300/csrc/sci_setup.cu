@@ -513,6 +513,7 @@ int build_buckets(sci_ctx *ctx, int holes, int per_det, Buckets &B)
 
 void free_dets(sci_ctx *ctx)
 {
+    sci_free_range(ctx);
     free_held(ctx, ctx->keys);
     free_held(ctx, ctx->hdiag);
     free_held(ctx, ctx->fref);
@@ -591,6 +592,9 @@ extern "C" int sci_create(sci_ctx **out, int device, void *cuda_stream)
     }
     if (device < 0 || device >= ndev) return SCI_ERR_ARG;
     if (cudaSetDevice(device) != cudaSuccess) return SCI_ERR_CUDA;
+    // commit the fixed scratch of sci_connections_noalloc() on this device now, so that
+    // its callers, who cannot allocate, never meet a lazy module load later
+    if (sci_noalloc_prepare(device) != cudaSuccess) return SCI_ERR_CUDA;
     sci_ctx *ctx = new sci_ctx();
     ctx->device = device;
     ctx->stream = (cudaStream_t)cuda_stream;
@@ -866,6 +870,14 @@ extern "C" int sci_set_determinants(sci_ctx *ctx, const uint64_t *keys, int64_t 
         free_dets(ctx);
         return sci_fail(ctx, SCI_ERR_OVERFLOW, "bucket larger than the table format allows");
     }
+    // a list that sci_sigma() could not run is rejected here, not at every launch: the
+    // largest bucket must fit the shared-memory window of a one-vector launch.  (With
+    // one-word keys a bucket holds at most C(norb - N + 2, 2) <= 2016 members, which
+    // always fits; the check guards the table format, not a case seen in practice.)
+    if (!sci_sigma_window_fits(ctx)) {
+        free_dets(ctx);
+        return sci_fail(ctx, SCI_ERR_OVERFLOW, "largest bucket does not fit the sigma kernel's shared-memory window");
+    }
     ctx->have_dets = 1;
     int64_t p2 = 0, p1 = 0;
     rc = sci_count_pairs_device(ctx, &p2, &p1);
@@ -928,7 +940,14 @@ extern "C" int sci_sigma_host(sci_ctx *ctx, const void *C_host, void *S_host, in
     SCI_CK(cudaMemcpyAsync(ctx->stage_c, C_host, cb, cudaMemcpyHostToDevice, ctx->stream));
     int rc = sci_sigma(ctx, ctx->stage_c, ctx->stage_s, nvec, prec);
     if (rc != SCI_OK) return rc;
-    SCI_CK(cudaMemcpyAsync(S_host, ctx->stage_s, obytes, cudaMemcpyDeviceToHost, ctx->stream));
+    if (ctx->ranged) {  // only the rows sigma computed; the rest of S_host is left alone
+        const size_t off = (size_t)ctx->row_b * nvec * sb, len = (size_t)(ctx->row_e - ctx->row_b) * nvec * sb;
+        if (len > 0)
+            SCI_CK(cudaMemcpyAsync((char *)S_host + off, (char *)ctx->stage_s + off, len, cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+    } else {
+        SCI_CK(cudaMemcpyAsync(S_host, ctx->stage_s, obytes, cudaMemcpyDeviceToHost, ctx->stream));
+    }
     SCI_CK(cudaStreamSynchronize(ctx->stream));
     return SCI_OK;
 }
@@ -969,7 +988,7 @@ extern "C" int sci_count_pairs(sci_ctx *ctx, int64_t *pairs)
 {
     if (!ctx || !pairs) return SCI_ERR_ARG;
     if (!ctx->have_dets) return sci_fail(ctx, SCI_ERR_STATE, "no determinants");
-    *pairs = ctx->pairs;
+    *pairs = ctx->ranged ? ctx->range_pairs : ctx->pairs;
     return SCI_OK;
 }
 

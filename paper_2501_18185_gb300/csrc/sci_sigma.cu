@@ -104,12 +104,51 @@ constexpr int kUnroll = 4;
 // 5.20 ms at 768 rows, 5.34 at 1024, 7.63 at 1280, where L1 is nearly gone).
 constexpr int kRowsPerCta = 768;
 
+// ------------------------------------------------------------------ row ranges
+// A RANGED launch walks the range tables of sci_set_row_range() and computes only the
+// members whose determinant lies in [rr.rb, rr.re).  Its CTA lists those rows of its
+// window, in window order, in shared memory (a ballot per warp and a prefix over the
+// warps), so that the lanes of a warp still own neighbouring rows of equal-size buckets;
+// a window with no such row returns before staging anything.  Returns the row count.
+__device__ __forceinline__ int owned_rows(const uint32_t *__restrict__ e_idx, int64_t r0, int W, sci::RowRange rr,
+                                          uint16_t *s_own)
+{
+    __shared__ int s_wcnt[kThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int total = 0;
+    for (int base = 0; base < W; base += blockDim.x) {
+        const int q = base + (int)threadIdx.x;
+        bool own = false;
+        if (q < W) {
+            const int64_t I = e_idx[r0 + q];
+            own = I >= rr.rb && I < rr.re;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, own);
+        if (lane == 0) s_wcnt[wid] = __popc(m);
+        __syncthreads();
+        int off = total, tot = total;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+            const int c = s_wcnt[w];
+            off += w < wid ? c : 0;
+            tot += c;
+        }
+        if (own) s_own[off + __popc(m & ((1u << lane) - 1u))] = (uint16_t)q;
+        total = tot;
+        __syncthreads();
+    }
+    return total;
+}
+
 // ------------------------------------------------------------------ sigma = diag * c
+// rows [row0, row0 + nrows) of S = H_II C
 template <typename TC, typename TA>
 __global__ void k_sigma_init(const double *__restrict__ hdiag, const TC *__restrict__ C, TA *__restrict__ S,
-                             int64_t M, int nvec)
+                             int64_t row0, int64_t nrows, int nvec)
 {
-    int64_t total = M * nvec;
+    const int64_t total = nrows * nvec;
+    C += row0 * nvec;
+    S += row0 * nvec;
+    hdiag += row0;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         double h = hdiag[t / nvec];
         TA s;
@@ -128,11 +167,11 @@ __global__ void k_sigma_init(const double *__restrict__ hdiag, const TC *__restr
 // TS: storage type of tab and staged coefficients; TA: accumulator (FP64 / complex128).
 // Shared memory per staged member: (ket code, ket table offset) as uint2, and its NV
 // coefficients times (-1)^pi.
-template <typename TS, typename TC, int NV>
+template <typename TS, typename TC, int NV, bool RANGED>
 __global__ void __launch_bounds__(kThreads)
 k_doubles(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_code, const uint32_t *__restrict__ e_pos,
           int64_t E, int CH, sci::TabRule tr, const TS *__restrict__ tab, const TC *__restrict__ C, int nvec, int v0,
-          typename AccOf<TS>::type *__restrict__ Sout)
+          typename AccOf<TS>::type *__restrict__ Sout, sci::RowRange rr)
 {
     using TA = typename AccOf<TS>::type;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -143,6 +182,12 @@ k_doubles(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_cod
     TS *s_c = reinterpret_cast<TS *>(smem);
     const size_t cbytes = ((size_t)W * NV * sizeof(TS) + 15) & ~(size_t)15;
     uint2 *s_kc = reinterpret_cast<uint2 *>(smem + cbytes);
+    uint16_t *s_own = reinterpret_cast<uint16_t *>(smem + cbytes + (size_t)W * sizeof(uint2));
+    int nrows = W;
+    if constexpr (RANGED) {
+        nrows = owned_rows(e_idx, r0, W, rr, s_own);
+        if (nrows == 0) return;
+    }
 
     for (int q = threadIdx.x; q < W; q += blockDim.x) {
         const int64_t g = r0 + q;
@@ -156,7 +201,8 @@ k_doubles(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_cod
     }
     __syncthreads();
 
-    for (int q0 = threadIdx.x; q0 < W; q0 += blockDim.x) {
+    for (int t_ = threadIdx.x; t_ < nrows; t_ += blockDim.x) {
+        const int q0 = RANGED ? (int)s_own[t_] : t_;
         const uint32_t code = e_code[r0 + q0], pos = e_pos[r0 + q0];
         uint32_t rowoff, colbase;
         sci::pair_offsets(tr, sci::code_x(code), sci::code_y(code), rowoff, colbase);
@@ -258,12 +304,12 @@ __device__ __forceinline__ void ds_fma1(Ds &a, float t, float c)
 
 // FP32 storage: the pair table rounded to FP32 (tab32) and FP32 coefficients, exact
 // products, compensated bucket sums, FP64 accumulation into sigma
-template <int NV>
+template <int NV, bool RANGED>
 __global__ void __launch_bounds__(kThreads)
 k_doubles_f32(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_code,
               const uint32_t *__restrict__ e_pos, int64_t E, int CH, sci::TabRule tr,
               const float *__restrict__ tab32, const float *__restrict__ C, int nvec, int v0,
-              double *__restrict__ Sout)
+              double *__restrict__ Sout, sci::RowRange rr)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     int64_t r0, r1;
@@ -273,6 +319,12 @@ k_doubles_f32(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e
     float *s_c = reinterpret_cast<float *>(smem);
     const size_t cbytes = ((size_t)W * NV * sizeof(float) + 15) & ~(size_t)15;
     uint2 *s_kc = reinterpret_cast<uint2 *>(smem + cbytes);
+    uint16_t *s_own = reinterpret_cast<uint16_t *>(smem + cbytes + (size_t)W * sizeof(uint2));
+    int nrows = W;
+    if constexpr (RANGED) {
+        nrows = owned_rows(e_idx, r0, W, rr, s_own);
+        if (nrows == 0) return;
+    }
 
     for (int q = threadIdx.x; q < W; q += blockDim.x) {
         const int64_t g = r0 + q;
@@ -286,7 +338,8 @@ k_doubles_f32(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e
     }
     __syncthreads();
 
-    for (int q0 = threadIdx.x; q0 < W; q0 += blockDim.x) {
+    for (int t_ = threadIdx.x; t_ < nrows; t_ += blockDim.x) {
+        const int q0 = RANGED ? (int)s_own[t_] : t_;
         const uint32_t code = e_code[r0 + q0], pos = e_pos[r0 + q0];
         uint32_t rowoff, colbase;
         sci::pair_offsets(tr, sci::code_x(code), sci::code_y(code), rowoff, colbase);
@@ -346,12 +399,12 @@ __global__ void k_split_cz(const zdbl *__restrict__ C, int64_t M, int nvec, int 
 }
 
 // real: tab2 is the (hi, lo) split of the pair table, C2 the split vector group
-template <int NV>
+template <int NV, bool RANGED>
 __global__ void __launch_bounds__(kThreads)
 k_doubles_ds(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_code,
              const uint32_t *__restrict__ e_pos, int64_t E, int CH, sci::TabRule tr,
              const float2 *__restrict__ tab2, const float2 *__restrict__ C2, int nvec, int v0,
-             double *__restrict__ Sout)
+             double *__restrict__ Sout, sci::RowRange rr)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     int64_t r0, r1;
@@ -361,6 +414,12 @@ k_doubles_ds(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_
     float2 *s_c = reinterpret_cast<float2 *>(smem);
     const size_t cbytes = ((size_t)W * NV * sizeof(float2) + 15) & ~(size_t)15;
     uint2 *s_kc = reinterpret_cast<uint2 *>(smem + cbytes);
+    uint16_t *s_own = reinterpret_cast<uint16_t *>(smem + cbytes + (size_t)W * sizeof(uint2));
+    int nrows = W;
+    if constexpr (RANGED) {
+        nrows = owned_rows(e_idx, r0, W, rr, s_own);
+        if (nrows == 0) return;
+    }
 
     for (int q = threadIdx.x; q < W; q += blockDim.x) {
         const int64_t g = r0 + q;
@@ -374,7 +433,8 @@ k_doubles_ds(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_
     }
     __syncthreads();
 
-    for (int q0 = threadIdx.x; q0 < W; q0 += blockDim.x) {
+    for (int t_ = threadIdx.x; t_ < nrows; t_ += blockDim.x) {
+        const int q0 = RANGED ? (int)s_own[t_] : t_;
         const uint32_t code = e_code[r0 + q0], pos = e_pos[r0 + q0];
         uint32_t rowoff, colbase;
         sci::pair_offsets(tr, sci::code_x(code), sci::code_y(code), rowoff, colbase);
@@ -425,11 +485,12 @@ k_doubles_ds(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_
 }
 
 // complex: tab4 holds (re_hi, re_lo, im_hi, im_lo); C4 the split vector group
-template <int NV>
+template <int NV, bool RANGED>
 __global__ void __launch_bounds__(kThreads)
 k_doubles_dsz(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_code,
               const uint32_t *__restrict__ e_pos, int64_t E, int CH, sci::TabRule tr,
-              const float4 *__restrict__ tab4, const float4 *__restrict__ C4, int nvec, int v0, zdbl *__restrict__ Sout)
+              const float4 *__restrict__ tab4, const float4 *__restrict__ C4, int nvec, int v0, zdbl *__restrict__ Sout,
+              sci::RowRange rr)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     int64_t r0, r1;
@@ -439,6 +500,12 @@ k_doubles_dsz(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e
     float4 *s_c = reinterpret_cast<float4 *>(smem);
     const size_t cbytes = ((size_t)W * NV * sizeof(float4) + 15) & ~(size_t)15;
     uint2 *s_kc = reinterpret_cast<uint2 *>(smem + cbytes);
+    uint16_t *s_own = reinterpret_cast<uint16_t *>(smem + cbytes + (size_t)W * sizeof(uint2));
+    int nrows = W;
+    if constexpr (RANGED) {
+        nrows = owned_rows(e_idx, r0, W, rr, s_own);
+        if (nrows == 0) return;
+    }
 
     for (int q = threadIdx.x; q < W; q += blockDim.x) {
         const int64_t g = r0 + q;
@@ -452,7 +519,8 @@ k_doubles_dsz(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e
     }
     __syncthreads();
 
-    for (int q0 = threadIdx.x; q0 < W; q0 += blockDim.x) {
+    for (int t_ = threadIdx.x; t_ < nrows; t_ += blockDim.x) {
+        const int q0 = RANGED ? (int)s_own[t_] : t_;
         const uint32_t code = e_code[r0 + q0], pos = e_pos[r0 + q0];
         uint32_t rowoff, colbase;
         sci::pair_offsets(tr, sci::code_x(code), sci::code_y(code), rowoff, colbase);
@@ -493,14 +561,18 @@ k_doubles_dsz(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e
 }
 
 // ------------------------------------------------------------------ singles
-template <typename TS, typename TC, int NV>
+template <typename TS, typename TC, int NV, bool RANGED>
 __global__ void __launch_bounds__(kThreads)
 k_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S, const uint32_t *__restrict__ e_meta,
           int64_t E, int norb, uint64_t ref, const TS *__restrict__ fref, const TS *__restrict__ g_so,
-          const TC *__restrict__ C, int nvec, int v0, typename AccOf<TS>::type *__restrict__ Sout)
+          const TC *__restrict__ C, int nvec, int v0, typename AccOf<TS>::type *__restrict__ Sout, sci::RowRange rr)
 {
     using TA = typename AccOf<TS>::type;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
+        if constexpr (RANGED) {
+            const int64_t I = e_idx[p];
+            if (I < rr.rb || I >= rr.re) continue;
+        }
         const uint32_t meta = e_meta[p];
         const int a = (int)(meta & 0x7F);
         const bool par = (meta >> 7) & 1;
@@ -543,13 +615,17 @@ k_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S, 
 // the doubles.  C2/C4 is the split vector group (row stride NV).
 using sci::ds_add;
 
-template <int NV>
+template <int NV, bool RANGED>
 __global__ void __launch_bounds__(kThreads)
 k_singles_ds(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S, const uint32_t *__restrict__ e_meta,
              int64_t E, int norb, uint64_t ref, const float2 *__restrict__ fref2, const float2 *__restrict__ g2,
-             const float2 *__restrict__ C2, int nvec, int v0, double *__restrict__ Sout)
+             const float2 *__restrict__ C2, int nvec, int v0, double *__restrict__ Sout, sci::RowRange rr)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
+        if constexpr (RANGED) {
+            const int64_t I = e_idx[p];
+            if (I < rr.rb || I >= rr.re) continue;
+        }
         const uint32_t meta = e_meta[p];
         const int a = (int)(meta & 0x7F);
         const bool par = (meta >> 7) & 1;
@@ -587,14 +663,18 @@ k_singles_ds(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_
     }
 }
 
-template <int NV>
+template <int NV, bool RANGED>
 __global__ void __launch_bounds__(kThreads)
 k_singles_dsz(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S,
               const uint32_t *__restrict__ e_meta, int64_t E, int norb, uint64_t ref,
               const float4 *__restrict__ fref4, const float4 *__restrict__ g4, const float4 *__restrict__ C4,
-              int nvec, int v0, zdbl *__restrict__ Sout)
+              int nvec, int v0, zdbl *__restrict__ Sout, sci::RowRange rr)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
+        if constexpr (RANGED) {
+            const int64_t I = e_idx[p];
+            if (I < rr.rb || I >= rr.re) continue;
+        }
         const uint32_t meta = e_meta[p];
         const int a = (int)(meta & 0x7F);
         const bool par = (meta >> 7) & 1;
@@ -674,33 +754,59 @@ int choose_rows(int maxb, size_t bytes_per_entry, size_t &smem)
 
 sci::TabRule tab_rule(const sci_ctx *ctx) { return sci::TabRule{ctx->spinors, ctx->n}; }
 
-template <typename TS, typename TC, int NV>
-int launch_doubles(sci_ctx *ctx, const TS *tab, const TC *C, typename AccOf<TS>::type *S, int nvec, int v0)
+// The tables a sigma launch walks and the rows it computes: the full tables (every row),
+// or the range tables of sci_set_row_range() (rows [row_b, row_e)).
+struct Tabs {
+    const uint32_t *e2_idx, *e2_code, *e2_pos;
+    int64_t e2;
+    const uint32_t *e1_idx;
+    const uint64_t *e1_S;
+    const uint32_t *e1_meta;
+    int64_t e1;
+    sci::RowRange rr;
+};
+
+Tabs tabs_of(const sci_ctx *ctx)
 {
-    if (ctx->e2 == 0) return SCI_OK;
-    size_t per = NV * sizeof(TS) + 8;
+    if (ctx->ranged)
+        return Tabs{ctx->r2_idx, ctx->r2_code, ctx->r2_pos, ctx->r2, ctx->r1_idx, ctx->r1_S, ctx->r1_meta, ctx->r1,
+                    sci::RowRange{ctx->row_b, ctx->row_e}};
+    return Tabs{ctx->e2_idx, ctx->e2_code, ctx->e2_pos, ctx->e2, ctx->e1_idx, ctx->e1_S, ctx->e1_meta, ctx->e1,
+                sci::RowRange{0, ctx->M}};
+}
+
+// staged bytes per window row: NV coefficients, the (code, offset) pair, and in a RANGED
+// launch the row's slot in the owned-row list
+template <bool RG> constexpr size_t row_extra() { return RG ? 8 + sizeof(uint16_t) : 8; }
+
+template <bool RG, typename TS, typename TC, int NV>
+int launch_doubles(sci_ctx *ctx, const Tabs &T, const TS *tab, const TC *C, typename AccOf<TS>::type *S, int nvec,
+                   int v0)
+{
+    if (T.e2 == 0) return SCI_OK;
+    size_t per = NV * sizeof(TS) + row_extra<RG>();
     size_t smem = 0;
     int ch = choose_rows(ctx->maxb2, per, smem);
     if (ch < 0) return sci_fail(ctx, SCI_ERR_OVERFLOW, "bucket too large for shared memory");
-    auto kern = k_doubles<TS, TC, NV>;
+    auto kern = k_doubles<TS, TC, NV, RG>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return sci_cuda_check(ctx, e, "cudaFuncSetAttribute");
-    int64_t blocks = (ctx->e2 + ch - 1) / ch;
-    kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(ctx->e2_idx, ctx->e2_code, ctx->e2_pos, ctx->e2, ch,
-                                                          tab_rule(ctx), tab, C, nvec, v0, S);
+    int64_t blocks = (T.e2 + ch - 1) / ch;
+    kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(T.e2_idx, T.e2_code, T.e2_pos, T.e2, ch, tab_rule(ctx), tab,
+                                                          C, nvec, v0, S, T.rr);
     return sci_cuda_check(ctx, cudaGetLastError(), "k_doubles launch");
 }
 
 // paired-FP32 doubles: real (float2 table, float2 staged c) or complex (float4 / float4)
-template <bool CPLX, int NV>
-int launch_doubles_ds(sci_ctx *ctx, const void *C, void *S, int nvec, int v0)
+template <bool RG, bool CPLX, int NV>
+int launch_doubles_ds(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int nvec, int v0)
 {
-    if (ctx->e2 == 0) return SCI_OK;
-    size_t per = NV * (CPLX ? sizeof(float4) : sizeof(float2)) + 8;
+    if (T.e2 == 0) return SCI_OK;
+    size_t per = NV * (CPLX ? sizeof(float4) : sizeof(float2)) + row_extra<RG>();
     size_t smem = 0;
     int ch = choose_rows(ctx->maxb2, per, smem);
     if (ch < 0) return sci_fail(ctx, SCI_ERR_OVERFLOW, "bucket too large for shared memory");
-    int64_t blocks = (ctx->e2 + ch - 1) / ch;
+    int64_t blocks = (T.e2 + ch - 1) / ch;
     cudaError_t e;
     // the vector group, split into paired floats in the context's c_ds buffer
     // (64 bytes per determinant: up to 8 real or 4 complex coefficients)
@@ -711,25 +817,25 @@ int launch_doubles_ds(sci_ctx *ctx, const void *C, void *S, int nvec, int v0)
         k_split_c<<<grid_for(ctx->M * NV), kThreads, 0, ctx->stream>>>((const double *)C, ctx->M, nvec, v0, NV,
                                                                        (float2 *)ctx->c_ds);
     if constexpr (CPLX) {
-        auto kern = k_doubles_dsz<NV>;
+        auto kern = k_doubles_dsz<NV, RG>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return sci_cuda_check(ctx, e, "cudaFuncSetAttribute");
-        kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(ctx->e2_idx, ctx->e2_code, ctx->e2_pos, ctx->e2, ch,
-                                                              tab_rule(ctx), (const float4 *)ctx->tab_ds,
-                                                              (const float4 *)ctx->c_ds, nvec, v0, (zdbl *)S);
+        kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(T.e2_idx, T.e2_code, T.e2_pos, T.e2, ch, tab_rule(ctx),
+                                                              (const float4 *)ctx->tab_ds, (const float4 *)ctx->c_ds,
+                                                              nvec, v0, (zdbl *)S, T.rr);
     } else {
-        auto kern = k_doubles_ds<NV>;
+        auto kern = k_doubles_ds<NV, RG>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return sci_cuda_check(ctx, e, "cudaFuncSetAttribute");
-        kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(ctx->e2_idx, ctx->e2_code, ctx->e2_pos, ctx->e2, ch,
-                                                              tab_rule(ctx), (const float2 *)ctx->tab_ds,
-                                                              (const float2 *)ctx->c_ds, nvec, v0, (double *)S);
+        kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(T.e2_idx, T.e2_code, T.e2_pos, T.e2, ch, tab_rule(ctx),
+                                                              (const float2 *)ctx->tab_ds, (const float2 *)ctx->c_ds,
+                                                              nvec, v0, (double *)S, T.rr);
     }
     return sci_cuda_check(ctx, cudaGetLastError(), "k_doubles_ds launch");
 }
 
-template <bool CPLX>
-int ds_groups(sci_ctx *ctx, const void *C, void *S, int nvec)
+template <bool RG, bool CPLX>
+int ds_groups(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int nvec)
 {
     int rc = SCI_OK;
     const size_t unit = CPLX ? sizeof(float4) : sizeof(float2);
@@ -738,12 +844,12 @@ int ds_groups(sci_ctx *ctx, const void *C, void *S, int nvec)
         int g = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
         if (CPLX && g > 4) g = 4;
         size_t smem_probe = 0;
-        while (g > 1 && choose_rows(ctx->maxb2, g * unit + 8, smem_probe) < 0) g >>= 1;
+        while (g > 1 && choose_rows(ctx->maxb2, g * unit + row_extra<RG>(), smem_probe) < 0) g >>= 1;
         switch (g) {
-        case 8: rc = launch_doubles_ds<CPLX, 8>(ctx, C, S, nvec, v0); break;
-        case 4: rc = launch_doubles_ds<CPLX, 4>(ctx, C, S, nvec, v0); break;
-        case 2: rc = launch_doubles_ds<CPLX, 2>(ctx, C, S, nvec, v0); break;
-        default: rc = launch_doubles_ds<CPLX, 1>(ctx, C, S, nvec, v0); break;
+        case 8: rc = launch_doubles_ds<RG, CPLX, 8>(ctx, T, C, S, nvec, v0); break;
+        case 4: rc = launch_doubles_ds<RG, CPLX, 4>(ctx, T, C, S, nvec, v0); break;
+        case 2: rc = launch_doubles_ds<RG, CPLX, 2>(ctx, T, C, S, nvec, v0); break;
+        default: rc = launch_doubles_ds<RG, CPLX, 1>(ctx, T, C, S, nvec, v0); break;
         }
         v0 += g;
     }
@@ -751,36 +857,37 @@ int ds_groups(sci_ctx *ctx, const void *C, void *S, int nvec)
 }
 
 // FP32-storage doubles (SCI_PREC_F32_STORE_F64_ACC)
-template <int NV>
-int launch_doubles_f32(sci_ctx *ctx, const float *C, double *S, int nvec, int v0)
+template <bool RG, int NV>
+int launch_doubles_f32(sci_ctx *ctx, const Tabs &T, const float *C, double *S, int nvec, int v0)
 {
-    if (ctx->e2 == 0) return SCI_OK;
-    size_t per = NV * sizeof(float) + 8;
+    if (T.e2 == 0) return SCI_OK;
+    size_t per = NV * sizeof(float) + row_extra<RG>();
     size_t smem = 0;
     int ch = choose_rows(ctx->maxb2, per, smem);
     if (ch < 0) return sci_fail(ctx, SCI_ERR_OVERFLOW, "bucket too large for shared memory");
-    int64_t blocks = (ctx->e2 + ch - 1) / ch;
-    auto kern = k_doubles_f32<NV>;
+    int64_t blocks = (T.e2 + ch - 1) / ch;
+    auto kern = k_doubles_f32<NV, RG>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return sci_cuda_check(ctx, e, "cudaFuncSetAttribute");
-    kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(ctx->e2_idx, ctx->e2_code, ctx->e2_pos, ctx->e2, ch,
-                                                          tab_rule(ctx), ctx->tab32, C, nvec, v0, S);
+    kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(T.e2_idx, T.e2_code, T.e2_pos, T.e2, ch, tab_rule(ctx),
+                                                          ctx->tab32, C, nvec, v0, S, T.rr);
     return sci_cuda_check(ctx, cudaGetLastError(), "k_doubles_f32 launch");
 }
 
-int f32_groups(sci_ctx *ctx, const float *C, double *S, int nvec)
+template <bool RG>
+int f32_groups(sci_ctx *ctx, const Tabs &T, const float *C, double *S, int nvec)
 {
     int rc = SCI_OK;
     for (int v0 = 0; v0 < nvec && rc == SCI_OK;) {
         int left = nvec - v0;
         int g = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
         size_t smem_probe = 0;
-        while (g > 1 && choose_rows(ctx->maxb2, g * sizeof(float) + 8, smem_probe) < 0) g >>= 1;
+        while (g > 1 && choose_rows(ctx->maxb2, g * sizeof(float) + row_extra<RG>(), smem_probe) < 0) g >>= 1;
         switch (g) {
-        case 8: rc = launch_doubles_f32<8>(ctx, C, S, nvec, v0); break;
-        case 4: rc = launch_doubles_f32<4>(ctx, C, S, nvec, v0); break;
-        case 2: rc = launch_doubles_f32<2>(ctx, C, S, nvec, v0); break;
-        default: rc = launch_doubles_f32<1>(ctx, C, S, nvec, v0); break;
+        case 8: rc = launch_doubles_f32<RG, 8>(ctx, T, C, S, nvec, v0); break;
+        case 4: rc = launch_doubles_f32<RG, 4>(ctx, T, C, S, nvec, v0); break;
+        case 2: rc = launch_doubles_f32<RG, 2>(ctx, T, C, S, nvec, v0); break;
+        default: rc = launch_doubles_f32<RG, 1>(ctx, T, C, S, nvec, v0); break;
         }
         v0 += g;
     }
@@ -788,31 +895,29 @@ int f32_groups(sci_ctx *ctx, const float *C, double *S, int nvec)
 }
 
 // paired-FP32 singles; real coefficients may come in as double or float
-template <bool CPLX, int NV, typename TC = double>
-int launch_singles_ds(sci_ctx *ctx, const void *C, void *S, int nvec, int v0)
+template <bool RG, bool CPLX, int NV, typename TC = double>
+int launch_singles_ds(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int nvec, int v0)
 {
-    if (ctx->e1 == 0) return SCI_OK;
-    const int g = grid_for(ctx->e1);
+    if (T.e1 == 0) return SCI_OK;
+    const int g = grid_for(T.e1);
     if constexpr (CPLX) {
         k_split_cz<<<grid_for(ctx->M * NV), kThreads, 0, ctx->stream>>>((const zdbl *)C, ctx->M, nvec, v0, NV,
                                                                         (float4 *)ctx->c_ds);
-        k_singles_dsz<NV><<<g, kThreads, 0, ctx->stream>>>(ctx->e1_idx, ctx->e1_S, ctx->e1_meta, ctx->e1, ctx->norb,
-                                                           ctx->ref, (const float4 *)ctx->fref_ds,
-                                                           (const float4 *)ctx->g_ds, (const float4 *)ctx->c_ds, nvec,
-                                                           v0, (zdbl *)S);
+        k_singles_dsz<NV, RG><<<g, kThreads, 0, ctx->stream>>>(T.e1_idx, T.e1_S, T.e1_meta, T.e1, ctx->norb, ctx->ref,
+                                                               (const float4 *)ctx->fref_ds, (const float4 *)ctx->g_ds,
+                                                               (const float4 *)ctx->c_ds, nvec, v0, (zdbl *)S, T.rr);
     } else {
         k_split_c<TC><<<grid_for(ctx->M * NV), kThreads, 0, ctx->stream>>>((const TC *)C, ctx->M, nvec, v0, NV,
                                                                            (float2 *)ctx->c_ds);
-        k_singles_ds<NV><<<g, kThreads, 0, ctx->stream>>>(ctx->e1_idx, ctx->e1_S, ctx->e1_meta, ctx->e1, ctx->norb,
-                                                          ctx->ref, (const float2 *)ctx->fref_ds,
-                                                          (const float2 *)ctx->g_ds, (const float2 *)ctx->c_ds, nvec,
-                                                          v0, (double *)S);
+        k_singles_ds<NV, RG><<<g, kThreads, 0, ctx->stream>>>(T.e1_idx, T.e1_S, T.e1_meta, T.e1, ctx->norb, ctx->ref,
+                                                              (const float2 *)ctx->fref_ds, (const float2 *)ctx->g_ds,
+                                                              (const float2 *)ctx->c_ds, nvec, v0, (double *)S, T.rr);
     }
     return sci_cuda_check(ctx, cudaGetLastError(), "k_singles_ds launch");
 }
 
-template <bool CPLX, typename TC = double>
-int ds_singles_groups(sci_ctx *ctx, const void *C, void *S, int nvec)
+template <bool RG, bool CPLX, typename TC = double>
+int ds_singles_groups(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int nvec)
 {
     int rc = SCI_OK;
     for (int v0 = 0; v0 < nvec && rc == SCI_OK;) {
@@ -820,28 +925,28 @@ int ds_singles_groups(sci_ctx *ctx, const void *C, void *S, int nvec)
         int g = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
         if (CPLX && g > 4) g = 4;
         switch (g) {
-        case 8: rc = launch_singles_ds<CPLX, 8, TC>(ctx, C, S, nvec, v0); break;
-        case 4: rc = launch_singles_ds<CPLX, 4, TC>(ctx, C, S, nvec, v0); break;
-        case 2: rc = launch_singles_ds<CPLX, 2, TC>(ctx, C, S, nvec, v0); break;
-        default: rc = launch_singles_ds<CPLX, 1, TC>(ctx, C, S, nvec, v0); break;
+        case 8: rc = launch_singles_ds<RG, CPLX, 8, TC>(ctx, T, C, S, nvec, v0); break;
+        case 4: rc = launch_singles_ds<RG, CPLX, 4, TC>(ctx, T, C, S, nvec, v0); break;
+        case 2: rc = launch_singles_ds<RG, CPLX, 2, TC>(ctx, T, C, S, nvec, v0); break;
+        default: rc = launch_singles_ds<RG, CPLX, 1, TC>(ctx, T, C, S, nvec, v0); break;
         }
         v0 += g;
     }
     return rc;
 }
 
-template <typename TS, typename TC, int NV>
-int launch_singles(sci_ctx *ctx, const TC *C, typename AccOf<TS>::type *S, int nvec, int v0)
+template <bool RG, typename TS, typename TC, int NV>
+int launch_singles(sci_ctx *ctx, const Tabs &T, const TC *C, typename AccOf<TS>::type *S, int nvec, int v0)
 {
-    if (ctx->e1 == 0) return SCI_OK;
-    k_singles<TS, TC, NV><<<grid_for(ctx->e1), kThreads, 0, ctx->stream>>>(
-        ctx->e1_idx, ctx->e1_S, ctx->e1_meta, ctx->e1, ctx->norb, ctx->ref, (const TS *)ctx->fref,
-        (const TS *)ctx->g_so, C, nvec, v0, S);
+    if (T.e1 == 0) return SCI_OK;
+    k_singles<TS, TC, NV, RG><<<grid_for(T.e1), kThreads, 0, ctx->stream>>>(
+        T.e1_idx, T.e1_S, T.e1_meta, T.e1, ctx->norb, ctx->ref, (const TS *)ctx->fref, (const TS *)ctx->g_so, C, nvec,
+        v0, S, T.rr);
     return sci_cuda_check(ctx, cudaGetLastError(), "k_singles launch");
 }
 
-template <typename TS, typename TC>
-int sigma_groups(sci_ctx *ctx, const TS *tab, const TC *C, typename AccOf<TS>::type *S, int nvec)
+template <bool RG, typename TS, typename TC>
+int sigma_groups(sci_ctx *ctx, const Tabs &T, const TS *tab, const TC *C, typename AccOf<TS>::type *S, int nvec)
 {
     int rc = SCI_OK;
     for (int v0 = 0; v0 < nvec && rc == SCI_OK;) {
@@ -849,29 +954,29 @@ int sigma_groups(sci_ctx *ctx, const TS *tab, const TC *C, typename AccOf<TS>::t
         int g = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
         if (sizeof(TS) == 16 && g > 4) g = 4;
         size_t smem_probe = 0;  // shrink the vector group until its window fits
-        while (g > 1 && choose_rows(ctx->maxb2, g * sizeof(TS) + 8, smem_probe) < 0) g >>= 1;
+        while (g > 1 && choose_rows(ctx->maxb2, g * sizeof(TS) + row_extra<RG>(), smem_probe) < 0) g >>= 1;
         switch (g) {
-        case 8: rc = launch_doubles<TS, TC, 8>(ctx, tab, C, S, nvec, v0); break;
-        case 4: rc = launch_doubles<TS, TC, 4>(ctx, tab, C, S, nvec, v0); break;
-        case 2: rc = launch_doubles<TS, TC, 2>(ctx, tab, C, S, nvec, v0); break;
-        default: rc = launch_doubles<TS, TC, 1>(ctx, tab, C, S, nvec, v0); break;
+        case 8: rc = launch_doubles<RG, TS, TC, 8>(ctx, T, tab, C, S, nvec, v0); break;
+        case 4: rc = launch_doubles<RG, TS, TC, 4>(ctx, T, tab, C, S, nvec, v0); break;
+        case 2: rc = launch_doubles<RG, TS, TC, 2>(ctx, T, tab, C, S, nvec, v0); break;
+        default: rc = launch_doubles<RG, TS, TC, 1>(ctx, T, tab, C, S, nvec, v0); break;
         }
         v0 += g;
     }
     return rc;
 }
 
-template <typename TS, typename TC>
-int singles_groups(sci_ctx *ctx, const TC *C, typename AccOf<TS>::type *S, int nvec)
+template <bool RG, typename TS, typename TC>
+int singles_groups(sci_ctx *ctx, const Tabs &T, const TC *C, typename AccOf<TS>::type *S, int nvec)
 {
     int rc = SCI_OK;
     for (int v0 = 0; v0 < nvec && rc == SCI_OK;) {
         int left = nvec - v0;
         int g = left >= 4 ? 4 : left >= 2 ? 2 : 1;
         switch (g) {
-        case 4: rc = launch_singles<TS, TC, 4>(ctx, C, S, nvec, v0); break;
-        case 2: rc = launch_singles<TS, TC, 2>(ctx, C, S, nvec, v0); break;
-        default: rc = launch_singles<TS, TC, 1>(ctx, C, S, nvec, v0); break;
+        case 4: rc = launch_singles<RG, TS, TC, 4>(ctx, T, C, S, nvec, v0); break;
+        case 2: rc = launch_singles<RG, TS, TC, 2>(ctx, T, C, S, nvec, v0); break;
+        default: rc = launch_singles<RG, TS, TC, 1>(ctx, T, C, S, nvec, v0); break;
         }
         v0 += g;
     }
@@ -969,51 +1074,77 @@ inline void mark(sci_ctx *ctx, int i)
         if (_rc != SCI_OK) return _rc;                               \
     } while (0)
 
-int sci_launch_sigma(sci_ctx *ctx, const void *C, void *S, int nvec, int prec)
+// whether the largest (N-2) bucket fits the staging window of a one-vector launch in the
+// context's scalar mode, row-range launches included (wider vector groups shrink until
+// they fit, down to one vector)
+bool sci_sigma_window_fits(const sci_ctx *ctx)
+{
+    size_t smem = 0;
+    const size_t per = (ctx->cplx ? sizeof(zdbl) : sizeof(double)) + row_extra<true>();
+    return ctx->e2 == 0 || choose_rows(ctx->maxb2, per, smem) >= 0;
+}
+
+namespace {
+
+// one sigma launch sequence over the tables T (RG: the rows of a row range only)
+template <bool RG>
+int launch_sigma(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int nvec, int prec)
 {
     cudaStream_t st = ctx->stream;
-    int64_t M = ctx->M;
+    const int64_t row0 = T.rr.rb, nrows = T.rr.re - T.rr.rb;
     int rc;
     mark(ctx, 0);
     if (ctx->cplx) {
         const zdbl *Cz = (const zdbl *)C;
         zdbl *Sz = (zdbl *)S;
-        k_sigma_init<zdbl, zdbl><<<grid_for(M * nvec), kThreads, 0, st>>>(ctx->hdiag, Cz, Sz, M, nvec);
+        if (nrows > 0)
+            k_sigma_init<zdbl, zdbl><<<grid_for(nrows * nvec), kThreads, 0, st>>>(ctx->hdiag, Cz, Sz, row0, nrows, nvec);
         SCI_CK(cudaGetLastError());
         mark(ctx, 1);
-        rc = prec == SCI_PREC_F64_DS ? ds_groups<true>(ctx, C, S, nvec)
-                                     : sigma_groups<zdbl, zdbl>(ctx, (const zdbl *)ctx->tab, Cz, Sz, nvec);
+        rc = prec == SCI_PREC_F64_DS ? ds_groups<RG, true>(ctx, T, C, S, nvec)
+                                     : sigma_groups<RG, zdbl, zdbl>(ctx, T, (const zdbl *)ctx->tab, Cz, Sz, nvec);
         mark(ctx, 2);
         if (rc == SCI_OK)
-            rc = prec == SCI_PREC_F64_DS ? ds_singles_groups<true>(ctx, C, S, nvec)
-                                         : singles_groups<zdbl, zdbl>(ctx, Cz, Sz, nvec);
+            rc = prec == SCI_PREC_F64_DS ? ds_singles_groups<RG, true>(ctx, T, C, S, nvec)
+                                         : singles_groups<RG, zdbl, zdbl>(ctx, T, Cz, Sz, nvec);
         mark(ctx, 3);
         return rc;
     }
     double *Sd = (double *)S;
     if (prec == SCI_PREC_F64 || prec == SCI_PREC_F64_DS) {
         const double *Cd = (const double *)C;
-        k_sigma_init<double, double><<<grid_for(M * nvec), kThreads, 0, st>>>(ctx->hdiag, Cd, Sd, M, nvec);
+        if (nrows > 0)
+            k_sigma_init<double, double><<<grid_for(nrows * nvec), kThreads, 0, st>>>(ctx->hdiag, Cd, Sd, row0, nrows,
+                                                                                       nvec);
         SCI_CK(cudaGetLastError());
         mark(ctx, 1);
-        rc = prec == SCI_PREC_F64_DS ? ds_groups<false>(ctx, C, S, nvec)
-                                     : sigma_groups<double, double>(ctx, (const double *)ctx->tab, Cd, Sd, nvec);
+        rc = prec == SCI_PREC_F64_DS ? ds_groups<RG, false>(ctx, T, C, S, nvec)
+                                     : sigma_groups<RG, double, double>(ctx, T, (const double *)ctx->tab, Cd, Sd, nvec);
         mark(ctx, 2);
         if (rc == SCI_OK)
-            rc = prec == SCI_PREC_F64_DS ? ds_singles_groups<false>(ctx, C, S, nvec)
-                                         : singles_groups<double, double>(ctx, Cd, Sd, nvec);
+            rc = prec == SCI_PREC_F64_DS ? ds_singles_groups<RG, false>(ctx, T, C, S, nvec)
+                                         : singles_groups<RG, double, double>(ctx, T, Cd, Sd, nvec);
         mark(ctx, 3);
         return rc;
     }
     const float *Cf = (const float *)C;
-    k_sigma_init<float, double><<<grid_for(M * nvec), kThreads, 0, st>>>(ctx->hdiag, Cf, Sd, M, nvec);
+    if (nrows > 0)
+        k_sigma_init<float, double><<<grid_for(nrows * nvec), kThreads, 0, st>>>(ctx->hdiag, Cf, Sd, row0, nrows, nvec);
     SCI_CK(cudaGetLastError());
     mark(ctx, 1);
-    rc = f32_groups(ctx, Cf, Sd, nvec);
+    rc = f32_groups<RG>(ctx, T, Cf, Sd, nvec);
     mark(ctx, 2);
-    if (rc == SCI_OK) rc = ds_singles_groups<false, float>(ctx, C, S, nvec);
+    if (rc == SCI_OK) rc = ds_singles_groups<RG, false, float>(ctx, T, C, S, nvec);
     mark(ctx, 3);
     return rc;
+}
+
+}  // namespace
+
+int sci_launch_sigma(sci_ctx *ctx, const void *C, void *S, int nvec, int prec)
+{
+    const Tabs T = tabs_of(ctx);
+    return ctx->ranged ? launch_sigma<true>(ctx, T, C, S, nvec, prec) : launch_sigma<false>(ctx, T, C, S, nvec, prec);
 }
 
 int sci_count_pairs_device(sci_ctx *ctx, int64_t *pairs2, int64_t *pairs1)

@@ -40,6 +40,8 @@ SIGNATURES = {
     "sci_set_determinants": (_i32, [_vp, _vp, _i64, _i32, _i32, _i32]),
     "sci_diagonal": (_i32, [_vp, _vp]),
     "sci_sigma": (_i32, [_vp, _vp, _vp, _i32, _i32]),
+    "sci_set_row_range": (_i32, [_vp, _i64, _i64]),
+    "sci_row_costs": (_i32, [_vp, _vp]),
     "sci_connections": (_i32, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _i64]),
     "sci_connections_noalloc": (_i32, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _i64]),
     "sci_count_pairs": (_i32, [_vp, _vp]),
@@ -70,6 +72,7 @@ SIGNATURES = {
     "sci_bv_gemm_tn": (_i32, [_vp, _i64, _i32, _i32, _vp, _i64, _vp, _i64, _vp, _i32]),
     "sci_bv_gemm_nn": (_i32, [_vp, _i64, _i32, _vp, _i64, _i32, _vp, _vp, _i64, _i32, _vp, ctypes.c_double, _vp,
                               _i64, _vp, _vp, _vp, _i32]),
+    "sci_peak_fma": (_i32, [_i32, _i32, _i32, _vp, _vp]),
     "sci_sync_status": (_i32, [_vp]),
     "sci_last_error": (ctypes.c_char_p, [_vp]),
 }
@@ -149,6 +152,14 @@ def sci_diagonal(ctx, hdiag):
 
 def sci_sigma(ctx, C, S, nvec, prec):
     return _check(ctx, load().sci_sigma(ctx, _p(C), _p(S), nvec, prec))
+
+
+def sci_set_row_range(ctx, row_begin, row_end):
+    return _check(ctx, load().sci_set_row_range(ctx, int(row_begin), int(row_end)))
+
+
+def sci_row_costs(ctx, cost):
+    return _check(ctx, load().sci_row_costs(ctx, _p(cost)))
 
 
 def sci_connections(ctx, row_begin, row_end, cap):
@@ -354,6 +365,16 @@ def sci_bv_gemm_nn(ctx, M, a, A1, lda1, k1, S1, A2, lda2, k2, S2, beta, C, ldc, 
                                              _p(C), ldc, _p(dg), _p(shift), _p(colsq), prec))
 
 
+def sci_peak_fma(device: int, prec: int, iters: int, stream: int | None = None) -> float:
+    """Measured FMAs per second of the FP64 (SCI_PREC_F64) or FP32
+    (SCI_PREC_F32_STORE_F64_ACC) pipes -- see sci_peak_fma in include/sci.h."""
+    out = np.zeros(1, dtype=np.float64)
+    rc = load().sci_peak_fma(device, prec, iters, ctypes.c_void_p(stream or 0), _p(out))
+    if rc != SCI_OK:
+        raise SciError(rc, "sci_peak_fma failed")
+    return float(out[0])
+
+
 def sci_sync_status(ctx):
     return _check(ctx, load().sci_sync_status(ctx))
 
@@ -425,6 +446,12 @@ class Hamiltonian:
             M = len(k)
         sci_set_determinants(self.ctx, k, M, n_alpha, n_beta if self.mode != "spinors" else -1, on_dev)
         self.M = M
+        self.n_alpha, self.n_beta = int(n_alpha), int(n_beta)
+        self.row_range = (0, M)
+
+    @property
+    def n_electrons(self) -> int:
+        return self.n_alpha + (self.n_beta if self.mode != "spinors" else 0)
 
     @classmethod
     def from_workload(cls, w, device: int = 0, use_chol: bool = True):
@@ -435,6 +462,18 @@ class Hamiltonian:
             H.set_integrals(w.mode, w.ints.h, eri=w.ints.eri())
         H.set_determinants(w.keys, w.n_alpha, w.n_beta)
         return H
+
+    def set_row_range(self, row_begin: int, row_end: int):
+        """Later sigma calls compute rows [row_begin, row_end) of S only (the other rows
+        of S are left as they were); (0, M) returns to the whole list."""
+        sci_set_row_range(self.ctx, row_begin, row_end)
+        self.row_range = (int(row_begin), int(row_end))
+
+    def row_costs(self):
+        """Per-row count of connected determinants (torch int64 on the device)."""
+        c = self.torch.empty(self.M, dtype=self.torch.int64, device=self.device)
+        sci_row_costs(self.ctx, c)
+        return c
 
     def diagonal(self):
         d = self.torch.empty(self.M, dtype=self.torch.float64, device=self.device)

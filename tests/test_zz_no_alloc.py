@@ -47,6 +47,23 @@ def test_noalloc_export_matches_allocating_export(gpu):
                 assert np.array_equal(a, b)
 
 
+def test_noalloc_export_takes_no_device_memory(gpu):
+    """The point of the entry point: a call changes the device's free memory by nothing,
+    the first call on a fresh context included (its scratch was committed when the first
+    context was created)."""
+    torch = gpu
+    w = W.selected_30o(M=60000)
+    H = sci.Hamiltonian.from_workload(w)
+    n_ref, _ = sci.sci_connections(H.ctx, 100, 400, 0)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        free0 = torch.cuda.mem_get_info()[0]
+        rc, n, _ = _call(H.ctx, 100, 400, n_ref)
+        free1 = torch.cuda.mem_get_info()[0]
+        assert rc == sci.SCI_OK and n == n_ref
+        assert free1 == free0, (free0, free1)
+
+
 def test_noalloc_export_rejects_ranges_beyond_its_scratch(gpu):
     w = W.selected_30o(M=60000)
     H = sci.Hamiltonian.from_workload(w)
