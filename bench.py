@@ -9,6 +9,11 @@ and doubles + seeded random triples/quadruples), Cholesky rank 120, FP64, one ve
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload sel_30o|sel_64s|fci_8o]
                     [--nvec V] [--impl gb300|reference]
 
+Beside the headline step, the default run times the side sections: the 8-root Davidson
+solvers (FP64 against FP32-refined), the density matrices and autograd energy, the 64
+batched instances, ENPT2, and one sigma on the 1,000,000-determinant 64-spinor complex
+space (`spinor`), each with its own figures.
+
 Under torchrun (N > 1) every rank runs an independent replica of the workload (weak
 scaling, no collective on the data path); the value is all ranks' pairs / max time.
 `--impl reference` times the CPU oracle (the only reference implementation: the paper
@@ -89,6 +94,42 @@ def hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+_PIPE_PEAKS = {}
+
+
+def pipe_peaks(device: int) -> dict:
+    """Measured FMA rates of the FP64 and FP32 pipes of this GPU (sci_peak_fma: 8 CTAs of
+    256 threads per SM, 8 independent FMA chains per thread, CUDA events), once per
+    process; with the SM clock seen right after the timed launch (nvidia-smi)."""
+    if device in _PIPE_PEAKS:
+        return _PIPE_PEAKS[device]
+    from paper_2501_18185_gb300 import sci
+
+    f64 = max(sci.sci_peak_fma(device, sci.SCI_PREC_F64, 2500) for _ in range(3))
+    f32 = max(sci.sci_peak_fma(device, sci.SCI_PREC_F32_STORE_F64_ACC, 160000) for _ in range(3))
+    mhz = None
+    try:
+        out = subprocess.run(["nvidia-smi", f"--id={device}", "--query-gpu=clocks.sm", "--format=csv,noheader,nounits"],
+                             capture_output=True, text=True, timeout=20).stdout.strip()
+        mhz = float(out.splitlines()[0])
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+        pass
+    _PIPE_PEAKS[device] = {"fp64_fma_per_s": f64, "fp32_fma_per_s": f32, "sm_mhz_after": mhz,
+                           "how": "sci_peak_fma: best of 3 timed launches (8 CTAs x 256 threads per SM, "
+                                  "8 independent FMA chains per thread)"}
+    return _PIPE_PEAKS[device]
+
+
+def profile_figures(key: str) -> dict:
+    """Per-launch DRAM and L2 bytes of the doubles kernel for a workload, from the ncu
+    summaries in profiles/traffic.json ({} if absent)."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    except (OSError, ValueError):
+        return {}
+    return {"dram": d.get(key), "l2": d.get("l2:" + key), "l2_note": d.get("_l2_note")}
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle samples during the timed region."""
 
@@ -133,36 +174,52 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(w, budget_s: float = 12.0, seed: int = 0):
-    """Time the CPU oracle, as it stands, on a bounded random sample of rows."""
+def cpu_baseline(w, budget_s: float = 12.0, seed: int = 0, one_thread_s: float = 5.0):
+    """Time the CPU oracle, as it stands, on a bounded random sample of rows: on all the
+    host's cores (the reported value) and on one thread (`one_thread`)."""
+    import oracle
     from oracle import Oracle
 
     o = Oracle.from_workload(w)
     rng = np.random.default_rng(seed)
-    rows = np.sort(rng.choice(w.M, min(w.M, 200), replace=False))
-    t = time.perf_counter()
-    o.sigma_rows(rows, w.c)
-    per_row = (time.perf_counter() - t) / len(rows)
-    n = int(min(w.M, max(200, budget_s / max(per_row, 1e-9))))
-    rows = np.sort(rng.choice(w.M, n, replace=False))
-    t = time.perf_counter()
-    o.sigma_rows(rows, w.c)
-    dt = time.perf_counter() - t
-    pairs = sum(len(o.connections(int(r))[0]) for r in rows)
     cores = len(os.sched_getaffinity(0))
-    return {"value": pairs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n} random rows of {w.M} ({pairs} pairs, {dt:.1f} s, OpenMP {cores} threads)"}
+
+    def sample(threads, budget):
+        oracle.set_threads(threads)
+        try:
+            rows = np.sort(rng.choice(w.M, min(w.M, 100), replace=False))
+            t = time.perf_counter()
+            o.sigma_rows(rows, w.c)
+            per_row = (time.perf_counter() - t) / len(rows)
+            n = int(min(w.M, max(100, budget / max(per_row, 1e-9))))
+            rows = np.sort(rng.choice(w.M, n, replace=False))
+            t = time.perf_counter()
+            o.sigma_rows(rows, w.c)
+            dt = time.perf_counter() - t
+        finally:
+            oracle.set_threads(0)
+        pairs = sum(len(o.connections(int(r))[0]) for r in rows)
+        return pairs / dt, f"{n} random rows of {w.M} ({pairs} pairs, {dt:.1f} s, OpenMP {threads} threads)"
+
+    v, smp = sample(cores, budget_s)
+    v1, smp1 = sample(1, one_thread_s)
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": smp,
+            "one_thread": {"value": v1, "unit": UNIT, "cores": 1, "sample": smp1}}
 
 
-def kato_temple(energies, residuals, nroots, target=1e-8):
-    """From nroots + 1 Ritz values and the residual norms of the first nroots: the gap of
-    each root to the nearest other value, the Kato-Temple bounds r_k^2 / gap_k on
-    |E_k - exact|, and the residual sqrt(target * min gap) that bounds every root's error
-    by `target`."""
+def kato_temple(energies, residuals, nroots, target=1e-8, floor=1e-12):
+    """From the Ritz values e_j of a reference run (at least nroots + 1 of them) and their
+    residual norms r_j: for each of the first nroots, the Kato-Temple gap
+        delta_k = min_{j != k} (|e_k - e_j| - r_j)   (clamped below at `floor`),
+    a lower bound on the distance from e_k to the rest of the exact spectrum (each exact
+    eigenvalue lies within r_j of some e_j), the bounds r_k^2 / delta_k on |E_k - exact|,
+    and the residual sqrt(target * min delta) that bounds every root's error by `target`."""
     e = np.asarray(energies, dtype=np.float64)
-    r = np.asarray(residuals, dtype=np.float64)[:nroots]
-    gaps = np.array([min(abs(e[k] - e[j]) for j in range(len(e)) if j != k) for k in range(nroots)])
-    return gaps, r ** 2 / gaps, float(np.sqrt(target * gaps.min()))
+    r = np.asarray(residuals, dtype=np.float64)
+    assert len(r) == len(e) and len(e) > nroots
+    gaps = np.array([max(floor, min(abs(e[k] - e[j]) - r[j] for j in range(len(e)) if j != k))
+                     for k in range(nroots)])
+    return gaps, r[:nroots] ** 2 / gaps, float(np.sqrt(target * gaps.min()))
 
 
 def davidson_bench(H, w, nroots=8, tol=1e-6):
@@ -334,10 +391,14 @@ def blockvec_bench(M=2_000_000, k=96, a=8, reps=5):
         t_tn = ev_ms(lambda: sci.sci_bv_gemm_tn(ctx, M, k + a, a, V, k + a, V[:, k:], k + a, P, prec))
         t_nn = ev_ms(lambda: sci.sci_bv_gemm_nn(ctx, M, a, W, k, k, Y, V, k + a, k, Yt, 0.0, R, a, d, th, cs, prec))
         res[name] = {"tn_ms": t_tn, "nn_ms": t_nn,
-                     "tn_tflops": flops_tn / t_tn / 1e9, "nn_tflops": flops_nn / t_nn / 1e9,
-                     "tn_frac_fp64_peak": flops_tn / t_tn / 1e9 / fp64_peak,
-                     "nn_frac_fp64_peak": flops_nn / t_nn / 1e9 / fp64_peak,
                      "tn_GBps": M * (k + a) * 8 / t_tn / 1e6, "nn_GBps": (M * 2 * k * 8 + M * a * 16) / t_nn / 1e6}
+        if name == "f64":   # FP64 FMAs on the FP64 pipe: a fraction of that pipe's peak
+            res[name].update({"tn_tflops": flops_tn / t_tn / 1e9, "nn_tflops": flops_nn / t_nn / 1e9,
+                              "tn_frac_fp64_peak": flops_tn / t_tn / 1e9 / fp64_peak,
+                              "nn_frac_fp64_peak": flops_nn / t_nn / 1e9 / fp64_peak})
+        else:               # paired FP32 on the FP32 pipes: FP64-equivalent rate, no FP64-pipe fraction
+            res[name].update({"tn_fp64_equiv_tflops": flops_tn / t_tn / 1e9,
+                              "nn_fp64_equiv_tflops": flops_nn / t_nn / 1e9})
     VT = V[:, :k + a]
     res["cublas_f64_tn_ms"] = ev_ms(lambda: VT.T @ V[:, k:])
     sci.sci_destroy(ctx)
@@ -472,6 +533,70 @@ def batch_ground_states(ws, hams, tol=1e-8):
             "max_abs_diff_Eh": float(np.abs(np.asarray(E1) - r.energies).max())}
 
 
+def spinor_bench(device, steps=10, warmup=3):
+    """The relativistic workload: 64 spinors, 14 electrons, 1,000,000 selected
+    determinants, complex128 (HF, singles, doubles and seeded random triples; 80 complex
+    Hermitian Cholesky vectors).  One sigma on one vector in FP64 and in paired FP32,
+    each timed as the main bench (CUDA events, L2 flushed between steps, per-kernel
+    events), with the doubles kernel's algorithmic-byte fraction of HBM (32 B per double
+    pair), its useful FP64 FMAs (4 per complex double pair) against the measured FP64
+    pipe rate, and the CPU oracle on sampled rows of the same space."""
+    import torch
+
+    from paper_2501_18185_gb300 import sci
+
+    dev = torch.device("cuda", device)
+    w = W.selected_spinor_64()
+    t = time.perf_counter()
+    H = sci.Hamiltonian.from_workload(w, device=device)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t
+    info = H.info()
+    gp = golden_pairs(w)
+    if gp is not None and gp != info["pairs"]:
+        raise SystemExit(f"spinor pair count {info['pairs']} differs from the oracle's {gp}")
+    C = torch.from_numpy(np.ascontiguousarray(w.c)).to(dev)
+    S = torch.empty_like(C)
+    flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    peak, peak_kind = hbm_peak()
+    pp = pipe_peaks(device)
+    sci.sci_profile(H.ctx, True)
+    out = {"workload": w.name, "M": w.M, "pairs_per_step": info["pairs"], "pairs_doubles": info["pairs_doubles"],
+           "setup_s": round(setup_s, 3), "l2": "flushed between timed steps (256 MB write)"}
+    for name, prec in (("f64", sci.SCI_PREC_F64), ("ds", sci.SCI_PREC_F64_DS)):
+        for _ in range(warmup):
+            H.sigma(C, out=S, prec=prec)
+        ms, kern = [], []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            H.sigma(C, out=S, prec=prec)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            kern.append(sci.sci_kernel_times(H.ctx))
+        m = statistics.mean(ms)
+        dbl = statistics.mean(k[1] for k in kern)
+        achieved = info["pairs_doubles"] * 32 / (dbl / 1e3) / 1e9
+        out[name] = {"ms_per_step": m, "pairs_per_s": info["pairs"] / (m / 1e3),
+                     "kernel_ms": {"init": statistics.mean(k[0] for k in kern), "doubles": dbl,
+                                   "singles": statistics.mean(k[2] for k in kern)},
+                     "doubles_alg_GBps": achieved, "doubles_alg_frac_hbm": achieved / peak}
+        if name == "f64":
+            fma = 4.0 * info["pairs_doubles"] / (dbl / 1e3)
+            out[name]["fp64_pipe"] = {"useful_fma_per_s": fma, "peak_fma_per_s": pp["fp64_fma_per_s"],
+                                      "frac": fma / pp["fp64_fma_per_s"]}
+    sci.sci_profile(H.ctx, False)
+    H.sync_status()
+    out["hbm_peak"] = {"GBps": peak, "source": peak_kind}
+    out["cpu_baseline"] = cpu_baseline(w, budget_s=8.0, one_thread_s=3.0)
+    del H
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args, rank, world):
     """--impl reference: the CPU oracle on bounded samples of the same workload."""
     if rank != 0:
@@ -517,7 +642,8 @@ def main():
     ap.add_argument("--no-davidson", action="store_true",
                     help="skip the 8-root Davidson timing and the density-matrix timing")
     ap.add_argument("--pt2-table-gb", type=float, default=96.0, help="hash-table memory of the pt2 section")
-    ap.add_argument("--only", default=None, choices=["blockvec", "rdm", "batch", "davidson", "pt2"],
+    ap.add_argument("--no-spinor", action="store_true", help="skip the 64-spinor complex workload section")
+    ap.add_argument("--only", default=None, choices=["blockvec", "rdm", "batch", "davidson", "pt2", "spinor"],
                     help="run one side section alone and print its JSON (profiling runs)")
     ap.add_argument("--prec", default="f64", choices=["f64", "ds", "f32"],
                     help="f64: FP64 FMA path; ds: paired-FP32 products/sums (FP64 tolerance); "
@@ -546,9 +672,10 @@ def main():
     torch.cuda.set_device(dev)
     build.build()
 
-    if args.only in ("blockvec", "batch", "pt2"):
+    if args.only in ("blockvec", "batch", "pt2", "spinor"):
         out = (blockvec_bench(M=args.M or 2_000_000) if args.only == "blockvec" else
                batch_bench() if args.only == "batch" else
+               spinor_bench(local) if args.only == "spinor" else
                pt2_bench(sizes=(args.M,) if args.M else (60_000, 200_000, 1_000_000, 2_000_000),
                          table_gb=args.pt2_table_gb))
         print(json.dumps({args.only: out}), flush=True)
@@ -652,19 +779,28 @@ def main():
     alg_bytes = info["pairs_doubles"] * (nv * sb + sb)
     peak, peak_kind = hbm_peak()
     achieved = alg_bytes / (dbl_ms / 1e3) / 1e9
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof):
-        try:
-            traffic = json.load(open(prof)).get(f"{w.name}/nvec{nv}")
-        except ValueError:
-            traffic = None
+    figs = profile_figures(f"{w.name}/nvec{nv}") if args.prec == "f64" else {}
+    traffic = figs.get("dram")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic if args.prec == "f64" else None,
+            "traffic": traffic,
+            "measure": "algorithmic-byte equivalent (what an HBM-streaming evaluation of the same pairs "
+                       "would move: double pairs x (nvec+1) x scalar bytes) / measured HBM copy peak",
+            "dram_GBps": traffic / (dbl_ms / 1e3) / 1e9 if traffic else None,
+            "dram_frac": traffic / (dbl_ms / 1e3) / 1e9 / peak if traffic else None,
             "kernel": {"f64": "k_doubles", "ds": "k_doubles_ds", "f32": "k_doubles_f32"}[args.prec],
             "peak_source": peak_kind,
             "algorithmic_bytes_per_launch": alg_bytes,
             "kernel_ms": {"init": init_ms, "doubles": dbl_ms, "singles": sgl_ms}}
+    # the resources that bind the doubles kernel: the FP64 pipe (one FMA per double pair
+    # and vector, four in complex mode) against its measured rate, and L2 (ncu bytes)
+    pp = pipe_peaks(local)
+    if args.prec == "f64":
+        fma = (4 if w.ints.complex_ else 1) * nv * info["pairs_doubles"] / (dbl_ms / 1e3)
+        roof["fp64_pipe"] = {"useful_fma_per_s": fma, "peak_fma_per_s": pp["fp64_fma_per_s"],
+                             "frac": fma / pp["fp64_fma_per_s"], "peak_source": pp["how"]}
+    if figs.get("l2"):
+        roof["l2"] = {"bytes_per_launch": figs["l2"], "GBps": figs["l2"] / (dbl_ms / 1e3) / 1e9,
+                      "source": figs.get("l2_note")}
 
     if rank != 0:
         if dist:
@@ -681,6 +817,9 @@ def main():
         rdm = rdm_bench(H, w)
         batch = batch_bench()
         pt2 = pt2_bench(sizes=(200_000,))
+    spinor = None
+    if not args.no_spinor and world == 1 and not w.ints.complex_:
+        spinor = spinor_bench(local)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
@@ -693,7 +832,8 @@ def main():
             "gpu_launches": args.steps * (1 + {"f64": 2, "ds": 4, "f32": 3}[args.prec]
                                           * ((nv + 7) // 8 if not w.ints.complex_ else (nv + 3) // 4)),
             "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "prec": args.prec,
-            "other_prec": variant, "davidson": dav, "rdm": rdm, "batch": batch, "pt2": pt2}
+            "other_prec": variant, "pipe_peaks": pp, "davidson": dav, "rdm": rdm, "batch": batch, "pt2": pt2,
+            "spinor": spinor}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -85,7 +85,11 @@ def test_kato_temple_bound_holds_and_sets_the_tolerance():
 def test_kato_temple_gaps():
     import bench
 
-    gaps, bounds, t = bench.kato_temple([-3.0, -2.9, -1.0, 0.5], [1e-3, 2e-3, 1e-4], 3, target=1e-8)
-    assert np.allclose(gaps, [0.1, 0.1, 1.5])
-    assert np.allclose(bounds, [1e-6 / 0.1, 4e-6 / 0.1, 1e-8 / 1.5])
-    assert abs(t - np.sqrt(1e-8 * 0.1)) < 1e-15
+    # delta_k = min_j (|e_k - e_j| - r_j): the other Ritz values' residuals shrink the gap
+    gaps, bounds, t = bench.kato_temple([-3.0, -2.9, -1.0, 0.5], [1e-3, 2e-3, 1e-4, 5e-4], 3, target=1e-8)
+    assert np.allclose(gaps, [0.1 - 2e-3, 0.1 - 1e-3, 1.5 - 5e-4])
+    assert np.allclose(bounds, [1e-6 / 0.098, 4e-6 / 0.099, 1e-8 / 1.4995])
+    assert abs(t - np.sqrt(1e-8 * 0.098)) < 1e-15
+    # a gap eaten by a residual is clamped, not negative
+    gaps, _, _ = bench.kato_temple([-1.0, -0.99], [1e-3, 0.5], 1)
+    assert gaps[0] == 1e-12
