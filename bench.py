@@ -14,8 +14,11 @@ solvers (FP64 against FP32-refined), the density matrices and autograd energy, t
 batched instances, ENPT2, and one sigma on the 1,000,000-determinant 64-spinor complex
 space (`spinor`), each with its own figures.
 
-Under torchrun (N > 1) every rank runs an independent replica of the workload (weak
-scaling, no collective on the data path); the value is all ranks' pairs / max time.
+Under torchrun (N > 1) the ranks share the sigma of one space: each holds the whole
+determinant list and the integrals, computes a contiguous range of rows balanced by the
+rows' connection counts, and one NCCL all-gather of the row slices ends the step (the
+paper's Sec. 3.1 split: static data replicated, results merged).  Strong scaling: the
+value is the space's pairs per step / the slowest rank's time per step.
 `--impl reference` times the CPU oracle (the only reference implementation: the paper
 ships no code) on a bounded sample of rows of the same workload.
 """
@@ -74,9 +77,15 @@ def max_over_ranks(x: float, dist=None, device="cpu") -> float:
 
 
 def job_throughput(pairs_per_step: int, steps: int, world: int, total_ms: float) -> float:
-    """Whole-job pairs/s: every rank runs its own replica of `pairs_per_step` pairs per
+    """Whole-job pairs/s when every rank runs its own replica of `pairs_per_step` pairs per
     step (weak scaling), timed by the slowest rank's total."""
     return world * pairs_per_step * steps / (total_ms / 1e3)
+
+
+def split_throughput(pairs_per_step: int, steps: int, total_ms: float) -> float:
+    """Whole-job pairs/s when the ranks share one sigma of `pairs_per_step` pairs per step
+    (row split, strong scaling), timed by the slowest rank's total."""
+    return pairs_per_step * steps / (total_ms / 1e3)
 
 
 def measured_peaks() -> dict:
@@ -597,6 +606,71 @@ def spinor_bench(device, steps=10, warmup=3):
     return out
 
 
+def rowsplit_bench(H, parts=(2, 4, 8), steps=5):
+    """The row split of the bench space, each rank timed alone on this GPU: for K ranks,
+    the K ranges balanced by connection count + C(N, 2) per row, then for each range its
+    set-up (range tables), its device bytes, its pairs and its sigma time (CUDA events, L2
+    flushed, median of `steps` after one warm-up).  A K-GPU step takes the slowest rank's
+    sigma plus one all-gather of sigma's M x 8 bytes; `speedup_vs_full` is the full
+    sigma's time over the slowest rank's (the all-gather left out: not measurable on one
+    GPU)."""
+    import math
+
+    import torch
+
+    from paper_2501_18185_gb300 import partition as PT
+
+    dev = H.device
+    stream = torch.cuda.current_stream(dev)
+    C = torch.ones((H.M, 1), dtype=torch.float64, device=dev) / math.sqrt(max(H.M, 1))
+    S = torch.empty_like(C)
+    flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=dev)
+
+    def med_ms():
+        H.sigma(C, out=S)
+        out = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            H.sigma(C, out=S)
+            e1.record(stream)
+            e1.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return statistics.median(out)
+
+    H.set_row_range(0, H.M)
+    full_ms = med_ms()
+    base_bytes = H.info()["device_bytes"]
+    cost = H.row_costs().cpu().numpy()
+    over = math.comb(H.n_electrons, 2)
+    res = {"full_ms": full_ms, "row_weight": f"connected determinants + C(N,2) = {over}", "parts": {}}
+    weights = PT.row_weights(cost, over)
+
+    def time_ranges(ranges):
+        ranks = []
+        for b, e in ranges:
+            t = time.perf_counter()
+            H.set_row_range(b, e)
+            setup = time.perf_counter() - t
+            inf = H.info()
+            ranks.append({"rows": [int(b), int(e)], "pairs": inf["pairs"], "setup_s": round(setup, 3),
+                          "range_table_bytes": inf["device_bytes"] - base_bytes, "ms": med_ms()})
+        H.set_row_range(0, H.M)
+        mx = max(r["ms"] for r in ranks)
+        return {"max_ms": mx, "mean_ms": statistics.mean(r["ms"] for r in ranks),
+                "speedup_vs_full": full_ms / mx, "ranks": ranks}
+
+    for K in parts:
+        first = time_ranges(PT.balanced_ranges(weights, K))
+        # one feedback round: the measured times re-cut the ranges (partition.rebalance)
+        again = time_ranges(PT.rebalance(weights, [tuple(r["rows"]) for r in first["ranks"]],
+                                         [r["ms"] for r in first["ranks"]]))
+        res["parts"][str(K)] = {"by_weights": first, "rebalanced": again}
+    H.sync_status()
+    return res
+
+
 def run_reference(args, rank, world):
     """--impl reference: the CPU oracle on bounded samples of the same workload."""
     if rank != 0:
@@ -643,7 +717,8 @@ def main():
                     help="skip the 8-root Davidson timing and the density-matrix timing")
     ap.add_argument("--pt2-table-gb", type=float, default=96.0, help="hash-table memory of the pt2 section")
     ap.add_argument("--no-spinor", action="store_true", help="skip the 64-spinor complex workload section")
-    ap.add_argument("--only", default=None, choices=["blockvec", "rdm", "batch", "davidson", "pt2", "spinor"],
+    ap.add_argument("--only", default=None, choices=["blockvec", "rdm", "batch", "davidson", "pt2", "spinor",
+                                                     "rowsplit"],
                     help="run one side section alone and print its JSON (profiling runs)")
     ap.add_argument("--prec", default="f64", choices=["f64", "ds", "f32"],
                     help="f64: FP64 FMA path; ds: paired-FP32 products/sums (FP64 tolerance); "
@@ -693,9 +768,30 @@ def main():
     gp = golden_pairs(w)
     if gp is not None and gp != pairs:
         raise SystemExit(f"pair count {pairs} differs from the oracle's {gp}")
+    split = None
+    if world > 1:   # row split: this rank's range of rows, merged by one all-gather per step
+        from paper_2501_18185_gb300.partition import RowSplitSigma, gather_rows
 
-    if args.only in ("rdm", "davidson"):
-        out = rdm_bench(H, w) if args.only == "rdm" else davidson_bench(H, w)
+        t = time.perf_counter()
+        split = RowSplitSigma.balanced(H, world, rank)
+        torch.cuda.synchronize()
+        split_setup_s = time.perf_counter() - t
+        # one feedback round: time this rank's sigma, re-cut the ranges from all ranks' times
+        Cw = torch.from_numpy(np.ascontiguousarray(w.c)).to(dev)
+        Sw = torch.empty_like(Cw)
+        H.sigma(Cw, out=Sw)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            H.sigma(Cw, out=Sw)
+        e1.record(stream)
+        e1.synchronize()
+        split.rebalance(e0.elapsed_time(e1) / 3, split.weights)
+        del Cw, Sw
+
+    if args.only in ("rdm", "davidson", "rowsplit"):
+        out = (rdm_bench(H, w) if args.only == "rdm" else davidson_bench(H, w) if args.only == "davidson"
+               else rowsplit_bench(H))
         print(json.dumps({args.only: out}), flush=True)
         return
     C64 = torch.from_numpy(np.ascontiguousarray(w.c)).to(dev)
@@ -710,9 +806,14 @@ def main():
     def vec(p):
         return C if p == prec else C64
 
+    def step(p):
+        H.sigma(vec(p), out=S, prec=p)
+        if split is not None:
+            gather_rows(S, split.ranges)
+
     for _ in range(args.warmup):
-        H.sigma(vec(prec), out=S, prec=prec)
-        H.sigma(vec(other), out=S, prec=other)
+        step(prec)
+        step(other)
     H.sync_status()
     sci.sci_profile(H.ctx, True)
 
@@ -729,7 +830,7 @@ def main():
         for _ in range(steps):
             flush.zero_()                      # evict L2 between timed steps
             ev0.record(stream)
-            H.sigma(vec(prec), out=S, prec=prec)
+            step(prec)
             ev1.record(stream)
             ev1.synchronize()
             ms_.append(ev0.elapsed_time(ev1))
@@ -745,7 +846,7 @@ def main():
     o_ms, o_kern = timed(other, max(3, min(args.steps, 5)))
     variant = {"prec": "ds" if other == sci.SCI_PREC_F64_DS else "f64",
                "ms_per_step": statistics.mean(o_ms),
-               "value": world * pairs / (statistics.mean(o_ms) / 1e3),
+               "value": pairs / (statistics.mean(o_ms) / 1e3),
                "kernel_ms": {"init": statistics.mean(k[0] for k in o_kern),
                              "doubles": statistics.mean(k[1] for k in o_kern),
                              "singles": statistics.mean(k[2] for k in o_kern)}}
@@ -754,24 +855,41 @@ def main():
 
     total_ms = max_over_ranks(sum(step_ms), dist, dev)
     ms = total_ms / args.steps
-    value = job_throughput(pairs, args.steps, world, total_ms)
+    value = split_throughput(pairs, args.steps, total_ms)
 
-    # end to end through the public API with host buffers (pinned), copies inside
+    # end to end through the public API with host buffers (pinned), copies inside: one
+    # process calls sci_sigma_host; with a row split each rank copies C in, computes its
+    # rows, the slices are all-gathered and S is copied out
     Ch = torch.from_numpy(np.ascontiguousarray(w.c, dtype=np.float32 if args.prec == "f32" else None)).pin_memory()
     Sh = torch.empty(tuple(C64.shape), dtype=C64.dtype).pin_memory()
-    sci.sci_sigma_host(H.ctx, Ch, Sh, nv, prec)
+
+    def e2e_step():
+        if split is None:
+            sci.sci_sigma_host(H.ctx, Ch, Sh, nv, prec)
+            return
+        vec(prec).copy_(Ch, non_blocking=True)
+        step(prec)
+        Sh.copy_(S, non_blocking=True)
+        torch.cuda.synchronize()
+
+    e2e_step()
     e2e_t = []
     for _ in range(max(3, min(args.steps, 10))):
         flush.zero_()
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         t = time.perf_counter()
-        sci.sci_sigma_host(H.ctx, Ch, Sh, nv, prec)
+        e2e_step()
         e2e_t.append(time.perf_counter() - t)
-    e2e = world * pairs / statistics.mean(e2e_t)
+    e2e = pairs / (max_over_ranks(statistics.mean(e2e_t) * 1e3, dist, dev) / 1e3)
     nbytes = Ch.numel() * Ch.element_size()
     nbytes_out = Sh.numel() * Sh.element_size()
 
     # roofline of the dominant kernel (double excitations): algorithmic bytes per launch
+    # (with a row split, of this rank's launch: its rows' double pairs)
+    if split is not None:
+        info = H.info()
     sb = 16 if w.ints.complex_ else (4 if args.prec == "f32" else 8)
     dbl_ms = statistics.mean(k[1] for k in kern)
     sgl_ms = statistics.mean(k[2] for k in kern)
@@ -810,30 +928,33 @@ def main():
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(w)
     dav = None
-    rdm = batch = pt2 = None
+    rdm = batch = pt2 = rowsplit = None
     if not args.no_davidson and world == 1 and not w.ints.complex_:
         dav = davidson_bench(H, w)
         dav["blockvec"] = blockvec_bench()
         rdm = rdm_bench(H, w)
         batch = batch_bench()
         pt2 = pt2_bench(sizes=(200_000,))
+        rowsplit = rowsplit_bench(H)
     spinor = None
     if not args.no_spinor and world == 1 and not w.ints.complex_:
         spinor = spinor_bench(local)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None,
             "dtype": "c128" if w.ints.complex_ else {"f64": "f64", "ds": "f64", "f32": "f32-store/f64-acc"}[args.prec],
             "data": "synthetic",
             "config": {"workload": w.name, "M": w.M, "nvec": nv, "pairs_per_step": pairs,
                        "l2": "flushed between timed steps (256 MB write)", "setup_s": round(setup_s, 3),
-                       "parallelism": f"replicas{world}" if world > 1 else "single"},
+                       "parallelism": f"rowsplit{world}" if world > 1 else "single",
+                       **({"rank0_rows": list(split.ranges[0]), "split_setup_s": round(split_setup_s, 3)}
+                          if split is not None else {})},
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes_out},
             "gpu_launches": args.steps * (1 + {"f64": 2, "ds": 4, "f32": 3}[args.prec]
                                           * ((nv + 7) // 8 if not w.ints.complex_ else (nv + 3) // 4)),
             "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "prec": args.prec,
             "other_prec": variant, "pipe_peaks": pp, "davidson": dav, "rdm": rdm, "batch": batch, "pt2": pt2,
-            "spinor": spinor}
+            "spinor": spinor, "rowsplit": rowsplit}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -154,7 +154,7 @@ struct sci_ctx {
     // pairs (I, J) with I in the range
     int ranged = 0;
     int64_t row_b = 0, row_e = 0;
-    int64_t r2 = 0, r1 = 0, range_pairs = 0;
+    int64_t r2 = 0, r1 = 0, range_pairs = 0, range_pairs2 = 0, range_pairs1 = 0;
     uint32_t *r2_idx = nullptr, *r2_code = nullptr, *r2_pos = nullptr;
     uint32_t *r1_idx = nullptr;
     uint64_t *r1_S = nullptr;
@@ -196,7 +196,9 @@ void sci_free_range(sci_ctx *ctx);
 
 // launchers (sci_sigma.cu)
 bool sci_sigma_window_fits(const sci_ctx *ctx);
-int sci_launch_sigma(sci_ctx *ctx, const void *C, void *S, int nvec, int prec);
+// whole_list: every row over the full tables whatever the context's row range (internal
+// callers such as ENPT2); otherwise the rows of the range, if one is set
+int sci_launch_sigma(sci_ctx *ctx, const void *C, void *S, int nvec, int prec, bool whole_list = false);
 int sci_count_pairs_device(sci_ctx *ctx, int64_t *pairs2, int64_t *pairs1);
 int sci_connections_device(sci_ctx *ctx, int64_t row_begin, int64_t row_end, int64_t *count,
                            int64_t *rows, int64_t *J, int8_t *degree, int8_t *phase,

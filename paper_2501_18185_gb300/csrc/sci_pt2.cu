@@ -410,7 +410,7 @@ int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t
     }
     // E2[P]: one FP64 sigma
     if (M > 0) {
-        rc = sci_launch_sigma(ctx, C, S, R, SCI_PREC_F64);
+        rc = sci_launch_sigma(ctx, C, S, R, SCI_PREC_F64, true);   // every row, whatever the row range
         if (rc) {
             cleanup();
             return rc;

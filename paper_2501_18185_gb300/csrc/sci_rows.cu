@@ -201,7 +201,7 @@ void sci_free_range(sci_ctx *ctx)
     ctx->range_bytes = 0;
     ctx->ranged = 0;
     ctx->row_b = ctx->row_e = 0;
-    ctx->r1 = ctx->r2 = ctx->range_pairs = 0;
+    ctx->r1 = ctx->r2 = ctx->range_pairs = ctx->range_pairs2 = ctx->range_pairs1 = 0;
 }
 
 extern "C" int sci_set_row_range(sci_ctx *ctx, int64_t row_begin, int64_t row_end)
@@ -243,6 +243,8 @@ extern "C" int sci_set_row_range(sci_ctx *ctx, int64_t row_begin, int64_t row_en
     }
     ctx->bytes_held += ctx->range_bytes;
     ctx->range_pairs = (int64_t)(h[0] + h[1]);
+    ctx->range_pairs2 = (int64_t)h[0];
+    ctx->range_pairs1 = (int64_t)h[1];
     ctx->row_b = row_begin;
     ctx->row_e = row_end;
     ctx->ranged = 1;

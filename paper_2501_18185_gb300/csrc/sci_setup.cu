@@ -995,8 +995,10 @@ extern "C" int sci_count_pairs(sci_ctx *ctx, int64_t *pairs)
 extern "C" int sci_info(sci_ctx *ctx, int64_t *out, int n)
 {
     if (!ctx || !out || n < 0 || n > 10) return SCI_ERR_ARG;
-    int64_t v[10] = {ctx->M, ctx->pairs, ctx->e2, ctx->nb2, ctx->e1, ctx->nb1, std::max(ctx->maxb1, ctx->maxb2),
-                     (int64_t)ctx->bytes_held, ctx->pairs2, ctx->pairs1};
+    const bool r = ctx->ranged;
+    int64_t v[10] = {ctx->M, r ? ctx->range_pairs : ctx->pairs, ctx->e2, ctx->nb2, ctx->e1, ctx->nb1,
+                     std::max(ctx->maxb1, ctx->maxb2), (int64_t)ctx->bytes_held, r ? ctx->range_pairs2 : ctx->pairs2,
+                     r ? ctx->range_pairs1 : ctx->pairs1};
     for (int i = 0; i < n; i++) out[i] = v[i];
     return SCI_OK;
 }

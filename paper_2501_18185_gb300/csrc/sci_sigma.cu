@@ -1141,10 +1141,16 @@ int launch_sigma(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int nvec, 
 
 }  // namespace
 
-int sci_launch_sigma(sci_ctx *ctx, const void *C, void *S, int nvec, int prec)
+int sci_launch_sigma(sci_ctx *ctx, const void *C, void *S, int nvec, int prec, bool whole_list)
 {
-    const Tabs T = tabs_of(ctx);
-    return ctx->ranged ? launch_sigma<true>(ctx, T, C, S, nvec, prec) : launch_sigma<false>(ctx, T, C, S, nvec, prec);
+    if (whole_list || !ctx->ranged) {
+        const bool ranged = ctx->ranged;
+        ctx->ranged = 0;   // tabs_of: the full tables
+        const Tabs T = tabs_of(ctx);
+        ctx->ranged = ranged;
+        return launch_sigma<false>(ctx, T, C, S, nvec, prec);
+    }
+    return launch_sigma<true>(ctx, tabs_of(ctx), C, S, nvec, prec);
 }
 
 int sci_count_pairs_device(sci_ctx *ctx, int64_t *pairs2, int64_t *pairs1)

@@ -55,6 +55,22 @@ def balanced_ranges(weights, parts: int) -> list[tuple[int, int]]:
     return [(cuts[k], cuts[k + 1]) for k in range(parts)]
 
 
+def rebalance(weights, ranges, times) -> list[tuple[int, int]]:
+    """Re-cut the ranges after timing them once: within each range the measured time is
+    spread over its rows in proportion to their weights (the weight model is trusted inside
+    a range, its scale is not), and the rows are cut again by balanced_ranges.  This
+    corrects costs the weights miss, such as the staging of the buckets a range touches,
+    which grows for ranges of highly excited rows."""
+    w = np.asarray(weights, dtype=np.float64).reshape(-1).copy()
+    if len(times) != len(ranges):
+        raise ValueError("one time per range")
+    for (b, e), t in zip(ranges, times):
+        s = float(w[b:e].sum())
+        if e > b and s > 0:
+            w[b:e] *= float(t) / s
+    return balanced_ranges(w, len(ranges))
+
+
 def gather_rows(S, ranges, group=None):
     """Merge the row slices of a row-partitioned sigma in place: rank r holds valid rows
     ranges[r] of S ([M] or [M, nvec] torch tensor, real or complex); afterwards every rank
@@ -101,8 +117,26 @@ class RowSplitSigma:
         C(N, 2) (N-2)-hole keys a row emits."""
         cost = H.row_costs().cpu().numpy()
         N = H.n_electrons
-        ranges = balanced_ranges(row_weights(cost, math.comb(N, 2)), world)
-        return cls(H, ranges, rank, group)
+        weights = row_weights(cost, math.comb(N, 2))
+        rs = cls(H, balanced_ranges(weights, world), rank, group)
+        rs.weights = weights
+        return rs
+
+    def rebalance(self, my_ms: float, weights):
+        """Re-cut the ranges from every rank's measured sigma time (all-gathered, so every
+        rank computes the same ranges) and set this rank's new range."""
+        import torch
+        import torch.distributed as dist
+
+        world = dist.get_world_size(self.group)
+        dev = self.H.device if dist.get_backend(self.group) == "nccl" else "cpu"
+        t = torch.tensor([float(my_ms)], dtype=torch.float64, device=dev)
+        all_t = torch.empty(world, dtype=torch.float64, device=dev)
+        dist.all_gather_into_tensor(all_t, t, group=self.group)
+        self.ranges = rebalance(weights, self.ranges, all_t.cpu().numpy())
+        b, e = self.ranges[self.rank]
+        self.H.set_row_range(b, e)
+        return self.ranges
 
     def __call__(self, C, out=None, prec=None):
         from . import sci

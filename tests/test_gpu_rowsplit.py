@@ -143,3 +143,22 @@ def test_row_split_sigma_class_one_rank(gpu):
         assert np.allclose(out.numpy(), ref, rtol=1e-13, atol=1e-15)
     finally:
         dist.destroy_process_group()
+
+
+def test_whole_list_calls_ignore_the_row_range(gpu):
+    """ENPT2 (its E2[P] sigma), the density matrices and the pair export of a context with
+    a row range set still cover the whole list, as include/sci.h states."""
+    torch = gpu
+    w = W.random_small(305, "spin_orbitals", 10, 2, 2, naux=6, frac=0.2)
+    H = sci.Hamiltonian.from_workload(w)
+    ev, U = np.linalg.eigh(Oracle.from_workload(w).dense())
+    C = torch.from_numpy(U[:, :2].copy()).cuda()
+    ref = H.enpt2(C, ev[:2])
+    g1, g2 = H.rdm12(C)
+    n_all, _ = sci.sci_connections(H.ctx, 0, w.M, 0)
+    H.set_row_range(w.M // 3, w.M // 2)
+    got = H.enpt2(C, ev[:2])
+    assert np.allclose(got[2], ref[2], rtol=1e-12) and np.allclose(got[1], ref[1], rtol=1e-12)
+    h1, h2 = H.rdm12(C)
+    assert torch.allclose(h1, g1, rtol=1e-12, atol=1e-14) and torch.allclose(h2, g2, rtol=1e-12, atol=1e-14)
+    assert sci.sci_connections(H.ctx, 0, w.M, 0)[0] == n_all

@@ -47,6 +47,27 @@ def test_balanced_ranges_edge_cases():
         PT.balanced_ranges(np.ones(3), 0)
 
 
+def test_rebalance_evens_out_a_cost_the_weights_miss():
+    """True row time = weight x a factor that grows along the list (as the staging of
+    touched buckets does): after one measured round, the re-cut ranges are more even."""
+    rng = np.random.default_rng(11)
+    w = rng.uniform(50, 150, size=20000)
+    true = w * np.linspace(1.0, 2.0, w.size)
+    for parts in (2, 4, 8):
+        r0 = PT.balanced_ranges(w, parts)
+        t0 = np.array([true[b:e].sum() for b, e in r0])
+        r1 = PT.rebalance(w, r0, t0)
+        _check_ranges(r1, w.size, parts)
+        t1 = np.array([true[b:e].sum() for b, e in r1])
+        assert t1.max() / t1.mean() < t0.max() / t0.mean()
+        assert t1.max() / t1.mean() - 1 < 0.15 * (t0.max() / t0.mean() - 1)    # one round
+        r2 = PT.rebalance(w, r1, t1)
+        t2 = np.array([true[b:e].sum() for b, e in r2])
+        assert t2.max() / t2.mean() < 1.005                                     # two rounds
+    with pytest.raises(ValueError):
+        PT.rebalance(w, PT.balanced_ranges(w, 2), [1.0])
+
+
 def test_row_weights():
     assert np.array_equal(PT.row_weights([0, 5, 2], 3), [3.0, 8.0, 5.0])
 

@@ -54,11 +54,13 @@ def test_noalloc_export_takes_no_device_memory(gpu):
     torch = gpu
     w = W.selected_30o(M=60000)
     H = sci.Hamiltonian.from_workload(w)
-    n_ref, _ = sci.sci_connections(H.ctx, 100, 400, 0)
+    rb, re = 30000, 30150          # a range well inside the fixed scratch's 524,288 pairs
+    n_ref, _ = sci.sci_connections(H.ctx, rb, re, 0)
+    assert 0 < n_ref <= 524288
     torch.cuda.synchronize()
     for _ in range(3):
         free0 = torch.cuda.mem_get_info()[0]
-        rc, n, _ = _call(H.ctx, 100, 400, n_ref)
+        rc, n, _ = _call(H.ctx, rb, re, n_ref)
         free1 = torch.cuda.mem_get_info()[0]
         assert rc == sci.SCI_OK and n == n_ref
         assert free1 == free0, (free0, free1)
