@@ -449,6 +449,35 @@ def pt2_bench(sizes=(60_000, 200_000, 1_000_000, 2_000_000), table_gb=96.0):
     return out
 
 
+def pt2_spinor_bench(M=200_000, table_gb=96.0):
+    """Epstein-Nesbet PT2 in complex spinor mode (the 4C workloads of the paper's Sec. 4) on
+    a space of the 64-spinor recipe: c is the recipe's complex vector (|c| = exp(-level),
+    random phases), normalised, and E0 its Rayleigh quotient c^+ H c; exact sci_enpt2 (no
+    screening), wall seconds (synchronous), batches, distinct W and the generated count
+    (M x (N (n - N) + C(N,2) C(n - N, 2)))."""
+    import torch
+
+    from paper_2501_18185_gb300 import sci
+
+    w = W.selected_spinor_64(M=M)
+    H = sci.Hamiltonian.from_workload(w)
+    c = torch.from_numpy(np.ascontiguousarray(w.c)).cuda()
+    c = c / torch.linalg.vector_norm(c)
+    E0 = [float((c.conj() * H.sigma(c)).sum().real)]
+    H.enpt2(c, E0, table_bytes=1 << 28)   # warm-up: loads the kernels
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    e2w, e2p, e2q, st = H.enpt2(c, E0, table_bytes=int(table_gb * (1 << 30)))
+    dt = time.perf_counter() - t
+    n, N = w.n, w.n_alpha
+    per = N * (n - N) + N * (N - 1) // 2 * ((n - N) * (n - N - 1) // 2)
+    out = {"workload": w.name, "M": M, "seconds": dt, "E0": E0[0], "E2_Q": float(e2q[0]), "E2_W": float(e2w[0]),
+           "E2_P": float(e2p[0]), "generated": M * per, "generated_per_s": M * per / dt, **st}
+    del H
+    torch.cuda.empty_cache()
+    return out
+
+
 def batch_bench(reps=10):
     """The 64 heterogeneous full-CI instances in one persistent launch: setup, autotuner
     time and choices, and CUDA-event milliseconds per batched sigma (L2 flushed before
@@ -718,7 +747,7 @@ def main():
     ap.add_argument("--pt2-table-gb", type=float, default=96.0, help="hash-table memory of the pt2 section")
     ap.add_argument("--no-spinor", action="store_true", help="skip the 64-spinor complex workload section")
     ap.add_argument("--only", default=None, choices=["blockvec", "rdm", "batch", "davidson", "pt2", "spinor",
-                                                     "rowsplit"],
+                                                     "rowsplit", "pt2_spinor"],
                     help="run one side section alone and print its JSON (profiling runs)")
     ap.add_argument("--prec", default="f64", choices=["f64", "ds", "f32"],
                     help="f64: FP64 FMA path; ds: paired-FP32 products/sums (FP64 tolerance); "
@@ -747,10 +776,11 @@ def main():
     torch.cuda.set_device(dev)
     build.build()
 
-    if args.only in ("blockvec", "batch", "pt2", "spinor"):
+    if args.only in ("blockvec", "batch", "pt2", "spinor", "pt2_spinor"):
         out = (blockvec_bench(M=args.M or 2_000_000) if args.only == "blockvec" else
                batch_bench() if args.only == "batch" else
                spinor_bench(local) if args.only == "spinor" else
+               pt2_spinor_bench(M=args.M or 200_000, table_gb=args.pt2_table_gb) if args.only == "pt2_spinor" else
                pt2_bench(sizes=(args.M,) if args.M else (60_000, 200_000, 1_000_000, 2_000_000),
                          table_gb=args.pt2_table_gb))
         print(json.dumps({args.only: out}), flush=True)
@@ -935,6 +965,7 @@ def main():
         rdm = rdm_bench(H, w)
         batch = batch_bench()
         pt2 = pt2_bench(sizes=(200_000,))
+        pt2.append({"spinor": pt2_spinor_bench()})
         rowsplit = rowsplit_bench(H)
     spinor = None
     if not args.no_spinor and world == 1 and not w.ints.complex_:

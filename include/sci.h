@@ -210,7 +210,8 @@ int sci_sigma_host(sci_ctx *ctx, const void *C_host, void *S_host, int nvec, int
 /* Table sizes, for reports: out[0..n) receives, in order, M, pairs, entries and buckets
  * of the (N-2)-hole table, entries and buckets of the (N-1)-hole table, the largest
  * bucket, the device bytes held by the context, the double-excitation pairs and the
- * single-excitation pairs.  n <= 10. */
+ * single-excitation pairs (with a row range set, the three pair counts are the range's:
+ * pairs (I, J) with I in the range).  n <= 10. */
 int sci_info(sci_ctx *ctx, int64_t *out, int n);
 
 /* Kernel timing for reports.  sci_profile(ctx, 1) makes later sci_sigma() calls record
@@ -242,20 +243,42 @@ int sci_kernel_times(sci_ctx *ctx, float *ms, int n);
  * SCI_ERR_NOMEM. */
 int sci_rdm12(sci_ctx *ctx, const void *C, int nvec, const double *weights, void *rdm1, void *rdm2);
 
+/* Gradients of weighted Rayleigh quotients with respect to the integrals, from the density
+ * matrices of sci_rdm12 (Sec. 3.4) contracted on the device.  Real spin-orbital mode.
+ * With g1, g2 the spin-orbital density matrices of sum_k w_k |c_k><c_k| (see sci_rdm12):
+ *   gamma[p][q]       = sum_s g1[ps][qs]                    (dE/dh_pq for E = c^T H c)
+ *   Gamma[p][q][r][s] = sum_{s1,s2} g2[p s1][q s1][r s2][s s2]  (dE/d(pq|rs) = Gamma / 2)
+ *   gchol[P][p][q]    = sum_rs Gamma[p][q][r][s] chol[P][r][s]
+ *                                   (dE/dL^P_pq for (pq|rs) = sum_P L^P_pq L^P_rs)
+ * over the n spatial orbitals (bit p < n alpha p, bit n + p beta p).
+ *   C: device [M][nvec] doubles; weights: HOST, nvec doubles or NULL (all ones).
+ *   gamma: device [n][n] or NULL.  Gamma: device [n]^4 or NULL.
+ *   chol: device [naux][n][n] and gchol: device [naux][n][n] (overwritten), or both NULL.
+ * The 2-RDM walk runs only when Gamma or chol is given.  Synchronous; allocates and frees
+ * a scratch buffer (the spin-orbital matrices, (2n)^4 doubles).  Errors: SCI_ERR_STATE,
+ * SCI_ERR_ARG (mode, NULL operands, naux < 1), SCI_ERR_NOMEM, and those of sci_rdm12. */
+int sci_rdm_grads(sci_ctx *ctx, const double *C, int nvec, const double *weights, double *gamma,
+                  double *Gamma, int naux, const double *chol, double *gchol);
+
 /* Epstein-Nesbet second-order energy of roots of the variational space (Sec. 2.4,
  * constraint-based ENPT2, with P_m = P):
  *   E2_k[Q] = E2_k[W] - E2_k[P]                                         (Eq. PT2final)
  *   E2_k[W] = sum_{I in W} (sum_{J in P} H_IJ c_Jk)^2 / (E0_k - H_II)    (Eq. EW1)
  *   E2_k[P] = sum_{I in P} (<I|H|c_k> - c_Ik H_II)^2 / (E0_k - H_II)     (Eq. EP1)
  * over W, the determinants within a single or double excitation of the list.  Real
- * spin-orbital mode, n <= 32.
- *   C: device, [M][nroots] doubles, 1 <= nroots <= 8 (need not be normalised; the
- *      formulas use c as given, so pass normalised eigenvectors for energies).
+ * spin-orbital mode (n <= 32; batches by a code of the beta string) or complex spinor
+ * mode (n <= 64, no spin conservation, the 4C workloads of Sec. 4; batches by a code of
+ * the whole string; the squares are |.|^2 of complex numerators).  Spinor mode with real
+ * integrals returns SCI_ERR_ARG.
+ *   C: device, [M][nroots] doubles (complex mode: complex128, interleaved), 1 <= nroots
+ *      <= 8 (need not be normalised; the formulas use c as given, so pass normalised
+ *      eigenvectors for energies).
  *   E0: HOST, nroots doubles (the zeroth-order energies E0_k).
  *   eps: screening; a generated contribution with |H_IJ| max_k |c_Jk| < eps is dropped
  *      (0 = exact).
  *   table_bytes: device memory for the hash table of one batch (8 + 8 nroots bytes per
- *      entry, capacity the largest power of two within the budget, at least 256).  W is split into
+ *      entry, 8 + 16 nroots in complex mode, capacity the largest power of two within the
+ *      budget, at least 256).  W is split into
  *      2^t batches (t <= 10) so that a batch's generated excitations fill at most 60% of
  *      it; a batch that still overflows (or probes too far) restarts the sum with twice
  *      the batches.

@@ -4,8 +4,9 @@ H is the Hamiltonian of Eq. Hamiltonian (Sec. 2.1) on the determinant list held 
 `sci.Hamiltonian`, built from h and either the dense (pq|rs) or Cholesky factors L^P with
 (pq|rs) = sum_P L^P_pq L^P_rs (real spin-orbital mode).  Forward: one sigma = H C.
 Backward, hand-written (the connections are recomputed by libsci's density-matrix walk,
-never stored), with G_k = grad_output_k / (c_k^T c_k) and the spin-summed density matrices
-gamma (n x n) and Gamma (n^4) of the weighted ensemble sum_k G_k |c_k><c_k|:
+never stored; the spin sums and the contraction with L run in libsci too, sci_rdm_grads),
+with G_k = grad_output_k / (c_k^T c_k) and the spin-summed density matrices gamma (n x n)
+and Gamma (n^4) of the weighted ensemble sum_k G_k |c_k><c_k|:
     dL/dh_pq        = gamma_pq                     (gamma_pq = sum_s g1[p s, q s])
     dL/d(pq|rs)     = 1/2 Gamma_pqrs               (Gamma_pqrs = sum_st g2[p s, q s, r t, s t])
     dL/dL^P_pq      = sum_rs Gamma_pqrs L^P_rs
@@ -19,21 +20,6 @@ from __future__ import annotations
 
 import numpy as np
 import torch
-
-
-def spin_sum_rdm(g1: torch.Tensor, g2: torch.Tensor | None, n: int):
-    """Spin-orbital (2n) -> spatial (n) density matrices: gamma[p,q] = sum_s g1[ps, qs],
-    Gamma[p,q,r,s] = sum_{s,t} g2[ps, qs, rt, st] (bit p < n is alpha p, bit n+p beta p)."""
-    g = g1.reshape(2, n, 2, n)
-    gamma = g[0, :, 0, :] + g[1, :, 1, :]
-    if g2 is None:
-        return gamma, None
-    G = g2.reshape(2, n, 2, n, 2, n, 2, n)
-    Gamma = torch.zeros((n, n, n, n), dtype=g2.dtype, device=g2.device)
-    for s in range(2):
-        for t in range(2):
-            Gamma += G[s, :, s, :, t, :, t, :]
-    return gamma, Gamma
 
 
 class _Energy(torch.autograd.Function):
@@ -62,17 +48,17 @@ class _Energy(torch.autograd.Function):
         need_h, need_L, need_C = ctx.needs_input_grad[0], ctx.needs_input_grad[1], ctx.needs_input_grad[2]
         gh = gL = gC = None
         if need_h or need_L:
-            g1, g2 = ham.rdm12(C, weights=G.cpu().numpy(), rdm2=need_L)
-            gamma, Gamma = spin_sum_rdm(g1, g2, n)
+            w = G.cpu().numpy()
+            if need_L and kind == "chol":
+                gamma, _, gL = ham.rdm_grads(C, weights=w, chol=L.detach().to(ham.device))
+            else:
+                gamma, Gamma, _ = ham.rdm_grads(C, weights=w, Gamma=need_L)
+                if need_L:
+                    gL = 0.5 * Gamma.to(L.device)
             if need_h:
                 gh = gamma.to(L.device)
-            if need_L:
-                Gamma = Gamma.to(L.device)
-                if kind == "chol":
-                    naux = L.shape[0]
-                    gL = (Gamma.reshape(n * n, n * n) @ L.reshape(naux, n * n).T).T.reshape(naux, n, n)
-                else:
-                    gL = 0.5 * Gamma
+            if gL is not None:
+                gL = gL.to(L.device)
         if need_C:
             gC = 2.0 * (S - C * E) * G
         return gh, gL, gC, None, None

@@ -25,6 +25,17 @@
 //          + sum_{pairs in holes} G + sum_{pairs in particles} G - sum_{holes x particles} G,
 // F the Fock diagonal of the reference and G_pq = (pp|qq) - (pq|qp): O(level^2) per I.
 // Element formulas and phases are those of the sigma kernels (bra I, ket J).
+//
+// Spinor mode (complex Hermitian integrals, no spin conservation; the 4C workloads of
+// Sec. 4): every single i -> a and double i < j -> a < b over the n <= 64 spinors.  The
+// batch code runs over the whole string, f(I) = XOR of g(o) over I's occupied spinors, so
+// the warp that owns J finds the excitations of batch b by lookups in the spinors grouped
+// by code:
+//   singles:  g(a) = b ^ f(J) ^ g(i)                         for each occupied i;
+//   doubles:  g(b') = b ^ f(J) ^ g(i) ^ g(j) ^ g(a), b' > a    for each occupied pair and
+//             first virtual a.
+// Numerators are complex (2 words per root in a slot) and a slot adds |num|^2 / (E0 - H_II);
+// E2[P] takes |<I|H|c> - c_I H_II|^2.
 #include <algorithm>
 #include <cstring>
 #include <random>
@@ -48,8 +59,8 @@ struct Pt2 {
     const double *tab, *fref, *g_so;
     const double *fdiag, *G;  // [norb], [norb][norb]
     const double *Eref;
-    uint32_t gcode[32];       // beta-orbital codes
-    uint8_t obc[32];          // the n beta orbitals sorted by code
+    uint32_t gcode[64];       // codes of the beta orbitals (spin-orbital mode) or spinors
+    uint8_t obc[64];          // those orbitals sorted by code
     uint8_t cstart[(1 << kMaxBits) + 1];  // first index in obc of each code
     uint64_t *tab2;           // slots of (key, value[R]) words, key 0 = empty
     uint64_t mask;            // capacity - 1
@@ -98,13 +109,14 @@ __device__ __forceinline__ double h_single(const Pt2 &p, uint64_t J, int i, int 
     return sflip(ph, f);
 }
 
-template <int R>
-__device__ __forceinline__ void insert(const Pt2 &p, uint64_t I, double hij, const double *cJ, double cmax)
+// The slot of key I in a table of (key, NW value words) slots, claimed if I is new; NULL
+// after kMaxProbe probes (the table is too full: flag bit 2).
+template <int NW>
+__device__ __forceinline__ uint64_t *claim(const Pt2 &p, uint64_t I)
 {
-    if (p.eps > 0.0 && fabs(hij) * cmax < p.eps) return;
     uint64_t s = mix64(I) & p.mask;
     for (int probe = 0; probe < kMaxProbe; probe++) {
-        uint64_t *slot = p.tab2 + s * (R + 1);
+        uint64_t *slot = p.tab2 + s * (NW + 1);
         uint64_t k = *slot;
         if (k == kEmpty) {
             k = atomicCAS(reinterpret_cast<unsigned long long *>(slot), (unsigned long long)kEmpty, (unsigned long long)I);
@@ -113,14 +125,21 @@ __device__ __forceinline__ void insert(const Pt2 &p, uint64_t I, double hij, con
                 k = I;
             }
         }
-        if (k == I) {   // the value words share the key's sector
-#pragma unroll
-            for (int v = 0; v < R; v++) atomicAdd(reinterpret_cast<double *>(slot + 1 + v), hij * cJ[v]);
-            return;
-        }
+        if (k == I) return slot;   // the value words share the key's sector
         s = (s + 1) & p.mask;
     }
     atomicOr(p.flag, 2);  // probe limit: the table is too full
+    return nullptr;
+}
+
+template <int R>
+__device__ __forceinline__ void insert(const Pt2 &p, uint64_t I, double hij, const double *cJ, double cmax)
+{
+    if (p.eps > 0.0 && fabs(hij) * cmax < p.eps) return;
+    uint64_t *slot = claim<R>(p, I);
+    if (!slot) return;
+#pragma unroll
+    for (int v = 0; v < R; v++) atomicAdd(reinterpret_cast<double *>(slot + 1 + v), hij * cJ[v]);
 }
 
 __device__ __forceinline__ uint32_t code_of(const uint32_t *g, uint32_t s)
@@ -233,14 +252,152 @@ k_pt2_gen(const uint64_t *__restrict__ Pkeys, int64_t M, const double *__restric
     }
 }
 
+
+// ------------------------------------------------------------------ spinor mode
+using sci::zdbl;
+
+__device__ __forceinline__ zdbl ldz(const zdbl *p)
+{
+    const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+    return zdbl{v.x, v.y};
+}
+
+// H_IJ (spinors) for I = J - {i, j} + {a, b}: the antisymmetrised table entry of the bra
+// pair (a, b) and the ket pair (i, j), with the phase of the sigma kernels
+__device__ __forceinline__ zdbl hz_double(const Pt2 &p, uint64_t J, int i, int j, int a, int b)
+{
+    const uint64_t K = J & ~(1ull << i) & ~(1ull << j);
+    uint32_t rowoff, colbase, r2, c2;
+    const sci::TabRule tr{1, p.n};
+    sci::pair_offsets(tr, a, b, rowoff, r2);
+    sci::pair_offsets(tr, i, j, c2, colbase);
+    const bool ph = (below(K, a) + below(K, b) + below(K, i) + below(K, j)) & 1;
+    return sflip(ph, ldz(reinterpret_cast<const zdbl *>(p.tab) + rowoff + colbase));
+}
+
+// H_IJ (spinors) for I = J - {i} + {a}: F^ref_ai plus the terms of the spinors where
+// S = J - {i} and the reference differ
+__device__ __forceinline__ zdbl hz_single(const Pt2 &p, uint64_t J, int i, int a)
+{
+    const uint64_t S = J & ~(1ull << i);
+    const int norb = p.norb;
+    const zdbl *fref = reinterpret_cast<const zdbl *>(p.fref), *g = reinterpret_cast<const zdbl *>(p.g_so);
+    zdbl f = ldz(fref + i * norb + a);
+    const uint64_t part = S & ~p.ref, holes = p.ref & ~S;
+    for (uint64_t m = part; m; m &= m - 1) {
+        const zdbl t = ldz(g + ((int64_t)(__ffsll((long long)m) - 1) * norb + i) * norb + a);
+        f.x += t.x, f.y += t.y;
+    }
+    for (uint64_t m = holes; m; m &= m - 1) {
+        const zdbl t = ldz(g + ((int64_t)(__ffsll((long long)m) - 1) * norb + i) * norb + a);
+        f.x -= t.x, f.y -= t.y;
+    }
+    const bool ph = (below(S, a) + below(S, i)) & 1;
+    return sflip(ph, f);
+}
+
+template <int R>
+__device__ __forceinline__ void insert_z(const Pt2 &p, uint64_t I, zdbl h, const zdbl *cJ, double cmax)
+{
+    if (p.eps > 0.0 && sqrt(h.x * h.x + h.y * h.y) * cmax < p.eps) return;
+    uint64_t *slot = claim<2 * R>(p, I);
+    if (!slot) return;
+    double *val = reinterpret_cast<double *>(slot + 1);
+#pragma unroll
+    for (int v = 0; v < R; v++) {
+        atomicAdd(val + 2 * v, h.x * cJ[v].x - h.y * cJ[v].y);
+        atomicAdd(val + 2 * v + 1, h.x * cJ[v].y + h.y * cJ[v].x);
+    }
+}
+
+__device__ __forceinline__ uint32_t code_of64(const uint32_t *g, uint64_t s)
+{
+    uint32_t c = 0;
+    for (; s; s &= s - 1) c ^= g[__ffsll((long long)s) - 1];
+    return c;
+}
+
+// pairs x < y of at most 64 spinors, P = y(y-1)/2 + x  ->  x | y << 8
+constexpr int kMaxPairs64 = 64 * 63 / 2;
+
+// warp per determinant J of P: the excitations of J (spinors) that fall in batch `batch`
+template <int R>
+__global__ void __launch_bounds__(kThreads)
+k_pt2_gen_z(const uint64_t *__restrict__ Pkeys, int64_t M, const zdbl *__restrict__ C, Pt2 p, uint32_t batch, int tbits)
+{
+    __shared__ uint8_t s_orb[kWarps][128];       // occupied spinors | virtual spinors (+ 64)
+    __shared__ uint16_t s_pair[kMaxPairs64];     // P -> (x, y)
+    __shared__ uint8_t s_cstart[(1 << kMaxBits) + 1];
+    __shared__ uint8_t s_obc[64];                // spinors sorted by code
+    __shared__ uint32_t s_g[64];                 // spinor codes
+    for (int P = threadIdx.x; P < kMaxPairs64; P += blockDim.x) {
+        int y = 1;
+        while ((y + 1) * y / 2 <= P) y++;
+        s_pair[P] = (uint16_t)((P - y * (y - 1) / 2) | (y << 8));
+    }
+    for (int c = threadIdx.x; c <= (1 << tbits); c += blockDim.x) s_cstart[c] = p.cstart[c];
+    if (threadIdx.x < 64) s_obc[threadIdx.x] = p.obc[threadIdx.x], s_g[threadIdx.x] = p.gcode[threadIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint8_t *orb = s_orb[w];
+    const int n = p.n, N = p.na, nv = n - N;
+    const uint64_t full = n == 64 ? ~0ull : ((1ull << n) - 1);
+    const int npairs = N * (N - 1) / 2;
+    const int64_t warps_total = (int64_t)gridDim.x * kWarps;
+    for (int64_t J = (int64_t)blockIdx.x * kWarps + w; J < M; J += warps_total) {
+        const uint64_t key = Pkeys[J];
+        const uint64_t vir = full & ~key;
+        zdbl cJ[R];
+        double cmax = 0.0;
+#pragma unroll
+        for (int v = 0; v < R; v++) {
+            cJ[v] = C[J * R + v];
+            cmax = fmax(cmax, sqrt(cJ[v].x * cJ[v].x + cJ[v].y * cJ[v].y));
+        }
+        __syncwarp();
+        for (int o = lane; o < n; o += 32) {
+            const uint64_t lm = (1ull << o) - 1;
+            if ((key >> o) & 1) orb[__popcll(key & lm)] = (uint8_t)o;
+            else orb[64 + __popcll(vir & lm)] = (uint8_t)o;
+        }
+        __syncwarp();
+        const uint32_t target = batch ^ code_of64(s_g, key);
+        // singles i -> a of this batch: g(a) = target ^ g(i)
+        for (int x = lane; x < N; x += 32) {
+            const int i = orb[x];
+            const uint32_t c = target ^ s_g[i];
+            for (int q = s_cstart[c]; q < s_cstart[c + 1]; q++) {
+                const int a = s_obc[q];
+                if ((key >> a) & 1) continue;
+                insert_z<R>(p, (key & ~(1ull << i)) | (1ull << a), hz_single(p, key, i, a), cJ, cmax);
+            }
+        }
+        // doubles i < j -> a < b: for each occupied pair and first virtual a, the second
+        // virtual has code target ^ g(i) ^ g(j) ^ g(a)
+        for (int t = lane; t < npairs * nv; t += 32) {
+            const uint16_t po = s_pair[t / nv];
+            const int i = orb[po & 0xFF], j = orb[po >> 8], a = orb[64 + t % nv];
+            const uint32_t c = target ^ s_g[i] ^ s_g[j] ^ s_g[a];
+            for (int q = s_cstart[c]; q < s_cstart[c + 1]; q++) {
+                const int b = s_obc[q];
+                if (b <= a || ((key >> b) & 1)) continue;
+                const uint64_t I = (key & ~(1ull << i) & ~(1ull << j)) | (1ull << a) | (1ull << b);
+                insert_z<R>(p, I, hz_double(p, key, i, j, a, b), cJ, cmax);
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // sum over the table entries of num^2 / (E0 - H_II).  Each warp packs the occupied slots
 // it scans into a buffer of 32 and evaluates full buffers, so every lane works; H_II
 // (E_ref plus O(level^2) table terms) is summed in paired FP32 from split copies of F and
 // G in shared memory, and added to E_ref in FP64.
-template <int R>
+template <int R, bool CPLX>
 __global__ void __launch_bounds__(kThreads)
 k_pt2_eval(Pt2 p, uint64_t cap, const double *__restrict__ E0, double *__restrict__ out)
 {
+    constexpr int NW = CPLX ? 2 * R : R;   // value words per slot
     __shared__ float2 sG[64 * 64];
     __shared__ float2 sF[64];
     __shared__ uint64_t sbuf[kWarps][64];
@@ -255,7 +412,7 @@ k_pt2_eval(Pt2 p, uint64_t cap, const double *__restrict__ E0, double *__restric
 #pragma unroll
     for (int v = 0; v < R; v++) acc[v] = 0.0, e0[v] = E0[v];
     auto evaluate = [&](uint64_t s) {
-        const uint64_t *slot = p.tab2 + s * (R + 1);
+        const uint64_t *slot = p.tab2 + s * (NW + 1);
         const uint64_t I = slot[0];
         const uint64_t H = p.ref & ~I, Pm = I & ~p.ref;
         sci::Ds e;
@@ -278,15 +435,23 @@ k_pt2_eval(Pt2 p, uint64_t cap, const double *__restrict__ E0, double *__restric
         const double hii = Eref + sci::ds_value(e);
 #pragma unroll
         for (int v = 0; v < R; v++) {
-            const double num = __longlong_as_double((long long)slot[1 + v]);
-            acc[v] += num * num / (e0[v] - hii);
+            double num2;
+            if constexpr (CPLX) {
+                const double re = __longlong_as_double((long long)slot[1 + 2 * v]);
+                const double im = __longlong_as_double((long long)slot[2 + 2 * v]);
+                num2 = re * re + im * im;
+            } else {
+                const double num = __longlong_as_double((long long)slot[1 + v]);
+                num2 = num * num;
+            }
+            acc[v] += num2 / (e0[v] - hii);
         }
     };
     int nbuf = 0;  // occupied slots waiting in this warp's buffer (warp-uniform)
     const uint64_t stride = (uint64_t)gridDim.x * kThreads;
     for (uint64_t s0 = (uint64_t)blockIdx.x * kThreads + (uint64_t)w * 32; s0 < cap; s0 += stride) {
         const uint64_t s = s0 + lane;
-        const bool occ = s < cap && p.tab2[s * (R + 1)] != kEmpty;
+        const bool occ = s < cap && p.tab2[s * (NW + 1)] != kEmpty;
         const unsigned m = __ballot_sync(0xffffffffu, occ);
         if (occ) sbuf[w][nbuf + __popc(m & ((1u << lane) - 1))] = s;
         nbuf += __popc(m);
@@ -315,9 +480,16 @@ k_pt2_eval(Pt2 p, uint64_t cap, const double *__restrict__ E0, double *__restric
 }
 
 // E2[P] of Eq. EP1 from sigma = H c and the diagonal
-template <int R>
+__device__ __forceinline__ double abs2_minus(double s, double c, double d) { const double x = s - c * d; return x * x; }
+__device__ __forceinline__ double abs2_minus(zdbl s, zdbl c, double d)
+{
+    const double x = s.x - c.x * d, y = s.y - c.y * d;
+    return x * x + y * y;
+}
+
+template <int R, typename T>
 __global__ void __launch_bounds__(kThreads)
-k_pt2_p(int64_t M, const double *__restrict__ C, const double *__restrict__ S, const double *__restrict__ hdiag,
+k_pt2_p(int64_t M, const T *__restrict__ C, const T *__restrict__ S, const double *__restrict__ hdiag,
         const double *__restrict__ E0, double *__restrict__ out)
 {
     __shared__ double red[kWarps][R];
@@ -327,10 +499,7 @@ k_pt2_p(int64_t M, const double *__restrict__ C, const double *__restrict__ S, c
     for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < M; I += (int64_t)gridDim.x * blockDim.x) {
         const double d = hdiag[I];
 #pragma unroll
-        for (int v = 0; v < R; v++) {
-            const double num = S[I * R + v] - C[I * R + v] * d;
-            acc[v] += num * num / (E0[v] - d);
-        }
+        for (int v = 0; v < R; v++) acc[v] += abs2_minus(S[I * R + v], C[I * R + v], d) / (E0[v] - d);
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -347,18 +516,23 @@ k_pt2_p(int64_t M, const double *__restrict__ C, const double *__restrict__ S, c
     }
 }
 
-// G = (pp|qq) - (pq|qp) without the diagonal, the reference Fock diagonal and E_ref
-__global__ void k_pt2_setup(int norb, uint64_t ref, const double *__restrict__ h_so, const double *__restrict__ jd,
-                            const double *__restrict__ kd, double *__restrict__ G, double *__restrict__ fdiag,
+// G = (pp|qq) - (pq|qp) without the diagonal, the reference Fock diagonal and E_ref (real:
+// for Hermitian integrals (pp|qq), (pq|qp) and h_pp are real, the imaginary parts zero)
+__device__ __forceinline__ double re_of(double a) { return a; }
+__device__ __forceinline__ double re_of(zdbl a) { return a.x; }
+
+template <typename T>
+__global__ void k_pt2_setup(int norb, uint64_t ref, const T *__restrict__ h_so, const T *__restrict__ jd,
+                            const T *__restrict__ kd, double *__restrict__ G, double *__restrict__ fdiag,
                             double *__restrict__ Eref)
 {
     for (int t = threadIdx.x; t < norb * norb; t += blockDim.x) {
         const int a = t / norb, b = t % norb;
-        G[t] = a == b ? 0.0 : jd[t] - kd[t];
+        G[t] = a == b ? 0.0 : re_of(jd[t]) - re_of(kd[t]);
     }
     __syncthreads();
     for (int a = threadIdx.x; a < norb; a += blockDim.x) {
-        double f = h_so[a * norb + a];
+        double f = re_of(h_so[a * norb + a]);
         for (uint64_t m = ref; m; m &= m - 1) f += G[a * norb + __ffsll((long long)m) - 1];
         fdiag[a] = f;
     }
@@ -366,7 +540,7 @@ __global__ void k_pt2_setup(int norb, uint64_t ref, const double *__restrict__ h
         double e = 0.0;
         for (uint64_t m = ref; m; m &= m - 1) {
             const int i = __ffsll((long long)m) - 1;
-            e += h_so[i * norb + i];
+            e += re_of(h_so[i * norb + i]);
             for (uint64_t m2 = m & (m - 1); m2; m2 &= m2 - 1) e += G[i * norb + __ffsll((long long)m2) - 1];
         }
         *Eref = e;
@@ -378,9 +552,12 @@ int grid_for(int64_t n)
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, 152 * 8));
 }
 
-template <int R>
+// SPIN: complex spinor mode (C is [M][R] complex128); otherwise real spin-orbital mode
+template <int R, bool SPIN>
 int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t table_bytes, double *E2, int64_t *stats)
 {
+    constexpr int NW = SPIN ? 2 * R : R;   // value words per table slot
+    constexpr int SC = SPIN ? 2 : 1;       // doubles per coefficient
     const int64_t M = ctx->M;
     const int n = ctx->n, norb = ctx->norb, na = ctx->na, nb = ctx->nb;
     cudaStream_t st = ctx->stream;
@@ -394,7 +571,7 @@ int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t
         if (tab2) cudaFree(tab2);
     };
     const size_t nsmall = (size_t)R * 3 + (size_t)norb * norb + norb + 1 + 2;
-    if (cudaMalloc(&S, sizeof(double) * std::max<int64_t>(1, M) * R) != cudaSuccess ||
+    if (cudaMalloc(&S, sizeof(double) * SC * std::max<int64_t>(1, M) * R) != cudaSuccess ||
         cudaMalloc(&small, sizeof(double) * nsmall) != cudaSuccess) {
         cleanup();
         return sci_fail(ctx, SCI_ERR_NOMEM, "enpt2: scratch");
@@ -415,12 +592,20 @@ int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t
             cleanup();
             return rc;
         }
-        k_pt2_p<R><<<grid_for(M), kThreads, 0, st>>>(M, C, S, ctx->hdiag, dE0, outP);
+        if constexpr (SPIN)
+            k_pt2_p<R, zdbl><<<grid_for(M), kThreads, 0, st>>>(M, reinterpret_cast<const zdbl *>(C),
+                                                               reinterpret_cast<const zdbl *>(S), ctx->hdiag, dE0, outP);
+        else
+            k_pt2_p<R, double><<<grid_for(M), kThreads, 0, st>>>(M, C, S, ctx->hdiag, dE0, outP);
     }
-    k_pt2_setup<<<1, 256, 0, st>>>(norb, ctx->ref, (const double *)ctx->h_so, (const double *)ctx->jd,
-                                    (const double *)ctx->kd, G, fdiag, Eref);
+    if constexpr (SPIN)
+        k_pt2_setup<zdbl><<<1, 256, 0, st>>>(norb, ctx->ref, (const zdbl *)ctx->h_so, (const zdbl *)ctx->jd,
+                                             (const zdbl *)ctx->kd, G, fdiag, Eref);
+    else
+        k_pt2_setup<double><<<1, 256, 0, st>>>(norb, ctx->ref, (const double *)ctx->h_so, (const double *)ctx->jd,
+                                               (const double *)ctx->kd, G, fdiag, Eref);
     // the table: capacity a power of two within the budget
-    const size_t slot = sizeof(uint64_t) + sizeof(double) * R;
+    const size_t slot = sizeof(uint64_t) + sizeof(double) * NW;
     uint64_t cap = 1ull << 8;  // at least 256 entries
     while ((cap << 1) * slot <= table_bytes) cap <<= 1;
     if (cudaMalloc(&tab2, cap * slot) != cudaSuccess) {
@@ -429,9 +614,15 @@ int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t
     }
     // batches: the generated excitations (an upper bound on the distinct determinants)
     // split so that one batch fills at most 60% of the table
-    const int64_t ua = n - na, ub = n - nb;
-    const int64_t per = na * ua + nb * ub + (int64_t)na * (na - 1) / 2 * (ua * (ua - 1) / 2) +
-                        (int64_t)nb * (nb - 1) / 2 * (ub * (ub - 1) / 2) + (int64_t)na * ua * nb * ub;
+    int64_t per;  // excitations generated per determinant
+    if constexpr (SPIN) {
+        const int64_t N = na, u = n - na;
+        per = N * u + N * (N - 1) / 2 * (u * (u - 1) / 2);
+    } else {
+        const int64_t ua = n - na, ub = n - nb;
+        per = na * ua + nb * ub + (int64_t)na * (na - 1) / 2 * (ua * (ua - 1) / 2) +
+              (int64_t)nb * (nb - 1) / 2 * (ub * (ub - 1) / 2) + (int64_t)na * ua * nb * ub;
+    }
     const double total = (double)M * (double)per;
     // (at most 1024 batches: when even that bound does not fit, the distinct count decides,
     // and a batch that overflows the table ends with SCI_ERR_OVERFLOW)
@@ -458,10 +649,11 @@ int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t
         cleanup();
         return code;
     };
-    // the batch code: t random bits per beta orbital, and the orbitals grouped by code
+    // the batch code: t random bits per beta orbital (spinor mode: per spinor), and the
+    // orbitals grouped by code
     auto set_codes = [&](int t) {
         std::mt19937 rng(20250130u + (unsigned)t);
-        for (int o = 0; o < 32; o++) p.gcode[o] = t ? (uint32_t)(rng() & ((1u << t) - 1)) : 0u;
+        for (int o = 0; o < 64; o++) p.gcode[o] = t ? (uint32_t)(rng() & ((1u << t) - 1)) : 0u;
         std::vector<int> cnt((1 << t) + 1, 0);
         for (int o = 0; o < n; o++) cnt[p.gcode[o] + 1]++;
         for (int c = 1; c <= (1 << t); c++) cnt[c] += cnt[c - 1];
@@ -477,12 +669,17 @@ int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t
             sci_cuda_check(ctx, cudaMemsetAsync(count, 0, sizeof(unsigned long long) + sizeof(int) * 2, st), "enpt2 count") ||
             sci_cuda_check(ctx, cudaEventRecord(ev[1], st), "enpt2 event"))
             return SCI_ERR_CUDA;
-        if (M > 0)
-            k_pt2_gen<R><<<(unsigned)std::min<int64_t>((M + kWarps - 1) / kWarps, 152 * 16), kThreads, 0, st>>>(
-                ctx->keys, M, C, p, b, t);
+        if (M > 0) {
+            const unsigned blocks = (unsigned)std::min<int64_t>((M + kWarps - 1) / kWarps, 152 * 16);
+            if constexpr (SPIN)
+                k_pt2_gen_z<R><<<blocks, kThreads, 0, st>>>(ctx->keys, M, reinterpret_cast<const zdbl *>(C), p, b, t);
+            else
+                k_pt2_gen<R><<<blocks, kThreads, 0, st>>>(ctx->keys, M, C, p, b, t);
+        }
         if (sci_cuda_check(ctx, cudaEventRecord(ev[2], st), "enpt2 event")) return SCI_ERR_CUDA;
         if (eval)
-            k_pt2_eval<R><<<grid_for((int64_t)std::min<uint64_t>(cap, 1ull << 40)), kThreads, 0, st>>>(p, cap, dE0, outW);
+            k_pt2_eval<R, SPIN><<<grid_for((int64_t)std::min<uint64_t>(cap, 1ull << 40)), kThreads, 0, st>>>(p, cap, dE0,
+                                                                                                          outW);
         unsigned long long hc[2] = {0, 0};
         if (sci_cuda_check(ctx, cudaEventRecord(ev[3], st), "enpt2 event") ||
             sci_cuda_check(ctx, cudaMemcpyAsync(hc, count, sizeof(hc), cudaMemcpyDeviceToHost, st), "enpt2 flag") ||
@@ -561,19 +758,32 @@ extern "C" int sci_enpt2(sci_ctx *ctx, const double *C, int nroots, const double
 {
     if (!ctx) return SCI_ERR_ARG;
     if (!ctx->have_ints || !ctx->have_dets) return sci_fail(ctx, SCI_ERR_STATE, "enpt2: integrals and determinants first");
-    if (ctx->cplx || ctx->spinors) return sci_fail(ctx, SCI_ERR_ARG, "enpt2: real spin-orbital mode only");
+    if (ctx->spinors != ctx->cplx)
+        return sci_fail(ctx, SCI_ERR_ARG, "enpt2: real spin-orbital mode or complex spinor mode");
     if (nroots < 1 || nroots > 8 || !E0 || !E2 || (ctx->M > 0 && !C))
         return sci_fail(ctx, SCI_ERR_ARG, "enpt2: need 1 <= nroots <= 8, C, E0 and E2");
     if (eps < 0.0) return sci_fail(ctx, SCI_ERR_ARG, "enpt2: eps < 0");
     if (sci_cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) return SCI_ERR_CUDA;
+    if (ctx->spinors) {
+        switch (nroots) {
+            case 1: return pt2_run<1, true>(ctx, C, E0, eps, table_bytes, E2, stats);
+            case 2: return pt2_run<2, true>(ctx, C, E0, eps, table_bytes, E2, stats);
+            case 3: return pt2_run<3, true>(ctx, C, E0, eps, table_bytes, E2, stats);
+            case 4: return pt2_run<4, true>(ctx, C, E0, eps, table_bytes, E2, stats);
+            case 5: return pt2_run<5, true>(ctx, C, E0, eps, table_bytes, E2, stats);
+            case 6: return pt2_run<6, true>(ctx, C, E0, eps, table_bytes, E2, stats);
+            case 7: return pt2_run<7, true>(ctx, C, E0, eps, table_bytes, E2, stats);
+            default: return pt2_run<8, true>(ctx, C, E0, eps, table_bytes, E2, stats);
+        }
+    }
     switch (nroots) {
-        case 1: return pt2_run<1>(ctx, C, E0, eps, table_bytes, E2, stats);
-        case 2: return pt2_run<2>(ctx, C, E0, eps, table_bytes, E2, stats);
-        case 3: return pt2_run<3>(ctx, C, E0, eps, table_bytes, E2, stats);
-        case 4: return pt2_run<4>(ctx, C, E0, eps, table_bytes, E2, stats);
-        case 5: return pt2_run<5>(ctx, C, E0, eps, table_bytes, E2, stats);
-        case 6: return pt2_run<6>(ctx, C, E0, eps, table_bytes, E2, stats);
-        case 7: return pt2_run<7>(ctx, C, E0, eps, table_bytes, E2, stats);
-        default: return pt2_run<8>(ctx, C, E0, eps, table_bytes, E2, stats);
+        case 1: return pt2_run<1, false>(ctx, C, E0, eps, table_bytes, E2, stats);
+        case 2: return pt2_run<2, false>(ctx, C, E0, eps, table_bytes, E2, stats);
+        case 3: return pt2_run<3, false>(ctx, C, E0, eps, table_bytes, E2, stats);
+        case 4: return pt2_run<4, false>(ctx, C, E0, eps, table_bytes, E2, stats);
+        case 5: return pt2_run<5, false>(ctx, C, E0, eps, table_bytes, E2, stats);
+        case 6: return pt2_run<6, false>(ctx, C, E0, eps, table_bytes, E2, stats);
+        case 7: return pt2_run<7, false>(ctx, C, E0, eps, table_bytes, E2, stats);
+        default: return pt2_run<8, false>(ctx, C, E0, eps, table_bytes, E2, stats);
     }
 }

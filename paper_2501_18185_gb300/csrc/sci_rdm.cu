@@ -395,7 +395,110 @@ int rdm_run(sci_ctx *ctx, const TC *C, int nvec, const double *wk_dev, TC *g1, T
     return sci_cuda_check(ctx, cudaGetLastError(), "rdm12 launch") ? SCI_ERR_CUDA : SCI_OK;
 }
 
+// ------------------------------------------------------------------ gradients of E
+// Spin sums of the spin-orbital density matrices (bit p < n alpha p, bit n + p beta p):
+//   gamma[p][q]        = sum_s g1[ps][qs]
+//   Gamma[p][q][r][s]  = sum_{s1,s2} g2[p s1][q s1][r s2][s s2]
+__global__ void k_spin_sum1(int n, const double *__restrict__ g1, double *__restrict__ gamma)
+{
+    const int norb = 2 * n;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * n; t += gridDim.x * blockDim.x) {
+        const int p = t / n, q = t % n;
+        gamma[t] = g1[p * norb + q] + g1[(n + p) * norb + n + q];
+    }
+}
+
+__global__ void k_spin_sum2(int n, const double *__restrict__ g2, double *__restrict__ Gamma)
+{
+    const int64_t norb = 2 * n, n4 = (int64_t)n * n * n * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n4; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = t % n, r = (t / n) % n, q = (t / n / n) % n, p = t / n / n / n;
+        double v = 0.0;
+        for (int a = 0; a < 2; a++)
+            for (int b = 0; b < 2; b++)
+                v += g2[(((p + a * n) * norb + q + a * n) * norb + r + b * n) * norb + s + b * n];
+        Gamma[t] = v;
+    }
+}
+
+// gL[P][i] = sum_k Gamma[i][k] L[P][k] for i, k < n^2 (the chain rule of
+// (pq|rs) = sum_P L^P_pq L^P_rs through the free entries of L^P, with Gamma symmetric in
+// its two index pairs): a 64 x 32 output tile per CTA, k in steps of 16 staged in shared
+// memory, 8 outputs per thread, FP64 FMA
+constexpr int kGI = 64, kGP = 32, kGK = 16;
+__global__ void __launch_bounds__(256) k_gamma_chol(int nn, int naux, const double *__restrict__ Gamma,
+                                                     const double *__restrict__ L, double *__restrict__ gL)
+{
+    __shared__ double sG[kGK][kGI + 1];
+    __shared__ double sL[kGK][kGP + 1];
+    const int i0 = blockIdx.x * kGI, P0 = blockIdx.y * kGP;
+    const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;   // P = P0 + tx, i = i0 + ty + 8 u
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int k0 = 0; k0 < nn; k0 += kGK) {
+        for (int t = threadIdx.x; t < kGK * kGI; t += blockDim.x) {
+            const int kk = t % kGK, ii = t / kGK;
+            const int i = i0 + ii, k = k0 + kk;
+            sG[kk][ii] = (i < nn && k < nn) ? Gamma[(int64_t)i * nn + k] : 0.0;
+        }
+        for (int t = threadIdx.x; t < kGK * kGP; t += blockDim.x) {
+            const int kk = t % kGK, pp = t / kGK;
+            const int P = P0 + pp, k = k0 + kk;
+            sL[kk][pp] = (P < naux && k < nn) ? L[(int64_t)P * nn + k] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kGK; kk++) {
+            const double l = sL[kk][tx];
+#pragma unroll
+            for (int u = 0; u < 8; u++) acc[u] = fma(sG[kk][ty + 8 * u], l, acc[u]);
+        }
+        __syncthreads();
+    }
+    const int P = P0 + tx;
+    if (P < naux)
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int i = i0 + ty + 8 * u;
+            if (i < nn) gL[(int64_t)P * nn + i] = acc[u];
+        }
+}
+
 }  // namespace
+
+extern "C" int sci_rdm_grads(sci_ctx *ctx, const double *C, int nvec, const double *weights, double *gamma,
+                             double *Gamma, int naux, const double *chol, double *gchol)
+{
+    if (!ctx) return SCI_ERR_ARG;
+    if (!ctx->have_ints || !ctx->have_dets) return sci_fail(ctx, SCI_ERR_STATE, "rdm_grads: integrals and determinants first");
+    if (ctx->cplx || ctx->spinors) return sci_fail(ctx, SCI_ERR_ARG, "rdm_grads: real spin-orbital mode only");
+    if (nvec < 1 || (ctx->M > 0 && !C)) return sci_fail(ctx, SCI_ERR_ARG, "rdm_grads: need nvec >= 1 and C");
+    if ((chol == nullptr) != (gchol == nullptr) || (chol && naux < 1))
+        return sci_fail(ctx, SCI_ERR_ARG, "rdm_grads: chol and gchol go together, naux >= 1");
+    if (sci_cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) return SCI_ERR_CUDA;
+    const int n = ctx->n, norb = ctx->norb;
+    const int64_t nn = (int64_t)n * n, n4 = nn * nn, o2 = (int64_t)norb * norb, o4 = o2 * o2;
+    const bool two = Gamma || chol;
+    // spin-orbital g1, g2 and (when the caller passes no Gamma but needs the contraction)
+    // the spin-summed Gamma, in a buffer of their own
+    double *buf = nullptr;
+    const size_t need = sizeof(double) * (o2 + (two ? o4 : 0) + (two && !Gamma ? n4 : 0));
+    if (cudaMalloc(&buf, need) != cudaSuccess) return sci_fail(ctx, SCI_ERR_NOMEM, "rdm_grads: scratch");
+    double *g1 = buf, *g2 = two ? buf + o2 : nullptr, *G = Gamma ? Gamma : (two ? buf + o2 + o4 : nullptr);
+    int rc = sci_rdm12(ctx, C, nvec, weights, g1, g2);
+    cudaStream_t st = ctx->stream;
+    if (rc == SCI_OK && gamma) k_spin_sum1<<<grid_for(nn), kThreads, 0, st>>>(n, g1, gamma);
+    if (rc == SCI_OK && two) k_spin_sum2<<<grid_for(n4), kThreads, 0, st>>>(n, g2, G);
+    if (rc == SCI_OK && chol) {
+        const dim3 grid((unsigned)((nn + kGI - 1) / kGI), (unsigned)((naux + kGP - 1) / kGP));
+        k_gamma_chol<<<grid, 256, 0, st>>>((int)nn, naux, G, chol, gchol);
+    }
+    if (rc == SCI_OK) rc = sci_cuda_check(ctx, cudaGetLastError(), "rdm_grads launch");
+    // the buffer is freed after the queued work has read it
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaFree(buf);
+    if (rc == SCI_OK) rc = sci_cuda_check(ctx, e, "rdm_grads");
+    return rc;
+}
 
 extern "C" int sci_rdm12(sci_ctx *ctx, const void *C, int nvec, const double *weights, void *rdm1, void *rdm2)
 {

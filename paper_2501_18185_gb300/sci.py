@@ -50,6 +50,7 @@ SIGNATURES = {
     "sci_profile": (_i32, [_vp, _i32]),
     "sci_kernel_times": (_i32, [_vp, _vp, _i32]),
     "sci_rdm12": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp]),
+    "sci_rdm_grads": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp, _i32, _vp, _vp]),
     "sci_enpt2": (_i32, [_vp, _vp, _i32, _vp, ctypes.c_double, ctypes.c_size_t, _vp, _vp]),
     "sci_batch_create": (_i32, [ctypes.POINTER(_vp), _i32, _vp]),
     "sci_batch_destroy": (_i32, [_vp]),
@@ -223,6 +224,12 @@ def sci_kernel_times(ctx) -> list:
 def sci_rdm12(ctx, C, nvec, weights, rdm1, rdm2):
     w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
     return _check(ctx, load().sci_rdm12(ctx, _p(C), nvec, _p(w), _p(rdm1), _p(rdm2)))
+
+
+def sci_rdm_grads(ctx, C, nvec, weights, gamma, Gamma, naux, chol, gchol):
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    return _check(ctx, load().sci_rdm_grads(ctx, _p(C), nvec, _p(w), _p(gamma), _p(Gamma), int(naux), _p(chol),
+                                            _p(gchol)))
 
 
 def sci_enpt2(ctx, C, nroots, E0, eps=0.0, table_bytes=1 << 30):
@@ -514,10 +521,32 @@ class Hamiltonian:
         sci_rdm12(self.ctx, C2, C2.shape[1], weights, g1, g2)
         return g1, g2
 
-    def enpt2(self, C, E0, eps: float = 0.0, table_bytes: int = 1 << 30):
-        """Epstein-Nesbet second-order energies of the columns of C ([M, nroots] float64
-        CUDA) with zeroth-order energies E0: (E2[W], E2[P], E2[Q], stats) -- see sci_enpt2."""
+    def rdm_grads(self, C, weights=None, chol=None, Gamma: bool = False):
+        """(gamma [n, n], Gamma [n]^4 or None, gchol [naux, n, n] or None): the spin-summed
+        1-RDM, optionally the spin-summed 2-RDM, and sum_rs Gamma_pqrs chol[P, r, s] for
+        Cholesky factors `chol` (float64 CUDA) -- see sci_rdm_grads."""
+        torch = self.torch
         C2 = (C.reshape(-1, 1) if C.dim() == 1 else C).contiguous()
+        if C2.dtype != torch.float64 or self.complex:
+            raise ValueError("rdm_grads: real spin-orbital Hamiltonians, float64 C")
+        n = self.n
+        gam = torch.empty((n, n), dtype=torch.float64, device=self.device)
+        G = torch.empty((n, n, n, n), dtype=torch.float64, device=self.device) if Gamma else None
+        gL = None
+        if chol is not None:
+            chol = chol.contiguous()
+            gL = torch.empty_like(chol)
+        sci_rdm_grads(self.ctx, C2, C2.shape[1], weights, gam, G, 0 if chol is None else chol.shape[0], chol, gL)
+        return gam, G, gL
+
+    def enpt2(self, C, E0, eps: float = 0.0, table_bytes: int = 1 << 30):
+        """Epstein-Nesbet second-order energies of the columns of C ([M, nroots] CUDA,
+        float64 for a real spin-orbital Hamiltonian, complex128 for a complex spinor one)
+        with zeroth-order energies E0: (E2[W], E2[P], E2[Q], stats) -- see sci_enpt2."""
+        C2 = (C.reshape(-1, 1) if C.dim() == 1 else C).contiguous()
+        want = self.torch.complex128 if self.complex else self.torch.float64
+        if C2.dtype != want or not C2.is_cuda or (self.M and C2.shape[0] != self.M):
+            raise ValueError(f"C must be a [M, nroots] {want} CUDA tensor for this Hamiltonian")
         return sci_enpt2(self.ctx, C2, C2.shape[1], E0, eps, table_bytes)
 
     def connections(self, row_begin: int = 0, row_end: int | None = None):

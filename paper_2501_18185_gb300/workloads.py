@@ -314,6 +314,25 @@ def selected_30o_cut(M: int = 1000, seed: int = 7) -> Workload:
     return w
 
 
+def selected_spinor_64_cut(n1: int = 200, n2: int = 60, n3: int = 40, seed: int = 9) -> Workload:
+    """A small selected space of the 64-spinor recipe, for checks against slow routes: the
+    integrals of selected_spinor_64() and, from its 120,000-determinant space, HF plus n1
+    singles, n2 doubles and n3 triples drawn uniformly without replacement (rng seeded by
+    `seed`), sorted; complex c with |c| = exp(-level) and random phases, normalised."""
+    base = selected_spinor_64(M=120000)
+    hf = base.hf_key()
+    lev = excitation_level(base.keys, hf)
+    rng = np.random.default_rng(seed)
+    keep = [np.flatnonzero(lev == 0)]
+    for level, cnt in ((1, n1), (2, n2), (3, n3)):
+        keep.append(rng.choice(np.flatnonzero(lev == level), cnt, replace=False))
+    keys = base.keys[np.sort(np.concatenate(keep))]
+    w = Workload(f"sel_64s_14e_cut{len(keys)}_s{seed}", "spinors", 64, 14, -1, keys, base.ints, None,
+                 {"from": base.name})
+    w.c = coefficient_vector(rng, keys, hf, 1, True)
+    return w
+
+
 def selected_spinor_64(M: int = 1_000_000, nvec: int = 1, seed_offset: int = 4) -> Workload:
     """64 spinors, 14 electrons, selected space of M determinants (HF + singles + doubles
     + random triples); 80 Hermitian complex Cholesky vectors; complex c.

@@ -72,8 +72,10 @@ def test_enpt2_errors(gpu):
     torch = gpu
     w = W.random_small(307, "spinors", 8, 3, 0)
     H = sci.Hamiltonian.from_workload(w)
-    with pytest.raises(sci.SciError):
+    with pytest.raises(ValueError):     # a complex Hamiltonian takes complex coefficients
         H.enpt2(torch.zeros((w.M, 1), dtype=torch.float64, device="cuda"), [0.0])
+    with pytest.raises(sci.SciError):   # nroots > 8
+        H.enpt2(torch.zeros((w.M, 9), dtype=torch.complex128, device="cuda"), [0.0] * 9)
     w = W.random_small(308, "spin_orbitals", 6, 2, 2)
     H = sci.Hamiltonian.from_workload(w)
     with pytest.raises(sci.SciError):
@@ -118,4 +120,65 @@ def test_enpt2_30_orbital_space_matches_oracle(gpu, cut30, nroots):
     assert np.allclose(e2p, ep2, rtol=1e-9)
     e2w_b, e2p_b, e2q_b, st_b = H.enpt2(Ct, E0[:nroots], table_bytes=(1 << 22) * (8 + 8 * nroots))
     assert st_b["batches"] >= 8 and st_b["batches"] > st["batches"] and st_b["distinct_W"] == st["distinct_W"]
+    assert np.allclose(e2q_b, E2[:nroots], rtol=1e-10, atol=0)
+
+
+SPINOR_CASES = [  # (seed, n, N, frac, nroots): full spaces of 560 to 1820 determinants
+    (321, 14, 4, 0.3, 1),
+    (322, 16, 3, 0.2, 2),
+    (323, 12, 5, 0.25, 3),
+    (324, 16, 4, 0.1, 4),
+]
+
+
+@pytest.mark.parametrize("seed,n,N,frac,nroots", SPINOR_CASES)
+def test_enpt2_spinors_matches_oracle(gpu, seed, n, N, frac, nroots):
+    """Complex spinor mode (no spin conservation, complex numerators |sum_J H_IJ c_J|^2)
+    against the oracle's sum over the explicit complement Q of the full space, at 1e-10;
+    a 256-entry table (several batches of the whole-string code, restarts) gives the
+    same."""
+    torch = gpu
+    w = W.random_small(seed, "spinors", n, N, 0, naux=6, frac=frac)
+    C, E0 = roots_of(w, nroots)
+    ref = PT.enpt2("spinors", n, N, 0, w.ints.h, w.ints.eri(), w.keys, C, E0)
+    H = sci.Hamiltonian.from_workload(w)
+    Ct = torch.from_numpy(np.ascontiguousarray(C)).cuda()
+    e2w, e2p, e2q, st = H.enpt2(Ct, E0)
+    assert np.allclose(e2q, ref, rtol=1e-10, atol=1e-14), (e2q, ref)
+    e2w_b, e2p_b, e2q_b, st_b = H.enpt2(Ct, E0, table_bytes=256 * (8 + 16 * nroots))
+    assert st_b["batches"] > st["batches"]
+    assert np.allclose(e2q_b, e2q, rtol=1e-12, atol=1e-15)
+    d = H.diagonal().cpu().numpy()
+    ep2 = (np.abs(C) ** 2 * (E0[None, :] - d[:, None])).sum(0)
+    assert np.allclose(e2p, ep2, rtol=1e-9, atol=1e-12)
+
+
+@pytest.fixture(scope="module")
+def cut64():
+    """A 301-determinant space of the 64-spinor recipe (HF, sampled singles, doubles and
+    triples), its two lowest roots from the oracle's dense H and the oracle's direct sum
+    (sciref_enpt2) over its ~3e7 external determinants."""
+    w = W.selected_spinor_64_cut()
+    o = Oracle.from_workload(w)
+    ev, U = np.linalg.eigh(o.dense())
+    C, E0 = U[:, :2].copy(), ev[:2].copy()
+    E2, n_ext = o.enpt2(C, E0)
+    n_conn = sum(1 for r in range(w.M) if len(o.connections(r)[0]) > 0)
+    return w, C, E0, E2, n_ext, n_conn
+
+
+@pytest.mark.parametrize("nroots", [1, 2])
+def test_enpt2_64_spinor_space_matches_oracle(gpu, cut64, nroots):
+    """The spinor paths at the full-size shape (64 spinors, 14 electrons: 111,475 doubles
+    per determinant, the whole-string batch code, complex tables) against the oracle at
+    1e-10, with the distinct count exact; a 2^20-entry table gives the same sums."""
+    torch = gpu
+    w, C, E0, E2, n_ext, n_conn = cut64
+    H = sci.Hamiltonian.from_workload(w)
+    Ct = torch.from_numpy(C[:, :nroots].copy()).cuda()
+    e2w, e2p, e2q, st = H.enpt2(Ct, E0[:nroots])
+    assert np.allclose(e2q, E2[:nroots], rtol=1e-10, atol=0), (e2q, E2[:nroots])
+    assert st["distinct_W"] == n_ext + n_conn
+    e2w_b, e2p_b, e2q_b, st_b = H.enpt2(Ct, E0[:nroots], table_bytes=(1 << 20) * (8 + 16 * nroots))
+    assert st_b["batches"] > st["batches"] and st_b["distinct_W"] == st["distinct_W"]
     assert np.allclose(e2q_b, E2[:nroots], rtol=1e-10, atol=0)

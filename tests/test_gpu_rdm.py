@@ -77,11 +77,47 @@ def test_rdm_weights_linear_and_rdm1_only(gpu):
     assert none is None and np.abs(h1 - g1).max() < 1e-12 * scale
 
 
+def spin_sum_rdm(g1, g2, n: int):
+    """Spin-orbital (2n) -> spatial (n) density matrices by indexing, as a reference:
+    gamma[p,q] = sum_s g1[ps, qs], Gamma[p,q,r,s] = sum_{s,t} g2[ps, qs, rt, st]
+    (bit p < n is alpha p, bit n+p beta p)."""
+    g = g1.reshape(2, n, 2, n)
+    gamma = g[0, :, 0, :] + g[1, :, 1, :]
+    if g2 is None:
+        return gamma, None
+    G = g2.reshape(2, n, 2, n, 2, n, 2, n)
+    Gamma = sum(G[s, :, s, :, t, :, t, :] for s in range(2) for t in range(2))
+    return gamma, Gamma
+
+
+@pytest.mark.parametrize("name", ["fci_8o", "sel_30o_60k"])
+def test_rdm_grads_spin_sums_and_cholesky_contraction(gpu, name):
+    """sci_rdm_grads against the spin sums of sci_rdm12's matrices (indexing, above) and
+    the contraction gchol[P] = sum_rs Gamma[:, :, r, s] L[P, r, s] done in numpy."""
+    torch = gpu
+    w = W.fci_small_8o() if name == "fci_8o" else W.selected_30o(M=60000, nvec=3)
+    H = sci.Hamiltonian.from_workload(w)
+    C = torch.from_numpy(np.ascontiguousarray(w.c)).cuda()
+    wt = np.array([1.0, -0.5, 2.0])[: C.shape[1]]
+    g1, g2 = H.rdm12(C, weights=wt)
+    gamma_r, Gamma_r = spin_sum_rdm(g1.cpu().numpy(), g2.cpu().numpy(), w.n)
+    L = torch.from_numpy(w.ints.chol.copy()).cuda()
+    gamma, Gamma, gL = H.rdm_grads(C, weights=wt, chol=L, Gamma=True)
+    scale = np.abs(Gamma_r).max()
+    assert np.abs(gamma.cpu().numpy() - gamma_r).max() < 1e-12 * np.abs(gamma_r).max()
+    assert np.abs(Gamma.cpu().numpy() - Gamma_r).max() < 1e-12 * scale
+    n, naux = w.n, w.ints.chol.shape[0]
+    ref = (Gamma_r.reshape(n * n, n * n) @ w.ints.chol.reshape(naux, n * n).T).T.reshape(naux, n, n)
+    assert np.abs(gL.cpu().numpy() - ref).max() < 1e-12 * np.abs(ref).max()
+    # 1-RDM only: no 2-RDM walk, the same gamma
+    g_only, none1, none2 = H.rdm_grads(C, weights=wt)
+    assert none1 is None and none2 is None and torch.allclose(g_only, gamma, rtol=0, atol=1e-13 * float(gamma.abs().max()))
+
+
 def test_rdm_energy_identity_full_space_4_roots(gpu):
     """2M-determinant space, 4 vectors: sum h gamma + 1/2 sum (pq|rs) Gamma equals
     sum_k w_k c_k^T sigma_k (spin-summed spatial density matrices)."""
     torch = gpu
-    from paper_2501_18185_gb300.autograd import spin_sum_rdm
 
     w = W.selected_30o(nvec=4)
     H = sci.Hamiltonian.from_workload(w)
