@@ -103,6 +103,17 @@ constexpr int kUnroll = 4;
 // 256 KB L1 for caching decides the speed (measured on the 2M-determinant space:
 // 5.20 ms at 768 rows, 5.34 at 1024, 7.63 at 1280, where L1 is nearly gone).
 constexpr int kRowsPerCta = 768;
+// The FP32-storage kernel at 8 vectors (the mixed Davidson's block) stages 40 bytes per
+// window row, so its window rows and its CTAs per SM (registers) are set apart.  Measured
+// on the 2M-determinant space (doubles kernel, 8 vectors): 768 rows at 64 registers (4
+// CTAs/SM by shared memory and registers) 15.84 ms; 512 rows at 5 CTAs/SM (48 registers,
+// no spills) 14.88 ms; 448 rows at 6 (40 registers) 15.17 ms; 384 rows 15.57 ms.
+#ifndef SCI_F32_ROWS
+#define SCI_F32_ROWS 512
+#endif
+#ifndef SCI_F32_MINB
+#define SCI_F32_MINB 5
+#endif
 
 // ------------------------------------------------------------------ row ranges
 // A RANGED launch walks the range tables of sci_set_row_range() and computes only the
@@ -305,7 +316,7 @@ __device__ __forceinline__ void ds_fma1(Ds &a, float t, float c)
 // FP32 storage: the pair table rounded to FP32 (tab32) and FP32 coefficients, exact
 // products, compensated bucket sums, FP64 accumulation into sigma
 template <int NV, bool RANGED>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, NV >= 8 ? SCI_F32_MINB : 1)
 k_doubles_f32(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_code,
               const uint32_t *__restrict__ e_pos, int64_t E, int CH, sci::TabRule tr,
               const float *__restrict__ tab32, const float *__restrict__ C, int nvec, int v0,
@@ -737,13 +748,13 @@ int grid_for(int64_t n, int threads = kThreads)
 // Rows per CTA (CH) so that the staged window, at most CH + maxb - 1 members, fits the
 // shared-memory budget; small windows first (more resident CTAs per SM), larger ones
 // only when the buckets need them.
-int choose_rows(int maxb, size_t bytes_per_entry, size_t &smem)
+int choose_rows(int maxb, size_t bytes_per_entry, size_t &smem, int max_rows = kRowsPerCta)
 {
     const size_t budgets[3] = {48 * 1024, 100 * 1024, 200 * 1024};
     for (size_t budget : budgets) {
         int64_t ch = (int64_t)(budget / bytes_per_entry) - (int64_t)maxb - 8;
         if (ch >= 512 || (budget == budgets[2] && ch >= 64)) {
-            ch = std::min<int64_t>(ch, kRowsPerCta);
+            ch = std::min<int64_t>(ch, max_rows);
             ch = std::max<int64_t>(64, ch & ~(int64_t)63);
             smem = (size_t)(ch + maxb) * bytes_per_entry + 64;
             return (int)ch;
@@ -863,7 +874,7 @@ int launch_doubles_f32(sci_ctx *ctx, const Tabs &T, const float *C, double *S, i
     if (T.e2 == 0) return SCI_OK;
     size_t per = NV * sizeof(float) + row_extra<RG>();
     size_t smem = 0;
-    int ch = choose_rows(ctx->maxb2, per, smem);
+    int ch = choose_rows(ctx->maxb2, per, smem, NV >= 8 ? SCI_F32_ROWS : kRowsPerCta);
     if (ch < 0) return sci_fail(ctx, SCI_ERR_OVERFLOW, "bucket too large for shared memory");
     int64_t blocks = (T.e2 + ch - 1) / ch;
     auto kern = k_doubles_f32<NV, RG>;
