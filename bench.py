@@ -437,13 +437,22 @@ def pt2_bench(sizes=(60_000, 200_000, 1_000_000, 2_000_000), table_gb=96.0):
         t = time.perf_counter()
         e2w, e2p, e2q, st = H.enpt2(c, E0, table_bytes=int(table_gb * (1 << 30)))
         dt = time.perf_counter() - t
+        # the same with screening (eps = 1e-7): classes skipped by the bounds of their
+        # elements, single contributions below eps dropped
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        s2w, s2p, s2q, sst = H.enpt2(c, E0, eps=1e-7, table_bytes=int(table_gb * (1 << 30)))
+        dts = time.perf_counter() - t
+        screened = {"eps": 1e-7, "seconds": dts, "E2_Q": float(s2q[0]), "distinct_W": sst["distinct_W"],
+                    "batches": sst["batches"]}
         n, na, nb = w.n, w.n_alpha, w.n_beta
         ua, ub = n - na, n - nb
         per = na * ua + nb * ub + na * (na - 1) // 2 * (ua * (ua - 1) // 2) + nb * (nb - 1) // 2 * (ub * (ub - 1) // 2) \
             + na * ua * nb * ub
         out.append({"M": M, "seconds": dt, "davidson_converged": bool(r.converged), "E0": E0[0],
                     "E0_plus_E2": E0[0] + float(e2q[0]), "E2_Q": float(e2q[0]), "E2_W": float(e2w[0]),
-                    "E2_P": float(e2p[0]), "generated": M * per, "generated_per_s": M * per / dt, **st})
+                    "E2_P": float(e2p[0]), "generated": M * per, "generated_per_s": M * per / dt, **st,
+                    "screened": screened})
         del H
         torch.cuda.empty_cache()
     return out
@@ -635,6 +644,61 @@ def spinor_bench(device, steps=10, warmup=3):
     return out
 
 
+def deterministic_bench(H, w, steps=10):
+    """sigma with deterministic accumulation (sci_set_deterministic: row sums stored per
+    bucket entry, then summed per row in a fixed order) against the default FP64 atomics,
+    on the bench workload's vector: CUDA-event milliseconds per step (L2 flushed), the four
+    kernel times, the set-up seconds and device bytes of the mode, and whether two calls
+    agree bit for bit."""
+    import torch
+
+    from paper_2501_18185_gb300 import sci
+
+    dev = H.device
+    stream = torch.cuda.current_stream(dev)
+    C = torch.from_numpy(np.ascontiguousarray(w.c)).to(dev)
+    S = torch.empty_like(C)
+    flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=dev)
+
+    def timed():
+        H.sigma(C, out=S)
+        ms, kern = [], []
+        sci.sci_profile(H.ctx, True)
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            H.sigma(C, out=S)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            kern.append(sci.sci_kernel_times(H.ctx, 4))
+        sci.sci_profile(H.ctx, False)
+        return statistics.median(ms), [statistics.median(k[i] for k in kern) for i in range(4)]
+
+    atomic_ms, atomic_k = timed()
+    a1 = H.sigma(C).clone()
+    a2 = H.sigma(C)
+    b0 = H.info()["device_bytes"]
+    t = time.perf_counter()
+    H.set_deterministic(C.shape[1])
+    setup = time.perf_counter() - t
+    det_bytes = H.info()["device_bytes"] - b0
+    det_ms, det_k = timed()
+    d1 = H.sigma(C).clone()
+    d2 = H.sigma(C)
+    H.set_deterministic(0)
+    H.sync_status()
+    rel = float(torch.linalg.vector_norm(d1 - a1) / torch.linalg.vector_norm(a1))
+    return {"atomic_ms": atomic_ms, "atomic_kernel_ms": atomic_k, "deterministic_ms": det_ms,
+            "deterministic_kernel_ms": {"init": det_k[0], "doubles": det_k[1], "singles": det_k[2],
+                                        "row_sums": det_k[3]},
+            "setup_s": round(setup, 3), "device_bytes": det_bytes,
+            "atomic_repeat_bitwise_equal": bool(torch.equal(a1, a2)),
+            "deterministic_repeat_bitwise_equal": bool(torch.equal(d1, d2)),
+            "rel_diff_deterministic_vs_atomic": rel}
+
+
 def rowsplit_bench(H, parts=(2, 4, 8), steps=5):
     """The row split of the bench space, each rank timed alone on this GPU: for K ranks,
     the K ranges balanced by connection count + C(N, 2) per row, then for each range its
@@ -747,7 +811,7 @@ def main():
     ap.add_argument("--pt2-table-gb", type=float, default=96.0, help="hash-table memory of the pt2 section")
     ap.add_argument("--no-spinor", action="store_true", help="skip the 64-spinor complex workload section")
     ap.add_argument("--only", default=None, choices=["blockvec", "rdm", "batch", "davidson", "pt2", "spinor",
-                                                     "rowsplit", "pt2_spinor"],
+                                                     "rowsplit", "pt2_spinor", "deterministic"],
                     help="run one side section alone and print its JSON (profiling runs)")
     ap.add_argument("--prec", default="f64", choices=["f64", "ds", "f32"],
                     help="f64: FP64 FMA path; ds: paired-FP32 products/sums (FP64 tolerance); "
@@ -819,9 +883,9 @@ def main():
         split.rebalance(e0.elapsed_time(e1) / 3, split.weights)
         del Cw, Sw
 
-    if args.only in ("rdm", "davidson", "rowsplit"):
+    if args.only in ("rdm", "davidson", "rowsplit", "deterministic"):
         out = (rdm_bench(H, w) if args.only == "rdm" else davidson_bench(H, w) if args.only == "davidson"
-               else rowsplit_bench(H))
+               else rowsplit_bench(H) if args.only == "rowsplit" else deterministic_bench(H, w))
         print(json.dumps({args.only: out}), flush=True)
         return
     C64 = torch.from_numpy(np.ascontiguousarray(w.c)).to(dev)
@@ -958,7 +1022,7 @@ def main():
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(w)
     dav = None
-    rdm = batch = pt2 = rowsplit = None
+    rdm = batch = pt2 = rowsplit = determ = None
     if not args.no_davidson and world == 1 and not w.ints.complex_:
         dav = davidson_bench(H, w)
         dav["blockvec"] = blockvec_bench()
@@ -967,6 +1031,7 @@ def main():
         pt2 = pt2_bench(sizes=(200_000,))
         pt2.append({"spinor": pt2_spinor_bench()})
         rowsplit = rowsplit_bench(H)
+        determ = deterministic_bench(H, w)
     spinor = None
     if not args.no_spinor and world == 1 and not w.ints.complex_:
         spinor = spinor_bench(local)
@@ -985,7 +1050,7 @@ def main():
                                           * ((nv + 7) // 8 if not w.ints.complex_ else (nv + 3) // 4)),
             "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "prec": args.prec,
             "other_prec": variant, "pipe_peaks": pp, "davidson": dav, "rdm": rdm, "batch": batch, "pt2": pt2,
-            "spinor": spinor, "rowsplit": rowsplit}
+            "spinor": spinor, "rowsplit": rowsplit, "deterministic": determ}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

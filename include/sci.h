@@ -154,6 +154,24 @@ int sci_sigma(sci_ctx *ctx, const void *C, void *S, int nvec, int prec);
  * determinants, SCI_ERR_ARG for a range outside [0, M], SCI_ERR_NOMEM. */
 int sci_set_row_range(sci_ctx *ctx, int64_t row_begin, int64_t row_end);
 
+/* Deterministic accumulation for later sci_sigma() calls on this context.  By default
+ * sigma adds each (bucket, member) row sum into S with an FP64 atomic add, so the order of
+ * the additions, and the last bits of S, vary between calls.  With max_nvec > 0 the
+ * context holds, for up to max_nvec vectors, one slot per bucket entry and per vector for
+ * those row sums, in row order (each table's entries sorted by row with a stable sort, so
+ * ascending table position within a row; built once here); sigma then stores each row sum
+ * in its slot and a second kernel forms S_I = H_II C_I + the sum of row I's contiguous
+ * slots, one warp per row: lane l takes the row's slots l, l + 32, ... and the lanes are
+ * combined by a fixed butterfly of warp shuffles.  Repeated calls on the same inputs give
+ * bitwise equal S.  Costs
+ * device memory: (entries of both tables) x max_nvec scalars plus 4 bytes per entry and
+ * per row; sigma with nvec > max_nvec returns SCI_ERR_ARG.  Every precision mode is
+ * served; a row range (sci_set_row_range) cannot be combined with it (SCI_ERR_STATE).
+ * max_nvec = 0 returns to atomics and frees the buffers; a new determinant list clears it.
+ * Synchronous.  Errors: SCI_ERR_STATE without determinants or with a row range set,
+ * SCI_ERR_ARG for max_nvec < 0, SCI_ERR_NOMEM. */
+int sci_set_deterministic(sci_ctx *ctx, int max_nvec);
+
 /* Cost of each row of sigma, for balancing row ranges: cost[I] = the number of
  * determinants J != I of the list within a single or double excitation of I (the
  * off-diagonal elements of row I of H), exact.  cost: device, M int64, overwritten.
@@ -217,7 +235,8 @@ int sci_info(sci_ctx *ctx, int64_t *out, int n);
 /* Kernel timing for reports.  sci_profile(ctx, 1) makes later sci_sigma() calls record
  * CUDA events on the context stream around each of their kernels; sci_kernel_times()
  * waits for the last such call and writes the durations in milliseconds of its diagonal
- * initialisation, double-excitation and single-excitation kernels to ms[0..n), n <= 3. */
+ * initialisation, double-excitation and single-excitation kernels and, in deterministic
+ * mode (sci_set_deterministic), of the per-row sums (0 otherwise) to ms[0..n), n <= 4. */
 int sci_profile(sci_ctx *ctx, int enable);
 int sci_kernel_times(sci_ctx *ctx, float *ms, int n);
 

@@ -60,7 +60,7 @@ def _load():
             L.sciref_sigma_brute_rows.argtypes = [vp, vp, i64, vp, i32, vp]
             L.sciref_sigma_abs_rows.argtypes = [vp, vp, i64, vp, i32, vp]
             L.sciref_rdm12.argtypes = [vp, vp, vp, vp]
-            L.sciref_enpt2.argtypes = [vp, vp, i32, vp, vp, vp]
+            L.sciref_enpt2.argtypes = [vp, vp, i32, vp, ctypes.c_double, i32, vp, vp]
             L.sciref_set_threads.argtypes = [i32]
             L.sciref_set_threads.restype = i32
             _lib = L
@@ -213,17 +213,20 @@ class Oracle:
             raise ValueError(rc)
         return g1, g2
 
-    def enpt2(self, C, E0):
+    def enpt2(self, C, E0, eps: float = 0.0, over_w: bool = False):
         """Epstein-Nesbet E2_k (Eq. ENPT2E) of the columns of C on this list with
         zeroth-order energies E0, summed over the single and double excitations of the
-        list that are outside it (sciref_enpt2).  Returns (E2 [nroots], number of distinct
-        external determinants)."""
+        list that are outside it (sciref_enpt2); with eps > 0 a contribution H_IJ C_J with
+        |H_IJ| max_k |C_Jk| < eps is left out; over_w sums over W (the list's excitations,
+        members included: E2[W] of Eq. EW1) instead of Q.  Returns (E2 [nroots], number of
+        distinct determinants summed)."""
         C = np.ascontiguousarray(np.asarray(C).reshape(self.M, -1), dtype=self.dtype)
         e0 = np.ascontiguousarray(np.asarray(E0, dtype=np.float64).reshape(-1))
         assert e0.size == C.shape[1]
         E2 = np.zeros(C.shape[1], dtype=np.float64)
         nx = np.zeros(1, dtype=np.int64)
-        rc = self.L.sciref_enpt2(self.ctx, _ptr(C), C.shape[1], _ptr(e0), _ptr(E2), _ptr(nx))
+        rc = self.L.sciref_enpt2(self.ctx, _ptr(C), C.shape[1], _ptr(e0), float(eps), int(over_w), _ptr(E2),
+                                 _ptr(nx))
         if rc != SCIREF_OK:
             raise ValueError(rc)
         return E2, int(nx[0])

@@ -621,6 +621,14 @@ int sciref_rdm12(const sciref_ctx *c, const double *C, double *g1, double *g2)
  *      and add |numerator_k|^2 / (E0_k - H_II) to the bin's partial sum;
  *   4. E2_k = the bins' partial sums added in bin order (the result does not depend on the
  *      number of threads).
+ * over_w = 1 sums over W instead of Q: every single and double excitation of the list,
+ * members of the list included (their numerators run over the other members J, since an
+ * excitation of J is never J): the E2[W] of Eq. EW1, with E2[Q] = E2[W] - E2[P] (Eq.
+ * PT2final).
+ * Screening (eps > 0): a contribution H_IJ C_J is left out of every numerator of I when
+ * |H_IJ| max_k |C_Jk| < eps, the per-element form of the paper's screening of ENPT2
+ * contributions by the size of their matrix elements (Sec. 2.3, Table 1's bounds; Sec. 2.4);
+ * an I none of whose contributions is kept adds no term.  eps = 0 is the exact sum.
  * C: [M][nroots] row-major (complex interleaved); E0, E2: nroots doubles.  *n_external
  * (if not NULL) receives the number of distinct determinants summed (|Q| restricted as
  * above).  Memory: 16 bytes per generated external pair. */
@@ -633,9 +641,9 @@ static int cmp_ext(const void *x, const void *y)
     return (a->j > b->j) - (a->j < b->j);
 }
 
-/* single and double excitations of row j that are not in the list, written to out (if
- * not NULL) in generation order; returns their number */
-static int64_t external_excitations(const sciref_ctx *c, int64_t j, ext_pair *out)
+/* single and double excitations of row j that are not in the list (all of them when
+ * keep_members), written to out (if not NULL) in generation order; returns their number */
+static int64_t external_excitations(const sciref_ctx *c, int64_t j, ext_pair *out, int keep_members)
 {
     uint64_t d = c->keys[j];
     int occ[64], vir[64], no = 0, nv = 0;
@@ -648,7 +656,7 @@ static int64_t external_excitations(const sciref_ctx *c, int64_t j, ext_pair *ou
             int i = occ[x], a = vir[y];
             if (spin_of(c, i) != spin_of(c, a)) continue;
             uint64_t e = (d & ~((uint64_t)1 << i)) | ((uint64_t)1 << a);
-            if (find_key(c, e) >= 0) continue;
+            if (!keep_members && find_key(c, e) >= 0) continue;
             if (out) { out[cnt].key = e; out[cnt].j = (uint64_t)j; }
             cnt++;
         }
@@ -660,7 +668,7 @@ static int64_t external_excitations(const sciref_ctx *c, int64_t j, ext_pair *ou
                     if (spin_of(c, i) + spin_of(c, jj) != spin_of(c, a) + spin_of(c, b)) continue;
                     uint64_t e = d & ~((uint64_t)1 << i) & ~((uint64_t)1 << jj);
                     e |= ((uint64_t)1 << a) | ((uint64_t)1 << b);
-                    if (find_key(c, e) >= 0) continue;
+                    if (!keep_members && find_key(c, e) >= 0) continue;
                     if (out) { out[cnt].key = e; out[cnt].j = (uint64_t)j; }
                     cnt++;
                 }
@@ -670,24 +678,24 @@ static int64_t external_excitations(const sciref_ctx *c, int64_t j, ext_pair *ou
 #define ENPT2_BINS 256
 static unsigned enpt2_bin(uint64_t key) { return (unsigned)((key * 0x9E3779B97F4A7C15ull) >> 56); }
 
-int sciref_enpt2(const sciref_ctx *c, const double *C, int nroots, const double *E0, double *E2,
-                 int64_t *n_external)
+int sciref_enpt2(const sciref_ctx *c, const double *C, int nroots, const double *E0, double eps, int over_w,
+                 double *E2, int64_t *n_external)
 {
-    if (!c || !E0 || !E2 || nroots <= 0 || (c->M > 0 && !C)) return SCIREF_ERR_ARG;
+    if (!c || !E0 || !E2 || nroots <= 0 || (c->M > 0 && !C) || eps < 0) return SCIREF_ERR_ARG;
     const int z = c->is_complex;
     const int64_t M = c->M;
     /* 1. count, then write, the external pairs of each J */
     int64_t *off = (int64_t *)calloc((size_t)M + 1, sizeof(int64_t));
     if (!off) return SCIREF_ERR_ARG;
 #pragma omp parallel for schedule(dynamic, 16)
-    for (int64_t j = 0; j < M; j++) off[j + 1] = external_excitations(c, j, NULL);
+    for (int64_t j = 0; j < M; j++) off[j + 1] = external_excitations(c, j, NULL, over_w);
     for (int64_t j = 0; j < M; j++) off[j + 1] += off[j];
     const int64_t np = off[M];
     ext_pair *pairs = (ext_pair *)malloc((size_t)(np > 0 ? np : 1) * sizeof(ext_pair));
     ext_pair *binned = (ext_pair *)malloc((size_t)(np > 0 ? np : 1) * sizeof(ext_pair));
     if (!pairs || !binned) { free(off); free(pairs); free(binned); return SCIREF_ERR_ARG; }
 #pragma omp parallel for schedule(dynamic, 16)
-    for (int64_t j = 0; j < M; j++) external_excitations(c, j, pairs + off[j]);
+    for (int64_t j = 0; j < M; j++) external_excitations(c, j, pairs + off[j], over_w);
     free(off);
     /* 2. bins by hash of I (a counting sort), then each bin sorted by (I, J) */
     int64_t bstart[ENPT2_BINS + 1], bfill[ENPT2_BINS];
@@ -712,13 +720,26 @@ int sciref_enpt2(const sciref_ctx *c, const double *C, int nroots, const double 
             while (e < nb && v[e].key == v[s].key) e++;
             const uint64_t ext = v[s].key;
             for (int k = 0; k < nroots; k++) num[k] = 0;
+            int kept = 0;
             for (int64_t t = s; t < e; t++) {
                 int deg, sg;
                 const zd hIJ = offdiag_element(c, ext, c->keys[v[t].j], &deg, &sg);
+                double cmax = 0.0;
+                for (int k = 0; k < nroots; k++) {
+                    const size_t q = (size_t)v[t].j * nroots + k;
+                    const double m = z ? cabs(CMPLX(C[2 * q], C[2 * q + 1])) : fabs(C[q]);
+                    if (m > cmax) cmax = m;
+                }
+                if (eps > 0 && cabs(hIJ) * cmax < eps) continue;
+                kept = 1;
                 for (int k = 0; k < nroots; k++) {
                     const size_t q = (size_t)v[t].j * nroots + k;
                     num[k] += hIJ * (z ? CMPLX(C[2 * q], C[2 * q + 1]) : CMPLX(C[q], 0.0));
                 }
+            }
+            if (!kept) {
+                s = e;
+                continue;
             }
             const double hII = creal(diag_element(c, ext));
             for (int k = 0; k < nroots; k++) {

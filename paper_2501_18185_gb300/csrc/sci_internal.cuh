@@ -161,6 +161,16 @@ struct sci_ctx {
     uint32_t *r1_meta = nullptr;
     size_t range_bytes = 0;
 
+    // deterministic accumulation (sci_set_deterministic): when det_nvec > 0, sigma stores
+    // each (bucket, member) row sum at slot det_inv[entry] of det_part2 / det_part1
+    // ([entries][det_nvec] scalars), the entry's position among the entries sorted by row
+    // (stable, so ascending table position within a row), and a second kernel adds each
+    // row's contiguous segment [det_ptr[I], det_ptr[I + 1]) in a fixed order
+    int det_nvec = 0;
+    uint32_t *det_ptr2 = nullptr, *det_inv2 = nullptr, *det_ptr1 = nullptr, *det_inv1 = nullptr;
+    void *det_part2 = nullptr, *det_part1 = nullptr;
+    size_t det_bytes = 0;
+
     // host-buffer sigma staging
     void *stage_c = nullptr, *stage_s = nullptr;
     size_t stage_bytes = 0;
@@ -177,7 +187,7 @@ struct sci_ctx {
 
     // kernel timing
     int profile = 0;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 
     int *status = nullptr;  // device status word (sci::DevErr bits)
     size_t bytes_held = 0;
@@ -193,6 +203,8 @@ cudaError_t sci_noalloc_prepare(int device);
 
 // row ranges (sci_rows.cu): frees the range tables and clears the range
 void sci_free_range(sci_ctx *ctx);
+// deterministic accumulation (sci_rows.cu): frees its index and buffers, back to atomics
+void sci_free_det(sci_ctx *ctx);
 
 // launchers (sci_sigma.cu)
 bool sci_sigma_window_fits(const sci_ctx *ctx);

@@ -26,6 +26,17 @@
 // F the Fock diagonal of the reference and G_pq = (pp|qq) - (pq|qp): O(level^2) per I.
 // Element formulas and phases are those of the sigma kernels (bra I, ket J).
 //
+// Screening (eps > 0): a contribution with |H_IJ| max_k |c_Jk| < eps is left out.  Before
+// any element of a double-excitation class is evaluated, the class is tested against an
+// upper bound of its elements over the table, the GPU form of the paper's screening by the
+// upper bounds of Table 1 (Sec. 2.3): for determinants the double element is one entry of
+// the pair table, independent of the spectators, so
+//   same spin:   B[P(i,j)][a] = max_{b > a} |W(ij -> ab)|,  and its max over a;
+//   alpha-beta:  B[i, j] = max_{a,b} |(ai|bj)|;
+//   spinors:     B[P(i,j)][a] = max_{b > a} |W(ij -> ab)|.
+// A class whose bound times max_k |c_Jk| is below eps is skipped whole; since the bound is
+// at least every element of the class, the sum equals that of the per-element test.
+//
 // Spinor mode (complex Hermitian integrals, no spin conservation; the 4C workloads of
 // Sec. 4): every single i -> a and double i < j -> a < b over the n <= 64 spinors.  The
 // batch code runs over the whole string, f(I) = XOR of g(o) over I's occupied spinors, so
@@ -68,6 +79,10 @@ struct Pt2 {
     unsigned long long limit;
     int *flag;
     double eps;
+    // screening bounds (NULL when eps = 0): see the header
+    const double *bss3;   // [NP][n] same-spin (real) or spinor: max over b > a, per (pair, a)
+    const double *bss;    // [NP] same-spin (real): max over a of bss3
+    const double *bab;    // [n][n] alpha-beta (real): [j_beta * n + i_alpha]
 };
 
 using sci::below;
@@ -199,6 +214,7 @@ k_pt2_gen(const uint64_t *__restrict__ Pkeys, int64_t M, const double *__restric
                     const int s = t - c0;
                     const uint16_t po = s_pair[s / qa], pv = s_pair[s % qa];
                     const int i = orb[po & 0xFF], j = orb[po >> 8], a = orb[32 + (pv & 0xFF)], b = orb[32 + (pv >> 8)];
+                    if (p.bss && p.bss[j * (j - 1) / 2 + i] * cmax < p.eps) continue;   // the class's bound
                     const uint64_t I = (key & ~(1ull << i) & ~(1ull << j)) | (1ull << a) | (1ull << b);
                     insert<R>(p, I, h_double(p, key, i, j, a, b), cJ, cmax);
                 }
@@ -229,6 +245,7 @@ k_pt2_gen(const uint64_t *__restrict__ Pkeys, int64_t M, const double *__restric
                 insert<R>(p, (key & ~(1ull << jb)) | (1ull << vb_), h_single(p, key, jb, vb_), cJ, cmax);
             } else {
                 const int i = orb[(s - 1) / ua], a = orb[32 + (s - 1) % ua];
+                if (p.bab && p.bab[(e & 0xFF) * n + i] * cmax < p.eps) continue;   // the class's bound
                 const uint64_t I = (key & ~(1ull << i) & ~(1ull << jb)) | (1ull << a) | (1ull << vb_);
                 insert<R>(p, I, h_double(p, key, i, jb, a, vb_), cJ, cmax);
             }
@@ -240,6 +257,7 @@ k_pt2_gen(const uint64_t *__restrict__ Pkeys, int64_t M, const double *__restric
         for (int t = lane; t < pb * ub; t += 32) {
             const uint16_t po = s_pair[t / ub];
             const int j1 = orb[64 + (po & 0xFF)], j2 = orb[64 + (po >> 8)], b1 = orb[96 + t % ub];
+            if (p.bss3 && p.bss3[(j2 * (j2 - 1) / 2 + j1) * n + b1] * cmax < p.eps) continue;   // the class's bound
             const uint32_t c = target ^ s_g[j1] ^ s_g[j2] ^ s_g[b1];
             for (int q = s_cstart[c]; q < s_cstart[c + 1]; q++) {
                 const int b2 = s_obc[q];
@@ -377,6 +395,7 @@ k_pt2_gen_z(const uint64_t *__restrict__ Pkeys, int64_t M, const zdbl *__restric
         for (int t = lane; t < npairs * nv; t += 32) {
             const uint16_t po = s_pair[t / nv];
             const int i = orb[po & 0xFF], j = orb[po >> 8], a = orb[64 + t % nv];
+            if (p.bss3 && p.bss3[(j * (j - 1) / 2 + i) * n + a] * cmax < p.eps) continue;   // the class's bound
             const uint32_t c = target ^ s_g[i] ^ s_g[j] ^ s_g[a];
             for (int q = s_cstart[c]; q < s_cstart[c + 1]; q++) {
                 const int b = s_obc[q];
@@ -547,6 +566,46 @@ __global__ void k_pt2_setup(int norb, uint64_t ref, const T *__restrict__ h_so, 
     }
 }
 
+
+// Screening bounds of the double-excitation classes (see the header).  Real mode: the
+// same-spin region W[P(i,j)][P(a,b)] (after the n^4 alpha-beta block T) and the alpha-beta
+// block T[u_ket][u_bra] with u = j_beta * n + i_alpha; spinor mode: the complex W.
+__device__ __forceinline__ double mag(double a) { return fabs(a); }
+__device__ __forceinline__ double mag(zdbl a) { return sqrt(a.x * a.x + a.y * a.y); }
+
+template <typename T>
+__global__ void k_pt2_bounds3(int n, const T *__restrict__ W, double *__restrict__ b3)
+{
+    const int64_t NP = (int64_t)n * (n - 1) / 2;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < NP * n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t Pij = t / n;
+        const int a = (int)(t % n);
+        double m = 0.0;
+        for (int b = a + 1; b < n; b++) m = fmax(m, mag(W[Pij * NP + (int64_t)b * (b - 1) / 2 + a]));
+        b3[t] = m;
+    }
+}
+
+__global__ void k_pt2_bounds_pair(int n, const double *__restrict__ b3, double *__restrict__ b2)
+{
+    const int64_t NP = (int64_t)n * (n - 1) / 2;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < NP; t += (int64_t)gridDim.x * blockDim.x) {
+        double m = 0.0;
+        for (int a = 0; a < n; a++) m = fmax(m, b3[t * n + a]);
+        b2[t] = m;
+    }
+}
+
+__global__ void k_pt2_bounds_ab(int n, const double *__restrict__ T, double *__restrict__ bab)
+{
+    const int64_t n2 = (int64_t)n * n;
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n2; u += (int64_t)gridDim.x * blockDim.x) {
+        double m = 0.0;
+        for (int64_t r = 0; r < n2; r++) m = fmax(m, fabs(T[u * n2 + r]));
+        bab[u] = m;
+    }
+}
+
 int grid_for(int64_t n)
 {
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, 152 * 8));
@@ -565,10 +624,12 @@ int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t
     double *S = nullptr, *small = nullptr;
     uint64_t *tab2 = nullptr;
     int rc = SCI_OK;
+    double *bnd_free = nullptr;   // the screening bounds, once allocated
     auto cleanup = [&]() {
         if (S) cudaFree(S);
         if (small) cudaFree(small);
         if (tab2) cudaFree(tab2);
+        if (bnd_free) cudaFree(bnd_free);
     };
     const size_t nsmall = (size_t)R * 3 + (size_t)norb * norb + norb + 1 + 2;
     if (cudaMalloc(&S, sizeof(double) * SC * std::max<int64_t>(1, M) * R) != cudaSuccess ||
@@ -629,6 +690,27 @@ int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t
     int tbits = 0;
     while (tbits < kMaxBits && total / (double)(1ull << tbits) > 0.6 * (double)cap) tbits++;
     Pt2 p{};
+    // screening bounds of the double-excitation classes (eps > 0 only)
+    double *bnd = nullptr;
+    if (eps > 0.0) {
+        const int64_t NP = (int64_t)n * (n - 1) / 2, nb3 = NP * n, nb2 = NP, nab = SPIN ? 0 : (int64_t)n * n;
+        if (cudaMalloc(&bnd, sizeof(double) * std::max<int64_t>(1, nb3 + nb2 + nab)) != cudaSuccess) {
+            cleanup();
+            return sci_fail(ctx, SCI_ERR_NOMEM, "enpt2: screening bounds");
+        }
+        bnd_free = bnd;
+        double *b3 = bnd, *b2 = bnd + nb3, *bab = b2 + nb2;
+        if constexpr (SPIN) {
+            k_pt2_bounds3<zdbl><<<grid_for(nb3), kThreads, 0, st>>>(n, (const zdbl *)ctx->tab, b3);
+        } else {
+            const double *T = (const double *)ctx->tab;
+            k_pt2_bounds3<double><<<grid_for(nb3), kThreads, 0, st>>>(n, T + (int64_t)n * n * n * n, b3);
+            k_pt2_bounds_pair<<<grid_for(nb2), kThreads, 0, st>>>(n, b3, b2);
+            k_pt2_bounds_ab<<<grid_for(nab), kThreads, 0, st>>>(n, T, bab);
+            p.bss = b2, p.bab = bab;
+        }
+        p.bss3 = b3;
+    }
     p.n = n, p.norb = norb, p.na = na, p.nb = nb, p.ref = ctx->ref;
     p.tab = (const double *)ctx->tab, p.fref = (const double *)ctx->fref, p.g_so = (const double *)ctx->g_so;
     p.fdiag = fdiag, p.G = G, p.Eref = Eref;

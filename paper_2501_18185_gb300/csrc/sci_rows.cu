@@ -17,6 +17,11 @@
 // Row costs (sci_row_costs) count, per row, the connected determinants: the off-diagonal
 // elements of that row of H, which set the row's share of the sigma work and balance
 // the ranges.
+//
+// The same file builds the row order of the deterministic accumulation
+// (sci_set_deterministic): each table's entries sorted by row with a stable radix sort (so
+// a row's entries come in ascending table position), and for each entry its position in
+// that order, where sigma stores the entry's row sum.
 #include <cub/cub.cuh>
 
 #include <algorithm>
@@ -187,7 +192,111 @@ template <typename T> void release(T *&p)
     p = nullptr;
 }
 
+__global__ void k_iota(uint32_t *v, int64_t n)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        v[t] = (uint32_t)t;
+}
+
+__global__ void k_row_count(const uint32_t *__restrict__ idx, int64_t n, uint32_t *__restrict__ cnt)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(cnt + idx[t], 1u);
+}
+
+__global__ void k_invert(const uint32_t *__restrict__ ent, int64_t n, uint32_t *__restrict__ inv)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        inv[ent[t]] = (uint32_t)t;
+}
+
+// The row order of one table: ptr = exclusive prefix sum of the per-row counts (M + 1),
+// inv[p] = the position of entry p among the entries sorted by row (a stable radix sort,
+// so ascending table position within a row)
+int row_index(sci_ctx *ctx, int64_t E, const uint32_t *e_idx, uint32_t *&ptr, uint32_t *&inv)
+{
+    cudaStream_t st = ctx->stream;
+    const int64_t M = ctx->M;
+    SCI_CK(cudaMalloc(&ptr, sizeof(uint32_t) * (M + 1)));
+    SCI_CK(cudaMalloc(&inv, sizeof(uint32_t) * (E > 0 ? E : 1)));
+    Tmp cnt, keys_out, vals_in, tmp, ent;
+    SCI_CK(cudaMalloc(&ent.p, sizeof(uint32_t) * (E > 0 ? E : 1)));
+    SCI_CK(cudaMalloc(&cnt.p, sizeof(uint32_t) * (M + 1)));
+    SCI_CK(cudaMemsetAsync(cnt.p, 0, sizeof(uint32_t) * (M + 1), st));
+    if (E > 0) {
+        k_row_count<<<grid_for(E), 256, 0, st>>>(e_idx, E, cnt.as<uint32_t>());
+        SCI_CK(cudaMalloc(&keys_out.p, sizeof(uint32_t) * E));
+        SCI_CK(cudaMalloc(&vals_in.p, sizeof(uint32_t) * E));
+        k_iota<<<grid_for(E), 256, 0, st>>>(vals_in.as<uint32_t>(), E);
+        SCI_CK(cudaGetLastError());
+        int bits = 1;
+        while (bits < 32 && ((int64_t)1 << bits) < M) bits++;
+        size_t tb = 0;
+        SCI_CK(cub::DeviceRadixSort::SortPairs(nullptr, tb, e_idx, keys_out.as<uint32_t>(), vals_in.as<uint32_t>(),
+                                               ent.as<uint32_t>(), (int)E, 0, bits, st));
+        SCI_CK(cudaMalloc(&tmp.p, tb ? tb : 16));
+        SCI_CK(cub::DeviceRadixSort::SortPairs(tmp.p, tb, e_idx, keys_out.as<uint32_t>(), vals_in.as<uint32_t>(),
+                                               ent.as<uint32_t>(), (int)E, 0, bits, st));
+        k_invert<<<grid_for(E), 256, 0, st>>>(ent.as<uint32_t>(), E, inv);
+        SCI_CK(cudaGetLastError());
+    }
+    size_t tb2 = 0;
+    Tmp tmp2;
+    SCI_CK(cub::DeviceScan::ExclusiveSum(nullptr, tb2, cnt.as<uint32_t>(), ptr, (int)(M + 1), st));
+    SCI_CK(cudaMalloc(&tmp2.p, tb2 ? tb2 : 16));
+    SCI_CK(cub::DeviceScan::ExclusiveSum(tmp2.p, tb2, cnt.as<uint32_t>(), ptr, (int)(M + 1), st));
+    SCI_CK(cudaStreamSynchronize(st));
+    ctx->det_bytes += sizeof(uint32_t) * (M + 1 + E);
+    return SCI_OK;
+}
+
 }  // namespace
+
+void sci_free_det(sci_ctx *ctx)
+{
+    release(ctx->det_ptr2);
+    release(ctx->det_inv2);
+    release(ctx->det_ptr1);
+    release(ctx->det_inv1);
+    release(ctx->det_part2);
+    release(ctx->det_part1);
+    ctx->bytes_held -= std::min(ctx->bytes_held, ctx->det_bytes);
+    ctx->det_bytes = 0;
+    ctx->det_nvec = 0;
+}
+
+extern "C" int sci_set_deterministic(sci_ctx *ctx, int max_nvec)
+{
+    if (!ctx) return SCI_ERR_ARG;
+    if (!ctx->have_dets) return sci_fail(ctx, SCI_ERR_STATE, "no determinants");
+    if (max_nvec < 0) return sci_fail(ctx, SCI_ERR_ARG, "max_nvec < 0");
+    if (ctx->ranged && max_nvec > 0) return sci_fail(ctx, SCI_ERR_STATE, "a row range is set");
+    SCI_CK(cudaSetDevice(ctx->device));
+    SCI_CK(cudaStreamSynchronize(ctx->stream));
+    sci_free_det(ctx);
+    if (max_nvec == 0) return SCI_OK;
+    const size_t sc = ctx->cplx ? 16 : 8;
+    int rc = row_index(ctx, ctx->e2, ctx->e2_idx, ctx->det_ptr2, ctx->det_inv2);
+    if (rc == SCI_OK) rc = row_index(ctx, ctx->e1, ctx->e1_idx, ctx->det_ptr1, ctx->det_inv1);
+    if (rc == SCI_OK) {
+        const size_t b2 = sc * max_nvec * (size_t)std::max<int64_t>(ctx->e2, 1);
+        const size_t b1 = sc * max_nvec * (size_t)std::max<int64_t>(ctx->e1, 1);
+        if (cudaMalloc(&ctx->det_part2, b2) != cudaSuccess || cudaMalloc(&ctx->det_part1, b1) != cudaSuccess) {
+            cudaGetLastError();
+            rc = sci_fail(ctx, SCI_ERR_NOMEM, "deterministic sigma: per-entry buffers");
+        } else {
+            ctx->det_bytes += b1 + b2;
+        }
+    }
+    if (rc != SCI_OK) {
+        ctx->det_bytes = 0;  // not yet counted in bytes_held
+        sci_free_det(ctx);
+        return rc;
+    }
+    ctx->bytes_held += ctx->det_bytes;
+    ctx->det_nvec = max_nvec;
+    return SCI_OK;
+}
 
 void sci_free_range(sci_ctx *ctx)
 {
@@ -210,6 +319,8 @@ extern "C" int sci_set_row_range(sci_ctx *ctx, int64_t row_begin, int64_t row_en
     if (!ctx->have_dets) return sci_fail(ctx, SCI_ERR_STATE, "no determinants");
     if (row_begin < 0 || row_end > ctx->M || row_begin > row_end)
         return sci_fail(ctx, SCI_ERR_ARG, "row range outside [0, M]");
+    if (ctx->det_nvec > 0 && !(row_begin == 0 && row_end == ctx->M))
+        return sci_fail(ctx, SCI_ERR_STATE, "deterministic mode is on");
     SCI_CK(cudaSetDevice(ctx->device));
     SCI_CK(cudaStreamSynchronize(ctx->stream));  // no launch in flight reads the old tables
     sci_free_range(ctx);

@@ -514,6 +514,7 @@ int build_buckets(sci_ctx *ctx, int holes, int per_det, Buckets &B)
 void free_dets(sci_ctx *ctx)
 {
     sci_free_range(ctx);
+    sci_free_det(ctx);
     free_held(ctx, ctx->keys);
     free_held(ctx, ctx->hdiag);
     free_held(ctx, ctx->fref);
@@ -908,6 +909,8 @@ extern "C" int sci_sigma(sci_ctx *ctx, const void *C, void *S, int nvec, int pre
         return sci_fail(ctx, SCI_ERR_ARG, "bad prec");
     if (prec == SCI_PREC_F32_STORE_F64_ACC && ctx->cplx)
         return sci_fail(ctx, SCI_ERR_ARG, "FP32 storage is available for real Hamiltonians only");
+    if (ctx->det_nvec > 0 && nvec > ctx->det_nvec)
+        return sci_fail(ctx, SCI_ERR_ARG, "nvec exceeds the deterministic mode's max_nvec");
     if (ctx->M == 0) return SCI_OK;
     if (!C || !S) return sci_fail(ctx, SCI_ERR_ARG, "C or S is NULL");
     SCI_CK(cudaSetDevice(ctx->device));
@@ -965,10 +968,10 @@ extern "C" int sci_profile(sci_ctx *ctx, int enable)
 
 extern "C" int sci_kernel_times(sci_ctx *ctx, float *ms, int n)
 {
-    if (!ctx || !ms || n < 0 || n > 3) return SCI_ERR_ARG;
-    if (!ctx->ev[3]) return sci_fail(ctx, SCI_ERR_STATE, "profiling was never enabled");
+    if (!ctx || !ms || n < 0 || n > 4) return SCI_ERR_ARG;
+    if (!ctx->ev[4]) return sci_fail(ctx, SCI_ERR_STATE, "profiling was never enabled");
     SCI_CK(cudaSetDevice(ctx->device));
-    SCI_CK(cudaEventSynchronize(ctx->ev[3]));
+    SCI_CK(cudaEventSynchronize(ctx->ev[4]));
     for (int i = 0; i < n; i++) SCI_CK(cudaEventElapsedTime(&ms[i], ctx->ev[i], ctx->ev[i + 1]));
     return SCI_OK;
 }

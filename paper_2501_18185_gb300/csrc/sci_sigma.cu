@@ -178,11 +178,11 @@ __global__ void k_sigma_init(const double *__restrict__ hdiag, const TC *__restr
 // TS: storage type of tab and staged coefficients; TA: accumulator (FP64 / complex128).
 // Shared memory per staged member: (ket code, ket table offset) as uint2, and its NV
 // coefficients times (-1)^pi.
-template <typename TS, typename TC, int NV, bool RANGED>
+template <typename TS, typename TC, int NV, bool RANGED, bool STORE = false>
 __global__ void __launch_bounds__(kThreads)
 k_doubles(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_code, const uint32_t *__restrict__ e_pos,
           int64_t E, int CH, sci::TabRule tr, const TS *__restrict__ tab, const TC *__restrict__ C, int nvec, int v0,
-          typename AccOf<TS>::type *__restrict__ Sout, sci::RowRange rr)
+          typename AccOf<TS>::type *__restrict__ Sout, sci::RowRange rr, const uint32_t *__restrict__ slot)
 {
     using TA = typename AccOf<TS>::type;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -259,10 +259,15 @@ k_doubles(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_cod
 #pragma unroll
             for (int v = 0; v < NV; v++) fma_acc(acc[v], t, s_c[m * NV + v]);
         }
-        const uint32_t idx = e_idx[r0 + q0];
         const bool par = sci::code_par(code);
+        if constexpr (STORE) {   // the row sum to this entry's slot (summed per row later)
 #pragma unroll
-        for (int v = 0; v < NV; v++) red_add(Sout + (int64_t)idx * nvec + v0 + v, flip(par, acc[v]));
+            for (int v = 0; v < NV; v++) Sout[(int64_t)slot[r0 + q0] * nvec + v0 + v] = flip(par, acc[v]);
+        } else {
+            const uint32_t idx = e_idx[r0 + q0];
+#pragma unroll
+            for (int v = 0; v < NV; v++) red_add(Sout + (int64_t)idx * nvec + v0 + v, flip(par, acc[v]));
+        }
     }
 }
 
@@ -315,12 +320,12 @@ __device__ __forceinline__ void ds_fma1(Ds &a, float t, float c)
 
 // FP32 storage: the pair table rounded to FP32 (tab32) and FP32 coefficients, exact
 // products, compensated bucket sums, FP64 accumulation into sigma
-template <int NV, bool RANGED>
+template <int NV, bool RANGED, bool STORE = false>
 __global__ void __launch_bounds__(kThreads, NV >= 8 ? SCI_F32_MINB : 1)
 k_doubles_f32(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_code,
               const uint32_t *__restrict__ e_pos, int64_t E, int CH, sci::TabRule tr,
               const float *__restrict__ tab32, const float *__restrict__ C, int nvec, int v0,
-              double *__restrict__ Sout, sci::RowRange rr)
+              double *__restrict__ Sout, sci::RowRange rr, const uint32_t *__restrict__ slot)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     int64_t r0, r1;
@@ -392,10 +397,15 @@ k_doubles_f32(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e
 #pragma unroll
             for (int v = 0; v < NV; v++) ds_fma1(acc[v], t, s_c[j * NV + v]);
         }
-        const uint32_t idx = e_idx[r0 + q0];
         const bool par = sci::code_par(code);
+        if constexpr (STORE) {
 #pragma unroll
-        for (int v = 0; v < NV; v++) red_add_nz(Sout + (int64_t)idx * nvec + v0 + v, flip(par, ds_value(acc[v])));
+            for (int v = 0; v < NV; v++) Sout[(int64_t)slot[r0 + q0] * nvec + v0 + v] = flip(par, ds_value(acc[v]));
+        } else {
+            const uint32_t idx = e_idx[r0 + q0];
+#pragma unroll
+            for (int v = 0; v < NV; v++) red_add_nz(Sout + (int64_t)idx * nvec + v0 + v, flip(par, ds_value(acc[v])));
+        }
     }
 }
 
@@ -410,12 +420,12 @@ __global__ void k_split_cz(const zdbl *__restrict__ C, int64_t M, int nvec, int 
 }
 
 // real: tab2 is the (hi, lo) split of the pair table, C2 the split vector group
-template <int NV, bool RANGED>
+template <int NV, bool RANGED, bool STORE = false>
 __global__ void __launch_bounds__(kThreads)
 k_doubles_ds(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_code,
              const uint32_t *__restrict__ e_pos, int64_t E, int CH, sci::TabRule tr,
              const float2 *__restrict__ tab2, const float2 *__restrict__ C2, int nvec, int v0,
-             double *__restrict__ Sout, sci::RowRange rr)
+             double *__restrict__ Sout, sci::RowRange rr, const uint32_t *__restrict__ slot)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     int64_t r0, r1;
@@ -488,20 +498,25 @@ k_doubles_ds(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_
 #pragma unroll
             for (int v = 0; v < NV; v++) ds_fma(acc[v], t, s_c[j * NV + v]);
         }
-        const uint32_t idx = e_idx[r0 + q0];
         const bool par = sci::code_par(code);
+        if constexpr (STORE) {
 #pragma unroll
-        for (int v = 0; v < NV; v++) red_add(Sout + (int64_t)idx * nvec + v0 + v, flip(par, ds_value(acc[v])));
+            for (int v = 0; v < NV; v++) Sout[(int64_t)slot[r0 + q0] * nvec + v0 + v] = flip(par, ds_value(acc[v]));
+        } else {
+            const uint32_t idx = e_idx[r0 + q0];
+#pragma unroll
+            for (int v = 0; v < NV; v++) red_add(Sout + (int64_t)idx * nvec + v0 + v, flip(par, ds_value(acc[v])));
+        }
     }
 }
 
 // complex: tab4 holds (re_hi, re_lo, im_hi, im_lo); C4 the split vector group
-template <int NV, bool RANGED>
+template <int NV, bool RANGED, bool STORE = false>
 __global__ void __launch_bounds__(kThreads)
 k_doubles_dsz(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_code,
               const uint32_t *__restrict__ e_pos, int64_t E, int CH, sci::TabRule tr,
               const float4 *__restrict__ tab4, const float4 *__restrict__ C4, int nvec, int v0, zdbl *__restrict__ Sout,
-              sci::RowRange rr)
+              sci::RowRange rr, const uint32_t *__restrict__ slot)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     int64_t r0, r1;
@@ -563,20 +578,26 @@ k_doubles_dsz(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e
 #pragma unroll
                 for (int v = 0; v < NV; v++) ds_renorm(ar[v]), ds_renorm(ai[v]);
         }
-        const uint32_t idx = e_idx[r0 + q0];
         const bool par = sci::code_par(code);
+        if constexpr (STORE) {
 #pragma unroll
-        for (int v = 0; v < NV; v++)
-            red_add(Sout + (int64_t)idx * nvec + v0 + v, flip(par, zdbl{ds_value(ar[v]), ds_value(ai[v])}));
+            for (int v = 0; v < NV; v++)
+                Sout[(int64_t)slot[r0 + q0] * nvec + v0 + v] = flip(par, zdbl{ds_value(ar[v]), ds_value(ai[v])});
+        } else {
+            const uint32_t idx = e_idx[r0 + q0];
+#pragma unroll
+            for (int v = 0; v < NV; v++)
+                red_add(Sout + (int64_t)idx * nvec + v0 + v, flip(par, zdbl{ds_value(ar[v]), ds_value(ai[v])}));
+        }
     }
 }
 
 // ------------------------------------------------------------------ singles
-template <typename TS, typename TC, int NV, bool RANGED>
+template <typename TS, typename TC, int NV, bool RANGED, bool STORE = false>
 __global__ void __launch_bounds__(kThreads)
 k_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S, const uint32_t *__restrict__ e_meta,
           int64_t E, int norb, uint64_t ref, const TS *__restrict__ fref, const TS *__restrict__ g_so,
-          const TC *__restrict__ C, int nvec, int v0, typename AccOf<TS>::type *__restrict__ Sout, sci::RowRange rr)
+          const TC *__restrict__ C, int nvec, int v0, typename AccOf<TS>::type *__restrict__ Sout, sci::RowRange rr, const uint32_t *__restrict__ slot)
 {
     using TA = typename AccOf<TS>::type;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
@@ -614,9 +635,14 @@ k_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S, 
 #pragma unroll
             for (int v = 0; v < NV; v++) fma_acc(acc[v], f, flip(parq, C[(int64_t)idxq * nvec + v0 + v]));
         }
-        const uint32_t idx = e_idx[p];
+        if constexpr (STORE) {
 #pragma unroll
-        for (int v = 0; v < NV; v++) red_add(Sout + (int64_t)idx * nvec + v0 + v, flip(par, acc[v]));
+            for (int v = 0; v < NV; v++) Sout[(int64_t)slot[p] * nvec + v0 + v] = flip(par, acc[v]);
+        } else {
+            const uint32_t idx = e_idx[p];
+#pragma unroll
+            for (int v = 0; v < NV; v++) red_add(Sout + (int64_t)idx * nvec + v0 + v, flip(par, acc[v]));
+        }
     }
 }
 
@@ -626,11 +652,11 @@ k_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S, 
 // the doubles.  C2/C4 is the split vector group (row stride NV).
 using sci::ds_add;
 
-template <int NV, bool RANGED>
+template <int NV, bool RANGED, bool STORE = false>
 __global__ void __launch_bounds__(kThreads)
 k_singles_ds(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S, const uint32_t *__restrict__ e_meta,
              int64_t E, int norb, uint64_t ref, const float2 *__restrict__ fref2, const float2 *__restrict__ g2,
-             const float2 *__restrict__ C2, int nvec, int v0, double *__restrict__ Sout, sci::RowRange rr)
+             const float2 *__restrict__ C2, int nvec, int v0, double *__restrict__ Sout, sci::RowRange rr, const uint32_t *__restrict__ slot)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
         if constexpr (RANGED) {
@@ -668,18 +694,23 @@ k_singles_ds(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_
 #pragma unroll
             for (int v = 0; v < NV; v++) ds_fma(acc[v], fv, flip(parq, C2[(int64_t)idxq * NV + v]));
         }
-        const uint32_t idx = e_idx[p];
+        if constexpr (STORE) {
 #pragma unroll
-        for (int v = 0; v < NV; v++) red_add(Sout + (int64_t)idx * nvec + v0 + v, flip(par, ds_value(acc[v])));
+            for (int v = 0; v < NV; v++) Sout[(int64_t)slot[p] * nvec + v0 + v] = flip(par, ds_value(acc[v]));
+        } else {
+            const uint32_t idx = e_idx[p];
+#pragma unroll
+            for (int v = 0; v < NV; v++) red_add(Sout + (int64_t)idx * nvec + v0 + v, flip(par, ds_value(acc[v])));
+        }
     }
 }
 
-template <int NV, bool RANGED>
+template <int NV, bool RANGED, bool STORE = false>
 __global__ void __launch_bounds__(kThreads)
 k_singles_dsz(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S,
               const uint32_t *__restrict__ e_meta, int64_t E, int norb, uint64_t ref,
               const float4 *__restrict__ fref4, const float4 *__restrict__ g4, const float4 *__restrict__ C4,
-              int nvec, int v0, zdbl *__restrict__ Sout, sci::RowRange rr)
+              int nvec, int v0, zdbl *__restrict__ Sout, sci::RowRange rr, const uint32_t *__restrict__ slot)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
         if constexpr (RANGED) {
@@ -730,10 +761,15 @@ k_singles_dsz(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e
                 ds_fma(ai[v], ti, cr);
             }
         }
-        const uint32_t idx = e_idx[p];
+        if constexpr (STORE) {
 #pragma unroll
-        for (int v = 0; v < NV; v++)
-            red_add(Sout + (int64_t)idx * nvec + v0 + v, flip(par, zdbl{ds_value(ar[v]), ds_value(ai[v])}));
+            for (int v = 0; v < NV; v++) Sout[(int64_t)slot[p] * nvec + v0 + v] = flip(par, zdbl{ds_value(ar[v]), ds_value(ai[v])});
+        } else {
+            const uint32_t idx = e_idx[p];
+#pragma unroll
+            for (int v = 0; v < NV; v++)
+                red_add(Sout + (int64_t)idx * nvec + v0 + v, flip(par, zdbl{ds_value(ar[v]), ds_value(ai[v])}));
+        }
     }
 }
 
@@ -790,7 +826,7 @@ Tabs tabs_of(const sci_ctx *ctx)
 // launch the row's slot in the owned-row list
 template <bool RG> constexpr size_t row_extra() { return RG ? 8 + sizeof(uint16_t) : 8; }
 
-template <bool RG, typename TS, typename TC, int NV>
+template <bool RG, bool ST, typename TS, typename TC, int NV>
 int launch_doubles(sci_ctx *ctx, const Tabs &T, const TS *tab, const TC *C, typename AccOf<TS>::type *S, int nvec,
                    int v0)
 {
@@ -799,17 +835,17 @@ int launch_doubles(sci_ctx *ctx, const Tabs &T, const TS *tab, const TC *C, type
     size_t smem = 0;
     int ch = choose_rows(ctx->maxb2, per, smem);
     if (ch < 0) return sci_fail(ctx, SCI_ERR_OVERFLOW, "bucket too large for shared memory");
-    auto kern = k_doubles<TS, TC, NV, RG>;
+    auto kern = k_doubles<TS, TC, NV, RG, ST>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return sci_cuda_check(ctx, e, "cudaFuncSetAttribute");
     int64_t blocks = (T.e2 + ch - 1) / ch;
     kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(T.e2_idx, T.e2_code, T.e2_pos, T.e2, ch, tab_rule(ctx), tab,
-                                                          C, nvec, v0, S, T.rr);
+                                                          C, nvec, v0, S, T.rr, ST ? ctx->det_inv2 : nullptr);
     return sci_cuda_check(ctx, cudaGetLastError(), "k_doubles launch");
 }
 
 // paired-FP32 doubles: real (float2 table, float2 staged c) or complex (float4 / float4)
-template <bool RG, bool CPLX, int NV>
+template <bool RG, bool ST, bool CPLX, int NV>
 int launch_doubles_ds(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int nvec, int v0)
 {
     if (T.e2 == 0) return SCI_OK;
@@ -828,24 +864,24 @@ int launch_doubles_ds(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int n
         k_split_c<<<grid_for(ctx->M * NV), kThreads, 0, ctx->stream>>>((const double *)C, ctx->M, nvec, v0, NV,
                                                                        (float2 *)ctx->c_ds);
     if constexpr (CPLX) {
-        auto kern = k_doubles_dsz<NV, RG>;
+        auto kern = k_doubles_dsz<NV, RG, ST>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return sci_cuda_check(ctx, e, "cudaFuncSetAttribute");
         kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(T.e2_idx, T.e2_code, T.e2_pos, T.e2, ch, tab_rule(ctx),
                                                               (const float4 *)ctx->tab_ds, (const float4 *)ctx->c_ds,
-                                                              nvec, v0, (zdbl *)S, T.rr);
+                                                              nvec, v0, (zdbl *)S, T.rr, ST ? ctx->det_inv2 : nullptr);
     } else {
-        auto kern = k_doubles_ds<NV, RG>;
+        auto kern = k_doubles_ds<NV, RG, ST>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return sci_cuda_check(ctx, e, "cudaFuncSetAttribute");
         kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(T.e2_idx, T.e2_code, T.e2_pos, T.e2, ch, tab_rule(ctx),
                                                               (const float2 *)ctx->tab_ds, (const float2 *)ctx->c_ds,
-                                                              nvec, v0, (double *)S, T.rr);
+                                                              nvec, v0, (double *)S, T.rr, ST ? ctx->det_inv2 : nullptr);
     }
     return sci_cuda_check(ctx, cudaGetLastError(), "k_doubles_ds launch");
 }
 
-template <bool RG, bool CPLX>
+template <bool RG, bool ST, bool CPLX>
 int ds_groups(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int nvec)
 {
     int rc = SCI_OK;
@@ -857,10 +893,10 @@ int ds_groups(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int nvec)
         size_t smem_probe = 0;
         while (g > 1 && choose_rows(ctx->maxb2, g * unit + row_extra<RG>(), smem_probe) < 0) g >>= 1;
         switch (g) {
-        case 8: rc = launch_doubles_ds<RG, CPLX, 8>(ctx, T, C, S, nvec, v0); break;
-        case 4: rc = launch_doubles_ds<RG, CPLX, 4>(ctx, T, C, S, nvec, v0); break;
-        case 2: rc = launch_doubles_ds<RG, CPLX, 2>(ctx, T, C, S, nvec, v0); break;
-        default: rc = launch_doubles_ds<RG, CPLX, 1>(ctx, T, C, S, nvec, v0); break;
+        case 8: rc = launch_doubles_ds<RG, ST, CPLX, 8>(ctx, T, C, S, nvec, v0); break;
+        case 4: rc = launch_doubles_ds<RG, ST, CPLX, 4>(ctx, T, C, S, nvec, v0); break;
+        case 2: rc = launch_doubles_ds<RG, ST, CPLX, 2>(ctx, T, C, S, nvec, v0); break;
+        default: rc = launch_doubles_ds<RG, ST, CPLX, 1>(ctx, T, C, S, nvec, v0); break;
         }
         v0 += g;
     }
@@ -868,7 +904,7 @@ int ds_groups(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int nvec)
 }
 
 // FP32-storage doubles (SCI_PREC_F32_STORE_F64_ACC)
-template <bool RG, int NV>
+template <bool RG, bool ST, int NV>
 int launch_doubles_f32(sci_ctx *ctx, const Tabs &T, const float *C, double *S, int nvec, int v0)
 {
     if (T.e2 == 0) return SCI_OK;
@@ -877,15 +913,15 @@ int launch_doubles_f32(sci_ctx *ctx, const Tabs &T, const float *C, double *S, i
     int ch = choose_rows(ctx->maxb2, per, smem, NV >= 8 ? SCI_F32_ROWS : kRowsPerCta);
     if (ch < 0) return sci_fail(ctx, SCI_ERR_OVERFLOW, "bucket too large for shared memory");
     int64_t blocks = (T.e2 + ch - 1) / ch;
-    auto kern = k_doubles_f32<NV, RG>;
+    auto kern = k_doubles_f32<NV, RG, ST>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return sci_cuda_check(ctx, e, "cudaFuncSetAttribute");
     kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(T.e2_idx, T.e2_code, T.e2_pos, T.e2, ch, tab_rule(ctx),
-                                                          ctx->tab32, C, nvec, v0, S, T.rr);
+                                                          ctx->tab32, C, nvec, v0, S, T.rr, ST ? ctx->det_inv2 : nullptr);
     return sci_cuda_check(ctx, cudaGetLastError(), "k_doubles_f32 launch");
 }
 
-template <bool RG>
+template <bool RG, bool ST>
 int f32_groups(sci_ctx *ctx, const Tabs &T, const float *C, double *S, int nvec)
 {
     int rc = SCI_OK;
@@ -895,10 +931,10 @@ int f32_groups(sci_ctx *ctx, const Tabs &T, const float *C, double *S, int nvec)
         size_t smem_probe = 0;
         while (g > 1 && choose_rows(ctx->maxb2, g * sizeof(float) + row_extra<RG>(), smem_probe) < 0) g >>= 1;
         switch (g) {
-        case 8: rc = launch_doubles_f32<RG, 8>(ctx, T, C, S, nvec, v0); break;
-        case 4: rc = launch_doubles_f32<RG, 4>(ctx, T, C, S, nvec, v0); break;
-        case 2: rc = launch_doubles_f32<RG, 2>(ctx, T, C, S, nvec, v0); break;
-        default: rc = launch_doubles_f32<RG, 1>(ctx, T, C, S, nvec, v0); break;
+        case 8: rc = launch_doubles_f32<RG, ST, 8>(ctx, T, C, S, nvec, v0); break;
+        case 4: rc = launch_doubles_f32<RG, ST, 4>(ctx, T, C, S, nvec, v0); break;
+        case 2: rc = launch_doubles_f32<RG, ST, 2>(ctx, T, C, S, nvec, v0); break;
+        default: rc = launch_doubles_f32<RG, ST, 1>(ctx, T, C, S, nvec, v0); break;
         }
         v0 += g;
     }
@@ -906,7 +942,7 @@ int f32_groups(sci_ctx *ctx, const Tabs &T, const float *C, double *S, int nvec)
 }
 
 // paired-FP32 singles; real coefficients may come in as double or float
-template <bool RG, bool CPLX, int NV, typename TC = double>
+template <bool RG, bool ST, bool CPLX, int NV, typename TC = double>
 int launch_singles_ds(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int nvec, int v0)
 {
     if (T.e1 == 0) return SCI_OK;
@@ -914,20 +950,21 @@ int launch_singles_ds(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int n
     if constexpr (CPLX) {
         k_split_cz<<<grid_for(ctx->M * NV), kThreads, 0, ctx->stream>>>((const zdbl *)C, ctx->M, nvec, v0, NV,
                                                                         (float4 *)ctx->c_ds);
-        k_singles_dsz<NV, RG><<<g, kThreads, 0, ctx->stream>>>(T.e1_idx, T.e1_S, T.e1_meta, T.e1, ctx->norb, ctx->ref,
+        k_singles_dsz<NV, RG, ST><<<g, kThreads, 0, ctx->stream>>>(T.e1_idx, T.e1_S, T.e1_meta, T.e1, ctx->norb, ctx->ref,
                                                                (const float4 *)ctx->fref_ds, (const float4 *)ctx->g_ds,
-                                                               (const float4 *)ctx->c_ds, nvec, v0, (zdbl *)S, T.rr);
+                                                               (const float4 *)ctx->c_ds, nvec, v0, (zdbl *)S, T.rr,
+                                                               ST ? ctx->det_inv1 : nullptr);
     } else {
         k_split_c<TC><<<grid_for(ctx->M * NV), kThreads, 0, ctx->stream>>>((const TC *)C, ctx->M, nvec, v0, NV,
                                                                            (float2 *)ctx->c_ds);
-        k_singles_ds<NV, RG><<<g, kThreads, 0, ctx->stream>>>(T.e1_idx, T.e1_S, T.e1_meta, T.e1, ctx->norb, ctx->ref,
+        k_singles_ds<NV, RG, ST><<<g, kThreads, 0, ctx->stream>>>(T.e1_idx, T.e1_S, T.e1_meta, T.e1, ctx->norb, ctx->ref,
                                                               (const float2 *)ctx->fref_ds, (const float2 *)ctx->g_ds,
-                                                              (const float2 *)ctx->c_ds, nvec, v0, (double *)S, T.rr);
+                                                              (const float2 *)ctx->c_ds, nvec, v0, (double *)S, T.rr, ST ? ctx->det_inv1 : nullptr);
     }
     return sci_cuda_check(ctx, cudaGetLastError(), "k_singles_ds launch");
 }
 
-template <bool RG, bool CPLX, typename TC = double>
+template <bool RG, bool ST, bool CPLX, typename TC = double>
 int ds_singles_groups(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int nvec)
 {
     int rc = SCI_OK;
@@ -936,27 +973,27 @@ int ds_singles_groups(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int n
         int g = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
         if (CPLX && g > 4) g = 4;
         switch (g) {
-        case 8: rc = launch_singles_ds<RG, CPLX, 8, TC>(ctx, T, C, S, nvec, v0); break;
-        case 4: rc = launch_singles_ds<RG, CPLX, 4, TC>(ctx, T, C, S, nvec, v0); break;
-        case 2: rc = launch_singles_ds<RG, CPLX, 2, TC>(ctx, T, C, S, nvec, v0); break;
-        default: rc = launch_singles_ds<RG, CPLX, 1, TC>(ctx, T, C, S, nvec, v0); break;
+        case 8: rc = launch_singles_ds<RG, ST, CPLX, 8, TC>(ctx, T, C, S, nvec, v0); break;
+        case 4: rc = launch_singles_ds<RG, ST, CPLX, 4, TC>(ctx, T, C, S, nvec, v0); break;
+        case 2: rc = launch_singles_ds<RG, ST, CPLX, 2, TC>(ctx, T, C, S, nvec, v0); break;
+        default: rc = launch_singles_ds<RG, ST, CPLX, 1, TC>(ctx, T, C, S, nvec, v0); break;
         }
         v0 += g;
     }
     return rc;
 }
 
-template <bool RG, typename TS, typename TC, int NV>
+template <bool RG, bool ST, typename TS, typename TC, int NV>
 int launch_singles(sci_ctx *ctx, const Tabs &T, const TC *C, typename AccOf<TS>::type *S, int nvec, int v0)
 {
     if (T.e1 == 0) return SCI_OK;
-    k_singles<TS, TC, NV, RG><<<grid_for(T.e1), kThreads, 0, ctx->stream>>>(
+    k_singles<TS, TC, NV, RG, ST><<<grid_for(T.e1), kThreads, 0, ctx->stream>>>(
         T.e1_idx, T.e1_S, T.e1_meta, T.e1, ctx->norb, ctx->ref, (const TS *)ctx->fref, (const TS *)ctx->g_so, C, nvec,
-        v0, S, T.rr);
+        v0, S, T.rr, ST ? ctx->det_inv1 : nullptr);
     return sci_cuda_check(ctx, cudaGetLastError(), "k_singles launch");
 }
 
-template <bool RG, typename TS, typename TC>
+template <bool RG, bool ST, typename TS, typename TC>
 int sigma_groups(sci_ctx *ctx, const Tabs &T, const TS *tab, const TC *C, typename AccOf<TS>::type *S, int nvec)
 {
     int rc = SCI_OK;
@@ -967,17 +1004,17 @@ int sigma_groups(sci_ctx *ctx, const Tabs &T, const TS *tab, const TC *C, typena
         size_t smem_probe = 0;  // shrink the vector group until its window fits
         while (g > 1 && choose_rows(ctx->maxb2, g * sizeof(TS) + row_extra<RG>(), smem_probe) < 0) g >>= 1;
         switch (g) {
-        case 8: rc = launch_doubles<RG, TS, TC, 8>(ctx, T, tab, C, S, nvec, v0); break;
-        case 4: rc = launch_doubles<RG, TS, TC, 4>(ctx, T, tab, C, S, nvec, v0); break;
-        case 2: rc = launch_doubles<RG, TS, TC, 2>(ctx, T, tab, C, S, nvec, v0); break;
-        default: rc = launch_doubles<RG, TS, TC, 1>(ctx, T, tab, C, S, nvec, v0); break;
+        case 8: rc = launch_doubles<RG, ST, TS, TC, 8>(ctx, T, tab, C, S, nvec, v0); break;
+        case 4: rc = launch_doubles<RG, ST, TS, TC, 4>(ctx, T, tab, C, S, nvec, v0); break;
+        case 2: rc = launch_doubles<RG, ST, TS, TC, 2>(ctx, T, tab, C, S, nvec, v0); break;
+        default: rc = launch_doubles<RG, ST, TS, TC, 1>(ctx, T, tab, C, S, nvec, v0); break;
         }
         v0 += g;
     }
     return rc;
 }
 
-template <bool RG, typename TS, typename TC>
+template <bool RG, bool ST, typename TS, typename TC>
 int singles_groups(sci_ctx *ctx, const Tabs &T, const TC *C, typename AccOf<TS>::type *S, int nvec)
 {
     int rc = SCI_OK;
@@ -985,9 +1022,9 @@ int singles_groups(sci_ctx *ctx, const Tabs &T, const TC *C, typename AccOf<TS>:
         int left = nvec - v0;
         int g = left >= 4 ? 4 : left >= 2 ? 2 : 1;
         switch (g) {
-        case 4: rc = launch_singles<RG, TS, TC, 4>(ctx, T, C, S, nvec, v0); break;
-        case 2: rc = launch_singles<RG, TS, TC, 2>(ctx, T, C, S, nvec, v0); break;
-        default: rc = launch_singles<RG, TS, TC, 1>(ctx, T, C, S, nvec, v0); break;
+        case 4: rc = launch_singles<RG, ST, TS, TC, 4>(ctx, T, C, S, nvec, v0); break;
+        case 2: rc = launch_singles<RG, ST, TS, TC, 2>(ctx, T, C, S, nvec, v0); break;
+        default: rc = launch_singles<RG, ST, TS, TC, 1>(ctx, T, C, S, nvec, v0); break;
         }
         v0 += g;
     }
@@ -1097,10 +1134,103 @@ bool sci_sigma_window_fits(const sci_ctx *ctx)
 
 namespace {
 
-// one sigma launch sequence over the tables T (RG: the rows of a row range only)
-template <bool RG>
-int launch_sigma(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int nvec, int prec)
+// Deterministic accumulation: S_I = H_II C_I + the row sums the double- and single-
+// excitation kernels stored for row I's bucket entries.  They store them in row order (the
+// slot of an entry is its position among the entries sorted by row), so row I's sums are
+// the contiguous segment [ptr[I], ptr[I + 1]).  One warp per row: lane l adds the segment's
+// elements l, l + 32, ..., then the lanes are combined by a fixed butterfly of shuffles,
+// so the result does not depend on scheduling.
+__device__ __forceinline__ void add_to(double &a, double b) { a += b; }
+__device__ __forceinline__ void add_to(zdbl &a, zdbl b) { a.x += b.x, a.y += b.y; }
+__device__ __forceinline__ double shfl_xor(double a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+__device__ __forceinline__ zdbl shfl_xor(zdbl a, int o)
 {
+    return zdbl{__shfl_xor_sync(0xffffffffu, a.x, o), __shfl_xor_sync(0xffffffffu, a.y, o)};
+}
+__device__ __forceinline__ double diag_times(double h, double c) { return h * c; }
+__device__ __forceinline__ double diag_times(double h, float c) { return h * (double)c; }
+__device__ __forceinline__ zdbl diag_times(double h, zdbl c) { return zdbl{h * c.x, h * c.y}; }
+
+template <typename TC, typename TA, int NV>
+__global__ void __launch_bounds__(kThreads)
+k_row_sums(int64_t M, int nvec, int v0, const double *__restrict__ hdiag, const TC *__restrict__ C,
+           const uint32_t *__restrict__ ptr2, const TA *__restrict__ part2, const uint32_t *__restrict__ ptr1,
+           const TA *__restrict__ part1, TA *__restrict__ S)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (kThreads / 32);
+    for (int64_t I = ((int64_t)blockIdx.x * kThreads + threadIdx.x) / 32; I < M; I += warps) {
+        TA acc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) zero(acc[v]);
+        // the row's doubles slots, then its singles slots; four slots per lane in flight
+        // per step (loaded before they are added), each lane adding its own slots in order
+        for (int tab = 0; tab < 2; tab++) {
+            const uint32_t *ptr = tab ? ptr1 : ptr2;
+            const TA *part = tab ? part1 : part2;
+            const uint32_t end = ptr[I + 1];
+            for (uint32_t t0 = ptr[I] + lane; t0 < end; t0 += 4 * 32) {
+                TA x[4][NV];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const uint32_t t = t0 + 32u * u;
+                    const TA *src = part + (int64_t)t * nvec + v0;
+#pragma unroll
+                    for (int v = 0; v < NV; v++) {
+                        zero(x[u][v]);
+                        if (t < end) x[u][v] = src[v];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+#pragma unroll
+                    for (int v = 0; v < NV; v++) add_to(acc[v], x[u][v]);
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < NV; v++)
+            for (int o = 16; o; o >>= 1) add_to(acc[v], shfl_xor(acc[v], o));
+        if (lane < NV) {
+            TA out = diag_times(hdiag[I], C[I * nvec + v0 + lane]);
+#pragma unroll
+            for (int v = 0; v < NV; v++)
+                if (v == lane) add_to(out, acc[v]);
+            S[I * nvec + v0 + lane] = out;
+        }
+    }
+}
+
+template <typename TC, typename TA>
+int row_sums(sci_ctx *ctx, const TC *C, TA *S, int nvec)
+{
+    const int64_t M = ctx->M;
+    const int grid = grid_for(M * 32);
+    auto go = [&](auto kern, int v0) {
+        kern<<<grid, kThreads, 0, ctx->stream>>>(M, nvec, v0, ctx->hdiag, C, ctx->det_ptr2, (const TA *)ctx->det_part2,
+                                                 ctx->det_ptr1, (const TA *)ctx->det_part1, S);
+    };
+    for (int v0 = 0; v0 < nvec;) {
+        const int left = nvec - v0;
+        const int g = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+        switch (g) {
+        case 8: go(k_row_sums<TC, TA, 8>, v0); break;
+        case 4: go(k_row_sums<TC, TA, 4>, v0); break;
+        case 2: go(k_row_sums<TC, TA, 2>, v0); break;
+        default: go(k_row_sums<TC, TA, 1>, v0); break;
+        }
+        v0 += g;
+    }
+    return sci_cuda_check(ctx, cudaGetLastError(), "k_row_sums launch");
+}
+
+// one sigma launch sequence over the tables T (RG: the rows of a row range only; ST: the
+// deterministic accumulation, row sums stored in the entries' slots, then per-row sums)
+template <bool RG, bool ST>
+int launch_sigma(sci_ctx *ctx, const Tabs &T, const void *C, void *S_out, int nvec, int prec)
+{
+    // with ST the double- and single-excitation kernels write the slots, not S
+    void *S = ST ? ctx->det_part2 : S_out;
+    void *S1 = ST ? ctx->det_part1 : S_out;
     cudaStream_t st = ctx->stream;
     const int64_t row0 = T.rr.rb, nrows = T.rr.re - T.rr.rb;
     int rc;
@@ -1108,45 +1238,51 @@ int launch_sigma(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int nvec, 
     if (ctx->cplx) {
         const zdbl *Cz = (const zdbl *)C;
         zdbl *Sz = (zdbl *)S;
-        if (nrows > 0)
+        if (!ST && nrows > 0)
             k_sigma_init<zdbl, zdbl><<<grid_for(nrows * nvec), kThreads, 0, st>>>(ctx->hdiag, Cz, Sz, row0, nrows, nvec);
         SCI_CK(cudaGetLastError());
         mark(ctx, 1);
-        rc = prec == SCI_PREC_F64_DS ? ds_groups<RG, true>(ctx, T, C, S, nvec)
-                                     : sigma_groups<RG, zdbl, zdbl>(ctx, T, (const zdbl *)ctx->tab, Cz, Sz, nvec);
+        rc = prec == SCI_PREC_F64_DS ? ds_groups<RG, ST, true>(ctx, T, C, S, nvec)
+                                     : sigma_groups<RG, ST, zdbl, zdbl>(ctx, T, (const zdbl *)ctx->tab, Cz, Sz, nvec);
         mark(ctx, 2);
         if (rc == SCI_OK)
-            rc = prec == SCI_PREC_F64_DS ? ds_singles_groups<RG, true>(ctx, T, C, S, nvec)
-                                         : singles_groups<RG, zdbl, zdbl>(ctx, T, Cz, Sz, nvec);
+            rc = prec == SCI_PREC_F64_DS ? ds_singles_groups<RG, ST, true>(ctx, T, C, S1, nvec)
+                                         : singles_groups<RG, ST, zdbl, zdbl>(ctx, T, Cz, (zdbl *)S1, nvec);
         mark(ctx, 3);
+        if (ST && rc == SCI_OK) rc = row_sums<zdbl, zdbl>(ctx, Cz, (zdbl *)S_out, nvec);
+        mark(ctx, 4);
         return rc;
     }
     double *Sd = (double *)S;
     if (prec == SCI_PREC_F64 || prec == SCI_PREC_F64_DS) {
         const double *Cd = (const double *)C;
-        if (nrows > 0)
+        if (!ST && nrows > 0)
             k_sigma_init<double, double><<<grid_for(nrows * nvec), kThreads, 0, st>>>(ctx->hdiag, Cd, Sd, row0, nrows,
                                                                                        nvec);
         SCI_CK(cudaGetLastError());
         mark(ctx, 1);
-        rc = prec == SCI_PREC_F64_DS ? ds_groups<RG, false>(ctx, T, C, S, nvec)
-                                     : sigma_groups<RG, double, double>(ctx, T, (const double *)ctx->tab, Cd, Sd, nvec);
+        rc = prec == SCI_PREC_F64_DS ? ds_groups<RG, ST, false>(ctx, T, C, S, nvec)
+                                     : sigma_groups<RG, ST, double, double>(ctx, T, (const double *)ctx->tab, Cd, Sd, nvec);
         mark(ctx, 2);
         if (rc == SCI_OK)
-            rc = prec == SCI_PREC_F64_DS ? ds_singles_groups<RG, false>(ctx, T, C, S, nvec)
-                                         : singles_groups<RG, double, double>(ctx, T, Cd, Sd, nvec);
+            rc = prec == SCI_PREC_F64_DS ? ds_singles_groups<RG, ST, false>(ctx, T, C, S1, nvec)
+                                         : singles_groups<RG, ST, double, double>(ctx, T, Cd, (double *)S1, nvec);
         mark(ctx, 3);
+        if (ST && rc == SCI_OK) rc = row_sums<double, double>(ctx, Cd, (double *)S_out, nvec);
+        mark(ctx, 4);
         return rc;
     }
     const float *Cf = (const float *)C;
-    if (nrows > 0)
+    if (!ST && nrows > 0)
         k_sigma_init<float, double><<<grid_for(nrows * nvec), kThreads, 0, st>>>(ctx->hdiag, Cf, Sd, row0, nrows, nvec);
     SCI_CK(cudaGetLastError());
     mark(ctx, 1);
-    rc = f32_groups<RG>(ctx, T, Cf, Sd, nvec);
+    rc = f32_groups<RG, ST>(ctx, T, Cf, Sd, nvec);
     mark(ctx, 2);
-    if (rc == SCI_OK) rc = ds_singles_groups<RG, false, float>(ctx, T, C, S, nvec);
+    if (rc == SCI_OK) rc = ds_singles_groups<RG, ST, false, float>(ctx, T, C, S1, nvec);
     mark(ctx, 3);
+    if (ST && rc == SCI_OK) rc = row_sums<float, double>(ctx, Cf, (double *)S_out, nvec);
+    mark(ctx, 4);
     return rc;
 }
 
@@ -1159,9 +1295,10 @@ int sci_launch_sigma(sci_ctx *ctx, const void *C, void *S, int nvec, int prec, b
         ctx->ranged = 0;   // tabs_of: the full tables
         const Tabs T = tabs_of(ctx);
         ctx->ranged = ranged;
-        return launch_sigma<false>(ctx, T, C, S, nvec, prec);
+        if (ctx->det_nvec > 0 && nvec <= ctx->det_nvec) return launch_sigma<false, true>(ctx, T, C, S, nvec, prec);
+        return launch_sigma<false, false>(ctx, T, C, S, nvec, prec);
     }
-    return launch_sigma<true>(ctx, tabs_of(ctx), C, S, nvec, prec);
+    return launch_sigma<true, false>(ctx, tabs_of(ctx), C, S, nvec, prec);
 }
 
 int sci_count_pairs_device(sci_ctx *ctx, int64_t *pairs2, int64_t *pairs1)

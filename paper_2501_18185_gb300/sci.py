@@ -42,6 +42,7 @@ SIGNATURES = {
     "sci_sigma": (_i32, [_vp, _vp, _vp, _i32, _i32]),
     "sci_set_row_range": (_i32, [_vp, _i64, _i64]),
     "sci_row_costs": (_i32, [_vp, _vp]),
+    "sci_set_deterministic": (_i32, [_vp, _i32]),
     "sci_connections": (_i32, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _i64]),
     "sci_connections_noalloc": (_i32, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _i64]),
     "sci_count_pairs": (_i32, [_vp, _vp]),
@@ -159,6 +160,10 @@ def sci_set_row_range(ctx, row_begin, row_end):
     return _check(ctx, load().sci_set_row_range(ctx, int(row_begin), int(row_end)))
 
 
+def sci_set_deterministic(ctx, max_nvec: int):
+    return _check(ctx, load().sci_set_deterministic(ctx, int(max_nvec)))
+
+
 def sci_row_costs(ctx, cost):
     return _check(ctx, load().sci_row_costs(ctx, _p(cost)))
 
@@ -215,9 +220,9 @@ def sci_profile(ctx, enable: bool):
     return _check(ctx, load().sci_profile(ctx, int(enable)))
 
 
-def sci_kernel_times(ctx) -> list:
-    ms = np.zeros(3, dtype=np.float32)
-    _check(ctx, load().sci_kernel_times(ctx, _p(ms), 3))
+def sci_kernel_times(ctx, n: int = 3) -> list:
+    ms = np.zeros(n, dtype=np.float32)
+    _check(ctx, load().sci_kernel_times(ctx, _p(ms), n))
     return [float(x) for x in ms]
 
 
@@ -475,6 +480,11 @@ class Hamiltonian:
         of S are left as they were); (0, M) returns to the whole list."""
         sci_set_row_range(self.ctx, row_begin, row_end)
         self.row_range = (int(row_begin), int(row_end))
+
+    def set_deterministic(self, max_nvec: int):
+        """Later sigma calls with up to max_nvec vectors accumulate row sums in a fixed
+        order (bitwise reproducible S); 0 returns to FP64 atomics."""
+        sci_set_deterministic(self.ctx, max_nvec)
 
     def row_costs(self):
         """Per-row count of connected determinants (torch int64 on the device)."""

@@ -182,3 +182,27 @@ def test_enpt2_64_spinor_space_matches_oracle(gpu, cut64, nroots):
     e2w_b, e2p_b, e2q_b, st_b = H.enpt2(Ct, E0[:nroots], table_bytes=(1 << 20) * (8 + 16 * nroots))
     assert st_b["batches"] > st["batches"] and st_b["distinct_W"] == st["distinct_W"]
     assert np.allclose(e2q_b, E2[:nroots], rtol=1e-10, atol=0)
+
+
+@pytest.mark.parametrize("which,eps", [("30o", 1e-6), ("30o", 1e-4), ("64s", 1e-5)])
+def test_enpt2_screening_matches_screened_oracle(gpu, which, eps):
+    """Screening (eps > 0): the GPU skips whole double-excitation classes by upper bounds
+    of their elements (the paper's Table 1 screening) and drops single contributions below
+    eps, so its E2[W] is the sum over W with the per-element rule |H_IJ| max_k |c_Jk| < eps
+    applied to every contribution (the oracle's over-W sum with that rule, at 1e-10, with
+    the same number of distinct determinants), while E2[P] stays exact (Eq. EP1).  The
+    screening drops a real share of W."""
+    torch = gpu
+    w = W.selected_30o_cut(1000) if which == "30o" else W.selected_spinor_64_cut()
+    o = Oracle.from_workload(w)
+    ev, U = np.linalg.eigh(o.dense())
+    C, E0 = U[:, :2].copy(), ev[:2].copy()
+    refW, n_w = o.enpt2(C, E0, eps=eps, over_w=True)
+    H = sci.Hamiltonian.from_workload(w)
+    Ct = torch.from_numpy(C).cuda()
+    e2w, e2p, e2q, st = H.enpt2(Ct, E0, eps=eps)
+    x2w, x2p, x2q, xst = H.enpt2(Ct, E0)
+    assert np.allclose(e2w, refW, rtol=1e-10, atol=0), (e2w, refW)
+    assert st["distinct_W"] == n_w
+    assert np.allclose(e2p, x2p, rtol=1e-13)                                   # E2[P] unscreened
+    assert st["distinct_W"] < xst["distinct_W"] and np.all(np.abs(e2q - x2q) < 0.05 * np.abs(x2q))

@@ -147,3 +147,61 @@ def test_sciref_enpt2_thread_count_does_not_change_the_sum():
         set_threads(0)
     b, nb_ = o.enpt2(w.c, E0)
     assert np.array_equal(a, b) and na_ == nb_
+
+
+@pytest.mark.parametrize("mode,n,na,nb,frac", [("spin_orbitals", 6, 3, 2, 0.3), ("spinors", 8, 3, 0, 0.3)])
+def test_sciref_enpt2_screening_matches_masked_literal_route(mode, n, na, nb, frac):
+    """With eps > 0 a contribution H_IJ c_J is dropped when |H_IJ| max_k |c_Jk| < eps: the
+    same rule applied as a mask to the dense H of the literal operator route.  eps = 0 is
+    the exact sum, a huge eps leaves nothing."""
+    w = W.random_small(291 + n, mode, n, na, nb, naux=4, frac=frac, nvec=2)
+    h, eri = w.ints.h, w.ints.eri()
+    o = Oracle.from_workload(w)
+    E0 = np.array([-20.0, -18.5])
+    full = PT.full_space_keys(mode, n, na, 0 if mode == "spinors" else nb)
+    Hd = F.hamiltonian(full, h, eri) if mode == "spinors" else F.hamiltonian(full, *F.spin_orbital_integrals(h, eri))
+    pos = np.searchsorted(full, w.keys)
+    q = np.setdiff1d(np.arange(len(full)), pos)
+    HQP = Hd[np.ix_(q, pos)]
+    cmax = np.abs(w.c).max(axis=1)
+    for eps in (0.0, 1e-3, 3e-2):
+        keep = np.abs(HQP) * cmax[None, :] >= eps if eps > 0 else np.ones(HQP.shape, dtype=bool)
+        num = (HQP * keep) @ w.c
+        ref = (np.abs(num) ** 2 / (E0[None, :] - np.real(np.diag(Hd))[q][:, None])).sum(0)
+        nref = int((keep & (HQP != 0)).any(axis=1).sum()) if eps > 0 else None
+        got, nx = o.enpt2(w.c, E0, eps=eps)
+        assert np.allclose(got, ref, rtol=1e-12, atol=1e-15), eps
+        if eps > 0:
+            assert nx == nref
+    got, nx = o.enpt2(w.c, E0, eps=1e9)
+    assert nx == 0 and np.all(got == 0)
+
+
+@pytest.mark.parametrize("mode,n,na,nb,frac", [("spin_orbitals", 6, 3, 2, 0.3), ("spinors", 8, 3, 0, 0.3)])
+def test_sciref_enpt2_over_w_is_eq_ew1(mode, n, na, nb, frac):
+    """over_w: the sum over W (members of the list included, numerators over the other
+    members) against the dense literal route with H's diagonal removed; with eps = 0,
+    E2[W] - E2[P] (Eq. EP1 from the literal H) equals E2[Q] (Eq. PT2final)."""
+    w = W.random_small(301 + n, mode, n, na, nb, naux=4, frac=frac, nvec=2)
+    h, eri = w.ints.h, w.ints.eri()
+    o = Oracle.from_workload(w)
+    E0 = np.array([-20.0, -18.5])
+    full = PT.full_space_keys(mode, n, na, 0 if mode == "spinors" else nb)
+    Hd = F.hamiltonian(full, h, eri) if mode == "spinors" else F.hamiltonian(full, *F.spin_orbital_integrals(h, eri))
+    pos = np.searchsorted(full, w.keys)
+    Hoff = Hd.copy()
+    np.fill_diagonal(Hoff, 0)
+    HWP = Hoff[:, pos]
+    cmax = np.abs(w.c).max(axis=1)
+    d = np.real(np.diag(Hd))
+    for eps in (0.0, 1e-3):
+        keep = np.abs(HWP) * cmax[None, :] >= eps if eps > 0 else np.ones(HWP.shape, dtype=bool)
+        num = (HWP * keep) @ w.c
+        ref = (np.abs(num) ** 2 / (E0[None, :] - d[:, None])).sum(0)
+        got, _ = o.enpt2(w.c, E0, eps=eps, over_w=True)
+        assert np.allclose(got, ref, rtol=1e-12, atol=1e-15), eps
+    e2w, _ = o.enpt2(w.c, E0, over_w=True)
+    sig = Hd[np.ix_(pos, pos)] @ w.c
+    e2p = (np.abs(sig - w.c * d[pos][:, None]) ** 2 / (E0[None, :] - d[pos][:, None])).sum(0)
+    e2q, _ = o.enpt2(w.c, E0)
+    assert np.allclose(e2w - e2p, e2q, rtol=1e-11, atol=1e-14)
