@@ -1028,7 +1028,7 @@ def main():
         dav["blockvec"] = blockvec_bench()
         rdm = rdm_bench(H, w)
         batch = batch_bench()
-        pt2 = pt2_bench(sizes=(200_000,))
+        pt2 = pt2_bench(sizes=(200_000, 2_000_000))
         pt2.append({"spinor": pt2_spinor_bench()})
         rowsplit = rowsplit_bench(H)
         determ = deterministic_bench(H, w)

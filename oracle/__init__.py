@@ -51,6 +51,7 @@ def _load():
             L.sciref_destroy.argtypes = [vp]
             L.sciref_destroy.restype = None
             L.sciref_set_determinants.argtypes = [vp, vp, i64]
+            L.sciref_set_determinants_w.argtypes = [vp, vp, i32, i64]
             L.sciref_diagonal.argtypes = [vp, vp]
             L.sciref_hij.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, vp]
             L.sciref_connections.argtypes = [vp, i64, vp, vp, vp, vp, i64]
@@ -111,8 +112,11 @@ class Oracle:
             self.ctx = None
 
     def set_determinants(self, keys):
+        """keys: [M] uint64 strings, or [M, 2] uint64 words (word 0 = orbitals 0..63) for
+        more than 64 spin-orbitals (spinors)."""
         self.keys = np.ascontiguousarray(keys, dtype=np.uint64)
-        rc = self.L.sciref_set_determinants(self.ctx, _ptr(self.keys), len(self.keys))
+        nwords = 1 if self.keys.ndim == 1 else self.keys.shape[1]
+        rc = self.L.sciref_set_determinants_w(self.ctx, _ptr(self.keys), nwords, len(self.keys))
         if rc != SCIREF_OK:
             raise ValueError(f"sciref_set_determinants failed ({rc})")
         self.M = len(self.keys)

@@ -47,6 +47,10 @@
 
 typedef double complex zd;
 
+/* An occupation string of up to 128 spin-orbitals or spinors: bit p is orbital p (a GCC
+ * 128-bit integer; determinants of up to 64 orbitals use its low word only). */
+typedef unsigned __int128 bits_t;
+
 typedef struct sciref_ctx {
     int is_complex;   /* 0: real FP64 scalars, 1: complex128 scalars */
     int spinors;      /* 0: spin-orbital mode, 1: spinor mode */
@@ -54,7 +58,7 @@ typedef struct sciref_ctx {
     int norb;         /* bits in use: 2n (spin-orbital) or n (spinor) */
     zd *h;            /* norb x norb */
     zd *eri;          /* norb^4, [p][q][r][s] = (pq|rs) */
-    uint64_t *keys;
+    bits_t *keys;
     int64_t M;
 } sciref_ctx;
 
@@ -75,7 +79,7 @@ int sciref_create(sciref_ctx **out, int is_complex, int spinors, int n,
                   const double *h, const double *eri)
 {
     if (!out || !h || !eri || n <= 0) return SCIREF_ERR_ARG;
-    if (spinors ? n > 64 : n > 32) return SCIREF_ERR_ARG;
+    if (spinors ? n > 128 : n > 64) return SCIREF_ERR_ARG;
     sciref_ctx *c = (sciref_ctx *)calloc(1, sizeof(sciref_ctx));
     c->is_complex = is_complex;
     c->spinors = spinors;
@@ -116,17 +120,27 @@ void sciref_destroy(sciref_ctx *c)
     free(c);
 }
 
-/* The list must be strictly ascending as unsigned 64-bit integers. */
-int sciref_set_determinants(sciref_ctx *c, const uint64_t *keys, int64_t M)
+/* keys: M strings of nwords (1 or 2) 64-bit words each, word 0 holding orbitals 0..63;
+ * the list must be strictly ascending as unsigned (64 x nwords)-bit integers. */
+int sciref_set_determinants_w(sciref_ctx *c, const uint64_t *keys, int nwords, int64_t M)
 {
-    if (!c || (M > 0 && !keys) || M < 0) return SCIREF_ERR_ARG;
-    for (int64_t i = 1; i < M; i++)
-        if (!(keys[i - 1] < keys[i])) return SCIREF_ERR_UNSORTED;
+    if (!c || (M > 0 && !keys) || M < 0 || nwords < 1 || nwords > 2) return SCIREF_ERR_ARG;
+    bits_t *k = (bits_t *)malloc((size_t)(M > 0 ? M : 1) * sizeof(bits_t));
+    for (int64_t i = 0; i < M; i++) {
+        k[i] = (bits_t)keys[i * nwords];
+        if (nwords == 2) k[i] |= (bits_t)keys[i * nwords + 1] << 64;
+        if (i > 0 && !(k[i - 1] < k[i])) { free(k); return SCIREF_ERR_UNSORTED; }
+    }
     free(c->keys);
-    c->keys = (uint64_t *)malloc((size_t)(M > 0 ? M : 1) * sizeof(uint64_t));
-    if (M > 0) memcpy(c->keys, keys, (size_t)M * sizeof(uint64_t));
+    c->keys = k;
     c->M = M;
     return SCIREF_OK;
+}
+
+/* One-word strings: strictly ascending as unsigned 64-bit integers. */
+int sciref_set_determinants(sciref_ctx *c, const uint64_t *keys, int64_t M)
+{
+    return sciref_set_determinants_w(c, keys, 1, M);
 }
 
 /* OpenMP threads of the parallel loops below (n <= 0 restores the default); returns the
@@ -140,10 +154,11 @@ int sciref_set_threads(int n)
 }
 
 /* ------------------------------------------------------------------ helpers */
-static int occupied(uint64_t d, int p) { return (int)((d >> p) & 1u); }
+static int occupied(bits_t d, int p) { return (int)((d >> p) & 1u); }
+static bits_t bit(int p) { return (bits_t)1 << p; }
 
 /* number of occupied orbitals strictly below p, counted one bit at a time */
-static int count_below(uint64_t d, int p)
+static int count_below(bits_t d, int p)
 {
     int cnt = 0;
     for (int q = 0; q < p; q++) cnt += occupied(d, q);
@@ -151,31 +166,31 @@ static int count_below(uint64_t d, int p)
 }
 
 /* apply a_p to *d: returns +1/-1, or 0 if p is empty */
-static int annihilate(uint64_t *d, int p)
+static int annihilate(bits_t *d, int p)
 {
     if (!occupied(*d, p)) return 0;
     int s = (count_below(*d, p) & 1) ? -1 : 1;
-    *d &= ~((uint64_t)1 << p);
+    *d &= ~bit(p);
     return s;
 }
 
 /* apply a+_p to *d: returns +1/-1, or 0 if p is occupied */
-static int create(uint64_t *d, int p)
+static int create(bits_t *d, int p)
 {
     if (occupied(*d, p)) return 0;
     int s = (count_below(*d, p) & 1) ? -1 : 1;
-    *d |= ((uint64_t)1 << p);
+    *d |= bit(p);
     return s;
 }
 
-static int n_diff(uint64_t a, uint64_t b)
+static int n_diff(bits_t a, bits_t b)
 {
     int cnt = 0;
-    for (int p = 0; p < 64; p++) cnt += occupied(a, p) != occupied(b, p);
+    for (int p = 0; p < 128; p++) cnt += occupied(a, p) != occupied(b, p);
     return cnt;
 }
 
-static int64_t find_key(const sciref_ctx *c, uint64_t k)
+static int64_t find_key(const sciref_ctx *c, bits_t k)
 {
     int64_t lo = 0, hi = c->M;          /* first index with keys[idx] >= k */
     while (lo < hi) {
@@ -186,7 +201,7 @@ static int64_t find_key(const sciref_ctx *c, uint64_t k)
 }
 
 /* <D_I|H|D_I> */
-static zd diag_element(const sciref_ctx *c, uint64_t d)
+static zd diag_element(const sciref_ctx *c, bits_t d)
 {
     zd e = 0;
     for (int i = 0; i < c->norb; i++) {
@@ -202,18 +217,18 @@ static zd diag_element(const sciref_ctx *c, uint64_t d)
 
 /* <D_I|H|D_J> for I != J; *degree receives the excitation degree and *sign the phase.
  * Returns 0 with *degree > 2 when the pair is not connected. */
-static zd offdiag_element(const sciref_ctx *c, uint64_t bra, uint64_t ket, int *degree, int *sign)
+static zd offdiag_element(const sciref_ctx *c, bits_t bra, bits_t ket, int *degree, int *sign)
 {
     int nd = n_diff(bra, ket);
     *degree = nd / 2;
     *sign = 0;
     if (nd != 2 && nd != 4) return 0;
     int from[2], to[2], nf = 0, nt = 0;        /* from: in ket only; to: in bra only */
-    for (int p = 0; p < 64; p++) {
+    for (int p = 0; p < 128; p++) {
         if (occupied(ket, p) && !occupied(bra, p)) from[nf++] = p;
         if (occupied(bra, p) && !occupied(ket, p)) to[nt++] = p;
     }
-    uint64_t d = ket;
+    bits_t d = ket;
     if (nd == 2) {
         int i = from[0], a = to[0];
         int s = annihilate(&d, i);
@@ -246,8 +261,8 @@ static int cmp_conn(const void *x, const void *y)
 
 static int64_t row_connections(const sciref_ctx *c, int64_t row, conn_t **out)
 {
-    uint64_t d = c->keys[row];
-    int occ[64], vir[64], no = 0, nv = 0;
+    bits_t d = c->keys[row];
+    int occ[128], vir[128], no = 0, nv = 0;
     for (int p = 0; p < c->norb; p++) {
         if (occupied(d, p)) occ[no++] = p; else vir[nv++] = p;
     }
@@ -258,7 +273,7 @@ static int64_t row_connections(const sciref_ctx *c, int64_t row, conn_t **out)
         for (int y = 0; y < nv; y++) {
             int i = occ[x], a = vir[y];
             if (spin_of(c, i) != spin_of(c, a)) continue;
-            uint64_t e = (d & ~((uint64_t)1 << i)) | ((uint64_t)1 << a);
+            bits_t e = (d & ~bit(i)) | bit(a);
             int64_t J = find_key(c, e);
             if (J < 0) continue;
             if (cnt == cap) { cap *= 2; list = (conn_t *)realloc(list, cap * sizeof(conn_t)); }
@@ -274,8 +289,8 @@ static int64_t row_connections(const sciref_ctx *c, int64_t row, conn_t **out)
                 for (int y2 = y1 + 1; y2 < nv; y2++) {
                     int i = occ[x1], j = occ[x2], a = vir[y1], b = vir[y2];
                     if (spin_of(c, i) + spin_of(c, j) != spin_of(c, a) + spin_of(c, b)) continue;
-                    uint64_t e = d & ~((uint64_t)1 << i) & ~((uint64_t)1 << j);
-                    e |= ((uint64_t)1 << a) | ((uint64_t)1 << b);
+                    bits_t e = d & ~bit(i) & ~bit(j);
+                    e |= bit(a) | bit(b);
                     int64_t J = find_key(c, e);
                     if (J < 0) continue;
                     if (cnt == cap) { cap *= 2; list = (conn_t *)realloc(list, cap * sizeof(conn_t)); }
@@ -455,10 +470,10 @@ int sciref_sigma_brute_rows(const sciref_ctx *c, const int64_t *rows, int64_t nr
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t r = 0; r < nrows; r++) {
         int64_t row = rows[r];
-        uint64_t bra = c->keys[row];
+        bits_t bra = c->keys[row];
         zd *acc = (zd *)calloc((size_t)nvec, sizeof(zd));
         for (int64_t col = 0; col < c->M; col++) {
-            uint64_t ket = c->keys[col];
+            bits_t ket = c->keys[col];
             int nd = n_diff(bra, ket);
             if (nd > 4) continue;
             zd hv;
@@ -483,9 +498,9 @@ int sciref_sigma_brute_rows(const sciref_ctx *c, const int64_t *rows, int64_t nr
 /* ------------------------------------------------------------------ density matrices */
 /* <bra| a+_p a+_r a_s a_q |ket>: the operators applied one at a time to the ket, right
  * to left (a_q first); 0 when the result is not bra. */
-static int two_body_sign(uint64_t bra, uint64_t ket, int p, int q, int r, int s)
+static int two_body_sign(bits_t bra, bits_t ket, int p, int q, int r, int s)
 {
-    uint64_t d = ket;
+    bits_t d = ket;
     int sg = annihilate(&d, q);
     if (!sg) return 0;
     sg *= annihilate(&d, s);
@@ -497,9 +512,9 @@ static int two_body_sign(uint64_t bra, uint64_t ket, int p, int q, int r, int s)
     return sg;
 }
 
-static int one_body_sign(uint64_t bra, uint64_t ket, int p, int q)
+static int one_body_sign(bits_t bra, bits_t ket, int p, int q)
 {
-    uint64_t d = ket;
+    bits_t d = ket;
     int sg = annihilate(&d, q);
     if (!sg) return 0;
     sg *= create(&d, p);
@@ -537,20 +552,20 @@ int sciref_rdm12(const sciref_ctx *c, const double *C, double *g1, double *g2)
     memset(g2, 0, m * m * m * m * (z ? 2 : 1) * sizeof(double));
 #pragma omp parallel
     {
-        const int maxc = 2 * 64 * 64;  /* candidate operator strings per pair */
+        const int maxc = 2 * 128 * 128;  /* candidate operator strings per pair */
         int *cq = (int *)malloc(4 * sizeof(int) * maxc);
         int *cs = cq + maxc, *cp = cs + maxc, *cr = cp + maxc;
 #pragma omp for schedule(dynamic, 8)
         for (int64_t row = 0; row < c->M; row++) {
-            const uint64_t bra = c->keys[row];
+            const bits_t bra = c->keys[row];
             const zd cI = conj(z ? CMPLX(C[2 * row], C[2 * row + 1]) : CMPLX(C[row], 0.0));
             conn_t *list;
             int64_t n = row_connections(c, row, &list);
             for (int64_t t = -1; t < n; t++) {   /* t = -1: the diagonal */
                 const int64_t col = t < 0 ? row : list[t].j;
-                const uint64_t ket = c->keys[col];
+                const bits_t ket = c->keys[col];
                 const zd w = cI * (z ? CMPLX(C[2 * col], C[2 * col + 1]) : CMPLX(C[col], 0.0));
-                int occ[64], no = 0, from[2], to[2], nf = 0, nt = 0;
+                int occ[128], no = 0, from[2], to[2], nf = 0, nt = 0;
                 for (int p = 0; p < c->norb; p++) {
                     if (occupied(ket, p)) occ[no++] = p;
                     if (occupied(ket, p) && !occupied(bra, p)) from[nf++] = p;
@@ -632,7 +647,7 @@ int sciref_rdm12(const sciref_ctx *c, const double *C, double *g1, double *g2)
  * C: [M][nroots] row-major (complex interleaved); E0, E2: nroots doubles.  *n_external
  * (if not NULL) receives the number of distinct determinants summed (|Q| restricted as
  * above).  Memory: 16 bytes per generated external pair. */
-typedef struct { uint64_t key; uint64_t j; } ext_pair;
+typedef struct { bits_t key; uint64_t j; } ext_pair;
 
 static int cmp_ext(const void *x, const void *y)
 {
@@ -645,8 +660,8 @@ static int cmp_ext(const void *x, const void *y)
  * keep_members), written to out (if not NULL) in generation order; returns their number */
 static int64_t external_excitations(const sciref_ctx *c, int64_t j, ext_pair *out, int keep_members)
 {
-    uint64_t d = c->keys[j];
-    int occ[64], vir[64], no = 0, nv = 0;
+    bits_t d = c->keys[j];
+    int occ[128], vir[128], no = 0, nv = 0;
     for (int p = 0; p < c->norb; p++) {
         if (occupied(d, p)) occ[no++] = p; else vir[nv++] = p;
     }
@@ -655,7 +670,7 @@ static int64_t external_excitations(const sciref_ctx *c, int64_t j, ext_pair *ou
         for (int y = 0; y < nv; y++) {
             int i = occ[x], a = vir[y];
             if (spin_of(c, i) != spin_of(c, a)) continue;
-            uint64_t e = (d & ~((uint64_t)1 << i)) | ((uint64_t)1 << a);
+            bits_t e = (d & ~bit(i)) | bit(a);
             if (!keep_members && find_key(c, e) >= 0) continue;
             if (out) { out[cnt].key = e; out[cnt].j = (uint64_t)j; }
             cnt++;
@@ -666,8 +681,8 @@ static int64_t external_excitations(const sciref_ctx *c, int64_t j, ext_pair *ou
                 for (int y2 = y1 + 1; y2 < nv; y2++) {
                     int i = occ[x1], jj = occ[x2], a = vir[y1], b = vir[y2];
                     if (spin_of(c, i) + spin_of(c, jj) != spin_of(c, a) + spin_of(c, b)) continue;
-                    uint64_t e = d & ~((uint64_t)1 << i) & ~((uint64_t)1 << jj);
-                    e |= ((uint64_t)1 << a) | ((uint64_t)1 << b);
+                    bits_t e = d & ~bit(i) & ~bit(jj);
+                    e |= bit(a) | bit(b);
                     if (!keep_members && find_key(c, e) >= 0) continue;
                     if (out) { out[cnt].key = e; out[cnt].j = (uint64_t)j; }
                     cnt++;
@@ -676,7 +691,11 @@ static int64_t external_excitations(const sciref_ctx *c, int64_t j, ext_pair *ou
 }
 
 #define ENPT2_BINS 256
-static unsigned enpt2_bin(uint64_t key) { return (unsigned)((key * 0x9E3779B97F4A7C15ull) >> 56); }
+static unsigned enpt2_bin(bits_t key)
+{
+    const uint64_t folded = (uint64_t)key ^ (uint64_t)(key >> 64) * 0xC2B2AE3D27D4EB4Full;
+    return (unsigned)((folded * 0x9E3779B97F4A7C15ull) >> 56);
+}
 
 int sciref_enpt2(const sciref_ctx *c, const double *C, int nroots, const double *E0, double eps, int over_w,
                  double *E2, int64_t *n_external)
@@ -718,7 +737,7 @@ int sciref_enpt2(const sciref_ctx *c, const double *C, int nroots, const double 
         for (int64_t s = 0; s < nb;) {
             int64_t e = s;
             while (e < nb && v[e].key == v[s].key) e++;
-            const uint64_t ext = v[s].key;
+            const bits_t ext = v[s].key;
             for (int k = 0; k < nroots; k++) num[k] = 0;
             int kept = 0;
             for (int64_t t = s; t < e; t++) {

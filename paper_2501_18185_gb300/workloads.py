@@ -333,6 +333,73 @@ def selected_spinor_64_cut(n1: int = 200, n2: int = 60, n3: int = 40, seed: int 
     return w
 
 
+def two_word_keys(alpha: np.ndarray, beta: np.ndarray, n: int) -> np.ndarray:
+    """Spin-orbital keys of more than 64 bits (alpha string in bits 0..n-1, beta string in
+    bits n..2n-1, 2n <= 128) as [M, 2] uint64 words, word 0 holding bits 0..63."""
+    a = np.asarray(alpha, dtype=np.uint64)
+    b = np.asarray(beta, dtype=np.uint64)
+    lo = a | (b << np.uint64(n)) if n < 64 else a
+    hi = b >> np.uint64(64 - n) if n < 64 else b << np.uint64(n - 64)
+    return np.stack([lo, hi], axis=1)
+
+
+def sort_words(keys: np.ndarray) -> np.ndarray:
+    """[M, 2] word keys in ascending order as 128-bit integers."""
+    return keys[np.lexsort((keys[:, 0], keys[:, 1]))]
+
+
+def excitation_level_words(keys: np.ndarray, hf: np.ndarray) -> np.ndarray:
+    x = keys ^ hf[None, :]
+    return (np.bitwise_count(x).sum(axis=1) // 2).astype(np.int64)
+
+
+def selected_two_word(n: int = 40, na: int = 4, nb: int = 4, M: int = 40000, naux: int = 40, nvec: int = 1,
+                      seed: int = 2501181860) -> Workload:
+    """A selected space of more than 64 spin-orbitals (two-word keys): n spatial orbitals
+    (2n > 64), na + nb electrons, HF + all singles + all Sz-conserving doubles + random
+    triples (uniform over all spin splits, without replacement) up to M determinants,
+    sorted as 128-bit integers; real integrals with naux Cholesky vectors of Frobenius norms
+    0.3 n 0.95^P; |c| = exp(-level) with random signs, normalised.
+    Draw order: integrals, triples, c."""
+    rng = np.random.default_rng(seed)
+    ints = real_integrals(rng, n, naux, 0.95)
+    parts = []
+    for level in range(3):
+        for ka in range(level + 1):
+            kb = level - ka
+            if ka > min(na, n - na) or kb > min(nb, n - nb):
+                continue
+            A = strings_at_level(n, na, ka)
+            B = strings_at_level(n, nb, kb)
+            parts.append(two_word_keys(np.repeat(A, len(B)), np.tile(B, len(A)), n))
+    base = np.concatenate(parts)
+    rest = M - len(base)
+    if rest < 0:
+        raise ValueError("M smaller than HF+singles+doubles")
+    splits = [(ka, 3 - ka) for ka in range(4) if ka <= min(na, n - na) and 3 - ka <= min(nb, n - nb)]
+    sizes = [n_strings_at_level(n, na, ka) * n_strings_at_level(n, nb, kb) for ka, kb in splits]
+    idx = np.sort(rng.choice(int(sum(sizes)), size=rest, replace=False))
+    trip, off = [], 0
+    for (ka, kb), sz in zip(splits, sizes):
+        sel = idx[(idx >= off) & (idx < off + sz)] - off
+        off += sz
+        if sel.size:
+            A = strings_at_level(n, na, ka)
+            B = strings_at_level(n, nb, kb)
+            trip.append(two_word_keys(A[sel // len(B)], B[sel % len(B)], n))
+    keys = sort_words(np.concatenate([base] + trip))
+    assert len(keys) == M
+    hf = two_word_keys(np.array([(1 << na) - 1], dtype=np.uint64), np.array([(1 << nb) - 1], dtype=np.uint64), n)[0]
+    lev = excitation_level_words(keys, hf)
+    cols = []
+    for _ in range(nvec):
+        v = np.exp(-lev.astype(np.float64)) * rng.choice(np.array([-1.0, 1.0]), size=M)
+        cols.append(v / np.linalg.norm(v))
+    w = Workload(f"sel2w_{n}o_{na}a{nb}b_M{M}", "spin_orbitals", n, na, nb, keys, ints, np.stack(cols, axis=1),
+                 {"hf_words": hf})
+    return w
+
+
 def selected_spinor_64(M: int = 1_000_000, nvec: int = 1, seed_offset: int = 4) -> Workload:
     """64 spinors, 14 electrons, selected space of M determinants (HF + singles + doubles
     + random triples); 80 Hermitian complex Cholesky vectors; complex c.
