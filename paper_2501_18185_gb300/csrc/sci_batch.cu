@@ -421,6 +421,7 @@ extern "C" int sci_batch_add(sci_batch *b, sci_ctx *ctx)
     if (!b || !ctx) return SCI_ERR_ARG;
     if (!ctx->have_ints || !ctx->have_dets) return bfail(b, SCI_ERR_STATE, "batch_add: instance needs integrals and determinants");
     if (ctx->cplx || ctx->spinors) return bfail(b, SCI_ERR_ARG, "batch_add: real spin-orbital instances only");
+    if (ctx->nwords != 1) return bfail(b, SCI_ERR_ARG, "batch_add: one-word keys only");
     if (ctx->device != b->device) return bfail(b, SCI_ERR_ARG, "batch_add: instance on another device");
     Inst B{};
     B.M = ctx->M;

@@ -67,6 +67,13 @@ __host__ __device__ __forceinline__ uint64_t code_mask(uint32_t c)
 {
     return (1ull << code_x(c)) | (1ull << code_y(c));
 }
+// whether two members of a bucket share an extra orbital (then they are a single
+// excitation of each other, not a double); valid for orbitals up to 255
+__host__ __device__ __forceinline__ bool codes_overlap(uint32_t a, uint32_t b)
+{
+    const int xa = code_x(a), ya = code_y(a), xb = code_x(b), yb = code_y(b);
+    return xa == xb || xa == yb || ya == xb || ya == yb;
+}
 
 // Rows whose sigma a launch computes: [rb, re) (sci_set_row_range), every row otherwise.
 struct RowRange {
@@ -132,8 +139,10 @@ struct sci_ctx {
     int have_dets = 0;
     int64_t M = 0;
     int na = 0, nb = 0, N = 0;
-    uint64_t ref = 0;
-    uint64_t *keys = nullptr;
+    uint64_t ref = 0;       // the reference (lowest orbitals), bits 0..63
+    uint64_t ref_hi = 0;    // its bits 64..127 (two-word lists)
+    int nwords = 1;         // 64-bit words per key: 1, or 2 for more than 64 spin-orbitals
+    uint64_t *keys = nullptr;  // [M][nwords], word 0 holding orbitals 0..63
     double *hdiag = nullptr;
     void *fref = nullptr;   // [norb][norb]
 
@@ -143,7 +152,7 @@ struct sci_ctx {
     uint32_t *e2_pos = nullptr;
     int64_t e1 = 0, nb1 = 0;
     uint32_t *e1_idx = nullptr;
-    uint64_t *e1_S = nullptr;
+    uint64_t *e1_S = nullptr;   // [e1][nwords]: the bucket key S of each entry
     uint32_t *e1_meta = nullptr;
     int maxb2 = 0, maxb1 = 0;
     int64_t pairs = 0, pairs2 = 0, pairs1 = 0;

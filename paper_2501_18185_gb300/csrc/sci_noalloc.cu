@@ -74,11 +74,10 @@ __global__ void k_conn2_noalloc(const uint32_t *__restrict__ e_idx, const uint32
         if (I < rb || I >= re) continue;
         const uint32_t pos = e_pos[p], code = e_code[p];
         int64_t bs = p - sci::pos_off(pos), be = bs + sci::pos_size(pos);
-        uint64_t m = sci::code_mask(code);
         int par = sci::code_par(code);
         for (int64_t q = bs; q < be; q++) {
             const uint32_t cq = e_code[q];
-            if (sci::code_mask(cq) & m) continue;
+            if (sci::codes_overlap(cq, code)) continue;
             put(s, (uint32_t)I, e_idx[q], 1, par ^ (int)sci::code_par(cq));
         }
     }

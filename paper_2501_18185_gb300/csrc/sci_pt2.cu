@@ -842,6 +842,8 @@ extern "C" int sci_enpt2(sci_ctx *ctx, const double *C, int nroots, const double
     if (!ctx->have_ints || !ctx->have_dets) return sci_fail(ctx, SCI_ERR_STATE, "enpt2: integrals and determinants first");
     if (ctx->spinors != ctx->cplx)
         return sci_fail(ctx, SCI_ERR_ARG, "enpt2: real spin-orbital mode or complex spinor mode");
+    if (ctx->nwords != 1 || (!ctx->spinors && ctx->n > 32) || ctx->n > 64)
+        return sci_fail(ctx, SCI_ERR_ARG, "enpt2: one-word keys, n <= 32 (spin-orbitals) or n <= 64 (spinors)");
     if (nroots < 1 || nroots > 8 || !E0 || !E2 || (ctx->M > 0 && !C))
         return sci_fail(ctx, SCI_ERR_ARG, "enpt2: need 1 <= nroots <= 8, C, E0 and E2");
     if (eps < 0.0) return sci_fail(ctx, SCI_ERR_ARG, "enpt2: eps < 0");

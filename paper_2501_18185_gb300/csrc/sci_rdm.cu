@@ -505,7 +505,7 @@ extern "C" int sci_rdm12(sci_ctx *ctx, const void *C, int nvec, const double *we
     if (!ctx) return SCI_ERR_ARG;
     if (!ctx->have_ints || !ctx->have_dets) return sci_fail(ctx, SCI_ERR_STATE, "rdm12: integrals and determinants first");
     if (nvec < 1 || !rdm1 || (ctx->M > 0 && !C)) return sci_fail(ctx, SCI_ERR_ARG, "rdm12: need nvec >= 1, C and rdm1");
-    if (ctx->norb > 64) return sci_fail(ctx, SCI_ERR_ARG, "rdm12: at most 64 orbitals");
+    if (ctx->norb > 64 || ctx->nwords != 1) return sci_fail(ctx, SCI_ERR_ARG, "rdm12: one-word keys, at most 64 orbitals");
     if (sci_cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) return SCI_ERR_CUDA;
     // weights to the device (a host array of nvec doubles, NULL = all ones)
     const size_t wbytes = sizeof(double) * nvec;

@@ -104,8 +104,8 @@ __global__ void k_range_count2(const uint32_t *__restrict__ e_idx, const uint32_
         if (I < rb || I >= re) continue;
         const uint32_t pos = e_pos[p];
         const int64_t bs = p - sci::pos_off(pos), be = bs + sci::pos_size(pos);
-        const uint64_t m = sci::code_mask(e_code[p]);
-        for (int64_t q = bs; q < be; q++) cnt += (sci::code_mask(e_code[q]) & m) == 0;
+        const uint32_t cp = e_code[p];
+        for (int64_t q = bs; q < be; q++) cnt += !sci::codes_overlap(e_code[q], cp);
     }
     for (int o = 16; o; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
     if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(out, cnt);
@@ -131,9 +131,9 @@ __global__ void k_cost2(const uint32_t *__restrict__ e_idx, const uint32_t *__re
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t pos = e_pos[p];
         const int64_t bs = p - sci::pos_off(pos), be = bs + sci::pos_size(pos);
-        const uint64_t m = sci::code_mask(e_code[p]);
+        const uint32_t cp = e_code[p];
         unsigned long long cnt = 0;
-        for (int64_t q = bs; q < be; q++) cnt += (sci::code_mask(e_code[q]) & m) == 0;
+        for (int64_t q = bs; q < be; q++) cnt += !sci::codes_overlap(e_code[q], cp);
         if (cnt) atomicAdd(cost + e_idx[p], cnt);
     }
 }
@@ -321,6 +321,8 @@ extern "C" int sci_set_row_range(sci_ctx *ctx, int64_t row_begin, int64_t row_en
         return sci_fail(ctx, SCI_ERR_ARG, "row range outside [0, M]");
     if (ctx->det_nvec > 0 && !(row_begin == 0 && row_end == ctx->M))
         return sci_fail(ctx, SCI_ERR_STATE, "deterministic mode is on");
+    if (ctx->nwords != 1 && !(row_begin == 0 && row_end == ctx->M))
+        return sci_fail(ctx, SCI_ERR_ARG, "row ranges need one-word keys");
     SCI_CK(cudaSetDevice(ctx->device));
     SCI_CK(cudaStreamSynchronize(ctx->stream));  // no launch in flight reads the old tables
     sci_free_range(ctx);

@@ -205,88 +205,114 @@ struct KeyRule {
     int spinors, n, na, nb, N;
 };
 
+// Keys of KW 64-bit words (KW = 2: up to 128 spin-orbitals or spinors, word 0 holding
+// orbitals 0..63, the paper's orbital configurations as arrays of 64-bit integers,
+// Sec. 3.2): occupied orbitals of a key below orbital p
+__device__ __forceinline__ int below2(uint64_t lo, uint64_t hi, int p)
+{
+    if (p <= 0) return 0;
+    if (p < 64) return __popcll(lo & ((1ull << p) - 1ull));
+    if (p == 64) return __popcll(lo);
+    if (p < 128) return __popcll(lo) + __popcll(hi & ((1ull << (p - 64)) - 1ull));
+    return __popcll(lo) + __popcll(hi);
+}
+
+// calls f(p) for every occupied orbital p of the key (lo, hi), ascending
+template <int KW, typename F> __device__ __forceinline__ void for_bits(uint64_t lo, uint64_t hi, F f)
+{
+    for (uint64_t m = lo; m; m &= m - 1) f(__ffsll((long long)m) - 1);
+    if constexpr (KW == 2)
+        for (uint64_t m = hi; m; m &= m - 1) f(64 + __ffsll((long long)m) - 1);
+}
+
+template <int KW>
 __global__ void k_validate(const uint64_t *__restrict__ keys, int64_t M, KeyRule r, int *status)
 {
+    const int nbits = r.spinors ? r.n : 2 * r.n;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t d = keys[i];
+        const uint64_t lo = keys[i * KW], hi = KW == 2 ? keys[i * KW + 1] : 0ull;
+        const int tot = __popcll(lo) + __popcll(hi);
         int bad = 0;
         if (r.spinors) {
-            if (__popcll(d) != r.N) bad |= sci::DEV_POPCOUNT;
-            if (r.n < 64 && (d >> r.n) != 0) bad |= sci::DEV_POPCOUNT;
+            if (tot != r.N) bad |= sci::DEV_POPCOUNT;
         } else {
-            uint64_t am = (r.n >= 64) ? ~0ull : ((1ull << r.n) - 1);
-            if (__popcll(d & am) != r.na || __popcll((d >> r.n) & am) != r.nb) bad |= sci::DEV_POPCOUNT;
-            if (2 * r.n < 64 && (d >> (2 * r.n)) != 0) bad |= sci::DEV_POPCOUNT;
+            const int na = below2(lo, hi, r.n);
+            if (na != r.na || below2(lo, hi, 2 * r.n) - na != r.nb) bad |= sci::DEV_POPCOUNT;
         }
+        if (tot != below2(lo, hi, nbits)) bad |= sci::DEV_POPCOUNT;   // bits above the orbitals
         if (i > 0) {
-            uint64_t prev = keys[i - 1];
-            if (prev == d) bad |= sci::DEV_DUPLICATE;
-            else if (prev > d) bad |= sci::DEV_UNSORTED;
+            const uint64_t plo = keys[(i - 1) * KW], phi = KW == 2 ? keys[(i - 1) * KW + 1] : 0ull;
+            if (phi == hi && plo == lo) bad |= sci::DEV_DUPLICATE;
+            else if (phi > hi || (phi == hi && plo > lo)) bad |= sci::DEV_UNSORTED;
         }
         if (bad) atomicOr(status, bad);
     }
 }
 
 // H_II = sum_{i in occ} h_ii + 1/2 sum_{i,j in occ} [(ii|jj) - (ij|ji)]
-template <typename S>
+template <typename S, int KW>
 __global__ void k_diag(const uint64_t *__restrict__ keys, int64_t M, int norb, const S *__restrict__ h_so,
                        const S *__restrict__ jd, const S *__restrict__ kd, double *__restrict__ hdiag)
 {
     for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < M; I += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t d = keys[I];
+        const uint64_t lo = keys[I * KW], hi = KW == 2 ? keys[I * KW + 1] : 0ull;
         double e1 = 0.0, e2 = 0.0;
-        for (uint64_t m = d; m; m &= m - 1) {
-            int i = __ffsll((long long)m) - 1;
+        for_bits<KW>(lo, hi, [&](int i) {
             e1 += Sc<S>::re(h_so[i * norb + i]);
-            for (uint64_t m2 = d; m2; m2 &= m2 - 1) {
-                int j = __ffsll((long long)m2) - 1;
-                e2 += Sc<S>::re(jd[i * norb + j]) - Sc<S>::re(kd[i * norb + j]);
-            }
-        }
+            for_bits<KW>(lo, hi, [&](int j) { e2 += Sc<S>::re(jd[i * norb + j]) - Sc<S>::re(kd[i * norb + j]); });
+        });
         hdiag[I] = e1 + 0.5 * e2;
     }
 }
 
 // fref[i][a] = h_ai + sum_{k in ref} g_so[k][i][a]
 template <typename S>
-__global__ void k_fref(int norb, uint64_t ref, const S *__restrict__ h_so, const S *__restrict__ g_so,
+__global__ void k_fref(int norb, uint64_t ref, uint64_t ref_hi, const S *__restrict__ h_so, const S *__restrict__ g_so,
                        S *__restrict__ fref)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= norb * norb) return;
     int i = t / norb, a = t % norb;
     S f = h_so[a * norb + i];
-    for (uint64_t m = ref; m; m &= m - 1) {
-        int k = __ffsll((long long)m) - 1;
-        f = Sc<S>::add(f, g_so[((int64_t)k * norb + i) * norb + a]);
-    }
+    for_bits<2>(ref, ref_hi, [&](int k) { f = Sc<S>::add(f, g_so[((int64_t)k * norb + i) * norb + a]); });
     fref[t] = f;
 }
 
-// every determinant emits its keys with `holes` occupied bits removed (1 or 2)
+// every determinant emits its keys with `holes` occupied bits removed (1 or 2): the key
+// words (out_hi only for KW = 2) and the value I | x << 32 | y << 40
+template <int KW>
 __global__ void k_emit(const uint64_t *__restrict__ keys, int64_t M, int holes, int per_det,
-                       uint64_t *__restrict__ out_keys, uint64_t *__restrict__ out_vals)
+                       uint64_t *__restrict__ out_keys, uint64_t *__restrict__ out_hi, uint64_t *__restrict__ out_vals)
 {
     for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < M; I += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t d = keys[I];
-        int64_t base = I * per_det;
+        const uint64_t lo = keys[I * KW], hi = KW == 2 ? keys[I * KW + 1] : 0ull;
+        const int64_t base = I * per_det;
         int t = 0;
-        for (uint64_t m1 = d; m1; m1 &= m1 - 1) {
-            int x = __ffsll((long long)m1) - 1;
-            uint64_t bx = 1ull << x;
+        auto clear = [](uint64_t &l, uint64_t &h, int p) {
+            if (p < 64) l &= ~(1ull << p);
+            else h &= ~(1ull << (p - 64));
+        };
+        for_bits<KW>(lo, hi, [&](int x) {
             if (holes == 1) {
-                out_keys[base + t] = d & ~bx;
+                uint64_t l = lo, h = hi;
+                clear(l, h, x);
+                out_keys[base + t] = l;
+                if constexpr (KW == 2) out_hi[base + t] = h;
                 out_vals[base + t] = (uint64_t)I | ((uint64_t)x << 32);
                 t++;
-                continue;
+                return;
             }
-            for (uint64_t m2 = m1 & (m1 - 1); m2; m2 &= m2 - 1) {
-                int y = __ffsll((long long)m2) - 1;
-                out_keys[base + t] = d & ~bx & ~(1ull << y);
+            for_bits<KW>(lo, hi, [&](int y) {
+                if (y <= x) return;
+                uint64_t l = lo, h = hi;
+                clear(l, h, x);
+                clear(l, h, y);
+                out_keys[base + t] = l;
+                if constexpr (KW == 2) out_hi[base + t] = h;
                 out_vals[base + t] = (uint64_t)I | ((uint64_t)x << 32) | ((uint64_t)y << 40);
                 t++;
-            }
-        }
+            });
+        });
     }
 }
 
@@ -324,11 +350,12 @@ __global__ void k_gather_sizes(const uint32_t *__restrict__ order, const uint32_
         out[t] = counts[order[t]];
 }
 
-__device__ inline int count_below(uint64_t k, int p) { return __popcll(k & ((1ull << p) - 1ull)); }
+
 
 // warp per kept bucket: scatter members into the final doubles table.  Members of a
 // bucket arrive in ascending determinant order, i.e. ascending (y, x); a y-group is the
 // run of members with the same y.
+template <int KW>
 __global__ void k_fill2(const uint32_t *__restrict__ order, const uint32_t *__restrict__ counts,
                         const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ newoff,
                         const uint64_t *__restrict__ ukeys, const uint64_t *__restrict__ vals, int64_t kept,
@@ -340,14 +367,14 @@ __global__ void k_fill2(const uint32_t *__restrict__ order, const uint32_t *__re
     for (int64_t j = w; j < kept; j += nw) {
         uint32_t b = order[j];
         uint32_t size = counts[b], old = offsets[b], dst = newoff[j];
-        uint64_t K = ukeys[b];
+        const uint64_t K = ukeys[(int64_t)b * KW], Kh = KW == 2 ? ukeys[(int64_t)b * KW + 1] : 0ull;
         for (uint32_t t = lane; t < size; t += 32) {
             uint64_t v = vals[old + t];
             int x = (int)((v >> 32) & 0xFF), y = (int)((v >> 40) & 0xFF);
             uint32_t gs = t, ge = t + 1;
             while (gs > 0 && (int)((vals[old + gs - 1] >> 40) & 0xFF) == y) gs--;
             while (ge < size && (int)((vals[old + ge] >> 40) & 0xFF) == y) ge++;
-            int par = (count_below(K, x) + count_below(K, y)) & 1;
+            int par = (below2(K, Kh, x) + below2(K, Kh, y)) & 1;
             e_idx[dst + t] = (uint32_t)(v & 0xFFFFFFFFull);
             e_code[dst + t] = sci::make_code(x, y, par, (int)(t - gs), (int)(ge - gs));
             e_pos[dst + t] = t | (size << 16);
@@ -355,6 +382,7 @@ __global__ void k_fill2(const uint32_t *__restrict__ order, const uint32_t *__re
     }
 }
 
+template <int KW>
 __global__ void k_fill1(const uint32_t *__restrict__ order, const uint32_t *__restrict__ counts,
                         const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ newoff,
                         const uint64_t *__restrict__ ukeys, const uint64_t *__restrict__ vals, int64_t kept,
@@ -366,13 +394,14 @@ __global__ void k_fill1(const uint32_t *__restrict__ order, const uint32_t *__re
     for (int64_t j = w; j < kept; j += nw) {
         uint32_t b = order[j];
         uint32_t size = counts[b], old = offsets[b], dst = newoff[j];
-        uint64_t K = ukeys[b];
+        const uint64_t K = ukeys[(int64_t)b * KW], Kh = KW == 2 ? ukeys[(int64_t)b * KW + 1] : 0ull;
         for (uint32_t t = lane; t < size; t += 32) {
             uint64_t v = vals[old + t];
             int x = (int)((v >> 32) & 0xFF);
-            uint32_t par = (uint32_t)(count_below(K, x) & 1);
+            uint32_t par = (uint32_t)(below2(K, Kh, x) & 1);
             e_idx[dst + t] = (uint32_t)(v & 0xFFFFFFFFull);
-            e_S[dst + t] = K;
+            e_S[(int64_t)(dst + t) * KW] = K;
+            if constexpr (KW == 2) e_S[(int64_t)(dst + t) * KW + 1] = Kh;
             e_meta[dst + t] = (uint32_t)x | (par << 7) | (t << 8) | (size << 20);
         }
     }
@@ -394,6 +423,116 @@ struct Buckets {
     int maxb = 0;
 };
 
+int order_runs(sci_ctx *ctx, int nruns, Buckets &B);
+
+__global__ void k_gather_u64(const uint64_t *__restrict__ src, const uint32_t *__restrict__ idx, int64_t n,
+                             uint64_t *__restrict__ dst)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        dst[t] = src[idx[t]];
+}
+
+__global__ void k_compose(const uint32_t *__restrict__ p1, const uint32_t *__restrict__ p2, int64_t n,
+                          uint32_t *__restrict__ out)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        out[t] = p1[p2[t]];
+}
+
+__global__ void k_run_flags2(const uint64_t *__restrict__ lo, const uint64_t *__restrict__ hi, int64_t n,
+                             uint32_t *__restrict__ flag)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        flag[t] = t == 0 || lo[t] != lo[t - 1] || hi[t] != hi[t - 1];
+}
+
+__global__ void k_runs2(const uint32_t *__restrict__ flag, const uint32_t *__restrict__ rid,
+                        const uint64_t *__restrict__ lo, const uint64_t *__restrict__ hi, int64_t n,
+                        uint64_t *__restrict__ ukeys, uint32_t *__restrict__ start)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        if (flag[t]) {
+            const uint32_t r = rid[t];
+            start[r] = (uint32_t)t;
+            ukeys[2 * (int64_t)r] = lo[t];
+            ukeys[2 * (int64_t)r + 1] = hi[t];
+        }
+}
+
+__global__ void k_run_counts(const uint32_t *__restrict__ start, int64_t nruns, int64_t n, uint32_t *__restrict__ counts)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nruns; r += (int64_t)gridDim.x * blockDim.x)
+        counts[r] = (uint32_t)((r + 1 < nruns ? (int64_t)start[r + 1] : n) - start[r]);
+}
+
+// Two-word keys: emit, sort as 128-bit integers (two stable radix passes: by the low word,
+// then by the high word) and find the runs of equal keys.  Produces B.vals_sorted,
+// B.ukeys ([nruns][2]) and B.counts.
+int sort_runs_2w(sci_ctx *ctx, int holes, int per_det, int64_t total, Buckets &B, int &nruns)
+{
+    cudaStream_t st = ctx->stream;
+    const int64_t M = ctx->M;
+    const int nitems = (int)total;
+    TmpBuf lo, hi, vals, lo_s, idx, perm1, hi_g, hi_s, iota2, perm2, fin, flag, rid, start, tmp, nr;
+    SCI_CK(cudaMalloc(&lo.p, total * 8));
+    SCI_CK(cudaMalloc(&hi.p, total * 8));
+    SCI_CK(cudaMalloc(&vals.p, total * 8));
+    SCI_CK(cudaMalloc(&lo_s.p, total * 8));
+    SCI_CK(cudaMalloc(&idx.p, total * 4));
+    SCI_CK(cudaMalloc(&perm1.p, total * 4));
+    SCI_CK(cudaMalloc(&hi_g.p, total * 8));
+    SCI_CK(cudaMalloc(&hi_s.p, total * 8));
+    SCI_CK(cudaMalloc(&iota2.p, total * 4));
+    SCI_CK(cudaMalloc(&perm2.p, total * 4));
+    SCI_CK(cudaMalloc(&fin.p, total * 4));
+    SCI_CK(cudaMalloc(&B.vals_sorted.p, total * 8));
+    k_emit<2><<<grid_for(M), 256, 0, st>>>(ctx->keys, M, holes, per_det, lo.as<uint64_t>(), hi.as<uint64_t>(),
+                                          vals.as<uint64_t>());
+    k_iota_u32<<<grid_for(total), 256, 0, st>>>(idx.as<uint32_t>(), total);
+    k_iota_u32<<<grid_for(total), 256, 0, st>>>(iota2.as<uint32_t>(), total);
+    SCI_CK(cudaGetLastError());
+    size_t tb = 0, tb2 = 0;
+    const int hibits = std::max(1, ctx->norb - 64);
+    SCI_CK(cub::DeviceRadixSort::SortPairs(nullptr, tb, lo.as<uint64_t>(), lo_s.as<uint64_t>(), idx.as<uint32_t>(),
+                                           perm1.as<uint32_t>(), nitems, 0, 64, st));
+    SCI_CK(cub::DeviceRadixSort::SortPairs(nullptr, tb2, hi_g.as<uint64_t>(), hi_s.as<uint64_t>(),
+                                           iota2.as<uint32_t>(), perm2.as<uint32_t>(), nitems, 0, hibits, st));
+    SCI_CK(cudaMalloc(&tmp.p, std::max<size_t>(std::max(tb, tb2), 16)));
+    SCI_CK(cub::DeviceRadixSort::SortPairs(tmp.p, tb, lo.as<uint64_t>(), lo_s.as<uint64_t>(), idx.as<uint32_t>(),
+                                           perm1.as<uint32_t>(), nitems, 0, 64, st));
+    k_gather_u64<<<grid_for(total), 256, 0, st>>>(hi.as<uint64_t>(), perm1.as<uint32_t>(), total, hi_g.as<uint64_t>());
+    SCI_CK(cub::DeviceRadixSort::SortPairs(tmp.p, tb2, hi_g.as<uint64_t>(), hi_s.as<uint64_t>(), iota2.as<uint32_t>(),
+                                           perm2.as<uint32_t>(), nitems, 0, hibits, st));
+    k_compose<<<grid_for(total), 256, 0, st>>>(perm1.as<uint32_t>(), perm2.as<uint32_t>(), total, fin.as<uint32_t>());
+    k_gather_u64<<<grid_for(total), 256, 0, st>>>(lo.as<uint64_t>(), fin.as<uint32_t>(), total, lo_s.as<uint64_t>());
+    k_gather_u64<<<grid_for(total), 256, 0, st>>>(vals.as<uint64_t>(), fin.as<uint32_t>(), total,
+                                                  B.vals_sorted.as<uint64_t>());
+    // runs of equal (hi, lo): hi_s and lo_s now hold the sorted words
+    SCI_CK(cudaMalloc(&flag.p, total * 4));
+    SCI_CK(cudaMalloc(&rid.p, total * 4));
+    k_run_flags2<<<grid_for(total), 256, 0, st>>>(lo_s.as<uint64_t>(), hi_s.as<uint64_t>(), total, flag.as<uint32_t>());
+    SCI_CK(cudaGetLastError());
+    size_t tb3 = 0;
+    SCI_CK(cub::DeviceScan::ExclusiveSum(nullptr, tb3, flag.as<uint32_t>(), rid.as<uint32_t>(), nitems, st));
+    TmpBuf tmp3;
+    SCI_CK(cudaMalloc(&tmp3.p, std::max<size_t>(tb3, 16)));
+    SCI_CK(cub::DeviceScan::ExclusiveSum(tmp3.p, tb3, flag.as<uint32_t>(), rid.as<uint32_t>(), nitems, st));
+    uint32_t last[2] = {0, 0};
+    SCI_CK(cudaMemcpyAsync(&last[0], rid.as<uint32_t>() + (total - 1), 4, cudaMemcpyDeviceToHost, st));
+    SCI_CK(cudaMemcpyAsync(&last[1], flag.as<uint32_t>() + (total - 1), 4, cudaMemcpyDeviceToHost, st));
+    SCI_CK(cudaStreamSynchronize(st));
+    nruns = (int)(last[0] + last[1]);
+    SCI_CK(cudaMalloc(&B.ukeys.p, (size_t)nruns * 16));
+    SCI_CK(cudaMalloc(&B.counts.p, (size_t)nruns * 4));
+    SCI_CK(cudaMalloc(&start.p, (size_t)nruns * 4));
+    k_runs2<<<grid_for(total), 256, 0, st>>>(flag.as<uint32_t>(), rid.as<uint32_t>(), lo_s.as<uint64_t>(),
+                                             hi_s.as<uint64_t>(), total, B.ukeys.as<uint64_t>(), start.as<uint32_t>());
+    k_run_counts<<<grid_for(nruns), 256, 0, st>>>(start.as<uint32_t>(), nruns, total, B.counts.as<uint32_t>());
+    SCI_CK(cudaGetLastError());
+    SCI_CK(cudaStreamSynchronize(st));
+    return SCI_OK;
+}
+
 int build_buckets(sci_ctx *ctx, int holes, int per_det, Buckets &B)
 {
     cudaStream_t st = ctx->stream;
@@ -402,12 +541,19 @@ int build_buckets(sci_ctx *ctx, int holes, int per_det, Buckets &B)
     if (total >= (int64_t)1 << 31) return sci_fail(ctx, SCI_ERR_OVERFLOW, "too many bucket entries (>= 2^31)");
     if (total == 0) return SCI_OK;
     int nitems = (int)total;
+    int nruns = 0;
+    if (ctx->nwords == 2) {
+        int rc = sort_runs_2w(ctx, holes, per_det, total, B, nruns);
+        if (rc != SCI_OK) return rc;
+        return order_runs(ctx, nruns, B);
+    }
     TmpBuf ka, kb, va;
     SCI_CK(cudaMalloc(&ka.p, total * 8));
     SCI_CK(cudaMalloc(&kb.p, total * 8));
     SCI_CK(cudaMalloc(&va.p, total * 8));
     SCI_CK(cudaMalloc(&B.vals_sorted.p, total * 8));
-    k_emit<<<grid_for(M), 256, 0, st>>>(ctx->keys, M, holes, per_det, ka.as<uint64_t>(), va.as<uint64_t>());
+    k_emit<1><<<grid_for(M), 256, 0, st>>>(ctx->keys, M, holes, per_det, ka.as<uint64_t>(), nullptr,
+                                          va.as<uint64_t>());
     SCI_CK(cudaGetLastError());
     cub::DoubleBuffer<uint64_t> dk(ka.as<uint64_t>(), kb.as<uint64_t>());
     cub::DoubleBuffer<uint64_t> dv(va.as<uint64_t>(), B.vals_sorted.as<uint64_t>());
@@ -439,12 +585,19 @@ int build_buckets(sci_ctx *ctx, int holes, int per_det, Buckets &B)
         SCI_CK(cub::DeviceRunLengthEncode::Encode(tmp.p, tb, sorted_keys, B.ukeys.as<uint64_t>(),
                                                   B.counts.as<uint32_t>(), nruns_d.as<int>(), nitems, st));
     }
-    int nruns = 0;
     SCI_CK(cudaMemcpyAsync(&nruns, nruns_d.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     SCI_CK(cudaStreamSynchronize(st));
     cudaFree(ka.p); ka.p = nullptr;
     cudaFree(kb.p); kb.p = nullptr;
+    return order_runs(ctx, nruns, B);
+}
 
+// Given the runs of equal keys (B.counts, B.ukeys, B.vals_sorted), drop the singletons and
+// order the kept buckets by size, largest first, with their new offsets.
+int order_runs(sci_ctx *ctx, int nruns, Buckets &B)
+{
+    cudaStream_t st = ctx->stream;
+    size_t tb = 0;
     // offsets of the runs in sorted order
     SCI_CK(cudaMalloc(&B.offsets.p, (size_t)nruns * 4));
     tb = 0;
@@ -527,6 +680,8 @@ void free_dets(sci_ctx *ctx)
     free_held(ctx, ctx->e1_S);
     free_held(ctx, ctx->e1_meta);
     ctx->have_dets = 0;
+    ctx->nwords = 1;
+    ctx->ref_hi = 0;
     ctx->M = 0;
     ctx->e1 = ctx->e2 = ctx->nb1 = ctx->nb2 = 0;
     ctx->maxb1 = ctx->maxb2 = 0;
@@ -556,18 +711,21 @@ int compute_diag_fref(sci_ctx *ctx)
     if (!ctx->fref) SCI_CK(alloc_held(ctx, &ctx->fref, (size_t)norb * norb * scalar_bytes(ctx)));
     int nn = norb * norb;
     if (ctx->cplx) {
-        k_fref<zdbl><<<(nn + 255) / 256, 256, 0, st>>>(norb, ctx->ref, (const zdbl *)ctx->h_so,
+        k_fref<zdbl><<<(nn + 255) / 256, 256, 0, st>>>(norb, ctx->ref, ctx->ref_hi, (const zdbl *)ctx->h_so,
                                                         (const zdbl *)ctx->g_so, (zdbl *)ctx->fref);
-        if (ctx->M > 0)
-            k_diag<zdbl><<<grid_for(ctx->M), 256, 0, st>>>(ctx->keys, ctx->M, norb, (const zdbl *)ctx->h_so,
-                                                           (const zdbl *)ctx->jd, (const zdbl *)ctx->kd, ctx->hdiag);
+        if (ctx->M > 0) {
+            auto kd = ctx->nwords == 2 ? k_diag<zdbl, 2> : k_diag<zdbl, 1>;
+            kd<<<grid_for(ctx->M), 256, 0, st>>>(ctx->keys, ctx->M, norb, (const zdbl *)ctx->h_so,
+                                                 (const zdbl *)ctx->jd, (const zdbl *)ctx->kd, ctx->hdiag);
+        }
     } else {
-        k_fref<double><<<(nn + 255) / 256, 256, 0, st>>>(norb, ctx->ref, (const double *)ctx->h_so,
+        k_fref<double><<<(nn + 255) / 256, 256, 0, st>>>(norb, ctx->ref, ctx->ref_hi, (const double *)ctx->h_so,
                                                           (const double *)ctx->g_so, (double *)ctx->fref);
-        if (ctx->M > 0)
-            k_diag<double><<<grid_for(ctx->M), 256, 0, st>>>(ctx->keys, ctx->M, norb, (const double *)ctx->h_so,
-                                                             (const double *)ctx->jd, (const double *)ctx->kd,
-                                                             ctx->hdiag);
+        if (ctx->M > 0) {
+            auto kd = ctx->nwords == 2 ? k_diag<double, 2> : k_diag<double, 1>;
+            kd<<<grid_for(ctx->M), 256, 0, st>>>(ctx->keys, ctx->M, norb, (const double *)ctx->h_so,
+                                                 (const double *)ctx->jd, (const double *)ctx->kd, ctx->hdiag);
+        }
     }
     // paired-FP32 copy of fref for the paired-FP32 singles
     const int64_t nd = (int64_t)nn * (ctx->cplx ? 2 : 1);
@@ -641,8 +799,8 @@ extern "C" int sci_set_integrals(sci_ctx *ctx, int scalar, int mode, int n, cons
     ctx->err.clear();
     if (scalar != SCI_REAL64 && scalar != SCI_COMPLEX128) return sci_fail(ctx, SCI_ERR_ARG, "bad scalar type");
     if (mode != SCI_SPIN_ORBITALS && mode != SCI_SPINORS) return sci_fail(ctx, SCI_ERR_ARG, "bad mode");
-    if (mode == SCI_SPIN_ORBITALS && (n < 1 || n > 32)) return sci_fail(ctx, SCI_ERR_ARG, "spin-orbital mode needs 1 <= n <= 32");
-    if (mode == SCI_SPINORS && (n < 1 || n > 64)) return sci_fail(ctx, SCI_ERR_ARG, "spinor mode needs 1 <= n <= 64");
+    if (mode == SCI_SPIN_ORBITALS && (n < 1 || n > 64)) return sci_fail(ctx, SCI_ERR_ARG, "spin-orbital mode needs 1 <= n <= 64");
+    if (mode == SCI_SPINORS && (n < 1 || n > 128)) return sci_fail(ctx, SCI_ERR_ARG, "spinor mode needs 1 <= n <= 128");
     if (mode == SCI_SPIN_ORBITALS && scalar != SCI_REAL64)
         return sci_fail(ctx, SCI_ERR_ARG, "spin-orbital mode takes real integrals");
     if (!h) return sci_fail(ctx, SCI_ERR_ARG, "h is NULL");
@@ -773,10 +931,32 @@ extern "C" int sci_set_integrals(sci_ctx *ctx, int scalar, int mode, int n, cons
     return SCI_OK;
 }
 
+namespace {
+int set_dets(sci_ctx *ctx, const uint64_t *keys, int nwords, int64_t M, int n_alpha, int n_beta, int keys_on_device);
+}
+
 extern "C" int sci_set_determinants(sci_ctx *ctx, const uint64_t *keys, int64_t M, int n_alpha, int n_beta,
                                     int keys_on_device)
 {
     if (!ctx) return SCI_ERR_ARG;
+    if (ctx->have_ints && ctx->norb > 64)
+        return sci_fail(ctx, SCI_ERR_ARG, "more than 64 spin-orbitals: use sci_set_determinants_w with two words");
+    return set_dets(ctx, keys, 1, M, n_alpha, n_beta, keys_on_device);
+}
+
+extern "C" int sci_set_determinants_w(sci_ctx *ctx, const uint64_t *keys, int nwords, int64_t M, int n_alpha,
+                                      int n_beta, int keys_on_device)
+{
+    if (!ctx) return SCI_ERR_ARG;
+    if (nwords != 1 && nwords != 2) return sci_fail(ctx, SCI_ERR_ARG, "nwords must be 1 or 2");
+    if (nwords == 1 && ctx->have_ints && ctx->norb > 64)
+        return sci_fail(ctx, SCI_ERR_ARG, "more than 64 spin-orbitals need two words");
+    return set_dets(ctx, keys, nwords, M, n_alpha, n_beta, keys_on_device);
+}
+
+namespace {
+int set_dets(sci_ctx *ctx, const uint64_t *keys, int nwords, int64_t M, int n_alpha, int n_beta, int keys_on_device)
+{
     ctx->err.clear();
     if (!ctx->have_ints) return sci_fail(ctx, SCI_ERR_STATE, "set integrals before determinants");
     if (M < 0 || (M > 0 && !keys)) return sci_fail(ctx, SCI_ERR_ARG, "bad key array");
@@ -798,20 +978,30 @@ extern "C" int sci_set_determinants(sci_ctx *ctx, const uint64_t *keys, int64_t 
     ctx->na = n_alpha;
     ctx->nb = ctx->spinors ? -1 : n_beta;
     ctx->N = N;
-    if (ctx->spinors) ctx->ref = (N >= 64) ? ~0ull : ((1ull << N) - 1);
-    else ctx->ref = ((1ull << n_alpha) - 1) | (((1ull << n_beta) - 1) << ctx->n);
+    ctx->nwords = nwords;
+    {
+        // the reference: the lowest N spinors, or the lowest n_alpha alpha and n_beta beta
+        // orbitals, over two words
+        unsigned __int128 r;
+        auto low = [](int k) -> unsigned __int128 { return k >= 128 ? ~(unsigned __int128)0 : (((unsigned __int128)1 << k) - 1); };
+        if (ctx->spinors) r = low(N);
+        else r = low(n_alpha) | (low(n_beta) << ctx->n);
+        ctx->ref = (uint64_t)r;
+        ctx->ref_hi = (uint64_t)(r >> 64);
+    }
 
-    SCI_CK(alloc_held(ctx, (void **)&ctx->keys, (size_t)M * 8));
+    SCI_CK(alloc_held(ctx, (void **)&ctx->keys, (size_t)M * 8 * nwords));
     SCI_CK(alloc_held(ctx, (void **)&ctx->hdiag, (size_t)M * 8));
     SCI_CK(alloc_held(ctx, &ctx->c_ds, (size_t)M * 64));  // paired-FP32 coefficients, 64 B per determinant
     if (M > 0)
-        SCI_CK(cudaMemcpyAsync(ctx->keys, keys, (size_t)M * 8,
+        SCI_CK(cudaMemcpyAsync(ctx->keys, keys, (size_t)M * 8 * nwords,
                                keys_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     // K0: validation
     SCI_CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), st));
     if (M > 0) {
         KeyRule kr{ctx->spinors, ctx->n, n_alpha, n_beta, N};
-        k_validate<<<grid_for(M), 256, 0, st>>>(ctx->keys, M, kr, ctx->status);
+        if (nwords == 2) k_validate<2><<<grid_for(M), 256, 0, st>>>(ctx->keys, M, kr, ctx->status);
+        else k_validate<1><<<grid_for(M), 256, 0, st>>>(ctx->keys, M, kr, ctx->status);
         SCI_CK(cudaGetLastError());
     }
     int dev_status = 0;
@@ -839,7 +1029,8 @@ extern "C" int sci_set_determinants(sci_ctx *ctx, const uint64_t *keys, int64_t 
         SCI_CK(alloc_held(ctx, (void **)&ctx->e2_code, (size_t)B.entries * 4));
         SCI_CK(alloc_held(ctx, (void **)&ctx->e2_pos, (size_t)B.entries * 4));
         if (B.kept > 0) {
-            k_fill2<<<grid_for(B.kept * 32), 256, 0, st>>>(B.order.as<uint32_t>(), B.counts.as<uint32_t>(),
+            auto kf = nwords == 2 ? k_fill2<2> : k_fill2<1>;
+            kf<<<grid_for(B.kept * 32), 256, 0, st>>>(B.order.as<uint32_t>(), B.counts.as<uint32_t>(),
                                                           B.offsets.as<uint32_t>(), B.newoff.as<uint32_t>(),
                                                           B.ukeys.as<uint64_t>(), B.vals_sorted.as<uint64_t>(), B.kept,
                                                           ctx->e2_idx, ctx->e2_code, ctx->e2_pos);
@@ -856,10 +1047,11 @@ extern "C" int sci_set_determinants(sci_ctx *ctx, const uint64_t *keys, int64_t 
         ctx->nb1 = B.kept;
         ctx->maxb1 = B.maxb;
         SCI_CK(alloc_held(ctx, (void **)&ctx->e1_idx, (size_t)B.entries * 4));
-        SCI_CK(alloc_held(ctx, (void **)&ctx->e1_S, (size_t)B.entries * 8));
+        SCI_CK(alloc_held(ctx, (void **)&ctx->e1_S, (size_t)B.entries * 8 * nwords));
         SCI_CK(alloc_held(ctx, (void **)&ctx->e1_meta, (size_t)B.entries * 4));
         if (B.kept > 0) {
-            k_fill1<<<grid_for(B.kept * 32), 256, 0, st>>>(B.order.as<uint32_t>(), B.counts.as<uint32_t>(),
+            auto kf = nwords == 2 ? k_fill1<2> : k_fill1<1>;
+            kf<<<grid_for(B.kept * 32), 256, 0, st>>>(B.order.as<uint32_t>(), B.counts.as<uint32_t>(),
                                                           B.offsets.as<uint32_t>(), B.newoff.as<uint32_t>(),
                                                           B.ukeys.as<uint64_t>(), B.vals_sorted.as<uint64_t>(), B.kept,
                                                           ctx->e1_idx, ctx->e1_S, ctx->e1_meta);
@@ -888,6 +1080,7 @@ extern "C" int sci_set_determinants(sci_ctx *ctx, const uint64_t *keys, int64_t 
     ctx->pairs = p1 + p2;
     return SCI_OK;
 }
+}  // namespace
 
 extern "C" int sci_diagonal(sci_ctx *ctx, double *hdiag)
 {

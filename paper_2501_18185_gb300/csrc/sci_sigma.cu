@@ -593,10 +593,10 @@ k_doubles_dsz(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e
 }
 
 // ------------------------------------------------------------------ singles
-template <typename TS, typename TC, int NV, bool RANGED, bool STORE = false>
+template <typename TS, typename TC, int NV, bool RANGED, bool STORE = false, int KW = 1>
 __global__ void __launch_bounds__(kThreads)
 k_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S, const uint32_t *__restrict__ e_meta,
-          int64_t E, int norb, uint64_t ref, const TS *__restrict__ fref, const TS *__restrict__ g_so,
+          int64_t E, int norb, uint64_t ref, uint64_t ref_hi, const TS *__restrict__ fref, const TS *__restrict__ g_so,
           const TC *__restrict__ C, int nvec, int v0, typename AccOf<TS>::type *__restrict__ Sout, sci::RowRange rr, const uint32_t *__restrict__ slot)
 {
     using TA = typename AccOf<TS>::type;
@@ -610,8 +610,9 @@ k_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S, 
         const bool par = (meta >> 7) & 1;
         const int64_t bs = p - (int64_t)((meta >> 8) & 0xFFF);
         const int64_t be = bs + (int64_t)(meta >> 20);
-        const uint64_t Sk = e_S[p];
+        const uint64_t Sk = e_S[p * KW], Sk1 = KW == 2 ? e_S[p * KW + 1] : 0ull;
         const uint64_t part = Sk & ~ref, holes = ref & ~Sk;
+        const uint64_t part1 = Sk1 & ~ref_hi, holes1 = ref_hi & ~Sk1;   // orbitals 64.. (two words)
         TA acc[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) zero(acc[v]);
@@ -622,13 +623,15 @@ k_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S, 
             const bool parq = (mq >> 7) & 1;
             const uint32_t idxq = e_idx[q];
             TS f = ldg(fref + i * norb + a);
-            for (uint64_t m = part; m; m &= m - 1) {
-                int k = __ffsll((long long)m) - 1;
+            for (int w_ = 0; w_ < KW; w_++)
+            for (uint64_t m = w_ ? part1 : part; m; m &= m - 1) {
+                int k = 64 * w_ + __ffsll((long long)m) - 1;
                 TS g = ldg(g_so + ((int64_t)k * norb + i) * norb + a);
                 if constexpr (sizeof(TS) == sizeof(zdbl)) { f.x += g.x; f.y += g.y; } else { f += g; }
             }
-            for (uint64_t m = holes; m; m &= m - 1) {
-                int k = __ffsll((long long)m) - 1;
+            for (int w_ = 0; w_ < KW; w_++)
+            for (uint64_t m = w_ ? holes1 : holes; m; m &= m - 1) {
+                int k = 64 * w_ + __ffsll((long long)m) - 1;
                 TS g = ldg(g_so + ((int64_t)k * norb + i) * norb + a);
                 if constexpr (sizeof(TS) == sizeof(zdbl)) { f.x -= g.x; f.y -= g.y; } else { f -= g; }
             }
@@ -652,10 +655,10 @@ k_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S, 
 // the doubles.  C2/C4 is the split vector group (row stride NV).
 using sci::ds_add;
 
-template <int NV, bool RANGED, bool STORE = false>
+template <int NV, bool RANGED, bool STORE = false, int KW = 1>
 __global__ void __launch_bounds__(kThreads)
 k_singles_ds(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S, const uint32_t *__restrict__ e_meta,
-             int64_t E, int norb, uint64_t ref, const float2 *__restrict__ fref2, const float2 *__restrict__ g2,
+             int64_t E, int norb, uint64_t ref, uint64_t ref_hi, const float2 *__restrict__ fref2, const float2 *__restrict__ g2,
              const float2 *__restrict__ C2, int nvec, int v0, double *__restrict__ Sout, sci::RowRange rr, const uint32_t *__restrict__ slot)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
@@ -668,8 +671,9 @@ k_singles_ds(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_
         const bool par = (meta >> 7) & 1;
         const int64_t bs = p - (int64_t)((meta >> 8) & 0xFFF);
         const int64_t be = bs + (int64_t)(meta >> 20);
-        const uint64_t Sk = e_S[p];
+        const uint64_t Sk = e_S[p * KW], Sk1 = KW == 2 ? e_S[p * KW + 1] : 0ull;
         const uint64_t part = Sk & ~ref, holes = ref & ~Sk;
+        const uint64_t part1 = Sk1 & ~ref_hi, holes1 = ref_hi & ~Sk1;   // orbitals 64.. (two words)
         Ds acc[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) ds_zero(acc[v]);
@@ -681,12 +685,14 @@ k_singles_ds(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_
             const uint32_t idxq = e_idx[q];
             const float2 f0 = __ldg(fref2 + i * norb + a);
             Ds f{f0.x, f0.y};
-            for (uint64_t m = part; m; m &= m - 1) {
-                const int k = __ffsll((long long)m) - 1;
+            for (int w_ = 0; w_ < KW; w_++)
+            for (uint64_t m = w_ ? part1 : part; m; m &= m - 1) {
+                const int k = 64 * w_ + __ffsll((long long)m) - 1;
                 ds_add(f, __ldg(g2 + ((int64_t)k * norb + i) * norb + a));
             }
-            for (uint64_t m = holes; m; m &= m - 1) {
-                const int k = __ffsll((long long)m) - 1;
+            for (int w_ = 0; w_ < KW; w_++)
+            for (uint64_t m = w_ ? holes1 : holes; m; m &= m - 1) {
+                const int k = 64 * w_ + __ffsll((long long)m) - 1;
                 ds_add(f, flip(true, __ldg(g2 + ((int64_t)k * norb + i) * norb + a)));
             }
             ds_renorm(f);
@@ -705,10 +711,10 @@ k_singles_ds(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_
     }
 }
 
-template <int NV, bool RANGED, bool STORE = false>
+template <int NV, bool RANGED, bool STORE = false, int KW = 1>
 __global__ void __launch_bounds__(kThreads)
 k_singles_dsz(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S,
-              const uint32_t *__restrict__ e_meta, int64_t E, int norb, uint64_t ref,
+              const uint32_t *__restrict__ e_meta, int64_t E, int norb, uint64_t ref, uint64_t ref_hi,
               const float4 *__restrict__ fref4, const float4 *__restrict__ g4, const float4 *__restrict__ C4,
               int nvec, int v0, zdbl *__restrict__ Sout, sci::RowRange rr, const uint32_t *__restrict__ slot)
 {
@@ -722,8 +728,9 @@ k_singles_dsz(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e
         const bool par = (meta >> 7) & 1;
         const int64_t bs = p - (int64_t)((meta >> 8) & 0xFFF);
         const int64_t be = bs + (int64_t)(meta >> 20);
-        const uint64_t Sk = e_S[p];
+        const uint64_t Sk = e_S[p * KW], Sk1 = KW == 2 ? e_S[p * KW + 1] : 0ull;
         const uint64_t part = Sk & ~ref, holes = ref & ~Sk;
+        const uint64_t part1 = Sk1 & ~ref_hi, holes1 = ref_hi & ~Sk1;   // orbitals 64.. (two words)
         Ds ar[NV], ai[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) ds_zero(ar[v]), ds_zero(ai[v]);
@@ -735,14 +742,16 @@ k_singles_dsz(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e
             const uint32_t idxq = e_idx[q];
             const float4 f0 = __ldg(fref4 + i * norb + a);
             Ds fr{f0.x, f0.y}, fi{f0.z, f0.w};
-            for (uint64_t m = part; m; m &= m - 1) {
-                const int k = __ffsll((long long)m) - 1;
+            for (int w_ = 0; w_ < KW; w_++)
+            for (uint64_t m = w_ ? part1 : part; m; m &= m - 1) {
+                const int k = 64 * w_ + __ffsll((long long)m) - 1;
                 const float4 g = __ldg(g4 + ((int64_t)k * norb + i) * norb + a);
                 ds_add(fr, make_float2(g.x, g.y));
                 ds_add(fi, make_float2(g.z, g.w));
             }
-            for (uint64_t m = holes; m; m &= m - 1) {
-                const int k = __ffsll((long long)m) - 1;
+            for (int w_ = 0; w_ < KW; w_++)
+            for (uint64_t m = w_ ? holes1 : holes; m; m &= m - 1) {
+                const int k = 64 * w_ + __ffsll((long long)m) - 1;
                 const float4 g = flip(true, __ldg(g4 + ((int64_t)k * norb + i) * norb + a));
                 ds_add(fr, make_float2(g.x, g.y));
                 ds_add(fi, make_float2(g.z, g.w));
@@ -941,27 +950,36 @@ int f32_groups(sci_ctx *ctx, const Tabs &T, const float *C, double *S, int nvec)
     return rc;
 }
 
-// paired-FP32 singles; real coefficients may come in as double or float
-template <bool RG, bool ST, bool CPLX, int NV, typename TC = double>
-int launch_singles_ds(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int nvec, int v0)
+// paired-FP32 singles; real coefficients may come in as double or float; keys of one or
+// two words (KW)
+template <bool RG, bool ST, bool CPLX, int NV, typename TC, int KW>
+int launch_singles_ds_w(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int nvec, int v0)
 {
-    if (T.e1 == 0) return SCI_OK;
     const int g = grid_for(T.e1);
     if constexpr (CPLX) {
         k_split_cz<<<grid_for(ctx->M * NV), kThreads, 0, ctx->stream>>>((const zdbl *)C, ctx->M, nvec, v0, NV,
                                                                         (float4 *)ctx->c_ds);
-        k_singles_dsz<NV, RG, ST><<<g, kThreads, 0, ctx->stream>>>(T.e1_idx, T.e1_S, T.e1_meta, T.e1, ctx->norb, ctx->ref,
-                                                               (const float4 *)ctx->fref_ds, (const float4 *)ctx->g_ds,
-                                                               (const float4 *)ctx->c_ds, nvec, v0, (zdbl *)S, T.rr,
-                                                               ST ? ctx->det_inv1 : nullptr);
+        k_singles_dsz<NV, RG, ST, KW><<<g, kThreads, 0, ctx->stream>>>(
+            T.e1_idx, T.e1_S, T.e1_meta, T.e1, ctx->norb, ctx->ref, ctx->ref_hi, (const float4 *)ctx->fref_ds,
+            (const float4 *)ctx->g_ds, (const float4 *)ctx->c_ds, nvec, v0, (zdbl *)S, T.rr,
+            ST ? ctx->det_inv1 : nullptr);
     } else {
         k_split_c<TC><<<grid_for(ctx->M * NV), kThreads, 0, ctx->stream>>>((const TC *)C, ctx->M, nvec, v0, NV,
                                                                            (float2 *)ctx->c_ds);
-        k_singles_ds<NV, RG, ST><<<g, kThreads, 0, ctx->stream>>>(T.e1_idx, T.e1_S, T.e1_meta, T.e1, ctx->norb, ctx->ref,
-                                                              (const float2 *)ctx->fref_ds, (const float2 *)ctx->g_ds,
-                                                              (const float2 *)ctx->c_ds, nvec, v0, (double *)S, T.rr, ST ? ctx->det_inv1 : nullptr);
+        k_singles_ds<NV, RG, ST, KW><<<g, kThreads, 0, ctx->stream>>>(
+            T.e1_idx, T.e1_S, T.e1_meta, T.e1, ctx->norb, ctx->ref, ctx->ref_hi, (const float2 *)ctx->fref_ds,
+            (const float2 *)ctx->g_ds, (const float2 *)ctx->c_ds, nvec, v0, (double *)S, T.rr,
+            ST ? ctx->det_inv1 : nullptr);
     }
     return sci_cuda_check(ctx, cudaGetLastError(), "k_singles_ds launch");
+}
+
+template <bool RG, bool ST, bool CPLX, int NV, typename TC = double>
+int launch_singles_ds(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int nvec, int v0)
+{
+    if (T.e1 == 0) return SCI_OK;
+    if (ctx->nwords == 2) return launch_singles_ds_w<RG, ST, CPLX, NV, TC, 2>(ctx, T, C, S, nvec, v0);
+    return launch_singles_ds_w<RG, ST, CPLX, NV, TC, 1>(ctx, T, C, S, nvec, v0);
 }
 
 template <bool RG, bool ST, bool CPLX, typename TC = double>
@@ -987,9 +1005,10 @@ template <bool RG, bool ST, typename TS, typename TC, int NV>
 int launch_singles(sci_ctx *ctx, const Tabs &T, const TC *C, typename AccOf<TS>::type *S, int nvec, int v0)
 {
     if (T.e1 == 0) return SCI_OK;
-    k_singles<TS, TC, NV, RG, ST><<<grid_for(T.e1), kThreads, 0, ctx->stream>>>(
-        T.e1_idx, T.e1_S, T.e1_meta, T.e1, ctx->norb, ctx->ref, (const TS *)ctx->fref, (const TS *)ctx->g_so, C, nvec,
-        v0, S, T.rr, ST ? ctx->det_inv1 : nullptr);
+    auto kern = ctx->nwords == 2 ? k_singles<TS, TC, NV, RG, ST, 2> : k_singles<TS, TC, NV, RG, ST, 1>;
+    kern<<<grid_for(T.e1), kThreads, 0, ctx->stream>>>(T.e1_idx, T.e1_S, T.e1_meta, T.e1, ctx->norb, ctx->ref,
+                                                       ctx->ref_hi, (const TS *)ctx->fref, (const TS *)ctx->g_so, C,
+                                                       nvec, v0, S, T.rr, ST ? ctx->det_inv1 : nullptr);
     return sci_cuda_check(ctx, cudaGetLastError(), "k_singles launch");
 }
 
@@ -1039,8 +1058,8 @@ __global__ void k_count2(const uint32_t *__restrict__ e_code, const uint32_t *__
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t pos = e_pos[p];
         const int64_t bs = p - sci::pos_off(pos), be = bs + sci::pos_size(pos);
-        const uint64_t m = sci::code_mask(e_code[p]);
-        for (int64_t q = bs; q < be; q++) cnt += (sci::code_mask(e_code[q]) & m) == 0;
+        const uint32_t cp = e_code[p];
+        for (int64_t q = bs; q < be; q++) cnt += !sci::codes_overlap(e_code[q], cp);
     }
     for (int o = 16; o; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
     if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(out, cnt);
@@ -1082,11 +1101,10 @@ __global__ void k_conn2(const uint32_t *__restrict__ e_idx, const uint32_t *__re
         if (I < rb || I >= re) continue;
         const uint32_t pos = e_pos[p], code = e_code[p];
         const int64_t bs = p - sci::pos_off(pos), be = bs + sci::pos_size(pos);
-        const uint64_t m = sci::code_mask(code);
         const int par = sci::code_par(code);
         for (int64_t q = bs; q < be; q++) {
             const uint32_t cq = e_code[q];
-            if (sci::code_mask(cq) & m) continue;
+            if (sci::codes_overlap(cq, code)) continue;
             conn_put(o, I, e_idx[q], 2, (par ^ (int)sci::code_par(cq)) ? -1 : 1);
         }
     }

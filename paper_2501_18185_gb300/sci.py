@@ -38,6 +38,7 @@ SIGNATURES = {
     "sci_set_stream": (_i32, [_vp, _vp]),
     "sci_set_integrals": (_i32, [_vp, _i32, _i32, _i32, _vp, _vp, _i32, _vp]),
     "sci_set_determinants": (_i32, [_vp, _vp, _i64, _i32, _i32, _i32]),
+    "sci_set_determinants_w": (_i32, [_vp, _vp, _i32, _i64, _i32, _i32, _i32]),
     "sci_diagonal": (_i32, [_vp, _vp]),
     "sci_sigma": (_i32, [_vp, _vp, _vp, _i32, _i32]),
     "sci_set_row_range": (_i32, [_vp, _i64, _i64]),
@@ -146,6 +147,10 @@ def sci_set_integrals(ctx, scalar, mode, n, h, eri=None, naux=0, chol=None):
 
 def sci_set_determinants(ctx, keys, M, n_alpha, n_beta, keys_on_device):
     return _check(ctx, load().sci_set_determinants(ctx, _p(keys), M, n_alpha, n_beta, keys_on_device))
+
+
+def sci_set_determinants_w(ctx, keys, nwords, M, n_alpha, n_beta, keys_on_device):
+    return _check(ctx, load().sci_set_determinants_w(ctx, _p(keys), nwords, M, n_alpha, n_beta, keys_on_device))
 
 
 def sci_diagonal(ctx, hdiag):
@@ -451,12 +456,13 @@ class Hamiltonian:
         if isinstance(keys, torch.Tensor):
             k = keys.contiguous()
             on_dev = int(k.is_cuda)
-            M = k.numel()
+            M = k.shape[0] if k.dim() else 0
         else:
             k = np.ascontiguousarray(keys, dtype=np.uint64)
             on_dev = 0
             M = len(k)
-        sci_set_determinants(self.ctx, k, M, n_alpha, n_beta if self.mode != "spinors" else -1, on_dev)
+        nwords = 1 if k.ndim == 1 else k.shape[1]      # [M] strings or [M, 2] words
+        sci_set_determinants_w(self.ctx, k, nwords, M, n_alpha, n_beta if self.mode != "spinors" else -1, on_dev)
         self.M = M
         self.n_alpha, self.n_beta = int(n_alpha), int(n_beta)
         self.row_range = (0, M)

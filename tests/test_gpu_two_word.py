@@ -1,0 +1,146 @@
+"""Determinants of more than 64 spin-orbitals (two-word keys, sci_set_determinants_w)
+against the oracle, which holds every string as a 128-bit integer.
+
+The selected 40-orbital space (80 spin-orbitals: beta strings cross the word boundary):
+connections, degrees and phases bit-exact, per-row pair counts exact, the diagonal to 1e-12,
+FP64 and paired-FP32 sigma to 1e-11, FP32-storage sigma within its per-row bound, the
+deterministic mode bit for bit.  The opposite-spin two-electron closed form on 40 orbitals
+and a 72-spinor space are checked as dense matrices.
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from paper_2501_18185_gb300 import sci
+from paper_2501_18185_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-11
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def sel2w():
+    w = W.selected_two_word(n=40, na=4, nb=4, M=40000, nvec=3)
+    return w, Oracle.from_workload(w)
+
+
+def _rows(w, k=600, seed=0):
+    r = np.random.default_rng(seed).choice(w.M, k, replace=False)
+    return np.unique(np.concatenate([r, [0, w.M - 1]]))
+
+
+def test_two_word_connections_counts_and_diagonal(gpu, sel2w):
+    torch = gpu
+    w, o = sel2w
+    H = sci.Hamiltonian.from_workload(w)
+    rows = _rows(w, 200)
+    for r in rows[:60]:
+        J, deg, ph = o.connections(int(r))
+        got = H.connections(int(r), int(r) + 1)
+        assert np.array_equal(got[1], J) and np.array_equal(got[2], deg) and np.array_equal(got[3], ph), r
+    cost = H.row_costs().cpu().numpy()
+    for r in rows:
+        assert cost[r] == len(o.connections(int(r))[0])
+    assert int(cost.sum()) == H.count_pairs()
+    d = H.diagonal().cpu().numpy()
+    ref = o.diagonal()
+    assert np.abs(d - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_two_word_sigma_all_precisions(gpu, sel2w):
+    torch = gpu
+    w, o = sel2w
+    H = sci.Hamiltonian.from_workload(w)
+    C = torch.from_numpy(np.ascontiguousarray(w.c)).cuda()
+    rows = _rows(w)
+    ref = o.sigma_rows(rows, w.c)
+    assert _rel(H.sigma(C).cpu().numpy()[rows], ref) < TOL
+    assert _rel(H.sigma(C, prec=sci.SCI_PREC_F64_DS).cpu().numpy()[rows], ref) < TOL
+    # FP32 storage: within 2^-24 of each row's magnitude sum, against the oracle on the
+    # FP32-rounded vectors (the pair table's one rounding)
+    C32 = np.ascontiguousarray(w.c, dtype=np.float32)
+    S32 = H.sigma(torch.from_numpy(C32).cuda(), prec=sci.SCI_PREC_F32_STORE_F64_ACC).cpu().numpy()
+    ref32 = o.sigma_rows(rows, C32.astype(np.float64))
+    A = o.sigma_abs_rows(rows, C32.astype(np.float64))
+    assert (np.abs(S32[rows] - ref32) <= 1.05 * 2.0 ** -24 * A + 1e-300).all()
+    # deterministic accumulation: bit for bit, and the atomic result to 1e-13
+    at = H.sigma(C).cpu().numpy()
+    H.set_deterministic(3)
+    a, b = H.sigma(C).cpu().numpy(), H.sigma(C).cpu().numpy()
+    assert np.array_equal(a, b) and _rel(a, at) < 1e-13
+    H.sync_status()
+
+
+def test_two_word_opposite_spin_closed_form_and_one_word_encoding(gpu):
+    """1 alpha + 1 beta over 40 orbitals: H from sigma on the unit vectors equals
+    h x 1 + 1 x h + V; and a one-word space given as two words gives the one-word sigma."""
+    torch = gpu
+    n = 40
+    rng = np.random.default_rng(11)
+    ints = W.real_integrals(rng, n, 6, 0.95)
+    a = np.array([1 << p for q in range(n) for p in range(n)], dtype=np.uint64)
+    b = np.array([1 << q for q in range(n) for p in range(n)], dtype=np.uint64)
+    keys = W.sort_words(W.two_word_keys(a, b, n))
+    H = sci.Hamiltonian()
+    H.set_integrals("spin_orbitals", ints.h, chol=ints.chol)
+    H.set_determinants(keys, 1, 1)
+    E = torch.eye(n * n, dtype=torch.float64, device="cuda")
+    Hd = H.sigma(E).cpu().numpy()
+    h, eri = ints.h, ints.eri()
+    expected = np.kron(np.eye(n), h) + np.kron(h, np.eye(n)) + eri.transpose(2, 0, 3, 1).reshape(n * n, n * n)
+    assert np.abs(Hd - expected).max() < 1e-12 * np.abs(expected).max()
+    # one-word space as two words
+    w = W.random_small(31, "spin_orbitals", 6, 3, 2, naux=4, frac=0.5)
+    H1 = sci.Hamiltonian.from_workload(w)
+    H2 = sci.Hamiltonian()
+    H2.set_integrals(w.mode, w.ints.h, chol=w.ints.chol)
+    H2.set_determinants(np.stack([w.keys, np.zeros_like(w.keys)], axis=1), w.n_alpha, w.n_beta)
+    C = torch.from_numpy(w.c).cuda()
+    assert _rel(H2.sigma(C).cpu().numpy(), H1.sigma(C).cpu().numpy()) < 1e-14
+
+
+def test_two_word_spinors(gpu):
+    """72 complex spinors, 3 electrons on a random subset: dense H by sigma against the
+    oracle's dense H (elements by operator application)."""
+    torch = gpu
+    n, N = 72, 3
+    rng = np.random.default_rng(21)
+    ints = W.complex_integrals(rng, n, 5, 0.95)
+    import itertools
+    occ = [c for c in itertools.combinations(range(n), N) if rng.random() < 0.004 or c == (0, 1, 2)]
+    lo = np.array([sum(1 << p for p in c if p < 64) for c in occ], dtype=np.uint64)
+    hi = np.array([sum(1 << (p - 64) for p in c if p >= 64) for c in occ], dtype=np.uint64)
+    keys = W.sort_words(np.stack([lo, hi], axis=1))
+    o = Oracle("spinors", n, ints.h, ints.eri(), keys)
+    H = sci.Hamiltonian()
+    H.set_integrals("spinors", ints.h, chol=ints.chol)
+    H.set_determinants(keys, N, -1)
+    M = len(keys)
+    E = torch.eye(M, dtype=torch.complex128, device="cuda")
+    Hd = H.sigma(E).cpu().numpy()
+    ref = o.dense()
+    assert np.abs(Hd - ref).max() < 1e-12 * np.abs(ref).max()
+    assert M > 200
+
+
+def test_two_word_limits(gpu, sel2w):
+    torch = gpu
+    w, _ = sel2w
+    H = sci.Hamiltonian.from_workload(w)
+    C = torch.from_numpy(np.ascontiguousarray(w.c[:, :1])).cuda()
+    with pytest.raises(sci.SciError):            # one-word keys only
+        H.rdm12(C)
+    with pytest.raises(sci.SciError):
+        H.enpt2(C, [0.0])
+    with pytest.raises(sci.SciError):
+        H.set_row_range(0, 100)
+    with pytest.raises(sci.SciError):            # more than 64 spin-orbitals need two words
+        sci.sci_set_determinants(H.ctx, np.ascontiguousarray(w.keys[:, 0]), w.M, 4, 4, 0)
+    bad = w.keys.copy()
+    bad[[3, 4]] = bad[[4, 3]]
+    with pytest.raises(sci.SciError):
+        H.set_determinants(bad, 4, 4)            # not ascending as 128-bit integers
