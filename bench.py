@@ -644,6 +644,89 @@ def spinor_bench(device, steps=10, warmup=3):
     return out
 
 
+def two_word_bench(H, w, device, steps=10, warmup=3, M=2_000_000):
+    """Occupation strings of more than 64 spin-orbitals (two 64-bit words per key).
+    (1) The bench space given as [M, 2] keys with a zero high word: the same pairs through
+    the two-word set-up and singles code, against the one-word sigma of `H`.  (2) A
+    selected space of 40 spatial orbitals (80 spin-orbitals, 8 alpha + 8 beta electrons:
+    HF, all singles and doubles, seeded random triples up to M): FP64 sigma on one vector,
+    CUDA-event milliseconds (L2 flushed), the doubles kernel's algorithmic-byte fraction of
+    HBM and useful FMAs against the measured FP64 pipe rate, and the oracle (128-bit keys)
+    on sampled rows."""
+    import torch
+
+    from paper_2501_18185_gb300 import sci
+
+    dev = torch.device("cuda", device)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=dev)
+
+    def timed(Hx, C):
+        S = torch.empty_like(C)
+        for _ in range(warmup):
+            Hx.sigma(C, out=S)
+        sci.sci_profile(Hx.ctx, True)
+        ms, kern = [], []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            Hx.sigma(C, out=S)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            kern.append(sci.sci_kernel_times(Hx.ctx))
+        sci.sci_profile(Hx.ctx, False)
+        Hx.sync_status()
+        return S, statistics.mean(ms), {"init": statistics.mean(k[0] for k in kern),
+                                        "doubles": statistics.mean(k[1] for k in kern),
+                                        "singles": statistics.mean(k[2] for k in kern)}
+
+    out = {}
+    C = torch.from_numpy(np.ascontiguousarray(w.c)).to(dev)
+    S1, ms1, k1 = timed(H, C)
+    keys2 = np.zeros((w.M, 2), dtype=np.uint64)
+    keys2[:, 0] = w.keys
+    t = time.perf_counter()
+    H2 = sci.Hamiltonian(device, stream)
+    H2.set_integrals(w.mode, w.ints.h, chol=w.ints.chol)
+    H2.set_determinants(keys2, w.n_alpha, w.n_beta)
+    torch.cuda.synchronize()
+    setup2 = time.perf_counter() - t
+    if H2.count_pairs() != H.count_pairs():
+        raise SystemExit("two-word pair count differs from the one-word count")
+    S2, ms2, k2 = timed(H2, C)
+    rel = float(torch.linalg.norm(S2 - S1) / torch.linalg.norm(S1))
+    out["same_space_two_words"] = {"workload": w.name, "one_word_ms": ms1, "two_word_ms": ms2,
+                                   "one_word_kernel_ms": k1, "two_word_kernel_ms": k2,
+                                   "two_word_setup_s": round(setup2, 3), "rel_diff": rel}
+    del H2, S1, S2, C
+    torch.cuda.empty_cache()
+
+    w2 = W.selected_two_word(n=40, na=8, nb=8, M=M)
+    t = time.perf_counter()
+    H3 = sci.Hamiltonian.from_workload(w2, device=device)
+    torch.cuda.synchronize()
+    setup3 = time.perf_counter() - t
+    info = H3.info()
+    C = torch.from_numpy(np.ascontiguousarray(w2.c)).to(dev)
+    _, ms3, k3 = timed(H3, C)
+    peak, peak_kind = hbm_peak()
+    pp = pipe_peaks(device)
+    achieved = info["pairs_doubles"] * 16 / (k3["doubles"] / 1e3) / 1e9
+    fma = info["pairs_doubles"] / (k3["doubles"] / 1e3)
+    out["selected_80so"] = {"workload": w2.name, "M": w2.M, "pairs_per_step": info["pairs"],
+                            "pairs_doubles": info["pairs_doubles"], "setup_s": round(setup3, 3),
+                            "ms_per_step": ms3, "pairs_per_s": info["pairs"] / (ms3 / 1e3), "kernel_ms": k3,
+                            "doubles_alg_GBps": achieved, "doubles_alg_frac_hbm": achieved / peak,
+                            "fp64_pipe_frac": fma / pp["fp64_fma_per_s"],
+                            "l2": "flushed between timed steps (256 MB write)",
+                            "cpu_baseline": cpu_baseline(w2, budget_s=6.0, one_thread_s=2.0)}
+    del H3, C
+    torch.cuda.empty_cache()
+    return out
+
+
 def deterministic_bench(H, w, steps=10):
     """sigma with deterministic accumulation (sci_set_deterministic: row sums stored per
     bucket entry, then summed per row in a fixed order) against the default FP64 atomics,
@@ -811,7 +894,7 @@ def main():
     ap.add_argument("--pt2-table-gb", type=float, default=96.0, help="hash-table memory of the pt2 section")
     ap.add_argument("--no-spinor", action="store_true", help="skip the 64-spinor complex workload section")
     ap.add_argument("--only", default=None, choices=["blockvec", "rdm", "batch", "davidson", "pt2", "spinor",
-                                                     "rowsplit", "pt2_spinor", "deterministic"],
+                                                     "rowsplit", "pt2_spinor", "deterministic", "two_word"],
                     help="run one side section alone and print its JSON (profiling runs)")
     ap.add_argument("--prec", default="f64", choices=["f64", "ds", "f32"],
                     help="f64: FP64 FMA path; ds: paired-FP32 products/sums (FP64 tolerance); "
@@ -883,9 +966,10 @@ def main():
         split.rebalance(e0.elapsed_time(e1) / 3, split.weights)
         del Cw, Sw
 
-    if args.only in ("rdm", "davidson", "rowsplit", "deterministic"):
+    if args.only in ("rdm", "davidson", "rowsplit", "deterministic", "two_word"):
         out = (rdm_bench(H, w) if args.only == "rdm" else davidson_bench(H, w) if args.only == "davidson"
-               else rowsplit_bench(H) if args.only == "rowsplit" else deterministic_bench(H, w))
+               else rowsplit_bench(H) if args.only == "rowsplit" else two_word_bench(H, w, local)
+               if args.only == "two_word" else deterministic_bench(H, w))
         print(json.dumps({args.only: out}), flush=True)
         return
     C64 = torch.from_numpy(np.ascontiguousarray(w.c)).to(dev)
@@ -1022,7 +1106,7 @@ def main():
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(w)
     dav = None
-    rdm = batch = pt2 = rowsplit = determ = None
+    rdm = batch = pt2 = rowsplit = determ = two_word = None
     if not args.no_davidson and world == 1 and not w.ints.complex_:
         dav = davidson_bench(H, w)
         dav["blockvec"] = blockvec_bench()
@@ -1032,6 +1116,7 @@ def main():
         pt2.append({"spinor": pt2_spinor_bench()})
         rowsplit = rowsplit_bench(H)
         determ = deterministic_bench(H, w)
+        two_word = two_word_bench(H, w, local)
     spinor = None
     if not args.no_spinor and world == 1 and not w.ints.complex_:
         spinor = spinor_bench(local)
@@ -1050,7 +1135,7 @@ def main():
                                           * ((nv + 7) // 8 if not w.ints.complex_ else (nv + 3) // 4)),
             "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "prec": args.prec,
             "other_prec": variant, "pipe_peaks": pp, "davidson": dav, "rdm": rdm, "batch": batch, "pt2": pt2,
-            "spinor": spinor, "rowsplit": rowsplit, "deterministic": determ}
+            "spinor": spinor, "rowsplit": rowsplit, "deterministic": determ, "two_word": two_word}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
