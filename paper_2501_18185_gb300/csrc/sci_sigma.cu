@@ -1169,51 +1169,68 @@ __device__ __forceinline__ double diag_times(double h, double c) { return h * c;
 __device__ __forceinline__ double diag_times(double h, float c) { return h * (double)c; }
 __device__ __forceinline__ zdbl diag_times(double h, zdbl c) { return zdbl{h * c.x, h * c.y}; }
 
+// Lanes per row of k_row_sums.  A row holds ~C(N,2)/2 + N slots on average (about 100 on
+// the 20-electron spaces), so four lanes per row keep the lanes busy and the butterfly at
+// two levels; a warp per row spent more FP64 adds on its butterfly and on padding than on
+// the slots (2M-determinant space, one vector: 1.97 ms with a warp per row, FP64 pipe 83%
+// busy in ncu; 0.80 ms with four lanes).
+constexpr int kRowLanes = 4;
+
 template <typename TC, typename TA, int NV>
 __global__ void __launch_bounds__(kThreads)
 k_row_sums(int64_t M, int nvec, int v0, const double *__restrict__ hdiag, const TC *__restrict__ C,
            const uint32_t *__restrict__ ptr2, const TA *__restrict__ part2, const uint32_t *__restrict__ ptr1,
            const TA *__restrict__ part1, TA *__restrict__ S)
 {
-    const int lane = threadIdx.x & 31;
+    constexpr int G = kRowLanes, RPW = 32 / G;   // lanes per row, rows per warp
+    const int lane = threadIdx.x & 31, gl = lane & (G - 1);
     const int64_t warps = (int64_t)gridDim.x * (kThreads / 32);
-    for (int64_t I = ((int64_t)blockIdx.x * kThreads + threadIdx.x) / 32; I < M; I += warps) {
+    // warp-uniform loop (the butterfly needs every lane); a lane past M adds nothing
+    for (int64_t Ib = ((int64_t)blockIdx.x * kThreads + threadIdx.x) / 32 * RPW; Ib < M; Ib += warps * RPW) {
+        const int64_t I = Ib + lane / G;
         TA acc[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) zero(acc[v]);
-        // the row's doubles slots, then its singles slots; four slots per lane in flight
-        // per step (loaded before they are added), each lane adding its own slots in order
-        for (int tab = 0; tab < 2; tab++) {
-            const uint32_t *ptr = tab ? ptr1 : ptr2;
-            const TA *part = tab ? part1 : part2;
-            const uint32_t end = ptr[I + 1];
-            for (uint32_t t0 = ptr[I] + lane; t0 < end; t0 += 4 * 32) {
-                TA x[4][NV];
+        if (I < M) {
+            // the row's doubles slots, then its singles slots: lane gl adds slots gl, gl + G,
+            // ... in order, four loads in flight per step, each add predicated on its slot
+            for (int tab = 0; tab < 2; tab++) {
+                const uint32_t *ptr = tab ? ptr1 : ptr2;
+                const TA *part = tab ? part1 : part2;
+                const uint32_t end = ptr[I + 1];
+                for (uint32_t t0 = ptr[I] + gl; t0 < end; t0 += 4 * G) {
+                    TA x[4][NV];
 #pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    const uint32_t t = t0 + 32u * u;
-                    const TA *src = part + (int64_t)t * nvec + v0;
+                    for (int u = 0; u < 4; u++) {
+                        const uint32_t t = t0 + G * u;
+                        const TA *src = part + (int64_t)t * nvec + v0;
 #pragma unroll
-                    for (int v = 0; v < NV; v++) {
-                        zero(x[u][v]);
-                        if (t < end) x[u][v] = src[v];
+                        for (int v = 0; v < NV; v++) {
+                            zero(x[u][v]);
+                            if (t < end) x[u][v] = src[v];
+                        }
                     }
+#pragma unroll
+                    for (int u = 0; u < 4; u++)
+                        if (t0 + G * u < end)
+#pragma unroll
+                            for (int v = 0; v < NV; v++) add_to(acc[v], x[u][v]);
                 }
-#pragma unroll
-                for (int u = 0; u < 4; u++)
-#pragma unroll
-                    for (int v = 0; v < NV; v++) add_to(acc[v], x[u][v]);
             }
         }
 #pragma unroll
         for (int v = 0; v < NV; v++)
-            for (int o = 16; o; o >>= 1) add_to(acc[v], shfl_xor(acc[v], o));
-        if (lane < NV) {
-            TA out = diag_times(hdiag[I], C[I * nvec + v0 + lane]);
+#pragma unroll
+            for (int o = G / 2; o; o >>= 1) add_to(acc[v], shfl_xor(acc[v], o));
+        if (I < M) {
+            // lane gl writes vectors gl, gl + G, ...: H_II c_I plus the row sum
 #pragma unroll
             for (int v = 0; v < NV; v++)
-                if (v == lane) add_to(out, acc[v]);
-            S[I * nvec + v0 + lane] = out;
+                if (v % G == gl) {
+                    TA out = diag_times(hdiag[I], C[I * nvec + v0 + v]);
+                    add_to(out, acc[v]);
+                    S[I * nvec + v0 + v] = out;
+                }
         }
     }
 }
@@ -1222,7 +1239,7 @@ template <typename TC, typename TA>
 int row_sums(sci_ctx *ctx, const TC *C, TA *S, int nvec)
 {
     const int64_t M = ctx->M;
-    const int grid = grid_for(M * 32);
+    const int grid = grid_for(M * kRowLanes);
     auto go = [&](auto kern, int v0) {
         kern<<<grid, kThreads, 0, ctx->stream>>>(M, nvec, v0, ctx->hdiag, C, ctx->det_ptr2, (const TA *)ctx->det_part2,
                                                  ctx->det_ptr1, (const TA *)ctx->det_part1, S);
