@@ -113,6 +113,16 @@ int sci_set_stream(sci_ctx *ctx, void *cuda_stream);
 int sci_set_integrals(sci_ctx *ctx, int scalar, int mode, int n, const void *h,
                       const void *eri, int naux, const void *chol);
 
+/* The same with the integrals' location given: on_device = 0 reads h, eri and chol from
+ * host memory (as sci_set_integrals); on_device = 1 reads them from memory of the
+ * context's device (or managed memory), in place, with the same layouts, and runs the
+ * symmetry checks on the device (max |a - b| over symmetric pairs against 1e-10 of the
+ * largest magnitude; a value that is not finite is rejected).  Pointers that are not
+ * memory of the context's device return SCI_ERR_ARG.  The caller keeps ownership; the
+ * buffers are not read after the call returns.  Synchronous. */
+int sci_set_integrals_ex(sci_ctx *ctx, int scalar, int mode, int n, const void *h,
+                         const void *eri, int naux, const void *chol, int on_device);
+
 /* Load a strictly ascending determinant list (Sec. 3.2, BasisManager) and build the
  * connection tables: keys are validated on the device (order, duplicates, electron
  * counts), the (N-2)- and (N-1)-hole bucket tables are sorted out, and the diagonal

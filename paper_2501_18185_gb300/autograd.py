@@ -26,12 +26,13 @@ class _Energy(torch.autograd.Function):
     @staticmethod
     def forward(ctx, h, L, C, ham, kind):
         n = h.shape[0]
-        hn = h.detach().cpu().numpy()
-        Ln = L.detach().cpu().numpy()
+        # the integrals stay on the device: sci_set_integrals_ex reads them in place
+        hd = h.detach().to(ham.device)
+        Ld = L.detach().to(ham.device)
         if kind == "chol":
-            ham.set_integrals("spin_orbitals", hn, chol=Ln)
+            ham.set_integrals("spin_orbitals", hd, chol=Ld)
         else:
-            ham.set_integrals("spin_orbitals", hn, eri=Ln)
+            ham.set_integrals("spin_orbitals", hd, eri=Ld)
         Cd = C.detach().contiguous()
         S = ham.sigma(Cd)
         den = (Cd * Cd).sum(dim=0)

@@ -164,6 +164,37 @@ __device__ __forceinline__ uint32_t code_of(const uint32_t *g, uint32_t s)
     return c;
 }
 
+// A warp's queue of found excitations (packed orbital quadruples), in shared memory, 64
+// entries.  The code lookups find 0, 1 or a few second virtuals per (pair, first virtual)
+// class, so a lane that inserted its own finds would leave most of the warp idle; the
+// finds of a step are appended by ballot instead, and each time 32 are queued every lane
+// inserts one.  `cnt` is the same in every lane.  Spinor mode, 120k-determinant 64-spinor
+// space, 1 GB table: 10 -> 27 active lanes per instruction, 8.9 -> 3.3 ms per generation
+// launch (ncu), 1.09 -> 0.88 s for the whole sum.
+template <typename F>
+__device__ __forceinline__ void wq_push(uint32_t *q, int &cnt, bool hit, uint32_t e, int lane, F &&proc)
+{
+    const unsigned m = __ballot_sync(0xffffffffu, hit);
+    if (hit) q[cnt + __popc(m & ((1u << lane) - 1u))] = e;
+    cnt += __popc(m);
+    __syncwarp();
+    if (cnt >= 32) {
+        proc(q[lane]);
+        __syncwarp();
+        cnt -= 32;
+        if (lane < cnt) q[lane] = q[32 + lane];
+        __syncwarp();
+    }
+}
+
+template <typename F>
+__device__ __forceinline__ void wq_flush(uint32_t *q, int &cnt, int lane, F &&proc)
+{
+    if (lane < cnt) proc(q[lane]);
+    __syncwarp();
+    cnt = 0;
+}
+
 // warp per determinant J of P: the excitations of J that fall in batch `batch`
 template <int R>
 __global__ void __launch_bounds__(kThreads)
@@ -252,7 +283,8 @@ k_pt2_gen(const uint64_t *__restrict__ Pkeys, int64_t M, const double *__restric
         }
 
         // beta-beta doubles j1 < j2 -> b1 < b2: for each occupied pair and first virtual
-        // b1, the second virtual has code target ^ g(j1) ^ g(j2) ^ g(b1)
+        // b1, the second virtual has code target ^ g(j1) ^ g(j2) ^ g(b1).  (A warp queue
+        // as in spinor mode made the 2M-space sum slower here: 7.9 -> 9.4 s.)
         const int pb = nb * (nb - 1) / 2;
         for (int t = lane; t < pb * ub; t += 32) {
             const uint16_t po = s_pair[t / ub];
@@ -348,6 +380,7 @@ k_pt2_gen_z(const uint64_t *__restrict__ Pkeys, int64_t M, const zdbl *__restric
     __shared__ uint8_t s_cstart[(1 << kMaxBits) + 1];
     __shared__ uint8_t s_obc[64];                // spinors sorted by code
     __shared__ uint32_t s_g[64];                 // spinor codes
+    __shared__ uint32_t s_q[kWarps][64];         // the warp's queue of double finds
     for (int P = threadIdx.x; P < kMaxPairs64; P += blockDim.x) {
         int y = 1;
         while ((y + 1) * y / 2 <= P) y++;
@@ -391,20 +424,36 @@ k_pt2_gen_z(const uint64_t *__restrict__ Pkeys, int64_t M, const zdbl *__restric
             }
         }
         // doubles i < j -> a < b: for each occupied pair and first virtual a, the second
-        // virtual has code target ^ g(i) ^ g(j) ^ g(a)
-        for (int t = lane; t < npairs * nv; t += 32) {
-            const uint16_t po = s_pair[t / nv];
-            const int i = orb[po & 0xFF], j = orb[po >> 8], a = orb[64 + t % nv];
-            if (p.bss3 && p.bss3[(j * (j - 1) / 2 + i) * n + a] * cmax < p.eps) continue;   // the class's bound
-            const uint32_t c = target ^ s_g[i] ^ s_g[j] ^ s_g[a];
-            for (int q = s_cstart[c]; q < s_cstart[c + 1]; q++) {
-                const int b = s_obc[q];
-                if (b <= a || ((key >> b) & 1)) continue;
-                const uint64_t I = (key & ~(1ull << i) & ~(1ull << j)) | (1ull << a) | (1ull << b);
-                insert_z<R>(p, I, hz_double(p, key, i, j, a, b), cJ, cmax);
+        // virtual has code target ^ g(i) ^ g(j) ^ g(a); the finds go through the warp's queue
+        auto ins = [&](uint32_t e) {
+            const int i = e & 0xFF, j = (e >> 8) & 0xFF, a = (e >> 16) & 0xFF, b = e >> 24;
+            const uint64_t I = (key & ~(1ull << i) & ~(1ull << j)) | (1ull << a) | (1ull << b);
+            insert_z<R>(p, I, hz_double(p, key, i, j, a, b), cJ, cmax);
+        };
+        int cnt = 0;
+        for (int base = 0; base < npairs * nv; base += 32) {
+            const int t = base + lane;
+            int q = 0, qe = 0, i = 0, j = 0, a = 0;
+            if (t < npairs * nv) {
+                const uint16_t po = s_pair[t / nv];
+                i = orb[po & 0xFF], j = orb[po >> 8], a = orb[64 + t % nv];
+                if (!(p.bss3 && p.bss3[(j * (j - 1) / 2 + i) * n + a] * cmax < p.eps)) {   // the class's bound
+                    const uint32_t c = target ^ s_g[i] ^ s_g[j] ^ s_g[a];
+                    q = s_cstart[c], qe = s_cstart[c + 1];
+                }
+            }
+            for (; __any_sync(0xffffffffu, q < qe); q++) {
+                bool hit = false;
+                int b = 0;
+                if (q < qe) {
+                    b = s_obc[q];
+                    hit = b > a && !((key >> b) & 1);
+                }
+                wq_push(s_q[w], cnt, hit, (uint32_t)i | (uint32_t)j << 8 | (uint32_t)a << 16 | (uint32_t)b << 24, lane,
+                        ins);
             }
         }
-        __syncwarp();
+        wq_flush(s_q[w], cnt, lane, ins);
     }
 }
 

@@ -735,6 +735,76 @@ int compute_diag_fref(sci_ctx *ctx)
     return SCI_OK;
 }
 
+// Symmetry checks of integrals given on the device: o[0] = max |x|, o[1] = max |a - b| over
+// the pairs that the symmetry makes equal, by atomicMax on the bits of nonnegative doubles
+// (their order as unsigned integers is that of the values).  A thread that meets a value
+// that is not finite posts a NaN, whose bits sort above every number.
+__device__ __forceinline__ void amax_bits(unsigned long long *o, double v, bool bad)
+{
+    const unsigned long long nan_bits = 0x7FF8000000000000ull;
+    atomicMax(o, bad ? nan_bits : (unsigned long long)__double_as_longlong(fabs(v)));
+}
+
+__device__ __forceinline__ bool finite(double x) { return fabs(x) <= 1.7976931348623157e308; }
+
+__global__ void k_chk_abs(const double *__restrict__ x, int64_t cnt, unsigned long long *o)
+{
+    double m = 0.0;
+    bool bad = false;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x) {
+        m = fmax(m, fabs(x[t]));
+        bad |= !finite(x[t]);
+    }
+    amax_bits(o, m, bad);
+}
+
+// h Hermitian: h_pq = conj(h_qp)
+__global__ void k_chk_h(const double *__restrict__ h, int n, int sw, unsigned long long *o)
+{
+    double m = 0.0;
+    bool bad = false;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)n * n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = t / n, q = t % n, a = p * n + q, b = q * n + p;
+        m = fmax(m, fabs(h[a * sw] - h[b * sw]));
+        if (sw == 2) m = fmax(m, fabs(h[a * sw + 1] + h[b * sw + 1]));
+        bad |= !finite(h[a * sw]) || (sw == 2 && !finite(h[a * sw + 1]));
+    }
+    amax_bits(o, m, bad);
+}
+
+// (pq|rs) = (rs|pq) = conj((qp|sr))
+__global__ void k_chk_eri(const double *__restrict__ e, int n, int sw, unsigned long long *o)
+{
+    const int64_t n2 = (int64_t)n * n, n4 = n2 * n2;
+    double m = 0.0;
+    bool bad = false;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n4; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t pq = t / n2, rs = t % n2, p = pq / n, q = pq % n, r = rs / n, s_ = rs % n;
+        const int64_t b = rs * n2 + pq, c = (q * n + p) * n2 + s_ * n + r;
+        m = fmax(m, fmax(fabs(e[t * sw] - e[b * sw]), fabs(e[t * sw] - e[c * sw])));
+        if (sw == 2) m = fmax(m, fmax(fabs(e[t * sw + 1] - e[b * sw + 1]), fabs(e[t * sw + 1] + e[c * sw + 1])));
+        bad |= !finite(e[t * sw]) || (sw == 2 && !finite(e[t * sw + 1]));
+    }
+    amax_bits(o, m, bad);
+}
+
+// each Cholesky vector Hermitian: L^P_pq = conj(L^P_qp)
+__global__ void k_chk_chol(const double *__restrict__ L, int naux, int n, int sw, unsigned long long *o)
+{
+    const int64_t n2 = (int64_t)n * n;
+    double m = 0.0;
+    bool bad = false;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)naux * n2;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t P = t / n2, pq = t % n2, p = pq / n, q = pq % n, b = P * n2 + q * n + p;
+        m = fmax(m, fabs(L[t * sw] - L[b * sw]));
+        if (sw == 2) m = fmax(m, fabs(L[t * sw + 1] + L[b * sw + 1]));
+        bad |= !finite(L[t * sw]) || (sw == 2 && !finite(L[t * sw + 1]));
+    }
+    amax_bits(o, m, bad);
+}
+
 bool rel_close(double a, double b, double scale) { return std::fabs(a - b) <= 1e-10 * scale; }
 
 }  // namespace
@@ -792,8 +862,73 @@ extern "C" int sci_set_stream(sci_ctx *ctx, void *cuda_stream)
     return SCI_OK;
 }
 
+namespace {
+// the device-side form of the host symmetry checks below, for integrals given on the device
+int check_ints_device(sci_ctx *ctx, int cplx, int n, const double *h, const double *eri, int naux, const double *chol)
+{
+    cudaStream_t st = ctx->stream;
+    const int sw = cplx ? 2 : 1;
+    const int64_t n2 = (int64_t)n * n, n4 = n2 * n2;
+    TmpBuf o;
+    SCI_CK(cudaMalloc(&o.p, 4 * sizeof(unsigned long long)));
+    SCI_CK(cudaMemsetAsync(o.p, 0, 4 * sizeof(unsigned long long), st));
+    unsigned long long *ob = o.as<unsigned long long>();
+    k_chk_abs<<<grid_for(n2 * sw), 256, 0, st>>>(h, n2 * sw, ob);
+    k_chk_h<<<grid_for(n2), 256, 0, st>>>(h, n, sw, ob + 1);
+    if (eri) {
+        k_chk_abs<<<grid_for(n4 * sw), 256, 0, st>>>(eri, n4 * sw, ob + 2);
+        k_chk_eri<<<grid_for(n4), 256, 0, st>>>(eri, n, sw, ob + 3);
+    } else {
+        k_chk_abs<<<grid_for((int64_t)naux * n2 * sw), 256, 0, st>>>(chol, (int64_t)naux * n2 * sw, ob + 2);
+        k_chk_chol<<<grid_for((int64_t)naux * n2), 256, 0, st>>>(chol, naux, n, sw, ob + 3);
+    }
+    SCI_CK(cudaGetLastError());
+    unsigned long long r[4] = {0, 0, 0, 0};
+    SCI_CK(cudaMemcpyAsync(r, ob, sizeof(r), cudaMemcpyDeviceToHost, st));
+    SCI_CK(cudaStreamSynchronize(st));
+    const unsigned long long inf_bits = 0x7FF0000000000000ull;
+    if (r[0] >= inf_bits || r[1] >= inf_bits) return sci_fail(ctx, SCI_ERR_ARG, "h has a value that is not finite");
+    if (r[2] >= inf_bits || r[3] >= inf_bits)
+        return sci_fail(ctx, SCI_ERR_ARG, "the integrals have a value that is not finite");
+    double v[4];
+    std::memcpy(v, r, sizeof(v));
+    if (!rel_close(v[1], 0.0, v[0] + 1e-300)) return sci_fail(ctx, SCI_ERR_ARG, "h is not Hermitian");
+    if (!rel_close(v[3], 0.0, v[2] + 1e-300))
+        return sci_fail(ctx, SCI_ERR_ARG, eri ? "eri lacks (pq|rs)=(rs|pq)=(qp|sr)^* symmetry"
+                                              : "Cholesky vectors are not Hermitian");
+    return SCI_OK;
+}
+
+// a device pointer of the context's device (or managed memory)
+bool on_ctx_device(const sci_ctx *ctx, const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeManaged || (a.type == cudaMemoryTypeDevice && a.device == ctx->device);
+}
+
+int set_ints(sci_ctx *ctx, int scalar, int mode, int n, const void *h, const void *eri, int naux, const void *chol,
+             int on_device);
+}  // namespace
+
 extern "C" int sci_set_integrals(sci_ctx *ctx, int scalar, int mode, int n, const void *h, const void *eri,
                                  int naux, const void *chol)
+{
+    return set_ints(ctx, scalar, mode, n, h, eri, naux, chol, 0);
+}
+
+extern "C" int sci_set_integrals_ex(sci_ctx *ctx, int scalar, int mode, int n, const void *h, const void *eri,
+                                    int naux, const void *chol, int on_device)
+{
+    return set_ints(ctx, scalar, mode, n, h, eri, naux, chol, on_device);
+}
+
+namespace {
+int set_ints(sci_ctx *ctx, int scalar, int mode, int n, const void *h, const void *eri, int naux, const void *chol,
+             int on_device)
 {
     if (!ctx) return SCI_ERR_ARG;
     ctx->err.clear();
@@ -812,6 +947,12 @@ extern "C" int sci_set_integrals(sci_ctx *ctx, int scalar, int mode, int n, cons
     const double *hd = (const double *)h;
     int64_t n2 = (int64_t)n * n, n4 = n2 * n2;
 
+    if (on_device) {
+        if (!on_ctx_device(ctx, h) || (eri && !on_ctx_device(ctx, eri)) || (chol && !on_ctx_device(ctx, chol)))
+            return sci_fail(ctx, SCI_ERR_ARG, "on_device: h, eri and chol must be memory of the context's device");
+        int rc = check_ints_device(ctx, cplx, n, hd, (const double *)eri, naux, (const double *)chol);
+        if (rc != SCI_OK) return rc;
+    } else {
     // ---- host-side symmetry checks (h Hermitian; (pq|rs) = (rs|pq) = (qp|sr)^*)
     double hs = 0;
     for (int64_t t = 0; t < n2 * sw; t++) hs = std::max(hs, std::fabs(hd[t]));
@@ -853,6 +994,7 @@ extern "C" int sci_set_integrals(sci_ctx *ctx, int scalar, int mode, int n, cons
                         return sci_fail(ctx, SCI_ERR_ARG, "Cholesky vectors are not Hermitian");
                 }
     }
+    }
 
     int keep_dets = ctx->have_dets && ctx->have_ints && ctx->cplx == cplx && ctx->n == n &&
                     ctx->spinors == (mode == SCI_SPINORS);
@@ -865,18 +1007,29 @@ extern "C" int sci_set_integrals(sci_ctx *ctx, int scalar, int mode, int n, cons
     const size_t sb = cplx ? 16 : 8;
     cudaStream_t st = ctx->stream;
 
-    TmpBuf dh, deri;
-    SCI_CK(cudaMalloc(&dh.p, n2 * sb));
-    SCI_CK(cudaMemcpyAsync(dh.p, h, n2 * sb, cudaMemcpyHostToDevice, st));
-    SCI_CK(cudaMalloc(&deri.p, n4 * sb));
+    // device copies of h and (pq|rs); integrals given on the device are read in place
+    TmpBuf dh, deri, dl;
+    const void *hsrc = h, *esrc = eri;
+    if (!on_device) {
+        SCI_CK(cudaMalloc(&dh.p, n2 * sb));
+        SCI_CK(cudaMemcpyAsync(dh.p, h, n2 * sb, cudaMemcpyHostToDevice, st));
+        hsrc = dh.p;
+    }
+    if (!(eri && on_device)) {
+        SCI_CK(cudaMalloc(&deri.p, n4 * sb));
+        esrc = deri.p;
+    }
     if (eri) {
-        SCI_CK(cudaMemcpyAsync(deri.p, eri, n4 * sb, cudaMemcpyHostToDevice, st));
+        if (!on_device) SCI_CK(cudaMemcpyAsync(deri.p, eri, n4 * sb, cudaMemcpyHostToDevice, st));
     } else {
-        TmpBuf dl;
-        SCI_CK(cudaMalloc(&dl.p, (size_t)naux * n2 * sb));
-        SCI_CK(cudaMemcpyAsync(dl.p, chol, (size_t)naux * n2 * sb, cudaMemcpyHostToDevice, st));
-        if (cplx) k_eri_from_chol<zdbl><<<grid_for(n4), 256, 0, st>>>(dl.as<zdbl>(), naux, n, deri.as<zdbl>());
-        else k_eri_from_chol<double><<<grid_for(n4), 256, 0, st>>>(dl.as<double>(), naux, n, deri.as<double>());
+        const void *lsrc = chol;
+        if (!on_device) {
+            SCI_CK(cudaMalloc(&dl.p, (size_t)naux * n2 * sb));
+            SCI_CK(cudaMemcpyAsync(dl.p, chol, (size_t)naux * n2 * sb, cudaMemcpyHostToDevice, st));
+            lsrc = dl.p;
+        }
+        if (cplx) k_eri_from_chol<zdbl><<<grid_for(n4), 256, 0, st>>>((const zdbl *)lsrc, naux, n, deri.as<zdbl>());
+        else k_eri_from_chol<double><<<grid_for(n4), 256, 0, st>>>((const double *)lsrc, naux, n, deri.as<double>());
         SCI_CK(cudaGetLastError());
         SCI_CK(cudaStreamSynchronize(st));
     }
@@ -888,10 +1041,10 @@ extern "C" int sci_set_integrals(sci_ctx *ctx, int scalar, int mode, int n, cons
     OrbMap om{n, ctx->spinors};
     int64_t n3 = (int64_t)norb * norb * norb;
     if (cplx)
-        k_small_tables<zdbl><<<grid_for(n3), 256, 0, st>>>(dh.as<zdbl>(), deri.as<zdbl>(), om, norb, (zdbl *)ctx->h_so,
+        k_small_tables<zdbl><<<grid_for(n3), 256, 0, st>>>((const zdbl *)hsrc, (const zdbl *)esrc, om, norb, (zdbl *)ctx->h_so,
                                                            (zdbl *)ctx->jd, (zdbl *)ctx->kd, (zdbl *)ctx->g_so);
     else
-        k_small_tables<double><<<grid_for(n3), 256, 0, st>>>(dh.as<double>(), deri.as<double>(), om, norb,
+        k_small_tables<double><<<grid_for(n3), 256, 0, st>>>((const double *)hsrc, (const double *)esrc, om, norb,
                                                              (double *)ctx->h_so, (double *)ctx->jd, (double *)ctx->kd,
                                                              (double *)ctx->g_so);
     SCI_CK(cudaGetLastError());
@@ -901,14 +1054,14 @@ extern "C" int sci_set_integrals(sci_ctx *ctx, int scalar, int mode, int n, cons
         SCI_CK(alloc_held(ctx, &ctx->tab, (size_t)ctx->tab_elems * sb));
         if (cplx) {
             if (ctx->tab_elems > 0)
-                k_tab_spinor<<<grid_for(ctx->tab_elems), 256, 0, st>>>(deri.as<zdbl>(), n, (zdbl *)ctx->tab);
+                k_tab_spinor<<<grid_for(ctx->tab_elems), 256, 0, st>>>((const zdbl *)esrc, n, (zdbl *)ctx->tab);
         } else {
             return sci_fail(ctx, SCI_ERR_ARG, "spinor mode takes complex integrals");
         }
     } else {
         ctx->tab_elems = n4 + NP * NP;
         SCI_CK(alloc_held(ctx, &ctx->tab, (size_t)ctx->tab_elems * sb));
-        k_tab_real<<<grid_for(ctx->tab_elems), 256, 0, st>>>(deri.as<double>(), n, (double *)ctx->tab);
+        k_tab_real<<<grid_for(ctx->tab_elems), 256, 0, st>>>((const double *)esrc, n, (double *)ctx->tab);
         SCI_CK(alloc_held(ctx, (void **)&ctx->tab32, (size_t)ctx->tab_elems * 4));
         k_to_f32<<<grid_for(ctx->tab_elems), 256, 0, st>>>((const double *)ctx->tab, ctx->tab32, ctx->tab_elems);
     }
@@ -930,6 +1083,7 @@ extern "C" int sci_set_integrals(sci_ctx *ctx, int scalar, int mode, int n, cons
     SCI_CK(cudaStreamSynchronize(st));
     return SCI_OK;
 }
+}  // namespace
 
 namespace {
 int set_dets(sci_ctx *ctx, const uint64_t *keys, int nwords, int64_t M, int n_alpha, int n_beta, int keys_on_device);

@@ -37,6 +37,7 @@ SIGNATURES = {
     "sci_destroy": (_i32, [_vp]),
     "sci_set_stream": (_i32, [_vp, _vp]),
     "sci_set_integrals": (_i32, [_vp, _i32, _i32, _i32, _vp, _vp, _i32, _vp]),
+    "sci_set_integrals_ex": (_i32, [_vp, _i32, _i32, _i32, _vp, _vp, _i32, _vp, _i32]),
     "sci_set_determinants": (_i32, [_vp, _vp, _i64, _i32, _i32, _i32]),
     "sci_set_determinants_w": (_i32, [_vp, _vp, _i32, _i64, _i32, _i32, _i32]),
     "sci_diagonal": (_i32, [_vp, _vp]),
@@ -143,6 +144,11 @@ def sci_set_stream(ctx, stream: int | None):
 
 def sci_set_integrals(ctx, scalar, mode, n, h, eri=None, naux=0, chol=None):
     return _check(ctx, load().sci_set_integrals(ctx, scalar, mode, n, _p(h), _p(eri), naux, _p(chol)))
+
+
+def sci_set_integrals_ex(ctx, scalar, mode, n, h, eri=None, naux=0, chol=None, on_device=0):
+    return _check(ctx, load().sci_set_integrals_ex(ctx, scalar, mode, n, _p(h), _p(eri), naux, _p(chol),
+                                                   int(on_device)))
 
 
 def sci_set_determinants(ctx, keys, M, n_alpha, n_beta, keys_on_device):
@@ -439,16 +445,34 @@ class Hamiltonian:
         sci_set_stream(self.ctx, stream.cuda_stream)
 
     def set_integrals(self, mode: str, h, eri=None, chol=None):
-        self.mode = mode
-        self.complex = bool(np.iscomplexobj(h))
-        dt = np.complex128 if self.complex else np.float64
+        """h, and eri or chol, as numpy arrays (host) or CUDA tensors of this device, which
+        are read in place (sci_set_integrals_ex with on_device = 1)."""
+        torch = self.torch
         n = h.shape[0]
-        h = np.ascontiguousarray(h, dtype=dt)
-        e = None if eri is None else np.ascontiguousarray(eri, dtype=dt)
-        L = None if chol is None else np.ascontiguousarray(chol, dtype=dt)
-        sci_set_integrals(self.ctx, SCI_COMPLEX128 if self.complex else SCI_REAL64,
-                          SCI_SPINORS if mode == "spinors" else SCI_SPIN_ORBITALS, n, h, e,
-                          0 if L is None else L.shape[0], L)
+        if isinstance(h, torch.Tensor) and h.is_cuda:
+            self.complex = bool(h.is_complex())
+            dt = torch.complex128 if self.complex else torch.float64
+            hh = h.detach().to(dt).contiguous()
+            e = None if eri is None else eri.detach().to(dt).contiguous()
+            L = None if chol is None else chol.detach().to(dt).contiguous()
+            for t in (e, L):
+                if t is not None and not (t.is_cuda and t.device == hh.device):
+                    raise ValueError("h, eri and chol must be on the same CUDA device")
+            # the copies above ran on torch's current stream; the library reads on its own
+            self.stream.wait_stream(torch.cuda.current_stream(self.device))
+            sci_set_integrals_ex(self.ctx, SCI_COMPLEX128 if self.complex else SCI_REAL64,
+                                 SCI_SPINORS if mode == "spinors" else SCI_SPIN_ORBITALS, n, hh, e,
+                                 0 if L is None else L.shape[0], L, 1)
+        else:
+            self.complex = bool(np.iscomplexobj(h))
+            dt = np.complex128 if self.complex else np.float64
+            hh = np.ascontiguousarray(h, dtype=dt)
+            e = None if eri is None else np.ascontiguousarray(eri, dtype=dt)
+            L = None if chol is None else np.ascontiguousarray(chol, dtype=dt)
+            sci_set_integrals(self.ctx, SCI_COMPLEX128 if self.complex else SCI_REAL64,
+                              SCI_SPINORS if mode == "spinors" else SCI_SPIN_ORBITALS, n, hh, e,
+                              0 if L is None else L.shape[0], L)
+        self.mode = mode
         self.n = n
 
     def set_determinants(self, keys, n_alpha: int, n_beta: int):
