@@ -124,10 +124,12 @@ __device__ __forceinline__ double h_single(const Pt2 &p, uint64_t J, int i, int 
     return sflip(ph, f);
 }
 
-// The slot of key I in a table of (key, NW value words) slots, claimed if I is new; NULL
-// after kMaxProbe probes (the table is too full: flag bit 2).
+// The slot of key I in a table of (key, NW value words) slots, claimed if I is new (nc
+// counts the thread's claims: the kernel adds them to the distinct count once per warp at
+// its end, and the host compares that count with the load limit, instead of one add to a
+// single counter per claim); NULL after kMaxProbe probes (the table is too full: flag bit 2).
 template <int NW>
-__device__ __forceinline__ uint64_t *claim(const Pt2 &p, uint64_t I)
+__device__ __forceinline__ uint64_t *claim(const Pt2 &p, uint64_t I, uint32_t &nc)
 {
     uint64_t s = mix64(I) & p.mask;
     for (int probe = 0; probe < kMaxProbe; probe++) {
@@ -136,7 +138,7 @@ __device__ __forceinline__ uint64_t *claim(const Pt2 &p, uint64_t I)
         if (k == kEmpty) {
             k = atomicCAS(reinterpret_cast<unsigned long long *>(slot), (unsigned long long)kEmpty, (unsigned long long)I);
             if (k == kEmpty) {
-                if (atomicAdd(p.count, 1ull) >= p.limit) atomicOr(p.flag, 1);
+                nc++;
                 k = I;
             }
         }
@@ -148,10 +150,11 @@ __device__ __forceinline__ uint64_t *claim(const Pt2 &p, uint64_t I)
 }
 
 template <int R>
-__device__ __forceinline__ void insert(const Pt2 &p, uint64_t I, double hij, const double *cJ, double cmax)
+__device__ __forceinline__ void insert(const Pt2 &p, uint64_t I, double hij, const double *cJ, double cmax,
+                                       uint32_t &nc)
 {
     if (p.eps > 0.0 && fabs(hij) * cmax < p.eps) return;
-    uint64_t *slot = claim<R>(p, I);
+    uint64_t *slot = claim<R>(p, I, nc);
     if (!slot) return;
 #pragma unroll
     for (int v = 0; v < R; v++) atomicAdd(reinterpret_cast<double *>(slot + 1 + v), hij * cJ[v]);
@@ -162,6 +165,14 @@ __device__ __forceinline__ uint32_t code_of(const uint32_t *g, uint32_t s)
     uint32_t c = 0;
     for (; s; s &= s - 1) c ^= g[__ffs((int)s) - 1];
     return c;
+}
+
+// the claims of a warp's threads, added to the distinct count once
+__device__ __forceinline__ void add_claims(const Pt2 &p, uint32_t nc, int lane)
+{
+    unsigned long long t = nc;
+    for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0 && t) atomicAdd(p.count, t);
 }
 
 // A warp's queue of found excitations (packed orbital quadruples), in shared memory, 64
@@ -216,6 +227,7 @@ k_pt2_gen(const uint64_t *__restrict__ Pkeys, int64_t M, const double *__restric
     const int n = p.n, na = p.na, nb = p.nb, ua = n - na, ub = n - nb;
     const uint32_t full = (uint32_t)((1ull << n) - 1);
     const int64_t warps_total = (int64_t)gridDim.x * kWarps;
+    uint32_t nclaim = 0;
     for (int64_t J = (int64_t)blockIdx.x * kWarps + w; J < M; J += warps_total) {
         const uint64_t key = Pkeys[J];
         const uint32_t oa = (uint32_t)(key & full), ob = (uint32_t)(key >> n);
@@ -240,14 +252,14 @@ k_pt2_gen(const uint64_t *__restrict__ Pkeys, int64_t M, const double *__restric
             for (int t = lane; t < c0 + c2; t += 32) {
                 if (t < c0) {
                     const int i = orb[t / ua], a = orb[32 + t % ua];
-                    insert<R>(p, (key & ~(1ull << i)) | (1ull << a), h_single(p, key, i, a), cJ, cmax);
+                    insert<R>(p, (key & ~(1ull << i)) | (1ull << a), h_single(p, key, i, a), cJ, cmax, nclaim);
                 } else {
                     const int s = t - c0;
                     const uint16_t po = s_pair[s / qa], pv = s_pair[s % qa];
                     const int i = orb[po & 0xFF], j = orb[po >> 8], a = orb[32 + (pv & 0xFF)], b = orb[32 + (pv >> 8)];
                     if (p.bss && p.bss[j * (j - 1) / 2 + i] * cmax < p.eps) continue;   // the class's bound
                     const uint64_t I = (key & ~(1ull << i) & ~(1ull << j)) | (1ull << a) | (1ull << b);
-                    insert<R>(p, I, h_double(p, key, i, j, a, b), cJ, cmax);
+                    insert<R>(p, I, h_double(p, key, i, j, a, b), cJ, cmax, nclaim);
                 }
             }
         }
@@ -273,12 +285,12 @@ k_pt2_gen(const uint64_t *__restrict__ Pkeys, int64_t M, const double *__restric
             const int jb = n + (e & 0xFF), vb_ = n + (e >> 8);
             const int s = t % (1 + c0);
             if (s == 0) {
-                insert<R>(p, (key & ~(1ull << jb)) | (1ull << vb_), h_single(p, key, jb, vb_), cJ, cmax);
+                insert<R>(p, (key & ~(1ull << jb)) | (1ull << vb_), h_single(p, key, jb, vb_), cJ, cmax, nclaim);
             } else {
                 const int i = orb[(s - 1) / ua], a = orb[32 + (s - 1) % ua];
                 if (p.bab && p.bab[(e & 0xFF) * n + i] * cmax < p.eps) continue;   // the class's bound
                 const uint64_t I = (key & ~(1ull << i) & ~(1ull << jb)) | (1ull << a) | (1ull << vb_);
-                insert<R>(p, I, h_double(p, key, i, jb, a, vb_), cJ, cmax);
+                insert<R>(p, I, h_double(p, key, i, jb, a, vb_), cJ, cmax, nclaim);
             }
         }
 
@@ -295,11 +307,12 @@ k_pt2_gen(const uint64_t *__restrict__ Pkeys, int64_t M, const double *__restric
                 const int b2 = s_obc[q];
                 if (b2 <= b1 || ((ob >> b2) & 1)) continue;
                 const uint64_t I = (key & ~(1ull << (n + j1)) & ~(1ull << (n + j2))) | (1ull << (n + b1)) | (1ull << (n + b2));
-                insert<R>(p, I, h_double(p, key, n + j1, n + j2, n + b1, n + b2), cJ, cmax);
+                insert<R>(p, I, h_double(p, key, n + j1, n + j2, n + b1, n + b2), cJ, cmax, nclaim);
             }
         }
         __syncwarp();
     }
+    add_claims(p, nclaim, lane);
 }
 
 
@@ -347,10 +360,11 @@ __device__ __forceinline__ zdbl hz_single(const Pt2 &p, uint64_t J, int i, int a
 }
 
 template <int R>
-__device__ __forceinline__ void insert_z(const Pt2 &p, uint64_t I, zdbl h, const zdbl *cJ, double cmax)
+__device__ __forceinline__ void insert_z(const Pt2 &p, uint64_t I, zdbl h, const zdbl *cJ, double cmax,
+                                         uint32_t &nc)
 {
     if (p.eps > 0.0 && sqrt(h.x * h.x + h.y * h.y) * cmax < p.eps) return;
-    uint64_t *slot = claim<2 * R>(p, I);
+    uint64_t *slot = claim<2 * R>(p, I, nc);
     if (!slot) return;
     double *val = reinterpret_cast<double *>(slot + 1);
 #pragma unroll
@@ -395,6 +409,7 @@ k_pt2_gen_z(const uint64_t *__restrict__ Pkeys, int64_t M, const zdbl *__restric
     const uint64_t full = n == 64 ? ~0ull : ((1ull << n) - 1);
     const int npairs = N * (N - 1) / 2;
     const int64_t warps_total = (int64_t)gridDim.x * kWarps;
+    uint32_t nclaim = 0;
     for (int64_t J = (int64_t)blockIdx.x * kWarps + w; J < M; J += warps_total) {
         const uint64_t key = Pkeys[J];
         const uint64_t vir = full & ~key;
@@ -420,7 +435,7 @@ k_pt2_gen_z(const uint64_t *__restrict__ Pkeys, int64_t M, const zdbl *__restric
             for (int q = s_cstart[c]; q < s_cstart[c + 1]; q++) {
                 const int a = s_obc[q];
                 if ((key >> a) & 1) continue;
-                insert_z<R>(p, (key & ~(1ull << i)) | (1ull << a), hz_single(p, key, i, a), cJ, cmax);
+                insert_z<R>(p, (key & ~(1ull << i)) | (1ull << a), hz_single(p, key, i, a), cJ, cmax, nclaim);
             }
         }
         // doubles i < j -> a < b: for each occupied pair and first virtual a, the second
@@ -428,7 +443,7 @@ k_pt2_gen_z(const uint64_t *__restrict__ Pkeys, int64_t M, const zdbl *__restric
         auto ins = [&](uint32_t e) {
             const int i = e & 0xFF, j = (e >> 8) & 0xFF, a = (e >> 16) & 0xFF, b = e >> 24;
             const uint64_t I = (key & ~(1ull << i) & ~(1ull << j)) | (1ull << a) | (1ull << b);
-            insert_z<R>(p, I, hz_double(p, key, i, j, a, b), cJ, cmax);
+            insert_z<R>(p, I, hz_double(p, key, i, j, a, b), cJ, cmax, nclaim);
         };
         int cnt = 0;
         for (int base = 0; base < npairs * nv; base += 32) {
@@ -455,6 +470,7 @@ k_pt2_gen_z(const uint64_t *__restrict__ Pkeys, int64_t M, const zdbl *__restric
         }
         wq_flush(s_q[w], cnt, lane, ins);
     }
+    add_claims(p, nclaim, lane);
 }
 
 // sum over the table entries of num^2 / (E0 - H_II).  Each warp packs the occupied slots
@@ -822,7 +838,8 @@ int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t
         cudaEventElapsedTime(&e, ev[2], ev[3]);
         t_clear += a, t_gen += g, t_eval += e;
         cnt_out = (int64_t)hc[0];
-        flag_out = (int)(hc[1] & 0xFFFFFFFFull);
+        // bit 1: the distinct count reached the load limit; bit 2: a probe limit was hit
+        flag_out = (int)(hc[1] & 0xFFFFFFFFull) | (hc[0] >= p.limit ? 1 : 0);
         return SCI_OK;
     };
     // sampling: one batch of a four-times finer split estimates the distinct determinants
