@@ -142,8 +142,8 @@ int sci_set_determinants(sci_ctx *ctx, const uint64_t *keys, int64_t M, int n_al
  * integers, Sec. 3.2), strictly ascending as unsigned (64 x nwords)-bit integers.  With
  * two words the bucket keys are 128-bit (sorted by two stable radix passes), and sigma
  * (every precision mode, deterministic mode included), the diagonal, pair counts, row
- * costs and the connection exports work as for one word; row ranges, density matrices,
- * ENPT2 and batches need one-word keys (SCI_ERR_ARG).  sci_set_integrals takes up to 64
+ * costs, the connection exports and the density matrices (sci_rdm12, sci_rdm_grads) work
+ * as for one word; row ranges, ENPT2 and batches need one-word keys (SCI_ERR_ARG).  sci_set_integrals takes up to 64
  * spatial orbitals or 128 spinors for these lists; sci_set_determinants (one word) returns
  * SCI_ERR_ARG when the orbitals do not fit one word.  Errors as sci_set_determinants. */
 int sci_set_determinants_w(sci_ctx *ctx, const uint64_t *keys, int nwords, int64_t M, int n_alpha,
@@ -269,7 +269,8 @@ int sci_kernel_times(sci_ctx *ctx, float *ms, int n);
  *   rdm1[p][q]       = sum_k w_k <c_k| a+_p a_q |c_k>
  *   rdm2[p][q][r][s] = sum_k w_k <c_k| a+_p a+_r a_s a_q |c_k>
  * over the norb = 2n spin-orbitals (spin-orbital mode, bit order of the keys) or the n
- * spinors, unnormalised: for a normalised c the energy of Eq. Hamiltonian is
+ * spinors, norb <= 128 (one- or two-word keys), unnormalised: for a normalised c the
+ * energy of Eq. Hamiltonian is
  * sum h_pq rdm1_pq + 1/2 sum (pq|rs) rdm2_pqrs (spin-orbital integrals).
  *   C: device, [M][nvec], double (real mode) or complex128 (complex mode), nvec >= 1.
  *   weights: HOST, nvec doubles, or NULL for all ones.

@@ -82,32 +82,58 @@ __device__ __forceinline__ void grad_offsets(sci::TabRule tr, int x, int y, uint
 }
 
 // ------------------------------------------------------------------ diagonal
-template <typename TC>
-__global__ void __launch_bounds__(kThreads)
-k_rdm_diag(const uint64_t *__restrict__ keys, int64_t M, int norb, uint64_t ref, const TC *__restrict__ C, int nvec, int v0,
-           int nv, const double *__restrict__ wk, double *__restrict__ Wt, double *__restrict__ D, double *__restrict__ DD)
+// occupation strings of KW 64-bit words: word w holds orbitals 64 w .. 64 w + 63
+template <int KW> struct Str {
+    uint64_t w[KW];
+};
+template <int KW> __device__ __forceinline__ Str<KW> load_str(const uint64_t *keys, int64_t I)
 {
-    __shared__ double sDD[64 * 64];
-    __shared__ double sD[64];
-    __shared__ double sW[kThreads / 32];
+    Str<KW> s;
+#pragma unroll
+    for (int k = 0; k < KW; k++) s.w[k] = keys[I * KW + k];
+    return s;
+}
+template <int KW> __device__ __forceinline__ bool occ(const Str<KW> &s, int p)
+{
+    return (s.w[p >> 6] >> (p & 63)) & 1;
+}
+
+// Diagonal class: O[p][r] = sum_I w_I n_p n_r in the reference decomposition n = n_ref + d
+// (d = key ^ ref has a few bits), accumulated per CTA in shared memory ([norb]^2 doubles,
+// dynamic: up to 128 KB for 128 spin-orbitals).
+template <typename TC, int KW>
+__global__ void __launch_bounds__(kThreads)
+k_rdm_diag(const uint64_t *__restrict__ keys, int64_t M, int norb, uint64_t ref, uint64_t ref_hi,
+           const TC *__restrict__ C, int nvec, int v0, int nv, const double *__restrict__ wk, double *__restrict__ Wt,
+           double *__restrict__ D, double *__restrict__ DD)
+{
+    extern __shared__ double s_dyn[];
+    double *sDD = s_dyn, *sD = s_dyn + norb * norb, *sW = sD + norb;
     for (int i = threadIdx.x; i < norb * norb; i += blockDim.x) sDD[i] = 0.0;
     for (int i = threadIdx.x; i < norb; i += blockDim.x) sD[i] = 0.0;
     __syncthreads();
+    Str<KW> rs;
+    rs.w[0] = ref;
+    if (KW > 1) rs.w[KW - 1] = ref_hi;
     double wsum = 0.0;
     for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < M; I += (int64_t)gridDim.x * blockDim.x) {
         double w = 0.0;
         for (int v = 0; v < nv; v++) w = fma(wk[v0 + v], sqnorm(C[I * nvec + v0 + v]), w);
         wsum += w;
-        const uint64_t key = keys[I], d = key ^ ref;
-        for (uint64_t m = d; m; m &= m - 1) {
-            const int p = __ffsll((long long)m) - 1;
-            const double wp = (key >> p) & 1 ? w : -w;
-            atomicAdd(&sD[p], wp);
-            for (uint64_t m2 = d; m2; m2 &= m2 - 1) {
-                const int r = __ffsll((long long)m2) - 1;
-                atomicAdd(&sDD[p * norb + r], (key >> r) & 1 ? wp : -wp);
+        const Str<KW> key = load_str<KW>(keys, I);
+#pragma unroll
+        for (int k1 = 0; k1 < KW; k1++)
+            for (uint64_t m = key.w[k1] ^ rs.w[k1]; m; m &= m - 1) {
+                const int p = 64 * k1 + __ffsll((long long)m) - 1;
+                const double wp = occ(key, p) ? w : -w;
+                atomicAdd(&sD[p], wp);
+#pragma unroll
+                for (int k2 = 0; k2 < KW; k2++)
+                    for (uint64_t m2 = key.w[k2] ^ rs.w[k2]; m2; m2 &= m2 - 1) {
+                        const int r = 64 * k2 + __ffsll((long long)m2) - 1;
+                        atomicAdd(&sDD[p * norb + r], occ(key, r) ? wp : -wp);
+                    }
             }
-        }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, off);
@@ -125,10 +151,10 @@ k_rdm_diag(const uint64_t *__restrict__ keys, int64_t M, int norb, uint64_t ref,
 }
 
 // ------------------------------------------------------------------ singles
-template <typename TC, int NV>
+template <typename TC, int NV, int KW>
 __global__ void __launch_bounds__(kThreads)
 k_rdm_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S, const uint32_t *__restrict__ e_meta,
-              int64_t E, int norb, uint64_t ref, const TC *__restrict__ C, int nvec, int v0,
+              int64_t E, int norb, uint64_t ref, uint64_t ref_hi, const TC *__restrict__ C, int nvec, int v0,
               const double *__restrict__ wk, TC *__restrict__ A, TC *__restrict__ Bc)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
@@ -137,8 +163,14 @@ k_rdm_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e
         const bool par = (meta >> 7) & 1;
         const int64_t bs = p - (int64_t)((meta >> 8) & 0xFFF);
         const int64_t be = bs + (int64_t)(meta >> 20);
-        const uint64_t Sk = e_S[p];
-        const uint64_t part = Sk & ~ref, holes = ref & ~Sk;
+        // the spectator string's orbitals outside (part) and missing from (holes) the
+        // reference, per word
+        uint64_t part[KW], holes[KW];
+#pragma unroll
+        for (int k = 0; k < KW; k++) {
+            const uint64_t Sk = e_S[p * KW + k], rk = k == 0 ? ref : ref_hi;
+            part[k] = Sk & ~rk, holes[k] = rk & ~Sk;
+        }
         const int64_t idx = e_idx[p];
         TC rowc[NV];
 #pragma unroll
@@ -155,9 +187,12 @@ k_rdm_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e
             for (int v = 0; v < NV; v++) mac(w, rowc[v], sflip(parq, C[idxq * nvec + v0 + v]));
             const int64_t xy = (int64_t)x * norb + y;
             red(A + xy, w);
-            for (uint64_t m = part; m; m &= m - 1) red(Bc + xy * norb + (__ffsll((long long)m) - 1), w);
             const TC nw = neg(w);
-            for (uint64_t m = holes; m; m &= m - 1) red(Bc + xy * norb + (__ffsll((long long)m) - 1), nw);
+#pragma unroll
+            for (int k = 0; k < KW; k++) {
+                for (uint64_t m = part[k]; m; m &= m - 1) red(Bc + xy * norb + 64 * k + (__ffsll((long long)m) - 1), w);
+                for (uint64_t m = holes[k]; m; m &= m - 1) red(Bc + xy * norb + 64 * k + (__ffsll((long long)m) - 1), nw);
+            }
         }
     }
 }
@@ -221,15 +256,21 @@ k_rdm_doubles(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e
 // ------------------------------------------------------------------ expansion
 // g1 and the g2 elements of the diagonal and single-excitation classes; one thread per
 // (x, y)
+// occupation of orbital k in the reference (ref: orbitals 0..63, ref_hi: 64..127)
+__device__ __forceinline__ double ref_occ(uint64_t ref, uint64_t ref_hi, int k)
+{
+    return (double)(k < 64 ? (ref >> k) & 1 : (ref_hi >> (k - 64)) & 1);
+}
+
 template <typename TC>
-__global__ void k_rdm_expand1(int norb, uint64_t ref, const double *__restrict__ Wt, const double *__restrict__ D,
-                              const double *__restrict__ DD, const TC *__restrict__ A, const TC *__restrict__ Bc,
-                              TC *__restrict__ g1, TC *__restrict__ g2)
+__global__ void k_rdm_expand1(int norb, uint64_t ref, uint64_t ref_hi, const double *__restrict__ Wt,
+                              const double *__restrict__ D, const double *__restrict__ DD, const TC *__restrict__ A,
+                              const TC *__restrict__ Bc, TC *__restrict__ g1, TC *__restrict__ g2)
 {
     const int64_t n2 = (int64_t)norb * norb, n3 = n2 * norb;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n2; t += (int64_t)gridDim.x * blockDim.x) {
         const int x = (int)(t / norb), y = (int)(t % norb);
-        const double nx = (double)((ref >> x) & 1), ny = (double)((ref >> y) & 1);
+        const double nx = ref_occ(ref, ref_hi, x), ny = ref_occ(ref, ref_hi, y);
         const double O = *Wt * nx * ny + nx * D[y] + D[x] * ny + DD[t];
         const TC o = from_real<TC>(O);
         if (x == y) {
@@ -243,7 +284,7 @@ __global__ void k_rdm_expand1(int norb, uint64_t ref, const double *__restrict__
         g2[(int64_t)x * n3 + (int64_t)y * n2 + (int64_t)y * norb + x] = neg(o);    // (x y | y x)
         for (int k = 0; k < norb; k++) {
             if (k == x || k == y) continue;
-            const TC b = add(scale(a, (double)((ref >> k) & 1)), Bc[t * norb + k]);
+            const TC b = add(scale(a, ref_occ(ref, ref_hi, k)), Bc[t * norb + k]);
             const TC nb = neg(b);
             g2[(int64_t)x * n3 + (int64_t)y * n2 + (int64_t)k * norb + k] = b;     // (x y | k k)
             g2[(int64_t)k * n3 + (int64_t)k * n2 + (int64_t)x * norb + y] = b;     // (k k | x y)
@@ -320,9 +361,11 @@ template <typename TC> struct Walk {
 template <typename TC, int NV>
 int launch_walks(sci_ctx *ctx, const Walk<TC> &w)
 {
-    if (ctx->e1 > 0)
-        k_rdm_singles<TC, NV><<<grid_for(ctx->e1), kThreads, 0, ctx->stream>>>(
-            ctx->e1_idx, ctx->e1_S, ctx->e1_meta, ctx->e1, ctx->norb, ctx->ref, w.C, w.nvec, w.v0, w.wk, w.A, w.Bc);
+    if (ctx->e1 > 0) {
+        auto ks = ctx->nwords == 2 ? k_rdm_singles<TC, NV, 2> : k_rdm_singles<TC, NV, 1>;
+        ks<<<grid_for(ctx->e1), kThreads, 0, ctx->stream>>>(ctx->e1_idx, ctx->e1_S, ctx->e1_meta, ctx->e1, ctx->norb,
+                                                            ctx->ref, ctx->ref_hi, w.C, w.nvec, w.v0, w.wk, w.A, w.Bc);
+    }
     if (w.dT) {
         auto kern = k_rdm_doubles<TC, NV>;
         if (w.smem > 48 * 1024 &&
@@ -372,10 +415,19 @@ int rdm_run(sci_ctx *ctx, const TC *C, int nvec, const double *wk_dev, TC *g1, T
     while (kv > 1 && stage_bytes(kv) > 200 * 1024) kv >>= 1;
     if (g2 && ctx->e2 > 0 && stage_bytes(kv) > 200 * 1024)
         return sci_fail(ctx, SCI_ERR_OVERFLOW, "rdm12: largest bucket too large for shared memory");
+    // the diagonal kernel's shared memory: DD [norb]^2, D [norb] and the warp sums
+    const size_t diag_smem = sizeof(double) * ((size_t)norb * norb + norb + kThreads / 32);
+    {
+        auto kd = ctx->nwords == 2 ? k_rdm_diag<TC, 2> : k_rdm_diag<TC, 1>;
+        if (sci_cuda_check(ctx, cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diag_smem),
+                           "rdm12 diag attr"))
+            return SCI_ERR_CUDA;
+    }
     for (int v0 = 0; v0 < nvec; v0 += kv) {
         const int nv = std::min(kv, nvec - v0);
-        k_rdm_diag<TC><<<grid_for(ctx->M), kThreads, 0, ctx->stream>>>(ctx->keys, ctx->M, norb, ctx->ref, C, nvec, v0, nv,
-                                                                       wk_dev, Wt, D, DD);
+        auto kd = ctx->nwords == 2 ? k_rdm_diag<TC, 2> : k_rdm_diag<TC, 1>;
+        kd<<<grid_for(ctx->M), kThreads, diag_smem, ctx->stream>>>(ctx->keys, ctx->M, norb, ctx->ref, ctx->ref_hi, C,
+                                                                   nvec, v0, nv, wk_dev, Wt, D, DD);
         const Walk<TC> wlk{C, nvec, v0, wk_dev, A, Bc, g2 && ctx->e2 > 0 ? dT : nullptr, CH, stage_bytes(nv), tr, bb_off};
         int rc = SCI_OK;
         switch (nv) {
@@ -390,7 +442,7 @@ int rdm_run(sci_ctx *ctx, const TC *C, int nvec, const double *wk_dev, TC *g1, T
         }
         if (rc) return rc;
     }
-    k_rdm_expand1<TC><<<grid_for(n2), kThreads, 0, ctx->stream>>>(norb, ctx->ref, Wt, D, DD, A, Bc, g1, g2);
+    k_rdm_expand1<TC><<<grid_for(n2), kThreads, 0, ctx->stream>>>(norb, ctx->ref, ctx->ref_hi, Wt, D, DD, A, Bc, g1, g2);
     if (g2) k_rdm_expand2<TC><<<grid_for(nT), kThreads, 0, ctx->stream>>>(tr, norb, nT, dT, g2);
     return sci_cuda_check(ctx, cudaGetLastError(), "rdm12 launch") ? SCI_ERR_CUDA : SCI_OK;
 }
@@ -505,7 +557,7 @@ extern "C" int sci_rdm12(sci_ctx *ctx, const void *C, int nvec, const double *we
     if (!ctx) return SCI_ERR_ARG;
     if (!ctx->have_ints || !ctx->have_dets) return sci_fail(ctx, SCI_ERR_STATE, "rdm12: integrals and determinants first");
     if (nvec < 1 || !rdm1 || (ctx->M > 0 && !C)) return sci_fail(ctx, SCI_ERR_ARG, "rdm12: need nvec >= 1, C and rdm1");
-    if (ctx->norb > 64 || ctx->nwords != 1) return sci_fail(ctx, SCI_ERR_ARG, "rdm12: one-word keys, at most 64 orbitals");
+    if (ctx->norb > 128 || ctx->nwords > 2) return sci_fail(ctx, SCI_ERR_ARG, "rdm12: at most 128 orbitals (two words)");
     if (sci_cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) return SCI_ERR_CUDA;
     // weights to the device (a host array of nvec doubles, NULL = all ones)
     const size_t wbytes = sizeof(double) * nvec;

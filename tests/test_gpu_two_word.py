@@ -4,7 +4,7 @@ against the oracle, which holds every string as a 128-bit integer.
 The selected 40-orbital space (80 spin-orbitals: beta strings cross the word boundary):
 connections, degrees and phases bit-exact, per-row pair counts exact, the diagonal to 1e-12,
 FP64 and paired-FP32 sigma to 1e-11, FP32-storage sigma within its per-row bound, the
-deterministic mode bit for bit.  The opposite-spin two-electron closed form on 40 orbitals
+deterministic mode bit for bit; the density matrices and their spin sums against the oracle.  The opposite-spin two-electron closed form on 40 orbitals
 and a 72-spinor space are checked as dense matrices.
 """
 import numpy as np
@@ -133,8 +133,6 @@ def test_two_word_limits(gpu, sel2w):
     H = sci.Hamiltonian.from_workload(w)
     C = torch.from_numpy(np.ascontiguousarray(w.c[:, :1])).cuda()
     with pytest.raises(sci.SciError):            # one-word keys only
-        H.rdm12(C)
-    with pytest.raises(sci.SciError):
         H.enpt2(C, [0.0])
     with pytest.raises(sci.SciError):
         H.set_row_range(0, 100)
@@ -171,4 +169,36 @@ def test_two_word_full_size_sampled(gpu):
         assert np.array_equal(deg, np.concatenate([x[1] for x in conn]))
         assert np.array_equal(ph, np.concatenate([x[2] for x in conn]))
     assert int(H.row_costs().sum()) == H.count_pairs()
+    H.sync_status()
+
+
+def test_two_word_rdm12_and_grads(gpu):
+    """Density matrices on 40 orbitals (80 spin-orbitals, 2 + 2 electrons, 10,000 selected
+    determinants), two weighted vectors, against the oracle's per-vector matrices; the spin
+    sums and the Cholesky contraction of sci_rdm_grads against numpy on them."""
+    torch = gpu
+    w = W.selected_two_word(n=40, na=2, nb=2, M=10000, nvec=2)
+    o = Oracle.from_workload(w)
+    H = sci.Hamiltonian.from_workload(w)
+    C = torch.from_numpy(np.ascontiguousarray(w.c)).cuda()
+    wt = np.array([1.0, -0.5])
+    g1, g2 = H.rdm12(C, weights=wt)
+    r1 = np.zeros((80, 80))
+    r2 = np.zeros((80,) * 4)
+    for k in range(2):
+        a1, a2 = o.rdm12(w.c[:, k])
+        r1 += wt[k] * a1
+        r2 += wt[k] * a2
+    g1, g2 = g1.cpu().numpy(), g2.cpu().numpy()
+    assert np.abs(g1 - r1).max() < 1e-12 * np.abs(r1).max()
+    assert np.abs(g2 - r2).max() < 1e-12 * np.abs(r2).max()
+    n = 40
+    gamma, Gamma, gL = H.rdm_grads(C, weights=wt, chol=torch.from_numpy(w.ints.chol.copy()).cuda(), Gamma=True)
+    gr = r1[:n, :n] + r1[n:, n:]
+    Gr = (r2[:n, :n, :n, :n] + r2[:n, :n, n:, n:] + r2[n:, n:, :n, :n] + r2[n:, n:, n:, n:])
+    assert np.abs(gamma.cpu().numpy() - gr).max() < 1e-12 * np.abs(gr).max()
+    assert np.abs(Gamma.cpu().numpy() - Gr).max() < 1e-12 * np.abs(Gr).max()
+    L = w.ints.chol
+    ref = (Gr.reshape(n * n, n * n) @ L.reshape(L.shape[0], n * n).T).T.reshape(L.shape[0], n, n)
+    assert np.abs(gL.cpu().numpy() - ref).max() < 1e-12 * np.abs(ref).max()
     H.sync_status()

@@ -119,3 +119,57 @@ def test_two_word_encoding_of_a_one_word_space():
     h, eri = w.ints.h, w.ints.eri()
     assert np.array_equal(Oracle("spin_orbitals", 6, h, eri, w.keys).dense(),
                           Oracle("spin_orbitals", 6, h, eri, k2).dense())
+
+
+def _small_two_word_space(n, na, nb, keep, seed):
+    """HF plus a random fraction `keep` of the other determinants of na + nb electrons over
+    n orbitals (two-word keys when n > 32)."""
+    rng = np.random.default_rng(seed)
+    al = list(itertools.combinations(range(n), na))
+    be = list(itertools.combinations(range(n), nb))
+    sets = [(a, b) for a in al for b in be if (a == tuple(range(na)) and b == tuple(range(nb))) or rng.random() < keep]
+    return sets
+
+
+def test_rdm12_two_words_energy_traces_and_symmetries():
+    """The oracle's density matrices on 40 orbitals (2 alpha + 1 beta electrons, beta bits
+    40..79 across the word boundary): sum h g1 + 1/2 sum (pq|rs) g2 = c^+ H c with the
+    oracle's sigma (pinned above by the closed forms), traces N and N(N - 1), Hermiticity and
+    electron exchange."""
+    from oracle import fock_route as F
+
+    n, na, nb = 40, 2, 1
+    ints = _ints(n, 37)
+    keys = _keys_from_sets(_small_two_word_space(n, na, nb, 0.04, 5), n)
+    o = Oracle("spin_orbitals", n, ints.h, ints.eri(), keys)
+    c = np.random.default_rng(6).standard_normal(len(keys))
+    c /= np.linalg.norm(c)
+    g1, g2 = o.rdm12(c)
+    hs, es = F.spin_orbital_integrals(ints.h, ints.eri())
+    E = np.einsum("pq,pq->", hs, g1) + 0.5 * np.einsum("pqrs,pqrs->", es, g2)
+    assert abs(E - np.vdot(c, o.sigma(c)[:, 0])) < 1e-11 * max(1.0, abs(E))
+    N = na + nb
+    assert abs(np.trace(g1) - N) < 1e-12 and abs(np.einsum("pprr->", g2) - N * (N - 1)) < 1e-11
+    assert np.abs(g1 - g1.T).max() < 1e-14
+    assert np.abs(g2 - g2.transpose(2, 3, 0, 1)).max() < 1e-14
+    assert np.abs(g2 - g2.transpose(1, 0, 3, 2)).max() < 1e-14
+    assert len(keys) > 1000
+
+
+def test_rdm12_two_word_encoding_of_a_one_word_space():
+    """A space of 24 spin-orbitals given as two words (high word 0) has the density matrices
+    of its one-word encoding (bit for bit on one thread), which the literal operator route
+    pins."""
+    w = W.random_small(107, "spin_orbitals", 12, 3, 2, naux=4, frac=0.3)
+    c = w.c[:, 0]
+    o1 = Oracle.from_workload(w)
+    o2 = Oracle(w.mode, w.n, w.ints.h, w.ints.eri(), np.stack([w.keys, np.zeros_like(w.keys)], axis=1))
+    import oracle
+
+    oracle.set_threads(1)          # one thread: the same summation order, so equal bits
+    try:
+        a1, a2 = o1.rdm12(c)
+        b1, b2 = o2.rdm12(c)
+    finally:
+        oracle.set_threads(0)
+    assert np.array_equal(a1, b1) and np.array_equal(a2, b2)
