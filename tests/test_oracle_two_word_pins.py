@@ -173,3 +173,41 @@ def test_rdm12_two_word_encoding_of_a_one_word_space():
     finally:
         oracle.set_threads(0)
     assert np.array_equal(a1, b1) and np.array_equal(a2, b2)
+
+
+def test_enpt2_two_words_against_the_definition_on_the_full_space():
+    """ENPT2 of a P inside the full 1 + 1-electron space of 40 orbitals (1,600 determinants,
+    beta bits 40..79 across the word boundary): sciref_enpt2 (generation of the excitations
+    of P, deduplication by key) against Eq. ENPT2E written out on the dense H of the whole
+    space (the oracle's sigma, pinned above by the closed form), two roots with arbitrary
+    E0; the external count against the size of Q."""
+    n = 40
+    ints = _ints(n, 53)
+    full = _keys_from_sets([((p,), (q,)) for p in range(n) for q in range(n)], n)
+    of = Oracle("spin_orbitals", n, ints.h, ints.eri(), full)
+    Hf = of.dense()
+    rng = np.random.default_rng(8)
+    inP = rng.random(len(full)) < 0.3
+    inP[0] = True
+    P = full[inP]
+    C = rng.standard_normal((len(P), 2))
+    E0 = np.array([-30.0, -25.0])
+    v = Hf[:, inP] @ C                       # sum_J H_IJ c_J for every I of the space
+    d = np.diag(Hf)
+    Q = ~inP
+    ref = ((v[Q] ** 2) / (E0[None, :] - d[Q, None])).sum(axis=0)
+    op = Oracle("spin_orbitals", n, ints.h, ints.eri(), P)
+    E2, nx = op.enpt2(C, E0)
+    assert np.allclose(E2, ref, rtol=1e-12, atol=0)
+    assert nx == int(Q.sum())              # every determinant of Q is one excitation of P
+
+
+def test_enpt2_two_word_encoding_of_a_one_word_space():
+    """A space of 24 spin-orbitals given as two words gives the one-word ENPT2."""
+    w = W.random_small(109, "spin_orbitals", 12, 3, 2, naux=4, frac=0.2, nvec=2)
+    o1 = Oracle.from_workload(w)
+    o2 = Oracle(w.mode, w.n, w.ints.h, w.ints.eri(), np.stack([w.keys, np.zeros_like(w.keys)], axis=1))
+    E0 = np.array([-20.0, -18.0])
+    a, na_ = o1.enpt2(w.c, E0)
+    b, nb_ = o2.enpt2(w.c, E0)
+    assert na_ == nb_ and np.allclose(a, b, rtol=1e-13, atol=0)
