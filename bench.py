@@ -414,7 +414,7 @@ def blockvec_bench(M=2_000_000, k=96, a=8, reps=5):
     return res
 
 
-def pt2_bench(sizes=(60_000, 200_000, 1_000_000, 2_000_000), table_gb=96.0):
+def pt2_bench(sizes=(60_000, 200_000, 1_000_000, 2_000_000), table_gb=16.0):
     """Epstein-Nesbet PT2 of the ground state on spaces of the bench recipe: (E0, c) from
     the FP64 block Davidson (residual 1e-6), then exact sci_enpt2 (no screening).  Wall
     seconds of sci_enpt2 (synchronous), batches, distinct determinants of W summed, the
@@ -458,7 +458,7 @@ def pt2_bench(sizes=(60_000, 200_000, 1_000_000, 2_000_000), table_gb=96.0):
     return out
 
 
-def pt2_spinor_bench(M=200_000, table_gb=96.0):
+def pt2_spinor_bench(M=200_000, table_gb=16.0):
     """Epstein-Nesbet PT2 in complex spinor mode (the 4C workloads of the paper's Sec. 4) on
     a space of the 64-spinor recipe: c is the recipe's complex vector (|c| = exp(-level),
     random phases), normalised, and E0 its Rayleigh quotient c^+ H c; exact sci_enpt2 (no
@@ -891,7 +891,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-davidson", action="store_true",
                     help="skip the 8-root Davidson timing and the density-matrix timing")
-    ap.add_argument("--pt2-table-gb", type=float, default=96.0, help="hash-table memory of the pt2 section")
+    ap.add_argument("--pt2-table-gb", type=float, default=16.0,
+                    help="hash-table memory of the pt2 section (16 GB: larger tables make the random inserts slower)")
     ap.add_argument("--no-spinor", action="store_true", help="skip the 64-spinor complex workload section")
     ap.add_argument("--only", default=None, choices=["blockvec", "rdm", "batch", "davidson", "pt2", "spinor",
                                                      "rowsplit", "pt2_spinor", "deterministic", "two_word"],

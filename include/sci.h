@@ -325,7 +325,10 @@ int sci_rdm_grads(sci_ctx *ctx, const double *C, int nvec, const double *weights
  *      budget, at least 256).  W is split into
  *      2^t batches (t <= 10) so that a batch's generated excitations fill at most 60% of
  *      it; a batch that still overflows (or probes too far) restarts the sum with twice
- *      the batches.
+ *      the batches.  Larger is not always faster: the inserts are random accesses, and a
+ *      table of tens of GB makes them slower than the extra passes of a smaller one
+ *      (measured on a 200k-determinant 64-spinor space: 1.9 s with 2-24 GB, 3.2 s with
+ *      96 GB; a 2M-determinant real space: 7.9-8.0 s with 16-96 GB, 8.7 s with 4 GB).
  *   E2: HOST, 3 x nroots doubles, overwritten: E2[W], then E2[P], then E2[Q].
  *   stats: HOST, 8 int64 or NULL: batches, distinct W determinants summed, passes run
  *      (with restarts), table capacity, microseconds spent clearing the table,
