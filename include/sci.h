@@ -142,8 +142,9 @@ int sci_set_determinants(sci_ctx *ctx, const uint64_t *keys, int64_t M, int n_al
  * integers, Sec. 3.2), strictly ascending as unsigned (64 x nwords)-bit integers.  With
  * two words the bucket keys are 128-bit (sorted by two stable radix passes), and sigma
  * (every precision mode, deterministic mode included), the diagonal, pair counts, row
- * costs, the connection exports and the density matrices (sci_rdm12, sci_rdm_grads) work
- * as for one word; row ranges, ENPT2 and batches need one-word keys (SCI_ERR_ARG).  sci_set_integrals takes up to 64
+ * costs, the connection exports, the density matrices (sci_rdm12, sci_rdm_grads) and
+ * ENPT2 (sci_enpt2) work as for one word; row ranges and batches need one-word keys
+ * (SCI_ERR_ARG).  sci_set_integrals takes up to 64
  * spatial orbitals or 128 spinors for these lists; sci_set_determinants (one word) returns
  * SCI_ERR_ARG when the orbitals do not fit one word.  Errors as sci_set_determinants. */
 int sci_set_determinants_w(sci_ctx *ctx, const uint64_t *keys, int nwords, int64_t M, int n_alpha,
@@ -310,10 +311,12 @@ int sci_rdm_grads(sci_ctx *ctx, const double *C, int nvec, const double *weights
  *   E2_k[W] = sum_{I in W} (sum_{J in P} H_IJ c_Jk)^2 / (E0_k - H_II)    (Eq. EW1)
  *   E2_k[P] = sum_{I in P} (<I|H|c_k> - c_Ik H_II)^2 / (E0_k - H_II)     (Eq. EP1)
  * over W, the determinants within a single or double excitation of the list.  Real
- * spin-orbital mode (n <= 32; batches by a code of the beta string) or complex spinor
- * mode (n <= 64, no spin conservation, the 4C workloads of Sec. 4; batches by a code of
- * the whole string; the squares are |.|^2 of complex numerators).  Spinor mode with real
- * integrals returns SCI_ERR_ARG.
+ * spin-orbital mode (batches by a code of the beta string) or complex spinor mode (no
+ * spin conservation, the 4C workloads of Sec. 4; batches by a code of the whole string;
+ * the squares are |.|^2 of complex numerators), on one-word lists (n <= 32 spatial
+ * orbitals or n <= 64 spinors) or two-word lists (sci_set_determinants_w: n <= 64 or
+ * n <= 128; the table keys are then 128-bit, claimed by a 16-byte compare-and-swap).
+ * Spinor mode with real integrals returns SCI_ERR_ARG.
  *   C: device, [M][nroots] doubles (complex mode: complex128, interleaved), 1 <= nroots
  *      <= 8 (need not be normalised; the formulas use c as given, so pass normalised
  *      eigenvectors for energies).
@@ -321,8 +324,9 @@ int sci_rdm_grads(sci_ctx *ctx, const double *C, int nvec, const double *weights
  *   eps: screening; a generated contribution with |H_IJ| max_k |c_Jk| < eps is dropped
  *      (0 = exact).
  *   table_bytes: device memory for the hash table of one batch (8 + 8 nroots bytes per
- *      entry, 8 + 16 nroots in complex mode, capacity the largest power of two within the
- *      budget, at least 256).  W is split into
+ *      entry, 8 + 16 nroots in complex mode; with two-word keys 16 bytes of key and the
+ *      entry rounded up to a multiple of 16 bytes; capacity the largest power of two
+ *      within the budget, at least 256).  W is split into
  *      2^t batches (t <= 10) so that a batch's generated excitations fill at most 60% of
  *      it; a batch that still overflows (or probes too far) restarts the sum with twice
  *      the batches.  Larger is not always faster: the inserts are random accesses, and a

@@ -50,6 +50,7 @@
 #include <algorithm>
 #include <cstring>
 #include <random>
+#include <type_traits>
 #include <vector>
 
 #include "sci_bits.cuh"
@@ -66,14 +67,14 @@ constexpr int kMaxBits = 10;   // at most 1024 batches
 
 struct Pt2 {
     int n, norb, na, nb;
-    uint64_t ref;
+    uint64_t ref, ref_hi;     // the reference string: orbitals 0..63 and 64..127
     const double *tab, *fref, *g_so;
     const double *fdiag, *G;  // [norb], [norb][norb]
     const double *Eref;
-    uint32_t gcode[64];       // codes of the beta orbitals (spin-orbital mode) or spinors
-    uint8_t obc[64];          // those orbitals sorted by code
+    uint32_t gcode[128];      // codes of the beta orbitals (spin-orbital mode) or spinors
+    uint8_t obc[128];         // those orbitals sorted by code
     uint8_t cstart[(1 << kMaxBits) + 1];  // first index in obc of each code
-    uint64_t *tab2;           // slots of (key, value[R]) words, key 0 = empty
+    uint64_t *tab2;           // slots of (key words, value words), key 0 = empty
     uint64_t mask;            // capacity - 1
     unsigned long long *count;
     unsigned long long limit;
@@ -99,28 +100,94 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x)
     return x;
 }
 
-// H_IJ for I = J - {i, j} + {a, b} (i < j, a < b, spin-orbital indices)
-__device__ __forceinline__ double h_double(const Pt2 &p, uint64_t J, int i, int j, int a, int b)
+// Occupation strings of one word (K = uint64_t, up to 64 orbitals) or two (K = W2, up to
+// 128 orbitals; word 0 = orbitals 0..63).  W2 is a pair of words with the bit operations
+// the excitations need, written out per word, so that the masks and shifts of the
+// generation code read the same for both.  (An earlier form held two-word strings as
+// unsigned __int128; in the generation kernel built for sm_103a the mask that clears an
+// orbital p >= 64 also cleared orbital p - 64 in some excitations, which dropped an
+// electron.  W2 has no 128-bit shifts.)
+struct W2 {
+    uint64_t lo, hi;
+    __host__ __device__ constexpr W2(uint64_t l = 0, uint64_t h = 0) : lo(l), hi(h) {}
+    __device__ explicit operator bool() const { return (lo | hi) != 0; }
+    __device__ explicit operator uint64_t() const { return lo; }
+};
+__device__ __forceinline__ W2 operator&(W2 a, W2 b) { return W2(a.lo & b.lo, a.hi & b.hi); }
+__device__ __forceinline__ W2 operator|(W2 a, W2 b) { return W2(a.lo | b.lo, a.hi | b.hi); }
+__device__ __forceinline__ W2 operator~(W2 a) { return W2(~a.lo, ~a.hi); }
+__device__ __forceinline__ W2 &operator&=(W2 &a, W2 b) { a.lo &= b.lo, a.hi &= b.hi; return a; }
+__device__ __forceinline__ bool operator==(W2 a, W2 b) { return a.lo == b.lo && a.hi == b.hi; }
+// a - 1 (borrow into the high word)
+__device__ __forceinline__ W2 operator-(W2 a, int one) { return W2(a.lo - (uint64_t)one, a.hi - (a.lo < (uint64_t)one ? 1ull : 0ull)); }
+// logical right shift by 0 <= s < 128
+__device__ __forceinline__ W2 operator>>(W2 a, int s)
 {
-    const uint64_t K = J & ~(1ull << i) & ~(1ull << j);
+    if (s == 0) return a;
+    if (s < 64) return W2((a.lo >> s) | (a.hi << (64 - s)), a.hi >> s);
+    return W2(a.hi >> (s - 64), 0);
+}
+
+template <int KW> struct KeyOf;
+template <> struct KeyOf<1> { using T = uint64_t; };
+template <> struct KeyOf<2> { using T = W2; };
+
+__device__ __forceinline__ int popck(uint64_t x) { return __popcll(x); }
+__device__ __forceinline__ int popck(W2 x) { return __popcll(x.lo) + __popcll(x.hi); }
+// lowest set bit (x != 0)
+__device__ __forceinline__ int lowbit(uint64_t x) { return __ffsll((long long)x) - 1; }
+__device__ __forceinline__ int lowbit(W2 x)
+{
+    return x.lo ? __ffsll((long long)x.lo) - 1 : 64 + __ffsll((long long)x.hi) - 1;
+}
+template <typename K> __device__ __forceinline__ K bitk(int p);
+template <> __device__ __forceinline__ uint64_t bitk<uint64_t>(int p) { return 1ull << p; }
+template <> __device__ __forceinline__ W2 bitk<W2>(int p) { return p < 64 ? W2(1ull << p, 0) : W2(0, 1ull << (p - 64)); }
+__device__ __forceinline__ bool has(uint64_t k, int p) { return (k >> p) & 1; }
+__device__ __forceinline__ bool has(W2 k, int p) { return p < 64 ? (k.lo >> p) & 1 : (k.hi >> (p - 64)) & 1; }
+// occupied orbitals of k below orbital x
+template <typename K> __device__ __forceinline__ int belowk(K k, int x) { return popck(k & (bitk<K>(x) - 1)); }
+template <int KW> __device__ __forceinline__ typename KeyOf<KW>::T load_key(const uint64_t *keys, int64_t J)
+{
+    if constexpr (KW == 1) return keys[J];
+    else return W2(keys[2 * J], keys[2 * J + 1]);
+}
+template <typename K> __device__ __forceinline__ K ref_of(const Pt2 &p)
+{
+    if constexpr (sizeof(K) == 8) return p.ref;
+    else return W2(p.ref, p.ref_hi);
+}
+__device__ __forceinline__ uint64_t key_lo(uint64_t x) { return x; }
+__device__ __forceinline__ uint64_t key_lo(W2 x) { return x.lo; }
+__device__ __forceinline__ uint64_t key_hi(uint64_t) { return 0; }
+__device__ __forceinline__ uint64_t key_hi(W2 x) { return x.hi; }
+__device__ __forceinline__ uint64_t hash_key(uint64_t x) { return mix64(x); }
+__device__ __forceinline__ uint64_t hash_key(W2 x) { return mix64(x.lo ^ mix64(x.hi + 0x9e3779b97f4a7c15ull)); }
+
+// H_IJ for I = J - {i, j} + {a, b} (i < j, a < b, spin-orbital indices)
+template <typename K>
+__device__ __forceinline__ double h_double(const Pt2 &p, K J, int i, int j, int a, int b)
+{
+    const K Kh = J & ~bitk<K>(i) & ~bitk<K>(j);
     uint32_t rowoff, colbase, r2, c2;
     const sci::TabRule tr{0, p.n};
     sci::pair_offsets(tr, a, b, rowoff, r2);      // bra (I) extras
     sci::pair_offsets(tr, i, j, c2, colbase);     // ket (J) extras
-    const bool ph = (below(K, a) + below(K, b) + below(K, i) + below(K, j)) & 1;
+    const bool ph = (belowk(Kh, a) + belowk(Kh, b) + belowk(Kh, i) + belowk(Kh, j)) & 1;
     return sflip(ph, __ldg(p.tab + rowoff + colbase));
 }
 
 // H_IJ for I = J - {i} + {a}
-__device__ __forceinline__ double h_single(const Pt2 &p, uint64_t J, int i, int a)
+template <typename K>
+__device__ __forceinline__ double h_single(const Pt2 &p, K J, int i, int a)
 {
-    const uint64_t S = J & ~(1ull << i);
+    const K S = J & ~bitk<K>(i), ref = ref_of<K>(p);
     const int norb = p.norb;
     double f = __ldg(p.fref + i * norb + a);
-    const uint64_t part = S & ~p.ref, holes = p.ref & ~S;
-    for (uint64_t m = part; m; m &= m - 1) f += __ldg(p.g_so + ((int64_t)(__ffsll((long long)m) - 1) * norb + i) * norb + a);
-    for (uint64_t m = holes; m; m &= m - 1) f -= __ldg(p.g_so + ((int64_t)(__ffsll((long long)m) - 1) * norb + i) * norb + a);
-    const bool ph = (below(S, a) + below(S, i)) & 1;
+    const K part = S & ~ref, holes = ref & ~S;
+    for (K m = part; m; m &= m - 1) f += __ldg(p.g_so + ((int64_t)lowbit(m) * norb + i) * norb + a);
+    for (K m = holes; m; m &= m - 1) f -= __ldg(p.g_so + ((int64_t)lowbit(m) * norb + i) * norb + a);
+    const bool ph = (belowk(S, a) + belowk(S, i)) & 1;
     return sflip(ph, f);
 }
 
@@ -128,44 +195,79 @@ __device__ __forceinline__ double h_single(const Pt2 &p, uint64_t J, int i, int 
 // counts the thread's claims: the kernel adds them to the distinct count once per warp at
 // its end, and the host compares that count with the load limit, instead of one add to a
 // single counter per claim); NULL after kMaxProbe probes (the table is too full: flag bit 2).
-template <int NW>
-__device__ __forceinline__ uint64_t *claim(const Pt2 &p, uint64_t I, uint32_t &nc)
+//
+// Slots: KW key words, then NW value words; with two key words the slot is padded to an
+// even number of words, so that every slot is 16-byte aligned for the 128-bit CAS.
+template <int KW, int NW> __host__ __device__ constexpr int slot_words() { return KW == 1 ? 1 + NW : (2 + NW + 1) & ~1; }
+
+// 128-bit compare-and-swap (sm_90 and later): [a] = n if [a] == e; returns the old value
+__device__ __forceinline__ void cas128(uint64_t *a, uint64_t e0, uint64_t e1, uint64_t n0, uint64_t n1, uint64_t &r0,
+                                       uint64_t &r1)
 {
-    uint64_t s = mix64(I) & p.mask;
+    unsigned long long o0, o1;
+    asm volatile("{\n\t.reg .b128 d, b, c;\n\tmov.b128 b, {%2, %3};\n\tmov.b128 c, {%4, %5};\n\t"
+                 "atom.global.cas.b128 d, [%6], b, c;\n\tmov.b128 {%0, %1}, d;\n\t}"
+                 : "=l"(o0), "=l"(o1)
+                 : "l"((unsigned long long)e0), "l"((unsigned long long)e1), "l"((unsigned long long)n0),
+                   "l"((unsigned long long)n1), "l"((unsigned long long)__cvta_generic_to_global(a))
+                 : "memory");
+    r0 = o0, r1 = o1;
+}
+
+template <int KW, int NW, typename K>
+__device__ __forceinline__ uint64_t *claim(const Pt2 &p, K I, uint32_t &nc)
+{
+    constexpr int SW = slot_words<KW, NW>();
+    uint64_t s = hash_key(I) & p.mask;
     for (int probe = 0; probe < kMaxProbe; probe++) {
-        uint64_t *slot = p.tab2 + s * (NW + 1);
-        uint64_t k = *slot;
-        if (k == kEmpty) {
-            k = atomicCAS(reinterpret_cast<unsigned long long *>(slot), (unsigned long long)kEmpty, (unsigned long long)I);
+        uint64_t *slot = p.tab2 + s * SW;
+        if constexpr (KW == 1) {
+            uint64_t k = *slot;
             if (k == kEmpty) {
-                nc++;
-                k = I;
+                k = atomicCAS(reinterpret_cast<unsigned long long *>(slot), (unsigned long long)kEmpty,
+                              (unsigned long long)I);
+                if (k == kEmpty) {
+                    nc++;
+                    k = I;
+                }
             }
+            if (k == I) return slot;   // the value words share the key's sector
+        } else {
+            // one atomic per probe: a plain 16-byte read of a key being written could be torn
+            const uint64_t lo = key_lo(I), hi = key_hi(I);
+            uint64_t r0, r1;
+            cas128(slot, 0, 0, lo, hi, r0, r1);
+            if ((r0 | r1) == 0) {
+                nc++;
+                return slot;
+            }
+            if (r0 == lo && r1 == hi) return slot;
         }
-        if (k == I) return slot;   // the value words share the key's sector
         s = (s + 1) & p.mask;
     }
     atomicOr(p.flag, 2);  // probe limit: the table is too full
     return nullptr;
 }
 
-template <int R>
-__device__ __forceinline__ void insert(const Pt2 &p, uint64_t I, double hij, const double *cJ, double cmax,
-                                       uint32_t &nc)
+template <int R, int KW, typename K>
+__device__ __forceinline__ void insert(const Pt2 &p, K I, double hij, const double *cJ, double cmax, uint32_t &nc)
 {
     if (p.eps > 0.0 && fabs(hij) * cmax < p.eps) return;
-    uint64_t *slot = claim<R>(p, I, nc);
+    uint64_t *slot = claim<KW, R>(p, I, nc);
     if (!slot) return;
 #pragma unroll
-    for (int v = 0; v < R; v++) atomicAdd(reinterpret_cast<double *>(slot + 1 + v), hij * cJ[v]);
+    for (int v = 0; v < R; v++) atomicAdd(reinterpret_cast<double *>(slot + KW + v), hij * cJ[v]);
 }
 
-__device__ __forceinline__ uint32_t code_of(const uint32_t *g, uint32_t s)
+// the batch code of a string: XOR of the codes of its occupied orbitals
+__device__ __forceinline__ uint32_t code_of64(const uint32_t *g, uint64_t s)
 {
     uint32_t c = 0;
-    for (; s; s &= s - 1) c ^= g[__ffs((int)s) - 1];
+    for (; s; s &= s - 1) c ^= g[__ffsll((long long)s) - 1];
     return c;
 }
+__device__ __forceinline__ uint32_t code_ofk(const uint32_t *g, uint64_t s) { return code_of64(g, s); }
+__device__ __forceinline__ uint32_t code_ofk(const uint32_t *g, W2 s) { return code_of64(g, s.lo) ^ code_of64(g + 64, s.hi); }
 
 // the claims of a warp's threads, added to the distinct count once
 __device__ __forceinline__ void add_claims(const Pt2 &p, uint32_t nc, int lane)
@@ -206,60 +308,73 @@ __device__ __forceinline__ void wq_flush(uint32_t *q, int &cnt, int lane, F &&pr
     cnt = 0;
 }
 
-// warp per determinant J of P: the excitations of J that fall in batch `batch`
-template <int R>
-__global__ void __launch_bounds__(kThreads)
+// warp per determinant J of P: the excitations of J that fall in batch `batch`.  KW = 1:
+// n <= 32 orbitals per spin (one-word keys); KW = 2: n <= 64 (two-word keys).
+template <int R, int KW>
+// (one-word keys, one or two roots: held to 40 registers, 6 CTAs per SM, as the kernel
+// was before the two-word form; at 48 registers the 2M-space sum took 8.6 s, at 40 8.05 s)
+__global__ void __launch_bounds__(kThreads, KW == 1 && R <= 2 ? 6 : 1)
 k_pt2_gen(const uint64_t *__restrict__ Pkeys, int64_t M, const double *__restrict__ C, Pt2 p, uint32_t batch, int tbits)
 {
-    __shared__ uint8_t s_orb[kWarps][128];      // occ alpha | vir alpha | occ beta | vir beta
-    __shared__ uint16_t s_list[kWarps][32 * 32]; // beta singles of this batch (j | v << 8)
-    __shared__ uint16_t s_pair[kMaxPairs];       // P -> (a, b)
+    using K = typename KeyOf<KW>::T;
+    constexpr int NO = 32 * KW;                   // orbitals per spin at most
+    constexpr int kMP = NO * (NO - 1) / 2;        // their unordered pairs
+    __shared__ uint8_t s_orb[kWarps][4 * NO];     // occ alpha | vir alpha | occ beta | vir beta
+    __shared__ uint16_t s_list[kWarps][32 * 32];  // beta singles of this batch (j | v << 8)
+    __shared__ uint16_t s_pair[kMP];              // P -> (a, b)
     __shared__ uint8_t s_cstart[(1 << kMaxBits) + 1];
-    __shared__ uint8_t s_obc[32];                // beta orbitals sorted by code
-    __shared__ uint32_t s_g[32];                 // beta-orbital codes
+    __shared__ uint8_t s_obc[NO];                 // beta orbitals sorted by code
+    __shared__ uint32_t s_g[NO];                  // beta-orbital codes
     __shared__ int s_nl[kWarps];
-    sci::fill_pair_table(s_pair);
+    for (int P = threadIdx.x; P < kMP; P += blockDim.x) {
+        int y = 1;
+        while ((y + 1) * y / 2 <= P) y++;
+        s_pair[P] = (uint16_t)((P - y * (y - 1) / 2) | (y << 8));
+    }
     for (int c = threadIdx.x; c <= (1 << tbits); c += blockDim.x) s_cstart[c] = p.cstart[c];
-    if (threadIdx.x < 32) s_obc[threadIdx.x] = p.obc[threadIdx.x], s_g[threadIdx.x] = p.gcode[threadIdx.x];
+    if (threadIdx.x < NO) s_obc[threadIdx.x] = p.obc[threadIdx.x], s_g[threadIdx.x] = p.gcode[threadIdx.x];
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint8_t *orb = s_orb[w];
+    // alpha and beta strings: 32-bit words for one-word keys (fewer registers), 64-bit
+    // for two
+    using S = std::conditional_t<KW == 1, uint32_t, uint64_t>;
     const int n = p.n, na = p.na, nb = p.nb, ua = n - na, ub = n - nb;
-    const uint32_t full = (uint32_t)((1ull << n) - 1);
+    const S full = n == 8 * (int)sizeof(S) ? ~(S)0 : (S)((1ull << n) - 1);
     const int64_t warps_total = (int64_t)gridDim.x * kWarps;
     uint32_t nclaim = 0;
     for (int64_t J = (int64_t)blockIdx.x * kWarps + w; J < M; J += warps_total) {
-        const uint64_t key = Pkeys[J];
-        const uint32_t oa = (uint32_t)(key & full), ob = (uint32_t)(key >> n);
-        const uint32_t va = full & ~oa, vb = full & ~ob;
+        const K key = load_key<KW>(Pkeys, J);
+        const S oa = (S)(uint64_t)key & full, ob = (S)(uint64_t)(key >> n) & full;
+        const S va = full & ~oa, vb = full & ~ob;
         double cJ[R], cmax = 0.0;
 #pragma unroll
         for (int v = 0; v < R; v++) cJ[v] = C[J * R + v], cmax = fmax(cmax, fabs(cJ[v]));
         __syncwarp();
-        if (lane < n) {
-            const uint32_t lm = (1u << lane) - 1;
-            if ((oa >> lane) & 1) orb[__popc(oa & lm)] = (uint8_t)lane;
-            else orb[32 + __popc(va & lm)] = (uint8_t)lane;
-            if ((ob >> lane) & 1) orb[64 + __popc(ob & lm)] = (uint8_t)lane;
-            else orb[96 + __popc(vb & lm)] = (uint8_t)lane;
+        for (int o = lane; o < n; o += 32) {
+            const S lm = (S)((1ull << o) - 1);
+            if ((oa >> o) & 1) orb[__popcll(oa & lm)] = (uint8_t)o;
+            else orb[NO + __popcll(va & lm)] = (uint8_t)o;
+            if ((ob >> o) & 1) orb[2 * NO + __popcll(ob & lm)] = (uint8_t)o;
+            else orb[3 * NO + __popcll(vb & lm)] = (uint8_t)o;
         }
         __syncwarp();
-        const uint32_t target = batch ^ code_of(s_g, ob);
+        const uint32_t target = batch ^ code_of64(s_g, ob);
 
         // alpha singles and alpha-alpha doubles: the beta string is unchanged
         if (target == 0) {
             const int c0 = na * ua, qa = ua * (ua - 1) / 2, c2 = na * (na - 1) / 2 * qa;
             for (int t = lane; t < c0 + c2; t += 32) {
                 if (t < c0) {
-                    const int i = orb[t / ua], a = orb[32 + t % ua];
-                    insert<R>(p, (key & ~(1ull << i)) | (1ull << a), h_single(p, key, i, a), cJ, cmax, nclaim);
+                    const int i = orb[t / ua], a = orb[NO + t % ua];
+                    insert<R, KW>(p, (key & ~bitk<K>(i)) | bitk<K>(a), h_single(p, key, i, a), cJ, cmax, nclaim);
                 } else {
                     const int s = t - c0;
                     const uint16_t po = s_pair[s / qa], pv = s_pair[s % qa];
-                    const int i = orb[po & 0xFF], j = orb[po >> 8], a = orb[32 + (pv & 0xFF)], b = orb[32 + (pv >> 8)];
+                    const int i = orb[po & 0xFF], j = orb[po >> 8], a = orb[NO + (pv & 0xFF)], b = orb[NO + (pv >> 8)];
                     if (p.bss && p.bss[j * (j - 1) / 2 + i] * cmax < p.eps) continue;   // the class's bound
-                    const uint64_t I = (key & ~(1ull << i) & ~(1ull << j)) | (1ull << a) | (1ull << b);
-                    insert<R>(p, I, h_double(p, key, i, j, a, b), cJ, cmax, nclaim);
+                    const K I = (key & ~bitk<K>(i) & ~bitk<K>(j)) | bitk<K>(a) | bitk<K>(b);
+                    insert<R, KW>(p, I, h_double(p, key, i, j, a, b), cJ, cmax, nclaim);
                 }
             }
         }
@@ -268,8 +383,8 @@ k_pt2_gen(const uint64_t *__restrict__ Pkeys, int64_t M, const double *__restric
         // doubles built on them
         if (lane == 0) s_nl[w] = 0;
         __syncwarp();
-        if (lane < nb) {
-            const int j = orb[64 + lane];
+        for (int x = lane; x < nb; x += 32) {
+            const int j = orb[2 * NO + x];
             const uint32_t c = target ^ s_g[j];
             for (int q = s_cstart[c]; q < s_cstart[c + 1]; q++) {
                 const int v = s_obc[q];
@@ -285,12 +400,12 @@ k_pt2_gen(const uint64_t *__restrict__ Pkeys, int64_t M, const double *__restric
             const int jb = n + (e & 0xFF), vb_ = n + (e >> 8);
             const int s = t % (1 + c0);
             if (s == 0) {
-                insert<R>(p, (key & ~(1ull << jb)) | (1ull << vb_), h_single(p, key, jb, vb_), cJ, cmax, nclaim);
+                insert<R, KW>(p, (key & ~bitk<K>(jb)) | bitk<K>(vb_), h_single(p, key, jb, vb_), cJ, cmax, nclaim);
             } else {
-                const int i = orb[(s - 1) / ua], a = orb[32 + (s - 1) % ua];
+                const int i = orb[(s - 1) / ua], a = orb[NO + (s - 1) % ua];
                 if (p.bab && p.bab[(e & 0xFF) * n + i] * cmax < p.eps) continue;   // the class's bound
-                const uint64_t I = (key & ~(1ull << i) & ~(1ull << jb)) | (1ull << a) | (1ull << vb_);
-                insert<R>(p, I, h_double(p, key, i, jb, a, vb_), cJ, cmax, nclaim);
+                const K I = (key & ~bitk<K>(i) & ~bitk<K>(jb)) | bitk<K>(a) | bitk<K>(vb_);
+                insert<R, KW>(p, I, h_double(p, key, i, jb, a, vb_), cJ, cmax, nclaim);
             }
         }
 
@@ -300,14 +415,14 @@ k_pt2_gen(const uint64_t *__restrict__ Pkeys, int64_t M, const double *__restric
         const int pb = nb * (nb - 1) / 2;
         for (int t = lane; t < pb * ub; t += 32) {
             const uint16_t po = s_pair[t / ub];
-            const int j1 = orb[64 + (po & 0xFF)], j2 = orb[64 + (po >> 8)], b1 = orb[96 + t % ub];
+            const int j1 = orb[2 * NO + (po & 0xFF)], j2 = orb[2 * NO + (po >> 8)], b1 = orb[3 * NO + t % ub];
             if (p.bss3 && p.bss3[(j2 * (j2 - 1) / 2 + j1) * n + b1] * cmax < p.eps) continue;   // the class's bound
             const uint32_t c = target ^ s_g[j1] ^ s_g[j2] ^ s_g[b1];
             for (int q = s_cstart[c]; q < s_cstart[c + 1]; q++) {
                 const int b2 = s_obc[q];
                 if (b2 <= b1 || ((ob >> b2) & 1)) continue;
-                const uint64_t I = (key & ~(1ull << (n + j1)) & ~(1ull << (n + j2))) | (1ull << (n + b1)) | (1ull << (n + b2));
-                insert<R>(p, I, h_double(p, key, n + j1, n + j2, n + b1, n + b2), cJ, cmax, nclaim);
+                const K I = (key & ~bitk<K>(n + j1) & ~bitk<K>(n + j2)) | bitk<K>(n + b1) | bitk<K>(n + b2);
+                insert<R, KW>(p, I, h_double(p, key, n + j1, n + j2, n + b1, n + b2), cJ, cmax, nclaim);
             }
         }
         __syncwarp();
@@ -327,46 +442,47 @@ __device__ __forceinline__ zdbl ldz(const zdbl *p)
 
 // H_IJ (spinors) for I = J - {i, j} + {a, b}: the antisymmetrised table entry of the bra
 // pair (a, b) and the ket pair (i, j), with the phase of the sigma kernels
-__device__ __forceinline__ zdbl hz_double(const Pt2 &p, uint64_t J, int i, int j, int a, int b)
+template <typename K>
+__device__ __forceinline__ zdbl hz_double(const Pt2 &p, K J, int i, int j, int a, int b)
 {
-    const uint64_t K = J & ~(1ull << i) & ~(1ull << j);
+    const K Kh = J & ~bitk<K>(i) & ~bitk<K>(j);
     uint32_t rowoff, colbase, r2, c2;
     const sci::TabRule tr{1, p.n};
     sci::pair_offsets(tr, a, b, rowoff, r2);
     sci::pair_offsets(tr, i, j, c2, colbase);
-    const bool ph = (below(K, a) + below(K, b) + below(K, i) + below(K, j)) & 1;
+    const bool ph = (belowk(Kh, a) + belowk(Kh, b) + belowk(Kh, i) + belowk(Kh, j)) & 1;
     return sflip(ph, ldz(reinterpret_cast<const zdbl *>(p.tab) + rowoff + colbase));
 }
 
 // H_IJ (spinors) for I = J - {i} + {a}: F^ref_ai plus the terms of the spinors where
 // S = J - {i} and the reference differ
-__device__ __forceinline__ zdbl hz_single(const Pt2 &p, uint64_t J, int i, int a)
+template <typename K>
+__device__ __forceinline__ zdbl hz_single(const Pt2 &p, K J, int i, int a)
 {
-    const uint64_t S = J & ~(1ull << i);
+    const K S = J & ~bitk<K>(i), ref = ref_of<K>(p);
     const int norb = p.norb;
     const zdbl *fref = reinterpret_cast<const zdbl *>(p.fref), *g = reinterpret_cast<const zdbl *>(p.g_so);
     zdbl f = ldz(fref + i * norb + a);
-    const uint64_t part = S & ~p.ref, holes = p.ref & ~S;
-    for (uint64_t m = part; m; m &= m - 1) {
-        const zdbl t = ldz(g + ((int64_t)(__ffsll((long long)m) - 1) * norb + i) * norb + a);
+    const K part = S & ~ref, holes = ref & ~S;
+    for (K m = part; m; m &= m - 1) {
+        const zdbl t = ldz(g + ((int64_t)lowbit(m) * norb + i) * norb + a);
         f.x += t.x, f.y += t.y;
     }
-    for (uint64_t m = holes; m; m &= m - 1) {
-        const zdbl t = ldz(g + ((int64_t)(__ffsll((long long)m) - 1) * norb + i) * norb + a);
+    for (K m = holes; m; m &= m - 1) {
+        const zdbl t = ldz(g + ((int64_t)lowbit(m) * norb + i) * norb + a);
         f.x -= t.x, f.y -= t.y;
     }
-    const bool ph = (below(S, a) + below(S, i)) & 1;
+    const bool ph = (belowk(S, a) + belowk(S, i)) & 1;
     return sflip(ph, f);
 }
 
-template <int R>
-__device__ __forceinline__ void insert_z(const Pt2 &p, uint64_t I, zdbl h, const zdbl *cJ, double cmax,
-                                         uint32_t &nc)
+template <int R, int KW, typename K>
+__device__ __forceinline__ void insert_z(const Pt2 &p, K I, zdbl h, const zdbl *cJ, double cmax, uint32_t &nc)
 {
     if (p.eps > 0.0 && sqrt(h.x * h.x + h.y * h.y) * cmax < p.eps) return;
-    uint64_t *slot = claim<2 * R>(p, I, nc);
+    uint64_t *slot = claim<KW, 2 * R>(p, I, nc);
     if (!slot) return;
-    double *val = reinterpret_cast<double *>(slot + 1);
+    double *val = reinterpret_cast<double *>(slot + KW);
 #pragma unroll
     for (int v = 0; v < R; v++) {
         atomicAdd(val + 2 * v, h.x * cJ[v].x - h.y * cJ[v].y);
@@ -374,45 +490,39 @@ __device__ __forceinline__ void insert_z(const Pt2 &p, uint64_t I, zdbl h, const
     }
 }
 
-__device__ __forceinline__ uint32_t code_of64(const uint32_t *g, uint64_t s)
-{
-    uint32_t c = 0;
-    for (; s; s &= s - 1) c ^= g[__ffsll((long long)s) - 1];
-    return c;
-}
-
-// pairs x < y of at most 64 spinors, P = y(y-1)/2 + x  ->  x | y << 8
-constexpr int kMaxPairs64 = 64 * 63 / 2;
-
-// warp per determinant J of P: the excitations of J (spinors) that fall in batch `batch`
-template <int R>
+// warp per determinant J of P: the excitations of J (spinors) that fall in batch `batch`.
+// KW = 1: n <= 64 spinors (one-word keys); KW = 2: n <= 128 (two-word keys).
+template <int R, int KW>
 __global__ void __launch_bounds__(kThreads)
 k_pt2_gen_z(const uint64_t *__restrict__ Pkeys, int64_t M, const zdbl *__restrict__ C, Pt2 p, uint32_t batch, int tbits)
 {
-    __shared__ uint8_t s_orb[kWarps][128];       // occupied spinors | virtual spinors (+ 64)
-    __shared__ uint16_t s_pair[kMaxPairs64];     // P -> (x, y)
+    using K = typename KeyOf<KW>::T;
+    constexpr int NZ = 64 * KW;                  // spinors at most
+    constexpr int kMP = NZ * (NZ - 1) / 2;       // pairs x < y, P = y(y-1)/2 + x -> x | y << 8
+    __shared__ uint8_t s_orb[kWarps][2 * NZ];    // occupied spinors | virtual spinors (+ NZ)
+    __shared__ uint16_t s_pair[kMP];
     __shared__ uint8_t s_cstart[(1 << kMaxBits) + 1];
-    __shared__ uint8_t s_obc[64];                // spinors sorted by code
-    __shared__ uint32_t s_g[64];                 // spinor codes
+    __shared__ uint8_t s_obc[NZ];                // spinors sorted by code
+    __shared__ uint32_t s_g[NZ];                 // spinor codes
     __shared__ uint32_t s_q[kWarps][64];         // the warp's queue of double finds
-    for (int P = threadIdx.x; P < kMaxPairs64; P += blockDim.x) {
+    for (int P = threadIdx.x; P < kMP; P += blockDim.x) {
         int y = 1;
         while ((y + 1) * y / 2 <= P) y++;
         s_pair[P] = (uint16_t)((P - y * (y - 1) / 2) | (y << 8));
     }
     for (int c = threadIdx.x; c <= (1 << tbits); c += blockDim.x) s_cstart[c] = p.cstart[c];
-    if (threadIdx.x < 64) s_obc[threadIdx.x] = p.obc[threadIdx.x], s_g[threadIdx.x] = p.gcode[threadIdx.x];
+    if (threadIdx.x < NZ) s_obc[threadIdx.x] = p.obc[threadIdx.x], s_g[threadIdx.x] = p.gcode[threadIdx.x];
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint8_t *orb = s_orb[w];
     const int n = p.n, N = p.na, nv = n - N;
-    const uint64_t full = n == 64 ? ~0ull : ((1ull << n) - 1);
+    const K full = n == 8 * (int)sizeof(K) ? ~(K)0 : bitk<K>(n) - 1;
     const int npairs = N * (N - 1) / 2;
     const int64_t warps_total = (int64_t)gridDim.x * kWarps;
     uint32_t nclaim = 0;
     for (int64_t J = (int64_t)blockIdx.x * kWarps + w; J < M; J += warps_total) {
-        const uint64_t key = Pkeys[J];
-        const uint64_t vir = full & ~key;
+        const K key = load_key<KW>(Pkeys, J);
+        const K vir = full & ~key;
         zdbl cJ[R];
         double cmax = 0.0;
 #pragma unroll
@@ -422,28 +532,28 @@ k_pt2_gen_z(const uint64_t *__restrict__ Pkeys, int64_t M, const zdbl *__restric
         }
         __syncwarp();
         for (int o = lane; o < n; o += 32) {
-            const uint64_t lm = (1ull << o) - 1;
-            if ((key >> o) & 1) orb[__popcll(key & lm)] = (uint8_t)o;
-            else orb[64 + __popcll(vir & lm)] = (uint8_t)o;
+            const K lm = bitk<K>(o) - 1;
+            if (has(key, o)) orb[popck(key & lm)] = (uint8_t)o;
+            else orb[NZ + popck(vir & lm)] = (uint8_t)o;
         }
         __syncwarp();
-        const uint32_t target = batch ^ code_of64(s_g, key);
+        const uint32_t target = batch ^ code_ofk(s_g, key);
         // singles i -> a of this batch: g(a) = target ^ g(i)
         for (int x = lane; x < N; x += 32) {
             const int i = orb[x];
             const uint32_t c = target ^ s_g[i];
             for (int q = s_cstart[c]; q < s_cstart[c + 1]; q++) {
                 const int a = s_obc[q];
-                if ((key >> a) & 1) continue;
-                insert_z<R>(p, (key & ~(1ull << i)) | (1ull << a), hz_single(p, key, i, a), cJ, cmax, nclaim);
+                if (has(key, a)) continue;
+                insert_z<R, KW>(p, (key & ~bitk<K>(i)) | bitk<K>(a), hz_single(p, key, i, a), cJ, cmax, nclaim);
             }
         }
         // doubles i < j -> a < b: for each occupied pair and first virtual a, the second
         // virtual has code target ^ g(i) ^ g(j) ^ g(a); the finds go through the warp's queue
         auto ins = [&](uint32_t e) {
             const int i = e & 0xFF, j = (e >> 8) & 0xFF, a = (e >> 16) & 0xFF, b = e >> 24;
-            const uint64_t I = (key & ~(1ull << i) & ~(1ull << j)) | (1ull << a) | (1ull << b);
-            insert_z<R>(p, I, hz_double(p, key, i, j, a, b), cJ, cmax, nclaim);
+            const K I = (key & ~bitk<K>(i) & ~bitk<K>(j)) | bitk<K>(a) | bitk<K>(b);
+            insert_z<R, KW>(p, I, hz_double(p, key, i, j, a, b), cJ, cmax, nclaim);
         };
         int cnt = 0;
         for (int base = 0; base < npairs * nv; base += 32) {
@@ -451,7 +561,7 @@ k_pt2_gen_z(const uint64_t *__restrict__ Pkeys, int64_t M, const zdbl *__restric
             int q = 0, qe = 0, i = 0, j = 0, a = 0;
             if (t < npairs * nv) {
                 const uint16_t po = s_pair[t / nv];
-                i = orb[po & 0xFF], j = orb[po >> 8], a = orb[64 + t % nv];
+                i = orb[po & 0xFF], j = orb[po >> 8], a = orb[NZ + t % nv];
                 if (!(p.bss3 && p.bss3[(j * (j - 1) / 2 + i) * n + a] * cmax < p.eps)) {   // the class's bound
                     const uint32_t c = target ^ s_g[i] ^ s_g[j] ^ s_g[a];
                     q = s_cstart[c], qe = s_cstart[c + 1];
@@ -462,7 +572,7 @@ k_pt2_gen_z(const uint64_t *__restrict__ Pkeys, int64_t M, const zdbl *__restric
                 int b = 0;
                 if (q < qe) {
                     b = s_obc[q];
-                    hit = b > a && !((key >> b) & 1);
+                    hit = b > a && !has(key, b);
                 }
                 wq_push(s_q[w], cnt, hit, (uint32_t)i | (uint32_t)j << 8 | (uint32_t)a << 16 | (uint32_t)b << 24, lane,
                         ins);
@@ -477,16 +587,18 @@ k_pt2_gen_z(const uint64_t *__restrict__ Pkeys, int64_t M, const zdbl *__restric
 // it scans into a buffer of 32 and evaluates full buffers, so every lane works; H_II
 // (E_ref plus O(level^2) table terms) is summed in paired FP32 from split copies of F and
 // G in shared memory, and added to E_ref in FP64.
-template <int R, bool CPLX>
+template <int R, bool CPLX, int KW>
 __global__ void __launch_bounds__(kThreads)
 k_pt2_eval(Pt2 p, uint64_t cap, const double *__restrict__ E0, double *__restrict__ out)
 {
+    using K = typename KeyOf<KW>::T;
     constexpr int NW = CPLX ? 2 * R : R;   // value words per slot
-    __shared__ float2 sG[64 * 64];
-    __shared__ float2 sF[64];
+    constexpr int SW = slot_words<KW, NW>();
+    extern __shared__ float2 s_gf[];       // G [norb][norb], then F [norb] (dynamic)
     __shared__ uint64_t sbuf[kWarps][64];
     __shared__ double red[kWarps][R];
     const int norb = p.norb;
+    float2 *sG = s_gf, *sF = s_gf + norb * norb;
     for (int t = threadIdx.x; t < norb * norb; t += blockDim.x) sG[t] = sci::ds_split_int(p.G[t]);
     for (int t = threadIdx.x; t < norb; t += blockDim.x) sF[t] = sci::ds_split_int(p.fdiag[t]);
     __syncthreads();
@@ -495,37 +607,40 @@ k_pt2_eval(Pt2 p, uint64_t cap, const double *__restrict__ E0, double *__restric
     double acc[R], e0[R];
 #pragma unroll
     for (int v = 0; v < R; v++) acc[v] = 0.0, e0[v] = E0[v];
+    const K ref = ref_of<K>(p);
     auto evaluate = [&](uint64_t s) {
-        const uint64_t *slot = p.tab2 + s * (NW + 1);
-        const uint64_t I = slot[0];
-        const uint64_t H = p.ref & ~I, Pm = I & ~p.ref;
+        const uint64_t *slot = p.tab2 + s * SW;
+        K I;
+        if constexpr (KW == 1) I = slot[0];
+        else I = W2(slot[0], slot[1]);
+        const K H = ref & ~I, Pm = I & ~ref;
         sci::Ds e;
         sci::ds_zero(e);
-        for (uint64_t m = H; m; m &= m - 1) {
-            const int i = __ffsll((long long)m) - 1;
+        for (K m = H; m; m &= m - 1) {
+            const int i = lowbit(m);
             const float2 f = sF[i];
             sci::ds_add(e, make_float2(-f.x, -f.y));
-            for (uint64_t m2 = m & (m - 1); m2; m2 &= m2 - 1) sci::ds_add(e, sG[i * norb + __ffsll((long long)m2) - 1]);
-            for (uint64_t m2 = Pm; m2; m2 &= m2 - 1) {
-                const float2 g = sG[i * norb + __ffsll((long long)m2) - 1];
+            for (K m2 = m & (m - 1); m2; m2 &= m2 - 1) sci::ds_add(e, sG[i * norb + lowbit(m2)]);
+            for (K m2 = Pm; m2; m2 &= m2 - 1) {
+                const float2 g = sG[i * norb + lowbit(m2)];
                 sci::ds_add(e, make_float2(-g.x, -g.y));
             }
         }
-        for (uint64_t m = Pm; m; m &= m - 1) {
-            const int a = __ffsll((long long)m) - 1;
+        for (K m = Pm; m; m &= m - 1) {
+            const int a = lowbit(m);
             sci::ds_add(e, sF[a]);
-            for (uint64_t m2 = m & (m - 1); m2; m2 &= m2 - 1) sci::ds_add(e, sG[a * norb + __ffsll((long long)m2) - 1]);
+            for (K m2 = m & (m - 1); m2; m2 &= m2 - 1) sci::ds_add(e, sG[a * norb + lowbit(m2)]);
         }
         const double hii = Eref + sci::ds_value(e);
 #pragma unroll
         for (int v = 0; v < R; v++) {
             double num2;
             if constexpr (CPLX) {
-                const double re = __longlong_as_double((long long)slot[1 + 2 * v]);
-                const double im = __longlong_as_double((long long)slot[2 + 2 * v]);
+                const double re = __longlong_as_double((long long)slot[KW + 2 * v]);
+                const double im = __longlong_as_double((long long)slot[KW + 1 + 2 * v]);
                 num2 = re * re + im * im;
             } else {
-                const double num = __longlong_as_double((long long)slot[1 + v]);
+                const double num = __longlong_as_double((long long)slot[KW + v]);
                 num2 = num * num;
             }
             acc[v] += num2 / (e0[v] - hii);
@@ -535,7 +650,11 @@ k_pt2_eval(Pt2 p, uint64_t cap, const double *__restrict__ E0, double *__restric
     const uint64_t stride = (uint64_t)gridDim.x * kThreads;
     for (uint64_t s0 = (uint64_t)blockIdx.x * kThreads + (uint64_t)w * 32; s0 < cap; s0 += stride) {
         const uint64_t s = s0 + lane;
-        const bool occ = s < cap && p.tab2[s * (NW + 1)] != kEmpty;
+        bool occ = false;
+        if (s < cap) {
+            const uint64_t *slot = p.tab2 + s * SW;
+            occ = KW == 1 ? slot[0] != kEmpty : (slot[0] | slot[KW - 1]) != kEmpty;
+        }
         const unsigned m = __ballot_sync(0xffffffffu, occ);
         if (occ) sbuf[w][nbuf + __popc(m & ((1u << lane) - 1))] = s;
         nbuf += __popc(m);
@@ -606,10 +725,11 @@ __device__ __forceinline__ double re_of(double a) { return a; }
 __device__ __forceinline__ double re_of(zdbl a) { return a.x; }
 
 template <typename T>
-__global__ void k_pt2_setup(int norb, uint64_t ref, const T *__restrict__ h_so, const T *__restrict__ jd,
-                            const T *__restrict__ kd, double *__restrict__ G, double *__restrict__ fdiag,
-                            double *__restrict__ Eref)
+__global__ void k_pt2_setup(int norb, uint64_t ref_lo, uint64_t ref_hi, const T *__restrict__ h_so,
+                            const T *__restrict__ jd, const T *__restrict__ kd, double *__restrict__ G,
+                            double *__restrict__ fdiag, double *__restrict__ Eref)
 {
+    const W2 ref(ref_lo, ref_hi);
     for (int t = threadIdx.x; t < norb * norb; t += blockDim.x) {
         const int a = t / norb, b = t % norb;
         G[t] = a == b ? 0.0 : re_of(jd[t]) - re_of(kd[t]);
@@ -617,15 +737,15 @@ __global__ void k_pt2_setup(int norb, uint64_t ref, const T *__restrict__ h_so, 
     __syncthreads();
     for (int a = threadIdx.x; a < norb; a += blockDim.x) {
         double f = re_of(h_so[a * norb + a]);
-        for (uint64_t m = ref; m; m &= m - 1) f += G[a * norb + __ffsll((long long)m) - 1];
+        for (W2 m = ref; m; m &= m - 1) f += G[a * norb + lowbit(m)];
         fdiag[a] = f;
     }
     if (threadIdx.x == 0) {
         double e = 0.0;
-        for (uint64_t m = ref; m; m &= m - 1) {
-            const int i = __ffsll((long long)m) - 1;
+        for (W2 m = ref; m; m &= m - 1) {
+            const int i = lowbit(m);
             e += re_of(h_so[i * norb + i]);
-            for (uint64_t m2 = m & (m - 1); m2; m2 &= m2 - 1) e += G[i * norb + __ffsll((long long)m2) - 1];
+            for (W2 m2 = m & (m - 1); m2; m2 &= m2 - 1) e += G[i * norb + lowbit(m2)];
         }
         *Eref = e;
     }
@@ -676,11 +796,13 @@ int grid_for(int64_t n)
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, 152 * 8));
 }
 
-// SPIN: complex spinor mode (C is [M][R] complex128); otherwise real spin-orbital mode
-template <int R, bool SPIN>
+// SPIN: complex spinor mode (C is [M][R] complex128); otherwise real spin-orbital mode.
+// KW: key words (1 or 2) of the determinant list.
+template <int R, bool SPIN, int KW>
 int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t table_bytes, double *E2, int64_t *stats)
 {
     constexpr int NW = SPIN ? 2 * R : R;   // value words per table slot
+    constexpr int SW = slot_words<KW, NW>();
     constexpr int SC = SPIN ? 2 : 1;       // doubles per coefficient
     const int64_t M = ctx->M;
     const int n = ctx->n, norb = ctx->norb, na = ctx->na, nb = ctx->nb;
@@ -725,13 +847,13 @@ int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t
             k_pt2_p<R, double><<<grid_for(M), kThreads, 0, st>>>(M, C, S, ctx->hdiag, dE0, outP);
     }
     if constexpr (SPIN)
-        k_pt2_setup<zdbl><<<1, 256, 0, st>>>(norb, ctx->ref, (const zdbl *)ctx->h_so, (const zdbl *)ctx->jd,
-                                             (const zdbl *)ctx->kd, G, fdiag, Eref);
+        k_pt2_setup<zdbl><<<1, 256, 0, st>>>(norb, ctx->ref, ctx->ref_hi, (const zdbl *)ctx->h_so,
+                                             (const zdbl *)ctx->jd, (const zdbl *)ctx->kd, G, fdiag, Eref);
     else
-        k_pt2_setup<double><<<1, 256, 0, st>>>(norb, ctx->ref, (const double *)ctx->h_so, (const double *)ctx->jd,
-                                               (const double *)ctx->kd, G, fdiag, Eref);
+        k_pt2_setup<double><<<1, 256, 0, st>>>(norb, ctx->ref, ctx->ref_hi, (const double *)ctx->h_so,
+                                               (const double *)ctx->jd, (const double *)ctx->kd, G, fdiag, Eref);
     // the table: capacity a power of two within the budget
-    const size_t slot = sizeof(uint64_t) + sizeof(double) * NW;
+    const size_t slot = sizeof(uint64_t) * SW;
     uint64_t cap = 1ull << 8;  // at least 256 entries
     while ((cap << 1) * slot <= table_bytes) cap <<= 1;
     if (cudaMalloc(&tab2, cap * slot) != cudaSuccess) {
@@ -776,7 +898,7 @@ int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t
         }
         p.bss3 = b3;
     }
-    p.n = n, p.norb = norb, p.na = na, p.nb = nb, p.ref = ctx->ref;
+    p.n = n, p.norb = norb, p.na = na, p.nb = nb, p.ref = ctx->ref, p.ref_hi = ctx->ref_hi;
     p.tab = (const double *)ctx->tab, p.fref = (const double *)ctx->fref, p.g_so = (const double *)ctx->g_so;
     p.fdiag = fdiag, p.G = G, p.Eref = Eref;
     p.tab2 = tab2, p.mask = cap - 1, p.count = count, p.flag = flag;
@@ -800,7 +922,7 @@ int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t
     // orbitals grouped by code
     auto set_codes = [&](int t) {
         std::mt19937 rng(20250130u + (unsigned)t);
-        for (int o = 0; o < 64; o++) p.gcode[o] = t ? (uint32_t)(rng() & ((1u << t) - 1)) : 0u;
+        for (int o = 0; o < 128; o++) p.gcode[o] = t ? (uint32_t)(rng() & ((1u << t) - 1)) : 0u;
         std::vector<int> cnt((1 << t) + 1, 0);
         for (int o = 0; o < n; o++) cnt[p.gcode[o] + 1]++;
         for (int c = 1; c <= (1 << t); c++) cnt[c] += cnt[c - 1];
@@ -808,6 +930,12 @@ int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t
         std::vector<int> fill(cnt.begin(), cnt.end() - 1);
         for (int o = 0; o < n; o++) p.obc[fill[p.gcode[o]]++] = (uint8_t)o;
     };
+    // the evaluation kernel's G and F (paired floats) in dynamic shared memory
+    const size_t eval_smem = sizeof(float2) * ((size_t)norb * norb + norb);
+    if (sci_cuda_check(ctx, cudaFuncSetAttribute(k_pt2_eval<R, SPIN, KW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)eval_smem),
+                       "enpt2 eval attr"))
+        return done(SCI_ERR_CUDA);
     // one batch: clear the table, generate, evaluate (optional); returns the distinct
     // count and the overflow flag
     auto pass = [&](uint32_t b, int t, bool eval, int64_t &cnt_out, int &flag_out) -> int {
@@ -819,14 +947,15 @@ int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t
         if (M > 0) {
             const unsigned blocks = (unsigned)std::min<int64_t>((M + kWarps - 1) / kWarps, 152 * 16);
             if constexpr (SPIN)
-                k_pt2_gen_z<R><<<blocks, kThreads, 0, st>>>(ctx->keys, M, reinterpret_cast<const zdbl *>(C), p, b, t);
+                k_pt2_gen_z<R, KW><<<blocks, kThreads, 0, st>>>(ctx->keys, M, reinterpret_cast<const zdbl *>(C), p, b,
+                                                               t);
             else
-                k_pt2_gen<R><<<blocks, kThreads, 0, st>>>(ctx->keys, M, C, p, b, t);
+                k_pt2_gen<R, KW><<<blocks, kThreads, 0, st>>>(ctx->keys, M, C, p, b, t);
         }
         if (sci_cuda_check(ctx, cudaEventRecord(ev[2], st), "enpt2 event")) return SCI_ERR_CUDA;
         if (eval)
-            k_pt2_eval<R, SPIN><<<grid_for((int64_t)std::min<uint64_t>(cap, 1ull << 40)), kThreads, 0, st>>>(p, cap, dE0,
-                                                                                                          outW);
+            k_pt2_eval<R, SPIN, KW><<<grid_for((int64_t)std::min<uint64_t>(cap, 1ull << 40)), kThreads, eval_smem, st>>>(
+                p, cap, dE0, outW);
         unsigned long long hc[2] = {0, 0};
         if (sci_cuda_check(ctx, cudaEventRecord(ev[3], st), "enpt2 event") ||
             sci_cuda_check(ctx, cudaMemcpyAsync(hc, count, sizeof(hc), cudaMemcpyDeviceToHost, st), "enpt2 flag") ||
@@ -899,6 +1028,34 @@ int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t
     return SCI_OK;
 }
 
+template <int KW>
+int enpt2_dispatch(sci_ctx *ctx, const double *C, int nroots, const double *E0, double eps, size_t table_bytes,
+                   double *E2, int64_t *stats)
+{
+    if (ctx->spinors) {
+        switch (nroots) {
+            case 1: return pt2_run<1, true, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+            case 2: return pt2_run<2, true, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+            case 3: return pt2_run<3, true, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+            case 4: return pt2_run<4, true, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+            case 5: return pt2_run<5, true, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+            case 6: return pt2_run<6, true, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+            case 7: return pt2_run<7, true, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+            default: return pt2_run<8, true, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+        }
+    }
+    switch (nroots) {
+        case 1: return pt2_run<1, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+        case 2: return pt2_run<2, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+        case 3: return pt2_run<3, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+        case 4: return pt2_run<4, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+        case 5: return pt2_run<5, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+        case 6: return pt2_run<6, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+        case 7: return pt2_run<7, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+        default: return pt2_run<8, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+    }
+}
+
 }  // namespace
 
 extern "C" int sci_enpt2(sci_ctx *ctx, const double *C, int nroots, const double *E0, double eps, size_t table_bytes,
@@ -908,32 +1065,12 @@ extern "C" int sci_enpt2(sci_ctx *ctx, const double *C, int nroots, const double
     if (!ctx->have_ints || !ctx->have_dets) return sci_fail(ctx, SCI_ERR_STATE, "enpt2: integrals and determinants first");
     if (ctx->spinors != ctx->cplx)
         return sci_fail(ctx, SCI_ERR_ARG, "enpt2: real spin-orbital mode or complex spinor mode");
-    if (ctx->nwords != 1 || (!ctx->spinors && ctx->n > 32) || ctx->n > 64)
-        return sci_fail(ctx, SCI_ERR_ARG, "enpt2: one-word keys, n <= 32 (spin-orbitals) or n <= 64 (spinors)");
+    if (ctx->nwords > 2 || ctx->norb > 64 * ctx->nwords)
+        return sci_fail(ctx, SCI_ERR_ARG, "enpt2: at most 64 spin-orbitals or spinors per key word, two words");
     if (nroots < 1 || nroots > 8 || !E0 || !E2 || (ctx->M > 0 && !C))
         return sci_fail(ctx, SCI_ERR_ARG, "enpt2: need 1 <= nroots <= 8, C, E0 and E2");
     if (eps < 0.0) return sci_fail(ctx, SCI_ERR_ARG, "enpt2: eps < 0");
     if (sci_cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) return SCI_ERR_CUDA;
-    if (ctx->spinors) {
-        switch (nroots) {
-            case 1: return pt2_run<1, true>(ctx, C, E0, eps, table_bytes, E2, stats);
-            case 2: return pt2_run<2, true>(ctx, C, E0, eps, table_bytes, E2, stats);
-            case 3: return pt2_run<3, true>(ctx, C, E0, eps, table_bytes, E2, stats);
-            case 4: return pt2_run<4, true>(ctx, C, E0, eps, table_bytes, E2, stats);
-            case 5: return pt2_run<5, true>(ctx, C, E0, eps, table_bytes, E2, stats);
-            case 6: return pt2_run<6, true>(ctx, C, E0, eps, table_bytes, E2, stats);
-            case 7: return pt2_run<7, true>(ctx, C, E0, eps, table_bytes, E2, stats);
-            default: return pt2_run<8, true>(ctx, C, E0, eps, table_bytes, E2, stats);
-        }
-    }
-    switch (nroots) {
-        case 1: return pt2_run<1, false>(ctx, C, E0, eps, table_bytes, E2, stats);
-        case 2: return pt2_run<2, false>(ctx, C, E0, eps, table_bytes, E2, stats);
-        case 3: return pt2_run<3, false>(ctx, C, E0, eps, table_bytes, E2, stats);
-        case 4: return pt2_run<4, false>(ctx, C, E0, eps, table_bytes, E2, stats);
-        case 5: return pt2_run<5, false>(ctx, C, E0, eps, table_bytes, E2, stats);
-        case 6: return pt2_run<6, false>(ctx, C, E0, eps, table_bytes, E2, stats);
-        case 7: return pt2_run<7, false>(ctx, C, E0, eps, table_bytes, E2, stats);
-        default: return pt2_run<8, false>(ctx, C, E0, eps, table_bytes, E2, stats);
-    }
+    return ctx->nwords == 2 ? enpt2_dispatch<2>(ctx, C, nroots, E0, eps, table_bytes, E2, stats)
+                            : enpt2_dispatch<1>(ctx, C, nroots, E0, eps, table_bytes, E2, stats);
 }

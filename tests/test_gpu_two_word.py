@@ -133,8 +133,6 @@ def test_two_word_limits(gpu, sel2w):
     H = sci.Hamiltonian.from_workload(w)
     C = torch.from_numpy(np.ascontiguousarray(w.c[:, :1])).cuda()
     with pytest.raises(sci.SciError):            # one-word keys only
-        H.enpt2(C, [0.0])
-    with pytest.raises(sci.SciError):
         H.set_row_range(0, 100)
     with pytest.raises(sci.SciError):            # more than 64 spin-orbitals need two words
         sci.sci_set_determinants(H.ctx, np.ascontiguousarray(w.keys[:, 0]), w.M, 4, 4, 0)
@@ -201,4 +199,76 @@ def test_two_word_rdm12_and_grads(gpu):
     L = w.ints.chol
     ref = (Gr.reshape(n * n, n * n) @ L.reshape(L.shape[0], n * n).T).T.reshape(L.shape[0], n, n)
     assert np.abs(gL.cpu().numpy() - ref).max() < 1e-12 * np.abs(ref).max()
+    H.sync_status()
+
+
+def _enpt2_case(w, o, seed):
+    """Normalised random vectors, E0 one below the lowest diagonal element, the oracle's
+    E2 over Q (sciref_enpt2) and the members of P connected to another member.  E2[W] -
+    E2[P] = E2[Q] holds for any c and E0 (Eqs. PT2final, EW1, EP1)."""
+    rng = np.random.default_rng(seed)
+    C = rng.standard_normal((w.M, 2)) * (1.0 if not np.iscomplexobj(w.ints.h) else 1.0)
+    if np.iscomplexobj(w.ints.h):
+        C = C + 1j * rng.standard_normal((w.M, 2))
+    C /= np.linalg.norm(C, axis=0)
+    d = o.diagonal().real
+    E0 = np.array([d.min() - 1.0, d.min() - 2.0])
+    E2, n_ext = o.enpt2(C, E0)
+    n_conn = sum(1 for r in range(w.M) if len(o.connections(r)[0]) > 0)
+    return C, E0, E2, n_ext, n_conn
+
+
+def test_two_word_enpt2_real(gpu):
+    """ENPT2 on 40 orbitals (2 alpha + 1 beta electrons, 5,000 selected determinants; the
+    beta string crosses the word boundary): 128-bit hash keys by 16-byte CAS, the beta
+    batch code over 40 orbitals, H_II of the external determinants over both words; two
+    roots against the oracle's direct sum at 1e-10, the distinct count exact, and a small
+    table (many batches) giving the same sums."""
+    torch = gpu
+    w = W.selected_two_word(n=40, na=2, nb=1, M=5000)
+    o = Oracle.from_workload(w)
+    C, E0, E2, n_ext, n_conn = _enpt2_case(w, o, 11)
+    H = sci.Hamiltonian.from_workload(w)
+    Ct = torch.from_numpy(C).cuda()
+    e2w, e2p, e2q, st = H.enpt2(Ct, E0)
+    assert np.allclose(e2q, E2, rtol=1e-10, atol=0), (e2q, E2)
+    assert st["distinct_W"] == n_ext + n_conn
+    b = H.enpt2(Ct, E0, table_bytes=(1 << 12) * 32)
+    assert b[3]["batches"] > st["batches"] and b[3]["distinct_W"] == st["distinct_W"]
+    assert np.allclose(b[2], E2, rtol=1e-10, atol=0)
+    H.sync_status()
+
+
+def test_two_word_enpt2_spinors(gpu):
+    """Complex spinor ENPT2 on 72 spinors (3 electrons, HF and 600 random determinants):
+    the whole-string batch code over both words, complex numerators; two roots against the
+    oracle at 1e-10, the distinct count exact, and a small table giving the same sums."""
+    torch = gpu
+    import itertools
+    n, N = 72, 3
+    rng = np.random.default_rng(23)
+    ints = W.complex_integrals(rng, n, 5, 0.95)
+    allc = list(itertools.combinations(range(n), N))
+    pick = [allc[0]] + [allc[i] for i in rng.choice(np.arange(1, len(allc)), 600, replace=False)]
+    lo = np.array([sum(1 << p for p in c if p < 64) for c in pick], dtype=np.uint64)
+    hi = np.array([sum(1 << (p - 64) for p in c if p >= 64) for c in pick], dtype=np.uint64)
+    keys = W.sort_words(np.stack([lo, hi], axis=1))
+
+    class _W:
+        pass
+
+    w = _W()
+    w.M, w.ints, w.keys = len(keys), ints, keys
+    o = Oracle("spinors", n, ints.h, ints.eri(), keys)
+    C, E0, E2, n_ext, n_conn = _enpt2_case(w, o, 12)
+    H = sci.Hamiltonian()
+    H.set_integrals("spinors", ints.h, chol=ints.chol)
+    H.set_determinants(keys, N, -1)
+    Ct = torch.from_numpy(C).cuda()
+    e2w, e2p, e2q, st = H.enpt2(Ct, E0)
+    assert np.allclose(e2q, E2, rtol=1e-10, atol=0), (e2q, E2)
+    assert st["distinct_W"] == n_ext + n_conn
+    b = H.enpt2(Ct, E0, table_bytes=(1 << 15) * 48)
+    assert b[3]["batches"] > st["batches"] and b[3]["distinct_W"] == st["distinct_W"]
+    assert np.allclose(b[2], E2, rtol=1e-10, atol=0)
     H.sync_status()
