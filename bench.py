@@ -724,6 +724,22 @@ def two_word_bench(H, w, device, steps=10, warmup=3, M=2_000_000):
                             "cpu_baseline": cpu_baseline(w2, budget_s=6.0, one_thread_s=2.0)}
     del H3, C
     torch.cuda.empty_cache()
+    # ENPT2 on a 200k-determinant space of the same recipe (128-bit table keys), one
+    # normalised vector with its Rayleigh quotient as E0
+    w4 = W.selected_two_word(n=40, na=8, nb=8, M=200_000)
+    H4 = sci.Hamiltonian.from_workload(w4, device=device)
+    c = torch.from_numpy(np.ascontiguousarray(w4.c)).to(dev)
+    c = c / torch.linalg.vector_norm(c)
+    E0 = [float((c * H4.sigma(c)).sum())]
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    e2w, e2p, e2q, st = H4.enpt2(c, E0, table_bytes=16 << 30)
+    sec = time.perf_counter() - t
+    out["pt2_80so"] = {"workload": w4.name, "M": w4.M, "seconds": sec, "E0": E0[0], "E2_Q": float(e2q[0]),
+                       "batches": st["batches"], "distinct_W": st["distinct_W"],
+                       "generate_us": st["generate_us"], "evaluate_us": st["evaluate_us"]}
+    del H4, c
+    torch.cuda.empty_cache()
     return out
 
 

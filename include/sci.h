@@ -142,9 +142,9 @@ int sci_set_determinants(sci_ctx *ctx, const uint64_t *keys, int64_t M, int n_al
  * integers, Sec. 3.2), strictly ascending as unsigned (64 x nwords)-bit integers.  With
  * two words the bucket keys are 128-bit (sorted by two stable radix passes), and sigma
  * (every precision mode, deterministic mode included), the diagonal, pair counts, row
- * costs, the connection exports, the density matrices (sci_rdm12, sci_rdm_grads) and
- * ENPT2 (sci_enpt2) work as for one word; row ranges and batches need one-word keys
- * (SCI_ERR_ARG).  sci_set_integrals takes up to 64
+ * costs, the connection exports, row ranges (sci_set_row_range), the density matrices
+ * (sci_rdm12, sci_rdm_grads) and ENPT2 (sci_enpt2) work as for one word; batches need
+ * one-word keys (SCI_ERR_ARG).  sci_set_integrals takes up to 64
  * spatial orbitals or 128 spinors for these lists; sci_set_determinants (one word) returns
  * SCI_ERR_ARG when the orbitals do not fit one word.  Errors as sci_set_determinants. */
 int sci_set_determinants_w(sci_ctx *ctx, const uint64_t *keys, int nwords, int64_t M, int n_alpha,

@@ -321,17 +321,23 @@ extern "C" int sci_set_row_range(sci_ctx *ctx, int64_t row_begin, int64_t row_en
         return sci_fail(ctx, SCI_ERR_ARG, "row range outside [0, M]");
     if (ctx->det_nvec > 0 && !(row_begin == 0 && row_end == ctx->M))
         return sci_fail(ctx, SCI_ERR_STATE, "deterministic mode is on");
-    if (ctx->nwords != 1 && !(row_begin == 0 && row_end == ctx->M))
-        return sci_fail(ctx, SCI_ERR_ARG, "row ranges need one-word keys");
     SCI_CK(cudaSetDevice(ctx->device));
     SCI_CK(cudaStreamSynchronize(ctx->stream));  // no launch in flight reads the old tables
     sci_free_range(ctx);
     if (row_begin == 0 && row_end == ctx->M) return SCI_OK;  // the whole list: full tables
     int rc = narrow<false, uint32_t>(ctx, ctx->e2, ctx->e2_idx, ctx->e2_code, ctx->e2_pos, row_begin, row_end,
                                      ctx->r2_idx, ctx->r2_code, ctx->r2_pos, ctx->r2);
-    if (rc == SCI_OK)
-        rc = narrow<true, uint64_t>(ctx, ctx->e1, ctx->e1_idx, ctx->e1_S, ctx->e1_meta, row_begin, row_end,
-                                    ctx->r1_idx, ctx->r1_S, ctx->r1_meta, ctx->r1);
+    if (rc == SCI_OK) {
+        if (ctx->nwords == 2) {   // spectator strings of two words: 16 bytes per entry
+            ulonglong2 *o = nullptr;
+            rc = narrow<true, ulonglong2>(ctx, ctx->e1, ctx->e1_idx, reinterpret_cast<const ulonglong2 *>(ctx->e1_S),
+                                          ctx->e1_meta, row_begin, row_end, ctx->r1_idx, o, ctx->r1_meta, ctx->r1);
+            ctx->r1_S = reinterpret_cast<uint64_t *>(o);
+        } else {
+            rc = narrow<true, uint64_t>(ctx, ctx->e1, ctx->e1_idx, ctx->e1_S, ctx->e1_meta, row_begin, row_end,
+                                        ctx->r1_idx, ctx->r1_S, ctx->r1_meta, ctx->r1);
+        }
+    }
     unsigned long long *cnt = nullptr, h[2] = {0, 0};
     if (rc == SCI_OK) rc = sci_cuda_check(ctx, cudaMalloc(&cnt, 16), "range pair count");
     if (rc == SCI_OK) {

@@ -127,13 +127,39 @@ def test_two_word_spinors(gpu):
     assert M > 200
 
 
+def test_two_word_row_ranges(gpu, sel2w):
+    """Row ranges on two-word lists (range tables with 16-byte spectator strings): K = 3 and
+    5 cost-balanced ranges concatenate to the whole-list sigma (FP64 and paired FP32), the
+    rows outside a range stay untouched, and the range pair counts sum to the total."""
+    from paper_2501_18185_gb300.partition import balanced_ranges, row_weights
+    torch = gpu
+    w, o = sel2w
+    H = sci.Hamiltonian.from_workload(w)
+    C = torch.from_numpy(np.ascontiguousarray(w.c)).cuda()
+    for prec in (sci.SCI_PREC_F64, sci.SCI_PREC_F64_DS):
+        full = H.sigma(C, prec=prec).cpu().numpy()
+        for K in (3, 5):
+            ranges = balanced_ranges(row_weights(H.row_costs().cpu().numpy(), 28), K)
+            S = np.zeros_like(full)
+            pairs = 0
+            for b, e in ranges:
+                H.set_row_range(b, e)
+                St = torch.full(C.shape, 7.0, dtype=torch.float64, device="cuda")
+                H.sigma(C, out=St, prec=prec)
+                Sn = St.cpu().numpy()
+                assert (Sn[:b] == 7.0).all() and (Sn[e:] == 7.0).all()
+                S[b:e] = Sn[b:e]
+                pairs += H.info()["pairs"]
+            H.set_row_range(0, w.M)
+            assert _rel(S, full) < 1e-12
+            assert pairs == H.count_pairs()
+    H.sync_status()
+
+
 def test_two_word_limits(gpu, sel2w):
     torch = gpu
     w, _ = sel2w
     H = sci.Hamiltonian.from_workload(w)
-    C = torch.from_numpy(np.ascontiguousarray(w.c[:, :1])).cuda()
-    with pytest.raises(sci.SciError):            # one-word keys only
-        H.set_row_range(0, 100)
     with pytest.raises(sci.SciError):            # more than 64 spin-orbitals need two words
         sci.sci_set_determinants(H.ctx, np.ascontiguousarray(w.keys[:, 0]), w.M, 4, 4, 0)
     bad = w.keys.copy()
