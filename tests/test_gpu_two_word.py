@@ -298,3 +298,30 @@ def test_two_word_enpt2_spinors(gpu):
     assert b[3]["batches"] > st["batches"] and b[3]["distinct_W"] == st["distinct_W"]
     assert np.allclose(b[2], E2, rtol=1e-10, atol=0)
     H.sync_status()
+
+
+def test_two_word_edge_cases(gpu):
+    """An empty two-word list, and one determinant: sigma is H_II c (no pairs), ENPT2 and
+    the density matrices run."""
+    torch = gpu
+    n = 40
+    ints = W.real_integrals(np.random.default_rng(71), n, 4, 0.95)
+    H = sci.Hamiltonian()
+    H.set_integrals("spin_orbitals", ints.h, chol=ints.chol)
+    H.set_determinants(np.zeros((0, 2), dtype=np.uint64), 1, 1)
+    S = H.sigma(torch.zeros((0, 1), dtype=torch.float64, device="cuda"))
+    assert S.shape[0] == 0 and H.count_pairs() == 0
+    one = W.two_word_keys(np.array([1], dtype=np.uint64), np.array([1 << 30], dtype=np.uint64), n)  # beta bit 70
+    H.set_determinants(one, 1, 1)
+    o = Oracle("spin_orbitals", n, ints.h, ints.eri(), one)
+    c = torch.tensor([[0.5]], dtype=torch.float64, device="cuda")
+    S = H.sigma(c).cpu().numpy()
+    d = o.diagonal()
+    assert H.count_pairs() == 0 and abs(S[0, 0] - 0.5 * d[0]) < 1e-12 * abs(d[0])
+    E2, nx = o.enpt2(np.array([[1.0]]), [d[0].real - 1.0])
+    e2w, e2p, e2q, st = H.enpt2(torch.tensor([[1.0]], dtype=torch.float64, device="cuda"), [d[0].real - 1.0])
+    assert np.allclose(e2q, E2, rtol=1e-10, atol=0) and st["distinct_W"] == nx + 0
+    g1, g2 = H.rdm12(torch.tensor([[1.0]], dtype=torch.float64, device="cuda"))
+    r1, r2 = o.rdm12(np.array([1.0]))
+    assert np.abs(g1.cpu().numpy() - r1).max() < 1e-14 and np.abs(g2.cpu().numpy() - r2).max() < 1e-14
+    H.sync_status()
