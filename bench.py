@@ -89,7 +89,7 @@ def split_throughput(pairs_per_step: int, steps: int, total_ms: float) -> float:
 
 
 def measured_peaks() -> dict:
-    """The generated peaks of this GPU pool ({} when the file is absent)."""
+    """The measured copy-bandwidth and GEMM peaks of MEASURED_PEAKS.json ({} when the file is absent)."""
     try:
         return json.load(open(PEAKS))
     except (OSError, ValueError):
