@@ -183,6 +183,27 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it (model name, or the Arm implementer and part
+    numbers when there is no model name)."""
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return "unknown"
+    for key in ("model name", "Model name"):
+        for ln in info:
+            if ln.startswith(key):
+                return ln.split(":", 1)[1].strip()
+    fields = {}
+    for ln in info:
+        if ":" in ln:
+            k, v = (x.strip() for x in ln.split(":", 1))
+            fields.setdefault(k, v)
+    if "CPU implementer" in fields:
+        return f"implementer {fields['CPU implementer']} part {fields.get('CPU part', '?')}"
+    return "unknown"
+
+
 def cpu_baseline(w, budget_s: float = 12.0, seed: int = 0, one_thread_s: float = 5.0):
     """Time the CPU oracle, as it stands, on a bounded random sample of rows: on all the
     host's cores (the reported value) and on one thread (`one_thread`)."""
@@ -212,7 +233,7 @@ def cpu_baseline(w, budget_s: float = 12.0, seed: int = 0, one_thread_s: float =
 
     v, smp = sample(cores, budget_s)
     v1, smp1 = sample(1, one_thread_s)
-    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": smp,
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": smp, "cpu": cpu_model(),
             "one_thread": {"value": v1, "unit": UNIT, "cores": 1, "sample": smp1}}
 
 
@@ -889,7 +910,7 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64" if not w.ints.complex_ else "c128",
             "data": "synthetic", "config": {"workload": w.name, "nvec": w.c.shape[1], "rows_per_step": int(nrows)},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} x {nrows} random rows of {w.M}"},
+                             "sample": f"{args.steps} x {nrows} random rows of {w.M}", "cpu": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
