@@ -47,9 +47,12 @@
 
 typedef double complex zd;
 
-/* An occupation string of up to 128 spin-orbitals or spinors: bit p is orbital p (a GCC
- * 128-bit integer; determinants of up to 64 orbitals use its low word only). */
-typedef unsigned __int128 bits_t;
+/* An occupation string of up to 192 spin-orbitals or spinors: orbital p is bit p % 64 of
+ * word p / 64 (determinants of up to 64 orbitals use word 0 only).  Strings compare as
+ * unsigned 192-bit integers, word 2 most significant. */
+#define SCIREF_WORDS 3
+#define SCIREF_MAXORB (64 * SCIREF_WORDS)
+typedef struct { uint64_t w[SCIREF_WORDS]; } bits_t;
 
 typedef struct sciref_ctx {
     int is_complex;   /* 0: real FP64 scalars, 1: complex128 scalars */
@@ -79,7 +82,7 @@ int sciref_create(sciref_ctx **out, int is_complex, int spinors, int n,
                   const double *h, const double *eri)
 {
     if (!out || !h || !eri || n <= 0) return SCIREF_ERR_ARG;
-    if (spinors ? n > 128 : n > 64) return SCIREF_ERR_ARG;
+    if (spinors ? n > SCIREF_MAXORB : 2 * n > SCIREF_MAXORB) return SCIREF_ERR_ARG;
     sciref_ctx *c = (sciref_ctx *)calloc(1, sizeof(sciref_ctx));
     c->is_complex = is_complex;
     c->spinors = spinors;
@@ -120,16 +123,17 @@ void sciref_destroy(sciref_ctx *c)
     free(c);
 }
 
-/* keys: M strings of nwords (1 or 2) 64-bit words each, word 0 holding orbitals 0..63;
+static int key_cmp(bits_t a, bits_t b);
+
+/* keys: M strings of nwords (1 to 3) 64-bit words each, word 0 holding orbitals 0..63;
  * the list must be strictly ascending as unsigned (64 x nwords)-bit integers. */
 int sciref_set_determinants_w(sciref_ctx *c, const uint64_t *keys, int nwords, int64_t M)
 {
-    if (!c || (M > 0 && !keys) || M < 0 || nwords < 1 || nwords > 2) return SCIREF_ERR_ARG;
-    bits_t *k = (bits_t *)malloc((size_t)(M > 0 ? M : 1) * sizeof(bits_t));
+    if (!c || (M > 0 && !keys) || M < 0 || nwords < 1 || nwords > SCIREF_WORDS) return SCIREF_ERR_ARG;
+    bits_t *k = (bits_t *)calloc((size_t)(M > 0 ? M : 1), sizeof(bits_t));
     for (int64_t i = 0; i < M; i++) {
-        k[i] = (bits_t)keys[i * nwords];
-        if (nwords == 2) k[i] |= (bits_t)keys[i * nwords + 1] << 64;
-        if (i > 0 && !(k[i - 1] < k[i])) { free(k); return SCIREF_ERR_UNSORTED; }
+        for (int t = 0; t < nwords; t++) k[i].w[t] = keys[i * nwords + t];
+        if (i > 0 && key_cmp(k[i - 1], k[i]) >= 0) { free(k); return SCIREF_ERR_UNSORTED; }
     }
     free(c->keys);
     c->keys = k;
@@ -154,8 +158,17 @@ int sciref_set_threads(int n)
 }
 
 /* ------------------------------------------------------------------ helpers */
-static int occupied(bits_t d, int p) { return (int)((d >> p) & 1u); }
-static bits_t bit(int p) { return (bits_t)1 << p; }
+static int occupied(bits_t d, int p) { return (int)((d.w[p >> 6] >> (p & 63)) & 1u); }
+static bits_t with_bit(bits_t d, int p) { d.w[p >> 6] |= 1ull << (p & 63); return d; }
+static bits_t without_bit(bits_t d, int p) { d.w[p >> 6] &= ~(1ull << (p & 63)); return d; }
+/* -1, 0, +1 as unsigned 192-bit integers */
+static int key_cmp(bits_t a, bits_t b)
+{
+    for (int t = SCIREF_WORDS - 1; t >= 0; t--)
+        if (a.w[t] != b.w[t]) return a.w[t] < b.w[t] ? -1 : 1;
+    return 0;
+}
+static int key_eq(bits_t a, bits_t b) { return key_cmp(a, b) == 0; }
 
 /* number of occupied orbitals strictly below p, counted one bit at a time */
 static int count_below(bits_t d, int p)
@@ -170,7 +183,7 @@ static int annihilate(bits_t *d, int p)
 {
     if (!occupied(*d, p)) return 0;
     int s = (count_below(*d, p) & 1) ? -1 : 1;
-    *d &= ~bit(p);
+    *d = without_bit(*d, p);
     return s;
 }
 
@@ -179,14 +192,14 @@ static int create(bits_t *d, int p)
 {
     if (occupied(*d, p)) return 0;
     int s = (count_below(*d, p) & 1) ? -1 : 1;
-    *d |= bit(p);
+    *d = with_bit(*d, p);
     return s;
 }
 
 static int n_diff(bits_t a, bits_t b)
 {
     int cnt = 0;
-    for (int p = 0; p < 128; p++) cnt += occupied(a, p) != occupied(b, p);
+    for (int p = 0; p < SCIREF_MAXORB; p++) cnt += occupied(a, p) != occupied(b, p);
     return cnt;
 }
 
@@ -195,9 +208,9 @@ static int64_t find_key(const sciref_ctx *c, bits_t k)
     int64_t lo = 0, hi = c->M;          /* first index with keys[idx] >= k */
     while (lo < hi) {
         int64_t mid = lo + (hi - lo) / 2;
-        if (c->keys[mid] < k) lo = mid + 1; else hi = mid;
+        if (key_cmp(c->keys[mid], k) < 0) lo = mid + 1; else hi = mid;
     }
-    return (lo < c->M && c->keys[lo] == k) ? lo : -1;
+    return (lo < c->M && key_eq(c->keys[lo], k)) ? lo : -1;
 }
 
 /* <D_I|H|D_I> */
@@ -224,7 +237,7 @@ static zd offdiag_element(const sciref_ctx *c, bits_t bra, bits_t ket, int *degr
     *sign = 0;
     if (nd != 2 && nd != 4) return 0;
     int from[2], to[2], nf = 0, nt = 0;        /* from: in ket only; to: in bra only */
-    for (int p = 0; p < 128; p++) {
+    for (int p = 0; p < SCIREF_MAXORB; p++) {
         if (occupied(ket, p) && !occupied(bra, p)) from[nf++] = p;
         if (occupied(bra, p) && !occupied(ket, p)) to[nt++] = p;
     }
@@ -262,7 +275,7 @@ static int cmp_conn(const void *x, const void *y)
 static int64_t row_connections(const sciref_ctx *c, int64_t row, conn_t **out)
 {
     bits_t d = c->keys[row];
-    int occ[128], vir[128], no = 0, nv = 0;
+    int occ[SCIREF_MAXORB], vir[SCIREF_MAXORB], no = 0, nv = 0;
     for (int p = 0; p < c->norb; p++) {
         if (occupied(d, p)) occ[no++] = p; else vir[nv++] = p;
     }
@@ -273,7 +286,7 @@ static int64_t row_connections(const sciref_ctx *c, int64_t row, conn_t **out)
         for (int y = 0; y < nv; y++) {
             int i = occ[x], a = vir[y];
             if (spin_of(c, i) != spin_of(c, a)) continue;
-            bits_t e = (d & ~bit(i)) | bit(a);
+            bits_t e = with_bit(without_bit(d, i), a);
             int64_t J = find_key(c, e);
             if (J < 0) continue;
             if (cnt == cap) { cap *= 2; list = (conn_t *)realloc(list, cap * sizeof(conn_t)); }
@@ -289,8 +302,7 @@ static int64_t row_connections(const sciref_ctx *c, int64_t row, conn_t **out)
                 for (int y2 = y1 + 1; y2 < nv; y2++) {
                     int i = occ[x1], j = occ[x2], a = vir[y1], b = vir[y2];
                     if (spin_of(c, i) + spin_of(c, j) != spin_of(c, a) + spin_of(c, b)) continue;
-                    bits_t e = d & ~bit(i) & ~bit(j);
-                    e |= bit(a) | bit(b);
+                    bits_t e = with_bit(with_bit(without_bit(without_bit(d, i), j), a), b);
                     int64_t J = find_key(c, e);
                     if (J < 0) continue;
                     if (cnt == cap) { cap *= 2; list = (conn_t *)realloc(list, cap * sizeof(conn_t)); }
@@ -322,9 +334,10 @@ int sciref_diagonal(const sciref_ctx *c, double *out)
 int sciref_hij(const sciref_ctx *c, uint64_t bra, uint64_t ket, double *out)
 {
     if (!c || !out) return SCIREF_ERR_ARG;
+    bits_t b = {{bra, 0, 0}}, k = {{ket, 0, 0}};
     zd v;
-    if (bra == ket) v = diag_element(c, bra);
-    else { int deg, sg; v = offdiag_element(c, bra, ket, &deg, &sg); }
+    if (bra == ket) v = diag_element(c, b);
+    else { int deg, sg; v = offdiag_element(c, b, k, &deg, &sg); }
     out[0] = creal(v);
     if (c->is_complex) out[1] = cimag(v);
     return SCIREF_OK;
@@ -508,7 +521,7 @@ static int two_body_sign(bits_t bra, bits_t ket, int p, int q, int r, int s)
     sg *= create(&d, r);
     if (!sg) return 0;
     sg *= create(&d, p);
-    if (!sg || d != bra) return 0;
+    if (!sg || !key_eq(d, bra)) return 0;
     return sg;
 }
 
@@ -518,7 +531,7 @@ static int one_body_sign(bits_t bra, bits_t ket, int p, int q)
     int sg = annihilate(&d, q);
     if (!sg) return 0;
     sg *= create(&d, p);
-    if (!sg || d != bra) return 0;
+    if (!sg || !key_eq(d, bra)) return 0;
     return sg;
 }
 
@@ -552,7 +565,7 @@ int sciref_rdm12(const sciref_ctx *c, const double *C, double *g1, double *g2)
     memset(g2, 0, m * m * m * m * (z ? 2 : 1) * sizeof(double));
 #pragma omp parallel
     {
-        const int maxc = 2 * 128 * 128;  /* candidate operator strings per pair */
+        const int maxc = 2 * SCIREF_MAXORB * SCIREF_MAXORB;  /* candidate operator strings per pair */
         int *cq = (int *)malloc(4 * sizeof(int) * maxc);
         int *cs = cq + maxc, *cp = cs + maxc, *cr = cp + maxc;
 #pragma omp for schedule(dynamic, 8)
@@ -565,7 +578,7 @@ int sciref_rdm12(const sciref_ctx *c, const double *C, double *g1, double *g2)
                 const int64_t col = t < 0 ? row : list[t].j;
                 const bits_t ket = c->keys[col];
                 const zd w = cI * (z ? CMPLX(C[2 * col], C[2 * col + 1]) : CMPLX(C[col], 0.0));
-                int occ[128], no = 0, from[2], to[2], nf = 0, nt = 0;
+                int occ[SCIREF_MAXORB], no = 0, from[2], to[2], nf = 0, nt = 0;
                 for (int p = 0; p < c->norb; p++) {
                     if (occupied(ket, p)) occ[no++] = p;
                     if (occupied(ket, p) && !occupied(bra, p)) from[nf++] = p;
@@ -652,7 +665,8 @@ typedef struct { bits_t key; uint64_t j; } ext_pair;
 static int cmp_ext(const void *x, const void *y)
 {
     const ext_pair *a = (const ext_pair *)x, *b = (const ext_pair *)y;
-    if (a->key != b->key) return (a->key > b->key) - (a->key < b->key);
+    const int k = key_cmp(a->key, b->key);
+    if (k) return k;
     return (a->j > b->j) - (a->j < b->j);
 }
 
@@ -661,7 +675,7 @@ static int cmp_ext(const void *x, const void *y)
 static int64_t external_excitations(const sciref_ctx *c, int64_t j, ext_pair *out, int keep_members)
 {
     bits_t d = c->keys[j];
-    int occ[128], vir[128], no = 0, nv = 0;
+    int occ[SCIREF_MAXORB], vir[SCIREF_MAXORB], no = 0, nv = 0;
     for (int p = 0; p < c->norb; p++) {
         if (occupied(d, p)) occ[no++] = p; else vir[nv++] = p;
     }
@@ -670,7 +684,7 @@ static int64_t external_excitations(const sciref_ctx *c, int64_t j, ext_pair *ou
         for (int y = 0; y < nv; y++) {
             int i = occ[x], a = vir[y];
             if (spin_of(c, i) != spin_of(c, a)) continue;
-            bits_t e = (d & ~bit(i)) | bit(a);
+            bits_t e = with_bit(without_bit(d, i), a);
             if (!keep_members && find_key(c, e) >= 0) continue;
             if (out) { out[cnt].key = e; out[cnt].j = (uint64_t)j; }
             cnt++;
@@ -681,8 +695,7 @@ static int64_t external_excitations(const sciref_ctx *c, int64_t j, ext_pair *ou
                 for (int y2 = y1 + 1; y2 < nv; y2++) {
                     int i = occ[x1], jj = occ[x2], a = vir[y1], b = vir[y2];
                     if (spin_of(c, i) + spin_of(c, jj) != spin_of(c, a) + spin_of(c, b)) continue;
-                    bits_t e = d & ~bit(i) & ~bit(jj);
-                    e |= bit(a) | bit(b);
+                    bits_t e = with_bit(with_bit(without_bit(without_bit(d, i), jj), a), b);
                     if (!keep_members && find_key(c, e) >= 0) continue;
                     if (out) { out[cnt].key = e; out[cnt].j = (uint64_t)j; }
                     cnt++;
@@ -693,7 +706,7 @@ static int64_t external_excitations(const sciref_ctx *c, int64_t j, ext_pair *ou
 #define ENPT2_BINS 256
 static unsigned enpt2_bin(bits_t key)
 {
-    const uint64_t folded = (uint64_t)key ^ (uint64_t)(key >> 64) * 0xC2B2AE3D27D4EB4Full;
+    const uint64_t folded = key.w[0] ^ key.w[1] * 0xC2B2AE3D27D4EB4Full ^ key.w[2] * 0x165667B19E3779F9ull;
     return (unsigned)((folded * 0x9E3779B97F4A7C15ull) >> 56);
 }
 
@@ -736,7 +749,7 @@ int sciref_enpt2(const sciref_ctx *c, const double *C, int nroots, const double 
         zd *num = (zd *)malloc((size_t)nroots * sizeof(zd));
         for (int64_t s = 0; s < nb;) {
             int64_t e = s;
-            while (e < nb && v[e].key == v[s].key) e++;
+            while (e < nb && key_eq(v[e].key, v[s].key)) e++;
             const bits_t ext = v[s].key;
             for (int k = 0; k < nroots; k++) num[k] = 0;
             int kept = 0;
