@@ -666,14 +666,15 @@ def spinor_bench(device, steps=10, warmup=3):
 
 
 def two_word_bench(H, w, device, steps=10, warmup=3, M=2_000_000):
-    """Occupation strings of more than 64 spin-orbitals (two 64-bit words per key).
-    (1) The bench space given as [M, 2] keys with a zero high word: the same pairs through
-    the two-word set-up and singles code, against the one-word sigma of `H`.  (2) A
-    selected space of 40 spatial orbitals (80 spin-orbitals, 8 alpha + 8 beta electrons:
-    HF, all singles and doubles, seeded random triples up to M): FP64 sigma on one vector,
-    CUDA-event milliseconds (L2 flushed), the doubles kernel's algorithmic-byte fraction of
-    HBM and useful FMAs against the measured FP64 pipe rate, and the oracle (128-bit keys)
-    on sampled rows."""
+    """Occupation strings of more than 64 spin-orbitals (two or three 64-bit words per
+    key).  (1) The bench space given as [M, 2] and [M, 3] keys with zero upper words: the
+    same pairs through the multi-word set-up and singles code, against the one-word sigma
+    of `H`.  (2) A selected space of 40 spatial orbitals (80 spin-orbitals, 8 alpha + 8
+    beta electrons: HF, all singles and doubles, seeded random triples up to M) and (3) one
+    of 70 spatial orbitals (140 spin-orbitals, 4 + 4 electrons, three words): FP64 sigma on
+    one vector, CUDA-event milliseconds (L2 flushed), the doubles kernel's algorithmic-byte
+    fraction of HBM and useful FMAs against the measured FP64 pipe rate, and the oracle
+    on sampled rows.  (4) ENPT2 on a 200k cut of the 80 spin-orbital recipe."""
     import torch
 
     from paper_2501_18185_gb300 import sci
@@ -721,7 +722,23 @@ def two_word_bench(H, w, device, steps=10, warmup=3, M=2_000_000):
     out["same_space_two_words"] = {"workload": w.name, "one_word_ms": ms1, "two_word_ms": ms2,
                                    "one_word_kernel_ms": k1, "two_word_kernel_ms": k2,
                                    "two_word_setup_s": round(setup2, 3), "rel_diff": rel}
-    del H2, S1, S2, C
+    del H2, S2
+    torch.cuda.empty_cache()
+    keys3 = np.zeros((w.M, 3), dtype=np.uint64)
+    keys3[:, 0] = w.keys
+    t = time.perf_counter()
+    H2 = sci.Hamiltonian(device, stream)
+    H2.set_integrals(w.mode, w.ints.h, chol=w.ints.chol)
+    H2.set_determinants(keys3, w.n_alpha, w.n_beta)
+    torch.cuda.synchronize()
+    setup3w = time.perf_counter() - t
+    if H2.count_pairs() != H.count_pairs():
+        raise SystemExit("three-word pair count differs from the one-word count")
+    S3, ms3w, k3w = timed(H2, C)
+    out["same_space_three_words"] = {"workload": w.name, "one_word_ms": ms1, "three_word_ms": ms3w,
+                                     "three_word_kernel_ms": k3w, "three_word_setup_s": round(setup3w, 3),
+                                     "rel_diff": float(torch.linalg.norm(S3 - S1) / torch.linalg.norm(S1))}
+    del H2, S1, S3, C
     torch.cuda.empty_cache()
 
     w2 = W.selected_two_word(n=40, na=8, nb=8, M=M)
@@ -743,6 +760,27 @@ def two_word_bench(H, w, device, steps=10, warmup=3, M=2_000_000):
                             "fp64_pipe_frac": fma / pp["fp64_fma_per_s"],
                             "l2": "flushed between timed steps (256 MB write)",
                             "cpu_baseline": cpu_baseline(w2, budget_s=6.0, one_thread_s=2.0)}
+    del H3, C
+    torch.cuda.empty_cache()
+    # three words: 70 spatial orbitals (140 spin-orbitals; alpha across words 0/1, beta
+    # across words 1/2), 4 alpha + 4 beta electrons, the same recipe
+    w3 = W.selected_three_word(n=70, na=4, nb=4, M=M)
+    t = time.perf_counter()
+    H3 = sci.Hamiltonian.from_workload(w3, device=device)
+    torch.cuda.synchronize()
+    setup3 = time.perf_counter() - t
+    info = H3.info()
+    C = torch.from_numpy(np.ascontiguousarray(w3.c)).to(dev)
+    _, ms3, k3 = timed(H3, C)
+    achieved = info["pairs_doubles"] * 16 / (k3["doubles"] / 1e3) / 1e9
+    fma = info["pairs_doubles"] / (k3["doubles"] / 1e3)
+    out["selected_140so"] = {"workload": w3.name, "M": w3.M, "pairs_per_step": info["pairs"],
+                             "pairs_doubles": info["pairs_doubles"], "setup_s": round(setup3, 3),
+                             "ms_per_step": ms3, "pairs_per_s": info["pairs"] / (ms3 / 1e3), "kernel_ms": k3,
+                             "doubles_alg_GBps": achieved, "doubles_alg_frac_hbm": achieved / peak,
+                             "fp64_pipe_frac": fma / pp["fp64_fma_per_s"],
+                             "l2": "flushed between timed steps (256 MB write)",
+                             "cpu_baseline": cpu_baseline(w3, budget_s=6.0, one_thread_s=2.0)}
     del H3, C
     torch.cuda.empty_cache()
     # ENPT2 on a 200k-determinant space of the same recipe (128-bit table keys), one

@@ -99,9 +99,10 @@ int sci_destroy(sci_ctx *ctx);
 int sci_set_stream(sci_ctx *ctx, void *cuda_stream);
 
 /* Load the Hamiltonian (Sec. 2.1, Eq. Hamiltonian; Sec. 3.2, IntegralManager).
- *   scalar: SCI_REAL64 or SCI_COMPLEX128.  mode: SCI_SPIN_ORBITALS (n <= 64 spatial
- *   orbitals, real only) or SCI_SPINORS (n <= 128 spinors); above 32 spatial orbitals or
- *   64 spinors the determinant list needs two-word keys (sci_set_determinants_w).
+ *   scalar: SCI_REAL64 or SCI_COMPLEX128.  mode: SCI_SPIN_ORBITALS (n <= 96 spatial
+ *   orbitals, real only) or SCI_SPINORS (n <= 192 spinors); above 32 spatial orbitals or
+ *   64 spinors the determinant list needs two-word keys, above 64 or 128 three-word keys
+ *   (sci_set_determinants_w).
  *   h:    host, n*n row-major, h[p*n+q] = h_pq, Hermitian (complex: interleaved re,im).
  *   eri:  host, n^4 row-major, eri[((p*n+q)*n+r)*n+s] = (pq|rs), or NULL.
  *   chol: host, naux*n*n, (pq|rs) = sum_P chol[P][p][q] chol[P][r][s], or NULL.
@@ -136,16 +137,17 @@ int sci_set_integrals_ex(sci_ctx *ctx, int scalar, int mode, int n, const void *
 int sci_set_determinants(sci_ctx *ctx, const uint64_t *keys, int64_t M, int n_alpha,
                          int n_beta, int keys_on_device);
 
-/* The same for occupation strings of more than 64 spin-orbitals or spinors (up to 128):
- * keys are M strings of nwords (1 or 2) 64-bit words, word 0 holding orbitals 0..63 and
- * word 1 orbitals 64..127 (the paper keeps an orbital configuration as an array of 64-bit
- * integers, Sec. 3.2), strictly ascending as unsigned (64 x nwords)-bit integers.  With
- * two words the bucket keys are 128-bit (sorted by two stable radix passes), and sigma
- * (every precision mode, deterministic mode included), the diagonal, pair counts, row
- * costs, the connection exports, row ranges (sci_set_row_range), the density matrices
- * (sci_rdm12, sci_rdm_grads) and ENPT2 (sci_enpt2) work as for one word; batches need
- * one-word keys (SCI_ERR_ARG).  sci_set_integrals takes up to 64
- * spatial orbitals or 128 spinors for these lists; sci_set_determinants (one word) returns
+/* The same for occupation strings of more than 64 spin-orbitals or spinors (up to 192):
+ * keys are M strings of nwords (1, 2 or 3) 64-bit words, word w holding orbitals
+ * 64w..64w+63 (the paper keeps an orbital configuration as an array of 64-bit integers,
+ * Sec. 3.2), strictly ascending as unsigned (64 x nwords)-bit integers; nwords must cover
+ * the orbitals (64 nwords >= 2n, or >= n spinors; SCI_ERR_ARG otherwise).  The bucket keys
+ * are then (64 x nwords)-bit, sorted by nwords stable radix passes.  Sigma (every precision
+ * mode, deterministic mode included), the diagonal, pair counts, row costs, the connection
+ * exports and row ranges (sci_set_row_range) work on two- and three-word lists as on one
+ * word; the density matrices (sci_rdm12, sci_rdm_grads) and ENPT2 (sci_enpt2) take one-
+ * and two-word lists (up to 128 spin-orbitals or spinors; SCI_ERR_ARG for three words);
+ * batches need one-word keys (SCI_ERR_ARG).  sci_set_determinants (one word) returns
  * SCI_ERR_ARG when the orbitals do not fit one word.  Errors as sci_set_determinants. */
 int sci_set_determinants_w(sci_ctx *ctx, const uint64_t *keys, int nwords, int64_t M, int n_alpha,
                            int n_beta, int keys_on_device);

@@ -114,19 +114,19 @@ __device__ void tile_singles(const Inst &B, int64_t a, const double *C, double *
     if (p >= B.e1) return;
     const int norb = B.norb;
     const uint32_t meta = B.e1_meta[p];
-    const int x = (int)(meta & 0x7F);
-    const bool par = (meta >> 7) & 1;
-    const int64_t bs = p - (int64_t)((meta >> 8) & 0xFFF), be = bs + (int64_t)(meta >> 20);
+    const int x = sci::meta_x(meta);
+    const bool par = sci::meta_par(meta);
+    const int64_t bs = p - (int64_t)sci::meta_off(meta), be = bs + (int64_t)sci::meta_size(meta);
     const uint64_t Sk = B.e1_S[p], part = Sk & ~B.ref, holes = B.ref & ~Sk;
     double acc = 0.0;
     for (int64_t q = bs; q < be; q++) {
         if (q == p) continue;
         const uint32_t mq = B.e1_meta[q];
-        const int y = (int)(mq & 0x7F);
+        const int y = sci::meta_x(mq);
         double f = __ldg(B.fref + y * norb + x);
         for (uint64_t m = part; m; m &= m - 1) f += __ldg(B.g_so + ((int64_t)(__ffsll((long long)m) - 1) * norb + y) * norb + x);
         for (uint64_t m = holes; m; m &= m - 1) f -= __ldg(B.g_so + ((int64_t)(__ffsll((long long)m) - 1) * norb + y) * norb + x);
-        acc = fma(f, sflip((mq >> 7) & 1, C[B.off + B.e1_idx[q]]), acc);
+        acc = fma(f, sflip(sci::meta_par(mq), C[B.off + B.e1_idx[q]]), acc);
     }
     atomicAdd(S + B.off + B.e1_idx[p], sflip(par, acc));
 }

@@ -63,10 +63,18 @@ __host__ __device__ __forceinline__ uint32_t make_code(int x, int y, int par, in
 }
 __host__ __device__ __forceinline__ int pos_off(uint32_t p) { return (int)(p & 0xFFFFu); }
 __host__ __device__ __forceinline__ int pos_size(uint32_t p) { return (int)(p >> 16); }
-__host__ __device__ __forceinline__ uint64_t code_mask(uint32_t c)
+// fields of an (N-1)-table meta word: the member's extra orbital x (8 bits, up to 255
+// orbitals), the parity of its position, its offset in the bucket (11 bits) and the bucket
+// size (12 bits)
+__host__ __device__ __forceinline__ int meta_x(uint32_t m) { return (int)(m & 0xFFu); }
+__host__ __device__ __forceinline__ bool meta_par(uint32_t m) { return (m >> 8) & 1u; }
+__host__ __device__ __forceinline__ int meta_off(uint32_t m) { return (int)((m >> 9) & 0x7FFu); }
+__host__ __device__ __forceinline__ int meta_size(uint32_t m) { return (int)(m >> 20); }
+__host__ __device__ __forceinline__ uint32_t make_meta(int x, int par, int off, int size)
 {
-    return (1ull << code_x(c)) | (1ull << code_y(c));
+    return (uint32_t)x | ((uint32_t)par << 8) | ((uint32_t)off << 9) | ((uint32_t)size << 20);
 }
+constexpr int kMaxBucket1 = 2047;   // the largest (N-1) bucket the meta word holds
 // whether two members of a bucket share an extra orbital (then they are a single
 // excitation of each other, not a double); valid for orbitals up to 255
 __host__ __device__ __forceinline__ bool codes_overlap(uint32_t a, uint32_t b)
@@ -141,6 +149,7 @@ struct sci_ctx {
     int na = 0, nb = 0, N = 0;
     uint64_t ref = 0;       // the reference (lowest orbitals), bits 0..63
     uint64_t ref_hi = 0;    // its bits 64..127 (two-word lists)
+    uint64_t ref_w2 = 0;    // its bits 128..191 (three-word lists)
     int nwords = 1;         // 64-bit words per key: 1, or 2 for more than 64 spin-orbitals
     uint64_t *keys = nullptr;  // [M][nwords], word 0 holding orbitals 0..63
     double *hdiag = nullptr;

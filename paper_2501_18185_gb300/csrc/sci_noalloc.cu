@@ -90,11 +90,11 @@ __global__ void k_conn1_noalloc(const uint32_t *__restrict__ e_idx, const uint32
         int64_t I = e_idx[p];
         if (I < rb || I >= re) continue;
         uint32_t meta = e_meta[p];
-        int64_t bs = p - (int64_t)((meta >> 8) & 0xFFF), be = bs + (int64_t)(meta >> 20);
-        int par = (meta >> 7) & 1;
+        int64_t bs = p - (int64_t)sci::meta_off(meta), be = bs + (int64_t)sci::meta_size(meta);
+        int par = sci::meta_par(meta);
         for (int64_t q = bs; q < be; q++) {
             if (q == p) continue;
-            put(s, (uint32_t)I, e_idx[q], 0, par ^ (int)((e_meta[q] >> 7) & 1));
+            put(s, (uint32_t)I, e_idx[q], 0, par ^ (int)sci::meta_par(e_meta[q]));
         }
     }
 }

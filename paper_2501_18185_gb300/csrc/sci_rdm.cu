@@ -159,10 +159,10 @@ k_rdm_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t meta = e_meta[p];
-        const int x = (int)(meta & 0x7F);
-        const bool par = (meta >> 7) & 1;
-        const int64_t bs = p - (int64_t)((meta >> 8) & 0xFFF);
-        const int64_t be = bs + (int64_t)(meta >> 20);
+        const int x = sci::meta_x(meta);
+        const bool par = sci::meta_par(meta);
+        const int64_t bs = p - (int64_t)sci::meta_off(meta);
+        const int64_t be = bs + (int64_t)sci::meta_size(meta);
         // the spectator string's orbitals outside (part) and missing from (holes) the
         // reference, per word
         uint64_t part[KW], holes[KW];
@@ -178,8 +178,8 @@ k_rdm_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e
         for (int64_t q = bs; q < be; q++) {
             if (q == p) continue;
             const uint32_t mq = e_meta[q];
-            const int y = (int)(mq & 0x7F);
-            const bool parq = (mq >> 7) & 1;
+            const int y = sci::meta_x(mq);
+            const bool parq = sci::meta_par(mq);
             const int64_t idxq = e_idx[q];
             TC w;
             zero(w);

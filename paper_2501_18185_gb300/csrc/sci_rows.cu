@@ -54,7 +54,7 @@ int grid_for(int64_t n)
 __device__ __forceinline__ int64_t start2(const uint32_t *e_pos, int64_t p) { return p - sci::pos_off(e_pos[p]); }
 __device__ __forceinline__ int64_t start1(const uint32_t *e_meta, int64_t p)
 {
-    return p - (int64_t)((e_meta[p] >> 8) & 0xFFF);
+    return p - (int64_t)sci::meta_off(e_meta[p]);
 }
 
 // mark[bucket start] = 1 for every bucket with a member in [rb, re)
@@ -117,7 +117,7 @@ __global__ void k_range_count1(const uint32_t *__restrict__ e_idx, const uint32_
     unsigned long long cnt = 0;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t I = e_idx[p];
-        if (I >= rb && I < re) cnt += (e_meta[p] >> 20) - 1;
+        if (I >= rb && I < re) cnt += sci::meta_size(e_meta[p]) - 1;
     }
     for (int o = 16; o; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
     if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(out, cnt);
@@ -142,13 +142,18 @@ __global__ void k_cost1(const uint32_t *__restrict__ e_idx, const uint32_t *__re
                         unsigned long long *__restrict__ cost)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
-        const unsigned long long c = (e_meta[p] >> 20) - 1;
+        const unsigned long long c = sci::meta_size(e_meta[p]) - 1;
         if (c) atomicAdd(cost + e_idx[p], c);
     }
 }
 
 // Narrow one table to the buckets with a member in [rb, re).  A: idx, B: code or S,
 // C: pos or meta (the field that locates the bucket start).
+// a spectator string of three words, moved as one entry
+struct Words3 {
+    uint64_t w[3];
+};
+
 template <bool ONE, typename B>
 int narrow(sci_ctx *ctx, int64_t E, const uint32_t *idx, const B *bfield, const uint32_t *posmeta, int64_t rb,
            int64_t re, uint32_t *&o_idx, B *&o_b, uint32_t *&o_pm, int64_t &o_n)
@@ -328,7 +333,12 @@ extern "C" int sci_set_row_range(sci_ctx *ctx, int64_t row_begin, int64_t row_en
     int rc = narrow<false, uint32_t>(ctx, ctx->e2, ctx->e2_idx, ctx->e2_code, ctx->e2_pos, row_begin, row_end,
                                      ctx->r2_idx, ctx->r2_code, ctx->r2_pos, ctx->r2);
     if (rc == SCI_OK) {
-        if (ctx->nwords == 2) {   // spectator strings of two words: 16 bytes per entry
+        if (ctx->nwords == 3) {   // spectator strings of three words: 24 bytes per entry
+            Words3 *o = nullptr;
+            rc = narrow<true, Words3>(ctx, ctx->e1, ctx->e1_idx, reinterpret_cast<const Words3 *>(ctx->e1_S),
+                                      ctx->e1_meta, row_begin, row_end, ctx->r1_idx, o, ctx->r1_meta, ctx->r1);
+            ctx->r1_S = reinterpret_cast<uint64_t *>(o);
+        } else if (ctx->nwords == 2) {   // spectator strings of two words: 16 bytes per entry
             ulonglong2 *o = nullptr;
             rc = narrow<true, ulonglong2>(ctx, ctx->e1, ctx->e1_idx, reinterpret_cast<const ulonglong2 *>(ctx->e1_S),
                                           ctx->e1_meta, row_begin, row_end, ctx->r1_idx, o, ctx->r1_meta, ctx->r1);

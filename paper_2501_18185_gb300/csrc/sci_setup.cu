@@ -205,24 +205,51 @@ struct KeyRule {
     int spinors, n, na, nb, N;
 };
 
-// Keys of KW 64-bit words (KW = 2: up to 128 spin-orbitals or spinors, word 0 holding
-// orbitals 0..63, the paper's orbital configurations as arrays of 64-bit integers,
-// Sec. 3.2): occupied orbitals of a key below orbital p
-__device__ __forceinline__ int below2(uint64_t lo, uint64_t hi, int p)
+// Keys of KW 64-bit words (up to 64 KW spin-orbitals or spinors, word 0 holding orbitals
+// 0..63: the paper's orbital configurations as arrays of 64-bit integers, Sec. 3.2)
+template <int KW> struct Kw {
+    uint64_t w[KW];
+};
+template <int KW> __device__ __forceinline__ Kw<KW> load_kw(const uint64_t *keys, int64_t I)
 {
-    if (p <= 0) return 0;
-    if (p < 64) return __popcll(lo & ((1ull << p) - 1ull));
-    if (p == 64) return __popcll(lo);
-    if (p < 128) return __popcll(lo) + __popcll(hi & ((1ull << (p - 64)) - 1ull));
-    return __popcll(lo) + __popcll(hi);
+    Kw<KW> k;
+#pragma unroll
+    for (int t = 0; t < KW; t++) k.w[t] = keys[I * KW + t];
+    return k;
 }
-
-// calls f(p) for every occupied orbital p of the key (lo, hi), ascending
-template <int KW, typename F> __device__ __forceinline__ void for_bits(uint64_t lo, uint64_t hi, F f)
+// occupied orbitals of the key below orbital p
+template <int KW> __device__ __forceinline__ int below_w(const Kw<KW> &k, int p)
 {
-    for (uint64_t m = lo; m; m &= m - 1) f(__ffsll((long long)m) - 1);
-    if constexpr (KW == 2)
-        for (uint64_t m = hi; m; m &= m - 1) f(64 + __ffsll((long long)m) - 1);
+    int c = 0;
+#pragma unroll
+    for (int t = 0; t < KW; t++) {
+        const int q = p - 64 * t;
+        if (q <= 0) break;
+        c += __popcll(q >= 64 ? k.w[t] : (k.w[t] & ((1ull << q) - 1ull)));
+    }
+    return c;
+}
+template <int KW> __device__ __forceinline__ int popc_w(const Kw<KW> &k)
+{
+    int c = 0;
+#pragma unroll
+    for (int t = 0; t < KW; t++) c += __popcll(k.w[t]);
+    return c;
+}
+// calls f(p) for every occupied orbital p of the key, ascending
+template <int KW, typename F> __device__ __forceinline__ void for_bits_w(const Kw<KW> &k, F f)
+{
+#pragma unroll
+    for (int t = 0; t < KW; t++)
+        for (uint64_t m = k.w[t]; m; m &= m - 1) f(64 * t + __ffsll((long long)m) - 1);
+}
+// -1, 0, +1 as unsigned (64 KW)-bit integers
+template <int KW> __device__ __forceinline__ int cmp_w(const Kw<KW> &a, const Kw<KW> &b)
+{
+#pragma unroll
+    for (int t = KW - 1; t >= 0; t--)
+        if (a.w[t] != b.w[t]) return a.w[t] < b.w[t] ? -1 : 1;
+    return 0;
 }
 
 template <int KW>
@@ -230,20 +257,20 @@ __global__ void k_validate(const uint64_t *__restrict__ keys, int64_t M, KeyRule
 {
     const int nbits = r.spinors ? r.n : 2 * r.n;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t lo = keys[i * KW], hi = KW == 2 ? keys[i * KW + 1] : 0ull;
-        const int tot = __popcll(lo) + __popcll(hi);
+        const Kw<KW> k = load_kw<KW>(keys, i);
+        const int tot = popc_w(k);
         int bad = 0;
         if (r.spinors) {
             if (tot != r.N) bad |= sci::DEV_POPCOUNT;
         } else {
-            const int na = below2(lo, hi, r.n);
-            if (na != r.na || below2(lo, hi, 2 * r.n) - na != r.nb) bad |= sci::DEV_POPCOUNT;
+            const int na = below_w(k, r.n);
+            if (na != r.na || below_w(k, 2 * r.n) - na != r.nb) bad |= sci::DEV_POPCOUNT;
         }
-        if (tot != below2(lo, hi, nbits)) bad |= sci::DEV_POPCOUNT;   // bits above the orbitals
+        if (tot != below_w(k, nbits)) bad |= sci::DEV_POPCOUNT;   // bits above the orbitals
         if (i > 0) {
-            const uint64_t plo = keys[(i - 1) * KW], phi = KW == 2 ? keys[(i - 1) * KW + 1] : 0ull;
-            if (phi == hi && plo == lo) bad |= sci::DEV_DUPLICATE;
-            else if (phi > hi || (phi == hi && plo > lo)) bad |= sci::DEV_UNSORTED;
+            const int c = cmp_w(load_kw<KW>(keys, i - 1), k);
+            if (c == 0) bad |= sci::DEV_DUPLICATE;
+            else if (c > 0) bad |= sci::DEV_UNSORTED;
         }
         if (bad) atomicOr(status, bad);
     }
@@ -255,11 +282,11 @@ __global__ void k_diag(const uint64_t *__restrict__ keys, int64_t M, int norb, c
                        const S *__restrict__ jd, const S *__restrict__ kd, double *__restrict__ hdiag)
 {
     for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < M; I += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t lo = keys[I * KW], hi = KW == 2 ? keys[I * KW + 1] : 0ull;
+        const Kw<KW> k = load_kw<KW>(keys, I);
         double e1 = 0.0, e2 = 0.0;
-        for_bits<KW>(lo, hi, [&](int i) {
+        for_bits_w(k, [&](int i) {
             e1 += Sc<S>::re(h_so[i * norb + i]);
-            for_bits<KW>(lo, hi, [&](int j) { e2 += Sc<S>::re(jd[i * norb + j]) - Sc<S>::re(kd[i * norb + j]); });
+            for_bits_w(k, [&](int j) { e2 += Sc<S>::re(jd[i * norb + j]) - Sc<S>::re(kd[i * norb + j]); });
         });
         hdiag[I] = e1 + 0.5 * e2;
     }
@@ -267,50 +294,44 @@ __global__ void k_diag(const uint64_t *__restrict__ keys, int64_t M, int norb, c
 
 // fref[i][a] = h_ai + sum_{k in ref} g_so[k][i][a]
 template <typename S>
-__global__ void k_fref(int norb, uint64_t ref, uint64_t ref_hi, const S *__restrict__ h_so, const S *__restrict__ g_so,
-                       S *__restrict__ fref)
+__global__ void k_fref(int norb, Kw<3> ref, const S *__restrict__ h_so, const S *__restrict__ g_so, S *__restrict__ fref)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= norb * norb) return;
     int i = t / norb, a = t % norb;
     S f = h_so[a * norb + i];
-    for_bits<2>(ref, ref_hi, [&](int k) { f = Sc<S>::add(f, g_so[((int64_t)k * norb + i) * norb + a]); });
+    for_bits_w(ref, [&](int k) { f = Sc<S>::add(f, g_so[((int64_t)k * norb + i) * norb + a]); });
     fref[t] = f;
 }
 
 // every determinant emits its keys with `holes` occupied bits removed (1 or 2): the key
-// words (out_hi only for KW = 2) and the value I | x << 32 | y << 40
+// words (word w at out_w + w * stride) and the value I | x << 32 | y << 40
 template <int KW>
-__global__ void k_emit(const uint64_t *__restrict__ keys, int64_t M, int holes, int per_det,
-                       uint64_t *__restrict__ out_keys, uint64_t *__restrict__ out_hi, uint64_t *__restrict__ out_vals)
+__global__ void k_emit(const uint64_t *__restrict__ keys, int64_t M, int holes, int per_det, uint64_t *__restrict__ out_w,
+                       int64_t stride, uint64_t *__restrict__ out_vals)
 {
     for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < M; I += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t lo = keys[I * KW], hi = KW == 2 ? keys[I * KW + 1] : 0ull;
+        const Kw<KW> k = load_kw<KW>(keys, I);
         const int64_t base = I * per_det;
         int t = 0;
-        auto clear = [](uint64_t &l, uint64_t &h, int p) {
-            if (p < 64) l &= ~(1ull << p);
-            else h &= ~(1ull << (p - 64));
+        auto put = [&](Kw<KW> e, uint64_t v) {
+#pragma unroll
+            for (int w = 0; w < KW; w++) out_w[w * stride + base + t] = e.w[w];
+            out_vals[base + t] = v;
+            t++;
         };
-        for_bits<KW>(lo, hi, [&](int x) {
+        for_bits_w(k, [&](int x) {
+            Kw<KW> e = k;
+            e.w[x >> 6] &= ~(1ull << (x & 63));
             if (holes == 1) {
-                uint64_t l = lo, h = hi;
-                clear(l, h, x);
-                out_keys[base + t] = l;
-                if constexpr (KW == 2) out_hi[base + t] = h;
-                out_vals[base + t] = (uint64_t)I | ((uint64_t)x << 32);
-                t++;
+                put(e, (uint64_t)I | ((uint64_t)x << 32));
                 return;
             }
-            for_bits<KW>(lo, hi, [&](int y) {
+            for_bits_w(k, [&](int y) {
                 if (y <= x) return;
-                uint64_t l = lo, h = hi;
-                clear(l, h, x);
-                clear(l, h, y);
-                out_keys[base + t] = l;
-                if constexpr (KW == 2) out_hi[base + t] = h;
-                out_vals[base + t] = (uint64_t)I | ((uint64_t)x << 32) | ((uint64_t)y << 40);
-                t++;
+                Kw<KW> f = e;
+                f.w[y >> 6] &= ~(1ull << (y & 63));
+                put(f, (uint64_t)I | ((uint64_t)x << 32) | ((uint64_t)y << 40));
             });
         });
     }
@@ -367,14 +388,14 @@ __global__ void k_fill2(const uint32_t *__restrict__ order, const uint32_t *__re
     for (int64_t j = w; j < kept; j += nw) {
         uint32_t b = order[j];
         uint32_t size = counts[b], old = offsets[b], dst = newoff[j];
-        const uint64_t K = ukeys[(int64_t)b * KW], Kh = KW == 2 ? ukeys[(int64_t)b * KW + 1] : 0ull;
+        const Kw<KW> K = load_kw<KW>(ukeys, b);
         for (uint32_t t = lane; t < size; t += 32) {
             uint64_t v = vals[old + t];
             int x = (int)((v >> 32) & 0xFF), y = (int)((v >> 40) & 0xFF);
             uint32_t gs = t, ge = t + 1;
             while (gs > 0 && (int)((vals[old + gs - 1] >> 40) & 0xFF) == y) gs--;
             while (ge < size && (int)((vals[old + ge] >> 40) & 0xFF) == y) ge++;
-            int par = (below2(K, Kh, x) + below2(K, Kh, y)) & 1;
+            int par = (below_w(K, x) + below_w(K, y)) & 1;
             e_idx[dst + t] = (uint32_t)(v & 0xFFFFFFFFull);
             e_code[dst + t] = sci::make_code(x, y, par, (int)(t - gs), (int)(ge - gs));
             e_pos[dst + t] = t | (size << 16);
@@ -394,15 +415,15 @@ __global__ void k_fill1(const uint32_t *__restrict__ order, const uint32_t *__re
     for (int64_t j = w; j < kept; j += nw) {
         uint32_t b = order[j];
         uint32_t size = counts[b], old = offsets[b], dst = newoff[j];
-        const uint64_t K = ukeys[(int64_t)b * KW], Kh = KW == 2 ? ukeys[(int64_t)b * KW + 1] : 0ull;
+        const Kw<KW> K = load_kw<KW>(ukeys, b);
         for (uint32_t t = lane; t < size; t += 32) {
             uint64_t v = vals[old + t];
             int x = (int)((v >> 32) & 0xFF);
-            uint32_t par = (uint32_t)(below2(K, Kh, x) & 1);
+            uint32_t par = (uint32_t)(below_w(K, x) & 1);
             e_idx[dst + t] = (uint32_t)(v & 0xFFFFFFFFull);
-            e_S[(int64_t)(dst + t) * KW] = K;
-            if constexpr (KW == 2) e_S[(int64_t)(dst + t) * KW + 1] = Kh;
-            e_meta[dst + t] = (uint32_t)x | (par << 7) | (t << 8) | (size << 20);
+#pragma unroll
+            for (int w = 0; w < KW; w++) e_S[(int64_t)(dst + t) * KW + w] = K.w[w];
+            e_meta[dst + t] = sci::make_meta(x, (int)par, (int)t, (int)size);
         }
     }
 }
@@ -439,23 +460,26 @@ __global__ void k_compose(const uint32_t *__restrict__ p1, const uint32_t *__res
         out[t] = p1[p2[t]];
 }
 
-__global__ void k_run_flags2(const uint64_t *__restrict__ lo, const uint64_t *__restrict__ hi, int64_t n,
-                             uint32_t *__restrict__ flag)
+// run starts of the sorted keys: any of the KW words (planar, stride n) differs from the
+// previous key's
+__global__ void k_run_flags_w(const uint64_t *__restrict__ words, int kw, int64_t n, uint32_t *__restrict__ flag)
 {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
-        flag[t] = t == 0 || lo[t] != lo[t - 1] || hi[t] != hi[t - 1];
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t f = t == 0;
+        for (int w = 0; w < kw && !f; w++) f = words[w * n + t] != words[w * n + t - 1];
+        flag[t] = f;
+    }
 }
 
-__global__ void k_runs2(const uint32_t *__restrict__ flag, const uint32_t *__restrict__ rid,
-                        const uint64_t *__restrict__ lo, const uint64_t *__restrict__ hi, int64_t n,
-                        uint64_t *__restrict__ ukeys, uint32_t *__restrict__ start)
+__global__ void k_runs_w(const uint32_t *__restrict__ flag, const uint32_t *__restrict__ rid,
+                         const uint64_t *__restrict__ words, int kw, int64_t n, uint64_t *__restrict__ ukeys,
+                         uint32_t *__restrict__ start)
 {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
         if (flag[t]) {
             const uint32_t r = rid[t];
             start[r] = (uint32_t)t;
-            ukeys[2 * (int64_t)r] = lo[t];
-            ukeys[2 * (int64_t)r + 1] = hi[t];
+            for (int w = 0; w < kw; w++) ukeys[kw * (int64_t)r + w] = words[w * n + t];
         }
 }
 
@@ -465,52 +489,54 @@ __global__ void k_run_counts(const uint32_t *__restrict__ start, int64_t nruns, 
         counts[r] = (uint32_t)((r + 1 < nruns ? (int64_t)start[r + 1] : n) - start[r]);
 }
 
-// Two-word keys: emit, sort as 128-bit integers (two stable radix passes: by the low word,
-// then by the high word) and find the runs of equal keys.  Produces B.vals_sorted,
-// B.ukeys ([nruns][2]) and B.counts.
-int sort_runs_2w(sci_ctx *ctx, int holes, int per_det, int64_t total, Buckets &B, int &nruns)
+// Keys of KW > 1 words: emit, sort as (64 KW)-bit integers by KW stable radix passes (word
+// 0 first, each pass on the previous permutation's order of the next word), and find the
+// runs of equal keys.  Produces B.vals_sorted, B.ukeys ([nruns][KW]) and B.counts.
+template <int KW>
+int sort_runs_w(sci_ctx *ctx, int holes, int per_det, int64_t total, Buckets &B, int &nruns)
 {
     cudaStream_t st = ctx->stream;
     const int64_t M = ctx->M;
     const int nitems = (int)total;
-    TmpBuf lo, hi, vals, lo_s, idx, perm1, hi_g, hi_s, iota2, perm2, fin, flag, rid, start, tmp, nr;
-    SCI_CK(cudaMalloc(&lo.p, total * 8));
-    SCI_CK(cudaMalloc(&hi.p, total * 8));
+    TmpBuf words, vals, perm, perm_new, iota, pass_perm, kg, ks, sorted, flag, rid, start, tmp;
+    SCI_CK(cudaMalloc(&words.p, total * 8 * KW));     // planar: word w of entry t at w * total + t
     SCI_CK(cudaMalloc(&vals.p, total * 8));
-    SCI_CK(cudaMalloc(&lo_s.p, total * 8));
-    SCI_CK(cudaMalloc(&idx.p, total * 4));
-    SCI_CK(cudaMalloc(&perm1.p, total * 4));
-    SCI_CK(cudaMalloc(&hi_g.p, total * 8));
-    SCI_CK(cudaMalloc(&hi_s.p, total * 8));
-    SCI_CK(cudaMalloc(&iota2.p, total * 4));
-    SCI_CK(cudaMalloc(&perm2.p, total * 4));
-    SCI_CK(cudaMalloc(&fin.p, total * 4));
+    SCI_CK(cudaMalloc(&perm.p, total * 4));
+    SCI_CK(cudaMalloc(&perm_new.p, total * 4));
+    SCI_CK(cudaMalloc(&iota.p, total * 4));
+    SCI_CK(cudaMalloc(&pass_perm.p, total * 4));
+    SCI_CK(cudaMalloc(&kg.p, total * 8));
+    SCI_CK(cudaMalloc(&ks.p, total * 8));
     SCI_CK(cudaMalloc(&B.vals_sorted.p, total * 8));
-    k_emit<2><<<grid_for(M), 256, 0, st>>>(ctx->keys, M, holes, per_det, lo.as<uint64_t>(), hi.as<uint64_t>(),
-                                          vals.as<uint64_t>());
-    k_iota_u32<<<grid_for(total), 256, 0, st>>>(idx.as<uint32_t>(), total);
-    k_iota_u32<<<grid_for(total), 256, 0, st>>>(iota2.as<uint32_t>(), total);
+    uint64_t *W = words.as<uint64_t>();
+    k_emit<KW><<<grid_for(M), 256, 0, st>>>(ctx->keys, M, holes, per_det, W, total, vals.as<uint64_t>());
+    k_iota_u32<<<grid_for(total), 256, 0, st>>>(perm.as<uint32_t>(), total);
+    k_iota_u32<<<grid_for(total), 256, 0, st>>>(iota.as<uint32_t>(), total);
     SCI_CK(cudaGetLastError());
-    size_t tb = 0, tb2 = 0;
-    const int hibits = std::max(1, ctx->norb - 64);
-    SCI_CK(cub::DeviceRadixSort::SortPairs(nullptr, tb, lo.as<uint64_t>(), lo_s.as<uint64_t>(), idx.as<uint32_t>(),
-                                           perm1.as<uint32_t>(), nitems, 0, 64, st));
-    SCI_CK(cub::DeviceRadixSort::SortPairs(nullptr, tb2, hi_g.as<uint64_t>(), hi_s.as<uint64_t>(),
-                                           iota2.as<uint32_t>(), perm2.as<uint32_t>(), nitems, 0, hibits, st));
-    SCI_CK(cudaMalloc(&tmp.p, std::max<size_t>(std::max(tb, tb2), 16)));
-    SCI_CK(cub::DeviceRadixSort::SortPairs(tmp.p, tb, lo.as<uint64_t>(), lo_s.as<uint64_t>(), idx.as<uint32_t>(),
-                                           perm1.as<uint32_t>(), nitems, 0, 64, st));
-    k_gather_u64<<<grid_for(total), 256, 0, st>>>(hi.as<uint64_t>(), perm1.as<uint32_t>(), total, hi_g.as<uint64_t>());
-    SCI_CK(cub::DeviceRadixSort::SortPairs(tmp.p, tb2, hi_g.as<uint64_t>(), hi_s.as<uint64_t>(), iota2.as<uint32_t>(),
-                                           perm2.as<uint32_t>(), nitems, 0, hibits, st));
-    k_compose<<<grid_for(total), 256, 0, st>>>(perm1.as<uint32_t>(), perm2.as<uint32_t>(), total, fin.as<uint32_t>());
-    k_gather_u64<<<grid_for(total), 256, 0, st>>>(lo.as<uint64_t>(), fin.as<uint32_t>(), total, lo_s.as<uint64_t>());
-    k_gather_u64<<<grid_for(total), 256, 0, st>>>(vals.as<uint64_t>(), fin.as<uint32_t>(), total,
+    size_t tb = 0;
+    SCI_CK(cub::DeviceRadixSort::SortPairs(nullptr, tb, kg.as<uint64_t>(), ks.as<uint64_t>(), iota.as<uint32_t>(),
+                                           pass_perm.as<uint32_t>(), nitems, 0, 64, st));
+    SCI_CK(cudaMalloc(&tmp.p, std::max<size_t>(tb, 16)));
+    for (int w = 0; w < KW; w++) {
+        const int bits = std::max(1, std::min(64, ctx->norb - 64 * w));
+        // word w in the current order, sorted stably; the order composes
+        k_gather_u64<<<grid_for(total), 256, 0, st>>>(W + w * total, perm.as<uint32_t>(), total, kg.as<uint64_t>());
+        SCI_CK(cub::DeviceRadixSort::SortPairs(tmp.p, tb, kg.as<uint64_t>(), ks.as<uint64_t>(), iota.as<uint32_t>(),
+                                               pass_perm.as<uint32_t>(), nitems, 0, bits, st));
+        k_compose<<<grid_for(total), 256, 0, st>>>(perm.as<uint32_t>(), pass_perm.as<uint32_t>(), total,
+                                                   perm_new.as<uint32_t>());
+        std::swap(perm.p, perm_new.p);
+    }
+    // the words and values in sorted order
+    SCI_CK(cudaMalloc(&sorted.p, total * 8 * KW));
+    uint64_t *SW = sorted.as<uint64_t>();
+    for (int w = 0; w < KW; w++)
+        k_gather_u64<<<grid_for(total), 256, 0, st>>>(W + w * total, perm.as<uint32_t>(), total, SW + w * total);
+    k_gather_u64<<<grid_for(total), 256, 0, st>>>(vals.as<uint64_t>(), perm.as<uint32_t>(), total,
                                                   B.vals_sorted.as<uint64_t>());
-    // runs of equal (hi, lo): hi_s and lo_s now hold the sorted words
     SCI_CK(cudaMalloc(&flag.p, total * 4));
     SCI_CK(cudaMalloc(&rid.p, total * 4));
-    k_run_flags2<<<grid_for(total), 256, 0, st>>>(lo_s.as<uint64_t>(), hi_s.as<uint64_t>(), total, flag.as<uint32_t>());
+    k_run_flags_w<<<grid_for(total), 256, 0, st>>>(SW, KW, total, flag.as<uint32_t>());
     SCI_CK(cudaGetLastError());
     size_t tb3 = 0;
     SCI_CK(cub::DeviceScan::ExclusiveSum(nullptr, tb3, flag.as<uint32_t>(), rid.as<uint32_t>(), nitems, st));
@@ -522,11 +548,11 @@ int sort_runs_2w(sci_ctx *ctx, int holes, int per_det, int64_t total, Buckets &B
     SCI_CK(cudaMemcpyAsync(&last[1], flag.as<uint32_t>() + (total - 1), 4, cudaMemcpyDeviceToHost, st));
     SCI_CK(cudaStreamSynchronize(st));
     nruns = (int)(last[0] + last[1]);
-    SCI_CK(cudaMalloc(&B.ukeys.p, (size_t)nruns * 16));
+    SCI_CK(cudaMalloc(&B.ukeys.p, (size_t)nruns * 8 * KW));
     SCI_CK(cudaMalloc(&B.counts.p, (size_t)nruns * 4));
     SCI_CK(cudaMalloc(&start.p, (size_t)nruns * 4));
-    k_runs2<<<grid_for(total), 256, 0, st>>>(flag.as<uint32_t>(), rid.as<uint32_t>(), lo_s.as<uint64_t>(),
-                                             hi_s.as<uint64_t>(), total, B.ukeys.as<uint64_t>(), start.as<uint32_t>());
+    k_runs_w<<<grid_for(total), 256, 0, st>>>(flag.as<uint32_t>(), rid.as<uint32_t>(), SW, KW, total,
+                                              B.ukeys.as<uint64_t>(), start.as<uint32_t>());
     k_run_counts<<<grid_for(nruns), 256, 0, st>>>(start.as<uint32_t>(), nruns, total, B.counts.as<uint32_t>());
     SCI_CK(cudaGetLastError());
     SCI_CK(cudaStreamSynchronize(st));
@@ -542,8 +568,9 @@ int build_buckets(sci_ctx *ctx, int holes, int per_det, Buckets &B)
     if (total == 0) return SCI_OK;
     int nitems = (int)total;
     int nruns = 0;
-    if (ctx->nwords == 2) {
-        int rc = sort_runs_2w(ctx, holes, per_det, total, B, nruns);
+    if (ctx->nwords > 1) {
+        int rc = ctx->nwords == 2 ? sort_runs_w<2>(ctx, holes, per_det, total, B, nruns)
+                                  : sort_runs_w<3>(ctx, holes, per_det, total, B, nruns);
         if (rc != SCI_OK) return rc;
         return order_runs(ctx, nruns, B);
     }
@@ -552,7 +579,7 @@ int build_buckets(sci_ctx *ctx, int holes, int per_det, Buckets &B)
     SCI_CK(cudaMalloc(&kb.p, total * 8));
     SCI_CK(cudaMalloc(&va.p, total * 8));
     SCI_CK(cudaMalloc(&B.vals_sorted.p, total * 8));
-    k_emit<1><<<grid_for(M), 256, 0, st>>>(ctx->keys, M, holes, per_det, ka.as<uint64_t>(), nullptr,
+    k_emit<1><<<grid_for(M), 256, 0, st>>>(ctx->keys, M, holes, per_det, ka.as<uint64_t>(), total,
                                           va.as<uint64_t>());
     SCI_CK(cudaGetLastError());
     cub::DoubleBuffer<uint64_t> dk(ka.as<uint64_t>(), kb.as<uint64_t>());
@@ -681,7 +708,7 @@ void free_dets(sci_ctx *ctx)
     free_held(ctx, ctx->e1_meta);
     ctx->have_dets = 0;
     ctx->nwords = 1;
-    ctx->ref_hi = 0;
+    ctx->ref_hi = ctx->ref_w2 = 0;
     ctx->M = 0;
     ctx->e1 = ctx->e2 = ctx->nb1 = ctx->nb2 = 0;
     ctx->maxb1 = ctx->maxb2 = 0;
@@ -711,18 +738,20 @@ int compute_diag_fref(sci_ctx *ctx)
     if (!ctx->fref) SCI_CK(alloc_held(ctx, &ctx->fref, (size_t)norb * norb * scalar_bytes(ctx)));
     int nn = norb * norb;
     if (ctx->cplx) {
-        k_fref<zdbl><<<(nn + 255) / 256, 256, 0, st>>>(norb, ctx->ref, ctx->ref_hi, (const zdbl *)ctx->h_so,
-                                                        (const zdbl *)ctx->g_so, (zdbl *)ctx->fref);
+        k_fref<zdbl><<<(nn + 255) / 256, 256, 0, st>>>(norb, Kw<3>{{ctx->ref, ctx->ref_hi, ctx->ref_w2}},
+                                                        (const zdbl *)ctx->h_so, (const zdbl *)ctx->g_so,
+                                                        (zdbl *)ctx->fref);
         if (ctx->M > 0) {
-            auto kd = ctx->nwords == 2 ? k_diag<zdbl, 2> : k_diag<zdbl, 1>;
+            auto kd = ctx->nwords == 3 ? k_diag<zdbl, 3> : ctx->nwords == 2 ? k_diag<zdbl, 2> : k_diag<zdbl, 1>;
             kd<<<grid_for(ctx->M), 256, 0, st>>>(ctx->keys, ctx->M, norb, (const zdbl *)ctx->h_so,
                                                  (const zdbl *)ctx->jd, (const zdbl *)ctx->kd, ctx->hdiag);
         }
     } else {
-        k_fref<double><<<(nn + 255) / 256, 256, 0, st>>>(norb, ctx->ref, ctx->ref_hi, (const double *)ctx->h_so,
-                                                          (const double *)ctx->g_so, (double *)ctx->fref);
+        k_fref<double><<<(nn + 255) / 256, 256, 0, st>>>(norb, Kw<3>{{ctx->ref, ctx->ref_hi, ctx->ref_w2}},
+                                                          (const double *)ctx->h_so, (const double *)ctx->g_so,
+                                                          (double *)ctx->fref);
         if (ctx->M > 0) {
-            auto kd = ctx->nwords == 2 ? k_diag<double, 2> : k_diag<double, 1>;
+            auto kd = ctx->nwords == 3 ? k_diag<double, 3> : ctx->nwords == 2 ? k_diag<double, 2> : k_diag<double, 1>;
             kd<<<grid_for(ctx->M), 256, 0, st>>>(ctx->keys, ctx->M, norb, (const double *)ctx->h_so,
                                                  (const double *)ctx->jd, (const double *)ctx->kd, ctx->hdiag);
         }
@@ -934,8 +963,8 @@ int set_ints(sci_ctx *ctx, int scalar, int mode, int n, const void *h, const voi
     ctx->err.clear();
     if (scalar != SCI_REAL64 && scalar != SCI_COMPLEX128) return sci_fail(ctx, SCI_ERR_ARG, "bad scalar type");
     if (mode != SCI_SPIN_ORBITALS && mode != SCI_SPINORS) return sci_fail(ctx, SCI_ERR_ARG, "bad mode");
-    if (mode == SCI_SPIN_ORBITALS && (n < 1 || n > 64)) return sci_fail(ctx, SCI_ERR_ARG, "spin-orbital mode needs 1 <= n <= 64");
-    if (mode == SCI_SPINORS && (n < 1 || n > 128)) return sci_fail(ctx, SCI_ERR_ARG, "spinor mode needs 1 <= n <= 128");
+    if (mode == SCI_SPIN_ORBITALS && (n < 1 || n > 96)) return sci_fail(ctx, SCI_ERR_ARG, "spin-orbital mode needs 1 <= n <= 96");
+    if (mode == SCI_SPINORS && (n < 1 || n > 192)) return sci_fail(ctx, SCI_ERR_ARG, "spinor mode needs 1 <= n <= 192");
     if (mode == SCI_SPIN_ORBITALS && scalar != SCI_REAL64)
         return sci_fail(ctx, SCI_ERR_ARG, "spin-orbital mode takes real integrals");
     if (!h) return sci_fail(ctx, SCI_ERR_ARG, "h is NULL");
@@ -1094,7 +1123,7 @@ extern "C" int sci_set_determinants(sci_ctx *ctx, const uint64_t *keys, int64_t 
 {
     if (!ctx) return SCI_ERR_ARG;
     if (ctx->have_ints && ctx->norb > 64)
-        return sci_fail(ctx, SCI_ERR_ARG, "more than 64 spin-orbitals: use sci_set_determinants_w with two words");
+        return sci_fail(ctx, SCI_ERR_ARG, "more than 64 spin-orbitals: use sci_set_determinants_w with two or three words");
     return set_dets(ctx, keys, 1, M, n_alpha, n_beta, keys_on_device);
 }
 
@@ -1102,9 +1131,9 @@ extern "C" int sci_set_determinants_w(sci_ctx *ctx, const uint64_t *keys, int nw
                                       int n_beta, int keys_on_device)
 {
     if (!ctx) return SCI_ERR_ARG;
-    if (nwords != 1 && nwords != 2) return sci_fail(ctx, SCI_ERR_ARG, "nwords must be 1 or 2");
-    if (nwords == 1 && ctx->have_ints && ctx->norb > 64)
-        return sci_fail(ctx, SCI_ERR_ARG, "more than 64 spin-orbitals need two words");
+    if (nwords < 1 || nwords > 3) return sci_fail(ctx, SCI_ERR_ARG, "nwords must be 1, 2 or 3");
+    if (ctx->have_ints && ctx->norb > 64 * nwords)
+        return sci_fail(ctx, SCI_ERR_ARG, "more spin-orbitals than the key words hold (64 per word)");
     return set_dets(ctx, keys, nwords, M, n_alpha, n_beta, keys_on_device);
 }
 
@@ -1135,13 +1164,18 @@ int set_dets(sci_ctx *ctx, const uint64_t *keys, int nwords, int64_t M, int n_al
     ctx->nwords = nwords;
     {
         // the reference: the lowest N spinors, or the lowest n_alpha alpha and n_beta beta
-        // orbitals, over two words
-        unsigned __int128 r;
-        auto low = [](int k) -> unsigned __int128 { return k >= 128 ? ~(unsigned __int128)0 : (((unsigned __int128)1 << k) - 1); };
-        if (ctx->spinors) r = low(N);
-        else r = low(n_alpha) | (low(n_beta) << ctx->n);
-        ctx->ref = (uint64_t)r;
-        ctx->ref_hi = (uint64_t)(r >> 64);
+        // orbitals, over three words
+        uint64_t r[3] = {0, 0, 0};
+        auto set = [&](int p) { r[p >> 6] |= 1ull << (p & 63); };
+        if (ctx->spinors) {
+            for (int p = 0; p < N; p++) set(p);
+        } else {
+            for (int p = 0; p < n_alpha; p++) set(p);
+            for (int p = 0; p < n_beta; p++) set(ctx->n + p);
+        }
+        ctx->ref = r[0];
+        ctx->ref_hi = r[1];
+        ctx->ref_w2 = r[2];
     }
 
     SCI_CK(alloc_held(ctx, (void **)&ctx->keys, (size_t)M * 8 * nwords));
@@ -1154,7 +1188,8 @@ int set_dets(sci_ctx *ctx, const uint64_t *keys, int nwords, int64_t M, int n_al
     SCI_CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), st));
     if (M > 0) {
         KeyRule kr{ctx->spinors, ctx->n, n_alpha, n_beta, N};
-        if (nwords == 2) k_validate<2><<<grid_for(M), 256, 0, st>>>(ctx->keys, M, kr, ctx->status);
+        if (nwords == 3) k_validate<3><<<grid_for(M), 256, 0, st>>>(ctx->keys, M, kr, ctx->status);
+        else if (nwords == 2) k_validate<2><<<grid_for(M), 256, 0, st>>>(ctx->keys, M, kr, ctx->status);
         else k_validate<1><<<grid_for(M), 256, 0, st>>>(ctx->keys, M, kr, ctx->status);
         SCI_CK(cudaGetLastError());
     }
@@ -1183,7 +1218,7 @@ int set_dets(sci_ctx *ctx, const uint64_t *keys, int nwords, int64_t M, int n_al
         SCI_CK(alloc_held(ctx, (void **)&ctx->e2_code, (size_t)B.entries * 4));
         SCI_CK(alloc_held(ctx, (void **)&ctx->e2_pos, (size_t)B.entries * 4));
         if (B.kept > 0) {
-            auto kf = nwords == 2 ? k_fill2<2> : k_fill2<1>;
+            auto kf = nwords == 3 ? k_fill2<3> : nwords == 2 ? k_fill2<2> : k_fill2<1>;
             kf<<<grid_for(B.kept * 32), 256, 0, st>>>(B.order.as<uint32_t>(), B.counts.as<uint32_t>(),
                                                           B.offsets.as<uint32_t>(), B.newoff.as<uint32_t>(),
                                                           B.ukeys.as<uint64_t>(), B.vals_sorted.as<uint64_t>(), B.kept,
@@ -1204,7 +1239,7 @@ int set_dets(sci_ctx *ctx, const uint64_t *keys, int nwords, int64_t M, int n_al
         SCI_CK(alloc_held(ctx, (void **)&ctx->e1_S, (size_t)B.entries * 8 * nwords));
         SCI_CK(alloc_held(ctx, (void **)&ctx->e1_meta, (size_t)B.entries * 4));
         if (B.kept > 0) {
-            auto kf = nwords == 2 ? k_fill1<2> : k_fill1<1>;
+            auto kf = nwords == 3 ? k_fill1<3> : nwords == 2 ? k_fill1<2> : k_fill1<1>;
             kf<<<grid_for(B.kept * 32), 256, 0, st>>>(B.order.as<uint32_t>(), B.counts.as<uint32_t>(),
                                                           B.offsets.as<uint32_t>(), B.newoff.as<uint32_t>(),
                                                           B.ukeys.as<uint64_t>(), B.vals_sorted.as<uint64_t>(), B.kept,
@@ -1213,7 +1248,7 @@ int set_dets(sci_ctx *ctx, const uint64_t *keys, int nwords, int64_t M, int n_al
         }
         SCI_CK(cudaStreamSynchronize(st));
     }
-    if (ctx->maxb2 > 0xFFFF || ctx->maxb1 > 4095) {
+    if (ctx->maxb2 > 0xFFFF || ctx->maxb1 > sci::kMaxBucket1) {
         free_dets(ctx);
         return sci_fail(ctx, SCI_ERR_OVERFLOW, "bucket larger than the table format allows");
     }

@@ -596,7 +596,7 @@ k_doubles_dsz(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e
 template <typename TS, typename TC, int NV, bool RANGED, bool STORE = false, int KW = 1>
 __global__ void __launch_bounds__(kThreads)
 k_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S, const uint32_t *__restrict__ e_meta,
-          int64_t E, int norb, uint64_t ref, uint64_t ref_hi, const TS *__restrict__ fref, const TS *__restrict__ g_so,
+          int64_t E, int norb, uint64_t ref, uint64_t ref_hi, uint64_t ref_w2, const TS *__restrict__ fref, const TS *__restrict__ g_so,
           const TC *__restrict__ C, int nvec, int v0, typename AccOf<TS>::type *__restrict__ Sout, sci::RowRange rr, const uint32_t *__restrict__ slot)
 {
     using TA = typename AccOf<TS>::type;
@@ -606,31 +606,36 @@ k_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S, 
             if (I < rr.rb || I >= rr.re) continue;
         }
         const uint32_t meta = e_meta[p];
-        const int a = (int)(meta & 0x7F);
-        const bool par = (meta >> 7) & 1;
-        const int64_t bs = p - (int64_t)((meta >> 8) & 0xFFF);
-        const int64_t be = bs + (int64_t)(meta >> 20);
-        const uint64_t Sk = e_S[p * KW], Sk1 = KW == 2 ? e_S[p * KW + 1] : 0ull;
-        const uint64_t part = Sk & ~ref, holes = ref & ~Sk;
-        const uint64_t part1 = Sk1 & ~ref_hi, holes1 = ref_hi & ~Sk1;   // orbitals 64.. (two words)
+        const int a = sci::meta_x(meta);
+        const bool par = sci::meta_par(meta);
+        const int64_t bs = p - (int64_t)sci::meta_off(meta);
+        const int64_t be = bs + (int64_t)sci::meta_size(meta);
+        uint64_t part[KW], holes[KW];   // S \ ref and ref \ S, word w holding orbitals 64w..64w+63
+#pragma unroll
+        for (int w_ = 0; w_ < KW; w_++) {
+            const uint64_t Sw = e_S[p * KW + w_], rw = w_ == 0 ? ref : w_ == 1 ? ref_hi : ref_w2;
+            part[w_] = Sw & ~rw, holes[w_] = rw & ~Sw;
+        }
         TA acc[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) zero(acc[v]);
         for (int64_t q = bs; q < be; q++) {
             if (q == p) continue;
             const uint32_t mq = e_meta[q];
-            const int i = (int)(mq & 0x7F);
-            const bool parq = (mq >> 7) & 1;
+            const int i = sci::meta_x(mq);
+            const bool parq = sci::meta_par(mq);
             const uint32_t idxq = e_idx[q];
             TS f = ldg(fref + i * norb + a);
+#pragma unroll
             for (int w_ = 0; w_ < KW; w_++)
-            for (uint64_t m = w_ ? part1 : part; m; m &= m - 1) {
+            for (uint64_t m = part[w_]; m; m &= m - 1) {
                 int k = 64 * w_ + __ffsll((long long)m) - 1;
                 TS g = ldg(g_so + ((int64_t)k * norb + i) * norb + a);
                 if constexpr (sizeof(TS) == sizeof(zdbl)) { f.x += g.x; f.y += g.y; } else { f += g; }
             }
+#pragma unroll
             for (int w_ = 0; w_ < KW; w_++)
-            for (uint64_t m = w_ ? holes1 : holes; m; m &= m - 1) {
+            for (uint64_t m = holes[w_]; m; m &= m - 1) {
                 int k = 64 * w_ + __ffsll((long long)m) - 1;
                 TS g = ldg(g_so + ((int64_t)k * norb + i) * norb + a);
                 if constexpr (sizeof(TS) == sizeof(zdbl)) { f.x -= g.x; f.y -= g.y; } else { f -= g; }
@@ -658,7 +663,7 @@ using sci::ds_add;
 template <int NV, bool RANGED, bool STORE = false, int KW = 1>
 __global__ void __launch_bounds__(kThreads)
 k_singles_ds(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S, const uint32_t *__restrict__ e_meta,
-             int64_t E, int norb, uint64_t ref, uint64_t ref_hi, const float2 *__restrict__ fref2, const float2 *__restrict__ g2,
+             int64_t E, int norb, uint64_t ref, uint64_t ref_hi, uint64_t ref_w2, const float2 *__restrict__ fref2, const float2 *__restrict__ g2,
              const float2 *__restrict__ C2, int nvec, int v0, double *__restrict__ Sout, sci::RowRange rr, const uint32_t *__restrict__ slot)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
@@ -667,31 +672,36 @@ k_singles_ds(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_
             if (I < rr.rb || I >= rr.re) continue;
         }
         const uint32_t meta = e_meta[p];
-        const int a = (int)(meta & 0x7F);
-        const bool par = (meta >> 7) & 1;
-        const int64_t bs = p - (int64_t)((meta >> 8) & 0xFFF);
-        const int64_t be = bs + (int64_t)(meta >> 20);
-        const uint64_t Sk = e_S[p * KW], Sk1 = KW == 2 ? e_S[p * KW + 1] : 0ull;
-        const uint64_t part = Sk & ~ref, holes = ref & ~Sk;
-        const uint64_t part1 = Sk1 & ~ref_hi, holes1 = ref_hi & ~Sk1;   // orbitals 64.. (two words)
+        const int a = sci::meta_x(meta);
+        const bool par = sci::meta_par(meta);
+        const int64_t bs = p - (int64_t)sci::meta_off(meta);
+        const int64_t be = bs + (int64_t)sci::meta_size(meta);
+        uint64_t part[KW], holes[KW];   // S \ ref and ref \ S, word w holding orbitals 64w..64w+63
+#pragma unroll
+        for (int w_ = 0; w_ < KW; w_++) {
+            const uint64_t Sw = e_S[p * KW + w_], rw = w_ == 0 ? ref : w_ == 1 ? ref_hi : ref_w2;
+            part[w_] = Sw & ~rw, holes[w_] = rw & ~Sw;
+        }
         Ds acc[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) ds_zero(acc[v]);
         for (int64_t q = bs; q < be; q++) {
             if (q == p) continue;
             const uint32_t mq = e_meta[q];
-            const int i = (int)(mq & 0x7F);
-            const bool parq = (mq >> 7) & 1;
+            const int i = sci::meta_x(mq);
+            const bool parq = sci::meta_par(mq);
             const uint32_t idxq = e_idx[q];
             const float2 f0 = __ldg(fref2 + i * norb + a);
             Ds f{f0.x, f0.y};
+#pragma unroll
             for (int w_ = 0; w_ < KW; w_++)
-            for (uint64_t m = w_ ? part1 : part; m; m &= m - 1) {
+            for (uint64_t m = part[w_]; m; m &= m - 1) {
                 const int k = 64 * w_ + __ffsll((long long)m) - 1;
                 ds_add(f, __ldg(g2 + ((int64_t)k * norb + i) * norb + a));
             }
+#pragma unroll
             for (int w_ = 0; w_ < KW; w_++)
-            for (uint64_t m = w_ ? holes1 : holes; m; m &= m - 1) {
+            for (uint64_t m = holes[w_]; m; m &= m - 1) {
                 const int k = 64 * w_ + __ffsll((long long)m) - 1;
                 ds_add(f, flip(true, __ldg(g2 + ((int64_t)k * norb + i) * norb + a)));
             }
@@ -714,7 +724,7 @@ k_singles_ds(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_
 template <int NV, bool RANGED, bool STORE = false, int KW = 1>
 __global__ void __launch_bounds__(kThreads)
 k_singles_dsz(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S,
-              const uint32_t *__restrict__ e_meta, int64_t E, int norb, uint64_t ref, uint64_t ref_hi,
+              const uint32_t *__restrict__ e_meta, int64_t E, int norb, uint64_t ref, uint64_t ref_hi, uint64_t ref_w2,
               const float4 *__restrict__ fref4, const float4 *__restrict__ g4, const float4 *__restrict__ C4,
               int nvec, int v0, zdbl *__restrict__ Sout, sci::RowRange rr, const uint32_t *__restrict__ slot)
 {
@@ -724,33 +734,38 @@ k_singles_dsz(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e
             if (I < rr.rb || I >= rr.re) continue;
         }
         const uint32_t meta = e_meta[p];
-        const int a = (int)(meta & 0x7F);
-        const bool par = (meta >> 7) & 1;
-        const int64_t bs = p - (int64_t)((meta >> 8) & 0xFFF);
-        const int64_t be = bs + (int64_t)(meta >> 20);
-        const uint64_t Sk = e_S[p * KW], Sk1 = KW == 2 ? e_S[p * KW + 1] : 0ull;
-        const uint64_t part = Sk & ~ref, holes = ref & ~Sk;
-        const uint64_t part1 = Sk1 & ~ref_hi, holes1 = ref_hi & ~Sk1;   // orbitals 64.. (two words)
+        const int a = sci::meta_x(meta);
+        const bool par = sci::meta_par(meta);
+        const int64_t bs = p - (int64_t)sci::meta_off(meta);
+        const int64_t be = bs + (int64_t)sci::meta_size(meta);
+        uint64_t part[KW], holes[KW];   // S \ ref and ref \ S, word w holding orbitals 64w..64w+63
+#pragma unroll
+        for (int w_ = 0; w_ < KW; w_++) {
+            const uint64_t Sw = e_S[p * KW + w_], rw = w_ == 0 ? ref : w_ == 1 ? ref_hi : ref_w2;
+            part[w_] = Sw & ~rw, holes[w_] = rw & ~Sw;
+        }
         Ds ar[NV], ai[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) ds_zero(ar[v]), ds_zero(ai[v]);
         for (int64_t q = bs; q < be; q++) {
             if (q == p) continue;
             const uint32_t mq = e_meta[q];
-            const int i = (int)(mq & 0x7F);
-            const bool parq = (mq >> 7) & 1;
+            const int i = sci::meta_x(mq);
+            const bool parq = sci::meta_par(mq);
             const uint32_t idxq = e_idx[q];
             const float4 f0 = __ldg(fref4 + i * norb + a);
             Ds fr{f0.x, f0.y}, fi{f0.z, f0.w};
+#pragma unroll
             for (int w_ = 0; w_ < KW; w_++)
-            for (uint64_t m = w_ ? part1 : part; m; m &= m - 1) {
+            for (uint64_t m = part[w_]; m; m &= m - 1) {
                 const int k = 64 * w_ + __ffsll((long long)m) - 1;
                 const float4 g = __ldg(g4 + ((int64_t)k * norb + i) * norb + a);
                 ds_add(fr, make_float2(g.x, g.y));
                 ds_add(fi, make_float2(g.z, g.w));
             }
+#pragma unroll
             for (int w_ = 0; w_ < KW; w_++)
-            for (uint64_t m = w_ ? holes1 : holes; m; m &= m - 1) {
+            for (uint64_t m = holes[w_]; m; m &= m - 1) {
                 const int k = 64 * w_ + __ffsll((long long)m) - 1;
                 const float4 g = flip(true, __ldg(g4 + ((int64_t)k * norb + i) * norb + a));
                 ds_add(fr, make_float2(g.x, g.y));
@@ -950,8 +965,8 @@ int f32_groups(sci_ctx *ctx, const Tabs &T, const float *C, double *S, int nvec)
     return rc;
 }
 
-// paired-FP32 singles; real coefficients may come in as double or float; keys of one or
-// two words (KW)
+// paired-FP32 singles; real coefficients may come in as double or float; keys of one to
+// three words (KW)
 template <bool RG, bool ST, bool CPLX, int NV, typename TC, int KW>
 int launch_singles_ds_w(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int nvec, int v0)
 {
@@ -960,14 +975,14 @@ int launch_singles_ds_w(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int
         k_split_cz<<<grid_for(ctx->M * NV), kThreads, 0, ctx->stream>>>((const zdbl *)C, ctx->M, nvec, v0, NV,
                                                                         (float4 *)ctx->c_ds);
         k_singles_dsz<NV, RG, ST, KW><<<g, kThreads, 0, ctx->stream>>>(
-            T.e1_idx, T.e1_S, T.e1_meta, T.e1, ctx->norb, ctx->ref, ctx->ref_hi, (const float4 *)ctx->fref_ds,
+            T.e1_idx, T.e1_S, T.e1_meta, T.e1, ctx->norb, ctx->ref, ctx->ref_hi, ctx->ref_w2, (const float4 *)ctx->fref_ds,
             (const float4 *)ctx->g_ds, (const float4 *)ctx->c_ds, nvec, v0, (zdbl *)S, T.rr,
             ST ? ctx->det_inv1 : nullptr);
     } else {
         k_split_c<TC><<<grid_for(ctx->M * NV), kThreads, 0, ctx->stream>>>((const TC *)C, ctx->M, nvec, v0, NV,
                                                                            (float2 *)ctx->c_ds);
         k_singles_ds<NV, RG, ST, KW><<<g, kThreads, 0, ctx->stream>>>(
-            T.e1_idx, T.e1_S, T.e1_meta, T.e1, ctx->norb, ctx->ref, ctx->ref_hi, (const float2 *)ctx->fref_ds,
+            T.e1_idx, T.e1_S, T.e1_meta, T.e1, ctx->norb, ctx->ref, ctx->ref_hi, ctx->ref_w2, (const float2 *)ctx->fref_ds,
             (const float2 *)ctx->g_ds, (const float2 *)ctx->c_ds, nvec, v0, (double *)S, T.rr,
             ST ? ctx->det_inv1 : nullptr);
     }
@@ -978,6 +993,7 @@ template <bool RG, bool ST, bool CPLX, int NV, typename TC = double>
 int launch_singles_ds(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int nvec, int v0)
 {
     if (T.e1 == 0) return SCI_OK;
+    if (ctx->nwords == 3) return launch_singles_ds_w<RG, ST, CPLX, NV, TC, 3>(ctx, T, C, S, nvec, v0);
     if (ctx->nwords == 2) return launch_singles_ds_w<RG, ST, CPLX, NV, TC, 2>(ctx, T, C, S, nvec, v0);
     return launch_singles_ds_w<RG, ST, CPLX, NV, TC, 1>(ctx, T, C, S, nvec, v0);
 }
@@ -1005,9 +1021,11 @@ template <bool RG, bool ST, typename TS, typename TC, int NV>
 int launch_singles(sci_ctx *ctx, const Tabs &T, const TC *C, typename AccOf<TS>::type *S, int nvec, int v0)
 {
     if (T.e1 == 0) return SCI_OK;
-    auto kern = ctx->nwords == 2 ? k_singles<TS, TC, NV, RG, ST, 2> : k_singles<TS, TC, NV, RG, ST, 1>;
+    auto kern = ctx->nwords == 3   ? k_singles<TS, TC, NV, RG, ST, 3>
+                : ctx->nwords == 2 ? k_singles<TS, TC, NV, RG, ST, 2>
+                                   : k_singles<TS, TC, NV, RG, ST, 1>;
     kern<<<grid_for(T.e1), kThreads, 0, ctx->stream>>>(T.e1_idx, T.e1_S, T.e1_meta, T.e1, ctx->norb, ctx->ref,
-                                                       ctx->ref_hi, (const TS *)ctx->fref, (const TS *)ctx->g_so, C,
+                                                       ctx->ref_hi, ctx->ref_w2, (const TS *)ctx->fref, (const TS *)ctx->g_so, C,
                                                        nvec, v0, S, T.rr, ST ? ctx->det_inv1 : nullptr);
     return sci_cuda_check(ctx, cudaGetLastError(), "k_singles launch");
 }
@@ -1069,7 +1087,7 @@ __global__ void k_count1(const uint32_t *__restrict__ e_meta, int64_t E, unsigne
 {
     unsigned long long cnt = 0;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x)
-        cnt += (e_meta[p] >> 20) - 1;
+        cnt += sci::meta_size(e_meta[p]) - 1;
     for (int o = 16; o; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
     if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(out, cnt);
 }
@@ -1117,11 +1135,11 @@ __global__ void k_conn1(const uint32_t *__restrict__ e_idx, const uint32_t *__re
         int64_t I = e_idx[p];
         if (I < rb || I >= re) continue;
         uint32_t meta = e_meta[p];
-        int64_t bs = p - (int64_t)((meta >> 8) & 0xFFF), be = bs + (int64_t)(meta >> 20);
-        int par = (meta >> 7) & 1;
+        int64_t bs = p - (int64_t)sci::meta_off(meta), be = bs + (int64_t)sci::meta_size(meta);
+        int par = sci::meta_par(meta);
         for (int64_t q = bs; q < be; q++) {
             if (q == p) continue;
-            int parq = (e_meta[q] >> 7) & 1;
+            int parq = sci::meta_par(e_meta[q]);
             conn_put(o, I, e_idx[q], 1, (par ^ parq) ? -1 : 1);
         }
     }

@@ -344,8 +344,36 @@ def two_word_keys(alpha: np.ndarray, beta: np.ndarray, n: int) -> np.ndarray:
 
 
 def sort_words(keys: np.ndarray) -> np.ndarray:
-    """[M, 2] word keys in ascending order as 128-bit integers."""
-    return keys[np.lexsort((keys[:, 0], keys[:, 1]))]
+    """[M, K] word keys in ascending order as (64 K)-bit integers (word K-1 most
+    significant)."""
+    return keys[np.lexsort(tuple(keys[:, w] for w in range(keys.shape[1])))]
+
+
+def occ_at_level(n: int, nocc: int, level: int) -> np.ndarray:
+    """Occupied-orbital lists [count, nocc] (ascending in each row) of the strings of
+    strings_at_level(n, nocc, level), in the same (holes, particles) order; no 64-orbital
+    limit."""
+    holes = _combos(range(nocc), level)
+    parts = _combos(range(nocc, n), level)
+    out = []
+    for h in holes:
+        kept = np.array([i for i in range(nocc) if i not in set(h.tolist())], dtype=np.int64)
+        out.append(np.concatenate([np.broadcast_to(kept, (len(parts), len(kept))), parts], axis=1))
+    return np.concatenate(out) if out else np.zeros((0, nocc), dtype=np.int64)
+
+
+def words_from_occ(occ: np.ndarray, nwords: int) -> np.ndarray:
+    """[M, nwords] uint64 words of the determinants whose occupied bits are the rows of
+    `occ` (bit b in word b // 64, position b % 64)."""
+    occ = np.asarray(occ, dtype=np.int64)
+    out = np.zeros((occ.shape[0], nwords), dtype=np.uint64)
+    if occ.shape[1] == 0:
+        return out
+    one = np.uint64(1)
+    for w in range(nwords):
+        bits = np.where((occ >> 6) == w, np.left_shift(one, (occ & 63).astype(np.uint64)), np.uint64(0))
+        out[:, w] = np.bitwise_or.reduce(bits, axis=1)
+    return out
 
 
 def excitation_level_words(keys: np.ndarray, hf: np.ndarray) -> np.ndarray:
@@ -398,6 +426,58 @@ def selected_two_word(n: int = 40, na: int = 4, nb: int = 4, M: int = 40000, nau
     w = Workload(f"sel2w_{n}o_{na}a{nb}b_M{M}", "spin_orbitals", n, na, nb, keys, ints, np.stack(cols, axis=1),
                  {"hf_words": hf})
     return w
+
+
+def selected_three_word(n: int = 70, na: int = 3, nb: int = 3, M: int = 60000, naux: int = 40, nvec: int = 1,
+                        seed: int = 2501181861) -> Workload:
+    """A selected space of more than 128 spin-orbitals (three-word keys): n spatial orbitals
+    (2n > 128), the recipe of selected_two_word (HF + all singles + all Sz-conserving
+    doubles + random triples over the spin splits, without replacement, up to M
+    determinants; real integrals with naux Cholesky vectors of Frobenius norms 0.3 n 0.95^P;
+    |c| = exp(-level) with random signs, normalised), built from occupied-orbital lists
+    and sorted as (64 x 3)-bit integers.  Alpha bits 0..n-1, beta bits n..2n-1: for
+    64 < n <= 96 the alpha string crosses words 0/1 and the beta string words 1/2.
+    Draw order: integrals, triples, c."""
+    rng = np.random.default_rng(seed)
+    ints = real_integrals(rng, n, naux, 0.95)
+
+    def dets(A, B):
+        return words_from_occ(np.concatenate([A, B + n], axis=1), 3)
+
+    parts = []
+    for level in range(3):
+        for ka in range(level + 1):
+            kb = level - ka
+            if ka > min(na, n - na) or kb > min(nb, n - nb):
+                continue
+            A = occ_at_level(n, na, ka)
+            B = occ_at_level(n, nb, kb)
+            parts.append(dets(np.repeat(A, len(B), axis=0), np.tile(B, (len(A), 1))))
+    base = np.concatenate(parts)
+    rest = M - len(base)
+    if rest < 0:
+        raise ValueError("M smaller than HF+singles+doubles")
+    splits = [(ka, 3 - ka) for ka in range(4) if ka <= min(na, n - na) and 3 - ka <= min(nb, n - nb)]
+    sizes = [n_strings_at_level(n, na, ka) * n_strings_at_level(n, nb, kb) for ka, kb in splits]
+    idx = np.sort(rng.choice(int(sum(sizes)), size=rest, replace=False))
+    trip, off = [], 0
+    for (ka, kb), sz in zip(splits, sizes):
+        sel = idx[(idx >= off) & (idx < off + sz)] - off
+        off += sz
+        if sel.size:
+            A = occ_at_level(n, na, ka)
+            B = occ_at_level(n, nb, kb)
+            trip.append(dets(A[sel // len(B)], B[sel % len(B)]))
+    keys = sort_words(np.concatenate([base] + trip))
+    assert len(keys) == M
+    hf = dets(np.arange(na)[None, :], np.arange(nb)[None, :])[0]
+    lev = excitation_level_words(keys, hf)
+    cols = []
+    for _ in range(nvec):
+        v = np.exp(-lev.astype(np.float64)) * rng.choice(np.array([-1.0, 1.0]), size=M)
+        cols.append(v / np.linalg.norm(v))
+    return Workload(f"sel3w_{n}o_{na}a{nb}b_M{M}", "spin_orbitals", n, na, nb, keys, ints, np.stack(cols, axis=1),
+                    {"hf_words": hf})
 
 
 def selected_spinor_64(M: int = 1_000_000, nvec: int = 1, seed_offset: int = 4) -> Workload:
