@@ -75,6 +75,11 @@ __host__ __device__ __forceinline__ uint32_t make_meta(int x, int par, int off, 
     return (uint32_t)x | ((uint32_t)par << 8) | ((uint32_t)off << 9) | ((uint32_t)size << 20);
 }
 constexpr int kMaxBucket1 = 2047;   // the largest (N-1) bucket the meta word holds
+// (N-2) buckets of more members than this go through the tiled sigma kernel by default
+// (with one-word keys a bucket holds at most C(64 - N + 2, 2) <= 2016 members, so
+// one-word lists never do)
+constexpr int kTileBucket = 2048;
+constexpr int kTileRows = 256;      // rows of a tile of the tiled kernel (one per thread)
 // whether two members of a bucket share an extra orbital (then they are a single
 // excitation of each other, not a double); valid for orbitals up to 255
 __host__ __device__ __forceinline__ bool codes_overlap(uint32_t a, uint32_t b)
@@ -166,6 +171,20 @@ struct sci_ctx {
     int maxb2 = 0, maxb1 = 0;
     int64_t pairs = 0, pairs2 = 0, pairs1 = 0;
 
+    // (N-2) buckets of more than tile_b members are walked by the tiled kernel (their
+    // members staged in shared memory a tile at a time) instead of the window kernels.
+    // Tables hold buckets largest first, so these are a prefix [0, e2_big) of the table;
+    // tiles2 lists the first entry of each tile of kTileRows rows (ntiles2 of them), and
+    // maxb2_small is the largest bucket left to the window kernels.  r2_big, rtiles2,
+    // nrtiles2 and rmaxb2_small are the same for the range tables.
+    int tile_b = sci::kTileBucket;
+    int64_t e2_big = 0, ntiles2 = 0;
+    uint32_t *tiles2 = nullptr;
+    int maxb2_small = 0;
+    int64_t r2_big = 0, nrtiles2 = 0;
+    uint32_t *rtiles2 = nullptr;
+    int rmaxb2_small = 0;
+
     // row range of sci_sigma() (sci_set_row_range): when `ranged`, sigma computes rows
     // [row_b, row_e) only, walking range tables r2_* / r1_* that keep (whole, in table
     // order) the buckets with a member in the range; range_pairs counts the connected
@@ -223,6 +242,12 @@ cudaError_t sci_noalloc_prepare(int device);
 void sci_free_range(sci_ctx *ctx);
 // deterministic accumulation (sci_rows.cu): frees its index and buffers, back to atomics
 void sci_free_det(sci_ctx *ctx);
+
+// the tiled prefix of the full (ranged = false) or range tables for the context's tile_b:
+// e2_big / r2_big, the tile list and the largest bucket left to the window kernels
+// (sci_setup.cu); synchronous
+int sci_table_split(sci_ctx *ctx, bool ranged);
+void sci_free_split(sci_ctx *ctx, bool ranged);
 
 // launchers (sci_sigma.cu)
 bool sci_sigma_window_fits(const sci_ctx *ctx);

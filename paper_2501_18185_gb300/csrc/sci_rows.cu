@@ -305,6 +305,7 @@ extern "C" int sci_set_deterministic(sci_ctx *ctx, int max_nvec)
 
 void sci_free_range(sci_ctx *ctx)
 {
+    sci_free_split(ctx, true);
     release(ctx->r2_idx);
     release(ctx->r2_code);
     release(ctx->r2_pos);
@@ -365,6 +366,9 @@ extern "C" int sci_set_row_range(sci_ctx *ctx, int64_t row_begin, int64_t row_en
         rc = sci_cuda_check(ctx, e, "range pair count");
     }
     if (cnt) cudaFree(cnt);
+    // the tiled prefix of the range tables (a subset of the full tables' buckets, in their
+    // order, so the buckets left to the window kernels fit as they do there)
+    if (rc == SCI_OK) rc = sci_table_split(ctx, true);
     if (rc != SCI_OK) {
         ctx->range_bytes = 0;  // not yet counted in bytes_held
         sci_free_range(ctx);

@@ -397,7 +397,8 @@ __global__ void k_fill2(const uint32_t *__restrict__ order, const uint32_t *__re
             while (ge < size && (int)((vals[old + ge] >> 40) & 0xFF) == y) ge++;
             int par = (below_w(K, x) + below_w(K, y)) & 1;
             e_idx[dst + t] = (uint32_t)(v & 0xFFFFFFFFull);
-            e_code[dst + t] = sci::make_code(x, y, par, (int)(t - gs), (int)(ge - gs));
+            // the y-group fields saturate (63, 127): no kernel reads them past that
+            e_code[dst + t] = sci::make_code(x, y, par, (int)min(t - gs, 63u), (int)min(ge - gs, 127u));
             e_pos[dst + t] = t | (size << 16);
         }
     }
@@ -691,10 +692,109 @@ int order_runs(sci_ctx *ctx, int nruns, Buckets &B)
     return SCI_OK;
 }
 
+// ------------------------------------------------------------------ tiled prefix
+// The (N-2) table holds its buckets largest first, so the buckets of more than thr
+// members are its first entries.  out[0] = the end of that prefix (written by the one
+// entry where the sizes cross thr); out[1] counts entries where a bucket above thr follows
+// one at or below it, which a table in size order never has.
+__global__ void k_split_point(const uint32_t *__restrict__ e_pos, int64_t E, int thr, unsigned long long *out)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
+        const bool big = sci::pos_size(e_pos[p]) > thr;
+        const bool next_big = p + 1 < E && sci::pos_size(e_pos[p + 1]) > thr;
+        if (big && !next_big) out[0] = (unsigned long long)(p + 1);
+        if (!big && next_big) atomicAdd(out + 1, 1ull);
+    }
+}
+
+// tile starts: the entries at bucket offsets 0, kTileRows, 2 kTileRows, ...
+__global__ void k_tile_flags(const uint32_t *__restrict__ e_pos, int64_t E, uint32_t *__restrict__ flag)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x)
+        flag[p] = sci::pos_off(e_pos[p]) % sci::kTileRows == 0;
+}
+
+__global__ void k_tile_fill(const uint32_t *__restrict__ flag, const uint32_t *__restrict__ at, int64_t E,
+                            uint32_t *__restrict__ tiles)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x)
+        if (flag[p]) tiles[at[p]] = (uint32_t)p;
+}
+
+}  // namespace
+
+void sci_free_split(sci_ctx *ctx, bool ranged)
+{
+    uint32_t *&t = ranged ? ctx->rtiles2 : ctx->tiles2;
+    if (t) cudaFree(t);
+    t = nullptr;
+    (ranged ? ctx->r2_big : ctx->e2_big) = 0;
+    (ranged ? ctx->nrtiles2 : ctx->ntiles2) = 0;
+    (ranged ? ctx->rmaxb2_small : ctx->maxb2_small) = 0;
+}
+
+int sci_table_split(sci_ctx *ctx, bool ranged)
+{
+    sci_free_split(ctx, ranged);
+    const uint32_t *e_pos = ranged ? ctx->r2_pos : ctx->e2_pos;
+    const int64_t E = ranged ? ctx->r2 : ctx->e2;
+    if (E == 0) return SCI_OK;
+    cudaStream_t st = ctx->stream;
+    TmpBuf cnt, flag, at, tmp;
+    unsigned long long h[2] = {0, 0};
+    SCI_CK(cudaMalloc(&cnt.p, 16));
+    SCI_CK(cudaMemsetAsync(cnt.p, 0, 16, st));
+    k_split_point<<<grid_for(E), 256, 0, st>>>(e_pos, E, ctx->tile_b, cnt.as<unsigned long long>());
+    SCI_CK(cudaGetLastError());
+    SCI_CK(cudaMemcpyAsync(h, cnt.p, 16, cudaMemcpyDeviceToHost, st));
+    SCI_CK(cudaStreamSynchronize(st));
+    if (h[1] != 0) return sci_fail(ctx, SCI_ERR_STATE, "internal: (N-2) buckets not in size order");
+    const int64_t big = (int64_t)h[0];
+    int maxb_small = 0;
+    if (big < E) {
+        uint32_t pos = 0;
+        SCI_CK(cudaMemcpy(&pos, e_pos + big, 4, cudaMemcpyDeviceToHost));
+        maxb_small = sci::pos_size(pos);
+    }
+    int64_t ntiles = 0;
+    uint32_t *tiles = nullptr;
+    if (big > 0) {
+        const int nitems = (int)big;
+        SCI_CK(cudaMalloc(&flag.p, (size_t)big * 4));
+        SCI_CK(cudaMalloc(&at.p, (size_t)big * 4));
+        k_tile_flags<<<grid_for(big), 256, 0, st>>>(e_pos, big, flag.as<uint32_t>());
+        size_t tb = 0;
+        SCI_CK(cub::DeviceScan::ExclusiveSum(nullptr, tb, flag.as<uint32_t>(), at.as<uint32_t>(), nitems, st));
+        SCI_CK(cudaMalloc(&tmp.p, std::max<size_t>(tb, 16)));
+        SCI_CK(cub::DeviceScan::ExclusiveSum(tmp.p, tb, flag.as<uint32_t>(), at.as<uint32_t>(), nitems, st));
+        uint32_t last[2] = {0, 0};
+        SCI_CK(cudaMemcpyAsync(&last[0], at.as<uint32_t>() + (big - 1), 4, cudaMemcpyDeviceToHost, st));
+        SCI_CK(cudaMemcpyAsync(&last[1], flag.as<uint32_t>() + (big - 1), 4, cudaMemcpyDeviceToHost, st));
+        SCI_CK(cudaStreamSynchronize(st));
+        ntiles = (int64_t)last[0] + last[1];
+        SCI_CK(cudaMalloc(&tiles, (size_t)ntiles * 4));
+        k_tile_fill<<<grid_for(big), 256, 0, st>>>(flag.as<uint32_t>(), at.as<uint32_t>(), big, tiles);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            cudaFree(tiles);
+            return sci_cuda_check(ctx, e, "tile list");
+        }
+    }
+    (ranged ? ctx->r2_big : ctx->e2_big) = big;
+    (ranged ? ctx->rtiles2 : ctx->tiles2) = tiles;
+    (ranged ? ctx->nrtiles2 : ctx->ntiles2) = ntiles;
+    (ranged ? ctx->rmaxb2_small : ctx->maxb2_small) = maxb_small;
+    return SCI_OK;
+}
+
+namespace {
+
 void free_dets(sci_ctx *ctx)
 {
     sci_free_range(ctx);
     sci_free_det(ctx);
+    sci_free_split(ctx, false);
     free_held(ctx, ctx->keys);
     free_held(ctx, ctx->hdiag);
     free_held(ctx, ctx->fref);
@@ -1137,6 +1237,28 @@ extern "C" int sci_set_determinants_w(sci_ctx *ctx, const uint64_t *keys, int nw
     return set_dets(ctx, keys, nwords, M, n_alpha, n_beta, keys_on_device);
 }
 
+extern "C" int sci_set_tile_threshold(sci_ctx *ctx, int members)
+{
+    if (!ctx) return SCI_ERR_ARG;
+    ctx->err.clear();
+    if (members < 0 || members > 0xFFFF) return sci_fail(ctx, SCI_ERR_ARG, "tile threshold outside [0, 65535]");
+    SCI_CK(cudaSetDevice(ctx->device));
+    SCI_CK(cudaStreamSynchronize(ctx->stream));   // no launch in flight reads the old tile lists
+    const int old = ctx->tile_b;
+    ctx->tile_b = members == 0 ? sci::kTileBucket : members;
+    if (!ctx->have_dets) return SCI_OK;
+    int rc = sci_table_split(ctx, false);
+    if (rc == SCI_OK && ctx->ranged) rc = sci_table_split(ctx, true);
+    if (rc == SCI_OK && !sci_sigma_window_fits(ctx))
+        rc = sci_fail(ctx, SCI_ERR_OVERFLOW, "buckets left to the window kernels do not fit shared memory");
+    if (rc != SCI_OK) {   // back to the previous threshold, whose split was valid
+        ctx->tile_b = old;
+        sci_table_split(ctx, false);
+        if (ctx->ranged) sci_table_split(ctx, true);
+    }
+    return rc;
+}
+
 namespace {
 int set_dets(sci_ctx *ctx, const uint64_t *keys, int nwords, int64_t M, int n_alpha, int n_beta, int keys_on_device)
 {
@@ -1253,9 +1375,11 @@ int set_dets(sci_ctx *ctx, const uint64_t *keys, int nwords, int64_t M, int n_al
         return sci_fail(ctx, SCI_ERR_OVERFLOW, "bucket larger than the table format allows");
     }
     // a list that sci_sigma() could not run is rejected here, not at every launch: the
-    // largest bucket must fit the shared-memory window of a one-vector launch.  (With
-    // one-word keys a bucket holds at most C(norb - N + 2, 2) <= 2016 members, which
-    // always fits; the check guards the table format, not a case seen in practice.)
+    // largest bucket left to the window kernels (the buckets of more than tile_b members
+    // go through the tiled kernel) must fit the shared-memory window of a one-vector
+    // launch (always so at the default tile_b)
+    rc = sci_table_split(ctx, false);
+    if (rc != SCI_OK) { free_dets(ctx); return rc; }
     if (!sci_sigma_window_fits(ctx)) {
         free_dets(ctx);
         return sci_fail(ctx, SCI_ERR_OVERFLOW, "largest bucket does not fit the sigma kernel's shared-memory window");

@@ -592,6 +592,192 @@ k_doubles_dsz(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e
     }
 }
 
+// ------------------------------------------------------------------ doubles, tiled
+// (N-2) buckets of more than tile_b members (sci_set_tile_threshold) are too large to
+// stage whole beside a window, so they run here.  A CTA takes kTileRows consecutive
+// members of one bucket as its rows (one per thread) and streams the bucket's members
+// through shared memory in column tiles, each staged once per CTA; every thread walks a
+// column tile against its row as the window kernels walk a bucket (disjointness test, one
+// table load per double, the FMAs), so a row sums the same products.  The row itself and
+// its single excitations fail the disjointness test and add nothing.  All threads of a
+// CTA share the bucket, so trip counts are uniform and the barriers are CTA-wide.
+// The arithmetic is a policy: staged element SC, table element TT, accumulator ACC,
+// output TO, input coefficients CI; how a coefficient is read, multiplied in,
+// renormalised (paired FP32) and written out.
+template <typename TS, typename TC> struct PolF64 {   // FP64 / complex128 (the k_doubles arithmetic)
+    using SC = TS;
+    using TT = TS;
+    using ACC = typename AccOf<TS>::type;
+    using TO = ACC;
+    using CI = TC;
+    __device__ static SC load(const CI *C, int64_t i) { return (SC)C[i]; }
+    __device__ static TT table(const TT *p) { return ldg(p); }
+    __device__ static void clear(ACC &a) { zero(a); }
+    __device__ static void mul_add(ACC &a, TT t, SC c) { fma_acc(a, t, c); }
+    __device__ static void renorm(ACC &) {}
+    __device__ static TO value(const ACC &a) { return a; }
+    __device__ static void add_out(TO *p, TO v) { red_add(p, v); }
+};
+struct PolDS {   // paired FP32, real (the k_doubles_ds arithmetic)
+    using SC = float2;
+    using TT = float2;
+    using ACC = Ds;
+    using TO = double;
+    using CI = float2;
+    __device__ static SC load(const CI *C, int64_t i) { return C[i]; }
+    __device__ static TT table(const TT *p) { return __ldg(p); }
+    __device__ static void clear(ACC &a) { ds_zero(a); }
+    __device__ static void mul_add(ACC &a, TT t, SC c) { ds_fma(a, t, c); }
+    __device__ static void renorm(ACC &a) { ds_renorm(a); }
+    __device__ static TO value(const ACC &a) { return ds_value(a); }
+    __device__ static void add_out(TO *p, TO v) { red_add(p, v); }
+};
+struct PolF32 {   // FP32 storage, paired-FP32 sums (the k_doubles_f32 arithmetic)
+    using SC = float;
+    using TT = float;
+    using ACC = Ds;
+    using TO = double;
+    using CI = float;
+    __device__ static SC load(const CI *C, int64_t i) { return C[i]; }
+    __device__ static TT table(const TT *p) { return __ldg(p); }
+    __device__ static void clear(ACC &a) { ds_zero(a); }
+    __device__ static void mul_add(ACC &a, TT t, SC c);
+    __device__ static void renorm(ACC &a) { ds_renorm(a); }
+    __device__ static TO value(const ACC &a) { return ds_value(a); }
+    __device__ static void add_out(TO *p, TO v) { red_add_nz(p, v); }
+};
+__device__ __forceinline__ void PolF32::mul_add(Ds &a, float t, float c) { ds_fma1(a, t, c); }
+struct DsZ {
+    Ds r, i;
+};
+struct PolDSZ {   // paired FP32, complex (the k_doubles_dsz arithmetic)
+    using SC = float4;
+    using TT = float4;
+    using ACC = DsZ;
+    using TO = zdbl;
+    using CI = float4;
+    __device__ static SC load(const CI *C, int64_t i) { return C[i]; }
+    __device__ static TT table(const TT *p) { return __ldg(p); }
+    __device__ static void clear(ACC &a) { ds_zero(a.r), ds_zero(a.i); }
+    __device__ static void mul_add(ACC &a, TT t, SC c)
+    {
+        const float2 tr_ = make_float2(t.x, t.y), ti = make_float2(t.z, t.w), mti = make_float2(-t.z, -t.w);
+        const float2 cr = make_float2(c.x, c.y), ci = make_float2(c.z, c.w);
+        ds_fma(a.r, tr_, cr);
+        ds_fma(a.r, mti, ci);
+        ds_fma(a.i, tr_, ci);
+        ds_fma(a.i, ti, cr);
+    }
+    __device__ static void renorm(ACC &a) { ds_renorm(a.r), ds_renorm(a.i); }
+    __device__ static TO value(const ACC &a) { return zdbl{ds_value(a.r), ds_value(a.i)}; }
+    __device__ static void add_out(TO *p, TO v) { red_add(p, v); }
+};
+
+// shared memory of the tiled kernel: at most this, which needs no opt-in
+constexpr size_t kTiledSmem = 48 * 1024;
+
+// C holds coefficient v of determinant I at C[I * cstride + coff + v]
+template <class P, int NV, bool RANGED, bool STORE>
+__global__ void __launch_bounds__(kThreads)
+k_doubles_tiled(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_code,
+                const uint32_t *__restrict__ e_pos, const uint32_t *__restrict__ tiles, int64_t ntiles, int TCOL,
+                sci::TabRule tr, const typename P::TT *__restrict__ tab, const typename P::CI *__restrict__ C,
+                int cstride, int coff, int nvec, int v0, typename P::TO *__restrict__ Sout, sci::RowRange rr,
+                const uint32_t *__restrict__ slot)
+{
+    using SC = typename P::SC;
+    using TT = typename P::TT;
+    using ACC = typename P::ACC;
+    extern __shared__ __align__(16) unsigned char smem[];
+    SC *s_c = reinterpret_cast<SC *>(smem);
+    uint2 *s_kc = reinterpret_cast<uint2 *>(smem + (((size_t)TCOL * NV * sizeof(SC) + 15) & ~(size_t)15));
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t r0 = tiles[t];
+        const uint32_t pos0 = e_pos[r0];
+        const int64_t bs = r0 - sci::pos_off(pos0);
+        const int bsize = sci::pos_size(pos0);
+        const int64_t row = r0 + threadIdx.x;
+        bool active = row < bs + bsize;
+        if (RANGED && active) {
+            const int64_t I = e_idx[row];
+            active = I >= rr.rb && I < rr.re;
+        }
+        if (!__syncthreads_or(active)) continue;   // no row of this tile is computed
+        uint32_t rc = 0;
+        const TT *trow = tab;
+        bool par = false;
+        if (active) {
+            const uint32_t code = e_code[row];
+            uint32_t rowoff, colbase;
+            sci::pair_offsets(tr, sci::code_x(code), sci::code_y(code), rowoff, colbase);
+            rc = row_code(code);
+            trow = tab + rowoff;
+            par = sci::code_par(code);
+        }
+        ACC acc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) P::clear(acc[v]);
+        for (int cs = 0; cs < bsize; cs += TCOL) {
+            const int n = min(TCOL, bsize - cs);
+            __syncthreads();   // every thread is done with the previous column tile
+            for (int q = threadIdx.x; q < n; q += blockDim.x) {
+                const int64_t g = bs + cs + q;
+                const uint32_t idx = e_idx[g], code = e_code[g];
+                uint32_t rowoff, colbase;
+                sci::pair_offsets(tr, sci::code_x(code), sci::code_y(code), rowoff, colbase);
+                s_kc[q] = make_uint2(col_code(code), colbase);
+                const bool pq = sci::code_par(code);
+#pragma unroll
+                for (int v = 0; v < NV; v++) s_c[q * NV + v] = flip(pq, P::load(C, (int64_t)idx * cstride + coff + v));
+            }
+            __syncthreads();
+            if (!active) continue;
+            int j = 0;
+            for (; j + kUnroll <= n; j += kUnroll) {
+                uint2 kc[kUnroll];
+                TT tv[kUnroll];
+                unsigned vm = 0;
+#pragma unroll
+                for (int u = 0; u < kUnroll; u++) {
+                    kc[u] = s_kc[j + u];
+                    vm |= (unsigned)disjoint(rc, kc[u].x) << u;
+                }
+                if (vm == 0) continue;
+#pragma unroll
+                for (int u = 0; u < kUnroll; u++) {
+                    tv[u] = TT{};
+                    if (vm & (1u << u)) tv[u] = P::table(trow + kc[u].y);
+                }
+#pragma unroll
+                for (int u = 0; u < kUnroll; u++)
+#pragma unroll
+                    for (int v = 0; v < NV; v++) P::mul_add(acc[v], tv[u], s_c[(j + u) * NV + v]);
+#pragma unroll
+                for (int v = 0; v < NV; v++) P::renorm(acc[v]);
+            }
+            for (; j < n; j++) {
+                const uint2 kc = s_kc[j];
+                if (!disjoint(rc, kc.x)) continue;
+                const TT tv = P::table(trow + kc.y);
+#pragma unroll
+                for (int v = 0; v < NV; v++) P::mul_add(acc[v], tv, s_c[j * NV + v]);
+            }
+#pragma unroll
+            for (int v = 0; v < NV; v++) P::renorm(acc[v]);
+        }
+        if (active) {
+            if constexpr (STORE) {
+#pragma unroll
+                for (int v = 0; v < NV; v++) Sout[(int64_t)slot[row] * nvec + v0 + v] = flip(par, P::value(acc[v]));
+            } else {
+                const uint32_t idx = e_idx[row];
+#pragma unroll
+                for (int v = 0; v < NV; v++) P::add_out(Sout + (int64_t)idx * nvec + v0 + v, flip(par, P::value(acc[v])));
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ singles
 template <typename TS, typename TC, int NV, bool RANGED, bool STORE = false, int KW = 1>
 __global__ void __launch_bounds__(kThreads)
@@ -827,6 +1013,9 @@ sci::TabRule tab_rule(const sci_ctx *ctx) { return sci::TabRule{ctx->spinors, ct
 
 // The tables a sigma launch walks and the rows it computes: the full tables (every row),
 // or the range tables of sci_set_row_range() (rows [row_b, row_e)).
+// The (N-2) entries [0, e2_big) are the buckets of the tiled kernel (tile starts in
+// tiles[0, ntiles)); the window kernels walk [e2_big, e2), whose largest bucket is
+// maxb_small.
 struct Tabs {
     const uint32_t *e2_idx, *e2_code, *e2_pos;
     int64_t e2;
@@ -835,15 +1024,36 @@ struct Tabs {
     const uint32_t *e1_meta;
     int64_t e1;
     sci::RowRange rr;
+    int64_t e2_big;
+    const uint32_t *tiles;
+    int64_t ntiles;
+    int maxb_small;
 };
 
 Tabs tabs_of(const sci_ctx *ctx)
 {
     if (ctx->ranged)
         return Tabs{ctx->r2_idx, ctx->r2_code, ctx->r2_pos, ctx->r2, ctx->r1_idx, ctx->r1_S, ctx->r1_meta, ctx->r1,
-                    sci::RowRange{ctx->row_b, ctx->row_e}};
+                    sci::RowRange{ctx->row_b, ctx->row_e}, ctx->r2_big, ctx->rtiles2, ctx->nrtiles2,
+                    ctx->rmaxb2_small};
     return Tabs{ctx->e2_idx, ctx->e2_code, ctx->e2_pos, ctx->e2, ctx->e1_idx, ctx->e1_S, ctx->e1_meta, ctx->e1,
-                sci::RowRange{0, ctx->M}};
+                sci::RowRange{0, ctx->M}, ctx->e2_big, ctx->tiles2, ctx->ntiles2, ctx->maxb2_small};
+}
+
+// the tiled kernel over the buckets of [0, T.e2_big) (nothing when there are none)
+template <class P, bool RG, bool ST, int NV>
+int launch_tiled(sci_ctx *ctx, const Tabs &T, const typename P::TT *tab, const typename P::CI *C, int cstride,
+                 int coff, int nvec, int v0, typename P::TO *S)
+{
+    if (T.ntiles == 0) return SCI_OK;
+    const size_t per = NV * sizeof(typename P::SC) + sizeof(uint2);
+    int tcol = (int)std::min<size_t>(1024, (kTiledSmem - 16) / per) & ~31;
+    const size_t smem = (((size_t)tcol * NV * sizeof(typename P::SC) + 15) & ~(size_t)15) + (size_t)tcol * sizeof(uint2);
+    const int64_t grid = std::min<int64_t>(T.ntiles, 152 * 16);
+    k_doubles_tiled<P, NV, RG, ST><<<(unsigned)grid, kThreads, smem, ctx->stream>>>(
+        T.e2_idx, T.e2_code, T.e2_pos, T.tiles, T.ntiles, tcol, tab_rule(ctx), tab, C, cstride, coff, nvec, v0, S,
+        T.rr, ST ? ctx->det_inv2 : nullptr);
+    return sci_cuda_check(ctx, cudaGetLastError(), "k_doubles_tiled launch");
 }
 
 // staged bytes per window row: NV coefficients, the (code, offset) pair, and in a RANGED
@@ -855,16 +1065,20 @@ int launch_doubles(sci_ctx *ctx, const Tabs &T, const TS *tab, const TC *C, type
                    int v0)
 {
     if (T.e2 == 0) return SCI_OK;
+    int rc = launch_tiled<PolF64<TS, TC>, RG, ST, NV>(ctx, T, tab, C, nvec, v0, nvec, v0, S);
+    const int64_t b = T.e2_big, E = T.e2 - b;
+    if (rc != SCI_OK || E == 0) return rc;
     size_t per = NV * sizeof(TS) + row_extra<RG>();
     size_t smem = 0;
-    int ch = choose_rows(ctx->maxb2, per, smem);
+    int ch = choose_rows(T.maxb_small, per, smem);
     if (ch < 0) return sci_fail(ctx, SCI_ERR_OVERFLOW, "bucket too large for shared memory");
     auto kern = k_doubles<TS, TC, NV, RG, ST>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return sci_cuda_check(ctx, e, "cudaFuncSetAttribute");
-    int64_t blocks = (T.e2 + ch - 1) / ch;
-    kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(T.e2_idx, T.e2_code, T.e2_pos, T.e2, ch, tab_rule(ctx), tab,
-                                                          C, nvec, v0, S, T.rr, ST ? ctx->det_inv2 : nullptr);
+    int64_t blocks = (E + ch - 1) / ch;
+    kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(T.e2_idx + b, T.e2_code + b, T.e2_pos + b, E, ch,
+                                                          tab_rule(ctx), tab, C, nvec, v0, S, T.rr,
+                                                          ST ? ctx->det_inv2 + b : nullptr);
     return sci_cuda_check(ctx, cudaGetLastError(), "k_doubles launch");
 }
 
@@ -873,11 +1087,11 @@ template <bool RG, bool ST, bool CPLX, int NV>
 int launch_doubles_ds(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int nvec, int v0)
 {
     if (T.e2 == 0) return SCI_OK;
+    const int64_t b = T.e2_big, E = T.e2 - b;
     size_t per = NV * (CPLX ? sizeof(float4) : sizeof(float2)) + row_extra<RG>();
     size_t smem = 0;
-    int ch = choose_rows(ctx->maxb2, per, smem);
+    int ch = E > 0 ? choose_rows(T.maxb_small, per, smem) : 0;
     if (ch < 0) return sci_fail(ctx, SCI_ERR_OVERFLOW, "bucket too large for shared memory");
-    int64_t blocks = (T.e2 + ch - 1) / ch;
     cudaError_t e;
     // the vector group, split into paired floats in the context's c_ds buffer
     // (64 bytes per determinant: up to 8 real or 4 complex coefficients)
@@ -887,20 +1101,30 @@ int launch_doubles_ds(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int n
     else
         k_split_c<<<grid_for(ctx->M * NV), kThreads, 0, ctx->stream>>>((const double *)C, ctx->M, nvec, v0, NV,
                                                                        (float2 *)ctx->c_ds);
+    int rc;
+    if constexpr (CPLX)
+        rc = launch_tiled<PolDSZ, RG, ST, NV>(ctx, T, (const float4 *)ctx->tab_ds, (const float4 *)ctx->c_ds, NV, 0,
+                                              nvec, v0, (zdbl *)S);
+    else
+        rc = launch_tiled<PolDS, RG, ST, NV>(ctx, T, (const float2 *)ctx->tab_ds, (const float2 *)ctx->c_ds, NV, 0,
+                                             nvec, v0, (double *)S);
+    if (rc != SCI_OK || E == 0) return rc;
+    const int64_t blocks = (E + ch - 1) / ch;
+    const uint32_t *slot = ST ? ctx->det_inv2 + b : nullptr;
     if constexpr (CPLX) {
         auto kern = k_doubles_dsz<NV, RG, ST>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return sci_cuda_check(ctx, e, "cudaFuncSetAttribute");
-        kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(T.e2_idx, T.e2_code, T.e2_pos, T.e2, ch, tab_rule(ctx),
-                                                              (const float4 *)ctx->tab_ds, (const float4 *)ctx->c_ds,
-                                                              nvec, v0, (zdbl *)S, T.rr, ST ? ctx->det_inv2 : nullptr);
+        kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(T.e2_idx + b, T.e2_code + b, T.e2_pos + b, E, ch,
+                                                              tab_rule(ctx), (const float4 *)ctx->tab_ds,
+                                                              (const float4 *)ctx->c_ds, nvec, v0, (zdbl *)S, T.rr, slot);
     } else {
         auto kern = k_doubles_ds<NV, RG, ST>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return sci_cuda_check(ctx, e, "cudaFuncSetAttribute");
-        kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(T.e2_idx, T.e2_code, T.e2_pos, T.e2, ch, tab_rule(ctx),
-                                                              (const float2 *)ctx->tab_ds, (const float2 *)ctx->c_ds,
-                                                              nvec, v0, (double *)S, T.rr, ST ? ctx->det_inv2 : nullptr);
+        kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(T.e2_idx + b, T.e2_code + b, T.e2_pos + b, E, ch,
+                                                              tab_rule(ctx), (const float2 *)ctx->tab_ds,
+                                                              (const float2 *)ctx->c_ds, nvec, v0, (double *)S, T.rr, slot);
     }
     return sci_cuda_check(ctx, cudaGetLastError(), "k_doubles_ds launch");
 }
@@ -915,7 +1139,7 @@ int ds_groups(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int nvec)
         int g = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
         if (CPLX && g > 4) g = 4;
         size_t smem_probe = 0;
-        while (g > 1 && choose_rows(ctx->maxb2, g * unit + row_extra<RG>(), smem_probe) < 0) g >>= 1;
+        while (g > 1 && choose_rows(T.maxb_small, g * unit + row_extra<RG>(), smem_probe) < 0) g >>= 1;
         switch (g) {
         case 8: rc = launch_doubles_ds<RG, ST, CPLX, 8>(ctx, T, C, S, nvec, v0); break;
         case 4: rc = launch_doubles_ds<RG, ST, CPLX, 4>(ctx, T, C, S, nvec, v0); break;
@@ -932,16 +1156,20 @@ template <bool RG, bool ST, int NV>
 int launch_doubles_f32(sci_ctx *ctx, const Tabs &T, const float *C, double *S, int nvec, int v0)
 {
     if (T.e2 == 0) return SCI_OK;
+    int rc = launch_tiled<PolF32, RG, ST, NV>(ctx, T, ctx->tab32, C, nvec, v0, nvec, v0, S);
+    const int64_t b = T.e2_big, E = T.e2 - b;
+    if (rc != SCI_OK || E == 0) return rc;
     size_t per = NV * sizeof(float) + row_extra<RG>();
     size_t smem = 0;
-    int ch = choose_rows(ctx->maxb2, per, smem, NV >= 8 ? SCI_F32_ROWS : kRowsPerCta);
+    int ch = choose_rows(T.maxb_small, per, smem, NV >= 8 ? SCI_F32_ROWS : kRowsPerCta);
     if (ch < 0) return sci_fail(ctx, SCI_ERR_OVERFLOW, "bucket too large for shared memory");
-    int64_t blocks = (T.e2 + ch - 1) / ch;
+    int64_t blocks = (E + ch - 1) / ch;
     auto kern = k_doubles_f32<NV, RG, ST>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return sci_cuda_check(ctx, e, "cudaFuncSetAttribute");
-    kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(T.e2_idx, T.e2_code, T.e2_pos, T.e2, ch, tab_rule(ctx),
-                                                          ctx->tab32, C, nvec, v0, S, T.rr, ST ? ctx->det_inv2 : nullptr);
+    kern<<<(unsigned)blocks, kThreads, smem, ctx->stream>>>(T.e2_idx + b, T.e2_code + b, T.e2_pos + b, E, ch,
+                                                          tab_rule(ctx), ctx->tab32, C, nvec, v0, S, T.rr,
+                                                          ST ? ctx->det_inv2 + b : nullptr);
     return sci_cuda_check(ctx, cudaGetLastError(), "k_doubles_f32 launch");
 }
 
@@ -953,7 +1181,7 @@ int f32_groups(sci_ctx *ctx, const Tabs &T, const float *C, double *S, int nvec)
         int left = nvec - v0;
         int g = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
         size_t smem_probe = 0;
-        while (g > 1 && choose_rows(ctx->maxb2, g * sizeof(float) + row_extra<RG>(), smem_probe) < 0) g >>= 1;
+        while (g > 1 && choose_rows(T.maxb_small, g * sizeof(float) + row_extra<RG>(), smem_probe) < 0) g >>= 1;
         switch (g) {
         case 8: rc = launch_doubles_f32<RG, ST, 8>(ctx, T, C, S, nvec, v0); break;
         case 4: rc = launch_doubles_f32<RG, ST, 4>(ctx, T, C, S, nvec, v0); break;
@@ -1039,7 +1267,7 @@ int sigma_groups(sci_ctx *ctx, const Tabs &T, const TS *tab, const TC *C, typena
         int g = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
         if (sizeof(TS) == 16 && g > 4) g = 4;
         size_t smem_probe = 0;  // shrink the vector group until its window fits
-        while (g > 1 && choose_rows(ctx->maxb2, g * sizeof(TS) + row_extra<RG>(), smem_probe) < 0) g >>= 1;
+        while (g > 1 && choose_rows(T.maxb_small, g * sizeof(TS) + row_extra<RG>(), smem_probe) < 0) g >>= 1;
         switch (g) {
         case 8: rc = launch_doubles<RG, ST, TS, TC, 8>(ctx, T, tab, C, S, nvec, v0); break;
         case 4: rc = launch_doubles<RG, ST, TS, TC, 4>(ctx, T, tab, C, S, nvec, v0); break;
@@ -1165,7 +1393,7 @@ bool sci_sigma_window_fits(const sci_ctx *ctx)
 {
     size_t smem = 0;
     const size_t per = (ctx->cplx ? sizeof(zdbl) : sizeof(double)) + row_extra<true>();
-    return ctx->e2 == 0 || choose_rows(ctx->maxb2, per, smem) >= 0;
+    return ctx->e2 == ctx->e2_big || choose_rows(ctx->maxb2_small, per, smem) >= 0;
 }
 
 namespace {

@@ -43,6 +43,7 @@ SIGNATURES = {
     "sci_diagonal": (_i32, [_vp, _vp]),
     "sci_sigma": (_i32, [_vp, _vp, _vp, _i32, _i32]),
     "sci_set_row_range": (_i32, [_vp, _i64, _i64]),
+    "sci_set_tile_threshold": (_i32, [_vp, _i32]),
     "sci_row_costs": (_i32, [_vp, _vp]),
     "sci_set_deterministic": (_i32, [_vp, _i32]),
     "sci_connections": (_i32, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _i64]),
@@ -169,6 +170,10 @@ def sci_sigma(ctx, C, S, nvec, prec):
 
 def sci_set_row_range(ctx, row_begin, row_end):
     return _check(ctx, load().sci_set_row_range(ctx, int(row_begin), int(row_end)))
+
+
+def sci_set_tile_threshold(ctx, members):
+    return _check(ctx, load().sci_set_tile_threshold(ctx, int(members)))
 
 
 def sci_set_deterministic(ctx, max_nvec: int):
@@ -510,6 +515,11 @@ class Hamiltonian:
         of S are left as they were); (0, M) returns to the whole list."""
         sci_set_row_range(self.ctx, row_begin, row_end)
         self.row_range = (int(row_begin), int(row_end))
+
+    def set_tile_threshold(self, members: int):
+        """(N-2) buckets of more than `members` members go through the tiled sigma kernel
+        (0 = the default, 2048)."""
+        sci_set_tile_threshold(self.ctx, members)
 
     def set_deterministic(self, max_nvec: int):
         """Later sigma calls with up to max_nvec vectors accumulate row sums in a fixed
