@@ -182,19 +182,19 @@ int sci_sigma(sci_ctx *ctx, const void *C, void *S, int nvec, int prec);
 int sci_set_row_range(sci_ctx *ctx, int64_t row_begin, int64_t row_end);
 
 /* Buckets walked in tiles.  The double excitations of sigma (Sec. 2.4) are summed per
- * (N-2)-hole bucket of the connection tables (the determinants that share N-2 electrons),
- * each bucket staged in shared memory beside a window of rows.  Buckets of more than `members` members (default
- * 2048; members = 0 restores it) are instead walked by a tiled kernel that takes 256 of a
- * bucket's members as rows per CTA and streams all its members through shared memory in
- * column tiles, so no bucket size is too large for sigma (up to the table format's 65,535
- * members).  Results are the same sums in another order: equal within rounding, and bit
- * for bit in deterministic mode.  With one-word keys no bucket exceeds 2,016 members, so
- * the default changes nothing there; two- and three-word lists and spaces of few
- * electrons reach larger buckets.  Density matrices (sci_rdm12) keep whole-bucket staging
- * and return SCI_ERR_OVERFLOW for a bucket that does not fit.  A threshold above what
- * the window kernels can stage returns SCI_ERR_OVERFLOW and keeps the previous one.
- * Synchronous (waits for the context stream; rebuilds the tile lists of the list and of
- * a row range).  Errors: SCI_ERR_ARG for members outside [0, 65535]. */
+ * (N-2)-hole bucket of the connection tables (the determinants that share N-2
+ * electrons), each bucket staged in shared memory beside a window of rows.  Buckets of
+ * more than `members` members (default 512; members = 0 restores it) are instead walked
+ * by a tiled kernel that takes 256 of a bucket's members as rows per CTA and streams all
+ * its members through shared memory in column tiles.  So no bucket is too large for sigma
+ * (up to the table format's 65,535 members), and a few large buckets no longer widen
+ * every window.  Results are the same sums in another order: equal within rounding, and
+ * the deterministic mode stays bit for bit reproducible at a fixed threshold.  Density
+ * matrices (sci_rdm12) keep whole-bucket staging and return SCI_ERR_OVERFLOW for a bucket
+ * that does not fit.  A threshold above what the window kernels can stage returns
+ * SCI_ERR_OVERFLOW and keeps the previous one.  Synchronous (waits for the context
+ * stream; rebuilds the tile lists of the list and of a row range).  Errors: SCI_ERR_ARG
+ * for members outside [0, 65535]. */
 int sci_set_tile_threshold(sci_ctx *ctx, int members);
 
 /* Deterministic accumulation for later sci_sigma() calls on this context.  By default

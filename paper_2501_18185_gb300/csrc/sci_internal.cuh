@@ -75,10 +75,12 @@ __host__ __device__ __forceinline__ uint32_t make_meta(int x, int par, int off, 
     return (uint32_t)x | ((uint32_t)par << 8) | ((uint32_t)off << 9) | ((uint32_t)size << 20);
 }
 constexpr int kMaxBucket1 = 2047;   // the largest (N-1) bucket the meta word holds
-// (N-2) buckets of more members than this go through the tiled sigma kernel by default
-// (with one-word keys a bucket holds at most C(64 - N + 2, 2) <= 2016 members, so
-// one-word lists never do)
-constexpr int kTileBucket = 2048;
+// (N-2) buckets of more members than this go through the tiled sigma kernel by default.
+// Measured on 2M-determinant spaces (doubles kernel, FP64, one vector): buckets of up to
+// 1,089 (80 spin-orbitals) 12.04 ms all in windows, 9.12 ms with those above 512 tiled;
+// up to 4,489 (140 spin-orbitals) 25.8 ms at 2048, 20.2 ms at 512; a space whose buckets
+// stay below 512 (30 orbitals, up to 441) is unchanged, and tiling it at 256 costs 2%.
+constexpr int kTileBucket = 512;
 constexpr int kTileRows = 256;      // rows of a tile of the tiled kernel (one per thread)
 // whether two members of a bucket share an extra orbital (then they are a single
 // excitation of each other, not a double); valid for orbitals up to 255

@@ -518,7 +518,7 @@ class Hamiltonian:
 
     def set_tile_threshold(self, members: int):
         """(N-2) buckets of more than `members` members go through the tiled sigma kernel
-        (0 = the default, 2048)."""
+        (0 = the default, 512)."""
         sci_set_tile_threshold(self.ctx, members)
 
     def set_deterministic(self, max_nvec: int):

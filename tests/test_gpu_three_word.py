@@ -131,10 +131,10 @@ def test_three_word_encodings_of_one_and_two_word_spaces(gpu):
 
 def test_three_word_spinors_one_and_two_electrons(gpu):
     """136 complex spinors (bits 0..135 over three words): one electron, sigma = h c; two
-    electrons on 4,000 of the 9,180 pairs (the whole pair space would put every determinant
-    in the one empty-string (N-2) bucket, past the shared-memory window), sigma against the
-    closed form with the Cholesky factors (no dense integrals; coefficients outside the list
-    are zero), two vectors, FP64 and paired FP32."""
+    electrons on 4,000 of the 9,180 pairs (the whole pair space, one (N-2) bucket of 9,180
+    members, is a case of the tiled-walk tests), sigma against the closed form with the
+    Cholesky factors (no dense integrals; coefficients outside the list are zero), two
+    vectors, FP64 and paired FP32."""
     torch = gpu
     n = 136
     ints = W.complex_integrals(np.random.default_rng(91), n, 6, 0.9)
