@@ -676,7 +676,11 @@ struct PolDSZ {   // paired FP32, complex (the k_doubles_dsz arithmetic)
 // shared memory of the tiled kernel: at most this, which needs no opt-in
 constexpr size_t kTiledSmem = 48 * 1024;
 
-// C holds coefficient v of determinant I at C[I * cstride + coff + v]
+// C holds coefficient v of determinant I at C[I * cstride + coff + v].  With few tiles
+// (a handful of very large buckets) the columns of a bucket are also split: CTA row y of
+// the grid (gridDim.y = nsplit) takes the y-th of nsplit equal runs of column tiles and
+// adds its partial row sums atomically (nsplit = 1 in the deterministic mode, where one
+// CTA writes a slot).
 template <class P, int NV, bool RANGED, bool STORE>
 __global__ void __launch_bounds__(kThreads)
 k_doubles_tiled(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e_code,
@@ -685,6 +689,7 @@ k_doubles_tiled(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__
                 int cstride, int coff, int nvec, int v0, typename P::TO *__restrict__ Sout, sci::RowRange rr,
                 const uint32_t *__restrict__ slot)
 {
+    const int nsplit = STORE ? 1 : (int)gridDim.y;
     using SC = typename P::SC;
     using TT = typename P::TT;
     using ACC = typename P::ACC;
@@ -696,6 +701,10 @@ k_doubles_tiled(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__
         const uint32_t pos0 = e_pos[r0];
         const int64_t bs = r0 - sci::pos_off(pos0);
         const int bsize = sci::pos_size(pos0);
+        // this CTA's column tiles: [c_lo, c_hi) in members of the bucket
+        const int nct = (bsize + TCOL - 1) / TCOL, per_split = (nct + nsplit - 1) / nsplit;
+        const int c_lo = (int)blockIdx.y * per_split * TCOL, c_hi = min(bsize, c_lo + per_split * TCOL);
+        if (c_lo >= c_hi) continue;   // uniform over the CTA
         const int64_t row = r0 + threadIdx.x;
         bool active = row < bs + bsize;
         if (RANGED && active) {
@@ -717,8 +726,8 @@ k_doubles_tiled(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__
         ACC acc[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) P::clear(acc[v]);
-        for (int cs = 0; cs < bsize; cs += TCOL) {
-            const int n = min(TCOL, bsize - cs);
+        for (int cs = c_lo; cs < c_hi; cs += TCOL) {
+            const int n = min(TCOL, c_hi - cs);
             __syncthreads();   // every thread is done with the previous column tile
             for (int q = threadIdx.x; q < n; q += blockDim.x) {
                 const int64_t g = bs + cs + q;
@@ -1050,7 +1059,15 @@ int launch_tiled(sci_ctx *ctx, const Tabs &T, const typename P::TT *tab, const t
     int tcol = (int)std::min<size_t>(1024, (kTiledSmem - 16) / per) & ~31;
     const size_t smem = (((size_t)tcol * NV * sizeof(typename P::SC) + 15) & ~(size_t)15) + (size_t)tcol * sizeof(uint2);
     const int64_t grid = std::min<int64_t>(T.ntiles, 152 * 16);
-    k_doubles_tiled<P, NV, RG, ST><<<(unsigned)grid, kThreads, smem, ctx->stream>>>(
+    // few tiles: split the columns too, up to the column tiles of the largest bucket, for
+    // about 8 CTAs per SM (not in the deterministic mode, whose slots have one writer)
+    int nsplit = 1;
+    if (!ST && T.ntiles < 152 * 8) {
+        const int64_t want = (152 * 8 + T.ntiles - 1) / T.ntiles;
+        const int64_t most = (ctx->maxb2 + tcol - 1) / tcol;
+        nsplit = (int)std::max<int64_t>(1, std::min<int64_t>({want, most, 65535}));
+    }
+    k_doubles_tiled<P, NV, RG, ST><<<dim3((unsigned)grid, (unsigned)nsplit), kThreads, smem, ctx->stream>>>(
         T.e2_idx, T.e2_code, T.e2_pos, T.tiles, T.ntiles, tcol, tab_rule(ctx), tab, C, cstride, coff, nvec, v0, S,
         T.rr, ST ? ctx->det_inv2 : nullptr);
     return sci_cuda_check(ctx, cudaGetLastError(), "k_doubles_tiled launch");
