@@ -144,10 +144,10 @@ int sci_set_determinants(sci_ctx *ctx, const uint64_t *keys, int64_t M, int n_al
  * the orbitals (64 nwords >= 2n, or >= n spinors; SCI_ERR_ARG otherwise).  The bucket keys
  * are then (64 x nwords)-bit, sorted by nwords stable radix passes.  Sigma (every precision
  * mode, deterministic mode included), the diagonal, pair counts, row costs, the connection
- * exports and row ranges (sci_set_row_range) work on two- and three-word lists as on one
- * word; the density matrices (sci_rdm12, sci_rdm_grads) and ENPT2 (sci_enpt2) take one-
- * and two-word lists (up to 128 spin-orbitals or spinors; SCI_ERR_ARG for three words);
- * batches need one-word keys (SCI_ERR_ARG).  sci_set_determinants (one word) returns
+ * exports, row ranges (sci_set_row_range) and the density matrices (sci_rdm12,
+ * sci_rdm_grads) work on two- and three-word lists as on one word; ENPT2 (sci_enpt2)
+ * takes one- and two-word lists (up to 128 spin-orbitals or spinors; SCI_ERR_ARG for three
+ * words); batches need one-word keys (SCI_ERR_ARG).  sci_set_determinants (one word) returns
  * SCI_ERR_ARG when the orbitals do not fit one word.  Errors as sci_set_determinants. */
 int sci_set_determinants_w(sci_ctx *ctx, const uint64_t *keys, int nwords, int64_t M, int n_alpha,
                            int n_beta, int keys_on_device);
@@ -288,7 +288,7 @@ int sci_kernel_times(sci_ctx *ctx, float *ms, int n);
  *   rdm1[p][q]       = sum_k w_k <c_k| a+_p a_q |c_k>
  *   rdm2[p][q][r][s] = sum_k w_k <c_k| a+_p a+_r a_s a_q |c_k>
  * over the norb = 2n spin-orbitals (spin-orbital mode, bit order of the keys) or the n
- * spinors, norb <= 128 (one- or two-word keys), unnormalised: for a normalised c the
+ * spinors, norb <= 192 (one- to three-word keys), unnormalised: for a normalised c the
  * energy of Eq. Hamiltonian is
  * sum h_pq rdm1_pq + 1/2 sum (pq|rs) rdm2_pqrs (spin-orbital integrals).
  *   C: device, [M][nvec], double (real mode) or complex128 (complex mode), nvec >= 1.

@@ -97,24 +97,33 @@ template <int KW> __device__ __forceinline__ bool occ(const Str<KW> &s, int p)
 {
     return (s.w[p >> 6] >> (p & 63)) & 1;
 }
+// the reference string (lowest orbitals occupied) in three words, orbitals 64w .. 64w + 63
+struct Ref3 {
+    uint64_t w[3];
+};
+Ref3 ref3(const sci_ctx *ctx) { return Ref3{{ctx->ref, ctx->ref_hi, ctx->ref_w2}}; }
 
 // Diagonal class: O[p][r] = sum_I w_I n_p n_r in the reference decomposition n = n_ref + d
 // (d = key ^ ref has a few bits), accumulated per CTA in shared memory ([norb]^2 doubles,
-// dynamic: up to 128 KB for 128 spin-orbitals).
-template <typename TC, int KW>
+// dynamic: up to 226 KB, 168 spin-orbitals) when SM, else straight into DD and D in
+// global memory (more orbitals).
+template <typename TC, int KW, bool SM = true>
 __global__ void __launch_bounds__(kThreads)
-k_rdm_diag(const uint64_t *__restrict__ keys, int64_t M, int norb, uint64_t ref, uint64_t ref_hi,
+k_rdm_diag(const uint64_t *__restrict__ keys, int64_t M, int norb, Ref3 ref,
            const TC *__restrict__ C, int nvec, int v0, int nv, const double *__restrict__ wk, double *__restrict__ Wt,
            double *__restrict__ D, double *__restrict__ DD)
 {
     extern __shared__ double s_dyn[];
-    double *sDD = s_dyn, *sD = s_dyn + norb * norb, *sW = sD + norb;
-    for (int i = threadIdx.x; i < norb * norb; i += blockDim.x) sDD[i] = 0.0;
-    for (int i = threadIdx.x; i < norb; i += blockDim.x) sD[i] = 0.0;
-    __syncthreads();
+    __shared__ double s_wsum[kThreads / 32];
+    double *sDD = SM ? s_dyn : DD, *sD = SM ? s_dyn + norb * norb : D, *sW = s_wsum;
+    if constexpr (SM) {
+        for (int i = threadIdx.x; i < norb * norb; i += blockDim.x) sDD[i] = 0.0;
+        for (int i = threadIdx.x; i < norb; i += blockDim.x) sD[i] = 0.0;
+        __syncthreads();
+    }
     Str<KW> rs;
-    rs.w[0] = ref;
-    if (KW > 1) rs.w[KW - 1] = ref_hi;
+#pragma unroll
+    for (int k = 0; k < KW; k++) rs.w[k] = ref.w[k];
     double wsum = 0.0;
     for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < M; I += (int64_t)gridDim.x * blockDim.x) {
         double w = 0.0;
@@ -144,17 +153,19 @@ k_rdm_diag(const uint64_t *__restrict__ keys, int64_t M, int norb, uint64_t ref,
         for (int i = 0; i < kThreads / 32; i++) t += sW[i];
         atomicAdd(Wt, t);
     }
-    for (int i = threadIdx.x; i < norb * norb; i += blockDim.x)
-        if (sDD[i] != 0.0) atomicAdd(DD + i, sDD[i]);
-    for (int i = threadIdx.x; i < norb; i += blockDim.x)
-        if (sD[i] != 0.0) atomicAdd(D + i, sD[i]);
+    if constexpr (SM) {
+        for (int i = threadIdx.x; i < norb * norb; i += blockDim.x)
+            if (sDD[i] != 0.0) atomicAdd(DD + i, sDD[i]);
+        for (int i = threadIdx.x; i < norb; i += blockDim.x)
+            if (sD[i] != 0.0) atomicAdd(D + i, sD[i]);
+    }
 }
 
 // ------------------------------------------------------------------ singles
 template <typename TC, int NV, int KW>
 __global__ void __launch_bounds__(kThreads)
 k_rdm_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S, const uint32_t *__restrict__ e_meta,
-              int64_t E, int norb, uint64_t ref, uint64_t ref_hi, const TC *__restrict__ C, int nvec, int v0,
+              int64_t E, int norb, Ref3 ref, const TC *__restrict__ C, int nvec, int v0,
               const double *__restrict__ wk, TC *__restrict__ A, TC *__restrict__ Bc)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
@@ -168,7 +179,7 @@ k_rdm_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e
         uint64_t part[KW], holes[KW];
 #pragma unroll
         for (int k = 0; k < KW; k++) {
-            const uint64_t Sk = e_S[p * KW + k], rk = k == 0 ? ref : ref_hi;
+            const uint64_t Sk = e_S[p * KW + k], rk = ref.w[k];
             part[k] = Sk & ~rk, holes[k] = rk & ~Sk;
         }
         const int64_t idx = e_idx[p];
@@ -256,21 +267,18 @@ k_rdm_doubles(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e
 // ------------------------------------------------------------------ expansion
 // g1 and the g2 elements of the diagonal and single-excitation classes; one thread per
 // (x, y)
-// occupation of orbital k in the reference (ref: orbitals 0..63, ref_hi: 64..127)
-__device__ __forceinline__ double ref_occ(uint64_t ref, uint64_t ref_hi, int k)
-{
-    return (double)(k < 64 ? (ref >> k) & 1 : (ref_hi >> (k - 64)) & 1);
-}
+// occupation of orbital k in the reference
+__device__ __forceinline__ double ref_occ(const Ref3 &ref, int k) { return (double)((ref.w[k >> 6] >> (k & 63)) & 1); }
 
 template <typename TC>
-__global__ void k_rdm_expand1(int norb, uint64_t ref, uint64_t ref_hi, const double *__restrict__ Wt,
+__global__ void k_rdm_expand1(int norb, Ref3 ref, const double *__restrict__ Wt,
                               const double *__restrict__ D, const double *__restrict__ DD, const TC *__restrict__ A,
                               const TC *__restrict__ Bc, TC *__restrict__ g1, TC *__restrict__ g2)
 {
     const int64_t n2 = (int64_t)norb * norb, n3 = n2 * norb;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n2; t += (int64_t)gridDim.x * blockDim.x) {
         const int x = (int)(t / norb), y = (int)(t % norb);
-        const double nx = ref_occ(ref, ref_hi, x), ny = ref_occ(ref, ref_hi, y);
+        const double nx = ref_occ(ref, x), ny = ref_occ(ref, y);
         const double O = *Wt * nx * ny + nx * D[y] + D[x] * ny + DD[t];
         const TC o = from_real<TC>(O);
         if (x == y) {
@@ -284,7 +292,7 @@ __global__ void k_rdm_expand1(int norb, uint64_t ref, uint64_t ref_hi, const dou
         g2[(int64_t)x * n3 + (int64_t)y * n2 + (int64_t)y * norb + x] = neg(o);    // (x y | y x)
         for (int k = 0; k < norb; k++) {
             if (k == x || k == y) continue;
-            const TC b = add(scale(a, ref_occ(ref, ref_hi, k)), Bc[t * norb + k]);
+            const TC b = add(scale(a, ref_occ(ref, k)), Bc[t * norb + k]);
             const TC nb = neg(b);
             g2[(int64_t)x * n3 + (int64_t)y * n2 + (int64_t)k * norb + k] = b;     // (x y | k k)
             g2[(int64_t)k * n3 + (int64_t)k * n2 + (int64_t)x * norb + y] = b;     // (k k | x y)
@@ -362,9 +370,11 @@ template <typename TC, int NV>
 int launch_walks(sci_ctx *ctx, const Walk<TC> &w)
 {
     if (ctx->e1 > 0) {
-        auto ks = ctx->nwords == 2 ? k_rdm_singles<TC, NV, 2> : k_rdm_singles<TC, NV, 1>;
+        auto ks = ctx->nwords == 3   ? k_rdm_singles<TC, NV, 3>
+                  : ctx->nwords == 2 ? k_rdm_singles<TC, NV, 2>
+                                     : k_rdm_singles<TC, NV, 1>;
         ks<<<grid_for(ctx->e1), kThreads, 0, ctx->stream>>>(ctx->e1_idx, ctx->e1_S, ctx->e1_meta, ctx->e1, ctx->norb,
-                                                            ctx->ref, ctx->ref_hi, w.C, w.nvec, w.v0, w.wk, w.A, w.Bc);
+                                                            ref3(ctx), w.C, w.nvec, w.v0, w.wk, w.A, w.Bc);
     }
     if (w.dT) {
         auto kern = k_rdm_doubles<TC, NV>;
@@ -415,19 +425,21 @@ int rdm_run(sci_ctx *ctx, const TC *C, int nvec, const double *wk_dev, TC *g1, T
     while (kv > 1 && stage_bytes(kv) > 200 * 1024) kv >>= 1;
     if (g2 && ctx->e2 > 0 && stage_bytes(kv) > 200 * 1024)
         return sci_fail(ctx, SCI_ERR_OVERFLOW, "rdm12: largest bucket too large for shared memory");
-    // the diagonal kernel's shared memory: DD [norb]^2, D [norb] and the warp sums
-    const size_t diag_smem = sizeof(double) * ((size_t)norb * norb + norb + kThreads / 32);
-    {
-        auto kd = ctx->nwords == 2 ? k_rdm_diag<TC, 2> : k_rdm_diag<TC, 1>;
-        if (sci_cuda_check(ctx, cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diag_smem),
-                           "rdm12 diag attr"))
-            return SCI_ERR_CUDA;
-    }
+    // the diagonal kernel: DD [norb]^2 and D [norb] in shared memory while they fit (up to
+    // 168 orbitals), else accumulated in global memory
+    size_t diag_smem = sizeof(double) * ((size_t)norb * norb + norb);
+    const bool diag_sm = diag_smem + 1024 <= 227 * 1024;
+    auto kd = ctx->nwords == 3 ? (diag_sm ? k_rdm_diag<TC, 3, true> : k_rdm_diag<TC, 3, false>)
+              : ctx->nwords == 2 ? k_rdm_diag<TC, 2, true>
+                                 : k_rdm_diag<TC, 1, true>;
+    if (!diag_sm) diag_smem = 0;
+    if (diag_sm && sci_cuda_check(ctx, cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                            (int)diag_smem), "rdm12 diag attr"))
+        return SCI_ERR_CUDA;
     for (int v0 = 0; v0 < nvec; v0 += kv) {
         const int nv = std::min(kv, nvec - v0);
-        auto kd = ctx->nwords == 2 ? k_rdm_diag<TC, 2> : k_rdm_diag<TC, 1>;
-        kd<<<grid_for(ctx->M), kThreads, diag_smem, ctx->stream>>>(ctx->keys, ctx->M, norb, ctx->ref, ctx->ref_hi, C,
-                                                                   nvec, v0, nv, wk_dev, Wt, D, DD);
+        kd<<<grid_for(ctx->M), kThreads, diag_smem, ctx->stream>>>(ctx->keys, ctx->M, norb, ref3(ctx), C, nvec, v0,
+                                                                   nv, wk_dev, Wt, D, DD);
         const Walk<TC> wlk{C, nvec, v0, wk_dev, A, Bc, g2 && ctx->e2 > 0 ? dT : nullptr, CH, stage_bytes(nv), tr, bb_off};
         int rc = SCI_OK;
         switch (nv) {
@@ -442,7 +454,7 @@ int rdm_run(sci_ctx *ctx, const TC *C, int nvec, const double *wk_dev, TC *g1, T
         }
         if (rc) return rc;
     }
-    k_rdm_expand1<TC><<<grid_for(n2), kThreads, 0, ctx->stream>>>(norb, ctx->ref, ctx->ref_hi, Wt, D, DD, A, Bc, g1, g2);
+    k_rdm_expand1<TC><<<grid_for(n2), kThreads, 0, ctx->stream>>>(norb, ref3(ctx), Wt, D, DD, A, Bc, g1, g2);
     if (g2) k_rdm_expand2<TC><<<grid_for(nT), kThreads, 0, ctx->stream>>>(tr, norb, nT, dT, g2);
     return sci_cuda_check(ctx, cudaGetLastError(), "rdm12 launch") ? SCI_ERR_CUDA : SCI_OK;
 }
@@ -557,7 +569,7 @@ extern "C" int sci_rdm12(sci_ctx *ctx, const void *C, int nvec, const double *we
     if (!ctx) return SCI_ERR_ARG;
     if (!ctx->have_ints || !ctx->have_dets) return sci_fail(ctx, SCI_ERR_STATE, "rdm12: integrals and determinants first");
     if (nvec < 1 || !rdm1 || (ctx->M > 0 && !C)) return sci_fail(ctx, SCI_ERR_ARG, "rdm12: need nvec >= 1, C and rdm1");
-    if (ctx->norb > 128 || ctx->nwords > 2) return sci_fail(ctx, SCI_ERR_ARG, "rdm12: at most 128 orbitals (two words)");
+    if (ctx->norb > 192 || ctx->nwords > 3) return sci_fail(ctx, SCI_ERR_ARG, "rdm12: at most 192 orbitals");
     if (sci_cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) return SCI_ERR_CUDA;
     // weights to the device (a host array of nvec doubles, NULL = all ones)
     const size_t wbytes = sizeof(double) * nvec;

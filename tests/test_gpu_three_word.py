@@ -189,10 +189,75 @@ def test_three_word_full_size_sampled(gpu):
     H.sync_status()
 
 
+def test_three_word_rdm12_and_grads(gpu):
+    """Density matrices on 65 orbitals (130 spin-orbitals: alpha orbital 64 in word 1, beta
+    orbitals 63 and 64 at bits 128 and 129 of word 2), 2 + 1 electrons, the 10,500
+    determinants of HF, singles, doubles and triples, two weighted vectors, against the
+    oracle's per-vector matrices (1e-12); the spin sums and the Cholesky contraction of
+    sci_rdm_grads against numpy on them."""
+    torch = gpu
+    n = 65
+    w = W.selected_three_word(n=n, na=2, nb=1, M=10500, naux=8, nvec=2)
+    assert (w.keys[:, 2] != 0).any()
+    o = Oracle.from_workload(w)
+    H = sci.Hamiltonian.from_workload(w)
+    C = torch.from_numpy(np.ascontiguousarray(w.c)).cuda()
+    wt = np.array([1.0, -0.5])
+    g1, g2 = H.rdm12(C, weights=wt)
+    g1, g2 = g1.cpu().numpy(), g2.cpu().numpy()
+    r1 = np.zeros_like(g1)
+    r2 = np.zeros_like(g2)
+    for k in range(2):
+        a1, a2 = o.rdm12(w.c[:, k])
+        r1 += wt[k] * a1
+        r2 += wt[k] * a2
+        del a2
+    assert np.abs(g1 - r1).max() < 1e-12 * np.abs(r1).max()
+    assert np.abs(g2 - r2).max() < 1e-12 * np.abs(r2).max()
+    del g2
+    gamma, Gamma, gL = H.rdm_grads(C, weights=wt, chol=torch.from_numpy(w.ints.chol.copy()).cuda(), Gamma=True)
+    gr = r1[:n, :n] + r1[n:, n:]
+    Gr = r2[:n, :n, :n, :n] + r2[:n, :n, n:, n:] + r2[n:, n:, :n, :n] + r2[n:, n:, n:, n:]
+    del r2
+    assert np.abs(gamma.cpu().numpy() - gr).max() < 1e-12 * np.abs(gr).max()
+    assert np.abs(Gamma.cpu().numpy() - Gr).max() < 1e-12 * np.abs(Gr).max()
+    L = w.ints.chol
+    ref = (Gr.reshape(n * n, n * n) @ L.reshape(L.shape[0], n * n).T).T.reshape(L.shape[0], n, n)
+    assert np.abs(gL.cpu().numpy() - ref).max() < 1e-12 * np.abs(ref).max()
+    H.sync_status()
+
+
+def test_three_word_rdm12_172_spin_orbitals_global_diagonal(gpu):
+    """172 spin-orbitals (86 orbitals, 2 + 2 electrons, 40,000 determinants): the diagonal
+    class's [norb]^2 sums no longer fit shared memory and go to global memory.  On the
+    device: the energy identity sum h g1 + 1/2 sum (pq|rs) g2 = c^+ H c against sigma, the
+    traces N and N(N - 1), and Hermiticity of g1."""
+    torch = gpu
+    n = 86
+    w = W.selected_three_word(n=n, na=2, nb=2, M=40000, naux=6)
+    H = sci.Hamiltonian.from_workload(w)
+    c = torch.from_numpy(np.ascontiguousarray(w.c[:, 0])).cuda()
+    c = c / torch.linalg.vector_norm(c)
+    g1, g2 = H.rdm12(c.reshape(-1, 1))
+    h = torch.from_numpy(w.ints.h).cuda()
+    L = torch.from_numpy(w.ints.chol).cuda()
+    eri = torch.einsum("Ppq,Prs->pqrs", L, L)
+    E1 = (h * g1[:n, :n]).sum() + (h * g1[n:, n:]).sum()
+    G = g2.reshape(2, n, 2, n, 2, n, 2, n)
+    E2 = sum((eri * G[a, :, a, :, b, :, b, :]).sum() for a in range(2) for b in range(2))
+    E = float(E1 + 0.5 * E2)
+    ref = float((c * H.sigma(c)).sum())
+    assert abs(E - ref) < 1e-11 * max(1.0, abs(ref))
+    assert abs(float(torch.trace(g1)) - 4) < 1e-12
+    assert abs(float(torch.einsum("pprr->", g2)) - 12) < 1e-10
+    assert float((g1 - g1.T).abs().max()) < 1e-14
+    H.sync_status()
+
+
 def test_three_word_limits_and_rejections(gpu, sel3w):
     """Keys of too few words for the orbital count, keys out of 192-bit order, orbital
-    counts above three words, and the parts that take at most two words (density
-    matrices, ENPT2, the batch) are refused with an error, never a wrong result."""
+    counts above three words, and ENPT2 (at most two words) are refused with an error,
+    never a wrong result."""
     torch = gpu
     w, o = sel3w
     H = sci.Hamiltonian.from_workload(w)
@@ -204,8 +269,6 @@ def test_three_word_limits_and_rejections(gpu, sel3w):
         H.set_determinants(bad, 3, 3)            # not ascending as 192-bit integers
     H.set_determinants(w.keys, 3, 3)
     C = torch.from_numpy(np.ascontiguousarray(w.c[:, :1])).cuda()
-    with pytest.raises(sci.SciError):
-        H.rdm12(C)
     with pytest.raises(sci.SciError):
         H.enpt2(C, [-10.0])
     H2 = sci.Hamiltonian()

@@ -127,3 +127,71 @@ def test_spinor_closed_forms_against_the_oracle():
     c2 = rng.standard_normal((len(pairs), 2)) + 1j * rng.standard_normal((len(pairs), 2))
     ref = spinor_pair_sigma(ints.h, ints.chol, pairs, c2)
     assert np.abs(o2.sigma(c2) - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def _spin_block_energy(h, eri, g1, g2):
+    """sum h g1 + 1/2 sum (pq|rs) g2 over spin-orbitals p = (sigma, p'), with the spin-orbital
+    integrals of a spin-free H: h and (pq|rs) inside each spin block, zero across."""
+    n = h.shape[0]
+    E1 = np.einsum("pq,pq->", h, g1[:n, :n]) + np.einsum("pq,pq->", h, g1[n:, n:])
+    G = g2.reshape(2, n, 2, n, 2, n, 2, n)
+    E2 = sum(np.einsum("pqrs,pqrs->", eri, G[a, :, a, :, b, :, b, :]) for a in range(2) for b in range(2))
+    return E1 + 0.5 * E2
+
+
+def test_rdm12_three_words_energy_traces_and_symmetries_65_orbitals():
+    """The oracle's density matrices on 65 orbitals (130 spin-orbitals: alpha 64 in word 1,
+    beta 63..64 at bits 128..129 of word 2), HF and 400 random 2 alpha + 1 beta
+    determinants: the energy identity against c^+ H c with the oracle's sigma (pinned above
+    by the closed forms), the traces N and N(N - 1), Hermiticity of g1 and the pair
+    symmetries of g2 on sampled elements."""
+    n, na, nb = 65, 2, 1
+    ints = _ints(n, 97, naux=4)
+    h, eri = ints.h, ints.eri()
+    rng = np.random.default_rng(98)
+    occ = {(tuple(range(na)), tuple(range(nb)))}
+    while len(occ) < 401:
+        occ.add((tuple(sorted(rng.choice(n, na, replace=False))), tuple(sorted(rng.choice(n, nb, replace=False)))))
+    occ = sorted(occ)
+    keys = W.sort_words(_keys([a for a, _ in occ], [b for _, b in occ], n))
+    assert (keys[:, 2] != 0).any()
+    o = Oracle("spin_orbitals", n, h, eri, keys)
+    c = rng.standard_normal(len(keys))
+    c /= np.linalg.norm(c)
+    g1, g2 = o.rdm12(c)
+    E = _spin_block_energy(h, eri, g1, g2)
+    assert abs(E - np.vdot(c, o.sigma(c)[:, 0])) < 1e-11 * max(1.0, abs(E))
+    N = na + nb
+    assert abs(np.trace(g1) - N) < 1e-12
+    assert abs(np.einsum("pprr->", g2) - N * (N - 1)) < 1e-10
+    assert np.abs(g1 - g1.T).max() < 1e-14
+    idx = rng.integers(0, 2 * n, size=(20000, 4))
+    p, q, r, s = idx.T
+    assert np.abs(g2[p, q, r, s] - g2[r, s, p, q]).max() < 1e-14
+    assert np.abs(g2[p, q, r, s] - g2[q, p, s, r]).max() < 1e-14
+
+
+def test_rdm12_three_word_encoding_of_a_two_word_space():
+    """A 40-orbital two-word space given as three words (top word 0) has the density
+    matrices of its two-word encoding, bit for bit on one thread."""
+    import oracle
+
+    n = 40
+    rng = np.random.default_rng(99)
+    occ = {((0, 1), (0,))}
+    while len(occ) < 500:
+        occ.add((tuple(sorted(rng.choice(n, 2, replace=False))), tuple(sorted(rng.choice(n, 1, replace=False)))))
+    occ = np.array([list(a) + [b[0] + n] for a, b in sorted(occ)])
+    k2 = W.sort_words(W.words_from_occ(occ, 2))
+    k3 = np.concatenate([k2, np.zeros((len(k2), 1), dtype=np.uint64)], axis=1)
+    ints = _ints(n, 100, naux=4)
+    c = rng.standard_normal(len(k2))
+    o2 = Oracle("spin_orbitals", n, ints.h, ints.eri(), k2)
+    o3 = Oracle("spin_orbitals", n, ints.h, ints.eri(), k3)
+    oracle.set_threads(1)
+    try:
+        a1, a2 = o2.rdm12(c)
+        b1, b2 = o3.rdm12(c)
+    finally:
+        oracle.set_threads(0)
+    assert np.array_equal(a1, b1) and np.array_equal(a2, b2)
