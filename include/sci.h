@@ -184,9 +184,11 @@ int sci_set_row_range(sci_ctx *ctx, int64_t row_begin, int64_t row_end);
 /* Buckets walked in tiles.  The double excitations of sigma (Sec. 2.4) are summed per
  * (N-2)-hole bucket of the connection tables (the determinants that share N-2
  * electrons), each bucket staged in shared memory beside a window of rows.  Buckets of
- * more than `members` members (default 512; members = 0 restores it) are instead walked
- * by a tiled kernel that takes 256 of a bucket's members as rows per CTA and streams all
- * its members through shared memory in column tiles.  So no bucket is too large for sigma
+ * more than `members` members are instead walked by a tiled kernel that takes 256 of a
+ * bucket's members as rows per CTA and streams all its members through shared memory in
+ * column tiles.  By default (members = 0) the threshold is 512 members, and 384 for
+ * launches that stage 64 bytes or more per window row (8 real vectors); a threshold set
+ * here applies to every launch.  So no bucket is too large for sigma
  * (up to the table format's 65,535 members), and a few large buckets no longer widen
  * every window.  Results are the same sums in another order: equal within rounding, and
  * the deterministic mode stays bit for bit reproducible at a fixed threshold.  Density

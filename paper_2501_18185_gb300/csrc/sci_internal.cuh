@@ -82,6 +82,25 @@ constexpr int kMaxBucket1 = 2047;   // the largest (N-1) bucket the meta word ho
 // stay below 512 (30 orbitals, up to 441) is unchanged, and tiling it at 256 costs 2%.
 constexpr int kTileBucket = 512;
 constexpr int kTileRows = 256;      // rows of a tile of the tiled kernel (one per thread)
+// launches that stage 64 bytes or more per window row (8 real vectors) tile from this
+// size instead (measured on the 30-orbital 2M space, buckets up to 441: FP64 x 8
+// 39.75 -> 38.66 ms, paired FP32 x 8 25.97 -> 22.52 ms; narrower launches lose 0-6%)
+constexpr int kTileBucketWide = 384;
+constexpr size_t kWideRowBytes = 64;
+
+// The split of an (N-2) table at one threshold: entries [0, big) are the buckets above it
+// (the table holds buckets largest first), their tiles are the first ntiles of the tile
+// list, and maxb_small is the largest bucket left to the window kernels.
+struct Split {
+    int64_t big = 0, ntiles = 0;
+    int maxb_small = 0;
+};
+// tile starts (table order) of the buckets above the lower of the two thresholds, and the
+// splits at the context's threshold (base) and at the wide-launch threshold (wide)
+struct TileSplit {
+    uint32_t *tiles = nullptr;
+    Split base, wide;
+};
 // whether two members of a bucket share an extra orbital (then they are a single
 // excitation of each other, not a double); valid for orbitals up to 255
 __host__ __device__ __forceinline__ bool codes_overlap(uint32_t a, uint32_t b)
@@ -173,19 +192,13 @@ struct sci_ctx {
     int maxb2 = 0, maxb1 = 0;
     int64_t pairs = 0, pairs2 = 0, pairs1 = 0;
 
-    // (N-2) buckets of more than tile_b members are walked by the tiled kernel (their
-    // members staged in shared memory a tile at a time) instead of the window kernels.
-    // Tables hold buckets largest first, so these are a prefix [0, e2_big) of the table;
-    // tiles2 lists the first entry of each tile of kTileRows rows (ntiles2 of them), and
-    // maxb2_small is the largest bucket left to the window kernels.  r2_big, rtiles2,
-    // nrtiles2 and rmaxb2_small are the same for the range tables.
+    // (N-2) buckets of more than tile_b members (min(tile_b, kTileBucketWide) for wide
+    // launches, unless the caller set the threshold) are walked by the tiled kernel, their
+    // members staged in shared memory a tile at a time, instead of the window kernels:
+    // split2 for the full tables, rsplit2 for the range tables
     int tile_b = sci::kTileBucket;
-    int64_t e2_big = 0, ntiles2 = 0;
-    uint32_t *tiles2 = nullptr;
-    int maxb2_small = 0;
-    int64_t r2_big = 0, nrtiles2 = 0;
-    uint32_t *rtiles2 = nullptr;
-    int rmaxb2_small = 0;
+    int tile_user = 0;   // the threshold was set by sci_set_tile_threshold: one for all launches
+    sci::TileSplit split2, rsplit2;
 
     // row range of sci_sigma() (sci_set_row_range): when `ranged`, sigma computes rows
     // [row_b, row_e) only, walking range tables r2_* / r1_* that keep (whole, in table
@@ -245,9 +258,8 @@ void sci_free_range(sci_ctx *ctx);
 // deterministic accumulation (sci_rows.cu): frees its index and buffers, back to atomics
 void sci_free_det(sci_ctx *ctx);
 
-// the tiled prefix of the full (ranged = false) or range tables for the context's tile_b:
-// e2_big / r2_big, the tile list and the largest bucket left to the window kernels
-// (sci_setup.cu); synchronous
+// the tiled prefixes of the full (ranged = false) or range tables for the context's
+// thresholds: split2 / rsplit2 (sci_setup.cu); synchronous
 int sci_table_split(sci_ctx *ctx, bool ranged);
 void sci_free_split(sci_ctx *ctx, bool ranged);
 

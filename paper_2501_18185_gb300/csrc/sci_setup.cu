@@ -725,13 +725,36 @@ __global__ void k_tile_fill(const uint32_t *__restrict__ flag, const uint32_t *_
 
 void sci_free_split(sci_ctx *ctx, bool ranged)
 {
-    uint32_t *&t = ranged ? ctx->rtiles2 : ctx->tiles2;
-    if (t) cudaFree(t);
-    t = nullptr;
-    (ranged ? ctx->r2_big : ctx->e2_big) = 0;
-    (ranged ? ctx->nrtiles2 : ctx->ntiles2) = 0;
-    (ranged ? ctx->rmaxb2_small : ctx->maxb2_small) = 0;
+    sci::TileSplit &sp = ranged ? ctx->rsplit2 : ctx->split2;
+    if (sp.tiles) cudaFree(sp.tiles);
+    sp = sci::TileSplit{};
 }
+
+namespace {
+// the split at threshold thr: the end of the prefix of buckets above thr and the largest
+// bucket after it
+int split_point(sci_ctx *ctx, const uint32_t *e_pos, int64_t E, int thr, sci::Split &out)
+{
+    cudaStream_t st = ctx->stream;
+    TmpBuf cnt;
+    unsigned long long h[2] = {0, 0};
+    SCI_CK(cudaMalloc(&cnt.p, 16));
+    SCI_CK(cudaMemsetAsync(cnt.p, 0, 16, st));
+    k_split_point<<<grid_for(E), 256, 0, st>>>(e_pos, E, thr, cnt.as<unsigned long long>());
+    SCI_CK(cudaGetLastError());
+    SCI_CK(cudaMemcpyAsync(h, cnt.p, 16, cudaMemcpyDeviceToHost, st));
+    SCI_CK(cudaStreamSynchronize(st));
+    if (h[1] != 0) return sci_fail(ctx, SCI_ERR_STATE, "internal: (N-2) buckets not in size order");
+    out.big = (int64_t)h[0];
+    out.maxb_small = 0;
+    if (out.big < E) {
+        uint32_t pos = 0;
+        SCI_CK(cudaMemcpy(&pos, e_pos + out.big, 4, cudaMemcpyDeviceToHost));
+        out.maxb_small = sci::pos_size(pos);
+    }
+    return SCI_OK;
+}
+}  // namespace
 
 int sci_table_split(sci_ctx *ctx, bool ranged)
 {
@@ -740,25 +763,14 @@ int sci_table_split(sci_ctx *ctx, bool ranged)
     const int64_t E = ranged ? ctx->r2 : ctx->e2;
     if (E == 0) return SCI_OK;
     cudaStream_t st = ctx->stream;
-    TmpBuf cnt, flag, at, tmp;
-    unsigned long long h[2] = {0, 0};
-    SCI_CK(cudaMalloc(&cnt.p, 16));
-    SCI_CK(cudaMemsetAsync(cnt.p, 0, 16, st));
-    k_split_point<<<grid_for(E), 256, 0, st>>>(e_pos, E, ctx->tile_b, cnt.as<unsigned long long>());
-    SCI_CK(cudaGetLastError());
-    SCI_CK(cudaMemcpyAsync(h, cnt.p, 16, cudaMemcpyDeviceToHost, st));
-    SCI_CK(cudaStreamSynchronize(st));
-    if (h[1] != 0) return sci_fail(ctx, SCI_ERR_STATE, "internal: (N-2) buckets not in size order");
-    const int64_t big = (int64_t)h[0];
-    int maxb_small = 0;
-    if (big < E) {
-        uint32_t pos = 0;
-        SCI_CK(cudaMemcpy(&pos, e_pos + big, 4, cudaMemcpyDeviceToHost));
-        maxb_small = sci::pos_size(pos);
-    }
-    int64_t ntiles = 0;
-    uint32_t *tiles = nullptr;
+    sci::TileSplit sp;
+    const int thr_wide = ctx->tile_user ? ctx->tile_b : std::min(ctx->tile_b, sci::kTileBucketWide);
+    int rc = split_point(ctx, e_pos, E, ctx->tile_b, sp.base);
+    if (rc == SCI_OK) rc = split_point(ctx, e_pos, E, thr_wide, sp.wide);
+    if (rc != SCI_OK) return rc;
+    const int64_t big = sp.wide.big;   // >= sp.base.big: the lower threshold tiles more
     if (big > 0) {
+        TmpBuf flag, at, tmp;
         const int nitems = (int)big;
         SCI_CK(cudaMalloc(&flag.p, (size_t)big * 4));
         SCI_CK(cudaMalloc(&at.p, (size_t)big * 4));
@@ -767,24 +779,24 @@ int sci_table_split(sci_ctx *ctx, bool ranged)
         SCI_CK(cub::DeviceScan::ExclusiveSum(nullptr, tb, flag.as<uint32_t>(), at.as<uint32_t>(), nitems, st));
         SCI_CK(cudaMalloc(&tmp.p, std::max<size_t>(tb, 16)));
         SCI_CK(cub::DeviceScan::ExclusiveSum(tmp.p, tb, flag.as<uint32_t>(), at.as<uint32_t>(), nitems, st));
-        uint32_t last[2] = {0, 0};
+        uint32_t last[3] = {0, 0, 0};
         SCI_CK(cudaMemcpyAsync(&last[0], at.as<uint32_t>() + (big - 1), 4, cudaMemcpyDeviceToHost, st));
         SCI_CK(cudaMemcpyAsync(&last[1], flag.as<uint32_t>() + (big - 1), 4, cudaMemcpyDeviceToHost, st));
+        if (sp.base.big < big)   // the tiles of the base prefix: those starting before its end
+            SCI_CK(cudaMemcpyAsync(&last[2], at.as<uint32_t>() + sp.base.big, 4, cudaMemcpyDeviceToHost, st));
         SCI_CK(cudaStreamSynchronize(st));
-        ntiles = (int64_t)last[0] + last[1];
-        SCI_CK(cudaMalloc(&tiles, (size_t)ntiles * 4));
-        k_tile_fill<<<grid_for(big), 256, 0, st>>>(flag.as<uint32_t>(), at.as<uint32_t>(), big, tiles);
+        sp.wide.ntiles = (int64_t)last[0] + last[1];
+        sp.base.ntiles = sp.base.big < big ? (int64_t)last[2] : sp.wide.ntiles;
+        SCI_CK(cudaMalloc(&sp.tiles, (size_t)sp.wide.ntiles * 4));
+        k_tile_fill<<<grid_for(big), 256, 0, st>>>(flag.as<uint32_t>(), at.as<uint32_t>(), big, sp.tiles);
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) {
-            cudaFree(tiles);
+            cudaFree(sp.tiles);
             return sci_cuda_check(ctx, e, "tile list");
         }
     }
-    (ranged ? ctx->r2_big : ctx->e2_big) = big;
-    (ranged ? ctx->rtiles2 : ctx->tiles2) = tiles;
-    (ranged ? ctx->nrtiles2 : ctx->ntiles2) = ntiles;
-    (ranged ? ctx->rmaxb2_small : ctx->maxb2_small) = maxb_small;
+    (ranged ? ctx->rsplit2 : ctx->split2) = sp;
     return SCI_OK;
 }
 
@@ -1244,15 +1256,16 @@ extern "C" int sci_set_tile_threshold(sci_ctx *ctx, int members)
     if (members < 0 || members > 0xFFFF) return sci_fail(ctx, SCI_ERR_ARG, "tile threshold outside [0, 65535]");
     SCI_CK(cudaSetDevice(ctx->device));
     SCI_CK(cudaStreamSynchronize(ctx->stream));   // no launch in flight reads the old tile lists
-    const int old = ctx->tile_b;
+    const int old = ctx->tile_b, old_user = ctx->tile_user;
     ctx->tile_b = members == 0 ? sci::kTileBucket : members;
+    ctx->tile_user = members != 0;
     if (!ctx->have_dets) return SCI_OK;
     int rc = sci_table_split(ctx, false);
     if (rc == SCI_OK && ctx->ranged) rc = sci_table_split(ctx, true);
     if (rc == SCI_OK && !sci_sigma_window_fits(ctx))
         rc = sci_fail(ctx, SCI_ERR_OVERFLOW, "buckets left to the window kernels do not fit shared memory");
     if (rc != SCI_OK) {   // back to the previous threshold, whose split was valid
-        ctx->tile_b = old;
+        ctx->tile_b = old, ctx->tile_user = old_user;
         sci_table_split(ctx, false);
         if (ctx->ranged) sci_table_split(ctx, true);
     }

@@ -1022,9 +1022,10 @@ sci::TabRule tab_rule(const sci_ctx *ctx) { return sci::TabRule{ctx->spinors, ct
 
 // The tables a sigma launch walks and the rows it computes: the full tables (every row),
 // or the range tables of sci_set_row_range() (rows [row_b, row_e)).
-// The (N-2) entries [0, e2_big) are the buckets of the tiled kernel (tile starts in
-// tiles[0, ntiles)); the window kernels walk [e2_big, e2), whose largest bucket is
-// maxb_small.
+// The (N-2) entries [0, sp.big) are the buckets of the tiled kernel (tile starts in
+// tiles[0, sp.ntiles)); the window kernels walk [sp.big, e2), whose largest bucket is
+// sp.maxb_small.  A launch takes the wide split when it stages kWideRowBytes or more per
+// window row.
 struct Tabs {
     const uint32_t *e2_idx, *e2_code, *e2_pos;
     int64_t e2;
@@ -1033,42 +1034,44 @@ struct Tabs {
     const uint32_t *e1_meta;
     int64_t e1;
     sci::RowRange rr;
-    int64_t e2_big;
-    const uint32_t *tiles;
-    int64_t ntiles;
-    int maxb_small;
+    const sci::TileSplit *ts;
+    const uint32_t *tiles() const { return ts->tiles; }
+    const sci::Split &split(size_t row_bytes) const
+    {
+        return row_bytes >= sci::kWideRowBytes ? ts->wide : ts->base;
+    }
+    int maxb_small() const { return ts->base.maxb_small; }   // the larger of the two
 };
 
 Tabs tabs_of(const sci_ctx *ctx)
 {
     if (ctx->ranged)
         return Tabs{ctx->r2_idx, ctx->r2_code, ctx->r2_pos, ctx->r2, ctx->r1_idx, ctx->r1_S, ctx->r1_meta, ctx->r1,
-                    sci::RowRange{ctx->row_b, ctx->row_e}, ctx->r2_big, ctx->rtiles2, ctx->nrtiles2,
-                    ctx->rmaxb2_small};
+                    sci::RowRange{ctx->row_b, ctx->row_e}, &ctx->rsplit2};
     return Tabs{ctx->e2_idx, ctx->e2_code, ctx->e2_pos, ctx->e2, ctx->e1_idx, ctx->e1_S, ctx->e1_meta, ctx->e1,
-                sci::RowRange{0, ctx->M}, ctx->e2_big, ctx->tiles2, ctx->ntiles2, ctx->maxb2_small};
+                sci::RowRange{0, ctx->M}, &ctx->split2};
 }
 
-// the tiled kernel over the buckets of [0, T.e2_big) (nothing when there are none)
+// the tiled kernel over the buckets of [0, sp.big) (nothing when there are none)
 template <class P, bool RG, bool ST, int NV>
-int launch_tiled(sci_ctx *ctx, const Tabs &T, const typename P::TT *tab, const typename P::CI *C, int cstride,
-                 int coff, int nvec, int v0, typename P::TO *S)
+int launch_tiled(sci_ctx *ctx, const Tabs &T, const sci::Split &sp, const typename P::TT *tab,
+                 const typename P::CI *C, int cstride, int coff, int nvec, int v0, typename P::TO *S)
 {
-    if (T.ntiles == 0) return SCI_OK;
+    if (sp.ntiles == 0) return SCI_OK;
     const size_t per = NV * sizeof(typename P::SC) + sizeof(uint2);
     int tcol = (int)std::min<size_t>(1024, (kTiledSmem - 16) / per) & ~31;
     const size_t smem = (((size_t)tcol * NV * sizeof(typename P::SC) + 15) & ~(size_t)15) + (size_t)tcol * sizeof(uint2);
-    const int64_t grid = std::min<int64_t>(T.ntiles, 152 * 16);
+    const int64_t grid = std::min<int64_t>(sp.ntiles, 152 * 16);
     // few tiles: split the columns too, up to the column tiles of the largest bucket, for
     // about 8 CTAs per SM (not in the deterministic mode, whose slots have one writer)
     int nsplit = 1;
-    if (!ST && T.ntiles < 152 * 8) {
-        const int64_t want = (152 * 8 + T.ntiles - 1) / T.ntiles;
+    if (!ST && sp.ntiles < 152 * 8) {
+        const int64_t want = (152 * 8 + sp.ntiles - 1) / sp.ntiles;
         const int64_t most = (ctx->maxb2 + tcol - 1) / tcol;
         nsplit = (int)std::max<int64_t>(1, std::min<int64_t>({want, most, 65535}));
     }
     k_doubles_tiled<P, NV, RG, ST><<<dim3((unsigned)grid, (unsigned)nsplit), kThreads, smem, ctx->stream>>>(
-        T.e2_idx, T.e2_code, T.e2_pos, T.tiles, T.ntiles, tcol, tab_rule(ctx), tab, C, cstride, coff, nvec, v0, S,
+        T.e2_idx, T.e2_code, T.e2_pos, T.tiles(), sp.ntiles, tcol, tab_rule(ctx), tab, C, cstride, coff, nvec, v0, S,
         T.rr, ST ? ctx->det_inv2 : nullptr);
     return sci_cuda_check(ctx, cudaGetLastError(), "k_doubles_tiled launch");
 }
@@ -1082,12 +1085,13 @@ int launch_doubles(sci_ctx *ctx, const Tabs &T, const TS *tab, const TC *C, type
                    int v0)
 {
     if (T.e2 == 0) return SCI_OK;
-    int rc = launch_tiled<PolF64<TS, TC>, RG, ST, NV>(ctx, T, tab, C, nvec, v0, nvec, v0, S);
-    const int64_t b = T.e2_big, E = T.e2 - b;
+    const size_t per = NV * sizeof(TS) + row_extra<RG>();
+    const sci::Split &sp = T.split(per);
+    int rc = launch_tiled<PolF64<TS, TC>, RG, ST, NV>(ctx, T, sp, tab, C, nvec, v0, nvec, v0, S);
+    const int64_t b = sp.big, E = T.e2 - b;
     if (rc != SCI_OK || E == 0) return rc;
-    size_t per = NV * sizeof(TS) + row_extra<RG>();
     size_t smem = 0;
-    int ch = choose_rows(T.maxb_small, per, smem);
+    int ch = choose_rows(sp.maxb_small, per, smem);
     if (ch < 0) return sci_fail(ctx, SCI_ERR_OVERFLOW, "bucket too large for shared memory");
     auto kern = k_doubles<TS, TC, NV, RG, ST>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1104,10 +1108,11 @@ template <bool RG, bool ST, bool CPLX, int NV>
 int launch_doubles_ds(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int nvec, int v0)
 {
     if (T.e2 == 0) return SCI_OK;
-    const int64_t b = T.e2_big, E = T.e2 - b;
-    size_t per = NV * (CPLX ? sizeof(float4) : sizeof(float2)) + row_extra<RG>();
+    const size_t per = NV * (CPLX ? sizeof(float4) : sizeof(float2)) + row_extra<RG>();
+    const sci::Split &sp = T.split(per);
+    const int64_t b = sp.big, E = T.e2 - b;
     size_t smem = 0;
-    int ch = E > 0 ? choose_rows(T.maxb_small, per, smem) : 0;
+    int ch = E > 0 ? choose_rows(sp.maxb_small, per, smem) : 0;
     if (ch < 0) return sci_fail(ctx, SCI_ERR_OVERFLOW, "bucket too large for shared memory");
     cudaError_t e;
     // the vector group, split into paired floats in the context's c_ds buffer
@@ -1120,11 +1125,11 @@ int launch_doubles_ds(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int n
                                                                        (float2 *)ctx->c_ds);
     int rc;
     if constexpr (CPLX)
-        rc = launch_tiled<PolDSZ, RG, ST, NV>(ctx, T, (const float4 *)ctx->tab_ds, (const float4 *)ctx->c_ds, NV, 0,
-                                              nvec, v0, (zdbl *)S);
+        rc = launch_tiled<PolDSZ, RG, ST, NV>(ctx, T, sp, (const float4 *)ctx->tab_ds, (const float4 *)ctx->c_ds, NV,
+                                              0, nvec, v0, (zdbl *)S);
     else
-        rc = launch_tiled<PolDS, RG, ST, NV>(ctx, T, (const float2 *)ctx->tab_ds, (const float2 *)ctx->c_ds, NV, 0,
-                                             nvec, v0, (double *)S);
+        rc = launch_tiled<PolDS, RG, ST, NV>(ctx, T, sp, (const float2 *)ctx->tab_ds, (const float2 *)ctx->c_ds, NV,
+                                             0, nvec, v0, (double *)S);
     if (rc != SCI_OK || E == 0) return rc;
     const int64_t blocks = (E + ch - 1) / ch;
     const uint32_t *slot = ST ? ctx->det_inv2 + b : nullptr;
@@ -1156,7 +1161,7 @@ int ds_groups(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int nvec)
         int g = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
         if (CPLX && g > 4) g = 4;
         size_t smem_probe = 0;
-        while (g > 1 && choose_rows(T.maxb_small, g * unit + row_extra<RG>(), smem_probe) < 0) g >>= 1;
+        while (g > 1 && choose_rows(T.maxb_small(), g * unit + row_extra<RG>(), smem_probe) < 0) g >>= 1;
         switch (g) {
         case 8: rc = launch_doubles_ds<RG, ST, CPLX, 8>(ctx, T, C, S, nvec, v0); break;
         case 4: rc = launch_doubles_ds<RG, ST, CPLX, 4>(ctx, T, C, S, nvec, v0); break;
@@ -1173,12 +1178,13 @@ template <bool RG, bool ST, int NV>
 int launch_doubles_f32(sci_ctx *ctx, const Tabs &T, const float *C, double *S, int nvec, int v0)
 {
     if (T.e2 == 0) return SCI_OK;
-    int rc = launch_tiled<PolF32, RG, ST, NV>(ctx, T, ctx->tab32, C, nvec, v0, nvec, v0, S);
-    const int64_t b = T.e2_big, E = T.e2 - b;
+    const size_t per = NV * sizeof(float) + row_extra<RG>();
+    const sci::Split &sp = T.split(per);
+    int rc = launch_tiled<PolF32, RG, ST, NV>(ctx, T, sp, ctx->tab32, C, nvec, v0, nvec, v0, S);
+    const int64_t b = sp.big, E = T.e2 - b;
     if (rc != SCI_OK || E == 0) return rc;
-    size_t per = NV * sizeof(float) + row_extra<RG>();
     size_t smem = 0;
-    int ch = choose_rows(T.maxb_small, per, smem, NV >= 8 ? SCI_F32_ROWS : kRowsPerCta);
+    int ch = choose_rows(sp.maxb_small, per, smem, NV >= 8 ? SCI_F32_ROWS : kRowsPerCta);
     if (ch < 0) return sci_fail(ctx, SCI_ERR_OVERFLOW, "bucket too large for shared memory");
     int64_t blocks = (E + ch - 1) / ch;
     auto kern = k_doubles_f32<NV, RG, ST>;
@@ -1198,7 +1204,7 @@ int f32_groups(sci_ctx *ctx, const Tabs &T, const float *C, double *S, int nvec)
         int left = nvec - v0;
         int g = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
         size_t smem_probe = 0;
-        while (g > 1 && choose_rows(T.maxb_small, g * sizeof(float) + row_extra<RG>(), smem_probe) < 0) g >>= 1;
+        while (g > 1 && choose_rows(T.maxb_small(), g * sizeof(float) + row_extra<RG>(), smem_probe) < 0) g >>= 1;
         switch (g) {
         case 8: rc = launch_doubles_f32<RG, ST, 8>(ctx, T, C, S, nvec, v0); break;
         case 4: rc = launch_doubles_f32<RG, ST, 4>(ctx, T, C, S, nvec, v0); break;
@@ -1284,7 +1290,7 @@ int sigma_groups(sci_ctx *ctx, const Tabs &T, const TS *tab, const TC *C, typena
         int g = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
         if (sizeof(TS) == 16 && g > 4) g = 4;
         size_t smem_probe = 0;  // shrink the vector group until its window fits
-        while (g > 1 && choose_rows(T.maxb_small, g * sizeof(TS) + row_extra<RG>(), smem_probe) < 0) g >>= 1;
+        while (g > 1 && choose_rows(T.maxb_small(), g * sizeof(TS) + row_extra<RG>(), smem_probe) < 0) g >>= 1;
         switch (g) {
         case 8: rc = launch_doubles<RG, ST, TS, TC, 8>(ctx, T, tab, C, S, nvec, v0); break;
         case 4: rc = launch_doubles<RG, ST, TS, TC, 4>(ctx, T, tab, C, S, nvec, v0); break;
@@ -1410,7 +1416,7 @@ bool sci_sigma_window_fits(const sci_ctx *ctx)
 {
     size_t smem = 0;
     const size_t per = (ctx->cplx ? sizeof(zdbl) : sizeof(double)) + row_extra<true>();
-    return ctx->e2 == ctx->e2_big || choose_rows(ctx->maxb2_small, per, smem) >= 0;
+    return ctx->e2 == ctx->split2.base.big || choose_rows(ctx->split2.base.maxb_small, per, smem) >= 0;
 }
 
 namespace {

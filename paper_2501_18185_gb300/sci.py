@@ -518,7 +518,7 @@ class Hamiltonian:
 
     def set_tile_threshold(self, members: int):
         """(N-2) buckets of more than `members` members go through the tiled sigma kernel
-        (0 = the default, 512)."""
+        (0 = the default: 512, or 384 for launches of 8 real vectors)."""
         sci_set_tile_threshold(self.ctx, members)
 
     def set_deterministic(self, max_nvec: int):
