@@ -146,8 +146,8 @@ int sci_set_determinants(sci_ctx *ctx, const uint64_t *keys, int64_t M, int n_al
  * mode, deterministic mode included), the diagonal, pair counts, row costs, the connection
  * exports, row ranges (sci_set_row_range) and the density matrices (sci_rdm12,
  * sci_rdm_grads) work on two- and three-word lists as on one word; ENPT2 (sci_enpt2)
- * takes one- and two-word lists (up to 128 spin-orbitals or spinors; SCI_ERR_ARG for three
- * words); batches need one-word keys (SCI_ERR_ARG).  sci_set_determinants (one word) returns
+ * takes one- and two-word lists, and three-word lists in spinor mode (SCI_ERR_ARG for a
+ * three-word spin-orbital list); batches need one-word keys (SCI_ERR_ARG).  sci_set_determinants (one word) returns
  * SCI_ERR_ARG when the orbitals do not fit one word.  Errors as sci_set_determinants. */
 int sci_set_determinants_w(sci_ctx *ctx, const uint64_t *keys, int nwords, int64_t M, int n_alpha,
                            int n_beta, int keys_on_device);
@@ -335,7 +335,9 @@ int sci_rdm_grads(sci_ctx *ctx, const double *C, int nvec, const double *weights
  * spin conservation, the 4C workloads of Sec. 4; batches by a code of the whole string;
  * the squares are |.|^2 of complex numerators), on one-word lists (n <= 32 spatial
  * orbitals or n <= 64 spinors) or two-word lists (sci_set_determinants_w: n <= 64 or
- * n <= 128; the table keys are then 128-bit, claimed by a 16-byte compare-and-swap).
+ * n <= 128; the table keys are then 128-bit, claimed by a 16-byte compare-and-swap), or
+ * three-word spinor lists (n <= 192, fewer than 64 electrons when n = 192: words 0-1 of a
+ * key are claimed by the 16-byte compare-and-swap and word 2 by an 8-byte one).
  * Spinor mode with real integrals returns SCI_ERR_ARG.
  *   C: device, [M][nroots] doubles (complex mode: complex128, interleaved), 1 <= nroots
  *      <= 8 (need not be normalised; the formulas use c as given, so pass normalised

@@ -67,12 +67,12 @@ constexpr int kMaxBits = 10;   // at most 1024 batches
 
 struct Pt2 {
     int n, norb, na, nb;
-    uint64_t ref, ref_hi;     // the reference string: orbitals 0..63 and 64..127
+    uint64_t ref, ref_hi, ref_w2;   // the reference string: orbitals 0..63, 64..127, 128..191
     const double *tab, *fref, *g_so;
     const double *fdiag, *G;  // [norb], [norb][norb]
     const double *Eref;
-    uint32_t gcode[128];      // codes of the beta orbitals (spin-orbital mode) or spinors
-    uint8_t obc[128];         // those orbitals sorted by code
+    uint32_t gcode[192];      // codes of the beta orbitals (spin-orbital mode) or spinors
+    uint8_t obc[192];         // those orbitals sorted by code
     uint8_t cstart[(1 << kMaxBits) + 1];  // first index in obc of each code
     uint64_t *tab2;           // slots of (key words, value words), key 0 = empty
     uint64_t mask;            // capacity - 1
@@ -128,41 +128,81 @@ __device__ __forceinline__ W2 operator>>(W2 a, int s)
     return W2(a.hi >> (s - 64), 0);
 }
 
+// three words (up to 192 spinors), written out the same way
+struct W3 {
+    uint64_t w0, w1, w2;
+    __host__ __device__ constexpr W3(uint64_t a = 0, uint64_t b = 0, uint64_t c = 0) : w0(a), w1(b), w2(c) {}
+    __device__ explicit operator bool() const { return (w0 | w1 | w2) != 0; }
+};
+__device__ __forceinline__ W3 operator&(W3 a, W3 b) { return W3(a.w0 & b.w0, a.w1 & b.w1, a.w2 & b.w2); }
+__device__ __forceinline__ W3 operator|(W3 a, W3 b) { return W3(a.w0 | b.w0, a.w1 | b.w1, a.w2 | b.w2); }
+__device__ __forceinline__ W3 operator~(W3 a) { return W3(~a.w0, ~a.w1, ~a.w2); }
+__device__ __forceinline__ W3 &operator&=(W3 &a, W3 b) { a.w0 &= b.w0, a.w1 &= b.w1, a.w2 &= b.w2; return a; }
+__device__ __forceinline__ bool operator==(W3 a, W3 b) { return a.w0 == b.w0 && a.w1 == b.w1 && a.w2 == b.w2; }
+// a - 1 (borrows through the words)
+__device__ __forceinline__ W3 operator-(W3 a, int one)
+{
+    const uint64_t u = (uint64_t)one;
+    const uint64_t b0 = a.w0 < u ? 1ull : 0ull, b1 = a.w1 < b0 ? 1ull : 0ull;
+    return W3(a.w0 - u, a.w1 - b0, a.w2 - b1);
+}
+
 template <int KW> struct KeyOf;
 template <> struct KeyOf<1> { using T = uint64_t; };
 template <> struct KeyOf<2> { using T = W2; };
+template <> struct KeyOf<3> { using T = W3; };
 
 __device__ __forceinline__ int popck(uint64_t x) { return __popcll(x); }
 __device__ __forceinline__ int popck(W2 x) { return __popcll(x.lo) + __popcll(x.hi); }
+__device__ __forceinline__ int popck(W3 x) { return __popcll(x.w0) + __popcll(x.w1) + __popcll(x.w2); }
 // lowest set bit (x != 0)
 __device__ __forceinline__ int lowbit(uint64_t x) { return __ffsll((long long)x) - 1; }
 __device__ __forceinline__ int lowbit(W2 x)
 {
     return x.lo ? __ffsll((long long)x.lo) - 1 : 64 + __ffsll((long long)x.hi) - 1;
 }
+__device__ __forceinline__ int lowbit(W3 x)
+{
+    return x.w0 ? __ffsll((long long)x.w0) - 1
+                : x.w1 ? 64 + __ffsll((long long)x.w1) - 1 : 128 + __ffsll((long long)x.w2) - 1;
+}
 template <typename K> __device__ __forceinline__ K bitk(int p);
 template <> __device__ __forceinline__ uint64_t bitk<uint64_t>(int p) { return 1ull << p; }
 template <> __device__ __forceinline__ W2 bitk<W2>(int p) { return p < 64 ? W2(1ull << p, 0) : W2(0, 1ull << (p - 64)); }
+template <> __device__ __forceinline__ W3 bitk<W3>(int p)
+{
+    const uint64_t b = 1ull << (p & 63);
+    return W3(p < 64 ? b : 0ull, p >= 64 && p < 128 ? b : 0ull, p >= 128 ? b : 0ull);
+}
 __device__ __forceinline__ bool has(uint64_t k, int p) { return (k >> p) & 1; }
 __device__ __forceinline__ bool has(W2 k, int p) { return p < 64 ? (k.lo >> p) & 1 : (k.hi >> (p - 64)) & 1; }
+__device__ __forceinline__ bool has(W3 k, int p) { return ((p < 64 ? k.w0 : p < 128 ? k.w1 : k.w2) >> (p & 63)) & 1; }
 // occupied orbitals of k below orbital x
 template <typename K> __device__ __forceinline__ int belowk(K k, int x) { return popck(k & (bitk<K>(x) - 1)); }
 template <int KW> __device__ __forceinline__ typename KeyOf<KW>::T load_key(const uint64_t *keys, int64_t J)
 {
     if constexpr (KW == 1) return keys[J];
-    else return W2(keys[2 * J], keys[2 * J + 1]);
+    else if constexpr (KW == 2) return W2(keys[2 * J], keys[2 * J + 1]);
+    else return W3(keys[3 * J], keys[3 * J + 1], keys[3 * J + 2]);
 }
 template <typename K> __device__ __forceinline__ K ref_of(const Pt2 &p)
 {
     if constexpr (sizeof(K) == 8) return p.ref;
-    else return W2(p.ref, p.ref_hi);
+    else if constexpr (sizeof(K) == 16) return W2(p.ref, p.ref_hi);
+    else return W3(p.ref, p.ref_hi, p.ref_w2);
 }
 __device__ __forceinline__ uint64_t key_lo(uint64_t x) { return x; }
 __device__ __forceinline__ uint64_t key_lo(W2 x) { return x.lo; }
 __device__ __forceinline__ uint64_t key_hi(uint64_t) { return 0; }
 __device__ __forceinline__ uint64_t key_hi(W2 x) { return x.hi; }
+__device__ __forceinline__ uint64_t key_lo(W3 x) { return x.w0; }
+__device__ __forceinline__ uint64_t key_hi(W3 x) { return x.w1; }
 __device__ __forceinline__ uint64_t hash_key(uint64_t x) { return mix64(x); }
 __device__ __forceinline__ uint64_t hash_key(W2 x) { return mix64(x.lo ^ mix64(x.hi + 0x9e3779b97f4a7c15ull)); }
+__device__ __forceinline__ uint64_t hash_key(W3 x)
+{
+    return mix64(x.w0 ^ mix64(x.w1 + 0x9e3779b97f4a7c15ull) ^ mix64(x.w2 + 0x632be59bd9b4e019ull));
+}
 
 // H_IJ for I = J - {i, j} + {a, b} (i < j, a < b, spin-orbital indices)
 template <typename K>
@@ -196,9 +236,12 @@ __device__ __forceinline__ double h_single(const Pt2 &p, K J, int i, int a)
 // its end, and the host compares that count with the load limit, instead of one add to a
 // single counter per claim); NULL after kMaxProbe probes (the table is too full: flag bit 2).
 //
-// Slots: KW key words, then NW value words; with two key words the slot is padded to an
-// even number of words, so that every slot is 16-byte aligned for the 128-bit CAS.
-template <int KW, int NW> __host__ __device__ constexpr int slot_words() { return KW == 1 ? 1 + NW : (2 + NW + 1) & ~1; }
+// Slots: KW key words, then NW value words; with two or three key words the slot is padded
+// to an even number of words, so that every slot is 16-byte aligned for the 128-bit CAS.
+// With three key words the third is stored complemented, so that 0 still marks a slot
+// whose third word is not yet set (a determinant of fewer than 64 electrons never has all
+// of orbitals 128..191 occupied).
+template <int KW, int NW> __host__ __device__ constexpr int slot_words() { return KW == 1 ? 1 + NW : (KW + NW + 1) & ~1; }
 
 // 128-bit compare-and-swap (sm_90 and later): [a] = n if [a] == e; returns the old value
 __device__ __forceinline__ void cas128(uint64_t *a, uint64_t e0, uint64_t e1, uint64_t n0, uint64_t n1, uint64_t &r0,
@@ -237,11 +280,29 @@ __device__ __forceinline__ uint64_t *claim(const Pt2 &p, K I, uint32_t &nc)
             const uint64_t lo = key_lo(I), hi = key_hi(I);
             uint64_t r0, r1;
             cas128(slot, 0, 0, lo, hi, r0, r1);
-            if ((r0 | r1) == 0) {
-                nc++;
-                return slot;
+            const bool first = (r0 | r1) == 0;
+            if constexpr (KW == 2) {
+                if (first) {
+                    nc++;
+                    return slot;
+                }
+                if (r0 == lo && r1 == hi) return slot;
+            } else {
+                // three words: the first two are claimed together; the slot's third word is
+                // then set by a 64-bit CAS from 0 by whichever thread with those two words
+                // gets there first (its claimer or another), and that key owns the slot.
+                // No thread waits on another: one whose third word lost probes on.
+                if (first || (r0 == lo && r1 == hi)) {
+                    const unsigned long long w2 = ~I.w2;
+                    const unsigned long long o =
+                        atomicCAS(reinterpret_cast<unsigned long long *>(slot + 2), 0ull, w2);
+                    if (o == 0ull) {
+                        nc++;
+                        return slot;
+                    }
+                    if (o == w2) return slot;
+                }
             }
-            if (r0 == lo && r1 == hi) return slot;
         }
         s = (s + 1) & p.mask;
     }
@@ -268,6 +329,10 @@ __device__ __forceinline__ uint32_t code_of64(const uint32_t *g, uint64_t s)
 }
 __device__ __forceinline__ uint32_t code_ofk(const uint32_t *g, uint64_t s) { return code_of64(g, s); }
 __device__ __forceinline__ uint32_t code_ofk(const uint32_t *g, W2 s) { return code_of64(g, s.lo) ^ code_of64(g + 64, s.hi); }
+__device__ __forceinline__ uint32_t code_ofk(const uint32_t *g, W3 s)
+{
+    return code_of64(g, s.w0) ^ code_of64(g + 64, s.w1) ^ code_of64(g + 128, s.w2);
+}
 
 // the claims of a warp's threads, added to the distinct count once
 __device__ __forceinline__ void add_claims(const Pt2 &p, uint32_t nc, int lane)
@@ -491,7 +556,7 @@ __device__ __forceinline__ void insert_z(const Pt2 &p, K I, zdbl h, const zdbl *
 }
 
 // warp per determinant J of P: the excitations of J (spinors) that fall in batch `batch`.
-// KW = 1: n <= 64 spinors (one-word keys); KW = 2: n <= 128 (two-word keys).
+// KW = 1: n <= 64 spinors (one-word keys); KW = 2: n <= 128; KW = 3: n <= 192.
 template <int R, int KW>
 __global__ void __launch_bounds__(kThreads)
 k_pt2_gen_z(const uint64_t *__restrict__ Pkeys, int64_t M, const zdbl *__restrict__ C, Pt2 p, uint32_t batch, int tbits)
@@ -587,21 +652,28 @@ k_pt2_gen_z(const uint64_t *__restrict__ Pkeys, int64_t M, const zdbl *__restric
 // it scans into a buffer of 32 and evaluates full buffers, so every lane works; H_II
 // (E_ref plus O(level^2) table terms) is summed in paired FP32 from split copies of F and
 // G in shared memory, and added to E_ref in FP64.
-template <int R, bool CPLX, int KW>
+// GS: G in shared memory (up to 168 orbitals); else read from global memory and split on
+// the fly.
+template <int R, bool CPLX, int KW, bool GS = true>
 __global__ void __launch_bounds__(kThreads)
 k_pt2_eval(Pt2 p, uint64_t cap, const double *__restrict__ E0, double *__restrict__ out)
 {
     using K = typename KeyOf<KW>::T;
     constexpr int NW = CPLX ? 2 * R : R;   // value words per slot
     constexpr int SW = slot_words<KW, NW>();
-    extern __shared__ float2 s_gf[];       // G [norb][norb], then F [norb] (dynamic)
+    extern __shared__ float2 s_gf[];       // F [norb], then G [norb][norb] (dynamic)
     __shared__ uint64_t sbuf[kWarps][64];
     __shared__ double red[kWarps][R];
     const int norb = p.norb;
-    float2 *sG = s_gf, *sF = s_gf + norb * norb;
-    for (int t = threadIdx.x; t < norb * norb; t += blockDim.x) sG[t] = sci::ds_split_int(p.G[t]);
+    float2 *sF = s_gf, *sGs = s_gf + norb;
     for (int t = threadIdx.x; t < norb; t += blockDim.x) sF[t] = sci::ds_split_int(p.fdiag[t]);
+    if constexpr (GS)
+        for (int t = threadIdx.x; t < norb * norb; t += blockDim.x) sGs[t] = sci::ds_split_int(p.G[t]);
     __syncthreads();
+    auto gget = [&](int t) -> float2 {
+        if constexpr (GS) return sGs[t];
+        else return sci::ds_split_int(__ldg(p.G + t));
+    };
     const double Eref = *p.Eref;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     double acc[R], e0[R];
@@ -612,7 +684,8 @@ k_pt2_eval(Pt2 p, uint64_t cap, const double *__restrict__ E0, double *__restric
         const uint64_t *slot = p.tab2 + s * SW;
         K I;
         if constexpr (KW == 1) I = slot[0];
-        else I = W2(slot[0], slot[1]);
+        else if constexpr (KW == 2) I = W2(slot[0], slot[1]);
+        else I = W3(slot[0], slot[1], ~slot[2]);
         const K H = ref & ~I, Pm = I & ~ref;
         sci::Ds e;
         sci::ds_zero(e);
@@ -620,16 +693,16 @@ k_pt2_eval(Pt2 p, uint64_t cap, const double *__restrict__ E0, double *__restric
             const int i = lowbit(m);
             const float2 f = sF[i];
             sci::ds_add(e, make_float2(-f.x, -f.y));
-            for (K m2 = m & (m - 1); m2; m2 &= m2 - 1) sci::ds_add(e, sG[i * norb + lowbit(m2)]);
+            for (K m2 = m & (m - 1); m2; m2 &= m2 - 1) sci::ds_add(e, gget(i * norb + lowbit(m2)));
             for (K m2 = Pm; m2; m2 &= m2 - 1) {
-                const float2 g = sG[i * norb + lowbit(m2)];
+                const float2 g = gget(i * norb + lowbit(m2));
                 sci::ds_add(e, make_float2(-g.x, -g.y));
             }
         }
         for (K m = Pm; m; m &= m - 1) {
             const int a = lowbit(m);
             sci::ds_add(e, sF[a]);
-            for (K m2 = m & (m - 1); m2; m2 &= m2 - 1) sci::ds_add(e, sG[a * norb + lowbit(m2)]);
+            for (K m2 = m & (m - 1); m2; m2 &= m2 - 1) sci::ds_add(e, gget(a * norb + lowbit(m2)));
         }
         const double hii = Eref + sci::ds_value(e);
 #pragma unroll
@@ -653,7 +726,7 @@ k_pt2_eval(Pt2 p, uint64_t cap, const double *__restrict__ E0, double *__restric
         bool occ = false;
         if (s < cap) {
             const uint64_t *slot = p.tab2 + s * SW;
-            occ = KW == 1 ? slot[0] != kEmpty : (slot[0] | slot[KW - 1]) != kEmpty;
+            occ = KW == 1 ? slot[0] != kEmpty : KW == 2 ? (slot[0] | slot[1]) != kEmpty : slot[2] != 0;
         }
         const unsigned m = __ballot_sync(0xffffffffu, occ);
         if (occ) sbuf[w][nbuf + __popc(m & ((1u << lane) - 1))] = s;
@@ -725,11 +798,11 @@ __device__ __forceinline__ double re_of(double a) { return a; }
 __device__ __forceinline__ double re_of(zdbl a) { return a.x; }
 
 template <typename T>
-__global__ void k_pt2_setup(int norb, uint64_t ref_lo, uint64_t ref_hi, const T *__restrict__ h_so,
+__global__ void k_pt2_setup(int norb, uint64_t ref_lo, uint64_t ref_hi, uint64_t ref_w2, const T *__restrict__ h_so,
                             const T *__restrict__ jd, const T *__restrict__ kd, double *__restrict__ G,
                             double *__restrict__ fdiag, double *__restrict__ Eref)
 {
-    const W2 ref(ref_lo, ref_hi);
+    const W3 ref(ref_lo, ref_hi, ref_w2);
     for (int t = threadIdx.x; t < norb * norb; t += blockDim.x) {
         const int a = t / norb, b = t % norb;
         G[t] = a == b ? 0.0 : re_of(jd[t]) - re_of(kd[t]);
@@ -737,15 +810,15 @@ __global__ void k_pt2_setup(int norb, uint64_t ref_lo, uint64_t ref_hi, const T 
     __syncthreads();
     for (int a = threadIdx.x; a < norb; a += blockDim.x) {
         double f = re_of(h_so[a * norb + a]);
-        for (W2 m = ref; m; m &= m - 1) f += G[a * norb + lowbit(m)];
+        for (W3 m = ref; m; m &= m - 1) f += G[a * norb + lowbit(m)];
         fdiag[a] = f;
     }
     if (threadIdx.x == 0) {
         double e = 0.0;
-        for (W2 m = ref; m; m &= m - 1) {
+        for (W3 m = ref; m; m &= m - 1) {
             const int i = lowbit(m);
             e += re_of(h_so[i * norb + i]);
-            for (W2 m2 = m & (m - 1); m2; m2 &= m2 - 1) e += G[i * norb + lowbit(m2)];
+            for (W3 m2 = m & (m - 1); m2; m2 &= m2 - 1) e += G[i * norb + lowbit(m2)];
         }
         *Eref = e;
     }
@@ -797,7 +870,7 @@ int grid_for(int64_t n)
 }
 
 // SPIN: complex spinor mode (C is [M][R] complex128); otherwise real spin-orbital mode.
-// KW: key words (1 or 2) of the determinant list.
+// KW: key words (1, 2, or 3 in spinor mode) of the determinant list.
 template <int R, bool SPIN, int KW>
 int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t table_bytes, double *E2, int64_t *stats)
 {
@@ -847,10 +920,10 @@ int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t
             k_pt2_p<R, double><<<grid_for(M), kThreads, 0, st>>>(M, C, S, ctx->hdiag, dE0, outP);
     }
     if constexpr (SPIN)
-        k_pt2_setup<zdbl><<<1, 256, 0, st>>>(norb, ctx->ref, ctx->ref_hi, (const zdbl *)ctx->h_so,
+        k_pt2_setup<zdbl><<<1, 256, 0, st>>>(norb, ctx->ref, ctx->ref_hi, ctx->ref_w2, (const zdbl *)ctx->h_so,
                                              (const zdbl *)ctx->jd, (const zdbl *)ctx->kd, G, fdiag, Eref);
     else
-        k_pt2_setup<double><<<1, 256, 0, st>>>(norb, ctx->ref, ctx->ref_hi, (const double *)ctx->h_so,
+        k_pt2_setup<double><<<1, 256, 0, st>>>(norb, ctx->ref, ctx->ref_hi, ctx->ref_w2, (const double *)ctx->h_so,
                                                (const double *)ctx->jd, (const double *)ctx->kd, G, fdiag, Eref);
     // the table: capacity a power of two within the budget
     const size_t slot = sizeof(uint64_t) * SW;
@@ -898,7 +971,7 @@ int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t
         }
         p.bss3 = b3;
     }
-    p.n = n, p.norb = norb, p.na = na, p.nb = nb, p.ref = ctx->ref, p.ref_hi = ctx->ref_hi;
+    p.n = n, p.norb = norb, p.na = na, p.nb = nb, p.ref = ctx->ref, p.ref_hi = ctx->ref_hi, p.ref_w2 = ctx->ref_w2;
     p.tab = (const double *)ctx->tab, p.fref = (const double *)ctx->fref, p.g_so = (const double *)ctx->g_so;
     p.fdiag = fdiag, p.G = G, p.Eref = Eref;
     p.tab2 = tab2, p.mask = cap - 1, p.count = count, p.flag = flag;
@@ -922,7 +995,7 @@ int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t
     // orbitals grouped by code
     auto set_codes = [&](int t) {
         std::mt19937 rng(20250130u + (unsigned)t);
-        for (int o = 0; o < 128; o++) p.gcode[o] = t ? (uint32_t)(rng() & ((1u << t) - 1)) : 0u;
+        for (int o = 0; o < 192; o++) p.gcode[o] = t ? (uint32_t)(rng() & ((1u << t) - 1)) : 0u;
         std::vector<int> cnt((1 << t) + 1, 0);
         for (int o = 0; o < n; o++) cnt[p.gcode[o] + 1]++;
         for (int c = 1; c <= (1 << t); c++) cnt[c] += cnt[c - 1];
@@ -930,10 +1003,14 @@ int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t
         std::vector<int> fill(cnt.begin(), cnt.end() - 1);
         for (int o = 0; o < n; o++) p.obc[fill[p.gcode[o]]++] = (uint8_t)o;
     };
-    // the evaluation kernel's G and F (paired floats) in dynamic shared memory
-    const size_t eval_smem = sizeof(float2) * ((size_t)norb * norb + norb);
-    if (sci_cuda_check(ctx, cudaFuncSetAttribute(k_pt2_eval<R, SPIN, KW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)eval_smem),
+    // the evaluation kernel's F and G (paired floats) in dynamic shared memory; past 165
+    // orbitals (three-word keys only) G is read from global memory
+    size_t eval_smem = sizeof(float2) * ((size_t)norb * norb + norb);
+    const bool eval_gs = KW < 3 || eval_smem <= 216 * 1024;
+    auto keval = k_pt2_eval<R, SPIN, KW, true>;
+    if constexpr (KW == 3)
+        if (!eval_gs) keval = k_pt2_eval<R, SPIN, KW, false>, eval_smem = sizeof(float2) * norb;
+    if (sci_cuda_check(ctx, cudaFuncSetAttribute(keval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eval_smem),
                        "enpt2 eval attr"))
         return done(SCI_ERR_CUDA);
     // one batch: clear the table, generate, evaluate (optional); returns the distinct
@@ -954,8 +1031,7 @@ int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t
         }
         if (sci_cuda_check(ctx, cudaEventRecord(ev[2], st), "enpt2 event")) return SCI_ERR_CUDA;
         if (eval)
-            k_pt2_eval<R, SPIN, KW><<<grid_for((int64_t)std::min<uint64_t>(cap, 1ull << 40)), kThreads, eval_smem, st>>>(
-                p, cap, dE0, outW);
+            keval<<<grid_for((int64_t)std::min<uint64_t>(cap, 1ull << 40)), kThreads, eval_smem, st>>>(p, cap, dE0, outW);
         unsigned long long hc[2] = {0, 0};
         if (sci_cuda_check(ctx, cudaEventRecord(ev[3], st), "enpt2 event") ||
             sci_cuda_check(ctx, cudaMemcpyAsync(hc, count, sizeof(hc), cudaMemcpyDeviceToHost, st), "enpt2 flag") ||
@@ -1044,15 +1120,19 @@ int enpt2_dispatch(sci_ctx *ctx, const double *C, int nroots, const double *E0, 
             default: return pt2_run<8, true, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
         }
     }
-    switch (nroots) {
-        case 1: return pt2_run<1, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
-        case 2: return pt2_run<2, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
-        case 3: return pt2_run<3, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
-        case 4: return pt2_run<4, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
-        case 5: return pt2_run<5, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
-        case 6: return pt2_run<6, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
-        case 7: return pt2_run<7, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
-        default: return pt2_run<8, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+    if constexpr (KW == 3) {
+        return sci_fail(ctx, SCI_ERR_ARG, "enpt2: three-word keys in spinor mode only");
+    } else {
+        switch (nroots) {
+            case 1: return pt2_run<1, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+            case 2: return pt2_run<2, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+            case 3: return pt2_run<3, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+            case 4: return pt2_run<4, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+            case 5: return pt2_run<5, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+            case 6: return pt2_run<6, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+            case 7: return pt2_run<7, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+            default: return pt2_run<8, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+        }
     }
 }
 
@@ -1065,12 +1145,17 @@ extern "C" int sci_enpt2(sci_ctx *ctx, const double *C, int nroots, const double
     if (!ctx->have_ints || !ctx->have_dets) return sci_fail(ctx, SCI_ERR_STATE, "enpt2: integrals and determinants first");
     if (ctx->spinors != ctx->cplx)
         return sci_fail(ctx, SCI_ERR_ARG, "enpt2: real spin-orbital mode or complex spinor mode");
-    if (ctx->nwords > 2 || ctx->norb > 64 * ctx->nwords)
-        return sci_fail(ctx, SCI_ERR_ARG, "enpt2: at most 64 spin-orbitals or spinors per key word, two words");
+    if (ctx->nwords > 3 || ctx->norb > 64 * ctx->nwords)
+        return sci_fail(ctx, SCI_ERR_ARG, "enpt2: at most 64 spin-orbitals or spinors per key word");
+    if (ctx->nwords == 3 && !ctx->spinors)
+        return sci_fail(ctx, SCI_ERR_ARG, "enpt2: three-word keys in spinor mode only");
+    if (ctx->nwords == 3 && ctx->norb == 192 && ctx->na >= 64)
+        return sci_fail(ctx, SCI_ERR_ARG, "enpt2: 64 or more electrons in 192 spinors");
     if (nroots < 1 || nroots > 8 || !E0 || !E2 || (ctx->M > 0 && !C))
         return sci_fail(ctx, SCI_ERR_ARG, "enpt2: need 1 <= nroots <= 8, C, E0 and E2");
     if (eps < 0.0) return sci_fail(ctx, SCI_ERR_ARG, "enpt2: eps < 0");
     if (sci_cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) return SCI_ERR_CUDA;
-    return ctx->nwords == 2 ? enpt2_dispatch<2>(ctx, C, nroots, E0, eps, table_bytes, E2, stats)
-                            : enpt2_dispatch<1>(ctx, C, nroots, E0, eps, table_bytes, E2, stats);
+    return ctx->nwords == 3   ? enpt2_dispatch<3>(ctx, C, nroots, E0, eps, table_bytes, E2, stats)
+           : ctx->nwords == 2 ? enpt2_dispatch<2>(ctx, C, nroots, E0, eps, table_bytes, E2, stats)
+                              : enpt2_dispatch<1>(ctx, C, nroots, E0, eps, table_bytes, E2, stats);
 }

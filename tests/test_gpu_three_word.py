@@ -254,10 +254,45 @@ def test_three_word_rdm12_172_spin_orbitals_global_diagonal(gpu):
     H.sync_status()
 
 
+def test_three_word_enpt2_spinors(gpu):
+    """Complex spinor ENPT2 on 130 spinors (three-word keys; 3 electrons, HF and 300 random
+    determinants): the whole-string batch code over three words, keys claimed by a 128-bit
+    compare-and-swap of words 0-1 and a 64-bit one of word 2, H_II over three words; two
+    roots against the oracle's sum over the deduplicated external determinants at 1e-10,
+    the distinct count exact, and a small table (many batches) giving the same sums."""
+    torch = gpu
+    n, N = 130, 3
+    ints = W.complex_integrals(np.random.default_rng(105), n, 4, 0.9)
+    rng = np.random.default_rng(106)
+    occ = {(0, 1, 2)}
+    while len(occ) < 301:
+        occ.add(tuple(sorted(rng.choice(n, N, replace=False))))
+    keys = W.sort_words(W.words_from_occ(np.array(sorted(occ)), 3))
+    assert (keys[:, 2] != 0).any()
+    o = Oracle("spinors", n, ints.h, ints.eri(), keys)
+    C = rng.standard_normal((len(keys), 2)) + 1j * rng.standard_normal((len(keys), 2))
+    C /= np.linalg.norm(C, axis=0)
+    d = o.diagonal().real
+    E0 = np.array([d.min() - 1.0, d.min() - 2.0])
+    E2, n_ext = o.enpt2(C, E0)
+    n_conn = sum(1 for r in range(len(keys)) if len(o.connections(r)[0]) > 0)
+    H = sci.Hamiltonian()
+    H.set_integrals("spinors", ints.h, chol=ints.chol)
+    H.set_determinants(keys, N, -1)
+    Ct = torch.from_numpy(C).cuda()
+    e2w, e2p, e2q, st = H.enpt2(Ct, E0)
+    assert np.allclose(e2q, E2, rtol=1e-10, atol=0), (e2q, E2)
+    assert st["distinct_W"] == n_ext + n_conn
+    b = H.enpt2(Ct, E0, table_bytes=(1 << 16) * 48)
+    assert b[3]["batches"] > st["batches"] and b[3]["distinct_W"] == st["distinct_W"]
+    assert np.allclose(b[2], E2, rtol=1e-10, atol=0)
+    H.sync_status()
+
+
 def test_three_word_limits_and_rejections(gpu, sel3w):
     """Keys of too few words for the orbital count, keys out of 192-bit order, orbital
-    counts above three words, and ENPT2 (at most two words) are refused with an error,
-    never a wrong result."""
+    counts above three words, and ENPT2 of a spin-orbital three-word list (three words in
+    spinor mode only) are refused with an error, never a wrong result."""
     torch = gpu
     w, o = sel3w
     H = sci.Hamiltonian.from_workload(w)

@@ -195,3 +195,52 @@ def test_rdm12_three_word_encoding_of_a_two_word_space():
     finally:
         oracle.set_threads(0)
     assert np.array_equal(a1, b1) and np.array_equal(a2, b2)
+
+
+def test_enpt2_three_words_against_the_definition_on_the_full_space():
+    """ENPT2 of a P inside the full 1 + 1-electron space of 65 orbitals (4,225 determinants;
+    alpha orbital 64 in word 1, beta orbitals 63 and 64 at bits 128 and 129 of word 2):
+    sciref_enpt2 (generation of the excitations of P, deduplication by three-word key)
+    against Eq. ENPT2E written out with H of the whole space (the oracle's sigma and
+    diagonal, pinned above by the closed form), two roots with arbitrary E0; the external
+    count against the size of Q."""
+    n = 65
+    ints = _ints(n, 101, naux=4)
+    P_, Q_ = np.meshgrid(np.arange(n), np.arange(n))
+    full = _keys(P_.reshape(-1, 1), Q_.reshape(-1, 1), n)
+    assert [_as_int(k) for k in full] == sorted(_as_int(k) for k in full)
+    of = Oracle("spin_orbitals", n, ints.h, ints.eri(), full)
+    rng = np.random.default_rng(102)
+    inP = rng.random(len(full)) < 0.3
+    inP[0] = True
+    P = full[inP]
+    C = rng.standard_normal((len(P), 2))
+    E0 = np.array([-30.0, -25.0])
+    Cf = np.zeros((len(full), 2))
+    Cf[inP] = C
+    v = of.sigma(Cf)                         # sum_J H_IJ c_J over J in P, for every I
+    d = of.diagonal()
+    Q = ~inP
+    ref = ((v[Q] ** 2) / (E0[None, :] - d[Q, None])).sum(axis=0)
+    op = Oracle("spin_orbitals", n, ints.h, ints.eri(), P)
+    E2, nx = op.enpt2(C, E0)
+    assert np.allclose(E2, ref, rtol=1e-12, atol=0)
+    assert nx == int(Q.sum())
+
+
+def test_enpt2_three_word_encoding_of_a_two_word_space():
+    """A 40-orbital two-word list given as three words gives the two-word ENPT2."""
+    n = 40
+    rng = np.random.default_rng(103)
+    occ = {((0, 1), (0,))}
+    while len(occ) < 300:
+        occ.add((tuple(sorted(rng.choice(n, 2, replace=False))), tuple(sorted(rng.choice(n, 1, replace=False)))))
+    occ = np.array([list(a) + [b[0] + n] for a, b in sorted(occ)])
+    k2 = W.sort_words(W.words_from_occ(occ, 2))
+    k3 = np.concatenate([k2, np.zeros((len(k2), 1), dtype=np.uint64)], axis=1)
+    ints = _ints(n, 104, naux=4)
+    C = rng.standard_normal((len(k2), 2))
+    E0 = np.array([-20.0, -18.0])
+    a, na_ = Oracle("spin_orbitals", n, ints.h, ints.eri(), k2).enpt2(C, E0)
+    b, nb_ = Oracle("spin_orbitals", n, ints.h, ints.eri(), k3).enpt2(C, E0)
+    assert na_ == nb_ and np.allclose(a, b, rtol=1e-13, atol=0)
