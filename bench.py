@@ -683,17 +683,17 @@ def two_word_bench(H, w, device, steps=10, warmup=3, M=2_000_000):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=dev)
 
-    def timed(Hx, C):
+    def timed(Hx, C, prec=sci.SCI_PREC_F64):
         S = torch.empty_like(C)
         for _ in range(warmup):
-            Hx.sigma(C, out=S)
+            Hx.sigma(C, out=S, prec=prec)
         sci.sci_profile(Hx.ctx, True)
         ms, kern = [], []
         for _ in range(steps):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            Hx.sigma(C, out=S)
+            Hx.sigma(C, out=S, prec=prec)
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
@@ -782,6 +782,41 @@ def two_word_bench(H, w, device, steps=10, warmup=3, M=2_000_000):
                              "l2": "flushed between timed steps (256 MB write)",
                              "cpu_baseline": cpu_baseline(w3, budget_s=6.0, one_thread_s=2.0)}
     del H3, C
+    torch.cuda.empty_cache()
+    # three-word spinors: 136 complex spinors (the size of the paper's 4C spaces), 14
+    # electrons, 1M determinants, FP64 and paired FP32; and ENPT2 of a 6-electron 150k space
+    # (oracle not timed: its dense complex integrals would take 5.5 GB)
+    w5 = W.selected_spinor_words(n=136, N=14, M=M // 2)
+    t = time.perf_counter()
+    H5 = sci.Hamiltonian.from_workload(w5, device=device)
+    torch.cuda.synchronize()
+    setup5 = time.perf_counter() - t
+    info = H5.info()
+    C = torch.from_numpy(np.ascontiguousarray(w5.c)).to(dev)
+    _, ms5, k5 = timed(H5, C)
+    _, ms5d, k5d = timed(H5, C, sci.SCI_PREC_F64_DS)
+    fma = 4 * info["pairs_doubles"] / (k5["doubles"] / 1e3)   # a complex product is 4 FMAs
+    out["selected_136s"] = {"workload": w5.name, "M": w5.M, "pairs_per_step": info["pairs"],
+                            "pairs_doubles": info["pairs_doubles"], "max_bucket": info["max_bucket"],
+                            "setup_s": round(setup5, 3), "f64": {"ms_per_step": ms5, "pairs_per_s": info["pairs"] / (ms5 / 1e3),
+                                                               "kernel_ms": k5, "fp64_pipe_frac": fma / pp["fp64_fma_per_s"]},
+                            "ds": {"ms_per_step": ms5d, "pairs_per_s": info["pairs"] / (ms5d / 1e3), "kernel_ms": k5d},
+                            "l2": "flushed between timed steps (256 MB write)"}
+    del H5, C
+    torch.cuda.empty_cache()
+    w6 = W.selected_spinor_words(n=136, N=6, M=150_000)
+    H6 = sci.Hamiltonian.from_workload(w6, device=device)
+    c = torch.from_numpy(np.ascontiguousarray(w6.c)).to(dev)
+    c = c / torch.linalg.vector_norm(c)
+    E0 = [float((c.conj() * H6.sigma(c)).sum().real)]
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    e2w, e2p, e2q, st = H6.enpt2(c, E0, table_bytes=16 << 30)
+    sec = time.perf_counter() - t
+    out["pt2_136s"] = {"workload": w6.name, "M": w6.M, "seconds": sec, "E0": E0[0], "E2_Q": float(e2q[0]),
+                       "batches": st["batches"], "distinct_W": st["distinct_W"],
+                       "generate_us": st["generate_us"], "evaluate_us": st["evaluate_us"]}
+    del H6, c
     torch.cuda.empty_cache()
     # ENPT2 on a 200k-determinant space of the same recipe (128-bit table keys), one
     # normalised vector with its Rayleigh quotient as E0

@@ -480,6 +480,35 @@ def selected_three_word(n: int = 70, na: int = 3, nb: int = 3, M: int = 60000, n
                     {"hf_words": hf})
 
 
+def selected_spinor_words(n: int = 136, N: int = 14, M: int = 1_000_000, naux: int = 80, nvec: int = 1,
+                          seed: int = 2501181862) -> Workload:
+    """A selected spinor space of n > 128 spinors (three-word keys), N electrons: HF + all
+    singles + all doubles + random triples (uniform, without replacement) up to M
+    determinants, sorted as (64 x 3)-bit integers; complex integrals as selected_spinor_64
+    (naux Cholesky vectors, decay 0.95); |c| = exp(-level) with random complex phases,
+    normalised.  Draw order: integrals, triples, c."""
+    rng = np.random.default_rng(seed)
+    ints = complex_integrals(rng, n, naux, 0.95)
+    parts = [words_from_occ(occ_at_level(n, N, L), 3) for L in range(3)]
+    rest = M - sum(len(x) for x in parts)
+    if rest < 0:
+        raise ValueError("M smaller than HF+singles+doubles")
+    holes = _combos(range(N), 3)
+    kept = np.array([[i for i in range(N) if i not in set(h.tolist())] for h in holes], dtype=np.int64)
+    prt = _combos(range(N, n), 3)
+    idx = np.sort(rng.choice(len(holes) * len(prt), size=rest, replace=False))
+    occ = np.concatenate([kept[idx // len(prt)], prt[idx % len(prt)]], axis=1)
+    keys = sort_words(np.concatenate(parts + [words_from_occ(occ, 3)]))
+    assert len(keys) == M
+    hf = words_from_occ(np.arange(N)[None, :], 3)[0]
+    lev = excitation_level_words(keys, hf)
+    cols = []
+    for _ in range(nvec):
+        v = np.exp(-lev.astype(np.float64)) * np.exp(2j * np.pi * rng.random(M))
+        cols.append(v / np.linalg.norm(v))
+    return Workload(f"sel_{n}s_{N}e_M{M}", "spinors", n, N, -1, keys, ints, np.stack(cols, axis=1), {"hf_words": hf})
+
+
 def selected_spinor_64(M: int = 1_000_000, nvec: int = 1, seed_offset: int = 4) -> Workload:
     """64 spinors, 14 electrons, selected space of M determinants (HF + singles + doubles
     + random triples); 80 Hermitian complex Cholesky vectors; complex c.
