@@ -59,3 +59,43 @@ def test_cholesky_decay():
     w = W.selected_30o(M=58000)
     norms = np.linalg.norm(w.ints.chol.reshape(120, -1), axis=1)
     assert np.allclose(norms, 0.3 * 30 * 0.95 ** np.arange(120))
+
+
+def _as_ints(keys):
+    return [sum(int(w) << (64 * i) for i, w in enumerate(k)) for k in keys]
+
+
+def test_words_from_occ_against_python_integers():
+    rng = np.random.default_rng(4)
+    occ = np.sort(rng.choice(192, (50, 7)), axis=1)
+    words = W.words_from_occ(occ, 3)
+    assert _as_ints(words) == [sum(1 << int(o) for o in set(row)) for row in occ]
+    assert _as_ints(W.sort_words(words)) == sorted(_as_ints(words))
+
+
+def test_selected_three_word_structure():
+    """HF, every single and Sz-conserving double, random triples; ascending, unique,
+    3 + 3 electrons in the right spin halves."""
+    n, na, nb, M = 70, 3, 3, 60000
+    w = W.selected_three_word(n=n, na=na, nb=nb, M=M)
+    ints = _as_ints(w.keys)
+    assert ints == sorted(set(ints)) and len(ints) == M
+    amask, bmask = (1 << n) - 1, ((1 << n) - 1) << n
+    assert all(bin(x & amask).count("1") == na and bin(x & bmask).count("1") == nb for x in ints[::97])
+    lv = W.excitation_level_words(w.keys, w.meta["hf_words"])
+    singles = na * (n - na) + nb * (n - nb)
+    doubles = comb(na, 2) * comb(n - na, 2) + comb(nb, 2) * comb(n - nb, 2) + na * (n - na) * nb * (n - nb)
+    assert (lv == 0).sum() == 1 and (lv == 1).sum() == singles and (lv == 2).sum() == doubles
+    assert (lv == 3).sum() == M - 1 - singles - doubles
+
+
+def test_selected_spinor_words_structure():
+    n, N, M = 136, 6, 130000
+    w = W.selected_spinor_words(n=n, N=N, M=M, naux=4)
+    ints = _as_ints(w.keys)
+    assert ints == sorted(set(ints)) and len(ints) == M
+    assert np.all(np.bitwise_count(w.keys).sum(axis=1) == N)
+    lv = W.excitation_level_words(w.keys, w.meta["hf_words"])
+    assert (lv == 1).sum() == N * (n - N) and (lv == 2).sum() == comb(N, 2) * comb(n - N, 2)
+    assert (lv == 3).sum() == M - 1 - N * (n - N) - comb(N, 2) * comb(n - N, 2)
+    assert np.isclose(np.linalg.norm(w.c), 1.0)
