@@ -818,6 +818,21 @@ def two_word_bench(H, w, device, steps=10, warmup=3, M=2_000_000):
                        "generate_us": st["generate_us"], "evaluate_us": st["evaluate_us"]}
     del H6, c
     torch.cuda.empty_cache()
+    # ENPT2 of a 150k space of the 140 spin-orbital recipe (three words, spin-orbital mode)
+    w7 = W.selected_three_word(n=70, na=4, nb=4, M=150_000)
+    H7 = sci.Hamiltonian.from_workload(w7, device=device)
+    c = torch.from_numpy(np.ascontiguousarray(w7.c)).to(dev)
+    c = c / torch.linalg.vector_norm(c)
+    E0 = [float((c * H7.sigma(c)).sum())]
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    e2w, e2p, e2q, st = H7.enpt2(c, E0, table_bytes=16 << 30)
+    sec = time.perf_counter() - t
+    out["pt2_140so"] = {"workload": w7.name, "M": w7.M, "seconds": sec, "E0": E0[0], "E2_Q": float(e2q[0]),
+                        "batches": st["batches"], "distinct_W": st["distinct_W"],
+                        "generate_us": st["generate_us"], "evaluate_us": st["evaluate_us"]}
+    del H7, c
+    torch.cuda.empty_cache()
     # ENPT2 on a 200k-determinant space of the same recipe (128-bit table keys), one
     # normalised vector with its Rayleigh quotient as E0
     w4 = W.selected_two_word(n=40, na=8, nb=8, M=200_000)

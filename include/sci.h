@@ -145,9 +145,8 @@ int sci_set_determinants(sci_ctx *ctx, const uint64_t *keys, int64_t M, int n_al
  * are then (64 x nwords)-bit, sorted by nwords stable radix passes.  Sigma (every precision
  * mode, deterministic mode included), the diagonal, pair counts, row costs, the connection
  * exports, row ranges (sci_set_row_range) and the density matrices (sci_rdm12,
- * sci_rdm_grads) work on two- and three-word lists as on one word; ENPT2 (sci_enpt2)
- * takes one- and two-word lists, and three-word lists in spinor mode (SCI_ERR_ARG for a
- * three-word spin-orbital list); batches need one-word keys (SCI_ERR_ARG).  sci_set_determinants (one word) returns
+ * sci_rdm_grads) and ENPT2 (sci_enpt2) work on two- and three-word lists as on one
+ * word; batches need one-word keys (SCI_ERR_ARG).  sci_set_determinants (one word) returns
  * SCI_ERR_ARG when the orbitals do not fit one word.  Errors as sci_set_determinants. */
 int sci_set_determinants_w(sci_ctx *ctx, const uint64_t *keys, int nwords, int64_t M, int n_alpha,
                            int n_beta, int keys_on_device);
@@ -336,8 +335,9 @@ int sci_rdm_grads(sci_ctx *ctx, const double *C, int nvec, const double *weights
  * the squares are |.|^2 of complex numerators), on one-word lists (n <= 32 spatial
  * orbitals or n <= 64 spinors) or two-word lists (sci_set_determinants_w: n <= 64 or
  * n <= 128; the table keys are then 128-bit, claimed by a 16-byte compare-and-swap), or
- * three-word spinor lists (n <= 192, fewer than 64 electrons when n = 192: words 0-1 of a
- * key are claimed by the 16-byte compare-and-swap and word 2 by an 8-byte one).
+ * three-word lists (n <= 96 or n <= 192, fewer than 64 electrons when the list has 192
+ * spin-orbitals or spinors: words 0-1 of a key are claimed by the 16-byte
+ * compare-and-swap and word 2 by an 8-byte one).
  * Spinor mode with real integrals returns SCI_ERR_ARG.
  *   C: device, [M][nroots] doubles (complex mode: complex128, interleaved), 1 <= nroots
  *      <= 8 (need not be normalised; the formulas use c as given, so pass normalised

@@ -320,6 +320,30 @@ __device__ __forceinline__ void insert(const Pt2 &p, K I, double hij, const doub
     for (int v = 0; v < R; v++) atomicAdd(reinterpret_cast<double *>(slot + KW + v), hij * cJ[v]);
 }
 
+// The alpha (bits 0..n-1) and beta (bits n..2n-1) strings of a spin-orbital key.  One-
+// and two-word keys give 32- or 64-bit strings (n <= 64); three-word keys (n <= 96) give
+// two-word strings.
+template <typename S, typename K> __device__ __forceinline__ void split_ab(K key, int n, S full, S &oa, S &ob)
+{
+    if constexpr (sizeof(K) == 24) {
+        // key >> n, its low 128 bits (0 < n <= 96: word 2 reaches at most bit 191 - n)
+        const int q = n >> 6, r = n & 63;
+        const uint64_t w[4] = {key.w0, key.w1, key.w2, 0ull};
+        const uint64_t lo = r ? (w[q] >> r) | (w[q + 1] << (64 - r)) : w[q];
+        const uint64_t hi = r ? (w[q + 1] >> r) | (w[q + 2] << (64 - r)) : w[q + 1];
+        oa = W2(key.w0, key.w1) & full;
+        ob = W2(lo, hi) & full;
+    } else {
+        oa = (S)(uint64_t)key & full;
+        ob = (S)(uint64_t)(key >> n) & full;
+    }
+}
+
+// orbital o of a string of the spin-orbital generator (32- or 64-bit, or two words)
+__device__ __forceinline__ bool bit_of(uint32_t s, int o) { return (s >> o) & 1u; }
+__device__ __forceinline__ bool bit_of(uint64_t s, int o) { return (s >> o) & 1ull; }
+__device__ __forceinline__ bool bit_of(W2 s, int o) { return has(s, o); }
+
 // the batch code of a string: XOR of the codes of its occupied orbitals
 __device__ __forceinline__ uint32_t code_of64(const uint32_t *g, uint64_t s)
 {
@@ -378,53 +402,82 @@ __device__ __forceinline__ void wq_flush(uint32_t *q, int &cnt, int lane, F &&pr
 template <int R, int KW>
 // (one-word keys, one or two roots: held to 40 registers, 6 CTAs per SM, as the kernel
 // was before the two-word form; at 48 registers the 2M-space sum took 8.6 s, at 40 8.05 s)
+// KW = 3: n <= 96 orbitals per spin; the pair table is then decoded arithmetically and
+// the beta-singles list holds (n/2)^2 entries, so that the static shared memory stays
+// under 48 KB.
 __global__ void __launch_bounds__(kThreads, KW == 1 && R <= 2 ? 6 : 1)
 k_pt2_gen(const uint64_t *__restrict__ Pkeys, int64_t M, const double *__restrict__ C, Pt2 p, uint32_t batch, int tbits)
 {
     using K = typename KeyOf<KW>::T;
     constexpr int NO = 32 * KW;                   // orbitals per spin at most
     constexpr int kMP = NO * (NO - 1) / 2;        // their unordered pairs
+    constexpr int kNL = (NO / 2) * (NO / 2);      // beta singles at most (nb (n - nb))
     __shared__ uint8_t s_orb[kWarps][4 * NO];     // occ alpha | vir alpha | occ beta | vir beta
-    __shared__ uint16_t s_list[kWarps][32 * 32];  // beta singles of this batch (j | v << 8)
-    __shared__ uint16_t s_pair[kMP];              // P -> (a, b)
+    __shared__ uint16_t s_list[kWarps][kNL];      // beta singles of this batch (j | v << 8)
+    __shared__ uint16_t s_pair[KW == 3 ? 1 : kMP];   // P -> (a, b)
     __shared__ uint8_t s_cstart[(1 << kMaxBits) + 1];
     __shared__ uint8_t s_obc[NO];                 // beta orbitals sorted by code
     __shared__ uint32_t s_g[NO];                  // beta-orbital codes
     __shared__ int s_nl[kWarps];
-    for (int P = threadIdx.x; P < kMP; P += blockDim.x) {
-        int y = 1;
-        while ((y + 1) * y / 2 <= P) y++;
-        s_pair[P] = (uint16_t)((P - y * (y - 1) / 2) | (y << 8));
-    }
+    if constexpr (KW != 3)
+        for (int P = threadIdx.x; P < kMP; P += blockDim.x) {
+            int y = 1;
+            while ((y + 1) * y / 2 <= P) y++;
+            s_pair[P] = (uint16_t)((P - y * (y - 1) / 2) | (y << 8));
+        }
+    // pair P = y(y-1)/2 + x, x < y -> x | y << 8
+    auto pair_of = [&](int P) -> uint16_t {
+        if constexpr (KW != 3) {
+            return s_pair[P];
+        } else {
+            int y = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)P)) * 0.5f);
+            while (y * (y - 1) / 2 > P) y--;
+            while ((y + 1) * y / 2 <= P) y++;
+            return (uint16_t)((P - y * (y - 1) / 2) | (y << 8));
+        }
+    };
     for (int c = threadIdx.x; c <= (1 << tbits); c += blockDim.x) s_cstart[c] = p.cstart[c];
     if (threadIdx.x < NO) s_obc[threadIdx.x] = p.obc[threadIdx.x], s_g[threadIdx.x] = p.gcode[threadIdx.x];
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint8_t *orb = s_orb[w];
     // alpha and beta strings: 32-bit words for one-word keys (fewer registers), 64-bit
-    // for two
-    using S = std::conditional_t<KW == 1, uint32_t, uint64_t>;
+    // for two, two words for three
+    using S = std::conditional_t<KW == 1, uint32_t, std::conditional_t<KW == 2, uint64_t, W2>>;
     const int n = p.n, na = p.na, nb = p.nb, ua = n - na, ub = n - nb;
-    const S full = n == 8 * (int)sizeof(S) ? ~(S)0 : (S)((1ull << n) - 1);
+    S full;
+    if constexpr (KW == 3) full = bitk<W2>(n) - 1;
+    else full = n == 8 * (int)sizeof(S) ? ~(S)0 : (S)((1ull << n) - 1);
     const int64_t warps_total = (int64_t)gridDim.x * kWarps;
     uint32_t nclaim = 0;
     for (int64_t J = (int64_t)blockIdx.x * kWarps + w; J < M; J += warps_total) {
         const K key = load_key<KW>(Pkeys, J);
-        const S oa = (S)(uint64_t)key & full, ob = (S)(uint64_t)(key >> n) & full;
+        S oa, ob;
+        split_ab<S>(key, n, full, oa, ob);
         const S va = full & ~oa, vb = full & ~ob;
         double cJ[R], cmax = 0.0;
 #pragma unroll
         for (int v = 0; v < R; v++) cJ[v] = C[J * R + v], cmax = fmax(cmax, fabs(cJ[v]));
         __syncwarp();
         for (int o = lane; o < n; o += 32) {
-            const S lm = (S)((1ull << o) - 1);
-            if ((oa >> o) & 1) orb[__popcll(oa & lm)] = (uint8_t)o;
-            else orb[NO + __popcll(va & lm)] = (uint8_t)o;
-            if ((ob >> o) & 1) orb[2 * NO + __popcll(ob & lm)] = (uint8_t)o;
-            else orb[3 * NO + __popcll(vb & lm)] = (uint8_t)o;
+            if constexpr (KW == 3) {
+                const W2 lm = bitk<W2>(o) - 1;
+                if (has(oa, o)) orb[popck(oa & lm)] = (uint8_t)o;
+                else orb[NO + popck(va & lm)] = (uint8_t)o;
+                if (has(ob, o)) orb[2 * NO + popck(ob & lm)] = (uint8_t)o;
+                else orb[3 * NO + popck(vb & lm)] = (uint8_t)o;
+            } else {
+                const S lm = (S)((1ull << o) - 1);
+                if ((oa >> o) & 1) orb[__popcll(oa & lm)] = (uint8_t)o;
+                else orb[NO + __popcll(va & lm)] = (uint8_t)o;
+                if ((ob >> o) & 1) orb[2 * NO + __popcll(ob & lm)] = (uint8_t)o;
+                else orb[3 * NO + __popcll(vb & lm)] = (uint8_t)o;
+            }
         }
         __syncwarp();
-        const uint32_t target = batch ^ code_of64(s_g, ob);
+        uint32_t target;
+        if constexpr (KW == 3) target = batch ^ code_ofk(s_g, ob);
+        else target = batch ^ code_of64(s_g, ob);
 
         // alpha singles and alpha-alpha doubles: the beta string is unchanged
         if (target == 0) {
@@ -435,7 +488,7 @@ k_pt2_gen(const uint64_t *__restrict__ Pkeys, int64_t M, const double *__restric
                     insert<R, KW>(p, (key & ~bitk<K>(i)) | bitk<K>(a), h_single(p, key, i, a), cJ, cmax, nclaim);
                 } else {
                     const int s = t - c0;
-                    const uint16_t po = s_pair[s / qa], pv = s_pair[s % qa];
+                    const uint16_t po = pair_of(s / qa), pv = pair_of(s % qa);
                     const int i = orb[po & 0xFF], j = orb[po >> 8], a = orb[NO + (pv & 0xFF)], b = orb[NO + (pv >> 8)];
                     if (p.bss && p.bss[j * (j - 1) / 2 + i] * cmax < p.eps) continue;   // the class's bound
                     const K I = (key & ~bitk<K>(i) & ~bitk<K>(j)) | bitk<K>(a) | bitk<K>(b);
@@ -453,7 +506,7 @@ k_pt2_gen(const uint64_t *__restrict__ Pkeys, int64_t M, const double *__restric
             const uint32_t c = target ^ s_g[j];
             for (int q = s_cstart[c]; q < s_cstart[c + 1]; q++) {
                 const int v = s_obc[q];
-                if ((ob >> v) & 1) continue;
+                if (bit_of(ob, v)) continue;
                 const int slot = atomicAdd(&s_nl[w], 1);
                 s_list[w][slot] = (uint16_t)(j | (v << 8));
             }
@@ -479,13 +532,13 @@ k_pt2_gen(const uint64_t *__restrict__ Pkeys, int64_t M, const double *__restric
         // as in spinor mode made the 2M-space sum slower here: 7.9 -> 9.4 s.)
         const int pb = nb * (nb - 1) / 2;
         for (int t = lane; t < pb * ub; t += 32) {
-            const uint16_t po = s_pair[t / ub];
+            const uint16_t po = pair_of(t / ub);
             const int j1 = orb[2 * NO + (po & 0xFF)], j2 = orb[2 * NO + (po >> 8)], b1 = orb[3 * NO + t % ub];
             if (p.bss3 && p.bss3[(j2 * (j2 - 1) / 2 + j1) * n + b1] * cmax < p.eps) continue;   // the class's bound
             const uint32_t c = target ^ s_g[j1] ^ s_g[j2] ^ s_g[b1];
             for (int q = s_cstart[c]; q < s_cstart[c + 1]; q++) {
                 const int b2 = s_obc[q];
-                if (b2 <= b1 || ((ob >> b2) & 1)) continue;
+                if (b2 <= b1 || bit_of(ob, b2)) continue;
                 const K I = (key & ~bitk<K>(n + j1) & ~bitk<K>(n + j2)) | bitk<K>(n + b1) | bitk<K>(n + b2);
                 insert<R, KW>(p, I, h_double(p, key, n + j1, n + j2, n + b1, n + b2), cJ, cmax, nclaim);
             }
@@ -870,7 +923,7 @@ int grid_for(int64_t n)
 }
 
 // SPIN: complex spinor mode (C is [M][R] complex128); otherwise real spin-orbital mode.
-// KW: key words (1, 2, or 3 in spinor mode) of the determinant list.
+// KW: key words (1, 2 or 3) of the determinant list.
 template <int R, bool SPIN, int KW>
 int pt2_run(sci_ctx *ctx, const double *C, const double *E0h, double eps, size_t table_bytes, double *E2, int64_t *stats)
 {
@@ -1120,19 +1173,15 @@ int enpt2_dispatch(sci_ctx *ctx, const double *C, int nroots, const double *E0, 
             default: return pt2_run<8, true, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
         }
     }
-    if constexpr (KW == 3) {
-        return sci_fail(ctx, SCI_ERR_ARG, "enpt2: three-word keys in spinor mode only");
-    } else {
-        switch (nroots) {
-            case 1: return pt2_run<1, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
-            case 2: return pt2_run<2, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
-            case 3: return pt2_run<3, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
-            case 4: return pt2_run<4, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
-            case 5: return pt2_run<5, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
-            case 6: return pt2_run<6, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
-            case 7: return pt2_run<7, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
-            default: return pt2_run<8, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
-        }
+    switch (nroots) {
+        case 1: return pt2_run<1, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+        case 2: return pt2_run<2, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+        case 3: return pt2_run<3, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+        case 4: return pt2_run<4, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+        case 5: return pt2_run<5, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+        case 6: return pt2_run<6, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+        case 7: return pt2_run<7, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
+        default: return pt2_run<8, false, KW>(ctx, C, E0, eps, table_bytes, E2, stats);
     }
 }
 
@@ -1147,10 +1196,8 @@ extern "C" int sci_enpt2(sci_ctx *ctx, const double *C, int nroots, const double
         return sci_fail(ctx, SCI_ERR_ARG, "enpt2: real spin-orbital mode or complex spinor mode");
     if (ctx->nwords > 3 || ctx->norb > 64 * ctx->nwords)
         return sci_fail(ctx, SCI_ERR_ARG, "enpt2: at most 64 spin-orbitals or spinors per key word");
-    if (ctx->nwords == 3 && !ctx->spinors)
-        return sci_fail(ctx, SCI_ERR_ARG, "enpt2: three-word keys in spinor mode only");
-    if (ctx->nwords == 3 && ctx->norb == 192 && ctx->na >= 64)
-        return sci_fail(ctx, SCI_ERR_ARG, "enpt2: 64 or more electrons in 192 spinors");
+    if (ctx->nwords == 3 && ctx->norb == 192 && ctx->na + (ctx->spinors ? 0 : ctx->nb) >= 64)
+        return sci_fail(ctx, SCI_ERR_ARG, "enpt2: 64 or more electrons in 192 spin-orbitals or spinors");
     if (nroots < 1 || nroots > 8 || !E0 || !E2 || (ctx->M > 0 && !C))
         return sci_fail(ctx, SCI_ERR_ARG, "enpt2: need 1 <= nroots <= 8, C, E0 and E2");
     if (eps < 0.0) return sci_fail(ctx, SCI_ERR_ARG, "enpt2: eps < 0");
