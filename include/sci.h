@@ -346,8 +346,8 @@ int sci_rdm_grads(sci_ctx *ctx, const double *C, int nvec, const double *weights
  *   eps: screening; a generated contribution with |H_IJ| max_k |c_Jk| < eps is dropped
  *      (0 = exact).
  *   table_bytes: device memory for the hash table of one batch (8 + 8 nroots bytes per
- *      entry, 8 + 16 nroots in complex mode; with two-word keys 16 bytes of key and the
- *      entry rounded up to a multiple of 16 bytes; capacity the largest power of two
+ *      entry, 8 + 16 nroots in complex mode; with two- or three-word keys 16 or 24 bytes
+ *      of key and the entry rounded up to a multiple of 16 bytes; capacity the largest power of two
  *      within the budget, at least 256).  W is split into
  *      2^t batches (t <= 10) so that a batch's generated excitations fill at most 60% of
  *      it; a batch that still overflows (or probes too far) restarts the sum with twice

@@ -174,9 +174,9 @@ struct sci_ctx {
     int64_t M = 0;
     int na = 0, nb = 0, N = 0;
     uint64_t ref = 0;       // the reference (lowest orbitals), bits 0..63
-    uint64_t ref_hi = 0;    // its bits 64..127 (two-word lists)
+    uint64_t ref_hi = 0;    // its bits 64..127 (two- and three-word lists)
     uint64_t ref_w2 = 0;    // its bits 128..191 (three-word lists)
-    int nwords = 1;         // 64-bit words per key: 1, or 2 for more than 64 spin-orbitals
+    int nwords = 1;         // 64-bit words per key: 1, 2 past 64 spin-orbitals, 3 past 128
     uint64_t *keys = nullptr;  // [M][nwords], word 0 holding orbitals 0..63
     double *hdiag = nullptr;
     void *fref = nullptr;   // [norb][norb]

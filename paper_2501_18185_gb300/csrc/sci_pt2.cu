@@ -398,7 +398,7 @@ __device__ __forceinline__ void wq_flush(uint32_t *q, int &cnt, int lane, F &&pr
 }
 
 // warp per determinant J of P: the excitations of J that fall in batch `batch`.  KW = 1:
-// n <= 32 orbitals per spin (one-word keys); KW = 2: n <= 64 (two-word keys).
+// n <= 32 orbitals per spin (one-word keys); KW = 2: n <= 64; KW = 3: n <= 96.
 template <int R, int KW>
 // (one-word keys, one or two roots: held to 40 registers, 6 CTAs per SM, as the kernel
 // was before the two-word form; at 48 registers the 2M-space sum took 8.6 s, at 40 8.05 s)
