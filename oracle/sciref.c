@@ -47,10 +47,10 @@
 
 typedef double complex zd;
 
-/* An occupation string of up to 192 spin-orbitals or spinors: orbital p is bit p % 64 of
+/* An occupation string of up to 256 spin-orbitals or spinors: orbital p is bit p % 64 of
  * word p / 64 (determinants of up to 64 orbitals use word 0 only).  Strings compare as
- * unsigned 192-bit integers, word 2 most significant. */
-#define SCIREF_WORDS 3
+ * unsigned 256-bit integers, word 3 most significant. */
+#define SCIREF_WORDS 4
 #define SCIREF_MAXORB (64 * SCIREF_WORDS)
 typedef struct { uint64_t w[SCIREF_WORDS]; } bits_t;
 
@@ -69,15 +69,21 @@ static int spin_of(const sciref_ctx *c, int p) { return c->spinors ? 0 : (p >= c
 static int spatial_of(const sciref_ctx *c, int p) { return c->spinors ? p : (p % c->n); }
 
 static zd H1(const sciref_ctx *c, int p, int q) { return c->h[(size_t)p * c->norb + q]; }
+/* (pq|rs) over spin-orbitals or spinors: in spin-orbital mode zero unless p, q share a spin
+ * and r, s share a spin, else the spatial integral of their orbitals (Eq. Hamiltonian with
+ * a spin-free two-electron operator); the n^4 input values are kept as given. */
 static zd ERI(const sciref_ctx *c, int p, int q, int r, int s)
 {
-    size_t m = (size_t)c->norb;
-    return c->eri[((p * m + q) * m + r) * m + s];
+    if (spin_of(c, p) != spin_of(c, q) || spin_of(c, r) != spin_of(c, s)) return 0.0;
+    const size_t n = (size_t)c->n;
+    const size_t P = spatial_of(c, p), Q = spatial_of(c, q), R = spatial_of(c, r), S = spatial_of(c, s);
+    return c->eri[((P * n + Q) * n + R) * n + S];
 }
 
 /* ------------------------------------------------------------------ creation */
 /* h: n*n, eri: n^4 (row-major, [p][q][r][s] = (pq|rs)); complex data interleaved re,im.
- * Spin-orbital mode expands them to the 2n spin-orbitals. */
+ * Spin-orbital mode expands h to the 2n spin-orbitals; ERI() maps spin-orbital indices to
+ * the n^4 values. */
 int sciref_create(sciref_ctx **out, int is_complex, int spinors, int n,
                   const double *h, const double *eri)
 {
@@ -88,9 +94,9 @@ int sciref_create(sciref_ctx **out, int is_complex, int spinors, int n,
     c->spinors = spinors;
     c->n = n;
     c->norb = spinors ? n : 2 * n;
-    size_t m = (size_t)c->norb;
+    size_t m = (size_t)c->norb, n4 = (size_t)n * n * n * n;
     c->h = (zd *)calloc(m * m, sizeof(zd));
-    c->eri = (zd *)calloc(m * m * m * m, sizeof(zd));
+    c->eri = (zd *)calloc(n4, sizeof(zd));
     if (!c->h || !c->eri) { free(c->h); free(c->eri); free(c); return SCIREF_ERR_ARG; }
     for (int p = 0; p < c->norb; p++)
         for (int q = 0; q < c->norb; q++) {
@@ -98,18 +104,7 @@ int sciref_create(sciref_ctx **out, int is_complex, int spinors, int n,
             size_t s = (size_t)spatial_of(c, p) * n + spatial_of(c, q);
             c->h[p * m + q] = is_complex ? CMPLX(h[2 * s], h[2 * s + 1]) : CMPLX(h[s], 0.0);
         }
-    for (int p = 0; p < c->norb; p++)
-        for (int q = 0; q < c->norb; q++) {
-            if (spin_of(c, p) != spin_of(c, q)) continue;
-            for (int r = 0; r < c->norb; r++)
-                for (int s = 0; s < c->norb; s++) {
-                    if (spin_of(c, r) != spin_of(c, s)) continue;
-                    size_t P = spatial_of(c, p), Q = spatial_of(c, q), R = spatial_of(c, r), S = spatial_of(c, s);
-                    size_t t = ((P * n + Q) * n + R) * n + S;
-                    c->eri[((p * m + q) * m + r) * m + s] =
-                        is_complex ? CMPLX(eri[2 * t], eri[2 * t + 1]) : CMPLX(eri[t], 0.0);
-                }
-        }
+    for (size_t t = 0; t < n4; t++) c->eri[t] = is_complex ? CMPLX(eri[2 * t], eri[2 * t + 1]) : CMPLX(eri[t], 0.0);
     *out = c;
     return SCIREF_OK;
 }
@@ -125,7 +120,7 @@ void sciref_destroy(sciref_ctx *c)
 
 static int key_cmp(bits_t a, bits_t b);
 
-/* keys: M strings of nwords (1 to 3) 64-bit words each, word 0 holding orbitals 0..63;
+/* keys: M strings of nwords (1 to 4) 64-bit words each, word 0 holding orbitals 0..63;
  * the list must be strictly ascending as unsigned (64 x nwords)-bit integers. */
 int sciref_set_determinants_w(sciref_ctx *c, const uint64_t *keys, int nwords, int64_t M)
 {
@@ -161,7 +156,7 @@ int sciref_set_threads(int n)
 static int occupied(bits_t d, int p) { return (int)((d.w[p >> 6] >> (p & 63)) & 1u); }
 static bits_t with_bit(bits_t d, int p) { d.w[p >> 6] |= 1ull << (p & 63); return d; }
 static bits_t without_bit(bits_t d, int p) { d.w[p >> 6] &= ~(1ull << (p & 63)); return d; }
-/* -1, 0, +1 as unsigned 192-bit integers */
+/* -1, 0, +1 as unsigned 256-bit integers */
 static int key_cmp(bits_t a, bits_t b)
 {
     for (int t = SCIREF_WORDS - 1; t >= 0; t--)
