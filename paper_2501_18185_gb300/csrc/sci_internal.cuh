@@ -75,6 +75,13 @@ __host__ __device__ __forceinline__ uint32_t make_meta(int x, int par, int off, 
     return (uint32_t)x | ((uint32_t)par << 8) | ((uint32_t)off << 9) | ((uint32_t)size << 20);
 }
 constexpr int kMaxBucket1 = 2047;   // the largest (N-1) bucket the meta word holds
+// 64-bit words of an occupation string at most: 256 spin-orbitals or spinors, the most the
+// 8-bit orbital fields of the bucket codes hold
+constexpr int kMaxWords = 4;
+// the reference string, word w holding orbitals 64w .. 64w + 63
+struct RefW {
+    uint64_t w[kMaxWords];
+};
 // (N-2) buckets of more members than this go through the tiled sigma kernel by default.
 // Measured on 2M-determinant spaces (doubles kernel, FP64, one vector): buckets of up to
 // 1,089 (80 spin-orbitals) 12.04 ms all in windows, 9.12 ms with those above 512 tiled;
@@ -175,8 +182,9 @@ struct sci_ctx {
     int na = 0, nb = 0, N = 0;
     uint64_t ref = 0;       // the reference (lowest orbitals), bits 0..63
     uint64_t ref_hi = 0;    // its bits 64..127 (two- and three-word lists)
-    uint64_t ref_w2 = 0;    // its bits 128..191 (three-word lists)
-    int nwords = 1;         // 64-bit words per key: 1, 2 past 64 spin-orbitals, 3 past 128
+    uint64_t ref_w2 = 0;    // its bits 128..191 (three- and four-word lists)
+    uint64_t ref_w3 = 0;    // its bits 192..255 (four-word lists)
+    int nwords = 1;         // 64-bit words per key: 1, 2 past 64 spin-orbitals, 3 past 128, 4 past 192
     uint64_t *keys = nullptr;  // [M][nwords], word 0 holding orbitals 0..63
     double *hdiag = nullptr;
     void *fref = nullptr;   // [norb][norb]
@@ -244,6 +252,9 @@ struct sci_ctx {
     int *status = nullptr;  // device status word (sci::DevErr bits)
     size_t bytes_held = 0;
 };
+
+// the context's reference string over all words
+inline sci::RefW ref_words(const sci_ctx *ctx) { return sci::RefW{{ctx->ref, ctx->ref_hi, ctx->ref_w2, ctx->ref_w3}}; }
 
 // helpers shared by the translation units of the library
 int sci_fail(sci_ctx *ctx, int code, const std::string &msg);

@@ -1195,7 +1195,7 @@ extern "C" int sci_enpt2(sci_ctx *ctx, const double *C, int nroots, const double
     if (ctx->spinors != ctx->cplx)
         return sci_fail(ctx, SCI_ERR_ARG, "enpt2: real spin-orbital mode or complex spinor mode");
     if (ctx->nwords > 3 || ctx->norb > 64 * ctx->nwords)
-        return sci_fail(ctx, SCI_ERR_ARG, "enpt2: at most 64 spin-orbitals or spinors per key word");
+        return sci_fail(ctx, SCI_ERR_ARG, "enpt2: at most three key words (192 spin-orbitals or spinors)");
     if (ctx->nwords == 3 && ctx->norb == 192 && ctx->na + (ctx->spinors ? 0 : ctx->nb) >= 64)
         return sci_fail(ctx, SCI_ERR_ARG, "enpt2: 64 or more electrons in 192 spin-orbitals or spinors");
     if (nroots < 1 || nroots > 8 || !E0 || !E2 || (ctx->M > 0 && !C))

@@ -97,11 +97,8 @@ template <int KW> __device__ __forceinline__ bool occ(const Str<KW> &s, int p)
 {
     return (s.w[p >> 6] >> (p & 63)) & 1;
 }
-// the reference string (lowest orbitals occupied) in three words, orbitals 64w .. 64w + 63
-struct Ref3 {
-    uint64_t w[3];
-};
-Ref3 ref3(const sci_ctx *ctx) { return Ref3{{ctx->ref, ctx->ref_hi, ctx->ref_w2}}; }
+using Ref3 = sci::RefW;   // the reference string over all words
+inline sci::RefW ref3(const sci_ctx *ctx) { return ref_words(ctx); }
 
 // Diagonal class: O[p][r] = sum_I w_I n_p n_r in the reference decomposition n = n_ref + d
 // (d = key ^ ref has a few bits), accumulated per CTA in shared memory ([norb]^2 doubles,
@@ -370,7 +367,8 @@ template <typename TC, int NV>
 int launch_walks(sci_ctx *ctx, const Walk<TC> &w)
 {
     if (ctx->e1 > 0) {
-        auto ks = ctx->nwords == 3   ? k_rdm_singles<TC, NV, 3>
+        auto ks = ctx->nwords == 4   ? k_rdm_singles<TC, NV, 4>
+                  : ctx->nwords == 3 ? k_rdm_singles<TC, NV, 3>
                   : ctx->nwords == 2 ? k_rdm_singles<TC, NV, 2>
                                      : k_rdm_singles<TC, NV, 1>;
         ks<<<grid_for(ctx->e1), kThreads, 0, ctx->stream>>>(ctx->e1_idx, ctx->e1_S, ctx->e1_meta, ctx->e1, ctx->norb,
@@ -429,7 +427,8 @@ int rdm_run(sci_ctx *ctx, const TC *C, int nvec, const double *wk_dev, TC *g1, T
     // 168 orbitals), else accumulated in global memory
     size_t diag_smem = sizeof(double) * ((size_t)norb * norb + norb);
     const bool diag_sm = diag_smem + 1024 <= 227 * 1024;
-    auto kd = ctx->nwords == 3 ? (diag_sm ? k_rdm_diag<TC, 3, true> : k_rdm_diag<TC, 3, false>)
+    auto kd = ctx->nwords == 4   ? (diag_sm ? k_rdm_diag<TC, 4, true> : k_rdm_diag<TC, 4, false>)
+              : ctx->nwords == 3 ? (diag_sm ? k_rdm_diag<TC, 3, true> : k_rdm_diag<TC, 3, false>)
               : ctx->nwords == 2 ? k_rdm_diag<TC, 2, true>
                                  : k_rdm_diag<TC, 1, true>;
     if (!diag_sm) diag_smem = 0;
@@ -569,7 +568,7 @@ extern "C" int sci_rdm12(sci_ctx *ctx, const void *C, int nvec, const double *we
     if (!ctx) return SCI_ERR_ARG;
     if (!ctx->have_ints || !ctx->have_dets) return sci_fail(ctx, SCI_ERR_STATE, "rdm12: integrals and determinants first");
     if (nvec < 1 || !rdm1 || (ctx->M > 0 && !C)) return sci_fail(ctx, SCI_ERR_ARG, "rdm12: need nvec >= 1, C and rdm1");
-    if (ctx->norb > 192 || ctx->nwords > 3) return sci_fail(ctx, SCI_ERR_ARG, "rdm12: at most 192 orbitals");
+    if (ctx->norb > 256 || ctx->nwords > sci::kMaxWords) return sci_fail(ctx, SCI_ERR_ARG, "rdm12: at most 256 orbitals");
     if (sci_cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) return SCI_ERR_CUDA;
     // weights to the device (a host array of nvec doubles, NULL = all ones)
     const size_t wbytes = sizeof(double) * nvec;

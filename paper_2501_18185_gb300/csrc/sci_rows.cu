@@ -149,9 +149,9 @@ __global__ void k_cost1(const uint32_t *__restrict__ e_idx, const uint32_t *__re
 
 // Narrow one table to the buckets with a member in [rb, re).  A: idx, B: code or S,
 // C: pos or meta (the field that locates the bucket start).
-// a spectator string of three words, moved as one entry
-struct Words3 {
-    uint64_t w[3];
+// a spectator string of K words, moved as one entry
+template <int K> struct Words {
+    uint64_t w[K];
 };
 
 template <bool ONE, typename B>
@@ -334,10 +334,15 @@ extern "C" int sci_set_row_range(sci_ctx *ctx, int64_t row_begin, int64_t row_en
     int rc = narrow<false, uint32_t>(ctx, ctx->e2, ctx->e2_idx, ctx->e2_code, ctx->e2_pos, row_begin, row_end,
                                      ctx->r2_idx, ctx->r2_code, ctx->r2_pos, ctx->r2);
     if (rc == SCI_OK) {
-        if (ctx->nwords == 3) {   // spectator strings of three words: 24 bytes per entry
-            Words3 *o = nullptr;
-            rc = narrow<true, Words3>(ctx, ctx->e1, ctx->e1_idx, reinterpret_cast<const Words3 *>(ctx->e1_S),
-                                      ctx->e1_meta, row_begin, row_end, ctx->r1_idx, o, ctx->r1_meta, ctx->r1);
+        if (ctx->nwords == 4) {   // spectator strings of four words: 32 bytes per entry
+            Words<4> *o = nullptr;
+            rc = narrow<true, Words<4>>(ctx, ctx->e1, ctx->e1_idx, reinterpret_cast<const Words<4> *>(ctx->e1_S),
+                                        ctx->e1_meta, row_begin, row_end, ctx->r1_idx, o, ctx->r1_meta, ctx->r1);
+            ctx->r1_S = reinterpret_cast<uint64_t *>(o);
+        } else if (ctx->nwords == 3) {   // spectator strings of three words: 24 bytes per entry
+            Words<3> *o = nullptr;
+            rc = narrow<true, Words<3>>(ctx, ctx->e1, ctx->e1_idx, reinterpret_cast<const Words<3> *>(ctx->e1_S),
+                                        ctx->e1_meta, row_begin, row_end, ctx->r1_idx, o, ctx->r1_meta, ctx->r1);
             ctx->r1_S = reinterpret_cast<uint64_t *>(o);
         } else if (ctx->nwords == 2) {   // spectator strings of two words: 16 bytes per entry
             ulonglong2 *o = nullptr;

@@ -294,7 +294,8 @@ __global__ void k_diag(const uint64_t *__restrict__ keys, int64_t M, int norb, c
 
 // fref[i][a] = h_ai + sum_{k in ref} g_so[k][i][a]
 template <typename S>
-__global__ void k_fref(int norb, Kw<3> ref, const S *__restrict__ h_so, const S *__restrict__ g_so, S *__restrict__ fref)
+__global__ void k_fref(int norb, Kw<sci::kMaxWords> ref, const S *__restrict__ h_so, const S *__restrict__ g_so,
+                       S *__restrict__ fref)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= norb * norb) return;
@@ -570,8 +571,9 @@ int build_buckets(sci_ctx *ctx, int holes, int per_det, Buckets &B)
     int nitems = (int)total;
     int nruns = 0;
     if (ctx->nwords > 1) {
-        int rc = ctx->nwords == 2 ? sort_runs_w<2>(ctx, holes, per_det, total, B, nruns)
-                                  : sort_runs_w<3>(ctx, holes, per_det, total, B, nruns);
+        int rc = ctx->nwords == 2   ? sort_runs_w<2>(ctx, holes, per_det, total, B, nruns)
+                 : ctx->nwords == 3 ? sort_runs_w<3>(ctx, holes, per_det, total, B, nruns)
+                                    : sort_runs_w<4>(ctx, holes, per_det, total, B, nruns);
         if (rc != SCI_OK) return rc;
         return order_runs(ctx, nruns, B);
     }
@@ -820,7 +822,7 @@ void free_dets(sci_ctx *ctx)
     free_held(ctx, ctx->e1_meta);
     ctx->have_dets = 0;
     ctx->nwords = 1;
-    ctx->ref_hi = ctx->ref_w2 = 0;
+    ctx->ref_hi = ctx->ref_w2 = ctx->ref_w3 = 0;
     ctx->M = 0;
     ctx->e1 = ctx->e2 = ctx->nb1 = ctx->nb2 = 0;
     ctx->maxb1 = ctx->maxb2 = 0;
@@ -850,20 +852,26 @@ int compute_diag_fref(sci_ctx *ctx)
     if (!ctx->fref) SCI_CK(alloc_held(ctx, &ctx->fref, (size_t)norb * norb * scalar_bytes(ctx)));
     int nn = norb * norb;
     if (ctx->cplx) {
-        k_fref<zdbl><<<(nn + 255) / 256, 256, 0, st>>>(norb, Kw<3>{{ctx->ref, ctx->ref_hi, ctx->ref_w2}},
+        k_fref<zdbl><<<(nn + 255) / 256, 256, 0, st>>>(norb, Kw<4>{{ctx->ref, ctx->ref_hi, ctx->ref_w2, ctx->ref_w3}},
                                                         (const zdbl *)ctx->h_so, (const zdbl *)ctx->g_so,
                                                         (zdbl *)ctx->fref);
         if (ctx->M > 0) {
-            auto kd = ctx->nwords == 3 ? k_diag<zdbl, 3> : ctx->nwords == 2 ? k_diag<zdbl, 2> : k_diag<zdbl, 1>;
+            auto kd = ctx->nwords == 4   ? k_diag<zdbl, 4>
+                      : ctx->nwords == 3 ? k_diag<zdbl, 3>
+                      : ctx->nwords == 2 ? k_diag<zdbl, 2>
+                                         : k_diag<zdbl, 1>;
             kd<<<grid_for(ctx->M), 256, 0, st>>>(ctx->keys, ctx->M, norb, (const zdbl *)ctx->h_so,
                                                  (const zdbl *)ctx->jd, (const zdbl *)ctx->kd, ctx->hdiag);
         }
     } else {
-        k_fref<double><<<(nn + 255) / 256, 256, 0, st>>>(norb, Kw<3>{{ctx->ref, ctx->ref_hi, ctx->ref_w2}},
+        k_fref<double><<<(nn + 255) / 256, 256, 0, st>>>(norb, Kw<4>{{ctx->ref, ctx->ref_hi, ctx->ref_w2, ctx->ref_w3}},
                                                           (const double *)ctx->h_so, (const double *)ctx->g_so,
                                                           (double *)ctx->fref);
         if (ctx->M > 0) {
-            auto kd = ctx->nwords == 3 ? k_diag<double, 3> : ctx->nwords == 2 ? k_diag<double, 2> : k_diag<double, 1>;
+            auto kd = ctx->nwords == 4   ? k_diag<double, 4>
+                      : ctx->nwords == 3 ? k_diag<double, 3>
+                      : ctx->nwords == 2 ? k_diag<double, 2>
+                                         : k_diag<double, 1>;
             kd<<<grid_for(ctx->M), 256, 0, st>>>(ctx->keys, ctx->M, norb, (const double *)ctx->h_so,
                                                  (const double *)ctx->jd, (const double *)ctx->kd, ctx->hdiag);
         }
@@ -1075,8 +1083,8 @@ int set_ints(sci_ctx *ctx, int scalar, int mode, int n, const void *h, const voi
     ctx->err.clear();
     if (scalar != SCI_REAL64 && scalar != SCI_COMPLEX128) return sci_fail(ctx, SCI_ERR_ARG, "bad scalar type");
     if (mode != SCI_SPIN_ORBITALS && mode != SCI_SPINORS) return sci_fail(ctx, SCI_ERR_ARG, "bad mode");
-    if (mode == SCI_SPIN_ORBITALS && (n < 1 || n > 96)) return sci_fail(ctx, SCI_ERR_ARG, "spin-orbital mode needs 1 <= n <= 96");
-    if (mode == SCI_SPINORS && (n < 1 || n > 192)) return sci_fail(ctx, SCI_ERR_ARG, "spinor mode needs 1 <= n <= 192");
+    if (mode == SCI_SPIN_ORBITALS && (n < 1 || n > 128)) return sci_fail(ctx, SCI_ERR_ARG, "spin-orbital mode needs 1 <= n <= 128");
+    if (mode == SCI_SPINORS && (n < 1 || n > 256)) return sci_fail(ctx, SCI_ERR_ARG, "spinor mode needs 1 <= n <= 256");
     if (mode == SCI_SPIN_ORBITALS && scalar != SCI_REAL64)
         return sci_fail(ctx, SCI_ERR_ARG, "spin-orbital mode takes real integrals");
     if (!h) return sci_fail(ctx, SCI_ERR_ARG, "h is NULL");
@@ -1235,7 +1243,7 @@ extern "C" int sci_set_determinants(sci_ctx *ctx, const uint64_t *keys, int64_t 
 {
     if (!ctx) return SCI_ERR_ARG;
     if (ctx->have_ints && ctx->norb > 64)
-        return sci_fail(ctx, SCI_ERR_ARG, "more than 64 spin-orbitals: use sci_set_determinants_w with two or three words");
+        return sci_fail(ctx, SCI_ERR_ARG, "more than 64 spin-orbitals: use sci_set_determinants_w with two to four words");
     return set_dets(ctx, keys, 1, M, n_alpha, n_beta, keys_on_device);
 }
 
@@ -1243,7 +1251,7 @@ extern "C" int sci_set_determinants_w(sci_ctx *ctx, const uint64_t *keys, int nw
                                       int n_beta, int keys_on_device)
 {
     if (!ctx) return SCI_ERR_ARG;
-    if (nwords < 1 || nwords > 3) return sci_fail(ctx, SCI_ERR_ARG, "nwords must be 1, 2 or 3");
+    if (nwords < 1 || nwords > sci::kMaxWords) return sci_fail(ctx, SCI_ERR_ARG, "nwords must be 1 to 4");
     if (ctx->have_ints && ctx->norb > 64 * nwords)
         return sci_fail(ctx, SCI_ERR_ARG, "more spin-orbitals than the key words hold (64 per word)");
     return set_dets(ctx, keys, nwords, M, n_alpha, n_beta, keys_on_device);
@@ -1299,8 +1307,8 @@ int set_dets(sci_ctx *ctx, const uint64_t *keys, int nwords, int64_t M, int n_al
     ctx->nwords = nwords;
     {
         // the reference: the lowest N spinors, or the lowest n_alpha alpha and n_beta beta
-        // orbitals, over three words
-        uint64_t r[3] = {0, 0, 0};
+        // orbitals, over four words
+        uint64_t r[4] = {0, 0, 0, 0};
         auto set = [&](int p) { r[p >> 6] |= 1ull << (p & 63); };
         if (ctx->spinors) {
             for (int p = 0; p < N; p++) set(p);
@@ -1311,6 +1319,7 @@ int set_dets(sci_ctx *ctx, const uint64_t *keys, int nwords, int64_t M, int n_al
         ctx->ref = r[0];
         ctx->ref_hi = r[1];
         ctx->ref_w2 = r[2];
+        ctx->ref_w3 = r[3];
     }
 
     SCI_CK(alloc_held(ctx, (void **)&ctx->keys, (size_t)M * 8 * nwords));
@@ -1323,7 +1332,8 @@ int set_dets(sci_ctx *ctx, const uint64_t *keys, int nwords, int64_t M, int n_al
     SCI_CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), st));
     if (M > 0) {
         KeyRule kr{ctx->spinors, ctx->n, n_alpha, n_beta, N};
-        if (nwords == 3) k_validate<3><<<grid_for(M), 256, 0, st>>>(ctx->keys, M, kr, ctx->status);
+        if (nwords == 4) k_validate<4><<<grid_for(M), 256, 0, st>>>(ctx->keys, M, kr, ctx->status);
+        else if (nwords == 3) k_validate<3><<<grid_for(M), 256, 0, st>>>(ctx->keys, M, kr, ctx->status);
         else if (nwords == 2) k_validate<2><<<grid_for(M), 256, 0, st>>>(ctx->keys, M, kr, ctx->status);
         else k_validate<1><<<grid_for(M), 256, 0, st>>>(ctx->keys, M, kr, ctx->status);
         SCI_CK(cudaGetLastError());
@@ -1353,7 +1363,7 @@ int set_dets(sci_ctx *ctx, const uint64_t *keys, int nwords, int64_t M, int n_al
         SCI_CK(alloc_held(ctx, (void **)&ctx->e2_code, (size_t)B.entries * 4));
         SCI_CK(alloc_held(ctx, (void **)&ctx->e2_pos, (size_t)B.entries * 4));
         if (B.kept > 0) {
-            auto kf = nwords == 3 ? k_fill2<3> : nwords == 2 ? k_fill2<2> : k_fill2<1>;
+            auto kf = nwords == 4 ? k_fill2<4> : nwords == 3 ? k_fill2<3> : nwords == 2 ? k_fill2<2> : k_fill2<1>;
             kf<<<grid_for(B.kept * 32), 256, 0, st>>>(B.order.as<uint32_t>(), B.counts.as<uint32_t>(),
                                                           B.offsets.as<uint32_t>(), B.newoff.as<uint32_t>(),
                                                           B.ukeys.as<uint64_t>(), B.vals_sorted.as<uint64_t>(), B.kept,
@@ -1374,7 +1384,7 @@ int set_dets(sci_ctx *ctx, const uint64_t *keys, int nwords, int64_t M, int n_al
         SCI_CK(alloc_held(ctx, (void **)&ctx->e1_S, (size_t)B.entries * 8 * nwords));
         SCI_CK(alloc_held(ctx, (void **)&ctx->e1_meta, (size_t)B.entries * 4));
         if (B.kept > 0) {
-            auto kf = nwords == 3 ? k_fill1<3> : nwords == 2 ? k_fill1<2> : k_fill1<1>;
+            auto kf = nwords == 4 ? k_fill1<4> : nwords == 3 ? k_fill1<3> : nwords == 2 ? k_fill1<2> : k_fill1<1>;
             kf<<<grid_for(B.kept * 32), 256, 0, st>>>(B.order.as<uint32_t>(), B.counts.as<uint32_t>(),
                                                           B.offsets.as<uint32_t>(), B.newoff.as<uint32_t>(),
                                                           B.ukeys.as<uint64_t>(), B.vals_sorted.as<uint64_t>(), B.kept,

@@ -791,7 +791,7 @@ k_doubles_tiled(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__
 template <typename TS, typename TC, int NV, bool RANGED, bool STORE = false, int KW = 1>
 __global__ void __launch_bounds__(kThreads)
 k_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S, const uint32_t *__restrict__ e_meta,
-          int64_t E, int norb, uint64_t ref, uint64_t ref_hi, uint64_t ref_w2, const TS *__restrict__ fref, const TS *__restrict__ g_so,
+          int64_t E, int norb, sci::RefW ref, const TS *__restrict__ fref, const TS *__restrict__ g_so,
           const TC *__restrict__ C, int nvec, int v0, typename AccOf<TS>::type *__restrict__ Sout, sci::RowRange rr, const uint32_t *__restrict__ slot)
 {
     using TA = typename AccOf<TS>::type;
@@ -808,7 +808,7 @@ k_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S, 
         uint64_t part[KW], holes[KW];   // S \ ref and ref \ S, word w holding orbitals 64w..64w+63
 #pragma unroll
         for (int w_ = 0; w_ < KW; w_++) {
-            const uint64_t Sw = e_S[p * KW + w_], rw = w_ == 0 ? ref : w_ == 1 ? ref_hi : ref_w2;
+            const uint64_t Sw = e_S[p * KW + w_], rw = ref.w[w_];
             part[w_] = Sw & ~rw, holes[w_] = rw & ~Sw;
         }
         TA acc[NV];
@@ -858,7 +858,7 @@ using sci::ds_add;
 template <int NV, bool RANGED, bool STORE = false, int KW = 1>
 __global__ void __launch_bounds__(kThreads)
 k_singles_ds(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S, const uint32_t *__restrict__ e_meta,
-             int64_t E, int norb, uint64_t ref, uint64_t ref_hi, uint64_t ref_w2, const float2 *__restrict__ fref2, const float2 *__restrict__ g2,
+             int64_t E, int norb, sci::RefW ref, const float2 *__restrict__ fref2, const float2 *__restrict__ g2,
              const float2 *__restrict__ C2, int nvec, int v0, double *__restrict__ Sout, sci::RowRange rr, const uint32_t *__restrict__ slot)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
@@ -874,7 +874,7 @@ k_singles_ds(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_
         uint64_t part[KW], holes[KW];   // S \ ref and ref \ S, word w holding orbitals 64w..64w+63
 #pragma unroll
         for (int w_ = 0; w_ < KW; w_++) {
-            const uint64_t Sw = e_S[p * KW + w_], rw = w_ == 0 ? ref : w_ == 1 ? ref_hi : ref_w2;
+            const uint64_t Sw = e_S[p * KW + w_], rw = ref.w[w_];
             part[w_] = Sw & ~rw, holes[w_] = rw & ~Sw;
         }
         Ds acc[NV];
@@ -919,7 +919,7 @@ k_singles_ds(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_
 template <int NV, bool RANGED, bool STORE = false, int KW = 1>
 __global__ void __launch_bounds__(kThreads)
 k_singles_dsz(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S,
-              const uint32_t *__restrict__ e_meta, int64_t E, int norb, uint64_t ref, uint64_t ref_hi, uint64_t ref_w2,
+              const uint32_t *__restrict__ e_meta, int64_t E, int norb, sci::RefW ref,
               const float4 *__restrict__ fref4, const float4 *__restrict__ g4, const float4 *__restrict__ C4,
               int nvec, int v0, zdbl *__restrict__ Sout, sci::RowRange rr, const uint32_t *__restrict__ slot)
 {
@@ -936,7 +936,7 @@ k_singles_dsz(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e
         uint64_t part[KW], holes[KW];   // S \ ref and ref \ S, word w holding orbitals 64w..64w+63
 #pragma unroll
         for (int w_ = 0; w_ < KW; w_++) {
-            const uint64_t Sw = e_S[p * KW + w_], rw = w_ == 0 ? ref : w_ == 1 ? ref_hi : ref_w2;
+            const uint64_t Sw = e_S[p * KW + w_], rw = ref.w[w_];
             part[w_] = Sw & ~rw, holes[w_] = rw & ~Sw;
         }
         Ds ar[NV], ai[NV];
@@ -1217,7 +1217,7 @@ int f32_groups(sci_ctx *ctx, const Tabs &T, const float *C, double *S, int nvec)
 }
 
 // paired-FP32 singles; real coefficients may come in as double or float; keys of one to
-// three words (KW)
+// four words (KW)
 template <bool RG, bool ST, bool CPLX, int NV, typename TC, int KW>
 int launch_singles_ds_w(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int nvec, int v0)
 {
@@ -1226,14 +1226,14 @@ int launch_singles_ds_w(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int
         k_split_cz<<<grid_for(ctx->M * NV), kThreads, 0, ctx->stream>>>((const zdbl *)C, ctx->M, nvec, v0, NV,
                                                                         (float4 *)ctx->c_ds);
         k_singles_dsz<NV, RG, ST, KW><<<g, kThreads, 0, ctx->stream>>>(
-            T.e1_idx, T.e1_S, T.e1_meta, T.e1, ctx->norb, ctx->ref, ctx->ref_hi, ctx->ref_w2, (const float4 *)ctx->fref_ds,
+            T.e1_idx, T.e1_S, T.e1_meta, T.e1, ctx->norb, ref_words(ctx), (const float4 *)ctx->fref_ds,
             (const float4 *)ctx->g_ds, (const float4 *)ctx->c_ds, nvec, v0, (zdbl *)S, T.rr,
             ST ? ctx->det_inv1 : nullptr);
     } else {
         k_split_c<TC><<<grid_for(ctx->M * NV), kThreads, 0, ctx->stream>>>((const TC *)C, ctx->M, nvec, v0, NV,
                                                                            (float2 *)ctx->c_ds);
         k_singles_ds<NV, RG, ST, KW><<<g, kThreads, 0, ctx->stream>>>(
-            T.e1_idx, T.e1_S, T.e1_meta, T.e1, ctx->norb, ctx->ref, ctx->ref_hi, ctx->ref_w2, (const float2 *)ctx->fref_ds,
+            T.e1_idx, T.e1_S, T.e1_meta, T.e1, ctx->norb, ref_words(ctx), (const float2 *)ctx->fref_ds,
             (const float2 *)ctx->g_ds, (const float2 *)ctx->c_ds, nvec, v0, (double *)S, T.rr,
             ST ? ctx->det_inv1 : nullptr);
     }
@@ -1244,6 +1244,7 @@ template <bool RG, bool ST, bool CPLX, int NV, typename TC = double>
 int launch_singles_ds(sci_ctx *ctx, const Tabs &T, const void *C, void *S, int nvec, int v0)
 {
     if (T.e1 == 0) return SCI_OK;
+    if (ctx->nwords == 4) return launch_singles_ds_w<RG, ST, CPLX, NV, TC, 4>(ctx, T, C, S, nvec, v0);
     if (ctx->nwords == 3) return launch_singles_ds_w<RG, ST, CPLX, NV, TC, 3>(ctx, T, C, S, nvec, v0);
     if (ctx->nwords == 2) return launch_singles_ds_w<RG, ST, CPLX, NV, TC, 2>(ctx, T, C, S, nvec, v0);
     return launch_singles_ds_w<RG, ST, CPLX, NV, TC, 1>(ctx, T, C, S, nvec, v0);
@@ -1272,11 +1273,12 @@ template <bool RG, bool ST, typename TS, typename TC, int NV>
 int launch_singles(sci_ctx *ctx, const Tabs &T, const TC *C, typename AccOf<TS>::type *S, int nvec, int v0)
 {
     if (T.e1 == 0) return SCI_OK;
-    auto kern = ctx->nwords == 3   ? k_singles<TS, TC, NV, RG, ST, 3>
+    auto kern = ctx->nwords == 4   ? k_singles<TS, TC, NV, RG, ST, 4>
+                : ctx->nwords == 3 ? k_singles<TS, TC, NV, RG, ST, 3>
                 : ctx->nwords == 2 ? k_singles<TS, TC, NV, RG, ST, 2>
                                    : k_singles<TS, TC, NV, RG, ST, 1>;
-    kern<<<grid_for(T.e1), kThreads, 0, ctx->stream>>>(T.e1_idx, T.e1_S, T.e1_meta, T.e1, ctx->norb, ctx->ref,
-                                                       ctx->ref_hi, ctx->ref_w2, (const TS *)ctx->fref, (const TS *)ctx->g_so, C,
+    kern<<<grid_for(T.e1), kThreads, 0, ctx->stream>>>(T.e1_idx, T.e1_S, T.e1_meta, T.e1, ctx->norb, ref_words(ctx),
+                                                       (const TS *)ctx->fref, (const TS *)ctx->g_so, C,
                                                        nvec, v0, S, T.rr, ST ? ctx->det_inv1 : nullptr);
     return sci_cuda_check(ctx, cudaGetLastError(), "k_singles launch");
 }

@@ -438,11 +438,18 @@ def selected_three_word(n: int = 70, na: int = 3, nb: int = 3, M: int = 60000, n
     and sorted as (64 x 3)-bit integers.  Alpha bits 0..n-1, beta bits n..2n-1: for
     64 < n <= 96 the alpha string crosses words 0/1 and the beta string words 1/2.
     Draw order: integrals, triples, c."""
+    return selected_words(n, na, nb, M, 3, naux, nvec, seed, "sel3w")
+
+
+def selected_words(n: int, na: int, nb: int, M: int, nwords: int, naux: int = 40, nvec: int = 1,
+                   seed: int = 2501181863, tag: str | None = None) -> Workload:
+    """The recipe of selected_three_word with keys of `nwords` words (64 nwords >= 2n): for
+    96 < n <= 128 and four words the beta string crosses words 1, 2 and 3."""
     rng = np.random.default_rng(seed)
     ints = real_integrals(rng, n, naux, 0.95)
 
     def dets(A, B):
-        return words_from_occ(np.concatenate([A, B + n], axis=1), 3)
+        return words_from_occ(np.concatenate([A, B + n], axis=1), nwords)
 
     parts = []
     for level in range(3):
@@ -476,8 +483,8 @@ def selected_three_word(n: int = 70, na: int = 3, nb: int = 3, M: int = 60000, n
     for _ in range(nvec):
         v = np.exp(-lev.astype(np.float64)) * rng.choice(np.array([-1.0, 1.0]), size=M)
         cols.append(v / np.linalg.norm(v))
-    return Workload(f"sel3w_{n}o_{na}a{nb}b_M{M}", "spin_orbitals", n, na, nb, keys, ints, np.stack(cols, axis=1),
-                    {"hf_words": hf})
+    return Workload(f"{tag or f'sel{nwords}w'}_{n}o_{na}a{nb}b_M{M}", "spin_orbitals", n, na, nb, keys, ints,
+                    np.stack(cols, axis=1), {"hf_words": hf})
 
 
 def selected_spinor_words(n: int = 136, N: int = 14, M: int = 1_000_000, naux: int = 80, nvec: int = 1,
