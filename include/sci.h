@@ -99,10 +99,10 @@ int sci_destroy(sci_ctx *ctx);
 int sci_set_stream(sci_ctx *ctx, void *cuda_stream);
 
 /* Load the Hamiltonian (Sec. 2.1, Eq. Hamiltonian; Sec. 3.2, IntegralManager).
- *   scalar: SCI_REAL64 or SCI_COMPLEX128.  mode: SCI_SPIN_ORBITALS (n <= 96 spatial
- *   orbitals, real only) or SCI_SPINORS (n <= 192 spinors); above 32 spatial orbitals or
- *   64 spinors the determinant list needs two-word keys, above 64 or 128 three-word keys
- *   (sci_set_determinants_w).
+ *   scalar: SCI_REAL64 or SCI_COMPLEX128.  mode: SCI_SPIN_ORBITALS (n <= 128 spatial
+ *   orbitals, real only) or SCI_SPINORS (n <= 256 spinors); above 32 spatial orbitals or
+ *   64 spinors the determinant list needs two-word keys, above 64 or 128 three-word keys,
+ *   above 96 or 192 four-word keys (sci_set_determinants_w).
  *   h:    host, n*n row-major, h[p*n+q] = h_pq, Hermitian (complex: interleaved re,im).
  *   eri:  host, n^4 row-major, eri[((p*n+q)*n+r)*n+s] = (pq|rs), or NULL.
  *   chol: host, naux*n*n, (pq|rs) = sum_P chol[P][p][q] chol[P][r][s], or NULL.
@@ -137,16 +137,16 @@ int sci_set_integrals_ex(sci_ctx *ctx, int scalar, int mode, int n, const void *
 int sci_set_determinants(sci_ctx *ctx, const uint64_t *keys, int64_t M, int n_alpha,
                          int n_beta, int keys_on_device);
 
-/* The same for occupation strings of more than 64 spin-orbitals or spinors (up to 192):
- * keys are M strings of nwords (1, 2 or 3) 64-bit words, word w holding orbitals
+/* The same for occupation strings of more than 64 spin-orbitals or spinors (up to 256):
+ * keys are M strings of nwords (1 to 4) 64-bit words, word w holding orbitals
  * 64w..64w+63 (the paper keeps an orbital configuration as an array of 64-bit integers,
  * Sec. 3.2), strictly ascending as unsigned (64 x nwords)-bit integers; nwords must cover
  * the orbitals (64 nwords >= 2n, or >= n spinors; SCI_ERR_ARG otherwise).  The bucket keys
  * are then (64 x nwords)-bit, sorted by nwords stable radix passes.  Sigma (every precision
  * mode, deterministic mode included), the diagonal, pair counts, row costs, the connection
  * exports, row ranges (sci_set_row_range) and the density matrices (sci_rdm12,
- * sci_rdm_grads) and ENPT2 (sci_enpt2) work on two- and three-word lists as on one
- * word; batches need one-word keys (SCI_ERR_ARG).  sci_set_determinants (one word) returns
+ * sci_rdm_grads) work on two- to four-word lists as on one word; ENPT2 (sci_enpt2) on
+ * up to three words (SCI_ERR_ARG for four); batches need one-word keys (SCI_ERR_ARG).  sci_set_determinants (one word) returns
  * SCI_ERR_ARG when the orbitals do not fit one word.  Errors as sci_set_determinants. */
 int sci_set_determinants_w(sci_ctx *ctx, const uint64_t *keys, int nwords, int64_t M, int n_alpha,
                            int n_beta, int keys_on_device);
@@ -289,7 +289,7 @@ int sci_kernel_times(sci_ctx *ctx, float *ms, int n);
  *   rdm1[p][q]       = sum_k w_k <c_k| a+_p a_q |c_k>
  *   rdm2[p][q][r][s] = sum_k w_k <c_k| a+_p a+_r a_s a_q |c_k>
  * over the norb = 2n spin-orbitals (spin-orbital mode, bit order of the keys) or the n
- * spinors, norb <= 192 (one- to three-word keys), unnormalised: for a normalised c the
+ * spinors, norb <= 256 (one- to four-word keys), unnormalised: for a normalised c the
  * energy of Eq. Hamiltonian is
  * sum h_pq rdm1_pq + 1/2 sum (pq|rs) rdm2_pqrs (spin-orbital integrals).
  *   C: device, [M][nvec], double (real mode) or complex128 (complex mode), nvec >= 1.
