@@ -25,7 +25,9 @@
 // the row itself); lanes of a warp that share a bucket read the same member, or one of
 // two neighbours (a shared-memory broadcast), and nearby pair-table entries (the table
 // stores bra indices fastest).  A row's partial sum is added to sigma with one FP64
-// atomic add per (bucket, member).
+// atomic add per (bucket, member).  Buckets too large to stage beside a window (above
+// the tile threshold) are walked by k_doubles_tiled instead: 256 members of one bucket as
+// the rows of a CTA, the whole bucket streamed through shared memory in column tiles.
 #include <algorithm>
 #include <cstdio>
 #include <vector>
