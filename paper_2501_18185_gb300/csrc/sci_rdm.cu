@@ -97,8 +97,7 @@ template <int KW> __device__ __forceinline__ bool occ(const Str<KW> &s, int p)
 {
     return (s.w[p >> 6] >> (p & 63)) & 1;
 }
-using Ref3 = sci::RefW;   // the reference string over all words
-inline sci::RefW ref3(const sci_ctx *ctx) { return ref_words(ctx); }
+using sci::RefW;   // the reference string over all words
 
 // Diagonal class: O[p][r] = sum_I w_I n_p n_r in the reference decomposition n = n_ref + d
 // (d = key ^ ref has a few bits), accumulated per CTA in shared memory ([norb]^2 doubles,
@@ -106,7 +105,7 @@ inline sci::RefW ref3(const sci_ctx *ctx) { return ref_words(ctx); }
 // global memory (more orbitals).
 template <typename TC, int KW, bool SM = true>
 __global__ void __launch_bounds__(kThreads)
-k_rdm_diag(const uint64_t *__restrict__ keys, int64_t M, int norb, Ref3 ref,
+k_rdm_diag(const uint64_t *__restrict__ keys, int64_t M, int norb, RefW ref,
            const TC *__restrict__ C, int nvec, int v0, int nv, const double *__restrict__ wk, double *__restrict__ Wt,
            double *__restrict__ D, double *__restrict__ DD)
 {
@@ -162,7 +161,7 @@ k_rdm_diag(const uint64_t *__restrict__ keys, int64_t M, int norb, Ref3 ref,
 template <typename TC, int NV, int KW>
 __global__ void __launch_bounds__(kThreads)
 k_rdm_singles(const uint32_t *__restrict__ e_idx, const uint64_t *__restrict__ e_S, const uint32_t *__restrict__ e_meta,
-              int64_t E, int norb, Ref3 ref, const TC *__restrict__ C, int nvec, int v0,
+              int64_t E, int norb, RefW ref, const TC *__restrict__ C, int nvec, int v0,
               const double *__restrict__ wk, TC *__restrict__ A, TC *__restrict__ Bc)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
@@ -265,10 +264,10 @@ k_rdm_doubles(const uint32_t *__restrict__ e_idx, const uint32_t *__restrict__ e
 // g1 and the g2 elements of the diagonal and single-excitation classes; one thread per
 // (x, y)
 // occupation of orbital k in the reference
-__device__ __forceinline__ double ref_occ(const Ref3 &ref, int k) { return (double)((ref.w[k >> 6] >> (k & 63)) & 1); }
+__device__ __forceinline__ double ref_occ(const RefW &ref, int k) { return (double)((ref.w[k >> 6] >> (k & 63)) & 1); }
 
 template <typename TC>
-__global__ void k_rdm_expand1(int norb, Ref3 ref, const double *__restrict__ Wt,
+__global__ void k_rdm_expand1(int norb, RefW ref, const double *__restrict__ Wt,
                               const double *__restrict__ D, const double *__restrict__ DD, const TC *__restrict__ A,
                               const TC *__restrict__ Bc, TC *__restrict__ g1, TC *__restrict__ g2)
 {
@@ -372,7 +371,7 @@ int launch_walks(sci_ctx *ctx, const Walk<TC> &w)
                   : ctx->nwords == 2 ? k_rdm_singles<TC, NV, 2>
                                      : k_rdm_singles<TC, NV, 1>;
         ks<<<grid_for(ctx->e1), kThreads, 0, ctx->stream>>>(ctx->e1_idx, ctx->e1_S, ctx->e1_meta, ctx->e1, ctx->norb,
-                                                            ref3(ctx), w.C, w.nvec, w.v0, w.wk, w.A, w.Bc);
+                                                            ref_words(ctx), w.C, w.nvec, w.v0, w.wk, w.A, w.Bc);
     }
     if (w.dT) {
         auto kern = k_rdm_doubles<TC, NV>;
@@ -437,7 +436,7 @@ int rdm_run(sci_ctx *ctx, const TC *C, int nvec, const double *wk_dev, TC *g1, T
         return SCI_ERR_CUDA;
     for (int v0 = 0; v0 < nvec; v0 += kv) {
         const int nv = std::min(kv, nvec - v0);
-        kd<<<grid_for(ctx->M), kThreads, diag_smem, ctx->stream>>>(ctx->keys, ctx->M, norb, ref3(ctx), C, nvec, v0,
+        kd<<<grid_for(ctx->M), kThreads, diag_smem, ctx->stream>>>(ctx->keys, ctx->M, norb, ref_words(ctx), C, nvec, v0,
                                                                    nv, wk_dev, Wt, D, DD);
         const Walk<TC> wlk{C, nvec, v0, wk_dev, A, Bc, g2 && ctx->e2 > 0 ? dT : nullptr, CH, stage_bytes(nv), tr, bb_off};
         int rc = SCI_OK;
@@ -453,7 +452,7 @@ int rdm_run(sci_ctx *ctx, const TC *C, int nvec, const double *wk_dev, TC *g1, T
         }
         if (rc) return rc;
     }
-    k_rdm_expand1<TC><<<grid_for(n2), kThreads, 0, ctx->stream>>>(norb, ref3(ctx), Wt, D, DD, A, Bc, g1, g2);
+    k_rdm_expand1<TC><<<grid_for(n2), kThreads, 0, ctx->stream>>>(norb, ref_words(ctx), Wt, D, DD, A, Bc, g1, g2);
     if (g2) k_rdm_expand2<TC><<<grid_for(nT), kThreads, 0, ctx->stream>>>(tr, norb, nT, dT, g2);
     return sci_cuda_check(ctx, cudaGetLastError(), "rdm12 launch") ? SCI_ERR_CUDA : SCI_OK;
 }
