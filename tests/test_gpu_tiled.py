@@ -159,3 +159,38 @@ def test_tile_threshold_errors(gpu):
     H.set_tile_threshold(500)
     assert _rel(H.sigma(C).cpu().numpy(), ref) < TOL
     H.sync_status()
+
+
+@pytest.mark.parametrize("npairs", [513, 1025])
+def test_tile_edges_ragged_row_and_column_tiles(gpu, npairs):
+    """Two electrons in 60 complex spinors on npairs random pairs: one (N-2) bucket of 513
+    (row tiles of 256, 256 and 1) or 1,025 members (five row tiles, and two column tiles of
+    1,024 and 1 split over two CTA rows), against the closed form with one and four
+    vectors, FP64 and paired FP32; the window walk (threshold npairs) agrees, and the
+    deterministic mode (one CTA per row tile) is bit for bit reproducible."""
+    torch = gpu
+    n = 60
+    ints = W.complex_integrals(np.random.default_rng(131), n, 4, 0.9)
+    rng = np.random.default_rng(132)
+    allp = np.array([(p, q) for q in range(n) for p in range(q)])
+    pairs = allp[np.sort(rng.choice(len(allp), npairs, replace=False))]
+    keys = np.array([(1 << int(p)) | (1 << int(q)) for p, q in pairs], dtype=np.uint64)
+    H = sci.Hamiltonian()
+    H.set_integrals("spinors", ints.h, chol=ints.chol)
+    H.set_determinants(keys, 2, -1)
+    assert H.info()["max_bucket"] == npairs
+    H.set_tile_threshold(npairs - 1)           # the one bucket is tiled
+    for nv in (1, 4):
+        c = rng.standard_normal((npairs, nv)) + 1j * rng.standard_normal((npairs, nv))
+        ref = spinor_pair_sigma(ints.h, ints.chol, pairs, c)
+        C = torch.from_numpy(c).cuda()
+        S = H.sigma(C).cpu().numpy()
+        assert _rel(S, ref) < TOL
+        assert _rel(H.sigma(C, prec=sci.SCI_PREC_F64_DS).cpu().numpy(), ref) < TOL
+        H.set_tile_threshold(npairs)           # the window walk
+        assert _rel(H.sigma(C).cpu().numpy(), S) < 1e-13
+        H.set_tile_threshold(npairs - 1)
+    H.set_deterministic(4)
+    a, b = H.sigma(C).cpu().numpy(), H.sigma(C).cpu().numpy()
+    assert np.array_equal(a, b) and _rel(a, ref) < TOL
+    H.sync_status()
