@@ -289,18 +289,20 @@ def test_three_word_enpt2_spinors(gpu):
     H.sync_status()
 
 
-def test_three_word_enpt2_spin_orbitals(gpu):
-    """Real spin-orbital ENPT2 on 70 orbitals (three-word keys: the alpha string crosses
-    words 0/1 and the beta string words 1/2; the generator holds each as two words), 2
-    alpha + 1 beta electrons, HF and 1,500 random determinants: two roots against the
-    oracle's sum over the deduplicated external determinants at 1e-10, the distinct count
-    exact, and a small table (many batches) giving the same sums."""
+@pytest.mark.parametrize("n,m", [(70, 1500), (90, 500)])
+def test_three_word_enpt2_spin_orbitals(gpu, n, m):
+    """Real spin-orbital ENPT2 on 70 and 90 orbitals (three-word keys: the alpha string
+    crosses words 0/1 and the beta string words 1/2; the generator holds each as two words;
+    at 180 spin-orbitals the evaluation reads G from global memory), 2 alpha + 1 beta
+    electrons, HF and m random determinants: two roots against the oracle's sum over the
+    deduplicated external determinants at 1e-10, the distinct count exact, and a small
+    table (many batches) giving the same sums."""
     torch = gpu
-    n, na, nb = 70, 2, 1
+    na, nb = 2, 1
     ints = W.real_integrals(np.random.default_rng(107), n, 4, 0.95)
     rng = np.random.default_rng(108)
     occ = {((0, 1), (0,))}
-    while len(occ) < 1501:
+    while len(occ) < m + 1:
         occ.add((tuple(sorted(rng.choice(n, na, replace=False))), tuple(sorted(rng.choice(n, nb, replace=False)))))
     occ = np.array([list(a) + [b[0] + n] for a, b in sorted(occ)])
     keys = W.sort_words(W.words_from_occ(occ, 3))
