@@ -117,7 +117,6 @@ __device__ __forceinline__ W2 operator&(W2 a, W2 b) { return W2(a.lo & b.lo, a.h
 __device__ __forceinline__ W2 operator|(W2 a, W2 b) { return W2(a.lo | b.lo, a.hi | b.hi); }
 __device__ __forceinline__ W2 operator~(W2 a) { return W2(~a.lo, ~a.hi); }
 __device__ __forceinline__ W2 &operator&=(W2 &a, W2 b) { a.lo &= b.lo, a.hi &= b.hi; return a; }
-__device__ __forceinline__ bool operator==(W2 a, W2 b) { return a.lo == b.lo && a.hi == b.hi; }
 // a - 1 (borrow into the high word)
 __device__ __forceinline__ W2 operator-(W2 a, int one) { return W2(a.lo - (uint64_t)one, a.hi - (a.lo < (uint64_t)one ? 1ull : 0ull)); }
 // logical right shift by 0 <= s < 128
@@ -138,7 +137,6 @@ __device__ __forceinline__ W3 operator&(W3 a, W3 b) { return W3(a.w0 & b.w0, a.w
 __device__ __forceinline__ W3 operator|(W3 a, W3 b) { return W3(a.w0 | b.w0, a.w1 | b.w1, a.w2 | b.w2); }
 __device__ __forceinline__ W3 operator~(W3 a) { return W3(~a.w0, ~a.w1, ~a.w2); }
 __device__ __forceinline__ W3 &operator&=(W3 &a, W3 b) { a.w0 &= b.w0, a.w1 &= b.w1, a.w2 &= b.w2; return a; }
-__device__ __forceinline__ bool operator==(W3 a, W3 b) { return a.w0 == b.w0 && a.w1 == b.w1 && a.w2 == b.w2; }
 // a - 1 (borrows through the words)
 __device__ __forceinline__ W3 operator-(W3 a, int one)
 {
@@ -191,9 +189,7 @@ template <typename K> __device__ __forceinline__ K ref_of(const Pt2 &p)
     else if constexpr (sizeof(K) == 16) return W2(p.ref, p.ref_hi);
     else return W3(p.ref, p.ref_hi, p.ref_w2);
 }
-__device__ __forceinline__ uint64_t key_lo(uint64_t x) { return x; }
 __device__ __forceinline__ uint64_t key_lo(W2 x) { return x.lo; }
-__device__ __forceinline__ uint64_t key_hi(uint64_t) { return 0; }
 __device__ __forceinline__ uint64_t key_hi(W2 x) { return x.hi; }
 __device__ __forceinline__ uint64_t key_lo(W3 x) { return x.w0; }
 __device__ __forceinline__ uint64_t key_hi(W3 x) { return x.w1; }

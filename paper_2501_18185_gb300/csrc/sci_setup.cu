@@ -60,7 +60,6 @@ template <typename T> void free_held(sci_ctx *ctx, T *&p)
     (void)ctx;
 }
 
-__host__ __device__ inline int pair_index(int a, int b) { return b * (b - 1) / 2 + a; }  // a < b
 
 // ------------------------------------------------------------------ scalar helpers
 template <typename S> struct Sc;
