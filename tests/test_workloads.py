@@ -99,3 +99,17 @@ def test_selected_spinor_words_structure():
     assert (lv == 1).sum() == N * (n - N) and (lv == 2).sum() == comb(N, 2) * comb(n - N, 2)
     assert (lv == 3).sum() == M - 1 - N * (n - N) - comb(N, 2) * comb(n - N, 2)
     assert np.isclose(np.linalg.norm(w.c), 1.0)
+
+
+def test_selected_words_four_words():
+    """The general generator at four words: 100 orbitals (beta bits 100..199 over words 1-3),
+    ascending unique keys, 2 + 2 electrons, the level counts of the recipe."""
+    n, na, nb, M = 100, 2, 2, 50000
+    w = W.selected_words(n, na, nb, M, 4, naux=4)
+    ints = _as_ints(w.keys)
+    assert ints == sorted(set(ints)) and len(ints) == M
+    assert (w.keys[:, 3] != 0).any()
+    lv = W.excitation_level_words(w.keys, w.meta["hf_words"])
+    singles = na * (n - na) + nb * (n - nb)
+    doubles = comb(na, 2) * comb(n - na, 2) + comb(nb, 2) * comb(n - nb, 2) + na * (n - na) * nb * (n - nb)
+    assert (lv == 1).sum() == singles and (lv == 2).sum() == doubles and (lv == 3).sum() == M - 1 - singles - doubles
